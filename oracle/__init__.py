@@ -1,0 +1,283 @@
+"""CPU oracle for the particle-mesh-particle cycle -- TEST INFRASTRUCTURE ONLY.
+
+A plain, slow, single-threaded FP64 restatement of He et al. (2025), Sec. 2.2
+(Steps 1-5), Sec. 3.1.1 (sink accretion) and Sec. 3.2.1 (supernova feedback),
+written in C (``pmp_oracle.c``) and driven from here through ctypes.  Only
+``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package; the library never does, and the two
+share no code.
+
+Functions take the (5, field_stride) float64 arrays and particle dicts that
+``paper_2509_18261_gb300.synthetic`` produces, and mutate outputs in place
+where the C function does.
+
+Parity unpinned: the covered fraction omega (its sub-sampling rule) and the
+code-unit constants A_sf, A_p have no printed values in the paper; they are
+pinned only by self-consistency tests (conservation, symmetry, convergence).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "pmp_oracle.c")
+_LIB = os.path.join(_HERE, "_build", "liboracle.so")
+
+KIND = {"feedback": 0, "sink": 1}
+FB_ROWS = ["M_snr", "V_snr", "vcom_x", "vcom_y", "vcom_z", "n_H", "R_M", "p_rad", "q", "e", "Pv", "regime"]
+SK_ROWS = ["rho_inf", "v_inf", "c_inf", "mdot", "r_acc", "sum_w", "K", "n_mem"]
+STATUS = {0: "ok", 1: "bad argument", 2: "particle outside", 3: "non-finite", 4: "out of memory"}
+
+
+class OracleError(RuntimeError):
+    pass
+
+
+def build(force=False):
+    """Compile the oracle (no fused multiply-add, no fast-math)."""
+    os.makedirs(os.path.dirname(_LIB), exist_ok=True)
+    if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC):
+        return _LIB
+    cmd = [
+        "gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fexcess-precision=standard",
+        "-fPIC", "-shared", "-o", _LIB, _SRC, "-lm",
+    ]
+    subprocess.check_call(cmd)
+    return _LIB
+
+
+class Params(ctypes.Structure):
+    _fields_ = [
+        ("kind", ctypes.c_int32), ("subsample", ctypes.c_int32),
+        ("r_K", ctypes.c_double), ("dt", ctypes.c_double), ("G", ctypes.c_double),
+        ("gamma", ctypes.c_double), ("lambda_bh", ctypes.c_double), ("J", ctypes.c_double),
+        ("cap", ctypes.c_double), ("rho_min", ctypes.c_double), ("A_sf", ctypes.c_double),
+        ("A_p", ctypes.c_double), ("mu_H", ctypes.c_double), ("RM_ej", ctypes.c_double),
+        ("RM_st", ctypes.c_double), ("eps_K", ctypes.c_double),
+    ]
+
+
+class Mesh(ctypes.Structure):
+    _fields_ = [
+        ("n", ctypes.c_int32 * 3), ("ng", ctypes.c_int32), ("periodic", ctypes.c_int32 * 3),
+        ("pad_", ctypes.c_int32), ("dx", ctypes.c_double), ("fstride", ctypes.c_int64),
+        ("u", ctypes.POINTER(ctypes.c_double)),
+    ]
+
+
+class Particles(ctypes.Structure):
+    _fields_ = [
+        ("count", ctypes.c_int64),
+        ("x", ctypes.POINTER(ctypes.c_double)), ("y", ctypes.POINTER(ctypes.c_double)),
+        ("z", ctypes.POINTER(ctypes.c_double)), ("m", ctypes.POINTER(ctypes.c_double)),
+        ("px", ctypes.POINTER(ctypes.c_double)), ("py", ctypes.POINTER(ctypes.c_double)),
+        ("pz", ctypes.POINTER(ctypes.c_double)), ("e", ctypes.POINTER(ctypes.c_double)),
+    ]
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        L = ctypes.CDLL(_LIB)
+        dp = ctypes.POINTER(ctypes.c_double)
+        for name in ("or_exp", "or_log"):
+            getattr(L, name).restype = ctypes.c_double
+            getattr(L, name).argtypes = [ctypes.c_double]
+        L.or_pow.restype = ctypes.c_double
+        L.or_pow.argtypes = [ctypes.c_double, ctypes.c_double]
+        L.or_bins_build.restype = ctypes.c_void_p
+        L.or_bins_build.argtypes = [ctypes.POINTER(Mesh), ctypes.POINTER(Particles)]
+        L.or_bins_free.argtypes = [ctypes.c_void_p]
+        L.or_cells_at.argtypes = [ctypes.POINTER(Params), ctypes.POINTER(Mesh), ctypes.POINTER(Particles),
+                                  ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_void_p,
+                                  dp, dp, dp, dp]
+        L.or_sinks_at.argtypes = [ctypes.POINTER(Params), ctypes.POINTER(Mesh), ctypes.POINTER(Particles),
+                                  ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_void_p, dp]
+        L.or_gather_at.argtypes = [ctypes.POINTER(Params), ctypes.POINTER(Mesh), ctypes.POINTER(Particles),
+                                   ctypes.c_int64, ctypes.c_void_p, dp]
+        L.or_kernel_of.argtypes = [ctypes.POINTER(Params), ctypes.POINTER(Mesh), ctypes.c_double,
+                                   ctypes.c_double, ctypes.c_double, ctypes.c_void_p, dp]
+        _lib = L
+    return _lib
+
+
+def _dp(a):
+    if a is None:
+        return None
+    assert a.dtype == np.float64 and a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def make_params(p):
+    return Params(
+        kind=KIND[p["kind"]], subsample=int(p["subsample"]), r_K=p["r_K"], dt=p["dt"], G=p["G"],
+        gamma=p["gamma"], lambda_bh=p["lambda_bh"], J=p["J"], cap=p["cap"], rho_min=p["rho_min"],
+        A_sf=p["A_sf"], A_p=p["A_p"], mu_H=p["mu_H"], RM_ej=p["RM_ej"], RM_st=p["RM_st"], eps_K=p["eps_K"],
+    )
+
+
+def make_mesh(box, arr, dx=1.0, periodic=(1, 1, 1)):
+    assert arr.shape == (5, box.field_stride)
+    return Mesh(n=(ctypes.c_int32 * 3)(*box.n), ng=box.g, periodic=(ctypes.c_int32 * 3)(*periodic),
+                pad_=0, dx=dx, fstride=box.field_stride, u=_dp(arr))
+
+
+def make_particles(p):
+    for k in ("x", "y", "z", "m", "px", "py", "pz", "e"):
+        assert p[k].dtype == np.float64 and p[k].flags["C_CONTIGUOUS"], k
+    return Particles(count=len(p["x"]), x=_dp(p["x"]), y=_dp(p["y"]), z=_dp(p["z"]), m=_dp(p["m"]),
+                     px=_dp(p["px"]), py=_dp(p["py"]), pz=_dp(p["pz"]), e=_dp(p["e"]))
+
+
+def _check(st, what, strict=True):
+    if st and strict:
+        raise OracleError(f"{what}: {STATUS.get(st, st)}")
+    return st
+
+
+def rows(kind):
+    return FB_ROWS if kind == "feedback" else SK_ROWS
+
+
+def exp(x):
+    return lib().or_exp(float(x))
+
+
+def log(x):
+    return lib().or_log(float(x))
+
+
+def gather(params, box, state, parts, dx=1.0, periodic=(1, 1, 1), strict=True):
+    """Gathered per-particle quantities, array [rows][count]."""
+    P = make_params(params)
+    n = len(parts["x"])
+    G = np.zeros((len(rows(params["kind"])), n), dtype=np.float64)
+    S = make_mesh(box, state, dx, periodic)
+    pp = make_particles(parts)
+    st = lib().or_gather(ctypes.byref(P), ctypes.byref(S), ctypes.byref(pp), _dp(G))
+    _check(st, "gather", strict)
+    return G
+
+
+def deposit(params, box, state, parts, gathered, buf, absbuf=None, dx=1.0, periodic=(1, 1, 1), strict=True):
+    """Step 1 into ``buf`` (and sum |dU| into ``absbuf``), in place."""
+    P = make_params(params)
+    S = make_mesh(box, state, dx, periodic)
+    B = make_mesh(box, buf, dx, periodic)
+    pp = make_particles(parts)
+    st = lib().or_deposit(ctypes.byref(P), ctypes.byref(S), ctypes.byref(pp), _dp(gathered), ctypes.byref(B),
+                          _dp(absbuf))
+    return _check(st, "deposit", strict)
+
+
+def fold(box, buf, absbuf=None, periodic=(1, 1, 1)):
+    B = make_mesh(box, buf, 1.0, periodic)
+    _check(lib().or_fold(ctypes.byref(B), _dp(absbuf)), "fold")
+
+
+def return_sinks(params, box, state, buf, parts, gathered, dx=1.0, periodic=(1, 1, 1), strict=True):
+    """Step 4 for sinks: parts['m'], parts['px'..'pz'] updated in place."""
+    P = make_params(params)
+    S = make_mesh(box, state, dx, periodic)
+    B = make_mesh(box, buf, dx, periodic)
+    pp = make_particles(parts)
+    st = lib().or_return_sinks(ctypes.byref(P), ctypes.byref(S), ctypes.byref(B), ctypes.byref(pp), _dp(gathered))
+    return _check(st, "return_sinks", strict)
+
+
+def apply(params, box, state, buf, dx=1.0, periodic=(1, 1, 1), want_eta=False):
+    """Steps 3 + 5 in place on ``state``; returns (eta or None, counts)."""
+    P = make_params(params)
+    S = make_mesh(box, state, dx, periodic)
+    B = make_mesh(box, buf, dx, periodic)
+    eta = np.empty(box.ncells_valid, dtype=np.float64) if want_eta else None
+    counts = np.zeros(2, dtype=np.int64)
+    st = lib().or_apply(ctypes.byref(P), ctypes.byref(S), ctypes.byref(B), _dp(eta),
+                        counts.ctypes.data_as(ctypes.c_void_p))
+    _check(st, "apply")
+    return eta, counts
+
+
+def cycle(params, box, state, parts, dx=1.0, periodic=(1, 1, 1), want_abs=False, want_eta=False):
+    """One full pass (Steps 1-5; Step 4 for sinks).  Mutates ``state`` and, for
+    sinks, the particle mass and momentum.  Returns a dict with the gathered
+    rows, the folded buffer, the |dU| buffer, eta and limiter counts."""
+    G = gather(params, box, state, parts, dx, periodic)
+    buf = box.empty(0.0)
+    absbuf = box.empty(0.0) if want_abs else None
+    deposit(params, box, state, parts, G, buf, absbuf, dx, periodic)
+    pre_fold = buf.copy()
+    fold(box, buf, absbuf, periodic)
+    if params["kind"] == "sink":
+        return_sinks(params, box, state, buf, parts, G, dx, periodic)
+    eta, counts = apply(params, box, state, buf, dx, periodic, want_eta=want_eta)
+    return dict(gathered=G, buf=buf, pre_fold=pre_fold, absbuf=absbuf, eta=eta, counts=counts)
+
+
+class Bins:
+    """Particles binned by host cell, for one-by-one evaluation on big boxes."""
+
+    def __init__(self, box, state, parts, dx=1.0, periodic=(1, 1, 1)):
+        self.box, self.state, self.parts = box, state, parts
+        self.dx, self.periodic = dx, periodic
+        self._S = make_mesh(box, state, dx, periodic)
+        self._p = make_particles(parts)
+        self._h = lib().or_bins_build(ctypes.byref(self._S), ctypes.byref(self._p))
+        if not self._h:
+            raise OracleError("bins: out of memory")
+
+    def __del__(self):
+        if getattr(self, "_h", None):
+            lib().or_bins_free(self._h)
+            self._h = None
+
+    def cells(self, params, ijk):
+        """Summed buffer, |dU| sum, updated state and eta at valid cells ijk (n, 3)."""
+        ijk = np.ascontiguousarray(ijk, dtype=np.int32)
+        n = ijk.shape[0]
+        s = np.empty((n, 5)); a = np.empty((n, 5)); u = np.empty((n, 5)); e = np.empty(n)
+        P = make_params(params)
+        st = lib().or_cells_at(ctypes.byref(P), ctypes.byref(self._S), ctypes.byref(self._p), self._h,
+                               self.box.g, n, ijk.ctypes.data_as(ctypes.c_void_p), _dp(s), _dp(a), _dp(u), _dp(e))
+        _check(st, "cells_at")
+        return s, a, u, e
+
+    def sinks(self, params, sel):
+        """Updated (m, px, py, pz) of the listed sinks, array (n, 4)."""
+        sel = np.ascontiguousarray(sel, dtype=np.int64)
+        out = np.empty((len(sel), 4))
+        P = make_params(params)
+        st = lib().or_sinks_at(ctypes.byref(P), ctypes.byref(self._S), ctypes.byref(self._p), self._h,
+                               self.box.g, len(sel), sel.ctypes.data_as(ctypes.c_void_p), _dp(out))
+        _check(st, "sinks_at")
+        return out
+
+    def gather(self, params, sel):
+        sel = np.ascontiguousarray(sel, dtype=np.int64)
+        G = np.empty((len(rows(params["kind"])), len(sel)))
+        P = make_params(params)
+        st = lib().or_gather_at(ctypes.byref(P), ctypes.byref(self._S), ctypes.byref(self._p), len(sel),
+                                sel.ctypes.data_as(ctypes.c_void_p), _dp(G))
+        _check(st, "gather_at")
+        return G
+
+
+def kernel_of(params, box, x, y, z, periodic=(1, 1, 1)):
+    """Kernel cells (unwrapped ijk, shape (n, 3)) and omega of a particle at (x, y, z)."""
+    R = int(np.ceil(params["r_K"]))
+    w = 2 * R + 1
+    ijk = np.zeros((w ** 3, 3), dtype=np.int32)
+    om = np.zeros(w ** 3)
+    P = make_params(params)
+    dummy = box.empty(0.0)
+    S = make_mesh(box, dummy, 1.0, periodic)
+    n = lib().or_kernel_of(ctypes.byref(P), ctypes.byref(S), x, y, z, ijk.ctypes.data_as(ctypes.c_void_p), _dp(om))
+    return ijk[:n].copy(), om[:n].copy()
