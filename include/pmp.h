@@ -1,0 +1,226 @@
+/*
+ * pmp.h -- C ABI of the particle-mesh-particle (PMP) library for NVIDIA GB300
+ * (sm_103a).
+ *
+ * The library implements the five-step particle-mesh-particle cycle of He,
+ * Wibking, Vijayan, Krumholz & Li, "A novel algorithm for GPU-accelerated
+ * particle-mesh interactions implemented in the Quokka code"
+ * (arXiv:2509.18261), Sec. 2.2, for the two interaction kinds of Sec. 3:
+ * supernova feedback (Sec. 3.2.1) and sink accretion (Sec. 3.1.1).
+ *
+ * Memory.  Every pointer handed to a pmp_* call is a DEVICE pointer owned by
+ * the caller (for example the storage of a torch tensor), except where a
+ * comment says "host".  The library borrows device pointers only for the work
+ * it enqueues and never frees them.  It allocates device memory only in
+ * pmp_create (a few hundred bytes for status words) and frees it in
+ * pmp_destroy.  Scratch memory for the sorted deposit is the caller's
+ * (pmp_workspace_size).
+ *
+ * Streams.  Work is enqueued on the context's stream (pmp_create /
+ * pmp_set_stream) and returns immediately, except where a comment says the
+ * call synchronises.
+ *
+ * Errors.  Argument errors are detected on the host: the call returns a
+ * non-zero pmp_status and enqueues nothing.  Errors found while kernels run
+ * (a particle outside the box, a non-finite or non-positive input) set a
+ * sticky device status word; the affected particle or cell is skipped, no
+ * kernel traps, and pmp_get_error reads and clears the word.
+ *
+ * Mesh layout (pmp_mesh).  Five FP64 fields (rho, p_x, p_y, p_z, E) of a box
+ * of n[0] x n[1] x n[2] valid cells with ng ghost cells on every side.
+ * Field f, cell (i, j, k), -ng <= i < n[0] + ng (likewise j, k), lives at
+ *   data[f * field_stride + ((k + ng) * (n[1] + 2 ng) + (j + ng)) * (n[0] + 2 ng) + (i + ng)].
+ * field_stride >= (n[0] + 2 ng)(n[1] + 2 ng)(n[2] + 2 ng); a multiple of 32
+ * keeps every field 256-byte aligned.  Cells are cubes of side dx; positions
+ * are in cell units, the centre of cell i at i + 1/2.
+ *
+ * The STATE mesh holds the conserved quantities U; only its valid cells are
+ * read or written (ghost cells are never touched; on a periodic axis the
+ * kernel wraps).  The BUFFER mesh holds Delta U^buf (Step 1, Eq.
+ * delta_u_buf); it must have the state's n and periodic flags and
+ * ng >= ceil(r_K), and must not overlap the state.
+ *
+ * Particles (pmp_particles).  Structure-of-arrays FP64, count entries each.
+ *   x, y, z  position in cell units, 0 <= x < n[0] (likewise y, z).
+ *   m        feedback: ejecta mass M_ej; sink: sink mass m_s.
+ *   px..pz   feedback: ejecta momentum M_ej v_ej; sink: sink momentum.
+ *   e        feedback: supernova energy E_sn; sink: unused (may be NULL).
+ * Step 4 (sinks) updates m and p in place.
+ *
+ * Gathered rows.  pmp_gather writes a [rows][count] FP64 array (row r of
+ * particle s at gathered[r * count + s]); rows = pmp_gathered_rows(kind):
+ *   feedback (12): M_snr, V_snr, v_COM x, y, z, n_H, R_M, |p_radial|,
+ *                  q = M_ej/V_snr, e = (E_sn + E_kin)/V_snr, |p_radial|/V_snr,
+ *                  regime (0 EJ, 1 ST, 2 MC)                     (Sec. 3.2.1)
+ *   sink (8):      rho_inf, v_inf, c_inf, mdot_BH, r_acc (cell units), sum w,
+ *                  K = mdot_BH dt / V / sum w, kernel cell count  (Sec. 3.1.1)
+ *
+ * Numerics.  All arithmetic is FP64 with no fused multiply-add, in one fixed
+ * order per quantity, so the sorted deposit is bit-for-bit reproducible
+ * across runs and launch shapes.  exp and log are the library's own
+ * (Cody & Waite reduction plus a Taylor / atanh series).
+ */
+#ifndef PMP_H
+#define PMP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pmp_ctx pmp_ctx;
+typedef struct CUstream_st *pmp_stream; /* a cudaStream_t; NULL = legacy default stream */
+
+typedef enum {
+    PMP_OK = 0,
+    PMP_ERR_ARG = 1,              /* invalid argument (host check; nothing enqueued) */
+    PMP_ERR_GHOST_TOO_THIN = 2,   /* buffer ng < ceil(r_K), or ng > n on some axis */
+    PMP_ERR_PARTICLE_OUTSIDE = 3, /* device: a position outside [0, n) */
+    PMP_ERR_NONFINITE = 4,        /* device: NaN/Inf or a non-positive mass/density */
+    PMP_ERR_TIMEOUT = 5,          /* device: a bounded wait gave up */
+    PMP_ERR_WORKSPACE = 6,        /* workspace missing or smaller than pmp_workspace_size */
+    PMP_ERR_CUDA = 7              /* a CUDA runtime call failed */
+} pmp_status;
+
+typedef enum { PMP_KIND_FEEDBACK = 0, PMP_KIND_SINK = 1 } pmp_kind;
+
+/* Step-1 accumulation strategy.
+ * ATOMIC: FP64 atomic additions (Sec. 2.2, Step 1); per cell the sum equals
+ *         the sorted one up to the order of additions.
+ * SORTED: (cell, particle) pairs sorted by cell, then each cell summed in
+ *         particle-index order; deterministic. */
+typedef enum { PMP_MODE_ATOMIC = 0, PMP_MODE_SORTED = 1 } pmp_mode;
+
+typedef struct {
+    int32_t n[3];        /* valid cells per axis, >= 1 */
+    int32_t ng;          /* ghost cells on each side, >= 0 */
+    int32_t periodic[3]; /* 1 = axis wraps; 0 = kernel cut at the domain face */
+    int32_t reserved;    /* set to 0 */
+    double dx;           /* cell size (physical units); V = dx^3 */
+    int64_t field_stride;/* doubles between consecutive fields */
+    double *data;        /* device, [5][field_stride] */
+} pmp_mesh;
+
+typedef struct {
+    int64_t count;
+    const double *x, *y, *z; /* device */
+    double *m;               /* device */
+    double *px, *py, *pz;    /* device */
+    const double *e;         /* device; feedback only */
+} pmp_particles;
+
+/* Parameters of one interaction kind.  Units are the caller's (code units). */
+typedef struct {
+    int32_t kind;      /* pmp_kind */
+    int32_t subsample; /* feedback: sub-points per axis (1..8) for the covered
+                          fraction omega of a kernel cell (Sec. 3.2.1) */
+    double r_K;        /* kernel radius in cells, 1 <= r_K <= 6 (Sec. 2.1) */
+    double dt;         /* sink: time step (Eq. accretion_function) */
+    double G;          /* sink: gravitational constant (Eq. rbh, Eq. truelove) */
+    double gamma;      /* adiabatic index, > 1 */
+    double lambda_bh;  /* sink: lambda of Eq. mdot (e^1.5 / 4 in the paper) */
+    double J;          /* sink: Jeans number of Eq. truelove (0.25) */
+    double cap;        /* sink: largest removed fraction of a cell's mass (0.25) */
+    double rho_min;    /* sink: density floor */
+    double A_sf;       /* feedback: M_sf = A_sf n_H^-0.26 */
+    double A_p;        /* feedback: P_snr = A_p n_H^-0.17 (Eq. psnr) */
+    double mu_H;       /* feedback: mass per H nucleus */
+    double RM_ej;      /* feedback: EJ if R_M <= RM_ej (0.027) */
+    double RM_st;      /* feedback: ST if RM_ej < R_M <= RM_st (1), else MC */
+    double eps_K;      /* feedback: kinetic fraction of Eq. dp (0.28) */
+} pmp_params;
+
+/* Creates a context for one interaction kind; validates params (returns
+ * PMP_ERR_ARG on a bad value) and allocates its device status words on the
+ * current device.  *out is set to NULL on failure. */
+pmp_status pmp_create(pmp_ctx **out, const pmp_params *params, pmp_stream stream);
+
+/* Frees the context (synchronises its stream first).  NULL is ignored. */
+void pmp_destroy(pmp_ctx *ctx);
+
+/* Changes the stream later calls enqueue on. */
+pmp_status pmp_set_stream(pmp_ctx *ctx, pmp_stream stream);
+
+/* Number of gathered rows for a kind (12 feedback, 8 sink); 0 if unknown. */
+int32_t pmp_gathered_rows(int32_t kind);
+
+/* Bytes of device workspace pmp_deposit needs for `mode` with this buffer and
+ * this many particles (0 for PMP_MODE_ATOMIC).  Host only, no device work. */
+pmp_status pmp_workspace_size(const pmp_ctx *ctx, const pmp_mesh *buffer, int64_t n_particles, int32_t mode,
+                              size_t *bytes);
+
+/* Step 1, preparation: Delta U^buf = 0 on every cell of the buffer, ghosts
+ * included (Sec. 2.2, Step 1: "all cells initialized to zero"). */
+pmp_status pmp_zero_buffer(pmp_ctx *ctx, pmp_mesh *buffer);
+
+/* Particle side of Step 1: the per-particle quantities the deposition
+ * function needs, summed over the particle's kernel cells in a fixed order
+ * (z slowest, x fastest): M_snr, V_snr, v_COM, n_H, R_M and |p_radial| for
+ * feedback (Sec. 3.2.1); rho_inf, v_inf, c_inf, r_BH -> mdot_BH (Eq. mdot),
+ * r_acc and sum w (Eq. kernel, Eq. kernel_wgt) for sinks (Sec. 3.1.1).
+ * gathered: device, [rows][count]; particles outside the box get zero rows
+ * and set PMP_ERR_PARTICLE_OUTSIDE. */
+pmp_status pmp_gather(pmp_ctx *ctx, const pmp_mesh *state, const pmp_particles *particles, double *gathered);
+
+/* Step 1 (Eq. delta_u_buf): every particle adds its deposition function
+ * Delta U^s (Eq. du for feedback; Eq. accretion_function for sinks, the
+ * removal entering with a minus sign) to every kernel cell of the buffer,
+ * ghost zones included, on top of what the buffer holds.  ATOMIC uses FP64
+ * atomics; SORTED needs `workspace` of pmp_workspace_size bytes (device,
+ * 256-byte aligned) and synchronises the stream once to read the pair count.
+ * Kernel cells with omega = 0 receive nothing. */
+pmp_status pmp_deposit(pmp_ctx *ctx, const pmp_mesh *state, const pmp_particles *particles, const double *gathered,
+                       pmp_mesh *buffer, int32_t mode, void *workspace, size_t workspace_bytes);
+
+/* Step 2 on one GPU (Sec. 2.2, Step 2): each ghost cell of the buffer is added
+ * to the valid cell that owns it (periodic axes only); a valid cell with
+ * several images sums them in the fixed order of App. A.2 taken as the
+ * lexicographic order of the image offset (oz, oy, ox) in {-1,0,1}^3:
+ * ((B_c + B_img1) + B_img2) + ...  Ghost cells are left as they were.
+ * Needs ng <= n on every periodic axis. */
+pmp_status pmp_fold_ghosts(pmp_ctx *ctx, pmp_mesh *buffer);
+
+/* Steps 3-5 (Sec. 2.2): the cell-wise limiter eta = f_lim(U, Delta U^sum)/
+ * Delta U^sum, then for sinks Step 4 -- u_s := u_s - sum_c eta_c Delta U^s_c V,
+ * with Delta U^s recomputed and eta of a ghost image taken from its owner --
+ * and finally Step 5, U := U + eta Delta U^sum on every valid cell.
+ * Feedback: the momentum limiter of Eq. lambda, eta = (1, l, l, l, 1);
+ *   `particles` and `gathered` may be NULL (Step 4 is skipped, Sec. 3.2.1).
+ * Sink: the accretion limiter of Sec. 3.1.1 with the 25% cap (params.cap),
+ *   the Truelove floor and the density floor rho_min; the same eta for all
+ *   fields; `particles`/`gathered` are those of pmp_gather.
+ * eta_out: optional device array, one FP64 per valid cell (x fastest): the
+ *   momentum eta (feedback) or the common eta (sink). */
+pmp_status pmp_apply_limited(pmp_ctx *ctx, pmp_mesh *state, const pmp_mesh *buffer, pmp_particles *particles,
+                             const double *gathered, double *eta_out);
+
+/* Adjoint of one feedback pass (gather, deposit, fold, limited apply) with
+ * respect to the particle inputs, for a loss L whose gradient with respect to
+ * the updated state is gU (device, a [5][field_stride] array laid out like
+ * the state; ghosts ignored).  The limited apply is differentiated with eta
+ * held fixed, and cells where the limiter is active (eta < 1) pass no
+ * gradient.  The kernel cell set and omega are piecewise constant in
+ * position and contribute no derivative.  Weights are recomputed, not
+ * stored.  g_out: device [8][count] = dL/d(m, e, px, py, pz, x, y, z).
+ * `state_in` is the state BEFORE the apply; `buffer` the folded buffer;
+ * `gathered` from pmp_gather.  Feedback contexts only. */
+pmp_status pmp_backward(pmp_ctx *ctx, const pmp_mesh *state_in, const pmp_mesh *buffer, const pmp_particles *particles,
+                        const double *gathered, const double *gU, double *g_out);
+
+/* Synchronises the context's stream, then returns the first device error
+ * since the last call (PMP_OK if none) in *code and the index of the
+ * offending particle or cell in *index (-1 if none), and clears them. */
+pmp_status pmp_get_error(pmp_ctx *ctx, int32_t *code, int64_t *index);
+
+/* Synchronises the stream and reads the counters of the last
+ * pmp_apply_limited (host array of 2): cells with eta < 1, and feedback cells
+ * for which Eq. lambda had no root in [0, 1] (lambda set to 0). */
+pmp_status pmp_limiter_counts(pmp_ctx *ctx, int64_t *counts);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PMP_H */

@@ -1,0 +1,375 @@
+// pmp_device.cuh -- device-side building blocks of the PMP library (sm_103a).
+//
+// Everything here is FP64 and is compiled with -fmad=false: each product and
+// sum is rounded on its own, in the order written, so that one quantity has
+// one value whichever kernel computes it (gather, deposit, sorted segment sum,
+// Step 4).  That fixed order is the contract that makes the sorted deposit
+// deterministic.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "pmp.h"
+
+namespace pmp {
+
+constexpr int NF = 5;
+constexpr double kPi = 3.141592653589793;
+constexpr int kMaxR = 6;
+constexpr int kMaxS = 8;
+
+// Geometry of one mesh as the kernels see it.
+struct Box {
+    int n0, n1, n2, g;
+    int per0, per1, per2, pad_;
+    long long px, pxy;  // padded row length and padded plane size
+    long long fs;       // field stride (doubles)
+    long long ncells;   // padded cell count
+
+    __host__ __device__ __forceinline__ long long at(int i, int j, int k) const
+    {
+        return (long long)(k + g) * pxy + (long long)(j + g) * px + (long long)(i + g);
+    }
+};
+
+// Parameters with the derived constants each formula uses, all computed on
+// the host in the same order as the formulas below state them.
+struct KParams {
+    double rK, r2;   // r_K, r_K * r_K
+    double dt, G;
+    double gg;       // gamma * (gamma - 1)
+    double lam2;     // lambda_bh * lambda_bh
+    double ctr;      // ((J * J) * pi) / (G * (dx * dx)): rho_Tr = ctr c_s^2
+    double cap, rho_min;
+    double A_sf, A_p, mu_H, RM_ej, RM_st, eps_K;
+    double V, dx;    // V = (dx * dx) * dx
+    double four_pi;  // 4 * pi
+    int S, S3, R, kind;
+};
+
+struct Parts {
+    long long count;
+    const double *x, *y, *z;
+    double *m, *px, *py, *pz;
+    const double *e;
+};
+
+// Device status words of a context.
+struct DevStatus {
+    int code;
+    int pad_;
+    long long index;
+    unsigned long long n_limited;
+    unsigned long long n_noroot;
+};
+
+__device__ __forceinline__ void report(DevStatus *st, int code, long long index)
+{
+    if (atomicCAS(&st->code, 0, code) == 0) st->index = index;
+}
+
+__device__ __forceinline__ int wrapi(int i, int n)
+{
+    int r = i % n;
+    return r < 0 ? r + n : r;
+}
+
+// ---------------------------------------------------------------------------
+// exp and log (the library's own; see pmp.h)
+// ---------------------------------------------------------------------------
+
+// ln 2 = 0.6931471805599453094172321...: kLn2Hi holds its leading 32
+// significant bits (so k * kLn2Hi is exact for |k| < 2^21), kLn2Lo the rest
+// rounded to double.
+constexpr double kLn2Hi = 6.93147180369123816490e-01;
+constexpr double kLn2Lo = 1.90821492927058770002e-10;
+constexpr double kInvLn2 = 1.44269504088896338700e+00;
+
+__host__ __device__ constexpr double fact_d(int j) { return j <= 1 ? 1.0 : (double)j * fact_d(j - 1); }
+
+// 2^k for -1022 <= k <= 1023 (exact).
+__device__ __forceinline__ double two_to(int k) { return __longlong_as_double((long long)(k + 1023) << 52); }
+
+// exp(x) by Cody & Waite reduction x = k ln2 + r (|r| <= ln2 / 2), the
+// degree-13 Taylor polynomial of e^r in Horner form (coefficients 1/j!,
+// correctly rounded; j! is exact), and scaling by 2^k.
+__device__ __forceinline__ double pmp_exp(double x)
+{
+    if (x != x) return x;
+    if (x > 709.79) return __longlong_as_double(0x7ff0000000000000LL);
+    if (x < -745.2) return 0.0;
+    const double kd = floor(x * kInvLn2 + 0.5);
+    const int k = (int)kd;
+    const double r = (x - kd * kLn2Hi) - kd * kLn2Lo;
+    constexpr double c13 = 1.0 / fact_d(13), c12 = 1.0 / fact_d(12), c11 = 1.0 / fact_d(11),
+                     c10 = 1.0 / fact_d(10), c9 = 1.0 / fact_d(9), c8 = 1.0 / fact_d(8), c7 = 1.0 / fact_d(7),
+                     c6 = 1.0 / fact_d(6), c5 = 1.0 / fact_d(5), c4 = 1.0 / fact_d(4), c3 = 1.0 / fact_d(3),
+                     c2 = 1.0 / fact_d(2);
+    double p = c13;
+    p = p * r + c12;
+    p = p * r + c11;
+    p = p * r + c10;
+    p = p * r + c9;
+    p = p * r + c8;
+    p = p * r + c7;
+    p = p * r + c6;
+    p = p * r + c5;
+    p = p * r + c4;
+    p = p * r + c3;
+    p = p * r + c2;
+    p = p * r + 1.0;
+    p = p * r + 1.0;
+    if (k < -1000) return (p * two_to(k + 200)) * two_to(-200);
+    if (k > 1000) return (p * two_to(k - 200)) * two_to(200);
+    return p * two_to(k);
+}
+
+// log(x), x > 0: x = 2^e (1 + f), 1 + f in [sqrt(1/2), sqrt(2)); with
+// s = f / (2 + f), z = s^2, R = sum_{j=1..11} 2 z^j / (2j + 1) and hf = f^2/2,
+// log(1 + f) = 2 atanh(s) = f - (hf - s (hf + R)); log x = e ln2 + log(1 + f)
+// with the small terms added first.
+__device__ __forceinline__ double pmp_log(double x)
+{
+    if (x != x || x < 0.0) return __longlong_as_double(0x7ff8000000000000LL);
+    if (x == 0.0) return __longlong_as_double(0xfff0000000000000LL);
+    if (isinf(x)) return x;
+    int e;
+    double m = frexp(x, &e);  // exact: x = m 2^e, m in [0.5, 1)
+    m = m * 2.0;
+    e = e - 1;
+    if (m > 1.4142135623730951) {
+        m = m * 0.5;
+        e = e + 1;
+    }
+    const double f = m - 1.0;
+    const double s = f / (2.0 + f);
+    const double z = s * s;
+    double R = 2.0 / 23.0;
+    R = R * z + 2.0 / 21.0;
+    R = R * z + 2.0 / 19.0;
+    R = R * z + 2.0 / 17.0;
+    R = R * z + 2.0 / 15.0;
+    R = R * z + 2.0 / 13.0;
+    R = R * z + 2.0 / 11.0;
+    R = R * z + 2.0 / 9.0;
+    R = R * z + 2.0 / 7.0;
+    R = R * z + 2.0 / 5.0;
+    R = R * z + 2.0 / 3.0;
+    R = R * z;
+    const double hf = 0.5 * (f * f);
+    const double ed = (double)e;
+    return ed * kLn2Hi - ((hf - (s * (hf + R) + ed * kLn2Lo)) - f);
+}
+
+__device__ __forceinline__ double pmp_pow(double x, double a) { return pmp_exp(a * pmp_log(x)); }
+
+// ---------------------------------------------------------------------------
+// per-cell formulas
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ void load_cell(const double *__restrict__ u, const Box &B, long long c, double U[NF])
+{
+#pragma unroll
+    for (int f = 0; f < NF; ++f) U[f] = __ldg(u + (long long)f * B.fs + c);
+}
+
+// Ideal-gas c_s^2 = gamma (gamma - 1) e_int / rho, e_int = E - |p|^2 / (2 rho)
+// clamped at 0; c_s; and rho_Tr = J^2 pi c_s^2 / (G dx^2) (Eq. truelove).
+__device__ __forceinline__ void sink_cell(const KParams &P, const double U[NF], double &cs, double &rho_tr)
+{
+    const double ke2 = (U[1] * U[1] + U[2] * U[2]) + U[3] * U[3];
+    double eint = U[4] - ke2 / (2.0 * U[0]);
+    if (eint < 0.0) eint = 0.0;
+    const double cs2 = (P.gg * eint) / U[0];
+    cs = sqrt(cs2);
+    rho_tr = P.ctr * cs2;
+}
+
+__device__ __forceinline__ double sink_rho_tr(const KParams &P, const double U[NF])
+{
+    const double ke2 = (U[1] * U[1] + U[2] * U[2]) + U[3] * U[3];
+    double eint = U[4] - ke2 / (2.0 * U[0]);
+    if (eint < 0.0) eint = 0.0;
+    const double cs2 = (P.gg * eint) / U[0];
+    return P.ctr * cs2;
+}
+
+// Accretion limiter of Sec. 3.1.1 composed with the density floor, on the
+// removal a = -drho: a_lim = max(0, min(max(min(a, cap rho), rho - rho_Tr),
+// rho - rho_min)), eta = a_lim / a if a_lim < a else 1.  When a <= cap rho and
+// a <= rho - rho_min, a_lim >= a follows from the definition, so eta = 1
+// without computing rho_Tr.
+__device__ __forceinline__ double sink_eta(const KParams &P, const double U[NF], const double D[NF])
+{
+    const double a = -D[0];
+    if (!(a > 0.0)) return 1.0;
+    const double rho = U[0];
+    const double capr = P.cap * rho;
+    const double fl = rho - P.rho_min;
+    if (a <= capr && a <= fl) return 1.0;
+    const double rtr = sink_rho_tr(P, U);
+    double al = a < capr ? a : capr;
+    const double t = rho - rtr;
+    al = al > t ? al : t;
+    al = al < fl ? al : fl;
+    if (al < 0.0) al = 0.0;
+    return al < a ? al / a : 1.0;
+}
+
+// Supernova momentum limiter (Eq. lambda) with T the pre-deposit temperature:
+// lambda = 1 if the constraint holds at 1; otherwise the largest root in
+// [0, 1] of |dp|^2 l^2 + 2 (p . dp) l + |p|^2 - 2 rho' (E' - e_int0 rho'/rho),
+// from the cancellation-free quadratic formula (Press et al., Numerical
+// Recipes, Sec. 5.6); 0 if there is none (noroot set).
+__device__ __forceinline__ double sn_lambda(const double U[NF], const double D[NF], int &noroot)
+{
+    noroot = 0;
+    if (D[1] == 0.0 && D[2] == 0.0 && D[3] == 0.0) return 1.0;
+    const double rho1 = U[0] + D[0];
+    const double E1 = U[4] + D[4];
+    const double p2 = (U[1] * U[1] + U[2] * U[2]) + U[3] * U[3];
+    const double eint0 = U[4] - p2 / (2.0 * U[0]);
+    const double pn0 = U[1] + D[1], pn1 = U[2] + D[2], pn2 = U[3] + D[3];
+    const double pnn = (pn0 * pn0 + pn1 * pn1) + pn2 * pn2;
+    const double therm = (eint0 * rho1) / U[0];
+    const double lhs = therm + pnn / (2.0 * rho1);
+    if (lhs <= E1) return 1.0;
+    const double A = (D[1] * D[1] + D[2] * D[2]) + D[3] * D[3];
+    if (!(A > 0.0)) return 1.0;
+    const double B = (U[1] * D[1] + U[2] * D[2]) + U[3] * D[3];
+    const double C = p2 - (2.0 * rho1) * (E1 - therm);
+    const double disc = B * B - A * C;
+    if (!(disc >= 0.0)) {
+        noroot = 1;
+        return 0.0;
+    }
+    const double sq = sqrt(disc);
+    double hi, lo;
+    if (B >= 0.0) {
+        const double Q = -(B + sq);
+        hi = Q != 0.0 ? C / Q : 0.0;
+        lo = Q / A;
+    } else {
+        const double Q = sq - B;
+        hi = Q / A;
+        lo = C / Q;
+    }
+    if (hi < 0.0 || lo > 1.0) {
+        noroot = 1;
+        return 0.0;
+    }
+    return hi < 1.0 ? hi : 1.0;
+}
+
+// ---------------------------------------------------------------------------
+// kernel geometry of one particle
+// ---------------------------------------------------------------------------
+
+// Per-axis data of a particle's kernel: for offset o in [-R, R] the unwrapped
+// cell c = host + o, its owning valid index, whether it is inside the domain
+// (always on a periodic axis), and the centre offset d = (c + 1/2) - x.
+template <int R>
+struct Axis {
+    static constexpr int W = 2 * R + 1;
+    int c[W];
+    int w[W];
+    bool in[W];
+    double d[W];
+    double sq[W];
+
+    __device__ __forceinline__ void init(double x, int n, int per)
+    {
+        const int h = (int)floor(x);
+#pragma unroll
+        for (int o = 0; o < W; ++o) {
+            const int ci = h + o - R;
+            c[o] = ci;
+            w[o] = wrapi(ci, n);
+            in[o] = per || (ci >= 0 && ci < n);
+            d[o] = ((double)ci + 0.5) - x;
+            sq[o] = d[o] * d[o];
+        }
+    }
+};
+
+// Sub-points per axis of a cell for the covered fraction: ((c + (a + 1/2)/S) - x)^2.
+__device__ __forceinline__ void sub_squares(int S, int c, double x, double out[kMaxS])
+{
+    for (int a = 0; a < S; ++a) {
+        const double t = ((double)c + ((double)a + 0.5) / (double)S) - x;
+        out[a] = t * t;
+    }
+}
+
+// Number of the S^3 sub-points of cell (ci, cj, ck) strictly inside r_K.  A
+// cell whose farthest corner is inside has all S^3 (each sub-point offset is
+// bounded by the corner offset, and rounding is monotone).
+__device__ __forceinline__ int covered_count(const KParams &P, int ci, int cj, int ck, double x, double y, double z)
+{
+    const int S = P.S;
+    {
+        const double ax0 = fabs((double)ci - x), ax1 = fabs(((double)ci + 1.0) - x);
+        const double ay0 = fabs((double)cj - y), ay1 = fabs(((double)cj + 1.0) - y);
+        const double az0 = fabs((double)ck - z), az1 = fabs(((double)ck + 1.0) - z);
+        const double fx = ax0 > ax1 ? ax0 : ax1, fy = ay0 > ay1 ? ay0 : ay1, fz = az0 > az1 ? az0 : az1;
+        if ((fx * fx + fy * fy) + fz * fz < P.r2) return P.S3;
+    }
+    double sx[kMaxS], sy[kMaxS], sz[kMaxS];
+    sub_squares(S, ci, x, sx);
+    sub_squares(S, cj, y, sy);
+    sub_squares(S, ck, z, sz);
+    int cnt = 0;
+    for (int c = 0; c < S; ++c)
+        for (int b = 0; b < S; ++b) {
+            for (int a = 0; a < S; ++a) cnt += ((sx[a] + sy[b]) + sz[c] < P.r2) ? 1 : 0;
+        }
+    return cnt;
+}
+
+// Feedback deposition function (Eq. du, with omega on every row; see pmp.h).
+// G points at the particle's gathered row 0 with row stride gs.
+__device__ __forceinline__ void feedback_delta(double w, const double U[NF], double q, double e, double Pv,
+                                               const double vc[3], double d0, double d1, double d2, double dd,
+                                               double dU[NF])
+{
+    const double rn = U[0] + q;
+    const double dist = sqrt(dd);
+    const double s = dd > 0.0 ? (w * Pv) / dist : 0.0;
+    const double pr0 = s * d0, pr1 = s * d1, pr2 = s * d2;
+    dU[0] = w * q;
+    dU[1] = w * (rn * vc[0] - U[1]) + pr0;
+    dU[2] = w * (rn * vc[1] - U[2]) + pr1;
+    dU[3] = w * (rn * vc[2] - U[3]) + pr2;
+    dU[4] = w * e + ((vc[0] * pr0 + vc[1] * pr1) + vc[2] * pr2);
+}
+
+// Sink deposition function (Eq. accretion_function with the Truelove rate in
+// the max): a = max(K w, rho - rho_Tr), Delta U = -a (1, p/rho, E/rho).
+__device__ __forceinline__ void sink_delta(const KParams &P, const double U[NF], double K, double w, double dU[NF])
+{
+    const double rtr = sink_rho_tr(P, U);
+    const double bh = K * w;
+    const double tr = U[0] - rtr;
+    const double a = bh >= tr ? bh : tr;
+    dU[0] = -a;
+    dU[1] = -(a * (U[1] / U[0]));
+    dU[2] = -(a * (U[2] / U[0]));
+    dU[3] = -(a * (U[3] / U[0]));
+    dU[4] = -(a * (U[4] / U[0]));
+}
+
+// Gathered-row indices.
+enum { FB_MSNR = 0, FB_VSNR, FB_VX, FB_VY, FB_VZ, FB_NH, FB_RM, FB_PRAD, FB_Q, FB_E, FB_PV, FB_REGIME, FB_ROWS };
+enum { SK_RHO = 0, SK_VINF, SK_CINF, SK_MDOT, SK_RACC, SK_SUMW, SK_K, SK_NMEM, SK_ROWS };
+
+// Position check: 0 <= x < n on each axis (NaN fails).
+__device__ __forceinline__ int position_status(const Box &B, double x, double y, double z)
+{
+    if (!(x == x && y == y && z == z)) return PMP_ERR_NONFINITE;
+    if (!(x >= 0.0 && x < (double)B.n0 && y >= 0.0 && y < (double)B.n1 && z >= 0.0 && z < (double)B.n2))
+        return PMP_ERR_PARTICLE_OUTSIDE;
+    return PMP_OK;
+}
+
+}  // namespace pmp

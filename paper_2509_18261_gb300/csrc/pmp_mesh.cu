@@ -1,0 +1,159 @@
+// pmp_mesh.cu -- cell-side kernels: buffer zeroing, the ghost fold (Step 2 on
+// one GPU) and the limited apply (Steps 3 + 5).
+#include "pmp_device.cuh"
+#include "pmp_launch.h"
+
+namespace pmp {
+
+// Zero fields [0, 5) over cells [0, ncells), 16-byte stores where aligned.
+__global__ void __launch_bounds__(256) k_zero(double *__restrict__ b, long long fs, long long ncells)
+{
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    for (int f = 0; f < NF; ++f) {
+        double *base = b + (long long)f * fs;
+        const long long head = (reinterpret_cast<uintptr_t>(base) & 15) ? 1 : 0;
+        const long long nvec = (ncells - head) / 2;
+        double2 *v = reinterpret_cast<double2 *>(base + head);
+        for (long long i = tid; i < nvec; i += stride) v[i] = make_double2(0.0, 0.0);
+        if (tid == 0) {
+            if (head) base[0] = 0.0;
+            if (head + 2 * nvec < ncells) base[ncells - 1] = 0.0;
+        }
+    }
+}
+
+// Step 2: one warp per valid row (j, k).  Rows inside the y and z ghost
+// shells are folded whole; other rows only at the x ends.  Images are added
+// in lexicographic order of (oz, oy, ox).
+__global__ void __launch_bounds__(256) k_fold(Box B, double *__restrict__ b)
+{
+    const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    const long long nrows = (long long)B.n1 * B.n2;
+    if (warp >= nrows) return;
+    const int j = (int)(warp % B.n1), k = (int)(warp / B.n1);
+    const int g = B.g;
+    const bool yz_shell = (B.per1 && (j < g || j >= B.n1 - g)) || (B.per2 && (k < g || k >= B.n2 - g));
+    int ends = 0;  // cells per end of the row to visit
+    if (yz_shell) ends = B.n0;
+    else if (B.per0) ends = g < B.n0 ? g : B.n0;
+    else return;
+    const int nvisit = yz_shell ? B.n0 : (2 * ends < B.n0 ? 2 * ends : B.n0);
+    for (int t = lane; t < nvisit; t += 32) {
+        int i;
+        if (yz_shell || 2 * ends >= B.n0) i = t;
+        else i = t < ends ? t : B.n0 - 2 * ends + t;
+        const long long c = B.at(i, j, k);
+        double v[NF];
+#pragma unroll
+        for (int f = 0; f < NF; ++f) v[f] = b[(long long)f * B.fs + c];
+        for (int oz = -1; oz <= 1; ++oz) {
+            if (oz && !B.per2) continue;
+            const int gk = k + oz * B.n2;
+            if (gk < -g || gk >= B.n2 + g) continue;
+            for (int oy = -1; oy <= 1; ++oy) {
+                if (oy && !B.per1) continue;
+                const int gj = j + oy * B.n1;
+                if (gj < -g || gj >= B.n1 + g) continue;
+                for (int ox = -1; ox <= 1; ++ox) {
+                    if (ox && !B.per0) continue;
+                    if (!ox && !oy && !oz) continue;
+                    const int gi = i + ox * B.n0;
+                    if (gi < -g || gi >= B.n0 + g) continue;
+                    const long long im = B.at(gi, gj, gk);
+#pragma unroll
+                    for (int f = 0; f < NF; ++f) v[f] = v[f] + b[(long long)f * B.fs + im];
+                }
+            }
+        }
+#pragma unroll
+        for (int f = 0; f < NF; ++f) b[(long long)f * B.fs + c] = v[f];
+    }
+}
+
+// Steps 3 + 5 for feedback: eta = (1, l, l, l, 1) from Eq. lambda.
+__global__ void __launch_bounds__(256) k_apply_fb(Box S, double *__restrict__ u, Box B, const double *__restrict__ b,
+                                                  double *__restrict__ eta_out, DevStatus *st)
+{
+    const long long nvalid = (long long)S.n0 * S.n1 * S.n2;
+    const long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    int lim = 0, nr = 0;
+    if (v < nvalid) {
+        const int i = (int)(v % S.n0);
+        const long long r = v / S.n0;
+        const int j = (int)(r % S.n1), k = (int)(r / S.n1);
+        const long long cs = S.at(i, j, k), cb = B.at(i, j, k);
+        double U[NF], D[NF];
+#pragma unroll
+        for (int f = 0; f < NF; ++f) {
+            U[f] = u[(long long)f * S.fs + cs];
+            D[f] = __ldg(b + (long long)f * B.fs + cb);
+        }
+        const double l = sn_lambda(U, D, nr);
+        lim = l < 1.0;
+        if (eta_out) eta_out[v] = l;
+        u[cs] = U[0] + D[0];
+        u[S.fs + cs] = U[1] + l * D[1];
+        u[2 * S.fs + cs] = U[2] + l * D[2];
+        u[3 * S.fs + cs] = U[3] + l * D[3];
+        u[4 * S.fs + cs] = U[4] + D[4];
+    }
+    const unsigned m1 = __ballot_sync(0xffffffffu, lim), m2 = __ballot_sync(0xffffffffu, nr);
+    if ((threadIdx.x & 31) == 0) {
+        if (m1) atomicAdd(&st->n_limited, (unsigned long long)__popc(m1));
+        if (m2) atomicAdd(&st->n_noroot, (unsigned long long)__popc(m2));
+    }
+}
+
+// Steps 3 + 5 for sinks: one eta for all five fields.
+__global__ void __launch_bounds__(256) k_apply_sink(KParams P, Box S, double *__restrict__ u, Box B,
+                                                    const double *__restrict__ b, double *__restrict__ eta_out,
+                                                    DevStatus *st)
+{
+    const long long nvalid = (long long)S.n0 * S.n1 * S.n2;
+    const long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    int lim = 0;
+    if (v < nvalid) {
+        const int i = (int)(v % S.n0);
+        const long long r = v / S.n0;
+        const int j = (int)(r % S.n1), k = (int)(r / S.n1);
+        const long long cs = S.at(i, j, k), cb = B.at(i, j, k);
+        double U[NF], D[NF];
+#pragma unroll
+        for (int f = 0; f < NF; ++f) {
+            U[f] = u[(long long)f * S.fs + cs];
+            D[f] = __ldg(b + (long long)f * B.fs + cb);
+        }
+        const double eta = sink_eta(P, U, D);
+        lim = eta < 1.0;
+        if (eta_out) eta_out[v] = eta;
+#pragma unroll
+        for (int f = 0; f < NF; ++f) u[(long long)f * S.fs + cs] = U[f] + eta * D[f];
+    }
+    const unsigned m1 = __ballot_sync(0xffffffffu, lim);
+    if ((threadIdx.x & 31) == 0 && m1) atomicAdd(&st->n_limited, (unsigned long long)__popc(m1));
+}
+
+void launch_zero(const Box &B, double *b, cudaStream_t stream)
+{
+    k_zero<<<152 * 8, 256, 0, stream>>>(b, B.fs, B.ncells);
+}
+
+void launch_fold(const Box &B, double *b, cudaStream_t stream)
+{
+    const long long nrows = (long long)B.n1 * B.n2;
+    const long long threads = nrows * 32;
+    k_fold<<<(unsigned)((threads + 255) / 256), 256, 0, stream>>>(B, b);
+}
+
+void launch_apply(const KParams &P, const Box &S, double *u, const Box &B, const double *b, double *eta_out,
+                  DevStatus *st, cudaStream_t stream)
+{
+    const long long nvalid = (long long)S.n0 * S.n1 * S.n2;
+    const unsigned nb = (unsigned)((nvalid + 255) / 256);
+    if (P.kind == PMP_KIND_FEEDBACK) k_apply_fb<<<nb, 256, 0, stream>>>(S, u, B, b, eta_out, st);
+    else k_apply_sink<<<nb, 256, 0, stream>>>(P, S, u, B, b, eta_out, st);
+}
+
+}  // namespace pmp

@@ -1,0 +1,298 @@
+"""Python binding of the PMP C ABI (include/pmp.h).
+
+Argument marshalling only: every step of the cycle runs in the CUDA kernels
+of libpmp.so.  Meshes are float64 CUDA tensors of shape (5, field_stride);
+particles are dicts of 1-D float64 CUDA tensors x, y, z, m, px, py, pz, e.
+Each call enqueues on torch's current CUDA stream.
+
+There is no CPU fallback: if libpmp.so is missing or no GPU is present, the
+calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_lib", "libpmp.so")
+
+FEEDBACK, SINK = 0, 1
+ATOMIC, SORTED = 0, 1
+KINDS = {"feedback": FEEDBACK, "sink": SINK}
+MODES = {"atomic": ATOMIC, "sorted": SORTED}
+STATUS = {
+    0: "PMP_OK", 1: "PMP_ERR_ARG", 2: "PMP_ERR_GHOST_TOO_THIN", 3: "PMP_ERR_PARTICLE_OUTSIDE",
+    4: "PMP_ERR_NONFINITE", 5: "PMP_ERR_TIMEOUT", 6: "PMP_ERR_WORKSPACE", 7: "PMP_ERR_CUDA",
+}
+EXPORTS = [
+    "pmp_create", "pmp_destroy", "pmp_set_stream", "pmp_gathered_rows", "pmp_workspace_size", "pmp_zero_buffer",
+    "pmp_gather", "pmp_deposit", "pmp_fold_ghosts", "pmp_apply_limited", "pmp_backward", "pmp_get_error",
+    "pmp_limiter_counts",
+]
+
+
+class PMPError(RuntimeError):
+    def __init__(self, what, code):
+        super().__init__(f"{what}: {STATUS.get(code, code)}")
+        self.code = code
+
+
+class _Params(ctypes.Structure):
+    _fields_ = [
+        ("kind", ctypes.c_int32), ("subsample", ctypes.c_int32),
+        ("r_K", ctypes.c_double), ("dt", ctypes.c_double), ("G", ctypes.c_double),
+        ("gamma", ctypes.c_double), ("lambda_bh", ctypes.c_double), ("J", ctypes.c_double),
+        ("cap", ctypes.c_double), ("rho_min", ctypes.c_double), ("A_sf", ctypes.c_double),
+        ("A_p", ctypes.c_double), ("mu_H", ctypes.c_double), ("RM_ej", ctypes.c_double),
+        ("RM_st", ctypes.c_double), ("eps_K", ctypes.c_double),
+    ]
+
+
+class _Mesh(ctypes.Structure):
+    _fields_ = [
+        ("n", ctypes.c_int32 * 3), ("ng", ctypes.c_int32), ("periodic", ctypes.c_int32 * 3),
+        ("reserved", ctypes.c_int32), ("dx", ctypes.c_double), ("field_stride", ctypes.c_int64),
+        ("data", ctypes.c_void_p),
+    ]
+
+
+class _Particles(ctypes.Structure):
+    _fields_ = [
+        ("count", ctypes.c_int64), ("x", ctypes.c_void_p), ("y", ctypes.c_void_p), ("z", ctypes.c_void_p),
+        ("m", ctypes.c_void_p), ("px", ctypes.c_void_p), ("py", ctypes.c_void_p), ("pz", ctypes.c_void_p),
+        ("e", ctypes.c_void_p),
+    ]
+
+
+_lib = None
+
+
+def load():
+    """Load libpmp.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"libpmp.so not found at {LIB_PATH}: build it first (__graft_entry__.build())")
+    L = ctypes.CDLL(LIB_PATH)
+    vp, i32, i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+    P, M, Pa = ctypes.POINTER(_Params), ctypes.POINTER(_Mesh), ctypes.POINTER(_Particles)
+    sig = {
+        "pmp_create": ([ctypes.POINTER(vp), P, vp], i32),
+        "pmp_destroy": ([vp], None),
+        "pmp_set_stream": ([vp, vp], i32),
+        "pmp_gathered_rows": ([i32], i32),
+        "pmp_workspace_size": ([vp, M, i64, i32, ctypes.POINTER(ctypes.c_size_t)], i32),
+        "pmp_zero_buffer": ([vp, M], i32),
+        "pmp_gather": ([vp, M, Pa, vp], i32),
+        "pmp_deposit": ([vp, M, Pa, vp, M, i32, vp, ctypes.c_size_t], i32),
+        "pmp_fold_ghosts": ([vp, M], i32),
+        "pmp_apply_limited": ([vp, M, M, Pa, vp, vp], i32),
+        "pmp_backward": ([vp, M, M, Pa, vp, vp, vp], i32),
+        "pmp_get_error": ([vp, ctypes.POINTER(i32), ctypes.POINTER(i64)], i32),
+        "pmp_limiter_counts": ([vp, ctypes.POINTER(i64)], i32),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = res
+    _lib = L
+    return L
+
+
+def _check(what, code):
+    if code != 0:
+        raise PMPError(what, code)
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float64:
+        raise TypeError("expected a float64 CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Mesh:
+    """A (5, field_stride) float64 CUDA tensor with its box geometry."""
+
+    def __init__(self, data, n, ng, periodic=(1, 1, 1), dx=1.0):
+        if data.dim() != 2 or data.shape[0] != 5:
+            raise ValueError("mesh data must have shape (5, field_stride)")
+        self.data, self.n, self.ng = data, tuple(int(v) for v in n), int(ng)
+        self.periodic, self.dx = tuple(int(v) for v in periodic), float(dx)
+
+    def c(self):
+        return _Mesh(n=(ctypes.c_int32 * 3)(*self.n), ng=self.ng, periodic=(ctypes.c_int32 * 3)(*self.periodic),
+                     reserved=0, dx=self.dx, field_stride=self.data.shape[1], data=_ptr(self.data))
+
+
+def _parts(p):
+    if p is None:
+        return None
+    n = int(p["x"].numel())
+    return _Particles(count=n, x=_ptr(p["x"]), y=_ptr(p["y"]), z=_ptr(p["z"]), m=_ptr(p["m"]), px=_ptr(p["px"]),
+                      py=_ptr(p["py"]), pz=_ptr(p["pz"]), e=_ptr(p.get("e")))
+
+
+def _stream():
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+class Context:
+    """An opaque pmp_ctx for one interaction kind (pmp_create / pmp_destroy)."""
+
+    def __init__(self, params):
+        L = load()
+        self.params = dict(params)
+        self.kind = KINDS[params["kind"]]
+        cp = _Params(kind=self.kind, subsample=int(params["subsample"]), r_K=params["r_K"], dt=params["dt"],
+                     G=params["G"], gamma=params["gamma"], lambda_bh=params["lambda_bh"], J=params["J"],
+                     cap=params["cap"], rho_min=params["rho_min"], A_sf=params["A_sf"], A_p=params["A_p"],
+                     mu_H=params["mu_H"], RM_ej=params["RM_ej"], RM_st=params["RM_st"], eps_K=params["eps_K"])
+        h = ctypes.c_void_p()
+        _check("pmp_create", L.pmp_create(ctypes.byref(h), ctypes.byref(cp), _stream()))
+        self.h = h
+
+    def _sync_stream(self):
+        _check("pmp_set_stream", load().pmp_set_stream(self.h, _stream()))
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().pmp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def pmp_create(params):
+    return Context(params)
+
+
+def pmp_gathered_rows(kind):
+    return load().pmp_gathered_rows(KINDS.get(kind, kind))
+
+
+def pmp_workspace_size(ctx, buffer, n_particles, mode):
+    out = ctypes.c_size_t()
+    _check("pmp_workspace_size",
+           load().pmp_workspace_size(ctx.h, ctypes.byref(buffer.c()), int(n_particles), MODES.get(mode, mode),
+                                     ctypes.byref(out)))
+    return out.value
+
+
+def pmp_zero_buffer(ctx, buffer):
+    ctx._sync_stream()
+    _check("pmp_zero_buffer", load().pmp_zero_buffer(ctx.h, ctypes.byref(buffer.c())))
+
+
+def pmp_gather(ctx, state, parts, gathered):
+    ctx._sync_stream()
+    pp = _parts(parts)
+    _check("pmp_gather", load().pmp_gather(ctx.h, ctypes.byref(state.c()), ctypes.byref(pp), _ptr(gathered)))
+
+
+def pmp_deposit(ctx, state, parts, gathered, buffer, mode="atomic", workspace=None):
+    ctx._sync_stream()
+    pp = _parts(parts)
+    ws, wsb = None, 0
+    if workspace is not None:
+        if not workspace.is_cuda or not workspace.is_contiguous():
+            raise ValueError("workspace must be a contiguous CUDA tensor")
+        ws, wsb = ctypes.c_void_p(workspace.data_ptr()), workspace.numel() * workspace.element_size()
+    _check("pmp_deposit", load().pmp_deposit(ctx.h, ctypes.byref(state.c()), ctypes.byref(pp), _ptr(gathered),
+                                             ctypes.byref(buffer.c()), MODES.get(mode, mode), ws, wsb))
+
+
+def pmp_fold_ghosts(ctx, buffer):
+    ctx._sync_stream()
+    _check("pmp_fold_ghosts", load().pmp_fold_ghosts(ctx.h, ctypes.byref(buffer.c())))
+
+
+def pmp_apply_limited(ctx, state, buffer, parts=None, gathered=None, eta_out=None):
+    ctx._sync_stream()
+    pp = _parts(parts)
+    _check("pmp_apply_limited",
+           load().pmp_apply_limited(ctx.h, ctypes.byref(state.c()), ctypes.byref(buffer.c()),
+                                    ctypes.byref(pp) if pp is not None else None, _ptr(gathered), _ptr(eta_out)))
+
+
+def pmp_backward(ctx, state_in, buffer, parts, gathered, gU, g_out):
+    ctx._sync_stream()
+    pp = _parts(parts)
+    _check("pmp_backward", load().pmp_backward(ctx.h, ctypes.byref(state_in.c()), ctypes.byref(buffer.c()),
+                                               ctypes.byref(pp), _ptr(gathered), _ptr(gU), _ptr(g_out)))
+
+
+def pmp_get_error(ctx):
+    code, idx = ctypes.c_int32(), ctypes.c_int64()
+    ctx._sync_stream()
+    _check("pmp_get_error", load().pmp_get_error(ctx.h, ctypes.byref(code), ctypes.byref(idx)))
+    return code.value, idx.value
+
+
+def pmp_limiter_counts(ctx):
+    c = (ctypes.c_int64 * 2)()
+    ctx._sync_stream()
+    _check("pmp_limiter_counts", load().pmp_limiter_counts(ctx.h, c))
+    return c[0], c[1]
+
+
+# ---------------------------------------------------------------------------
+# conveniences built only from the calls above
+# ---------------------------------------------------------------------------
+
+def to_device(arr, device="cuda"):
+    return torch.from_numpy(arr).to(device)
+
+
+def parts_to_device(p, device="cuda"):
+    return {k: torch.from_numpy(v).to(device) for k, v in p.items()}
+
+
+class Pass:
+    """One PMP pass (zero, gather, deposit, fold, limited apply) of one kind
+    on one box, with its buffers allocated once."""
+
+    def __init__(self, params, box, state, parts, mode="atomic", dx=1.0, periodic=(1, 1, 1), want_eta=False):
+        self.ctx = Context(params)
+        self.box, self.mode = box, mode
+        dev = state.device
+        self.state = Mesh(state, box.n, box.g, periodic, dx)
+        self.buffer = Mesh(torch.empty((5, box.field_stride), dtype=torch.float64, device=dev), box.n, box.g,
+                           periodic, dx)
+        self.parts = parts
+        n = int(parts["x"].numel()) if parts is not None else 0
+        self.gathered = torch.empty((pmp_gathered_rows(params["kind"]), max(n, 1)), dtype=torch.float64, device=dev)
+        self.eta = torch.empty(box.ncells_valid, dtype=torch.float64, device=dev) if want_eta else None
+        self.workspace = None
+        if mode == "sorted":
+            nbytes = pmp_workspace_size(self.ctx, self.buffer, n, "sorted")
+            self.workspace = torch.empty(max(nbytes, 1), dtype=torch.uint8, device=dev)
+
+    def gathered_view(self):
+        n = int(self.parts["x"].numel())
+        return self.gathered[:, :n]
+
+    def run(self, stop_after=None):
+        c = self.ctx
+        pmp_zero_buffer(c, self.buffer)
+        if self.parts is not None and self.parts["x"].numel() > 0:
+            pmp_gather(c, self.state, self.parts, self.gathered)
+            pmp_deposit(c, self.state, self.parts, self.gathered, self.buffer, self.mode, self.workspace)
+        if stop_after == "deposit":
+            return
+        pmp_fold_ghosts(c, self.buffer)
+        if stop_after == "fold":
+            return
+        has = self.parts is not None and self.parts["x"].numel() > 0
+        pmp_apply_limited(c, self.state, self.buffer, self.parts if has else None, self.gathered if has else None,
+                          self.eta)
