@@ -1,0 +1,483 @@
+"""Benchmark of the particle-mesh-particle (PMP) cycle on GB300.
+
+One step = one full mixed cycle on the 512^3 workload: the supernova pass
+(gather, deposit, fold, limited apply; Sec. 3.2.1) then the sink pass on the
+updated state (gather, deposit, fold, Step-4 return, limited apply;
+Sec. 3.1.1), atomic accumulation.  Every step starts from the same gas state
+and sink masses/momenta (a device copy of the initial ones, 5.7 GB, counted
+in the step's time), so every timed step does the same work.  Inputs
+(state + buffer 11.2 GB) are larger than L2.
+
+    python bench.py [--gpus N --steps K --warmup W] [--impl ours|reference]
+
+Prints one JSON line.  With N > 1 (torchrun, one rank per GPU) every rank
+runs an independent replica of the workload (weak scaling; the cycle has no
+exchange step on one GPU) and the slowest rank's time is reported.
+``--impl reference`` times the CPU oracle (the reference arm of this build)
+on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import re
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "PMP cycle particles/s & cells/s on 1 GB300, % HBM roofline, fwd+bwd time"
+WORKLOAD = "c5_512"
+FP64_PEAK_TFLOPS = 1.25  # nominal dense FP64 of GB300 (fused multiply-add counted as 2)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--mode", default="atomic", choices=["atomic", "sorted"])
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample-n", type=int, default=128)
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# distributed plumbing (replicas only)
+# ---------------------------------------------------------------------------
+
+def dist_init():
+    import torch
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    elif torch.cuda.is_available():
+        torch.cuda.set_device(0)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+def max_over_ranks(world, value):
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([value], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+
+class Clocks:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-f", self.path], stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        try:
+            for line in open(self.path):
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        finally:
+            os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------
+# algorithmic work of one cycle (for the roofline)
+# ---------------------------------------------------------------------------
+
+def kernel_cell_count(parts, n, rK, chunk=1 << 20):
+    """Number of (particle, kernel cell) pairs: cell centres strictly inside r_K
+    (the per-pair unit of the particle kernels)."""
+    import torch
+
+    R = int(math.ceil(rK))
+    o = torch.arange(-R, R + 1, device="cuda", dtype=torch.float64)
+    total = 0
+    N = parts["x"].numel()
+    for s0 in range(0, N, chunk):
+        d2 = None
+        for a, key in enumerate(("x", "y", "z")):
+            x = parts[key][s0:s0 + chunk]
+            d = (torch.floor(x)[:, None] + o[None, :] + 0.5) - x[:, None]
+            sq = d * d
+            shape = [x.numel(), 1, 1, 1]
+            shape[3 - a] = 2 * R + 1
+            sq = sq.reshape(shape)
+            d2 = sq if d2 is None else d2 + sq
+        total += int((d2 < rK * rK).sum().item())
+    return total
+
+
+# canonical FP64 operations per pair / per cell (add, sub, mul, div, sqrt = 1)
+FLOPS_PER_PAIR = {"fb_gather": 9, "fb_deposit": 29, "sink_gather": 27, "sink_deposit": 21, "sink_return": 30}
+BYTES_PER_CELL = {"zero": 40, "apply": 120}
+
+
+def src_digest():
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2509_18261_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        h.update(open(os.path.join(d, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(kernel):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if it
+    was taken on the current kernel sources; else None."""
+    path = os.path.join(ROOT, "profiles", "traffic.md")
+    if not os.path.exists(path):
+        return None
+    txt = open(path).read()
+    m = re.search(r"csrc_sha:\s*([0-9a-f]+)", txt)
+    if not m or m.group(1) != src_digest():
+        return None
+    m = re.search(rf"^\|\s*{re.escape(kernel)}\s*\|\s*([0-9.eE+]+)\s*\|", txt, re.M)
+    return float(m.group(1)) if m else None
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return float(d.get("hbm_gbs", 6800.0)), "measured"
+    return 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+
+def run_ours(args, world, rank, local):
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_2509_18261_gb300 import pmp
+    from paper_2509_18261_gb300 import synthetic as syn
+
+    w = syn.make_workload(args.workload)
+    box = w["box"]
+    dev = "cuda"
+    state = torch.from_numpy(w["state"]).to(dev)
+    fb = pmp.parts_to_device(w["fb"], dev)
+    sk = pmp.parts_to_device(w["sink"], dev)
+    n_fb, n_sk = fb["x"].numel(), sk["x"].numel()
+    n_particles = n_fb + n_sk
+    P_fb = pmp.Pass(w["fb_params"], box, state, fb, mode=args.mode)
+    P_sk = pmp.Pass(w["sink_params"], box, state, sk, mode=args.mode)
+    stream = torch.cuda.current_stream()
+
+    phases = ["fb_zero", "fb_gather", "fb_deposit", "fb_fold", "fb_apply",
+              "sink_zero", "sink_gather", "sink_deposit", "sink_fold", "sink_apply"]
+    # own kernels per step: zero, [host keys], plan count, plan emit, gather,
+    # deposit (+ sort keys, segment sum when sorted), fold, apply; sinks add the
+    # per-cell quantities, eta and the Step-4 return
+    per_pass = 7 + (0 if args.mode == "sorted" else 1) + (1 if args.mode == "sorted" else 0)
+    launches_per_step = 2 * per_pass + 3
+    state0 = state.clone()
+    sink0 = {k: sk[k].clone() for k in ("m", "px", "py", "pz")}
+
+    def restore():
+        state.copy_(state0)
+        for k in sink0:
+            sk[k].copy_(sink0[k])
+
+    def cycle(events=None, restore_state=True):
+        marks = []
+        if restore_state:
+            restore()
+
+        def mark():
+            if events is not None:
+                e = torch.cuda.Event(enable_timing=True)
+                e.record(stream)
+                marks.append(e)
+
+        for ps, parts in ((P_fb, fb), (P_sk, sk)):
+            c = ps.ctx
+            mark()
+            pmp.pmp_zero_buffer(c, ps.buffer)
+            mark()
+            pmp.pmp_gather(c, ps.state, parts, ps.gathered, args.mode, ps.workspace)
+            mark()
+            pmp.pmp_deposit(c, ps.state, parts, ps.gathered, ps.buffer, args.mode, ps.workspace)
+            mark()
+            pmp.pmp_fold_ghosts(c, ps.buffer)
+            mark()
+            pmp.pmp_apply_limited(c, ps.state, ps.buffer, parts, ps.gathered, None, ps.workspace)
+            mark()
+        if events is not None:
+            events.append(marks)
+
+    for _ in range(args.warmup):
+        cycle()
+    torch.cuda.synchronize()
+    for ps in (P_fb, P_sk):
+        code, idx = pmp.pmp_get_error(ps.ctx)
+        if code:
+            raise RuntimeError(f"device error {code} at {idx}")
+
+    clocks = Clocks(local)
+    clocks.start()
+    barrier(world)
+    torch.cuda.synchronize()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    events = []
+    t0.record(stream)
+    for _ in range(args.steps):
+        cycle(events)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    clk = clocks.stop()
+    ms_total = t0.elapsed_time(t1)
+    ms_per_step = max_over_ranks(world, ms_total / args.steps)
+    phase_ms = {}
+    for marks in events:
+        # marks per pass: zero|gather|deposit|fold|apply boundaries (6 marks each)
+        for p in range(2):
+            m = marks[p * 6:(p + 1) * 6]
+            for i in range(5):
+                name = phases[p * 5 + i]
+                phase_ms[name] = phase_ms.get(name, 0.0) + m[i].elapsed_time(m[i + 1]) / args.steps
+    lim_fb = pmp.pmp_limiter_counts(P_fb.ctx)
+    lim_sk = pmp.pmp_limiter_counts(P_sk.ctx)
+
+    # e2e: pinned host inputs -> device -> cycle -> results back to pinned host
+    h_state = torch.from_numpy(w["state"]).pin_memory()
+    h_fb = {k: torch.from_numpy(v).pin_memory() for k, v in w["fb"].items()}
+    h_sk = {k: torch.from_numpy(v).pin_memory() for k, v in w["sink"].items()}
+    o_state = torch.empty_like(h_state).pin_memory()
+    o_sk = {k: torch.empty_like(h_sk[k]).pin_memory() for k in ("m", "px", "py", "pz")}
+    bi = h_state.numel() * 8 + sum(v.numel() * 8 for v in h_fb.values()) + sum(v.numel() * 8 for v in h_sk.values())
+    bo = o_state.numel() * 8 + sum(v.numel() * 8 for v in o_sk.values())
+    barrier(world)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.e2e_steps):
+        state.copy_(h_state, non_blocking=True)
+        for k in h_fb:
+            fb[k].copy_(h_fb[k], non_blocking=True)
+        for k in h_sk:
+            sk[k].copy_(h_sk[k], non_blocking=True)
+        cycle(restore_state=False)
+        o_state.copy_(state, non_blocking=True)
+        for k in o_sk:
+            o_sk[k].copy_(sk[k], non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    e2e_ms = max_over_ranks(world, e0.elapsed_time(e1) / args.e2e_steps)
+
+    # roofline of the dominant kernel
+    pairs = {"fb": kernel_cell_count(fb, box.n, w["fb_params"]["r_K"]),
+             "sink": kernel_cell_count(sk, box.n, w["sink_params"]["r_K"])}
+    dominant = max(phase_ms, key=phase_ms.get)
+    hbm_peak, peak_src = peaks()
+    kind = dominant.split("_")[0]
+    stage = dominant.split("_", 1)[1]
+    ncells_valid = box.ncells_valid
+    if stage in ("zero", "apply", "fold"):
+        if stage == "zero":
+            nbytes = BYTES_PER_CELL["zero"] * box.ncells_padded
+        elif stage == "apply":
+            nbytes = BYTES_PER_CELL["apply"] * ncells_valid
+            if kind == "sink":
+                nbytes += n_sk * 64 + pairs["sink"] * 80
+        else:
+            nbytes = 120 * (box.ncells_padded - ncells_valid)
+        achieved = nbytes / (phase_ms[dominant] * 1e-3) / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                "frac": achieved / hbm_peak, "peak_source": peak_src}
+    else:
+        key = f"{kind}_{stage}"
+        flops = FLOPS_PER_PAIR.get(key, 0) * pairs[kind]
+        achieved = flops / (phase_ms[dominant] * 1e-3) / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP64_PEAK_TFLOPS, "peak_source": "nominal FP64 (derived)"}
+    roof["kernel"] = dominant
+    roof["traffic"] = profiled_traffic(dominant)
+
+    result = {
+        "metric": METRIC,
+        "value": n_particles * world / (ms_per_step * 1e-3),
+        "unit": "particles/s",
+        "cells_per_s": ncells_valid * world / (ms_per_step * 1e-3),
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms_per_step,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64",
+        "data": "synthetic",
+        "config": {
+            "workload": (f"{args.workload}: {box.n[0]}^3 box, {box.g} ghost cells, 5 FP64 fields; "
+                         f"{n_fb} supernova particles (r_K=2, S=4) + {n_sk} sinks (r_K=4), "
+                         "25% in 256 Plummer clusters (a=2 cells); supernova pass then sink pass"),
+            "mode": args.mode,
+            "l2": "inputs larger than L2 (state + buffer 11.2 GB)",
+            "parallelism": f"replicas x{world}",
+            "kernel_pairs": pairs,
+        },
+        "phases_ms": {k: round(v, 4) for k, v in phase_ms.items()},
+        "limiter": {"fb_cells_eta_lt_1": lim_fb[0], "fb_noroot": lim_fb[1], "sink_cells_eta_lt_1": lim_sk[0]},
+        "roofline": roof,
+        "e2e": {"value": n_particles * world / (e2e_ms * 1e-3), "unit": "particles/s",
+                "ms_per_step": e2e_ms, "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo},
+        "gpu_launches": launches_per_step * args.steps,
+        "clocks": clk,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        result["cpu_baseline"] = cpu_baseline(args)
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle: the baseline leg and the reference arm
+# ---------------------------------------------------------------------------
+
+def oracle_cycle_sample(n, seed_workload=WORKLOAD):
+    """One mixed cycle of the oracle on the workload shrunk to an n^3 box with
+    the same particle density; returns (seconds, particles, cells)."""
+    import oracle
+    from paper_2509_18261_gb300 import synthetic as syn
+
+    full = syn.WORKLOADS[seed_workload]["n"]
+    w = syn.make_workload(seed_workload, n=n, count_scale=(n / full) ** 3)
+    box = w["box"]
+    st = w["state"].copy()
+    t = time.perf_counter()
+    oracle.cycle(w["fb_params"], box, st, w["fb"])
+    oracle.cycle(w["sink_params"], box, st, w["sink"])
+    dt = time.perf_counter() - t
+    return dt, len(w["fb"]["x"]) + len(w["sink"]["x"]), box.ncells_valid
+
+
+def cpu_baseline(args):
+    dt, npart, ncells = oracle_cycle_sample(args.cpu_sample_n)
+    return {"value": npart / dt, "unit": "particles/s", "cores": 1, "kind": "oracle",
+            "cells_per_s": ncells / dt,
+            "sample": f"one mixed cycle of the same workload shrunk to {args.cpu_sample_n}^3 at equal particle "
+                      f"density ({npart} particles), single-threaded C oracle, {dt:.2f} s"}
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    n = 64
+    for _ in range(args.warmup):
+        oracle_cycle_sample(n)
+    times = []
+    npart = ncells = 0
+    for _ in range(args.steps):
+        dt, npart, ncells = oracle_cycle_sample(n)
+        times.append(dt)
+    ms = 1e3 * sum(times) / len(times)
+    value = npart / (ms * 1e-3)
+    line = {
+        "impl": "reference",
+        "metric": METRIC,
+        "value": value,
+        "unit": "particles/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": f"{args.workload} shrunk to {n}^3 at equal particle density ({npart} particles)"},
+        "cpu_baseline": {"value": value, "unit": "particles/s", "cores": 1, "kind": "oracle",
+                         "sample": f"{n}^3 sample of {args.workload}, one mixed cycle per step"},
+        "e2e": {"value": value, "unit": "particles/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        world = int(os.environ.get("WORLD_SIZE", "1"))
+        rank = int(os.environ.get("RANK", "0"))
+        run_reference(args, world, rank)
+        return
+    world, rank, local = dist_init()
+    run_ours(args, world, rank, local)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

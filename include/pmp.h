@@ -13,8 +13,10 @@
  * comment says "host".  The library borrows device pointers only for the work
  * it enqueues and never frees them.  It allocates device memory only in
  * pmp_create (a few hundred bytes for status words) and frees it in
- * pmp_destroy.  Scratch memory for the sorted deposit is the caller's
- * (pmp_workspace_size).
+ * pmp_destroy.  Scratch memory of a pass is the caller's: pmp_workspace_size
+ * gives its size, pmp_gather writes the pass's plan into it (each particle's
+ * kernel cells, found once), and pmp_deposit, pmp_apply_limited and
+ * pmp_backward read it.
  *
  * Streams.  Work is enqueued on the context's stream (pmp_create /
  * pmp_set_stream) and returns immediately, except where a comment says the
@@ -146,8 +148,9 @@ pmp_status pmp_set_stream(pmp_ctx *ctx, pmp_stream stream);
 /* Number of gathered rows for a kind (12 feedback, 8 sink); 0 if unknown. */
 int32_t pmp_gathered_rows(int32_t kind);
 
-/* Bytes of device workspace pmp_deposit needs for `mode` with this buffer and
- * this many particles (0 for PMP_MODE_ATOMIC).  Host only, no device work. */
+/* Bytes of device workspace one pass needs for `n_particles` particles of
+ * the context's kind on a mesh with the buffer's n, with the deposit
+ * strategy `mode`.  Host only, no device work. */
 pmp_status pmp_workspace_size(const pmp_ctx *ctx, const pmp_mesh *buffer, int64_t n_particles, int32_t mode,
                               size_t *bytes);
 
@@ -161,16 +164,23 @@ pmp_status pmp_zero_buffer(pmp_ctx *ctx, pmp_mesh *buffer);
  * feedback (Sec. 3.2.1); rho_inf, v_inf, c_inf, r_BH -> mdot_BH (Eq. mdot),
  * r_acc and sum w (Eq. kernel, Eq. kernel_wgt) for sinks (Sec. 3.1.1).
  * gathered: device, [rows][count]; particles outside the box get zero rows
- * and set PMP_ERR_PARTICLE_OUTSIDE. */
-pmp_status pmp_gather(pmp_ctx *ctx, const pmp_mesh *state, const pmp_particles *particles, double *gathered);
+ * and set PMP_ERR_PARTICLE_OUTSIDE.
+ * Also records the pass's plan in `workspace` (device, 256-byte aligned, at
+ * least pmp_workspace_size bytes for `mode`): each particle's kernel cells
+ * with their covered fractions, and for sinks the per-cell quantities of the
+ * state.  The plan stays valid until the particles' positions or the state
+ * change or pmp_gather runs again with this context. */
+pmp_status pmp_gather(pmp_ctx *ctx, const pmp_mesh *state, const pmp_particles *particles, double *gathered,
+                      int32_t mode, void *workspace, size_t workspace_bytes);
 
 /* Step 1 (Eq. delta_u_buf): every particle adds its deposition function
  * Delta U^s (Eq. du for feedback; Eq. accretion_function for sinks, the
  * removal entering with a minus sign) to every kernel cell of the buffer,
- * ghost zones included, on top of what the buffer holds.  ATOMIC uses FP64
- * atomics; SORTED needs `workspace` of pmp_workspace_size bytes (device,
- * 256-byte aligned) and synchronises the stream once to read the pair count.
- * Kernel cells with omega = 0 receive nothing. */
+ * ghost zones included, on top of what the buffer holds.  `workspace` must
+ * hold the plan of the preceding pmp_gather on these particles with the same
+ * `mode` (else PMP_ERR_WORKSPACE).  ATOMIC uses FP64 atomics; SORTED
+ * synchronises the stream once to read the pair count.  Kernel cells with
+ * omega = 0 receive nothing. */
 pmp_status pmp_deposit(pmp_ctx *ctx, const pmp_mesh *state, const pmp_particles *particles, const double *gathered,
                        pmp_mesh *buffer, int32_t mode, void *workspace, size_t workspace_bytes);
 
@@ -192,9 +202,11 @@ pmp_status pmp_fold_ghosts(pmp_ctx *ctx, pmp_mesh *buffer);
  *   the Truelove floor and the density floor rho_min; the same eta for all
  *   fields; `particles`/`gathered` are those of pmp_gather.
  * eta_out: optional device array, one FP64 per valid cell (x fastest): the
- *   momentum eta (feedback) or the common eta (sink). */
+ *   momentum eta (feedback) or the common eta (sink).
+ * workspace: sinks need the one pmp_gather filled for this pass (its plan and
+ *   per-cell quantities); feedback ignores it (may be NULL). */
 pmp_status pmp_apply_limited(pmp_ctx *ctx, pmp_mesh *state, const pmp_mesh *buffer, pmp_particles *particles,
-                             const double *gathered, double *eta_out);
+                             const double *gathered, double *eta_out, void *workspace, size_t workspace_bytes);
 
 /* Adjoint of one feedback pass (gather, deposit, fold, limited apply) with
  * respect to the particle inputs, for a loss L whose gradient with respect to
@@ -205,9 +217,11 @@ pmp_status pmp_apply_limited(pmp_ctx *ctx, pmp_mesh *state, const pmp_mesh *buff
  * position and contribute no derivative.  Weights are recomputed, not
  * stored.  g_out: device [8][count] = dL/d(m, e, px, py, pz, x, y, z).
  * `state_in` is the state BEFORE the apply; `buffer` the folded buffer;
- * `gathered` from pmp_gather.  Feedback contexts only. */
+ * `gathered` and `workspace` from the pass's pmp_gather.  Feedback contexts
+ * only. */
 pmp_status pmp_backward(pmp_ctx *ctx, const pmp_mesh *state_in, const pmp_mesh *buffer, const pmp_particles *particles,
-                        const double *gathered, const double *gU, double *g_out);
+                        const double *gathered, const double *gU, double *g_out, void *workspace,
+                        size_t workspace_bytes);
 
 /* Synchronises the context's stream, then returns the first device error
  * since the last call (PMP_OK if none) in *code and the index of the

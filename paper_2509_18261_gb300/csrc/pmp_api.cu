@@ -15,6 +15,11 @@ struct pmp_ctx {
     cudaStream_t stream;
     pmp::DevStatus *st;  // device
     int device;
+    // the plan recorded by the last pmp_gather
+    const void *plan_ws;
+    long long plan_n;
+    long long plan_nvalid;
+    int plan_mode;
 };
 
 namespace {
@@ -70,6 +75,10 @@ KParams make_kparams(const pmp_params &p, double dx)
     k.four_pi = 4.0 * pmp::kPi;
     k.S = p.kind == PMP_KIND_FEEDBACK ? p.subsample : 1;
     k.S3 = k.S * k.S * k.S;
+    for (int a = 0; a < 8; ++a) k.frac[a] = a < k.S ? ((double)a + 0.5) / (double)k.S : 0.0;
+    k.Slog = -1;
+    for (int b = 0; b < 4; ++b)
+        if (k.S == (1 << b)) k.Slog = b;
     k.R = (int)std::ceil(p.r_K);
     k.kind = p.kind;
     return k;
@@ -155,35 +164,104 @@ pmp_status last_launch()
 
 size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
 
-struct SortedLayout {
-    size_t counts, offsets, kin, kout, vin, vout, temp, temp_bytes, total;
-    long long cap;
+// Upper bound on the kernel cells of one particle: offsets o in [-R, R]^3 whose
+// cell centre can come within r_K of some point of the host cell, i.e.
+// sum_a max(0, |o_a| - 1/2)^2 <= r_K^2 (with a little slack for rounding).
+long long max_pairs_per_particle(double rK)
+{
+    const int R = (int)std::ceil(rK);
+    const double lim = rK * rK * (1.0 + 1e-9);
+    long long n = 0;
+    for (int a = -R; a <= R; ++a)
+        for (int b = -R; b <= R; ++b)
+            for (int c = -R; c <= R; ++c) {
+                double s = 0.0;
+                for (int o : {a, b, c}) {
+                    const double m = std::fabs((double)o) - 0.5;
+                    if (m > 0.0) s += m * m;
+                }
+                if (s <= lim) ++n;
+            }
+    return n;
+}
+
+struct Layout {
+    size_t keys, ids, keys2, ids2, counts, slots, hosts, wts, aux, eta, offsets, skeys, skeys2, svals, svals2;
+    size_t temp, temp_bytes, total;
+    long long cap, aux_stride;
 };
 
-SortedLayout sorted_layout(int R, long long n)
+Layout layout(const pmp_params &p, long long n, long long nvalid, int mode)
 {
-    SortedLayout L;
-    const long long W = 2LL * R + 1;
-    L.cap = n * W * W * W;
+    Layout L;
+    std::memset(&L, 0, sizeof(L));
+    const int R = (int)std::ceil(p.r_K);
+    const int W = 2 * R + 1;
+    const bool sink = p.kind == PMP_KIND_SINK;
+    const bool sorted = mode == PMP_MODE_SORTED;
+    L.cap = max_pairs_per_particle(p.r_K);
+    L.aux_stride = nvalid;
     size_t off = 0;
-    L.counts = off;
-    off = align256(off + sizeof(long long) * (size_t)(n + 1));
-    L.offsets = off;
-    off = align256(off + sizeof(long long) * (size_t)(n + 1));
-    L.kin = off;
-    off = align256(off + sizeof(unsigned) * (size_t)L.cap);
-    L.kout = off;
-    off = align256(off + sizeof(unsigned) * (size_t)L.cap);
-    L.vin = off;
-    off = align256(off + sizeof(int) * (size_t)L.cap);
-    L.vout = off;
-    off = align256(off + sizeof(int) * (size_t)L.cap);
-    L.temp = off;
-    L.temp_bytes = pmp::sort_temp_bytes(L.cap > 0 ? L.cap : 1, n);
-    off = align256(off + L.temp_bytes);
+    auto take = [&](size_t bytes) {
+        const size_t at = off;
+        off = align256(off + bytes);
+        return at;
+    };
+    const size_t n1 = (size_t)(n > 0 ? n : 1);
+    const size_t pairs = n1 * (size_t)L.cap;
+    if (!sorted) {
+        L.keys = take(4 * n1);
+        L.ids = take(4 * n1);
+        L.keys2 = take(4 * n1);
+        L.ids2 = take(4 * n1);
+    }
+    L.counts = take(4 * (n1 + 1));
+    L.slots = take(8 * pairs);
+    L.hosts = take(8 * n1);
+    if (sink) {
+        L.wts = take(8 * n1 * 3 * (size_t)W);
+        L.aux = take(8 * (size_t)pmp::AUX_ROWS * (size_t)(nvalid > 0 ? nvalid : 1));
+        L.eta = take(8 * (size_t)(nvalid > 0 ? nvalid : 1));
+    }
+    if (sorted) {
+        L.offsets = take(8 * (n1 + 1));
+        L.skeys = take(4 * pairs);
+        L.skeys2 = take(4 * pairs);
+        L.svals = take(4 * pairs);
+        L.svals2 = take(4 * pairs);
+    }
+    L.temp_bytes = pmp::cub_temp_bytes(n, (long long)pairs, sorted);
+    L.temp = take(L.temp_bytes);
     L.total = off;
     return L;
 }
+
+pmp::PlanPtrs plan_ptrs(const Layout &L, void *ws, const pmp_params &p, int mode)
+{
+    char *w = static_cast<char *>(ws);
+    pmp::PlanPtrs pl;
+    std::memset(&pl, 0, sizeof(pl));
+    pl.perm = mode == PMP_MODE_SORTED ? nullptr : reinterpret_cast<const unsigned *>(w + L.ids2);
+    pl.counts = reinterpret_cast<unsigned *>(w + L.counts);
+    pl.slots = reinterpret_cast<unsigned long long *>(w + L.slots);
+    pl.hosts = reinterpret_cast<unsigned long long *>(w + L.hosts);
+    if (p.kind == PMP_KIND_SINK) {
+        pl.wts = reinterpret_cast<double *>(w + L.wts);
+        pl.aux = reinterpret_cast<double *>(w + L.aux);
+        pl.eta = reinterpret_cast<double *>(w + L.eta);
+    }
+    pl.aux_stride = L.aux_stride;
+    pl.cap = (unsigned long long)L.cap;
+    return pl;
+}
+
+pmp_status check_workspace(const Layout &L, const void *ws, size_t bytes)
+{
+    if (!ws || bytes < L.total || (reinterpret_cast<uintptr_t>(ws) & 255)) return PMP_ERR_WORKSPACE;
+    return PMP_OK;
+}
+
+long long nvalid_of(const pmp_mesh *m) { return (long long)m->n[0] * m->n[1] * m->n[2]; }
 
 }  // namespace
 
@@ -200,6 +278,10 @@ pmp_status pmp_create(pmp_ctx **out, const pmp_params *params, pmp_stream stream
     c->p = *params;
     c->stream = reinterpret_cast<cudaStream_t>(stream);
     c->st = nullptr;
+    c->plan_ws = nullptr;
+    c->plan_n = -1;
+    c->plan_nvalid = -1;
+    c->plan_mode = PMP_MODE_ATOMIC;
     if (cudaGetDevice(&c->device) != cudaSuccess || cudaMalloc(&c->st, sizeof(pmp::DevStatus)) != cudaSuccess ||
         cudaMemset(c->st, 0, sizeof(pmp::DevStatus)) != cudaSuccess) {
         if (c->st) cudaFree(c->st);
@@ -233,13 +315,11 @@ int32_t pmp_gathered_rows(int32_t kind)
 pmp_status pmp_workspace_size(const pmp_ctx *ctx, const pmp_mesh *buffer, int64_t n_particles, int32_t mode,
                               size_t *bytes)
 {
-    if (!ctx || !buffer || !bytes || n_particles < 0) return PMP_ERR_ARG;
-    if (mode == PMP_MODE_ATOMIC) {
-        *bytes = 0;
-        return PMP_OK;
-    }
-    if (mode != PMP_MODE_SORTED) return PMP_ERR_ARG;
-    *bytes = sorted_layout((int)std::ceil(ctx->p.r_K), n_particles).total;
+    if (!ctx || !buffer || !bytes || n_particles < 0 || n_particles > 0x7fffffffLL) return PMP_ERR_ARG;
+    if (mode != PMP_MODE_ATOMIC && mode != PMP_MODE_SORTED) return PMP_ERR_ARG;
+    for (int a = 0; a < 3; ++a)
+        if (buffer->n[a] < 1) return PMP_ERR_ARG;
+    *bytes = layout(ctx->p, n_particles, nvalid_of(buffer), mode).total;
     return PMP_OK;
 }
 
@@ -253,67 +333,110 @@ pmp_status pmp_zero_buffer(pmp_ctx *ctx, pmp_mesh *buffer)
     return last_launch();
 }
 
-pmp_status pmp_gather(pmp_ctx *ctx, const pmp_mesh *state, const pmp_particles *particles, double *gathered)
+pmp_status pmp_gather(pmp_ctx *ctx, const pmp_mesh *state, const pmp_particles *particles, double *gathered,
+                      int32_t mode, void *workspace, size_t workspace_bytes)
 {
     if (!ctx || (!gathered && particles && particles->count > 0)) return PMP_ERR_ARG;
+    if (mode != PMP_MODE_ATOMIC && mode != PMP_MODE_SORTED) return PMP_ERR_ARG;
     Box S;
     Parts q;
     pmp_status s = make_box(state, &S);
     if (s) return s;
     s = make_parts(ctx, particles, &q);
     if (s) return s;
+    const int R = (int)std::ceil(ctx->p.r_K);
+    for (int a = 0; a < 3; ++a) {
+        if (state->n[a] + 2 * R > 0xffff) return PMP_ERR_ARG;
+        // a kernel cell wraps by at most one period
+        if (state->periodic[a] && R > state->n[a]) return PMP_ERR_GHOST_TOO_THIN;
+    }
+    const long long nv = nvalid_of(state);
+    if (nv > 0xfffffffeLL) return PMP_ERR_ARG;
+    const Layout L = layout(ctx->p, q.count, nv, mode);
+    if (mode == PMP_MODE_SORTED && (unsigned long long)q.count * (unsigned long long)L.cap > 0xffffffffULL)
+        return PMP_ERR_ARG;  // slot indices of the sorted lists are 32-bit
+    s = check_workspace(L, workspace, workspace_bytes);
+    if (s) return s;
+    ctx->plan_ws = nullptr;
     const KParams P = make_kparams(ctx->p, state->dx);
-    pmp::launch_gather(P, S, state->data, q, gathered, ctx->st, ctx->stream);
-    return last_launch();
+    const pmp::PlanPtrs pl = plan_ptrs(L, workspace, ctx->p, mode);
+    char *w = static_cast<char *>(workspace);
+    void *temp = w + L.temp;
+    cudaStream_t st = ctx->stream;
+    if (q.count > 0) {
+        if (mode == PMP_MODE_ATOMIC) {
+            unsigned *keys = reinterpret_cast<unsigned *>(w + L.keys), *ids = reinterpret_cast<unsigned *>(w + L.ids);
+            unsigned *keys2 = reinterpret_cast<unsigned *>(w + L.keys2),
+                     *ids2 = reinterpret_cast<unsigned *>(w + L.ids2);
+            pmp::launch_host_keys(S, q, keys, ids, st);
+            if (pmp::sort_host_keys(temp, L.temp_bytes, keys, keys2, ids, ids2, q.count, st) != cudaSuccess)
+                return PMP_ERR_CUDA;
+        }
+        pmp::launch_plan(P, S, q, pl, ctx->st, st);
+    }
+    if (ctx->p.kind == PMP_KIND_SINK) pmp::launch_sink_aux(P, S, state->data, pl.aux, pl.aux_stride, st);
+    if (q.count > 0) pmp::launch_gather(P, S, state->data, q, pl, gathered, ctx->st, st);
+    s = last_launch();
+    if (s) return s;
+    ctx->plan_ws = workspace;
+    ctx->plan_n = q.count;
+    ctx->plan_nvalid = nv;
+    ctx->plan_mode = mode;
+    return PMP_OK;
+}
+
+static pmp_status check_plan(const pmp_ctx *ctx, long long n, long long nvalid, const void *ws)
+{
+    if (!ws || ctx->plan_ws != ws || ctx->plan_n != n || ctx->plan_nvalid != nvalid) return PMP_ERR_WORKSPACE;
+    return PMP_OK;
 }
 
 pmp_status pmp_deposit(pmp_ctx *ctx, const pmp_mesh *state, const pmp_particles *particles, const double *gathered,
                        pmp_mesh *buffer, int32_t mode, void *workspace, size_t workspace_bytes)
 {
     if (!ctx || (!gathered && particles && particles->count > 0)) return PMP_ERR_ARG;
+    if (mode != PMP_MODE_ATOMIC && mode != PMP_MODE_SORTED) return PMP_ERR_ARG;
     Box S, B;
     Parts q;
     pmp_status s = check_pair(ctx, state, buffer, &S, &B);
     if (s) return s;
     s = make_parts(ctx, particles, &q);
     if (s) return s;
+    if (q.count == 0) return PMP_OK;
+    const long long nv = nvalid_of(state);
+    const Layout L = layout(ctx->p, q.count, nv, mode);
+    s = check_workspace(L, workspace, workspace_bytes);
+    if (s) return s;
+    s = check_plan(ctx, q.count, nv, workspace);
+    if (s) return s;
+    if (ctx->plan_mode != mode) return PMP_ERR_WORKSPACE;
     const KParams P = make_kparams(ctx->p, state->dx);
+    const pmp::PlanPtrs pl = plan_ptrs(L, workspace, ctx->p, mode);
+    cudaStream_t st = ctx->stream;
     if (mode == PMP_MODE_ATOMIC) {
-        pmp::launch_deposit_atomic(P, S, state->data, B, buffer->data, q, gathered, ctx->st, ctx->stream);
+        pmp::launch_deposit_atomic(P, S, state->data, B, buffer->data, q, gathered, pl, st);
         return last_launch();
     }
-    if (mode != PMP_MODE_SORTED) return PMP_ERR_ARG;
     if (B.ncells > 0xffffffffLL) return PMP_ERR_ARG;
-    const SortedLayout L = sorted_layout(P.R, q.count);
-    if (!workspace || workspace_bytes < L.total || (reinterpret_cast<uintptr_t>(workspace) & 255))
-        return PMP_ERR_WORKSPACE;
-    if (q.count == 0) return PMP_OK;
     char *w = static_cast<char *>(workspace);
-    long long *counts = reinterpret_cast<long long *>(w + L.counts);
-    long long *offsets = reinterpret_cast<long long *>(w + L.offsets);
-    unsigned *kin = reinterpret_cast<unsigned *>(w + L.kin), *kout = reinterpret_cast<unsigned *>(w + L.kout);
-    int *vin = reinterpret_cast<int *>(w + L.vin), *vout = reinterpret_cast<int *>(w + L.vout);
-    void *temp = w + L.temp;
-    if (cudaMemsetAsync(counts + q.count, 0, sizeof(long long), ctx->stream) != cudaSuccess) return PMP_ERR_CUDA;
-    pmp::launch_pair_count(P, S, B, q, counts, ctx->st, ctx->stream);
-    if (last_launch()) return PMP_ERR_CUDA;
-    if (pmp::scan_counts(temp, L.temp_bytes, counts, offsets, q.count + 1, ctx->stream) != cudaSuccess)
+    unsigned long long *offsets = reinterpret_cast<unsigned long long *>(w + L.offsets);
+    if (cudaMemsetAsync(pl.counts + q.count, 0, sizeof(unsigned), st) != cudaSuccess) return PMP_ERR_CUDA;
+    if (pmp::scan_counts(w + L.temp, L.temp_bytes, pl.counts, offsets, q.count + 1, st) != cudaSuccess)
         return PMP_ERR_CUDA;
-    long long total = 0;
-    if (cudaMemcpyAsync(&total, offsets + q.count, sizeof(long long), cudaMemcpyDeviceToHost, ctx->stream) !=
-            cudaSuccess ||
-        cudaStreamSynchronize(ctx->stream) != cudaSuccess)
+    unsigned long long total = 0;
+    if (cudaMemcpyAsync(&total, offsets + q.count, sizeof(total), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
         return PMP_ERR_CUDA;
-    if (total < 0 || total > L.cap) return PMP_ERR_WORKSPACE;
+    if (total > (unsigned long long)q.count * (unsigned long long)L.cap) return PMP_ERR_WORKSPACE;
     if (total == 0) return PMP_OK;
-    pmp::launch_pair_emit(P, S, B, q, offsets, kin, vin, ctx->st, ctx->stream);
-    if (last_launch()) return PMP_ERR_CUDA;
+    unsigned *k1 = reinterpret_cast<unsigned *>(w + L.skeys), *k2 = reinterpret_cast<unsigned *>(w + L.skeys2);
+    unsigned *v1 = reinterpret_cast<unsigned *>(w + L.svals), *v2 = reinterpret_cast<unsigned *>(w + L.svals2);
+    pmp::launch_sort_keys(P, B, q, pl, offsets, k1, v1, st);
     int end_bit = 1;
     while (end_bit < 32 && (1LL << end_bit) < B.ncells) ++end_bit;
-    if (pmp::sort_pairs(temp, L.temp_bytes, kin, kout, vin, vout, total, end_bit, ctx->stream) != cudaSuccess)
+    if (pmp::sort_pairs(w + L.temp, L.temp_bytes, k1, k2, v1, v2, (long long)total, end_bit, st) != cudaSuccess)
         return PMP_ERR_CUDA;
-    pmp::launch_segment_sum(P, S, state->data, B, buffer->data, q, gathered, kout, vout, offsets + q.count, total,
-                            ctx->stream);
+    pmp::launch_segment_sum(P, S, state->data, B, buffer->data, q, gathered, pl, offsets + q.count, k2, v2, st);
     return last_launch();
 }
 
@@ -330,7 +453,7 @@ pmp_status pmp_fold_ghosts(pmp_ctx *ctx, pmp_mesh *buffer)
 }
 
 pmp_status pmp_apply_limited(pmp_ctx *ctx, pmp_mesh *state, const pmp_mesh *buffer, pmp_particles *particles,
-                             const double *gathered, double *eta_out)
+                             const double *gathered, double *eta_out, void *workspace, size_t workspace_bytes)
 {
     if (!ctx) return PMP_ERR_ARG;
     Box S, B;
@@ -342,23 +465,40 @@ pmp_status pmp_apply_limited(pmp_ctx *ctx, pmp_mesh *state, const pmp_mesh *buff
         if (state->n[a] != buffer->n[a] || state->periodic[a] != buffer->periodic[a]) return PMP_ERR_ARG;
     if (overlaps(state, buffer)) return PMP_ERR_ARG;
     const KParams P = make_kparams(ctx->p, state->dx);
-    if (ctx->p.kind == PMP_KIND_SINK && particles && particles->count > 0) {
-        if (!gathered) return PMP_ERR_ARG;
-        Parts q;
-        s = make_parts(ctx, particles, &q);
+    cudaStream_t st = ctx->stream;
+    const double *eta_in = nullptr;
+    if (ctx->p.kind == PMP_KIND_SINK) {
+        const long long n = particles ? particles->count : 0;
+        const long long nv = nvalid_of(state);
+        const Layout L = layout(ctx->p, n, nv, ctx->plan_mode);
+        s = check_workspace(L, workspace, workspace_bytes);
         if (s) return s;
-        pmp::launch_return_sinks(P, S, state->data, B, buffer->data, q, gathered, ctx->st, ctx->stream);
+        s = check_plan(ctx, n, nv, workspace);
+        if (s) return s;
+        const pmp::PlanPtrs pl = plan_ptrs(L, workspace, ctx->p, ctx->plan_mode);
+        pmp::launch_sink_eta(P, S, state->data, B, buffer->data, pl.aux, pl.aux_stride, pl.eta, st);
+        if (n > 0) {
+            if (!gathered) return PMP_ERR_ARG;
+            Parts q;
+            s = make_parts(ctx, particles, &q);
+            if (s) return s;
+            pmp::launch_return_sinks(P, S, q, gathered, pl, ctx->st, st);
+        }
+        eta_in = pl.eta;
         if (last_launch()) return PMP_ERR_CUDA;
     }
-    if (cudaMemsetAsync(&ctx->st->n_limited, 0, 2 * sizeof(unsigned long long), ctx->stream) != cudaSuccess)
+    if (cudaMemsetAsync(&ctx->st->n_limited, 0, 2 * sizeof(unsigned long long), st) != cudaSuccess)
         return PMP_ERR_CUDA;
-    pmp::launch_apply(P, S, state->data, B, buffer->data, eta_out, ctx->st, ctx->stream);
+    pmp::launch_apply(P, S, state->data, B, buffer->data, eta_in, eta_out, ctx->st, st);
     return last_launch();
 }
 
 pmp_status pmp_backward(pmp_ctx *ctx, const pmp_mesh *state_in, const pmp_mesh *buffer, const pmp_particles *particles,
-                        const double *gathered, const double *gU, double *g_out)
+                        const double *gathered, const double *gU, double *g_out, void *workspace,
+                        size_t workspace_bytes)
 {
+    (void)workspace;
+    (void)workspace_bytes;
     (void)state_in;
     (void)buffer;
     (void)particles;

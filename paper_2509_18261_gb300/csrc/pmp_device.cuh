@@ -45,7 +45,9 @@ struct KParams {
     double A_sf, A_p, mu_H, RM_ej, RM_st, eps_K;
     double V, dx;    // V = (dx * dx) * dx
     double four_pi;  // 4 * pi
+    double frac[8];  // (a + 1/2) / S, a < S: sub-point positions inside a cell
     int S, S3, R, kind;
+    int Slog;        // log2(S) when S is a power of two, else -1
 };
 
 struct Parts {
@@ -358,6 +360,10 @@ __device__ __forceinline__ void sink_delta(const KParams &P, const double U[NF],
     dU[3] = -(a * (U[3] / U[0]));
     dU[4] = -(a * (U[4] / U[0]));
 }
+
+// Rows of the per-cell sink quantities (valid cells, x fastest): rho c_s,
+// rho - rho_Tr, p/rho (3), E/rho.
+enum { AUX_RCS = 0, AUX_TR, AUX_V0, AUX_V1, AUX_V2, AUX_ES, AUX_ROWS };
 
 // Gathered-row indices.
 enum { FB_MSNR = 0, FB_VSNR, FB_VX, FB_VY, FB_VZ, FB_NH, FB_RM, FB_PRAD, FB_Q, FB_E, FB_PV, FB_REGIME, FB_ROWS };

@@ -7,29 +7,51 @@
 
 namespace pmp {
 
-void launch_gather(const KParams &P, const Box &S, const double *u, const Parts &p, double *G, DevStatus *st,
-                   cudaStream_t stream);
+// Device pointers into a pass's workspace (the plan and the per-cell arrays).
+// Particle t of the processing order owns slots [t * cap, t * cap + counts[t]).
+struct PlanPtrs {
+    const unsigned *perm;             // processing order (null: index order)
+    unsigned *counts;                 // [n + 1] kernel cells per processed particle
+    unsigned long long *slots;        // [n * cap] packed cell + omega count
+    unsigned long long *hosts;        // [n] packed host cell, by particle index
+    double *wts;                      // sink: [n][3][2R+1] per-axis Gaussian factors
+    double *aux;                      // sink: [AUX_ROWS][aux_stride] per valid cell
+    long long aux_stride;
+    double *eta;                      // sink: [valid cells]
+    unsigned long long cap;           // slots per particle
+};
+
+void launch_host_keys(const Box &S, const Parts &p, unsigned *keys, unsigned *ids, cudaStream_t stream);
+void launch_plan(const KParams &P, const Box &S, const Parts &p, const PlanPtrs &pl, DevStatus *st,
+                 cudaStream_t stream);
+void launch_gather(const KParams &P, const Box &S, const double *u, const Parts &p, const PlanPtrs &pl, double *G,
+                   DevStatus *st, cudaStream_t stream);
 void launch_deposit_atomic(const KParams &P, const Box &S, const double *u, const Box &B, double *b, const Parts &p,
-                           const double *G, DevStatus *st, cudaStream_t stream);
-void launch_pair_count(const KParams &P, const Box &S, const Box &B, const Parts &p, long long *counts,
-                       DevStatus *st, cudaStream_t stream);
-void launch_pair_emit(const KParams &P, const Box &S, const Box &B, const Parts &p, const long long *offsets,
-                      unsigned *keys, int *vals, DevStatus *st, cudaStream_t stream);
+                           const double *G, const PlanPtrs &pl, cudaStream_t stream);
+void launch_sort_keys(const KParams &P, const Box &B, const Parts &p, const PlanPtrs &pl,
+                      const unsigned long long *offsets, unsigned *keys, unsigned *vals, cudaStream_t stream);
 void launch_segment_sum(const KParams &P, const Box &S, const double *u, const Box &B, double *b, const Parts &p,
-                        const double *G, const unsigned *keys, const int *vals, const long long *total_dev,
-                        long long total, cudaStream_t stream);
-void launch_return_sinks(const KParams &P, const Box &S, const double *u, const Box &B, const double *b,
-                         const Parts &p, const double *G, DevStatus *st, cudaStream_t stream);
+                        const double *G, const PlanPtrs &pl, const unsigned long long *total, const unsigned *keys,
+                        const unsigned *vals, cudaStream_t stream);
+void launch_return_sinks(const KParams &P, const Box &S, const Parts &p, const double *G, const PlanPtrs &pl,
+                         DevStatus *st, cudaStream_t stream);
+
 void launch_zero(const Box &B, double *b, cudaStream_t stream);
 void launch_fold(const Box &B, double *b, cudaStream_t stream);
-void launch_apply(const KParams &P, const Box &S, double *u, const Box &B, const double *b, double *eta_out,
-                  DevStatus *st, cudaStream_t stream);
+void launch_sink_aux(const KParams &P, const Box &S, const double *u, double *aux, long long aux_stride,
+                     cudaStream_t stream);
+void launch_sink_eta(const KParams &P, const Box &S, const double *u, const Box &B, const double *b,
+                     const double *aux, long long aux_stride, double *eta, cudaStream_t stream);
+void launch_apply(const KParams &P, const Box &S, double *u, const Box &B, const double *b, const double *eta_in,
+                  double *eta_out, DevStatus *st, cudaStream_t stream);
 
-// sorted-mode scan and sort (CUB), in pmp_sort.cu
-size_t sort_temp_bytes(long long max_pairs, long long count);
-cudaError_t scan_counts(void *temp, size_t temp_bytes, const long long *counts, long long *offsets, long long n,
-                        cudaStream_t stream);
-cudaError_t sort_pairs(void *temp, size_t temp_bytes, const unsigned *kin, unsigned *kout, const int *vin, int *vout,
-                       long long n, int end_bit, cudaStream_t stream);
+// CUB primitives, in pmp_sort.cu
+size_t cub_temp_bytes(long long n, long long max_pairs, bool sorted);
+cudaError_t sort_host_keys(void *temp, size_t temp_bytes, const unsigned *kin, unsigned *kout, const unsigned *vin,
+                           unsigned *vout, long long n, cudaStream_t stream);
+cudaError_t scan_counts(void *temp, size_t temp_bytes, const unsigned *counts, unsigned long long *offsets,
+                        long long n, cudaStream_t stream);
+cudaError_t sort_pairs(void *temp, size_t temp_bytes, const unsigned *kin, unsigned *kout, const unsigned *vin,
+                       unsigned *vout, long long n, int end_bit, cudaStream_t stream);
 
 }  // namespace pmp

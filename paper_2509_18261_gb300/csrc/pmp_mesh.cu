@@ -72,6 +72,31 @@ __global__ void __launch_bounds__(256) k_fold(Box B, double *__restrict__ b)
     }
 }
 
+// FP32 pre-check of the Eq. lambda constraint at lambda = 1, on values
+// converted from the FP64 operands: f = e_int0 rho'/rho + |p + dp|^2/(2 rho')
+// - E' with e_int0 = E - |p|^2/(2 rho).  With rho' >= rho (a deposit that adds
+// mass), every FP32 rounding, the cancellations in E - |p|^2/(2 rho) and in
+// p + dp included, perturbs f by at most a few 2^-23 M, where M = (E +
+// |p|^2/(2 rho)) rho'/rho + |p + dp|^2/(2 rho') + |E'|; in all well under
+// 2^-18 M, while the FP64 expression is within 2^-48 M of exact.  f < -2^-14 M
+// therefore means the FP64 test passes (lambda = 1) as well.  Returns false
+// when undecided (including rho' < rho, over- or underflow), so the caller
+// runs the FP64 limiter, whose first step is the exact test.
+__device__ __forceinline__ bool sn_lambda_holds_f32(const double U[NF], const double D[NF])
+{
+    const float r = (float)U[0], p0 = (float)U[1], p1 = (float)U[2], p2 = (float)U[3], E = (float)U[4];
+    const float dr = (float)D[0], d0 = (float)D[1], d1 = (float)D[2], d2 = (float)D[3], dE = (float)D[4];
+    const float r1 = r + dr, E1 = E + dE;
+    const float pp = (p0 * p0 + p1 * p1) + p2 * p2;
+    const float k0 = pp / (2.0f * r);
+    const float q = r1 / r;
+    const float n0 = p0 + d0, n1 = p1 + d1, n2 = p2 + d2;
+    const float kn = ((n0 * n0 + n1 * n1) + n2 * n2) / (2.0f * r1);
+    const float f = ((E - k0) * q + kn) - E1;
+    const float M = (fabsf(E) + k0) * q + kn + fabsf(E1);
+    return dr >= 0.0f && M > 1e-30f && M < 1e30f && f < -6.103515625e-05f * M;
+}
+
 // Steps 3 + 5 for feedback: eta = (1, l, l, l, 1) from Eq. lambda.
 __global__ void __launch_bounds__(256) k_apply_fb(Box S, double *__restrict__ u, Box B, const double *__restrict__ b,
                                                   double *__restrict__ eta_out, DevStatus *st)
@@ -90,7 +115,8 @@ __global__ void __launch_bounds__(256) k_apply_fb(Box S, double *__restrict__ u,
             U[f] = u[(long long)f * S.fs + cs];
             D[f] = __ldg(b + (long long)f * B.fs + cb);
         }
-        const double l = sn_lambda(U, D, nr);
+        double l = 1.0;
+        if (!sn_lambda_holds_f32(U, D)) l = sn_lambda(U, D, nr);
         lim = l < 1.0;
         if (eta_out) eta_out[v] = l;
         u[cs] = U[0] + D[0];
@@ -106,10 +132,62 @@ __global__ void __launch_bounds__(256) k_apply_fb(Box S, double *__restrict__ u,
     }
 }
 
-// Steps 3 + 5 for sinks: one eta for all five fields.
-__global__ void __launch_bounds__(256) k_apply_sink(KParams P, Box S, double *__restrict__ u, Box B,
-                                                    const double *__restrict__ b, double *__restrict__ eta_out,
-                                                    DevStatus *st)
+// Per-cell sink quantities, each in the order the sink formulas state it:
+// rho c_s, rho - rho_Tr (Eq. truelove), p/rho and E/rho.
+__global__ void __launch_bounds__(256) k_sink_aux(KParams P, Box S, const double *__restrict__ u,
+                                                  double *__restrict__ aux, long long as)
+{
+    const long long nvalid = (long long)S.n0 * S.n1 * S.n2;
+    const long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= nvalid) return;
+    const int i = (int)(v % S.n0);
+    const long long r = v / S.n0;
+    const int j = (int)(r % S.n1), k = (int)(r / S.n1);
+    double U[NF], cs, rtr;
+    load_cell(u, S, S.at(i, j, k), U);
+    sink_cell(P, U, cs, rtr);
+    aux[AUX_RCS * as + v] = U[0] * cs;
+    aux[AUX_TR * as + v] = U[0] - rtr;
+    aux[AUX_V0 * as + v] = U[1] / U[0];
+    aux[AUX_V1 * as + v] = U[2] / U[0];
+    aux[AUX_V2 * as + v] = U[3] / U[0];
+    aux[AUX_ES * as + v] = U[4] / U[0];
+}
+
+// Step 3 for sinks: eta per valid cell from the pre-update density, the summed
+// removal and rho - rho_Tr (accretion limiter of Sec. 3.1.1 with the floor).
+__global__ void __launch_bounds__(256) k_sink_eta(KParams P, Box S, const double *__restrict__ u, Box B,
+                                                  const double *__restrict__ b, const double *__restrict__ aux,
+                                                  long long as, double *__restrict__ eta)
+{
+    const long long nvalid = (long long)S.n0 * S.n1 * S.n2;
+    const long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= nvalid) return;
+    const int i = (int)(v % S.n0);
+    const long long r = v / S.n0;
+    const int j = (int)(r % S.n1), k = (int)(r / S.n1);
+    const double rho = __ldg(u + S.at(i, j, k));
+    const double a = -__ldg(b + B.at(i, j, k));
+    double e = 1.0;
+    if (a > 0.0) {
+        const double capr = P.cap * rho;
+        const double fl = rho - P.rho_min;
+        if (!(a <= capr && a <= fl)) {
+            double al = a < capr ? a : capr;
+            const double t = __ldg(aux + AUX_TR * as + v);
+            al = al > t ? al : t;
+            al = al < fl ? al : fl;
+            if (al < 0.0) al = 0.0;
+            e = al < a ? al / a : 1.0;
+        }
+    }
+    eta[v] = e;
+}
+
+// Steps 3 + 5 for sinks: U += eta Delta U^sum, one eta for all five fields.
+__global__ void __launch_bounds__(256) k_apply_sink(Box S, double *__restrict__ u, Box B,
+                                                    const double *__restrict__ b, const double *__restrict__ eta,
+                                                    double *__restrict__ eta_out, DevStatus *st)
 {
     const long long nvalid = (long long)S.n0 * S.n1 * S.n2;
     const long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -119,17 +197,14 @@ __global__ void __launch_bounds__(256) k_apply_sink(KParams P, Box S, double *__
         const long long r = v / S.n0;
         const int j = (int)(r % S.n1), k = (int)(r / S.n1);
         const long long cs = S.at(i, j, k), cb = B.at(i, j, k);
-        double U[NF], D[NF];
+        const double e = __ldg(eta + v);
+        lim = e < 1.0;
+        if (eta_out) eta_out[v] = e;
 #pragma unroll
         for (int f = 0; f < NF; ++f) {
-            U[f] = u[(long long)f * S.fs + cs];
-            D[f] = __ldg(b + (long long)f * B.fs + cb);
+            const double d = __ldg(b + (long long)f * B.fs + cb);
+            u[(long long)f * S.fs + cs] = u[(long long)f * S.fs + cs] + (e == 1.0 ? d : e * d);
         }
-        const double eta = sink_eta(P, U, D);
-        lim = eta < 1.0;
-        if (eta_out) eta_out[v] = eta;
-#pragma unroll
-        for (int f = 0; f < NF; ++f) u[(long long)f * S.fs + cs] = U[f] + eta * D[f];
     }
     const unsigned m1 = __ballot_sync(0xffffffffu, lim);
     if ((threadIdx.x & 31) == 0 && m1) atomicAdd(&st->n_limited, (unsigned long long)__popc(m1));
@@ -147,13 +222,27 @@ void launch_fold(const Box &B, double *b, cudaStream_t stream)
     k_fold<<<(unsigned)((threads + 255) / 256), 256, 0, stream>>>(B, b);
 }
 
-void launch_apply(const KParams &P, const Box &S, double *u, const Box &B, const double *b, double *eta_out,
-                  DevStatus *st, cudaStream_t stream)
+void launch_sink_aux(const KParams &P, const Box &S, const double *u, double *aux, long long aux_stride,
+                     cudaStream_t stream)
+{
+    const long long nvalid = (long long)S.n0 * S.n1 * S.n2;
+    k_sink_aux<<<(unsigned)((nvalid + 255) / 256), 256, 0, stream>>>(P, S, u, aux, aux_stride);
+}
+
+void launch_sink_eta(const KParams &P, const Box &S, const double *u, const Box &B, const double *b,
+                     const double *aux, long long aux_stride, double *eta, cudaStream_t stream)
+{
+    const long long nvalid = (long long)S.n0 * S.n1 * S.n2;
+    k_sink_eta<<<(unsigned)((nvalid + 255) / 256), 256, 0, stream>>>(P, S, u, B, b, aux, aux_stride, eta);
+}
+
+void launch_apply(const KParams &P, const Box &S, double *u, const Box &B, const double *b, const double *eta_in,
+                  double *eta_out, DevStatus *st, cudaStream_t stream)
 {
     const long long nvalid = (long long)S.n0 * S.n1 * S.n2;
     const unsigned nb = (unsigned)((nvalid + 255) / 256);
     if (P.kind == PMP_KIND_FEEDBACK) k_apply_fb<<<nb, 256, 0, stream>>>(S, u, B, b, eta_out, st);
-    else k_apply_sink<<<nb, 256, 0, stream>>>(P, S, u, B, b, eta_out, st);
+    else k_apply_sink<<<nb, 256, 0, stream>>>(S, u, B, b, eta_in, eta_out, st);
 }
 
 }  // namespace pmp

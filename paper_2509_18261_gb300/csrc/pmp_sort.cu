@@ -1,5 +1,6 @@
-// pmp_sort.cu -- prefix sum of pair counts and the stable radix sort of
-// (cell, particle) pairs for the sorted deposit (CUB primitives).
+// pmp_sort.cu -- CUB primitives of the plan and the sorted deposit: the radix
+// sort of particles by host cell, the prefix sum of pair counts, and the
+// stable radix sort of (buffer cell, pair) keys.
 #include <cub/device/device_radix_sort.cuh>
 #include <cub/device/device_scan.cuh>
 
@@ -7,23 +8,39 @@
 
 namespace pmp {
 
-size_t sort_temp_bytes(long long max_pairs, long long count)
+size_t cub_temp_bytes(long long n, long long max_pairs, bool sorted)
 {
-    size_t a = 0, b = 0;
-    cub::DeviceScan::ExclusiveSum(nullptr, a, (const long long *)nullptr, (long long *)nullptr, count + 1);
-    cub::DeviceRadixSort::SortPairs(nullptr, b, (const unsigned *)nullptr, (unsigned *)nullptr, (const int *)nullptr,
-                                    (int *)nullptr, max_pairs, 0, 32);
-    return a > b ? a : b;
+    size_t a = 0, b = 0, c = 0;
+    const long long nn = n > 0 ? n : 1;
+    cub::DeviceRadixSort::SortPairs(nullptr, a, (const unsigned *)nullptr, (unsigned *)nullptr,
+                                    (const unsigned *)nullptr, (unsigned *)nullptr, nn, 0, 32);
+    if (sorted)
+        cub::DeviceScan::ExclusiveScan(nullptr, b, (const unsigned *)nullptr, (unsigned long long *)nullptr,
+                                       cuda::std::plus<unsigned long long>(), 0ULL, nn + 1);
+    if (sorted)
+        cub::DeviceRadixSort::SortPairs(nullptr, c, (const unsigned *)nullptr, (unsigned *)nullptr,
+                                        (const unsigned *)nullptr, (unsigned *)nullptr,
+                                        max_pairs > 0 ? max_pairs : 1, 0, 32);
+    size_t m = a > b ? a : b;
+    return m > c ? m : c;
 }
 
-cudaError_t scan_counts(void *temp, size_t temp_bytes, const long long *counts, long long *offsets, long long n,
-                        cudaStream_t stream)
+cudaError_t sort_host_keys(void *temp, size_t temp_bytes, const unsigned *kin, unsigned *kout, const unsigned *vin,
+                           unsigned *vout, long long n, cudaStream_t stream)
 {
-    return cub::DeviceScan::ExclusiveSum(temp, temp_bytes, counts, offsets, n, stream);
+    return cub::DeviceRadixSort::SortPairs(temp, temp_bytes, kin, kout, vin, vout, n, 0, 32, stream);
 }
 
-cudaError_t sort_pairs(void *temp, size_t temp_bytes, const unsigned *kin, unsigned *kout, const int *vin, int *vout,
-                       long long n, int end_bit, cudaStream_t stream)
+// Exclusive prefix sum of 32-bit counts accumulated in 64 bits.
+cudaError_t scan_counts(void *temp, size_t temp_bytes, const unsigned *counts, unsigned long long *offsets,
+                        long long n, cudaStream_t stream)
+{
+    return cub::DeviceScan::ExclusiveScan(temp, temp_bytes, counts, offsets, cuda::std::plus<unsigned long long>(),
+                                          0ULL, n, stream);
+}
+
+cudaError_t sort_pairs(void *temp, size_t temp_bytes, const unsigned *kin, unsigned *kout, const unsigned *vin,
+                       unsigned *vout, long long n, int end_bit, cudaStream_t stream)
 {
     return cub::DeviceRadixSort::SortPairs(temp, temp_bytes, kin, kout, vin, vout, n, 0, end_bit, stream);
 }

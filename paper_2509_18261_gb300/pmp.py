@@ -86,11 +86,11 @@ def load():
         "pmp_gathered_rows": ([i32], i32),
         "pmp_workspace_size": ([vp, M, i64, i32, ctypes.POINTER(ctypes.c_size_t)], i32),
         "pmp_zero_buffer": ([vp, M], i32),
-        "pmp_gather": ([vp, M, Pa, vp], i32),
+        "pmp_gather": ([vp, M, Pa, vp, i32, vp, ctypes.c_size_t], i32),
         "pmp_deposit": ([vp, M, Pa, vp, M, i32, vp, ctypes.c_size_t], i32),
         "pmp_fold_ghosts": ([vp, M], i32),
-        "pmp_apply_limited": ([vp, M, M, Pa, vp, vp], i32),
-        "pmp_backward": ([vp, M, M, Pa, vp, vp, vp], i32),
+        "pmp_apply_limited": ([vp, M, M, Pa, vp, vp, vp, ctypes.c_size_t], i32),
+        "pmp_backward": ([vp, M, M, Pa, vp, vp, vp, vp, ctypes.c_size_t], i32),
         "pmp_get_error": ([vp, ctypes.POINTER(i32), ctypes.POINTER(i64)], i32),
         "pmp_limiter_counts": ([vp, ctypes.POINTER(i64)], i32),
     }
@@ -194,20 +194,26 @@ def pmp_zero_buffer(ctx, buffer):
     _check("pmp_zero_buffer", load().pmp_zero_buffer(ctx.h, ctypes.byref(buffer.c())))
 
 
-def pmp_gather(ctx, state, parts, gathered):
+def _ws(workspace):
+    if workspace is None:
+        return None, 0
+    if not workspace.is_cuda or not workspace.is_contiguous():
+        raise ValueError("workspace must be a contiguous CUDA tensor")
+    return ctypes.c_void_p(workspace.data_ptr()), workspace.numel() * workspace.element_size()
+
+
+def pmp_gather(ctx, state, parts, gathered, mode="atomic", workspace=None):
     ctx._sync_stream()
     pp = _parts(parts)
-    _check("pmp_gather", load().pmp_gather(ctx.h, ctypes.byref(state.c()), ctypes.byref(pp), _ptr(gathered)))
+    ws, wsb = _ws(workspace)
+    _check("pmp_gather", load().pmp_gather(ctx.h, ctypes.byref(state.c()), ctypes.byref(pp), _ptr(gathered),
+                                           MODES.get(mode, mode), ws, wsb))
 
 
 def pmp_deposit(ctx, state, parts, gathered, buffer, mode="atomic", workspace=None):
     ctx._sync_stream()
     pp = _parts(parts)
-    ws, wsb = None, 0
-    if workspace is not None:
-        if not workspace.is_cuda or not workspace.is_contiguous():
-            raise ValueError("workspace must be a contiguous CUDA tensor")
-        ws, wsb = ctypes.c_void_p(workspace.data_ptr()), workspace.numel() * workspace.element_size()
+    ws, wsb = _ws(workspace)
     _check("pmp_deposit", load().pmp_deposit(ctx.h, ctypes.byref(state.c()), ctypes.byref(pp), _ptr(gathered),
                                              ctypes.byref(buffer.c()), MODES.get(mode, mode), ws, wsb))
 
@@ -217,19 +223,22 @@ def pmp_fold_ghosts(ctx, buffer):
     _check("pmp_fold_ghosts", load().pmp_fold_ghosts(ctx.h, ctypes.byref(buffer.c())))
 
 
-def pmp_apply_limited(ctx, state, buffer, parts=None, gathered=None, eta_out=None):
+def pmp_apply_limited(ctx, state, buffer, parts=None, gathered=None, eta_out=None, workspace=None):
     ctx._sync_stream()
     pp = _parts(parts)
+    ws, wsb = _ws(workspace)
     _check("pmp_apply_limited",
            load().pmp_apply_limited(ctx.h, ctypes.byref(state.c()), ctypes.byref(buffer.c()),
-                                    ctypes.byref(pp) if pp is not None else None, _ptr(gathered), _ptr(eta_out)))
+                                    ctypes.byref(pp) if pp is not None else None, _ptr(gathered), _ptr(eta_out),
+                                    ws, wsb))
 
 
-def pmp_backward(ctx, state_in, buffer, parts, gathered, gU, g_out):
+def pmp_backward(ctx, state_in, buffer, parts, gathered, gU, g_out, workspace=None):
     ctx._sync_stream()
     pp = _parts(parts)
+    ws, wsb = _ws(workspace)
     _check("pmp_backward", load().pmp_backward(ctx.h, ctypes.byref(state_in.c()), ctypes.byref(buffer.c()),
-                                               ctypes.byref(pp), _ptr(gathered), _ptr(gU), _ptr(g_out)))
+                                               ctypes.byref(pp), _ptr(gathered), _ptr(gU), _ptr(g_out), ws, wsb))
 
 
 def pmp_get_error(ctx):
@@ -273,10 +282,8 @@ class Pass:
         n = int(parts["x"].numel()) if parts is not None else 0
         self.gathered = torch.empty((pmp_gathered_rows(params["kind"]), max(n, 1)), dtype=torch.float64, device=dev)
         self.eta = torch.empty(box.ncells_valid, dtype=torch.float64, device=dev) if want_eta else None
-        self.workspace = None
-        if mode == "sorted":
-            nbytes = pmp_workspace_size(self.ctx, self.buffer, n, "sorted")
-            self.workspace = torch.empty(max(nbytes, 1), dtype=torch.uint8, device=dev)
+        nbytes = pmp_workspace_size(self.ctx, self.buffer, n, mode)
+        self.workspace = torch.empty(max(nbytes, 1), dtype=torch.uint8, device=dev)
 
     def gathered_view(self):
         n = int(self.parts["x"].numel())
@@ -284,15 +291,21 @@ class Pass:
 
     def run(self, stop_after=None):
         c = self.ctx
+        has = self.parts is not None and self.parts["x"].numel() > 0
         pmp_zero_buffer(c, self.buffer)
-        if self.parts is not None and self.parts["x"].numel() > 0:
-            pmp_gather(c, self.state, self.parts, self.gathered)
+        pmp_gather(c, self.state, self.parts if has else _EMPTY(self.state.data.device), self.gathered, self.mode,
+                   self.workspace)
+        if has:
             pmp_deposit(c, self.state, self.parts, self.gathered, self.buffer, self.mode, self.workspace)
         if stop_after == "deposit":
             return
         pmp_fold_ghosts(c, self.buffer)
         if stop_after == "fold":
             return
-        has = self.parts is not None and self.parts["x"].numel() > 0
         pmp_apply_limited(c, self.state, self.buffer, self.parts if has else None, self.gathered if has else None,
-                          self.eta)
+                          self.eta, self.workspace)
+
+
+def _EMPTY(device):
+    z = torch.zeros(1, dtype=torch.float64, device=device)
+    return {k: z[:0] for k in ("x", "y", "z", "m", "px", "py", "pz", "e")}

@@ -61,19 +61,21 @@ def test_host_argument_errors_raise():
     st = torch.from_numpy(syn.gas_state(np.random.default_rng(1), box)).cuda()
     parts = pmp.parts_to_device(_cloud(box.n, 4))
     ps = pmp.Pass(syn.feedback_params(), box, st, parts)
-    pmp.pmp_gather(ps.ctx, ps.state, parts, ps.gathered)
+    pmp.pmp_gather(ps.ctx, ps.state, parts, ps.gathered, "atomic", ps.workspace)
     with pytest.raises(pmp.PMPError) as e:
-        pmp.pmp_deposit(ps.ctx, ps.state, parts, ps.gathered, ps.buffer, "atomic")
+        pmp.pmp_deposit(ps.ctx, ps.state, parts, ps.gathered, ps.buffer, "atomic", ps.workspace)
     assert e.value.code == 2
     box2 = syn.Box((8, 8, 8), 2)
     st2 = torch.from_numpy(syn.gas_state(np.random.default_rng(1), box2)).cuda()
     ps2 = pmp.Pass(syn.feedback_params(), box2, st2, parts, mode="sorted")
-    pmp.pmp_gather(ps2.ctx, ps2.state, parts, ps2.gathered)
-    with pytest.raises(pmp.PMPError) as e:
-        pmp.pmp_deposit(ps2.ctx, ps2.state, parts, ps2.gathered, ps2.buffer, "sorted", ps2.workspace[:1024])
+    with pytest.raises(pmp.PMPError) as e:  # workspace smaller than pmp_workspace_size
+        pmp.pmp_gather(ps2.ctx, ps2.state, parts, ps2.gathered, "sorted", ps2.workspace[:1024])
     assert e.value.code == 6
-    # state and buffer may not overlap
-    with pytest.raises(pmp.PMPError) as e:
-        pmp.pmp_deposit(ps2.ctx, ps2.state, parts, ps2.gathered, ps2.state, "atomic")
+    pmp.pmp_gather(ps2.ctx, ps2.state, parts, ps2.gathered, "sorted", ps2.workspace)
+    with pytest.raises(pmp.PMPError) as e:  # a plan built for another mode
+        pmp.pmp_deposit(ps2.ctx, ps2.state, parts, ps2.gathered, ps2.buffer, "atomic", ps2.workspace)
+    assert e.value.code == 6
+    with pytest.raises(pmp.PMPError) as e:  # state and buffer may not overlap
+        pmp.pmp_deposit(ps2.ctx, ps2.state, parts, ps2.gathered, ps2.state, "sorted", ps2.workspace)
     assert e.value.code == 1
     assert pmp.pmp_get_error(ps2.ctx) == (0, -1)
