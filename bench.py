@@ -168,9 +168,47 @@ def kernel_cell_count(parts, n, rK, chunk=1 << 20):
     return total
 
 
-# canonical FP64 operations per pair / per cell (add, sub, mul, div, sqrt = 1)
-FLOPS_PER_PAIR = {"fb_gather": 9, "fb_deposit": 29, "sink_gather": 27, "sink_deposit": 21, "sink_return": 30}
-BYTES_PER_CELL = {"zero": 40, "apply": 120}
+
+
+# Algorithmic work per kernel launch.  Particle kernels: canonical FP64
+# operations per (particle, kernel cell) pair; cell kernels: bytes a perfect
+# implementation moves.  See the kernel table of the design notes.
+FLOPS_PER_PAIR = {"fb_gather": 9, "fb_deposit": 29, "sink_gather": 8, "sink_deposit": 7, "sink_return": 14}
+FP32_PEAK_TOPS = 36.9  # measured FP32 instruction rate of this GB300 (dependent-free FFMA stream)
+
+
+def roofline(kernel, ms, pairs, box, n_fb, n_sk, hbm_peak, peak_src):
+    kind, stage = kernel.split("_", 1)
+    nvalid = box.ncells_valid
+    hbm_bytes = {
+        "zero": 40 * box.ncells_padded,
+        "fold": 120 * (box.ncells_padded - nvalid),
+        "apply": 120 * nvalid + (8 * nvalid if kind == "sink" else 0),
+        "cell_records": (40 + 96) * nvalid,
+        "eta": (8 + 8 + 8 + 16) * nvalid,
+    }
+    if stage == "plan":
+        # FP32 decisions: 2 adds per candidate cell and per omega sub-point
+        W = 2 * (2 if kind == "fb" else 4) + 1
+        S3 = 64 if kind == "fb" else 0
+        nparts = n_fb if kind == "fb" else n_sk
+        ops = 2 * W ** 3 * nparts + 2 * S3 * pairs[kind]
+        achieved = ops / (ms * 1e-3) / 1e12
+        r = {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TOPS, "unit": "Tops/s (FP32)",
+             "frac": achieved / FP32_PEAK_TOPS, "peak_source": "measured FP32 issue rate"}
+    elif stage in hbm_bytes:
+        achieved = hbm_bytes[stage] / (ms * 1e-3) / 1e9
+        r = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
+             "peak_source": peak_src}
+    else:
+        flops = FLOPS_PER_PAIR.get(kernel, 0) * pairs[kind]
+        achieved = flops / (ms * 1e-3) / 1e12
+        r = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+             "frac": achieved / FP64_PEAK_TFLOPS, "peak_source": "nominal FP64, 152 SMs x 2 DFMA/clk x 2.07 GHz"}
+    r["kernel"] = kernel
+    r["ms_per_launch"] = ms
+    r["traffic"] = profiled_traffic(kernel)
+    return r
 
 
 def src_digest():
@@ -231,11 +269,11 @@ def run_ours(args, world, rank, local):
 
     phases = ["fb_zero", "fb_gather", "fb_deposit", "fb_fold", "fb_apply",
               "sink_zero", "sink_gather", "sink_deposit", "sink_fold", "sink_apply"]
-    # own kernels per step: zero, [host keys], plan count, plan emit, gather,
-    # deposit (+ sort keys, segment sum when sorted), fold, apply; sinks add the
-    # per-cell quantities, eta and the Step-4 return
-    per_pass = 7 + (0 if args.mode == "sorted" else 1) + (1 if args.mode == "sorted" else 0)
-    launches_per_step = 2 * per_pass + 3
+    # own kernels per step.  Supernova pass: zero, prologue, plan, gather,
+    # deposit, fold, apply (fast + queued); sink pass: zero, prologue, plan,
+    # per-cell quantities, gather, deposit, fold, eta, Step-4 return, apply.
+    # The sorted deposit adds a key kernel and a segment kernel per pass.
+    launches_per_step = 18 if args.mode == "atomic" else 20
     state0 = state.clone()
     sink0 = {k: sk[k].clone() for k in ("m", "px", "py", "pz")}
 
@@ -279,6 +317,9 @@ def run_ours(args, world, rank, local):
         if code:
             raise RuntimeError(f"device error {code} at {idx}")
 
+    for ps in (P_fb, P_sk):
+        pmp.pmp_timing_read(ps.ctx)
+        pmp.pmp_timing_enable(ps.ctx, True)
     clocks = Clocks(local)
     clocks.start()
     barrier(world)
@@ -303,6 +344,11 @@ def run_ours(args, world, rank, local):
             for i in range(5):
                 name = phases[p * 5 + i]
                 phase_ms[name] = phase_ms.get(name, 0.0) + m[i].elapsed_time(m[i + 1]) / args.steps
+    kernel_ms = {}
+    for tag, ps in (("fb", P_fb), ("sink", P_sk)):
+        for name, (nl, ms) in pmp.pmp_timing_read(ps.ctx).items():
+            kernel_ms[f"{tag}_{name}"] = (nl / args.steps, ms / nl)
+        pmp.pmp_timing_enable(ps.ctx, False)
     lim_fb = pmp.pmp_limiter_counts(P_fb.ctx)
     lim_sk = pmp.pmp_limiter_counts(P_sk.ctx)
 
@@ -334,40 +380,20 @@ def run_ours(args, world, rank, local):
     barrier(world)
     e2e_ms = max_over_ranks(world, e0.elapsed_time(e1) / args.e2e_steps)
 
-    # roofline of the dominant kernel
+    # roofline of the dominant kernel (per-launch time from the library's
+    # CUDA events on the launching stream)
     pairs = {"fb": kernel_cell_count(fb, box.n, w["fb_params"]["r_K"]),
              "sink": kernel_cell_count(sk, box.n, w["sink_params"]["r_K"])}
-    dominant = max(phase_ms, key=phase_ms.get)
     hbm_peak, peak_src = peaks()
-    kind = dominant.split("_")[0]
-    stage = dominant.split("_", 1)[1]
-    ncells_valid = box.ncells_valid
-    if stage in ("zero", "apply", "fold"):
-        if stage == "zero":
-            nbytes = BYTES_PER_CELL["zero"] * box.ncells_padded
-        elif stage == "apply":
-            nbytes = BYTES_PER_CELL["apply"] * ncells_valid
-            if kind == "sink":
-                nbytes += n_sk * 64 + pairs["sink"] * 80
-        else:
-            nbytes = 120 * (box.ncells_padded - ncells_valid)
-        achieved = nbytes / (phase_ms[dominant] * 1e-3) / 1e9
-        roof = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                "frac": achieved / hbm_peak, "peak_source": peak_src}
-    else:
-        key = f"{kind}_{stage}"
-        flops = FLOPS_PER_PAIR.get(key, 0) * pairs[kind]
-        achieved = flops / (phase_ms[dominant] * 1e-3) / 1e12
-        roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP64_PEAK_TFLOPS, "peak_source": "nominal FP64 (derived)"}
-    roof["kernel"] = dominant
-    roof["traffic"] = profiled_traffic(dominant)
+    step_ms_by_kernel = {k: nl * ms for k, (nl, ms) in kernel_ms.items()}
+    dominant = max(step_ms_by_kernel, key=step_ms_by_kernel.get)
+    roof = roofline(dominant, kernel_ms[dominant][1], pairs, box, n_fb, n_sk, hbm_peak, peak_src)
 
     result = {
         "metric": METRIC,
         "value": n_particles * world / (ms_per_step * 1e-3),
         "unit": "particles/s",
-        "cells_per_s": ncells_valid * world / (ms_per_step * 1e-3),
+        "cells_per_s": box.ncells_valid * world / (ms_per_step * 1e-3),
         "n_gpus": world,
         "steps": args.steps,
         "warmup": args.warmup,
@@ -387,6 +413,7 @@ def run_ours(args, world, rank, local):
             "kernel_pairs": pairs,
         },
         "phases_ms": {k: round(v, 4) for k, v in phase_ms.items()},
+        "kernels_ms_per_launch": {k: round(v[1], 4) for k, v in sorted(kernel_ms.items())},
         "limiter": {"fb_cells_eta_lt_1": lim_fb[0], "fb_noroot": lim_fb[1], "sink_cells_eta_lt_1": lim_sk[0]},
         "roofline": roof,
         "e2e": {"value": n_particles * world / (e2e_ms * 1e-3), "unit": "particles/s",

@@ -233,6 +233,20 @@ pmp_status pmp_get_error(pmp_ctx *ctx, int32_t *code, int64_t *index);
  * for which Eq. lambda had no root in [0, 1] (lambda set to 0). */
 pmp_status pmp_limiter_counts(pmp_ctx *ctx, int64_t *counts);
 
+/* Per-kernel timing.  When enabled, every kernel the context launches is
+ * bracketed by two CUDA events recorded on the context's stream.
+ * pmp_timing_read synchronises the stream, sums the bracketed durations per
+ * kernel name into `out` (host array of `max` entries; *n receives the number
+ * of distinct names, which may exceed max), and forgets the recorded events. */
+typedef struct {
+    char name[24];    /* e.g. "plan", "gather", "deposit", "fold", "apply" */
+    int64_t launches; /* launches summed */
+    double ms;        /* total duration, milliseconds */
+} pmp_kernel_time;
+
+pmp_status pmp_timing_enable(pmp_ctx *ctx, int32_t on);
+pmp_status pmp_timing_read(pmp_ctx *ctx, pmp_kernel_time *out, int32_t max, int32_t *n);
+
 #ifdef __cplusplus
 }
 #endif

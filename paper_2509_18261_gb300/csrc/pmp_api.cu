@@ -5,6 +5,8 @@
 #include <cstdlib>
 #include <cstring>
 #include <new>
+#include <string>
+#include <vector>
 
 #include "pmp.h"
 #include "pmp_device.cuh"
@@ -20,7 +22,51 @@ struct pmp_ctx {
     long long plan_n;
     long long plan_nvalid;
     int plan_mode;
+    // per-kernel CUDA-event timing (pmp_timing_enable)
+    bool timing;
+    struct Mark {
+        const char *name;
+        cudaEvent_t a, b;
+    };
+    std::vector<Mark> marks;
+    std::vector<cudaEvent_t> pool;
 };
+
+namespace {
+
+cudaEvent_t take_event(pmp_ctx *c)
+{
+    cudaEvent_t e;
+    if (!c->pool.empty()) {
+        e = c->pool.back();
+        c->pool.pop_back();
+    } else if (cudaEventCreate(&e) != cudaSuccess) {
+        e = nullptr;
+    }
+    return e;
+}
+
+// Brackets the kernel launched in its scope with two events on the context's
+// stream when timing is on.
+struct Timed {
+    pmp_ctx *c;
+    size_t idx;
+    Timed(pmp_ctx *ctx, const char *name) : c(ctx), idx((size_t)-1)
+    {
+        if (!c->timing) return;
+        pmp_ctx::Mark m{name, take_event(c), take_event(c)};
+        if (!m.a || !m.b) return;
+        cudaEventRecord(m.a, c->stream);
+        c->marks.push_back(m);
+        idx = c->marks.size() - 1;
+    }
+    ~Timed()
+    {
+        if (idx != (size_t)-1) cudaEventRecord(c->marks[idx].b, c->stream);
+    }
+};
+
+}  // namespace
 
 namespace {
 
@@ -79,6 +125,13 @@ KParams make_kparams(const pmp_params &p, double dx)
     k.Slog = -1;
     for (int b = 0; b < 4; ++b)
         if (k.S == (1 << b)) k.Slog = b;
+    for (int a = 0; a < 8; ++a) k.fracf[a] = (float)k.frac[a];
+    // FP32 band r2 (1 -/+ 2^-14), rounded outward
+    const double lo = k.r2 * (1.0 - 6.103515625e-05), hi = k.r2 * (1.0 + 6.103515625e-05);
+    k.band_lo = (float)lo;
+    if ((double)k.band_lo > lo) k.band_lo = std::nextafter(k.band_lo, 0.0f);
+    k.band_hi = (float)hi;
+    if ((double)k.band_hi < hi) k.band_hi = std::nextafter(k.band_hi, 3.0e38f);
     k.R = (int)std::ceil(p.r_K);
     k.kind = p.kind;
     return k;
@@ -186,7 +239,8 @@ long long max_pairs_per_particle(double rK)
 }
 
 struct Layout {
-    size_t keys, ids, keys2, ids2, counts, slots, hosts, wts, aux, eta, offsets, skeys, skeys2, svals, svals2;
+    size_t keys, ids, keys2, ids2, counts, slots, hosts, fr, wts, aux, eta, queue, qcount, offsets, skeys, skeys2,
+        svals, svals2;
     size_t temp, temp_bytes, total;
     long long cap, aux_stride;
 };
@@ -218,10 +272,14 @@ Layout layout(const pmp_params &p, long long n, long long nvalid, int mode)
     L.counts = take(4 * (n1 + 1));
     L.slots = take(8 * pairs);
     L.hosts = take(8 * n1);
+    L.fr = take(16 * n1);
     if (sink) {
         L.wts = take(8 * n1 * 3 * (size_t)W);
-        L.aux = take(8 * (size_t)pmp::AUX_ROWS * (size_t)(nvalid > 0 ? nvalid : 1));
+        L.aux = take(8 * 2 * (size_t)pmp::kRec * (size_t)(nvalid > 0 ? nvalid : 1));
         L.eta = take(8 * (size_t)(nvalid > 0 ? nvalid : 1));
+    } else {
+        L.queue = take(4 * (size_t)(nvalid > 0 ? nvalid : 1));
+        L.qcount = take(8);
     }
     if (sorted) {
         L.offsets = take(8 * (n1 + 1));
@@ -236,6 +294,8 @@ Layout layout(const pmp_params &p, long long n, long long nvalid, int mode)
     return L;
 }
 
+long long nvalid_rows(const Layout &L) { return L.aux_stride; }
+
 pmp::PlanPtrs plan_ptrs(const Layout &L, void *ws, const pmp_params &p, int mode)
 {
     char *w = static_cast<char *>(ws);
@@ -245,12 +305,13 @@ pmp::PlanPtrs plan_ptrs(const Layout &L, void *ws, const pmp_params &p, int mode
     pl.counts = reinterpret_cast<unsigned *>(w + L.counts);
     pl.slots = reinterpret_cast<unsigned long long *>(w + L.slots);
     pl.hosts = reinterpret_cast<unsigned long long *>(w + L.hosts);
+    pl.fr = reinterpret_cast<float4 *>(w + L.fr);
     if (p.kind == PMP_KIND_SINK) {
         pl.wts = reinterpret_cast<double *>(w + L.wts);
-        pl.aux = reinterpret_cast<double *>(w + L.aux);
+        pl.grec = reinterpret_cast<double *>(w + L.aux);
+        pl.drec = pl.grec + (size_t)pmp::kRec * (size_t)(nvalid_rows(L) > 0 ? nvalid_rows(L) : 1);
         pl.eta = reinterpret_cast<double *>(w + L.eta);
     }
-    pl.aux_stride = L.aux_stride;
     pl.cap = (unsigned long long)L.cap;
     return pl;
 }
@@ -282,6 +343,7 @@ pmp_status pmp_create(pmp_ctx **out, const pmp_params *params, pmp_stream stream
     c->plan_n = -1;
     c->plan_nvalid = -1;
     c->plan_mode = PMP_MODE_ATOMIC;
+    c->timing = false;
     if (cudaGetDevice(&c->device) != cudaSuccess || cudaMalloc(&c->st, sizeof(pmp::DevStatus)) != cudaSuccess ||
         cudaMemset(c->st, 0, sizeof(pmp::DevStatus)) != cudaSuccess) {
         if (c->st) cudaFree(c->st);
@@ -296,8 +358,47 @@ void pmp_destroy(pmp_ctx *ctx)
 {
     if (!ctx) return;
     cudaStreamSynchronize(ctx->stream);
+    for (auto &m : ctx->marks) {
+        cudaEventDestroy(m.a);
+        cudaEventDestroy(m.b);
+    }
+    for (auto e : ctx->pool) cudaEventDestroy(e);
     cudaFree(ctx->st);
     delete ctx;
+}
+
+pmp_status pmp_timing_enable(pmp_ctx *ctx, int32_t on)
+{
+    if (!ctx) return PMP_ERR_ARG;
+    ctx->timing = on != 0;
+    return PMP_OK;
+}
+
+pmp_status pmp_timing_read(pmp_ctx *ctx, pmp_kernel_time *out, int32_t max, int32_t *n)
+{
+    if (!ctx || !n || (max > 0 && !out)) return PMP_ERR_ARG;
+    if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return PMP_ERR_CUDA;
+    std::vector<pmp_kernel_time> acc;
+    for (auto &m : ctx->marks) {
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, m.a, m.b);
+        size_t k = 0;
+        while (k < acc.size() && std::string(acc[k].name) != m.name) ++k;
+        if (k == acc.size()) {
+            pmp_kernel_time z;
+            std::memset(&z, 0, sizeof(z));
+            std::strncpy(z.name, m.name, sizeof(z.name) - 1);
+            acc.push_back(z);
+        }
+        acc[k].launches += 1;
+        acc[k].ms += ms;
+        ctx->pool.push_back(m.a);
+        ctx->pool.push_back(m.b);
+    }
+    ctx->marks.clear();
+    *n = (int32_t)acc.size();
+    for (int32_t k = 0; k < *n && k < max; ++k) out[k] = acc[k];
+    return PMP_OK;
 }
 
 pmp_status pmp_set_stream(pmp_ctx *ctx, pmp_stream stream)
@@ -329,7 +430,10 @@ pmp_status pmp_zero_buffer(pmp_ctx *ctx, pmp_mesh *buffer)
     Box B;
     pmp_status s = make_box(buffer, &B);
     if (s) return s;
-    pmp::launch_zero(B, buffer->data, ctx->stream);
+    {
+        Timed tm(ctx, "zero");
+        pmp::launch_zero(B, buffer->data, ctx->stream);
+    }
     return last_launch();
 }
 
@@ -368,14 +472,28 @@ pmp_status pmp_gather(pmp_ctx *ctx, const pmp_mesh *state, const pmp_particles *
             unsigned *keys = reinterpret_cast<unsigned *>(w + L.keys), *ids = reinterpret_cast<unsigned *>(w + L.ids);
             unsigned *keys2 = reinterpret_cast<unsigned *>(w + L.keys2),
                      *ids2 = reinterpret_cast<unsigned *>(w + L.ids2);
-            pmp::launch_host_keys(S, q, keys, ids, st);
+            {
+                Timed tm(ctx, "prologue");
+                pmp::launch_prologue(S, q, keys, ids, pl, ctx->st, st);
+            }
+            Timed tm(ctx, "order_sort");
             if (pmp::sort_host_keys(temp, L.temp_bytes, keys, keys2, ids, ids2, q.count, st) != cudaSuccess)
                 return PMP_ERR_CUDA;
+        } else {
+            Timed tm(ctx, "prologue");
+            pmp::launch_prologue(S, q, nullptr, nullptr, pl, ctx->st, st);
         }
+        Timed tm(ctx, "plan");
         pmp::launch_plan(P, S, q, pl, ctx->st, st);
     }
-    if (ctx->p.kind == PMP_KIND_SINK) pmp::launch_sink_aux(P, S, state->data, pl.aux, pl.aux_stride, st);
-    if (q.count > 0) pmp::launch_gather(P, S, state->data, q, pl, gathered, ctx->st, st);
+    if (ctx->p.kind == PMP_KIND_SINK) {
+        Timed tm(ctx, "cell_records");
+        pmp::launch_sink_aux(P, S, state->data, pl.grec, pl.drec, st);
+    }
+    if (q.count > 0) {
+        Timed tm(ctx, "gather");
+        pmp::launch_gather(P, S, state->data, q, pl, gathered, ctx->st, st);
+    }
     s = last_launch();
     if (s) return s;
     ctx->plan_ws = workspace;
@@ -414,7 +532,10 @@ pmp_status pmp_deposit(pmp_ctx *ctx, const pmp_mesh *state, const pmp_particles 
     const pmp::PlanPtrs pl = plan_ptrs(L, workspace, ctx->p, mode);
     cudaStream_t st = ctx->stream;
     if (mode == PMP_MODE_ATOMIC) {
-        pmp::launch_deposit_atomic(P, S, state->data, B, buffer->data, q, gathered, pl, st);
+        {
+            Timed tm(ctx, "deposit");
+            pmp::launch_deposit_atomic(P, S, state->data, B, buffer->data, q, gathered, pl, st);
+        }
         return last_launch();
     }
     if (B.ncells > 0xffffffffLL) return PMP_ERR_ARG;
@@ -431,12 +552,18 @@ pmp_status pmp_deposit(pmp_ctx *ctx, const pmp_mesh *state, const pmp_particles 
     if (total == 0) return PMP_OK;
     unsigned *k1 = reinterpret_cast<unsigned *>(w + L.skeys), *k2 = reinterpret_cast<unsigned *>(w + L.skeys2);
     unsigned *v1 = reinterpret_cast<unsigned *>(w + L.svals), *v2 = reinterpret_cast<unsigned *>(w + L.svals2);
-    pmp::launch_sort_keys(P, B, q, pl, offsets, k1, v1, st);
+    {
+        Timed tm(ctx, "sort_keys");
+        pmp::launch_sort_keys(P, B, q, pl, offsets, k1, v1, st);
+    }
     int end_bit = 1;
     while (end_bit < 32 && (1LL << end_bit) < B.ncells) ++end_bit;
     if (pmp::sort_pairs(w + L.temp, L.temp_bytes, k1, k2, v1, v2, (long long)total, end_bit, st) != cudaSuccess)
         return PMP_ERR_CUDA;
-    pmp::launch_segment_sum(P, S, state->data, B, buffer->data, q, gathered, pl, offsets + q.count, k2, v2, st);
+    {
+        Timed tm(ctx, "segment_sum");
+        pmp::launch_segment_sum(P, S, state->data, B, buffer->data, q, gathered, pl, offsets + q.count, k2, v2, st);
+    }
     return last_launch();
 }
 
@@ -448,7 +575,10 @@ pmp_status pmp_fold_ghosts(pmp_ctx *ctx, pmp_mesh *buffer)
     if (s) return s;
     for (int a = 0; a < 3; ++a)
         if (buffer->periodic[a] && buffer->ng > buffer->n[a]) return PMP_ERR_GHOST_TOO_THIN;
-    pmp::launch_fold(B, buffer->data, ctx->stream);
+    {
+        Timed tm(ctx, "fold");
+        pmp::launch_fold(B, buffer->data, ctx->stream);
+    }
     return last_launch();
 }
 
@@ -476,12 +606,16 @@ pmp_status pmp_apply_limited(pmp_ctx *ctx, pmp_mesh *state, const pmp_mesh *buff
         s = check_plan(ctx, n, nv, workspace);
         if (s) return s;
         const pmp::PlanPtrs pl = plan_ptrs(L, workspace, ctx->p, ctx->plan_mode);
-        pmp::launch_sink_eta(P, S, state->data, B, buffer->data, pl.aux, pl.aux_stride, pl.eta, st);
+        {
+            Timed tm(ctx, "eta");
+            pmp::launch_sink_eta(P, S, state->data, B, buffer->data, pl.drec, pl.eta, st);
+        }
         if (n > 0) {
             if (!gathered) return PMP_ERR_ARG;
             Parts q;
             s = make_parts(ctx, particles, &q);
             if (s) return s;
+            Timed tm(ctx, "return");
             pmp::launch_return_sinks(P, S, q, gathered, pl, ctx->st, st);
         }
         eta_in = pl.eta;
@@ -489,7 +623,30 @@ pmp_status pmp_apply_limited(pmp_ctx *ctx, pmp_mesh *state, const pmp_mesh *buff
     }
     if (cudaMemsetAsync(&ctx->st->n_limited, 0, 2 * sizeof(unsigned long long), st) != cudaSuccess)
         return PMP_ERR_CUDA;
-    pmp::launch_apply(P, S, state->data, B, buffer->data, eta_in, eta_out, ctx->st, st);
+    const long long nv = nvalid_of(state);
+    if (ctx->p.kind == PMP_KIND_FEEDBACK && workspace && ctx->plan_ws == workspace && ctx->plan_nvalid == nv) {
+        // scratch for the queue of cells that need the FP64 limiter
+        const Layout L = layout(ctx->p, ctx->plan_n, nv, ctx->plan_mode);
+        s = check_workspace(L, workspace, workspace_bytes);
+        if (s) return s;
+        char *w = static_cast<char *>(workspace);
+        unsigned *queue = reinterpret_cast<unsigned *>(w + L.queue);
+        unsigned long long *qc = reinterpret_cast<unsigned long long *>(w + L.qcount);
+        if (cudaMemsetAsync(qc, 0, sizeof(unsigned long long), st) != cudaSuccess) return PMP_ERR_CUDA;
+        {
+            Timed tm(ctx, "apply");
+            pmp::launch_apply_fb_fast(S, state->data, B, buffer->data, eta_out, queue, qc, st);
+        }
+        {
+            Timed tm(ctx, "apply_fp64");
+            pmp::launch_apply_fb_slow(S, state->data, B, buffer->data, eta_out, queue, qc, ctx->st, st);
+        }
+        return last_launch();
+    }
+    {
+        Timed tm(ctx, "apply");
+        pmp::launch_apply(P, S, state->data, B, buffer->data, eta_in, eta_out, ctx->st, st);
+    }
     return last_launch();
 }
 

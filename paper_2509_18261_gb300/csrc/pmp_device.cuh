@@ -48,6 +48,8 @@ struct KParams {
     double frac[8];  // (a + 1/2) / S, a < S: sub-point positions inside a cell
     int S, S3, R, kind;
     int Slog;        // log2(S) when S is a power of two, else -1
+    float fracf[8];  // frac[] rounded to FP32
+    float band_lo, band_hi;  // r2 (1 -/+ 2^-14) rounded outward to FP32
 };
 
 struct Parts {
@@ -165,6 +167,17 @@ __device__ __forceinline__ double pmp_log(double x)
 }
 
 __device__ __forceinline__ double pmp_pow(double x, double a) { return pmp_exp(a * pmp_log(x)); }
+
+// FP64 -> FP32 by truncating the significand, with integer operations only
+// (the FP64 pipe of this GPU is scarce).  |result - v| <= 2^-23 |v| for
+// 2^-126 <= |v| < 2^128; returns exactly 0 for +-0 and NaN outside that range.
+__device__ __forceinline__ float f32_trunc(double v)
+{
+    const unsigned hi = (unsigned)__double2hiint(v), lo = (unsigned)__double2loint(v);
+    const int e = (int)((hi >> 20) & 0x7ffu) - 1023 + 127;
+    if (e <= 0 || e >= 255) return ((hi & 0x7fffffffu) | lo) == 0u ? 0.0f : __int_as_float(0x7fc00000);
+    return __uint_as_float((hi & 0x80000000u) | ((unsigned)e << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29));
+}
 
 // ---------------------------------------------------------------------------
 // per-cell formulas
@@ -361,9 +374,10 @@ __device__ __forceinline__ void sink_delta(const KParams &P, const double U[NF],
     dU[4] = -(a * (U[4] / U[0]));
 }
 
-// Rows of the per-cell sink quantities (valid cells, x fastest): rho c_s,
-// rho - rho_Tr, p/rho (3), E/rho.
-enum { AUX_RCS = 0, AUX_TR, AUX_V0, AUX_V1, AUX_V2, AUX_ES, AUX_ROWS };
+// Per-cell sink records (valid cells, x fastest), 6 doubles = 48 bytes each:
+//   G record (gather):          rho, p_x, p_y, p_z, rho c_s, 0
+//   D record (deposit, Step 4): rho - rho_Tr, p_x/rho, p_y/rho, p_z/rho, E/rho, eta
+constexpr int kRec = 6;
 
 // Gathered-row indices.
 enum { FB_MSNR = 0, FB_VSNR, FB_VX, FB_VY, FB_VZ, FB_NH, FB_RM, FB_PRAD, FB_Q, FB_E, FB_PV, FB_REGIME, FB_ROWS };

@@ -14,14 +14,16 @@ struct PlanPtrs {
     unsigned *counts;                 // [n + 1] kernel cells per processed particle
     unsigned long long *slots;        // [n * cap] packed cell + omega count
     unsigned long long *hosts;        // [n] packed host cell, by particle index
+    float4 *fr;                       // [n] fractional position in the host cell (FP32)
     double *wts;                      // sink: [n][3][2R+1] per-axis Gaussian factors
-    double *aux;                      // sink: [AUX_ROWS][aux_stride] per valid cell
-    long long aux_stride;
+    double *grec;                     // sink: [valid cells][6] G records
+    double *drec;                     // sink: [valid cells][6] D records
     double *eta;                      // sink: [valid cells]
     unsigned long long cap;           // slots per particle
 };
 
-void launch_host_keys(const Box &S, const Parts &p, unsigned *keys, unsigned *ids, cudaStream_t stream);
+void launch_prologue(const Box &S, const Parts &p, unsigned *keys, unsigned *ids, const PlanPtrs &pl, DevStatus *st,
+                     cudaStream_t stream);
 void launch_plan(const KParams &P, const Box &S, const Parts &p, const PlanPtrs &pl, DevStatus *st,
                  cudaStream_t stream);
 void launch_gather(const KParams &P, const Box &S, const double *u, const Parts &p, const PlanPtrs &pl, double *G,
@@ -38,10 +40,14 @@ void launch_return_sinks(const KParams &P, const Box &S, const Parts &p, const d
 
 void launch_zero(const Box &B, double *b, cudaStream_t stream);
 void launch_fold(const Box &B, double *b, cudaStream_t stream);
-void launch_sink_aux(const KParams &P, const Box &S, const double *u, double *aux, long long aux_stride,
+void launch_sink_aux(const KParams &P, const Box &S, const double *u, double *grec, double *drec,
                      cudaStream_t stream);
-void launch_sink_eta(const KParams &P, const Box &S, const double *u, const Box &B, const double *b,
-                     const double *aux, long long aux_stride, double *eta, cudaStream_t stream);
+void launch_sink_eta(const KParams &P, const Box &S, const double *u, const Box &B, const double *b, double *drec,
+                     double *eta, cudaStream_t stream);
+void launch_apply_fb_fast(const Box &S, double *u, const Box &B, const double *b, double *eta_out, unsigned *queue,
+                          unsigned long long *qcount, cudaStream_t stream);
+void launch_apply_fb_slow(const Box &S, double *u, const Box &B, const double *b, double *eta_out,
+                          const unsigned *queue, const unsigned long long *qcount, DevStatus *st, cudaStream_t stream);
 void launch_apply(const KParams &P, const Box &S, double *u, const Box &B, const double *b, const double *eta_in,
                   double *eta_out, DevStatus *st, cudaStream_t stream);
 

@@ -84,8 +84,10 @@ __global__ void __launch_bounds__(256) k_fold(Box B, double *__restrict__ b)
 // runs the FP64 limiter, whose first step is the exact test.
 __device__ __forceinline__ bool sn_lambda_holds_f32(const double U[NF], const double D[NF])
 {
-    const float r = (float)U[0], p0 = (float)U[1], p1 = (float)U[2], p2 = (float)U[3], E = (float)U[4];
-    const float dr = (float)D[0], d0 = (float)D[1], d1 = (float)D[2], d2 = (float)D[3], dE = (float)D[4];
+    const float r = f32_trunc(U[0]), p0 = f32_trunc(U[1]), p1 = f32_trunc(U[2]), p2 = f32_trunc(U[3]),
+                E = f32_trunc(U[4]);
+    const float dr = f32_trunc(D[0]), d0 = f32_trunc(D[1]), d1 = f32_trunc(D[2]), d2 = f32_trunc(D[3]),
+                dE = f32_trunc(D[4]);
     const float r1 = r + dr, E1 = E + dE;
     const float pp = (p0 * p0 + p1 * p1) + p2 * p2;
     const float k0 = pp / (2.0f * r);
@@ -97,7 +99,85 @@ __device__ __forceinline__ bool sn_lambda_holds_f32(const double U[NF], const do
     return dr >= 0.0f && M > 1e-30f && M < 1e30f && f < -6.103515625e-05f * M;
 }
 
-// Steps 3 + 5 for feedback: eta = (1, l, l, l, 1) from Eq. lambda.
+// Steps 3 + 5 for feedback, first pass: cells whose Eq. lambda constraint
+// holds at lambda = 1 by the FP32 pre-check (or that receive no momentum) are
+// updated here; the others are queued for the FP64 limiter.
+__global__ void __launch_bounds__(256) k_apply_fb_fast(Box S, double *__restrict__ u, Box B,
+                                                       const double *__restrict__ b, double *__restrict__ eta_out,
+                                                       unsigned *__restrict__ queue,
+                                                       unsigned long long *__restrict__ qcount)
+{
+    const long long nvalid = (long long)S.n0 * S.n1 * S.n2;
+    const long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    bool slow = false;
+    if (v < nvalid) {
+        const int i = (int)(v % S.n0);
+        const long long r = v / S.n0;
+        const int j = (int)(r % S.n1), k = (int)(r / S.n1);
+        const long long cs = S.at(i, j, k), cb = B.at(i, j, k);
+        double U[NF], D[NF];
+#pragma unroll
+        for (int f = 0; f < NF; ++f) {
+            U[f] = u[(long long)f * S.fs + cs];
+            D[f] = __ldg(b + (long long)f * B.fs + cb);
+        }
+        const bool nodp = D[1] == 0.0 && D[2] == 0.0 && D[3] == 0.0;
+        if (nodp || sn_lambda_holds_f32(U, D)) {
+            if (eta_out) eta_out[v] = 1.0;
+#pragma unroll
+            for (int f = 0; f < NF; ++f) u[(long long)f * S.fs + cs] = U[f] + D[f];
+        } else {
+            slow = true;
+        }
+    }
+    const unsigned m = __ballot_sync(0xffffffffu, slow);
+    if (m) {
+        const int lane = threadIdx.x & 31;
+        unsigned long long base = 0;
+        if (lane == __ffs(m) - 1) base = atomicAdd(qcount, (unsigned long long)__popc(m));
+        base = __shfl_sync(0xffffffffu, base, __ffs(m) - 1);
+        if (slow) queue[base + __popc(m & ((1u << lane) - 1u))] = (unsigned)v;
+    }
+}
+
+// Second pass: the queued cells through the FP64 limiter of Eq. lambda.
+__global__ void __launch_bounds__(256) k_apply_fb_slow(Box S, double *__restrict__ u, Box B,
+                                                       const double *__restrict__ b, double *__restrict__ eta_out,
+                                                       const unsigned *__restrict__ queue,
+                                                       const unsigned long long *__restrict__ qcount, DevStatus *st)
+{
+    const unsigned long long n = *qcount;
+    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+    unsigned long long nl = 0, nr = 0;
+    for (unsigned long long q = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += stride) {
+        const long long v = queue[q];
+        const int i = (int)(v % S.n0);
+        const long long r = v / S.n0;
+        const int j = (int)(r % S.n1), k = (int)(r / S.n1);
+        const long long cs = S.at(i, j, k), cb = B.at(i, j, k);
+        double U[NF], D[NF];
+#pragma unroll
+        for (int f = 0; f < NF; ++f) {
+            U[f] = u[(long long)f * S.fs + cs];
+            D[f] = __ldg(b + (long long)f * B.fs + cb);
+        }
+        int noroot;
+        const double l = sn_lambda(U, D, noroot);
+        nl += l < 1.0;
+        nr += noroot;
+        if (eta_out) eta_out[v] = l;
+        u[cs] = U[0] + D[0];
+        u[S.fs + cs] = U[1] + l * D[1];
+        u[2 * S.fs + cs] = U[2] + l * D[2];
+        u[3 * S.fs + cs] = U[3] + l * D[3];
+        u[4 * S.fs + cs] = U[4] + D[4];
+    }
+    if (nl) atomicAdd(&st->n_limited, nl);
+    if (nr) atomicAdd(&st->n_noroot, nr);
+}
+
+// Steps 3 + 5 for feedback in one pass (used without a workspace): eta =
+// (1, l, l, l, 1) from Eq. lambda in FP64 for every cell.
 __global__ void __launch_bounds__(256) k_apply_fb(Box S, double *__restrict__ u, Box B, const double *__restrict__ b,
                                                   double *__restrict__ eta_out, DevStatus *st)
 {
@@ -115,8 +195,7 @@ __global__ void __launch_bounds__(256) k_apply_fb(Box S, double *__restrict__ u,
             U[f] = u[(long long)f * S.fs + cs];
             D[f] = __ldg(b + (long long)f * B.fs + cb);
         }
-        double l = 1.0;
-        if (!sn_lambda_holds_f32(U, D)) l = sn_lambda(U, D, nr);
+        const double l = sn_lambda(U, D, nr);
         lim = l < 1.0;
         if (eta_out) eta_out[v] = l;
         u[cs] = U[0] + D[0];
@@ -132,10 +211,11 @@ __global__ void __launch_bounds__(256) k_apply_fb(Box S, double *__restrict__ u,
     }
 }
 
-// Per-cell sink quantities, each in the order the sink formulas state it:
-// rho c_s, rho - rho_Tr (Eq. truelove), p/rho and E/rho.
+// Per-cell sink records, each value in the order the sink formulas state it:
+// G = (rho, p, rho c_s) for the gather; D = (rho - rho_Tr (Eq. truelove),
+// p/rho, E/rho, eta) for the deposit and Step 4 (eta filled in later).
 __global__ void __launch_bounds__(256) k_sink_aux(KParams P, Box S, const double *__restrict__ u,
-                                                  double *__restrict__ aux, long long as)
+                                                  double *__restrict__ grec, double *__restrict__ drec)
 {
     const long long nvalid = (long long)S.n0 * S.n1 * S.n2;
     const long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -146,19 +226,22 @@ __global__ void __launch_bounds__(256) k_sink_aux(KParams P, Box S, const double
     double U[NF], cs, rtr;
     load_cell(u, S, S.at(i, j, k), U);
     sink_cell(P, U, cs, rtr);
-    aux[AUX_RCS * as + v] = U[0] * cs;
-    aux[AUX_TR * as + v] = U[0] - rtr;
-    aux[AUX_V0 * as + v] = U[1] / U[0];
-    aux[AUX_V1 * as + v] = U[2] / U[0];
-    aux[AUX_V2 * as + v] = U[3] / U[0];
-    aux[AUX_ES * as + v] = U[4] / U[0];
+    double2 *g = reinterpret_cast<double2 *>(grec + v * kRec);
+    g[0] = make_double2(U[0], U[1]);
+    g[1] = make_double2(U[2], U[3]);
+    g[2] = make_double2(U[0] * cs, 0.0);
+    double2 *d = reinterpret_cast<double2 *>(drec + v * kRec);
+    d[0] = make_double2(U[0] - rtr, U[1] / U[0]);
+    d[1] = make_double2(U[2] / U[0], U[3] / U[0]);
+    d[2] = make_double2(U[4] / U[0], 1.0);
 }
 
 // Step 3 for sinks: eta per valid cell from the pre-update density, the summed
-// removal and rho - rho_Tr (accretion limiter of Sec. 3.1.1 with the floor).
+// removal and rho - rho_Tr (accretion limiter of Sec. 3.1.1 with the floor);
+// written to the eta array and to the cell's D record.
 __global__ void __launch_bounds__(256) k_sink_eta(KParams P, Box S, const double *__restrict__ u, Box B,
-                                                  const double *__restrict__ b, const double *__restrict__ aux,
-                                                  long long as, double *__restrict__ eta)
+                                                  const double *__restrict__ b, double *__restrict__ drec,
+                                                  double *__restrict__ eta)
 {
     const long long nvalid = (long long)S.n0 * S.n1 * S.n2;
     const long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -174,7 +257,7 @@ __global__ void __launch_bounds__(256) k_sink_eta(KParams P, Box S, const double
         const double fl = rho - P.rho_min;
         if (!(a <= capr && a <= fl)) {
             double al = a < capr ? a : capr;
-            const double t = __ldg(aux + AUX_TR * as + v);
+            const double t = drec[v * kRec];
             al = al > t ? al : t;
             al = al < fl ? al : fl;
             if (al < 0.0) al = 0.0;
@@ -182,6 +265,7 @@ __global__ void __launch_bounds__(256) k_sink_eta(KParams P, Box S, const double
         }
     }
     eta[v] = e;
+    drec[v * kRec + 5] = e;
 }
 
 // Steps 3 + 5 for sinks: U += eta Delta U^sum, one eta for all five fields.
@@ -222,18 +306,31 @@ void launch_fold(const Box &B, double *b, cudaStream_t stream)
     k_fold<<<(unsigned)((threads + 255) / 256), 256, 0, stream>>>(B, b);
 }
 
-void launch_sink_aux(const KParams &P, const Box &S, const double *u, double *aux, long long aux_stride,
+void launch_sink_aux(const KParams &P, const Box &S, const double *u, double *grec, double *drec,
                      cudaStream_t stream)
 {
     const long long nvalid = (long long)S.n0 * S.n1 * S.n2;
-    k_sink_aux<<<(unsigned)((nvalid + 255) / 256), 256, 0, stream>>>(P, S, u, aux, aux_stride);
+    k_sink_aux<<<(unsigned)((nvalid + 255) / 256), 256, 0, stream>>>(P, S, u, grec, drec);
 }
 
-void launch_sink_eta(const KParams &P, const Box &S, const double *u, const Box &B, const double *b,
-                     const double *aux, long long aux_stride, double *eta, cudaStream_t stream)
+void launch_sink_eta(const KParams &P, const Box &S, const double *u, const Box &B, const double *b, double *drec,
+                     double *eta, cudaStream_t stream)
 {
     const long long nvalid = (long long)S.n0 * S.n1 * S.n2;
-    k_sink_eta<<<(unsigned)((nvalid + 255) / 256), 256, 0, stream>>>(P, S, u, B, b, aux, aux_stride, eta);
+    k_sink_eta<<<(unsigned)((nvalid + 255) / 256), 256, 0, stream>>>(P, S, u, B, b, drec, eta);
+}
+
+void launch_apply_fb_fast(const Box &S, double *u, const Box &B, const double *b, double *eta_out, unsigned *queue,
+                          unsigned long long *qcount, cudaStream_t stream)
+{
+    const long long nvalid = (long long)S.n0 * S.n1 * S.n2;
+    k_apply_fb_fast<<<(unsigned)((nvalid + 255) / 256), 256, 0, stream>>>(S, u, B, b, eta_out, queue, qcount);
+}
+
+void launch_apply_fb_slow(const Box &S, double *u, const Box &B, const double *b, double *eta_out,
+                          const unsigned *queue, const unsigned long long *qcount, DevStatus *st, cudaStream_t stream)
+{
+    k_apply_fb_slow<<<152 * 8, 256, 0, stream>>>(S, u, B, b, eta_out, queue, qcount, st);
 }
 
 void launch_apply(const KParams &P, const Box &S, double *u, const Box &B, const double *b, const double *eta_in,

@@ -33,67 +33,91 @@ __device__ __forceinline__ unsigned spread3(unsigned v)
     return v;
 }
 
-// Key of a particle: Morton (Z-order) code of its host cell (coordinates
-// shifted right by `sh` so that each fits in 10 bits); invalid positions sort
-// last.  Consecutive particles of this order have overlapping kernels.
-__global__ void __launch_bounds__(256) k_host_keys(Box S, Parts p, int sh, unsigned *__restrict__ keys,
-                                                   unsigned *__restrict__ ids)
+// Per-particle prologue (one thread per particle): host cell, the fractional
+// position x - floor(x) (exact in FP64) rounded to FP32 for the plan's
+// filters, and the processing-order key: the Morton (Z-order) code of the host
+// cell (coordinates shifted right by `sh` to fit 10 bits), so that consecutive
+// particles of the order have overlapping kernels.  Invalid positions get
+// host = kNoHost and sort last.
+constexpr unsigned long long kNoHost = ~0ULL;
+
+__global__ void __launch_bounds__(256) k_prologue(Box S, Parts p, int sh, unsigned *__restrict__ keys,
+                                                  unsigned *__restrict__ ids, unsigned long long *__restrict__ hosts,
+                                                  float4 *__restrict__ fr, DevStatus *st)
 {
     const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= p.count) return;
     const double x = p.x[s], y = p.y[s], z = p.z[s];
-    unsigned key = 0xffffffffu;
-    if (position_status(S, x, y, z) == PMP_OK) {
-        const unsigned hx = (unsigned)(int)floor(x) >> sh, hy = (unsigned)(int)floor(y) >> sh,
-                       hz = (unsigned)(int)floor(z) >> sh;
-        key = spread3(hx) | (spread3(hy) << 1) | (spread3(hz) << 2);
+    const int bad = position_status(S, x, y, z);
+    if (bad) {
+        report(st, bad, s);
+        hosts[s] = kNoHost;
+        fr[s] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (keys) {
+            keys[s] = 0xffffffffu;
+            ids[s] = (unsigned)s;
+        }
+        return;
     }
-    keys[s] = key;
-    ids[s] = (unsigned)s;
+    const double fx = floor(x), fy = floor(y), fz = floor(z);
+    const int hx = (int)fx, hy = (int)fy, hz = (int)fz;
+    hosts[s] = pack_host(hx, hy, hz);
+    fr[s] = make_float4((float)(x - fx), (float)(y - fy), (float)(z - fz), 0.f);
+    if (keys) {
+        const unsigned ux = (unsigned)hx >> sh, uy = (unsigned)hy >> sh, uz = (unsigned)hz >> sh;
+        keys[s] = spread3(ux) | (spread3(uy) << 1) | (spread3(uz) << 2);
+        ids[s] = (unsigned)s;
+    }
 }
 
 // ---------------------------------------------------------------------------
 // plan
 // ---------------------------------------------------------------------------
 
-// shared floats per warp: edges [3][W+1], centre squares [3][W], farthest-corner
-// squares [3][W], sub-point squares [3][W*S]
-__host__ __device__ constexpr int plan_warp_floats(int W, int S) { return 3 * (W + 1) + 6 * W + 3 * W * S; }
+// shared memory per warp: floats edges [3][W+1], centre squares [3][W],
+// farthest-corner squares [3][W], sub-point squares [3][W*S], x-row extremes
+// [2][W]; ints: the kernel-cell code of each lane, the needing-lane list, the
+// per-lane sub-point counts
+__host__ __device__ constexpr int plan_warp_floats(int W, int S) { return 3 * (W + 1) + 8 * W + 3 * W * S; }
+constexpr int kPlanWarpInts = 96;
 
 template <int R, bool FB>
 __global__ void __launch_bounds__(256) k_plan(KParams P, Box S, Parts p, const unsigned *__restrict__ perm,
-                                              unsigned cap, unsigned *__restrict__ counts,
-                                              unsigned long long *__restrict__ slots,
-                                              unsigned long long *__restrict__ hosts, DevStatus *st)
+                                              const unsigned long long *__restrict__ hosts,
+                                              const float4 *__restrict__ fr, unsigned cap,
+                                              unsigned *__restrict__ counts, unsigned long long *__restrict__ slots,
+                                              DevStatus *st)
 {
     constexpr int W = 2 * R + 1;
     constexpr int W3 = W * W * W;
     extern __shared__ float smem[];
-    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    const long long t = (long long)blockIdx.x * (blockDim.x >> 5) + wib;
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const long long t = (long long)blockIdx.x * nw + wib;
+    const int Sn = FB ? P.S : 1;
+    const int wf = plan_warp_floats(W, Sn);
+    float *edge = smem + (size_t)wib * wf;  // [3][W+1]
+    float *csq = edge + 3 * (W + 1);        // [3][W]
+    float *fc2 = csq + 3 * W;               // [3][W]
+    float *xlo = fc2 + 3 * W;               // [W]
+    float *xhi = xlo + W;                   // [W]
+    float *sub = xhi + W;                   // [3][W*S]
+    int *ism = reinterpret_cast<int *>(smem + (size_t)nw * wf) + wib * kPlanWarpInts;
+    int *code = ism, *list = ism + 32, *csum = ism + 64;
     if (t >= p.count) return;  // warp-uniform
-    const int Sn = P.S;
-    float *edge = smem + (size_t)wib * plan_warp_floats(W, FB ? Sn : 1);  // [3][W+1]
-    float *csq = edge + 3 * (W + 1);                                       // [3][W]
-    float *fc2 = csq + 3 * W;                                              // [3][W]
-    float *sub = fc2 + 3 * W;                                              // [3][W*S]
     const long long s = perm ? (long long)perm[t] : t;
-    const double x = p.x[s], y = p.y[s], z = p.z[s];
-    const int bad = position_status(S, x, y, z);
-    if (bad) {
-        if (lane == 0) {
-            report(st, bad, s);
-            counts[t] = 0;
-        }
+    const unsigned long long hp = hosts[s];
+    if (hp == kNoHost) {
+        if (lane == 0) counts[t] = 0;
         return;
     }
-    const int h0 = (int)floor(x), h1 = (int)floor(y), h2 = (int)floor(z);
-    if (lane == 0 && hosts) hosts[s] = pack_host(h0, h1, h2);
+    int h0, h1, h2;
+    unpack_host(hp, h0, h1, h2);
+    const float4 f4 = fr[s];
+    // FP32 offsets from the fractional position: e = (o - R) - frac
     for (int i = lane; i < 3 * (W + 1); i += 32) {
         const int a = i / (W + 1), o = i - a * (W + 1);
-        const int h = a == 0 ? h0 : (a == 1 ? h1 : h2);
-        const double xa = a == 0 ? x : (a == 1 ? y : z);
-        edge[i] = (float)((double)(h + o - R) - xa);
+        const float fa = a == 0 ? f4.x : (a == 1 ? f4.y : f4.z);
+        edge[i] = (float)(o - R) - fa;
     }
     __syncwarp();
     for (int i = lane; i < 3 * W; i += 32) {
@@ -107,12 +131,23 @@ __global__ void __launch_bounds__(256) k_plan(KParams P, Box S, Parts p, const u
     if (FB) {
         for (int i = lane; i < 3 * W * Sn; i += 32) {
             const int a = i / (W * Sn), r = i - a * (W * Sn), o = r / Sn, k = r - o * Sn;
-            const float u = edge[a * (W + 1) + o] + (float)P.frac[k];
+            const float u = edge[a * (W + 1) + o] + P.fracf[k];
             sub[i] = u * u;
+        }
+        __syncwarp();
+        for (int o = lane; o < W; o += 32) {
+            float lo = 3.0e38f, hi = 0.0f;
+            for (int k = 0; k < Sn; ++k) {
+                const float v = sub[o * Sn + k];
+                lo = v < lo ? v : lo;
+                hi = v > hi ? v : hi;
+            }
+            xlo[o] = lo;
+            xhi[o] = hi;
         }
     }
     __syncwarp();
-    const R2Band band = make_band(P.r2);
+    const float blo = P.band_lo, bhi = P.band_hi;
     unsigned nout = 0;
     const unsigned long long base = (unsigned long long)t * cap;
     for (int k0 = 0; k0 < W3; k0 += 32) {
@@ -128,45 +163,58 @@ __global__ void __launch_bounds__(256) k_plan(KParams P, Box S, Parts p, const u
                              (S.per2 || (c2 >= 0 && c2 < S.n2));
             if (dom) {
                 const float tf = (csq[ox] + csq[W + oy]) + csq[2 * W + oz];
-                if (tf < band.lo) mem = true;
-                else if (tf <= band.hi) mem = centre_inside_exact(P.r2, c0, c1, c2, x, y, z);
-                if (FB && mem) full = (fc2[ox] + fc2[W + oy]) + fc2[2 * W + oz] < band.lo;
+                if (tf < blo) mem = true;
+                else if (tf <= bhi) mem = centre_inside_exact(P.r2, c0, c1, c2, p.x[s], p.y[s], p.z[s]);
+                if (FB && mem) full = (fc2[ox] + fc2[W + oy]) + fc2[2 * W + oz] < blo;
             }
         }
         int cnt = 0;
         if (FB) {
             cnt = full ? P.S3 : 0;
-            unsigned need = __ballot_sync(kFull, mem && !full);
-            while (need) {
-                const int src = __ffs(need) - 1;
-                need &= need - 1;
-                const int cx = __shfl_sync(kFull, ox, src), cy = __shfl_sync(kFull, oy, src),
-                          cz = __shfl_sync(kFull, oz, src);
-                const float *sx = sub + cx * Sn, *sy = sub + (W + cy) * Sn, *sz = sub + (2 * W + cz) * Sn;
-                int c = 0;
-                for (int q0 = 0; q0 < P.S3; q0 += 32) {
-                    const int q = q0 + lane;
-                    bool in = false;
-                    if (q < P.S3) {
-                        int qa, qb, qc;
-                        if (P.Slog >= 0) {
-                            qa = q & (Sn - 1);
-                            qb = (q >> P.Slog) & (Sn - 1);
-                            qc = q >> (2 * P.Slog);
+            const bool needs = mem && !full;
+            const unsigned need = __ballot_sync(kFull, needs);
+            if (need) {
+                // sub-point counts of the cells that need one: lanes take
+                // (cell, row) items, a row being the S sub-points along x at a
+                // fixed (y, z) sub-position
+                code[lane] = ox | (oy << 8) | (oz << 16);
+                csum[lane] = 0;
+                if (needs) list[__popc(need & ((1u << lane) - 1u))] = lane;
+                __syncwarp();
+                const int S2 = Sn * Sn;
+                const int items = __popc(need) * S2;
+                for (int f0 = 0; f0 < items; f0 += 32) {
+                    const int f = f0 + lane;
+                    if (f < items) {
+                        const int mi = P.Slog >= 0 ? (f >> (2 * P.Slog)) : f / S2;
+                        const int row = f - mi * S2;
+                        const int src = list[mi];
+                        const int pk = code[src];
+                        const int cx = pk & 0xff, cy = (pk >> 8) & 0xff, cz = pk >> 16;
+                        const int b = P.Slog >= 0 ? (row & (Sn - 1)) : row % Sn;
+                        const int c = P.Slog >= 0 ? (row >> P.Slog) : row / Sn;
+                        const float bs = sub[(W + cy) * Sn + b] + sub[(2 * W + cz) * Sn + c];
+                        int add = 0;
+                        if (bs + xlo[cx] > bhi) {
+                            add = 0;
+                        } else if (bs + xhi[cx] < blo) {
+                            add = Sn;
                         } else {
-                            qa = q % Sn;
-                            qb = (q / Sn) % Sn;
-                            qc = q / (Sn * Sn);
+                            for (int a = 0; a < Sn; ++a) {
+                                const float tf = bs + sub[cx * Sn + a];
+                                if (tf < blo) ++add;
+                                else if (tf <= bhi &&
+                                         subpoint_inside_exact(P.r2, P.frac[a], P.frac[b], P.frac[c], h0 + cx - R,
+                                                               h1 + cy - R, h2 + cz - R, p.x[s], p.y[s], p.z[s]))
+                                    ++add;
+                            }
                         }
-                        const float tf = (sx[qa] + sy[qb]) + sz[qc];
-                        if (tf < band.lo) in = true;
-                        else if (tf <= band.hi)
-                            in = subpoint_inside_exact(P.r2, P.frac[qa], P.frac[qb], P.frac[qc], h0 + cx - R,
-                                                       h1 + cy - R, h2 + cz - R, x, y, z);
+                        if (add) atomicAdd(csum + src, add);
                     }
-                    c += __popc(__ballot_sync(kFull, in));
                 }
-                if (lane == src) cnt = c;
+                __syncwarp();
+                if (needs) cnt = csum[lane];
+                __syncwarp();
             }
             mem = mem && cnt > 0;
         }
@@ -185,24 +233,33 @@ __global__ void __launch_bounds__(256) k_plan(KParams P, Box S, Parts p, const u
 // gather
 // ---------------------------------------------------------------------------
 
+// Covered fractions omega = k / S^3 for k = 0..S^3, computed once per block.
+constexpr int kMaxS3 = kMaxS * kMaxS * kMaxS;
+
+__device__ __forceinline__ void fill_omega_table(const KParams &P, double *wtab)
+{
+    for (int i = threadIdx.x; i <= P.S3; i += blockDim.x) wtab[i] = (double)i / (double)P.S3;
+    __syncthreads();
+}
+
 __global__ void __launch_bounds__(128) k_gather_fb(KParams P, Box S, const double *__restrict__ u, Parts p,
                                                    PlanPtrs pl, double *__restrict__ G, DevStatus *st)
 {
+    __shared__ double wtab[kMaxS3 + 1];
+    fill_omega_table(P, wtab);
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= p.count) return;
     const long long s = pl.perm ? (long long)pl.perm[t] : t;
     const long long gs = p.count;
-    const double x = p.x[s], y = p.y[s], z = p.z[s];
     const double m = p.m[s], pe0 = p.px[s], pe1 = p.py[s], pe2 = p.pz[s], Esn = p.e[s];
-    int bad = position_status(S, x, y, z);
+    int bad = pl.hosts[s] == kNoHost ? PMP_ERR_PARTICLE_OUTSIDE : 0;
     if (!bad && !(m > 0.0)) bad = PMP_ERR_NONFINITE;
     if (bad) {
-        report(st, bad, s);
+        if (bad == PMP_ERR_NONFINITE) report(st, bad, s);
         for (int r = 0; r < FB_ROWS; ++r) G[r * gs + s] = 0.0;
         return;
     }
     double sw = 0.0, sr = 0.0, sp0 = 0.0, sp1 = 0.0, sp2 = 0.0;
-    const double s3 = (double)P.S3;
     const unsigned long long b0 = (unsigned long long)t * pl.cap;
     const unsigned nc = pl.counts[t];
     for (unsigned q = 0; q < nc; ++q) {
@@ -216,7 +273,7 @@ __global__ void __launch_bounds__(128) k_gather_fb(KParams P, Box S, const doubl
             sp1 = sp1 + U[2];
             sp2 = sp2 + U[3];
         } else {
-            const double w = (double)c.cnt / s3;
+            const double w = wtab[c.cnt];
             sw = sw + w;
             sr = sr + w * U[0];
             sp0 = sp0 + w * U[1];
@@ -284,18 +341,17 @@ __global__ void __launch_bounds__(128) k_gather_sink(KParams P, Box S, const dou
     }
     const unsigned long long b0 = (unsigned long long)t * pl.cap;
     const unsigned nc = pl.counts[t];
-    const long long as = pl.aux_stride;
     double srho = 0.0, sp0 = 0.0, sp1 = 0.0, sp2 = 0.0, src = 0.0;
     for (unsigned q = 0; q < nc; ++q) {
         const PairCell c = unpack_pair(pl.slots[b0 + q], P.R);
-        const int wi = owner(c.i, S.n0), wj = owner(c.j, S.n1), wk = owner(c.k, S.n2);
-        double U[NF];
-        load_cell(u, S, S.at(wi, wj, wk), U);
-        srho = srho + U[0];
-        sp0 = sp0 + U[1];
-        sp1 = sp1 + U[2];
-        sp2 = sp2 + U[3];
-        src = src + __ldg(pl.aux + AUX_RCS * as + vidx(S, wi, wj, wk));
+        const double2 *g =
+            reinterpret_cast<const double2 *>(pl.grec + vidx(S, owner(c.i, S.n0), owner(c.j, S.n1), owner(c.k, S.n2)) * kRec);
+        const double2 g0 = __ldg(g), g1 = __ldg(g + 1), g2 = __ldg(g + 2);
+        srho = srho + g0.x;
+        sp0 = sp0 + g0.y;
+        sp1 = sp1 + g1.x;
+        sp2 = sp2 + g1.y;
+        src = src + g2.x;
     }
     const int nk = (int)nc;
     const double rho_inf = srho / (double)nk;
@@ -364,26 +420,29 @@ __device__ __forceinline__ void fb_pair_delta(const KParams &P, const Box &S, co
                    d2, dd, dU);
 }
 
+// Sink deposition value of one pair; also returns the cell's eta (D record).
 template <int R>
 __device__ __forceinline__ void sink_pair_delta(const KParams &P, const Box &S, const Parts &p,
                                                 const double *__restrict__ G, const PlanPtrs &pl, long long s,
-                                                const PairCell &c, double dU[NF], long long &vcell)
+                                                const PairCell &c, double dU[NF], double &eta)
 {
     constexpr int W = 2 * R + 1;
     int hx, hy, hz;
     unpack_host(__ldg(pl.hosts + s), hx, hy, hz);
     const double *ws = pl.wts + s * (3 * W);
     const double w = (__ldg(ws + c.i - hx + R) * __ldg(ws + W + c.j - hy + R)) * __ldg(ws + 2 * W + c.k - hz + R);
-    vcell = vidx(S, owner(c.i, S.n0), owner(c.j, S.n1), owner(c.k, S.n2));
-    const long long as = pl.aux_stride;
+    const double2 *d =
+        reinterpret_cast<const double2 *>(pl.drec + vidx(S, owner(c.i, S.n0), owner(c.j, S.n1), owner(c.k, S.n2)) * kRec);
+    const double2 d0 = __ldg(d), d1 = __ldg(d + 1), d2 = __ldg(d + 2);
     const double bh = __ldg(G + SK_K * p.count + s) * w;
-    const double tr = __ldg(pl.aux + AUX_TR * as + vcell);
+    const double tr = d0.x;
     const double a = bh >= tr ? bh : tr;
     dU[0] = -a;
-    dU[1] = -(a * __ldg(pl.aux + AUX_V0 * as + vcell));
-    dU[2] = -(a * __ldg(pl.aux + AUX_V1 * as + vcell));
-    dU[3] = -(a * __ldg(pl.aux + AUX_V2 * as + vcell));
-    dU[4] = -(a * __ldg(pl.aux + AUX_ES * as + vcell));
+    dU[1] = -(a * d0.y);
+    dU[2] = -(a * d1.x);
+    dU[3] = -(a * d1.y);
+    dU[4] = -(a * d2.x);
+    eta = d2.y;
 }
 
 // ---------------------------------------------------------------------------
@@ -393,15 +452,34 @@ __device__ __forceinline__ void sink_pair_delta(const KParams &P, const Box &S, 
 
 constexpr int kPartsPerWarp = 8;
 
+// Feedback deposition value of one pair from precomputed centre offsets.
+__device__ __forceinline__ void fb_pair_delta_d(const double *__restrict__ u, const Box &S, const double *__restrict__ G,
+                                                long long gs, long long s, const PairCell &c, double w, double d0,
+                                                double d1, double d2, double dd, double dU[NF])
+{
+    double U[NF];
+    load_cell(u, S, S.at(owner(c.i, S.n0), owner(c.j, S.n1), owner(c.k, S.n2)), U);
+    const double vc[3] = {__ldg(G + FB_VX * gs + s), __ldg(G + FB_VY * gs + s), __ldg(G + FB_VZ * gs + s)};
+    feedback_delta(w, U, __ldg(G + FB_Q * gs + s), __ldg(G + FB_E * gs + s), __ldg(G + FB_PV * gs + s), vc, d0, d1,
+                   d2, dd, dU);
+}
+
 template <int R, bool FB>
 __global__ void __launch_bounds__(256) k_deposit_atomic(KParams P, Box S, const double *__restrict__ u, Box B,
                                                         double *__restrict__ b, Parts p,
                                                         const double *__restrict__ G, PlanPtrs pl)
 {
-    const int lane = threadIdx.x & 31;
+    constexpr int W = 2 * R + 1;
+    constexpr int TAB = kPartsPerWarp * 3 * W;  // per warp: [8 particles][3 axes][W offsets]
+    __shared__ double wtab[FB ? kMaxS3 + 1 : 1];
+    __shared__ double dtab[FB ? 8 * TAB : 1], qtab[FB ? 8 * TAB : 1];
+    __shared__ long long sidtab[8 * kPartsPerWarp];
+    if (FB) fill_omega_table(P, wtab);
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    double *dt = dtab + (FB ? wib * TAB : 0), *qt = qtab + (FB ? wib * TAB : 0);
     const long long nwarps = (long long)gridDim.x * (blockDim.x >> 5);
-    for (long long t0 = ((long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * kPartsPerWarp;
-         t0 < p.count; t0 += nwarps * kPartsPerWarp) {
+    for (long long t0 = ((long long)blockIdx.x * (blockDim.x >> 5) + wib) * kPartsPerWarp; t0 < p.count;
+         t0 += nwarps * kPartsPerWarp) {
         // inclusive prefix of the 8 particles' pair counts, held by lanes 0..7
         unsigned c = 0;
         long long sid = 0;
@@ -416,6 +494,29 @@ __global__ void __launch_bounds__(256) k_deposit_atomic(KParams P, Box S, const 
             if (lane >= d) incl += v;
         }
         const unsigned total = __shfl_sync(kFull, incl, kPartsPerWarp - 1);
+        if (FB) {
+            // centre offsets (c + 1/2) - x and their squares of the 8 particles
+            __syncwarp();
+            if (lane < kPartsPerWarp) sidtab[wib * kPartsPerWarp + lane] = sid;
+            __syncwarp();
+            for (int i = lane; i < TAB; i += 32) {
+                const int j = i / (3 * W), r = i - j * (3 * W), a = r / W, o = r - a * W;
+                const long long sj = sidtab[wib * kPartsPerWarp + j];
+                if (t0 + j < p.count) {
+                    const unsigned long long hp = __ldg(pl.hosts + sj);
+                    if (hp != kNoHost) {
+                        int hx, hy, hz;
+                        unpack_host(hp, hx, hy, hz);
+                        const int h = a == 0 ? hx : (a == 1 ? hy : hz);
+                        const double xa = a == 0 ? __ldg(p.x + sj) : (a == 1 ? __ldg(p.y + sj) : __ldg(p.z + sj));
+                        const double d = ((double)(h + o - R) + 0.5) - xa;
+                        dt[i] = d;
+                        qt[i] = d * d;
+                    }
+                }
+            }
+            __syncwarp();
+        }
         for (unsigned g0 = 0; g0 < total; g0 += 32) {
             const unsigned g = g0 + lane;
             // particle j of this pair: the first whose inclusive prefix exceeds g
@@ -435,10 +536,16 @@ __global__ void __launch_bounds__(256) k_deposit_atomic(KParams P, Box S, const 
                 const PairCell cell = unpack_pair(__ldg(pl.slots + slot), P.R);
                 double dU[NF];
                 if (FB) {
-                    fb_pair_delta(P, S, u, p, G, s, cell, dU);
+                    int hx, hy, hz;
+                    unpack_host(__ldg(pl.hosts + s), hx, hy, hz);
+                    const int ix = j * 3 * W + (cell.i - hx + R), iy = j * 3 * W + W + (cell.j - hy + R),
+                              iz = j * 3 * W + 2 * W + (cell.k - hz + R);
+                    const double dd = (qt[ix] + qt[iy]) + qt[iz];
+                    const double w = cell.cnt == P.S3 ? 1.0 : wtab[cell.cnt];
+                    fb_pair_delta_d(u, S, G, p.count, s, cell, w, dt[ix], dt[iy], dt[iz], dd, dU);
                 } else {
-                    long long vc;
-                    sink_pair_delta<R>(P, S, p, G, pl, s, cell, dU, vc);
+                    double e;
+                    sink_pair_delta<R>(P, S, p, G, pl, s, cell, dU, e);
                 }
                 const long long bc = B.at(cell.i, cell.j, cell.k);
 #pragma unroll
@@ -496,8 +603,8 @@ __global__ void __launch_bounds__(128) k_segment_sum(KParams P, Box S, const dou
             if (FB) {
                 fb_pair_delta(P, S, u, p, G, s, c, dU);
             } else {
-                long long vc;
-                sink_pair_delta<R>(P, S, p, G, pl, s, c, dU, vc);
+                double e;
+                sink_pair_delta<R>(P, S, p, G, pl, s, c, dU, e);
             }
 #pragma unroll
             for (int f = 0; f < NF; ++f) acc[f] = acc[f] + dU[f];
@@ -528,10 +635,8 @@ __global__ void __launch_bounds__(128) k_return_sinks(KParams P, Box S, Parts p,
     const unsigned nc = pl.counts[t];
     for (unsigned q = 0; q < nc; ++q) {
         const PairCell c = unpack_pair(pl.slots[b0 + q], P.R);
-        double dU[NF];
-        long long vc;
-        sink_pair_delta<R>(P, S, p, G, pl, s, c, dU, vc);
-        const double e = __ldg(pl.eta + vc);
+        double dU[NF], e;
+        sink_pair_delta<R>(P, S, p, G, pl, s, c, dU, e);
         if (e == 1.0) {
             a0 = a0 + dU[0];
             a1 = a1 + dU[1];
@@ -566,7 +671,8 @@ static inline unsigned blocks_for(long long n, int t) { return (unsigned)((n + t
     default: { constexpr int RR = 6; CALL; } break;      \
     }
 
-void launch_host_keys(const Box &S, const Parts &p, unsigned *keys, unsigned *ids, cudaStream_t stream)
+void launch_prologue(const Box &S, const Parts &p, unsigned *keys, unsigned *ids, const PlanPtrs &pl, DevStatus *st,
+                     cudaStream_t stream)
 {
     if (p.count == 0) return;
     int nmax = S.n0 > S.n1 ? S.n0 : S.n1;
@@ -574,7 +680,7 @@ void launch_host_keys(const Box &S, const Parts &p, unsigned *keys, unsigned *id
     int bits = 0;
     while ((1 << bits) < nmax) ++bits;
     const int sh = bits > 10 ? bits - 10 : 0;
-    k_host_keys<<<blocks_for(p.count, 256), 256, 0, stream>>>(S, p, sh, keys, ids);
+    k_prologue<<<blocks_for(p.count, 256), 256, 0, stream>>>(S, p, sh, keys, ids, pl.hosts, pl.fr, st);
 }
 
 template <int R, bool FB>
@@ -583,9 +689,9 @@ static void plan_one(const KParams &P, const Box &S, const Parts &p, const PlanP
 {
     constexpr int W = 2 * R + 1;
     const int warps = 8;
-    const size_t sm = (size_t)warps * plan_warp_floats(W, FB ? P.S : 1) * sizeof(float);
-    k_plan<R, FB><<<blocks_for(p.count, warps), warps * 32, sm, stream>>>(P, S, p, pl.perm, (unsigned)pl.cap,
-                                                                         pl.counts, pl.slots, pl.hosts, st);
+    const size_t sm = (size_t)warps * (plan_warp_floats(W, FB ? P.S : 1) * sizeof(float) + kPlanWarpInts * sizeof(int));
+    k_plan<R, FB><<<blocks_for(p.count, warps), warps * 32, sm, stream>>>(P, S, p, pl.perm, pl.hosts, pl.fr,
+                                                                         (unsigned)pl.cap, pl.counts, pl.slots, st);
 }
 
 void launch_plan(const KParams &P, const Box &S, const Parts &p, const PlanPtrs &pl, DevStatus *st,
@@ -619,7 +725,7 @@ void launch_deposit_atomic(const KParams &P, const Box &S, const double *u, cons
     const long long blocks_needed = (warps + 7) / 8;
     const unsigned nb = (unsigned)(blocks_needed < 152LL * 64 ? blocks_needed : 152LL * 64);
     if (P.kind == PMP_KIND_FEEDBACK) {
-        k_deposit_atomic<1, true><<<nb, 256, 0, stream>>>(P, S, u, B, b, p, G, pl);
+        PMP_DISPATCH_R(P.R, (k_deposit_atomic<RR, true><<<nb, 256, 0, stream>>>(P, S, u, B, b, p, G, pl)));
     } else {
         PMP_DISPATCH_R(P.R, (k_deposit_atomic<RR, false><<<nb, 256, 0, stream>>>(P, S, u, B, b, p, G, pl)));
     }

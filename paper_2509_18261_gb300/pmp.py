@@ -29,7 +29,7 @@ STATUS = {
 EXPORTS = [
     "pmp_create", "pmp_destroy", "pmp_set_stream", "pmp_gathered_rows", "pmp_workspace_size", "pmp_zero_buffer",
     "pmp_gather", "pmp_deposit", "pmp_fold_ghosts", "pmp_apply_limited", "pmp_backward", "pmp_get_error",
-    "pmp_limiter_counts",
+    "pmp_limiter_counts", "pmp_timing_enable", "pmp_timing_read",
 ]
 
 
@@ -56,6 +56,10 @@ class _Mesh(ctypes.Structure):
         ("reserved", ctypes.c_int32), ("dx", ctypes.c_double), ("field_stride", ctypes.c_int64),
         ("data", ctypes.c_void_p),
     ]
+
+
+class _KernelTime(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 24), ("launches", ctypes.c_int64), ("ms", ctypes.c_double)]
 
 
 class _Particles(ctypes.Structure):
@@ -93,6 +97,8 @@ def load():
         "pmp_backward": ([vp, M, M, Pa, vp, vp, vp, vp, ctypes.c_size_t], i32),
         "pmp_get_error": ([vp, ctypes.POINTER(i32), ctypes.POINTER(i64)], i32),
         "pmp_limiter_counts": ([vp, ctypes.POINTER(i64)], i32),
+        "pmp_timing_enable": ([vp, i32], i32),
+        "pmp_timing_read": ([vp, ctypes.POINTER(_KernelTime), i32, ctypes.POINTER(i32)], i32),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -253,6 +259,19 @@ def pmp_limiter_counts(ctx):
     ctx._sync_stream()
     _check("pmp_limiter_counts", load().pmp_limiter_counts(ctx.h, c))
     return c[0], c[1]
+
+
+def pmp_timing_enable(ctx, on=True):
+    _check("pmp_timing_enable", load().pmp_timing_enable(ctx.h, 1 if on else 0))
+
+
+def pmp_timing_read(ctx):
+    """{kernel name: (launches, total ms)} since the last read (synchronises)."""
+    buf = (_KernelTime * 64)()
+    n = ctypes.c_int32()
+    ctx._sync_stream()
+    _check("pmp_timing_read", load().pmp_timing_read(ctx.h, buf, 64, ctypes.byref(n)))
+    return {buf[i].name.decode(): (buf[i].launches, buf[i].ms) for i in range(min(n.value, 64))}
 
 
 # ---------------------------------------------------------------------------
