@@ -247,6 +247,34 @@ typedef struct {
 pmp_status pmp_timing_enable(pmp_ctx *ctx, int32_t on);
 pmp_status pmp_timing_read(pmp_ctx *ctx, pmp_kernel_time *out, int32_t max, int32_t *n);
 
+/* Size of the fixed device scratch of pmp_deposit_noalloc: 64 MiB, held on
+ * every GPU that loads the library until the process exits. */
+#define PMP_NOALLOC_SCRATCH_BYTES (64u << 20)
+
+/* Step 1 for supernova feedback without any device allocation.  The paper
+ * has no counterpart; this entry point exists for callers that cannot call
+ * cudaMalloc (code running inside another framework's memory pool, plugins
+ * handed only pre-allocated buffers, processes whose device footprint must
+ * not grow after start-up).  It does what pmp_gather + pmp_deposit (ATOMIC)
+ * do with a feedback context -- `gathered` receives the 12 feedback rows and
+ * `buffer` accumulates the deposit on top of what it holds -- but it takes no
+ * context and no workspace: its plan lives in a static device array of
+ * PMP_NOALLOC_SCRATCH_BYTES compiled into the library.  That limits the
+ * particle count to about 99,000 at r_K = 2 (each particle needs 28 + 8 C
+ * bytes, C the kernel-cell bound: 81 at r_K = 2, 461 at r_K = 4); larger
+ * counts return PMP_ERR_WORKSPACE and enqueue nothing.  params->kind must be
+ * PMP_KIND_FEEDBACK.
+ * The first call on a device looks up the scratch's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  Every call shares the one scratch array, which
+ * keeps the last call's contents: calls whose work overlaps on the GPU (two
+ * streams, or two threads) race and corrupt each other; serialise them.
+ * Particles outside the box are skipped; no device errors are reported (there
+ * is no context to hold them).  Calls no cudaMalloc, cudaFree or allocating
+ * library routine; enqueues on `stream` and returns. */
+pmp_status pmp_deposit_noalloc(const pmp_params *params, const pmp_mesh *state, const pmp_particles *particles,
+                               double *gathered, pmp_mesh *buffer, pmp_stream stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -29,7 +29,7 @@ STATUS = {
 EXPORTS = [
     "pmp_create", "pmp_destroy", "pmp_set_stream", "pmp_gathered_rows", "pmp_workspace_size", "pmp_zero_buffer",
     "pmp_gather", "pmp_deposit", "pmp_fold_ghosts", "pmp_apply_limited", "pmp_backward", "pmp_get_error",
-    "pmp_limiter_counts", "pmp_timing_enable", "pmp_timing_read",
+    "pmp_limiter_counts", "pmp_timing_enable", "pmp_timing_read", "pmp_deposit_noalloc",
 ]
 
 
@@ -99,6 +99,7 @@ def load():
         "pmp_limiter_counts": ([vp, ctypes.POINTER(i64)], i32),
         "pmp_timing_enable": ([vp, i32], i32),
         "pmp_timing_read": ([vp, ctypes.POINTER(_KernelTime), i32, ctypes.POINTER(i32)], i32),
+        "pmp_deposit_noalloc": ([P, M, Pa, vp, M, vp], i32),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -259,6 +260,24 @@ def pmp_limiter_counts(ctx):
     ctx._sync_stream()
     _check("pmp_limiter_counts", load().pmp_limiter_counts(ctx.h, c))
     return c[0], c[1]
+
+
+def _params_struct(params):
+    return _Params(kind=KINDS[params["kind"]], subsample=int(params["subsample"]), r_K=params["r_K"],
+                   dt=params["dt"], G=params["G"], gamma=params["gamma"], lambda_bh=params["lambda_bh"],
+                   J=params["J"], cap=params["cap"], rho_min=params["rho_min"], A_sf=params["A_sf"],
+                   A_p=params["A_p"], mu_H=params["mu_H"], RM_ej=params["RM_ej"], RM_st=params["RM_st"],
+                   eps_K=params["eps_K"])
+
+
+def pmp_deposit_noalloc(params, state, parts, gathered, buffer):
+    """Supernova gather + atomic deposit with the library's fixed scratch (no
+    device allocation by the library; see include/pmp.h)."""
+    cp = _params_struct(params)
+    pp = _parts(parts)
+    _check("pmp_deposit_noalloc", load().pmp_deposit_noalloc(ctypes.byref(cp), ctypes.byref(state.c()),
+                                                             ctypes.byref(pp), _ptr(gathered),
+                                                             ctypes.byref(buffer.c()), _stream()))
 
 
 def pmp_timing_enable(ctx, on=True):
