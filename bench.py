@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-n", type=int, default=128)
+    ap.add_argument("--n", type=int, default=None,
+                    help="shrink the box to n^3 at equal particle density (profiling captures)")
     return ap.parse_args()
 
 
@@ -255,7 +257,11 @@ def run_ours(args, world, rank, local):
     from paper_2509_18261_gb300 import pmp
     from paper_2509_18261_gb300 import synthetic as syn
 
-    w = syn.make_workload(args.workload)
+    if args.n:
+        full = syn.WORKLOADS[args.workload]["n"]
+        w = syn.make_workload(args.workload, n=args.n, count_scale=(args.n / full) ** 3)
+    else:
+        w = syn.make_workload(args.workload)
     box = w["box"]
     dev = "cuda"
     state = torch.from_numpy(w["state"]).to(dev)
@@ -365,7 +371,7 @@ def run_ours(args, world, rank, local):
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    for _ in range(args.e2e_steps):
+    for _ in range(max(args.e2e_steps, 1)):
         state.copy_(h_state, non_blocking=True)
         for k in h_fb:
             fb[k].copy_(h_fb[k], non_blocking=True)
@@ -378,7 +384,7 @@ def run_ours(args, world, rank, local):
     e1.record(stream)
     torch.cuda.synchronize()
     barrier(world)
-    e2e_ms = max_over_ranks(world, e0.elapsed_time(e1) / args.e2e_steps)
+    e2e_ms = max_over_ranks(world, e0.elapsed_time(e1) / max(args.e2e_steps, 1))
 
     # roofline of the dominant kernel (per-launch time from the library's
     # CUDA events on the launching stream)
