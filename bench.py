@@ -427,10 +427,54 @@ def run_ours(args, world, rank, local):
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clk,
     }
+    result["fwd_bwd_c4_128"] = fwd_bwd(args)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         result["cpu_baseline"] = cpu_baseline(args)
     if rank == 0:
         print(json.dumps(result), flush=True)
+
+
+def fwd_bwd(args):
+    """Forward + backward of one supernova pass on the 128^3 workload (262,144
+    supernovae, half in 32 clusters): CUDA-event times of the forward (gather,
+    deposit, fold, limited apply) and of pmp_backward, after 3 warm-ups."""
+    import torch
+
+    from paper_2509_18261_gb300 import pmp
+    from paper_2509_18261_gb300 import synthetic as syn
+
+    w = syn.make_workload("c4_128")
+    box = w["box"]
+    u0 = torch.from_numpy(w["state"]).cuda()
+    u = u0.clone()
+    parts = pmp.parts_to_device(w["fb"])
+    n = parts["x"].numel()
+    ps = pmp.Pass(w["fb_params"], box, u, parts, mode="atomic")
+    rng = torch.Generator(device="cuda").manual_seed(4)
+    gU = torch.randn(u.shape, dtype=torch.float64, device="cuda", generator=rng)
+    g = torch.empty((8, n), dtype=torch.float64, device="cuda")
+    state_in = pmp.Mesh(u0, box.n, box.g)
+    stream = torch.cuda.current_stream()
+    f_ms, b_ms = [], []
+    for it in range(3 + max(args.steps, 1)):
+        u.copy_(u0)
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record(stream)
+        ps.run()
+        e1.record(stream)
+        pmp.pmp_backward(ps.ctx, state_in, ps.buffer, parts, ps.gathered_view(), gU, g, ps.workspace)
+        e2.record(stream)
+        torch.cuda.synchronize()
+        if it >= 3:
+            f_ms.append(e0.elapsed_time(e1))
+            b_ms.append(e1.elapsed_time(e2))
+    code, idx = pmp.pmp_get_error(ps.ctx)
+    if code:
+        raise RuntimeError(f"device error {code} at {idx}")
+    ps.ctx.close()
+    fm, bm = sum(f_ms) / len(f_ms), sum(b_ms) / len(b_ms)
+    return {"fwd_ms": fm, "bwd_ms": bm, "total_ms": fm + bm, "particles": n,
+            "workload": "c4_128: 128^3, 4 ghosts, 262,144 supernovae (half in 32 Plummer clusters)"}
 
 
 # ---------------------------------------------------------------------------

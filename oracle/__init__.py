@@ -105,6 +105,8 @@ def lib():
                                    ctypes.c_int64, ctypes.c_void_p, dp]
         L.or_kernel_of.argtypes = [ctypes.POINTER(Params), ctypes.POINTER(Mesh), ctypes.c_double,
                                    ctypes.c_double, ctypes.c_double, ctypes.c_void_p, dp]
+        L.or_deltas.argtypes = [ctypes.POINTER(Params), ctypes.POINTER(Mesh), ctypes.POINTER(Particles), dp,
+                                ctypes.c_void_p, dp]
         _lib = L
     return _lib
 
@@ -281,3 +283,19 @@ def kernel_of(params, box, x, y, z, periodic=(1, 1, 1)):
     S = make_mesh(box, dummy, 1.0, periodic)
     n = lib().or_kernel_of(ctypes.byref(P), ctypes.byref(S), x, y, z, ijk.ctypes.data_as(ctypes.c_void_p), _dp(om))
     return ijk[:n].copy(), om[:n].copy()
+
+
+def deltas(params, box, state, one, dx=1.0, periodic=(1, 1, 1)):
+    """Gathered row and Delta U^s of a single particle (dict of length-1
+    arrays): returns (ijk (n, 3) unwrapped, dU (n, 5))."""
+    G = gather(params, box, state, one, dx, periodic)
+    R = int(np.ceil(params["r_K"]))
+    w = 2 * R + 1
+    ijk = np.zeros((w ** 3, 3), dtype=np.int32)
+    dU = np.zeros((w ** 3, 5))
+    P = make_params(params)
+    S = make_mesh(box, state, dx, periodic)
+    pp = make_particles(one)
+    n = lib().or_deltas(ctypes.byref(P), ctypes.byref(S), ctypes.byref(pp), _dp(np.ascontiguousarray(G)),
+                        ijk.ctypes.data_as(ctypes.c_void_p), _dp(dU))
+    return ijk[:n].copy(), dU[:n].copy()

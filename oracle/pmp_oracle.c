@@ -965,3 +965,30 @@ int or_kernel_of(const or_params *P, const or_mesh *S, double x, double y, doubl
     free(kc);
     return nk;
 }
+
+/* Deposition function of ONE particle: its kernel cells (unwrapped ijk) and
+ * Delta U^s_c ([n][5]) from its gathered row G ([rows][1]); returns n.  Used
+ * by the finite-difference tests of the adjoint. */
+int or_deltas(const or_params *P, const or_mesh *S, const or_particles *p, const double *G, int32_t *ijk, double *dU)
+{
+    kcell *kc = alloc_kcells(P->r_K);
+    if (!kc) return -1;
+    double x = p->x[0], y = p->y[0], z = p->z[0];
+    int nk = kernel_cells(S, P->r_K, x, y, z, kc);
+    int n = 0;
+    for (int t = 0; t < nk; t++) {
+        double w = cell_fraction(P, &kc[t], x, y, z);
+        if (w == 0.0) continue;
+        double U[NF], d[NF];
+        read_state(S, kc[t].wi, kc[t].wj, kc[t].wk, U);
+        if (P->kind == KIND_FEEDBACK) feedback_delta(w, U, G, 1, &kc[t], d);
+        else sink_delta(P, S->dx, U, G, 1, &kc[t], d);
+        ijk[3 * n] = kc[t].ci;
+        ijk[3 * n + 1] = kc[t].cj;
+        ijk[3 * n + 2] = kc[t].ck;
+        for (int f = 0; f < NF; f++) dU[NF * n + f] = d[f];
+        n++;
+    }
+    free(kc);
+    return n;
+}

@@ -654,16 +654,37 @@ pmp_status pmp_backward(pmp_ctx *ctx, const pmp_mesh *state_in, const pmp_mesh *
                         const double *gathered, const double *gU, double *g_out, void *workspace,
                         size_t workspace_bytes)
 {
-    (void)workspace;
-    (void)workspace_bytes;
-    (void)state_in;
-    (void)buffer;
-    (void)particles;
-    (void)gathered;
-    (void)gU;
-    (void)g_out;
-    if (!ctx) return PMP_ERR_ARG;
-    return PMP_ERR_ARG;
+    if (!ctx || ctx->p.kind != PMP_KIND_FEEDBACK) return PMP_ERR_ARG;
+    Box S, B;
+    Parts q;
+    pmp_status s = make_box(state_in, &S);
+    if (s) return s;
+    s = make_box(buffer, &B);
+    if (s) return s;
+    for (int a = 0; a < 3; ++a)
+        if (state_in->n[a] != buffer->n[a] || state_in->periodic[a] != buffer->periodic[a]) return PMP_ERR_ARG;
+    s = make_parts(ctx, particles, &q);
+    if (s) return s;
+    if (q.count > 0 && (!gathered || !gU || !g_out)) return PMP_ERR_ARG;
+    const long long nv = nvalid_of(state_in);
+    const Layout L = layout(ctx->p, q.count, nv, ctx->plan_mode);
+    s = check_workspace(L, workspace, workspace_bytes);
+    if (s) return s;
+    s = check_plan(ctx, q.count, nv, workspace);
+    if (s) return s;
+    if (q.count == 0) return PMP_OK;
+    const KParams P = make_kparams(ctx->p, state_in->dx);
+    const pmp::PlanPtrs pl = plan_ptrs(L, workspace, ctx->p, ctx->plan_mode);
+    unsigned char *pass = reinterpret_cast<unsigned char *>(static_cast<char *>(workspace) + L.queue);
+    {
+        Timed tm(ctx, "backward_mask");
+        pmp::launch_pass_mask(S, state_in->data, B, buffer->data, pass, ctx->stream);
+    }
+    {
+        Timed tm(ctx, "backward");
+        pmp::launch_backward_fb(P, S, state_in->data, gU, q, pl, pass, gathered, g_out, ctx->stream);
+    }
+    return last_launch();
 }
 
 pmp_status pmp_get_error(pmp_ctx *ctx, int32_t *code, int64_t *index)

@@ -38,6 +38,11 @@ void launch_segment_sum(const KParams &P, const Box &S, const double *u, const B
 void launch_return_sinks(const KParams &P, const Box &S, const Parts &p, const double *G, const PlanPtrs &pl,
                          DevStatus *st, cudaStream_t stream);
 
+void launch_backward_fb(const KParams &P, const Box &S, const double *u, const double *gU, const Parts &p,
+                        const PlanPtrs &pl, const unsigned char *pass, const double *G, double *gout,
+                        cudaStream_t stream);
+void launch_pass_mask(const Box &S, const double *u, const Box &B, const double *b, unsigned char *pass,
+                      cudaStream_t stream);
 void launch_zero(const Box &B, double *b, cudaStream_t stream);
 void launch_fold(const Box &B, double *b, cudaStream_t stream);
 void launch_sink_aux(const KParams &P, const Box &S, const double *u, double *grec, double *drec,

@@ -294,6 +294,40 @@ __global__ void __launch_bounds__(256) k_apply_sink(Box S, double *__restrict__ 
     if ((threadIdx.x & 31) == 0 && m1) atomicAdd(&st->n_limited, (unsigned long long)__popc(m1));
 }
 
+// Adjoint of the limited apply: pass[c] = 1 where the supernova limiter left
+// the cell's change unscaled (lambda = 1), 0 where it acted; gradients flow
+// only through the former.
+__global__ void __launch_bounds__(256) k_pass_mask(Box S, const double *__restrict__ u, Box B,
+                                                   const double *__restrict__ b, unsigned char *__restrict__ pass)
+{
+    const long long nvalid = (long long)S.n0 * S.n1 * S.n2;
+    const long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= nvalid) return;
+    const int i = (int)(v % S.n0);
+    const long long r = v / S.n0;
+    const int j = (int)(r % S.n1), k = (int)(r / S.n1);
+    const long long cs = S.at(i, j, k), cb = B.at(i, j, k);
+    double U[NF], D[NF];
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+        U[f] = __ldg(u + (long long)f * S.fs + cs);
+        D[f] = __ldg(b + (long long)f * B.fs + cb);
+    }
+    bool ok = (D[1] == 0.0 && D[2] == 0.0 && D[3] == 0.0) || sn_lambda_holds_f32(U, D);
+    if (!ok) {
+        int nr;
+        ok = sn_lambda(U, D, nr) == 1.0;
+    }
+    pass[v] = ok ? 1 : 0;
+}
+
+void launch_pass_mask(const Box &S, const double *u, const Box &B, const double *b, unsigned char *pass,
+                      cudaStream_t stream)
+{
+    const long long nvalid = (long long)S.n0 * S.n1 * S.n2;
+    k_pass_mask<<<(unsigned)((nvalid + 255) / 256), 256, 0, stream>>>(S, u, B, b, pass);
+}
+
 void launch_zero(const Box &B, double *b, cudaStream_t stream)
 {
     k_zero<<<152 * 8, 256, 0, stream>>>(b, B.fs, B.ncells);

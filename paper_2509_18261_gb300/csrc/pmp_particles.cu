@@ -760,3 +760,113 @@ void launch_return_sinks(const KParams &P, const Box &S, const Parts &p, const d
 }
 
 }  // namespace pmp
+
+// ---------------------------------------------------------------------------
+// adjoint of a supernova pass
+// ---------------------------------------------------------------------------
+
+namespace pmp {
+
+// L depends on particle s through Delta U^s_c (Eq. du with the readings of
+// the forward pass).  With a = dL/dU_new at the owner of c (zero where the
+// limiter acted) the per-pair sums are
+//   Sgr = sum w a_rho, Sgp = sum w a_p, Srgp = sum w rho_c a_p, SgE = sum w a_E,
+//   Sgpd = sum w a_p.dhat, SgEd = sum w a_E dhat,
+//   X = sum (w/|d|) (t - dhat (dhat.t)),  t = a_p + a_E v_COM,
+// and dL/dq = Sgr + v_COM.Sgp, dL/dv_COM = Srgp + q Sgp + Pv SgEd,
+// dL/de = SgE, dL/dPv = Sgpd + v_COM.SgEd, dL/dx_s = -Pv X; the chain rule
+// through q = m/V_snr, e = (E + |p|^2/2m)/V_snr, v_COM = (P_gas + p)/M_snr and
+// Pv = |p_radial|/V_snr gives dL/d(m, E, p).  The kernel-cell set and omega
+// are constant in position almost everywhere and carry no derivative.
+__global__ void __launch_bounds__(128) k_backward_fb(KParams P, Box S, const double *__restrict__ u,
+                                                     const double *__restrict__ gU, Parts p, PlanPtrs pl,
+                                                     const unsigned char *__restrict__ pass,
+                                                     const double *__restrict__ G, double *__restrict__ gout)
+{
+    __shared__ double wtab[kMaxS3 + 1];
+    fill_omega_table(P, wtab);
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= p.count) return;
+    const long long s = pl.perm ? (long long)pl.perm[t] : t;
+    const long long gs = p.count;
+    if (pl.hosts[s] == kNoHost || !(p.m[s] > 0.0)) {
+        for (int r = 0; r < 8; ++r) gout[r * gs + s] = 0.0;
+        return;
+    }
+    const double x = p.x[s], y = p.y[s], z = p.z[s];
+    const double m = p.m[s], pe0 = p.px[s], pe1 = p.py[s], pe2 = p.pz[s], Esn = p.e[s];
+    const double Msnr = G[FB_MSNR * gs + s], Vsnr = G[FB_VSNR * gs + s];
+    const double vc0 = G[FB_VX * gs + s], vc1 = G[FB_VY * gs + s], vc2 = G[FB_VZ * gs + s];
+    const double prad = G[FB_PRAD * gs + s], q = G[FB_Q * gs + s], Pv = G[FB_PV * gs + s];
+    const int regime = (int)G[FB_REGIME * gs + s];
+    double Sgr = 0.0, Sgp0 = 0.0, Sgp1 = 0.0, Sgp2 = 0.0, Srgp0 = 0.0, Srgp1 = 0.0, Srgp2 = 0.0, SgE = 0.0;
+    double Sgpd = 0.0, SgEd0 = 0.0, SgEd1 = 0.0, SgEd2 = 0.0, X0 = 0.0, X1 = 0.0, X2 = 0.0;
+    const unsigned long long b0 = (unsigned long long)t * pl.cap;
+    const unsigned nc = pl.counts[t];
+    for (unsigned k = 0; k < nc; ++k) {
+        const PairCell c = unpack_pair(pl.slots[b0 + k], P.R);
+        const int oi = owner(c.i, S.n0), oj = owner(c.j, S.n1), ok = owner(c.k, S.n2);
+        if (!pass[vidx(S, oi, oj, ok)]) continue;
+        const long long o = S.at(oi, oj, ok);
+        const double w = wtab[c.cnt];
+        const double ar = __ldg(gU + o), ap0 = __ldg(gU + S.fs + o), ap1 = __ldg(gU + 2 * S.fs + o),
+                     ap2 = __ldg(gU + 3 * S.fs + o), aE = __ldg(gU + 4 * S.fs + o);
+        const double rho = __ldg(u + o);
+        Sgr += w * ar;
+        Sgp0 += w * ap0;
+        Sgp1 += w * ap1;
+        Sgp2 += w * ap2;
+        Srgp0 += w * rho * ap0;
+        Srgp1 += w * rho * ap1;
+        Srgp2 += w * rho * ap2;
+        SgE += w * aE;
+        const double d0 = ((double)c.i + 0.5) - x, d1 = ((double)c.j + 0.5) - y, d2 = ((double)c.k + 0.5) - z;
+        const double dd = d0 * d0 + d1 * d1 + d2 * d2;
+        if (dd > 0.0) {
+            const double dist = sqrt(dd);
+            const double h0 = d0 / dist, h1 = d1 / dist, h2 = d2 / dist;
+            Sgpd += w * (ap0 * h0 + ap1 * h1 + ap2 * h2);
+            SgEd0 += w * aE * h0;
+            SgEd1 += w * aE * h1;
+            SgEd2 += w * aE * h2;
+            const double t0 = ap0 + aE * vc0, t1 = ap1 + aE * vc1, t2 = ap2 + aE * vc2;
+            const double th = t0 * h0 + t1 * h1 + t2 * h2;
+            const double f = w / dist;
+            X0 += f * (t0 - h0 * th);
+            X1 += f * (t1 - h1 * th);
+            X2 += f * (t2 - h2 * th);
+        }
+    }
+    const double dLdq = Sgr + (vc0 * Sgp0 + vc1 * Sgp1 + vc2 * Sgp2);
+    const double dLdv0 = Srgp0 + q * Sgp0 + Pv * SgEd0, dLdv1 = Srgp1 + q * Sgp1 + Pv * SgEd1,
+                 dLdv2 = Srgp2 + q * Sgp2 + Pv * SgEd2;
+    const double dLde = SgE;
+    const double dLdPv = Sgpd + (vc0 * SgEd0 + vc1 * SgEd1 + vc2 * SgEd2);
+    double dpr_dm = 0.0, dpr_dE = 0.0;
+    if (regime == 2) {
+        dpr_dm = -0.17 * prad / Msnr;
+    } else if (regime == 1) {
+        dpr_dm = prad / (2.0 * m);
+        dpr_dE = Esn != 0.0 ? prad / (2.0 * Esn) : 0.0;
+    }
+    const double pe2sum = pe0 * pe0 + pe1 * pe1 + pe2 * pe2;
+    const double vdot = dLdv0 * vc0 + dLdv1 * vc1 + dLdv2 * vc2;
+    gout[0 * gs + s] = dLdq / Vsnr - dLde * pe2sum / (2.0 * m * m * Vsnr) - vdot / Msnr + dLdPv * dpr_dm / Vsnr;
+    gout[1 * gs + s] = dLde / Vsnr + dLdPv * dpr_dE / Vsnr;
+    gout[2 * gs + s] = dLde * pe0 / (m * Vsnr) + dLdv0 / Msnr;
+    gout[3 * gs + s] = dLde * pe1 / (m * Vsnr) + dLdv1 / Msnr;
+    gout[4 * gs + s] = dLde * pe2 / (m * Vsnr) + dLdv2 / Msnr;
+    gout[5 * gs + s] = -Pv * X0;
+    gout[6 * gs + s] = -Pv * X1;
+    gout[7 * gs + s] = -Pv * X2;
+}
+
+void launch_backward_fb(const KParams &P, const Box &S, const double *u, const double *gU, const Parts &p,
+                        const PlanPtrs &pl, const unsigned char *pass, const double *G, double *gout,
+                        cudaStream_t stream)
+{
+    if (p.count == 0) return;
+    k_backward_fb<<<blocks_for(p.count, 128), 128, 0, stream>>>(P, S, u, gU, p, pl, pass, G, gout);
+}
+
+}  // namespace pmp

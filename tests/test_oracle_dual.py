@@ -1,0 +1,69 @@
+"""Pins of the dual-number oracle (oracle/dual.py) used for the adjoint tests:
+its primal values equal the C oracle's summed buffer, and its tangents equal
+central finite differences of the C oracle's deposition function."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2509_18261_gb300 import synthetic as syn
+
+FIELDS = ("m", "e", "px", "py", "pz", "x", "y", "z")
+
+
+def _case(seed=21, n=(12, 12, 12), count=14):
+    rng = np.random.default_rng(seed)
+    box = syn.Box(n, 2)
+    state = syn.gas_state(rng, box)
+    parts = syn.particles(rng, box.n, count, "feedback")
+    return box, state, parts
+
+
+def test_dual_primal_matches_c_oracle(orc):
+    from oracle import dual
+
+    box, state, parts = _case()
+    params = syn.feedback_params()
+    G = orc.gather(params, box, state, parts)
+    buf, A = box.empty(0.0), box.empty(0.0)
+    orc.deposit(params, box, state, parts, G, buf, A)
+    orc.fold(box, buf, A)
+    zero = {k: np.zeros_like(parts[k]) for k in FIELDS}
+    val, _ = dual.pass_tangent(orc, params, box, state, parts, zero, np.ones(box.n[::-1], bool))
+    assert np.all(np.abs(val - box.valid(buf)) <= 1e-13 * box.valid(A) + 1e-300)
+
+
+@pytest.mark.parametrize("field", FIELDS)
+def test_dual_tangent_matches_central_differences(orc, field):
+    from oracle import dual
+
+    box, state, parts = _case(seed=22, count=6)
+    params = syn.feedback_params()
+    rng = np.random.default_rng(5)
+    R = rng.standard_normal((5,) + box.n[::-1])
+    nx, ny, nz = box.n
+    for s in range(len(parts["x"])):
+        one = {k: parts[k][s:s + 1].copy() for k in FIELDS}
+        tang = {k: np.zeros(1) for k in FIELDS}
+        tang[field][0] = 1.0
+        _, tan = dual.pass_tangent(orc, params, box, state, one, tang, np.ones(box.n[::-1], bool))
+        want = float(np.sum(R * tan))
+        h = 1e-6 * max(1.0, abs(one[field][0]))
+
+        def L(v):
+            o = {k: a.copy() for k, a in one.items()}
+            o[field][0] = v
+            ijk, dU = orc.deltas(params, box, state, o)
+            return math.fsum(float(R[f, k % nz, j % ny, i % nx] * dU[c, f])
+                             for c, (i, j, k) in enumerate(ijk) for f in range(5))
+
+        x0 = one[field][0]
+        if field in ("x", "y", "z"):
+            a, b = dict(one), dict(one)
+            a[field] = np.array([x0 + h]); b[field] = np.array([x0 - h])
+            ka = orc.kernel_of(params, box, a["x"][0], a["y"][0], a["z"][0])
+            kb = orc.kernel_of(params, box, b["x"][0], b["y"][0], b["z"][0])
+            if not (np.array_equal(ka[0], kb[0]) and np.array_equal(ka[1], kb[1])):
+                continue  # omega or the kernel cells change inside [x - h, x + h]
+        fd = (L(x0 + h) - L(x0 - h)) / (2 * h)
+        assert fd == pytest.approx(want, rel=2e-6, abs=1e-9 * (abs(want) + 1e-3))
