@@ -299,3 +299,70 @@ def deltas(params, box, state, one, dx=1.0, periodic=(1, 1, 1)):
     n = lib().or_deltas(ctypes.byref(P), ctypes.byref(S), ctypes.byref(pp), _dp(np.ascontiguousarray(G)),
                         ijk.ctypes.data_as(ctypes.c_void_p), _dp(dU))
     return ijk[:n].copy(), dU[:n].copy()
+
+
+# --- batched patches ----------------------------------------------------------
+
+class BatchT(ctypes.Structure):
+    _fields_ = [
+        ("np", ctypes.c_int32), ("ng", ctypes.c_int32), ("dx", ctypes.c_double),
+        ("dims", ctypes.c_void_p), ("nb", ctypes.c_void_p), ("offset", ctypes.c_void_p),
+        ("fstride", ctypes.c_void_p), ("first", ctypes.c_void_p),
+    ]
+
+
+def _batch_struct(batch, first, dx=1.0):
+    """ctypes view of a synthetic.Batch (arrays kept alive by the caller)."""
+    keep = dict(
+        dims=np.ascontiguousarray(batch.dims, dtype=np.int32),
+        nb=np.ascontiguousarray(batch.nb, dtype=np.int32),
+        offset=np.ascontiguousarray(batch.offset, dtype=np.int64),
+        fstride=np.ascontiguousarray(batch.fstride, dtype=np.int64),
+        first=np.ascontiguousarray(first, dtype=np.int64),
+    )
+    T = BatchT(np=batch.np, ng=batch.g, dx=dx, **{k: v.ctypes.data for k, v in keep.items()})
+    return T, keep
+
+
+def _batch_lib():
+    L = lib()
+    if not getattr(L, "_batch_ready", False):
+        dp = ctypes.POINTER(ctypes.c_double)
+        L.or_batch_cycle.argtypes = [ctypes.POINTER(Params), ctypes.POINTER(BatchT), dp, dp, dp,
+                                     ctypes.POINTER(Particles), dp, dp, ctypes.c_void_p]
+        L.or_batch_fill_ghosts.argtypes = [ctypes.POINTER(BatchT), dp]
+        L.or_batch_fold.argtypes = [ctypes.POINTER(BatchT), dp]
+        L._batch_ready = True
+    return L
+
+
+def batch_fill_ghosts(batch, arena):
+    """Every ghost cell := the cell of the neighbour patch it stands for."""
+    T, keep = _batch_struct(batch, np.zeros(batch.np + 1, dtype=np.int64))
+    _batch_lib().or_batch_fill_ghosts(ctypes.byref(T), _dp(arena))
+
+
+def batch_fold(batch, arena):
+    """Cross-patch ghost summation of a buffer arena, in place."""
+    T, keep = _batch_struct(batch, np.zeros(batch.np + 1, dtype=np.int64))
+    _batch_lib().or_batch_fold(ctypes.byref(T), _dp(arena))
+
+
+def batch_cycle(params, batch, state, parts, first, dx=1.0, want_abs=False, want_eta=False):
+    """One pass over a batch of patches (Steps 1-5).  Mutates the valid cells of
+    ``state`` (an arena) and, for sinks, the particle mass and momentum.
+    Returns dict(gathered, buf, absbuf, eta, counts)."""
+    T, keep = _batch_struct(batch, first, dx)
+    n = int(first[-1])
+    assert len(parts["x"]) == n
+    G = np.zeros((len(rows(params["kind"])), n))
+    buf = batch.empty(0.0)
+    absbuf = batch.empty(0.0) if want_abs else None
+    eta = np.empty(batch.ncells_valid) if want_eta else None
+    counts = np.zeros(2, dtype=np.int64)
+    P = make_params(params)
+    pp = make_particles(parts)
+    st = _batch_lib().or_batch_cycle(ctypes.byref(P), ctypes.byref(T), _dp(state), _dp(buf), _dp(absbuf),
+                                     ctypes.byref(pp), _dp(G), _dp(eta), counts.ctypes.data_as(ctypes.c_void_p))
+    _check(st, "batch_cycle")
+    return dict(gathered=G, buf=buf, absbuf=absbuf, eta=eta, counts=counts)

@@ -63,7 +63,10 @@ typedef struct {
 typedef struct {
     int32_t n[3];        /* valid cells per axis */
     int32_t ng;          /* ghost cells on every side */
-    int32_t periodic[3]; /* 1: axis wraps */
+    int32_t periodic[3]; /* 1: axis wraps; 0: kernels are cut at the faces;
+                            2: the ghost cells hold the values of the cells
+                            they stand for (a patch of a batch, whose ghosts
+                            were filled from its neighbours) */
     int32_t pad_;
     double dx;           /* physical cell size; V = dx^3 */
     int64_t fstride;     /* doubles between fields */
@@ -239,7 +242,9 @@ static int kernel_cells(const or_mesh *S, double rK, double x, double y, double 
                 if (!inside(dd, r2)) continue;
                 kcell *kc = &out[cnt++];
                 kc->ci = ci; kc->cj = cj; kc->ck = ck;
-                kc->wi = wrap(ci, S->n[0]); kc->wj = wrap(cj, S->n[1]); kc->wk = wrap(ck, S->n[2]);
+                kc->wi = S->periodic[0] == 2 ? ci : wrap(ci, S->n[0]);
+                kc->wj = S->periodic[1] == 2 ? cj : wrap(cj, S->n[1]);
+                kc->wk = S->periodic[2] == 2 ? ck : wrap(ck, S->n[2]);
                 kc->d[0] = d0; kc->d[1] = d1; kc->d[2] = d2c;
                 kc->d2 = dd;
             }
@@ -501,11 +506,21 @@ static double cell_fraction(const or_params *P, const kcell *c, double x, double
  * absbuf is given, it accumulates sum_s |Delta U^s| per cell and field (the
  * analogue of the error buffer E of App. A.1, used for tolerances).  Cells
  * with omega = 0 receive nothing. */
+static int deposit_parts(const or_params *P, const or_mesh *S, const or_particles *p, const double *gathered,
+                         int64_t gstride, or_mesh *B, double *absbuf);
+
 int or_deposit(const or_params *P, const or_mesh *S, const or_particles *p, const double *gathered, or_mesh *B,
                double *absbuf)
 {
     if (!P || !S || !p || !gathered || !B) return OR_ERR_ARG;
     if (B->ng < stencil_halfwidth(P->r_K)) return OR_ERR_ARG;
+    return deposit_parts(P, S, p, gathered, p->count, B, absbuf);
+}
+
+/* or_deposit with particle s's gathered row r at gathered[r * gstride + s]. */
+static int deposit_parts(const or_params *P, const or_mesh *S, const or_particles *p, const double *gathered,
+                         int64_t gstride, or_mesh *B, double *absbuf)
+{
     kcell *kc = alloc_kcells(P->r_K);
     if (!kc) return OR_ERR_NOMEM;
     int status = OR_OK;
@@ -519,8 +534,8 @@ int or_deposit(const or_params *P, const or_mesh *S, const or_particles *p, cons
             if (w == 0.0) continue;
             double U[NF], dU[NF];
             read_state(S, kc[t].wi, kc[t].wj, kc[t].wk, U);
-            if (P->kind == KIND_FEEDBACK) feedback_delta(w, U, gathered + s, p->count, &kc[t], dU);
-            else sink_delta(P, S->dx, U, gathered + s, p->count, &kc[t], dU);
+            if (P->kind == KIND_FEEDBACK) feedback_delta(w, U, gathered + s, gstride, &kc[t], dU);
+            else sink_delta(P, S->dx, U, gathered + s, gstride, &kc[t], dU);
             int64_t b = cell_index(B, kc[t].ci, kc[t].cj, kc[t].ck);
             for (int f = 0; f < NF; f++) {
                 B->u[(int64_t)f * B->fstride + b] = B->u[(int64_t)f * B->fstride + b] + dU[f];
@@ -651,9 +666,19 @@ static double sink_eta(const or_params *P, double dx, const double U[NF], const 
  * in Step 1 and eta from the pre-update state and the summed buffer of the
  * owning cell (eta at a ghost image is its owner's).  V is common to all
  * cells, so u_s := u_s - V sum_c eta_c Delta U^s_c. */
+static int return_parts(const or_params *P, const or_mesh *S, const or_mesh *B, or_particles *p,
+                        const double *gathered, int64_t gstride);
+
 int or_return_sinks(const or_params *P, const or_mesh *S, const or_mesh *B, or_particles *p, const double *gathered)
 {
     if (!P || !S || !B || !p || !gathered || P->kind != KIND_SINK) return OR_ERR_ARG;
+    return return_parts(P, S, B, p, gathered, p->count);
+}
+
+/* or_return_sinks with particle s's gathered row r at gathered[r * gstride + s]. */
+static int return_parts(const or_params *P, const or_mesh *S, const or_mesh *B, or_particles *p,
+                        const double *gathered, int64_t gstride)
+{
     kcell *kc = alloc_kcells(P->r_K);
     if (!kc) return OR_ERR_NOMEM;
     double V = cell_volume(S->dx);
@@ -667,7 +692,7 @@ int or_return_sinks(const or_params *P, const or_mesh *S, const or_mesh *B, or_p
         for (int t = 0; t < nk; t++) {
             double U[NF], dU[NF], D[NF];
             read_state(S, kc[t].wi, kc[t].wj, kc[t].wk, U);
-            sink_delta(P, S->dx, U, gathered + s, p->count, &kc[t], dU);
+            sink_delta(P, S->dx, U, gathered + s, gstride, &kc[t], dU);
             int64_t o = cell_index(B, kc[t].wi, kc[t].wj, kc[t].wk);
             for (int f = 0; f < NF; f++) D[f] = B->u[(int64_t)f * B->fstride + o];
             double eta = sink_eta(P, S->dx, U, D);
@@ -991,4 +1016,224 @@ int or_deltas(const or_params *P, const or_mesh *S, const or_particles *p, const
     }
     free(kc);
     return n;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Batched form: many uneven patches of one level tiling a periodic domain   */
+/* ------------------------------------------------------------------------ */
+
+/* The patches form a rectilinear grid: every patch in a row of the grid has
+ * the same extent across that row.  Patch p lists its neighbours in nb[p][26],
+ * the patch displaced by o = (ox, oy, oz) in {-1,0,1}^3 \ {0}, in the order oz
+ * slowest, ox fastest.  A padded coordinate c of patch p is then the valid
+ * cell, on each axis a,
+ *   c_a + n_q,a   of the neighbour q below   (c_a < 0),
+ *   c_a - n_p,a   of the neighbour q above   (c_a >= n_p,a),
+ *   c_a           otherwise,
+ * q being nb[p][o] with o_a the sign of the case.  Each patch keeps state
+ * and buffer at offset[p] of two arenas, [5][fstride[p]], padded by ng ghost
+ * cells; its particles are [first[p], first[p] + count[p]) of one particle
+ * set, in patch-local cell units, and their gathered rows have stride
+ * first[np] (the total count). */
+typedef struct {
+    int32_t np;             /* number of patches */
+    int32_t ng;             /* ghost cells per side, the same for every patch */
+    double dx;              /* cell size (one level) */
+    const int32_t *dims;    /* [np][3] valid cells per axis */
+    const int32_t *nb;      /* [np][26] neighbour patches */
+    const int64_t *offset;  /* [np] arena offset of (field 0, padded cell 0) */
+    const int64_t *fstride; /* [np] elements between fields */
+    const int64_t *first;   /* [np + 1] particle ranges, first[np] = total */
+} or_batch;
+
+static int nb_slot(int ox, int oy, int oz)
+{
+    int t = ((oz + 1) * 3 + (oy + 1)) * 3 + (ox + 1);
+    return t > 13 ? t - 1 : t;
+}
+
+static or_mesh batch_view(const or_batch *T, int p, double *arena)
+{
+    or_mesh M;
+    for (int a = 0; a < 3; a++) { M.n[a] = T->dims[3 * p + a]; M.periodic[a] = 2; }
+    M.ng = T->ng;
+    M.pad_ = 0;
+    M.dx = T->dx;
+    M.fstride = T->fstride[p];
+    M.u = arena + T->offset[p];
+    return M;
+}
+
+/* Owning (patch, valid coordinate) of padded coordinate c of patch p. */
+static int batch_owner(const or_batch *T, int p, const int c[3], int w[3])
+{
+    const int32_t *np_ = T->dims + 3 * p;
+    int o[3];
+    for (int a = 0; a < 3; a++) o[a] = c[a] < 0 ? -1 : (c[a] >= np_[a] ? 1 : 0);
+    int q = (o[0] || o[1] || o[2]) ? T->nb[26 * p + nb_slot(o[0], o[1], o[2])] : p;
+    for (int a = 0; a < 3; a++) w[a] = c[a] + (o[a] < 0 ? T->dims[3 * q + a] : 0) - (o[a] > 0 ? np_[a] : 0);
+    return q;
+}
+
+/* Every ghost cell of every patch := the cell it stands for (all 5 fields). */
+static void batch_fill_ghosts(const or_batch *T, double *arena)
+{
+    int g = T->ng;
+    for (int p = 0; p < T->np; p++) {
+        or_mesh M = batch_view(T, p, arena);
+        for (int k = -g; k < M.n[2] + g; k++)
+            for (int j = -g; j < M.n[1] + g; j++)
+                for (int i = -g; i < M.n[0] + g; i++) {
+                    if (i >= 0 && i < M.n[0] && j >= 0 && j < M.n[1] && k >= 0 && k < M.n[2]) continue;
+                    int c[3] = {i, j, k}, w[3];
+                    int q = batch_owner(T, p, c, w);
+                    or_mesh Q = batch_view(T, q, arena);
+                    int64_t src = cell_index(&Q, w[0], w[1], w[2]), dst = cell_index(&M, i, j, k);
+                    for (int f = 0; f < NF; f++) M.u[(int64_t)f * M.fstride + dst] = Q.u[(int64_t)f * Q.fstride + src];
+                }
+    }
+}
+
+/* Ghost-zone summation across patches (Step 2, App. A.2): each valid cell c of
+ * patch p becomes ((B_c + B_img1) + B_img2) + ... over its ghost images, taken
+ * in lexicographic order of the image offset (oz, oy, ox).  The image at
+ * offset o lies in the patch q = nb[p][-o], at c_a + n_q,a (o_a = 1),
+ * c_a - n_p,a (o_a = -1) or c_a (o_a = 0), when that is inside q's padded
+ * box.  With one patch whose neighbours are all itself this is the fold of a
+ * periodic box.  Ghost cells are only read, so the fold runs in place. */
+static void batch_fold_arena(const or_batch *T, double *arena)
+{
+    int g = T->ng;
+    for (int p = 0; p < T->np; p++) {
+        or_mesh M = batch_view(T, p, arena);
+        for (int f = 0; f < NF; f++)
+            for (int k = 0; k < M.n[2]; k++)
+                for (int j = 0; j < M.n[1]; j++)
+                    for (int i = 0; i < M.n[0]; i++) {
+                        int64_t c = cell_index(&M, i, j, k);
+                        double v = M.u[(int64_t)f * M.fstride + c];
+                        for (int oz = -1; oz <= 1; oz++)
+                            for (int oy = -1; oy <= 1; oy++)
+                                for (int ox = -1; ox <= 1; ox++) {
+                                    if (ox == 0 && oy == 0 && oz == 0) continue;
+                                    int q = T->nb[26 * p + nb_slot(-ox, -oy, -oz)];
+                                    int o[3] = {ox, oy, oz}, cc[3] = {i, j, k}, gi[3], in = 1;
+                                    for (int a = 0; a < 3; a++) {
+                                        int nq = T->dims[3 * q + a], npa = M.n[a];
+                                        gi[a] = cc[a] + (o[a] > 0 ? nq : 0) - (o[a] < 0 ? npa : 0);
+                                        if (gi[a] < -g || gi[a] >= nq + g) in = 0;
+                                    }
+                                    if (!in) continue;
+                                    or_mesh Q = batch_view(T, q, arena);
+                                    v = v + Q.u[(int64_t)f * Q.fstride + cell_index(&Q, gi[0], gi[1], gi[2])];
+                                }
+                        M.u[(int64_t)f * M.fstride + c] = v;
+                    }
+    }
+}
+
+static int64_t batch_arena_len(const or_batch *T)
+{
+    int64_t len = 0;
+    for (int p = 0; p < T->np; p++) {
+        int64_t e = T->offset[p] + (int64_t)NF * T->fstride[p];
+        if (e > len) len = e;
+    }
+    return len;
+}
+
+static int batch_check(const or_params *P, const or_batch *T)
+{
+    if (!T || T->np <= 0 || T->ng < stencil_halfwidth(P->r_K)) return OR_ERR_ARG;
+    for (int p = 0; p < T->np; p++)
+        for (int a = 0; a < 3; a++)
+            if (T->dims[3 * p + a] < T->ng) return OR_ERR_ARG;
+    return OR_OK;
+}
+
+/* Exported for tests: fills the ghosts of a state arena, or folds a buffer
+ * arena, with the rules above. */
+void or_batch_fill_ghosts(const or_batch *T, double *arena) { batch_fill_ghosts(T, arena); }
+void or_batch_fold(const or_batch *T, double *arena) { batch_fold_arena(T, arena); }
+
+/* One PMP pass (Sec. 2.2) over a batch: Steps 1-5 with every patch's ghost
+ * cells read through its neighbours (a private copy of the state with filled
+ * ghosts; the caller's ghost cells are never read), particles of patch 0, 1,
+ * ... each in index order, the cross-patch fold above, Step 4 with eta at a
+ * ghost image taken from the cell it stands for, and the limited update of
+ * every valid cell.  buf (and absbuf) receive the deposits including ghosts,
+ * then the folded sums in valid cells.  eta_out gets one value per valid cell,
+ * patch after patch (x fastest).  counts as for or_apply, summed. */
+int or_batch_cycle(const or_params *P, const or_batch *T, double *state, double *buf, double *absbuf,
+                   or_particles *p, double *gathered, double *eta_out, int64_t *counts)
+{
+    int st = batch_check(P, T);
+    if (st) return st;
+    if (!p || !gathered || !state || !buf || p->count != T->first[T->np]) return OR_ERR_ARG;
+    int64_t len = batch_arena_len(T);
+    double *scratch = (double *)malloc(sizeof(double) * (size_t)len);
+    kcell *kc = alloc_kcells(P->r_K);
+    if (!scratch || !kc) { free(scratch); free(kc); return OR_ERR_NOMEM; }
+    memcpy(scratch, state, sizeof(double) * (size_t)len);
+    batch_fill_ghosts(T, scratch);
+    for (int q = 0; q < T->np; q++) {
+        or_mesh B = batch_view(T, q, buf);
+        int64_t pc = (int64_t)(B.n[0] + 2 * B.ng) * (B.n[1] + 2 * B.ng) * (B.n[2] + 2 * B.ng);
+        for (int f = 0; f < NF; f++)
+            for (int64_t c = 0; c < pc; c++) {
+                B.u[(int64_t)f * B.fstride + c] = 0.0;
+                if (absbuf) absbuf[T->offset[q] + (int64_t)f * B.fstride + c] = 0.0;
+            }
+    }
+    int status = OR_OK;
+    int64_t N = T->first[T->np];
+    for (int q = 0; q < T->np && !status; q++) {
+        or_mesh S = batch_view(T, q, scratch), B = batch_view(T, q, buf);
+        int64_t f0 = T->first[q];
+        or_particles pp = {T->first[q + 1] - f0, p->x + f0, p->y + f0, p->z + f0,
+                           p->m + f0, p->px + f0, p->py + f0, p->pz + f0, p->e ? p->e + f0 : NULL};
+        for (int64_t s = 0; s < pp.count; s++) {
+            int r = P->kind == KIND_FEEDBACK ? gather_feedback_one(P, &S, &pp, s, kc, gathered + f0 + s, N)
+                                             : gather_sink_one(P, &S, &pp, s, kc, gathered + f0 + s, N);
+            if (r && !status) status = r;
+        }
+        if (status) break;
+        int r = deposit_parts(P, &S, &pp, gathered + f0, N, &B, absbuf ? absbuf + T->offset[q] : NULL);
+        if (r && !status) status = r;
+    }
+    if (!status) {
+        batch_fold_arena(T, buf);
+        if (absbuf) batch_fold_arena(T, absbuf);
+    }
+    if (!status && P->kind == KIND_SINK) {
+        double *bcopy = (double *)malloc(sizeof(double) * (size_t)len);
+        if (!bcopy) status = OR_ERR_NOMEM;
+        else {
+            memcpy(bcopy, buf, sizeof(double) * (size_t)len);
+            batch_fill_ghosts(T, bcopy);
+            for (int q = 0; q < T->np && !status; q++) {
+                or_mesh S = batch_view(T, q, scratch), B = batch_view(T, q, bcopy);
+                int64_t f0 = T->first[q];
+                or_particles pp = {T->first[q + 1] - f0, p->x + f0, p->y + f0, p->z + f0,
+                                   p->m + f0, p->px + f0, p->py + f0, p->pz + f0, NULL};
+                status = return_parts(P, &S, &B, &pp, gathered + f0, N);
+            }
+            free(bcopy);
+        }
+    }
+    if (!status) {
+        int64_t tot[2] = {0, 0}, v = 0;
+        for (int q = 0; q < T->np; q++) {
+            or_mesh S = batch_view(T, q, state), B = batch_view(T, q, buf);
+            int64_t c2[2];
+            or_apply(P, &S, &B, eta_out ? eta_out + v : NULL, c2);
+            tot[0] += c2[0];
+            tot[1] += c2[1];
+            v += (int64_t)S.n[0] * S.n[1] * S.n[2];
+        }
+        if (counts) { counts[0] = tot[0]; counts[1] = tot[1]; }
+    }
+    free(scratch);
+    free(kc);
+    return status;
 }

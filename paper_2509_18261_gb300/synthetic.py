@@ -292,3 +292,141 @@ def make_workload(name, n=None, count_scale=1.0, ghost_fill=np.nan):
         fb_params=feedback_params(),
         sink_params=sink_params(),
     )
+
+
+# --- batched patches ----------------------------------------------------------
+
+# Neighbour offsets (ox, oy, oz) of a patch, in the table order: oz slowest,
+# ox fastest, the zero offset left out.
+NB_OFFSETS = tuple(
+    (ox, oy, oz) for oz in (-1, 0, 1) for oy in (-1, 0, 1) for ox in (-1, 0, 1) if (ox, oy, oz) != (0, 0, 0)
+)
+
+
+class Batch:
+    """Patches of one level tiling a periodic rectilinear super-grid.
+
+    ``edges = (sx, sy, sz)``: the x extent of every patch in super-column I is
+    sx[I] (likewise y, z), so the patches tile a periodic box of
+    (sum sx, sum sy, sum sz) cells.  Patch p = (K * P1 + J) * P0 + I.  Each
+    patch keeps [5][field_stride] doubles (padded by g, stride rounded up to 32
+    doubles) at ``offset[p]`` of one arena; ``nb[p]`` lists the patch displaced
+    by each of NB_OFFSETS (periodically).
+    """
+
+    def __init__(self, edges, g):
+        self.edges = tuple(tuple(int(v) for v in e) for e in edges)
+        self.g = int(g)
+        P0, P1, P2 = (len(e) for e in self.edges)
+        self.sgrid = (P0, P1, P2)
+        self.np = P0 * P1 * P2
+        self.dims = np.zeros((self.np, 3), dtype=np.int32)
+        self.origin = np.zeros((self.np, 3), dtype=np.int64)
+        self.nb = np.zeros((self.np, 26), dtype=np.int32)
+        starts = [np.concatenate([[0], np.cumsum(e)[:-1]]) for e in self.edges]
+        for K in range(P2):
+            for J in range(P1):
+                for I in range(P0):
+                    p = (K * P1 + J) * P0 + I
+                    self.dims[p] = (self.edges[0][I], self.edges[1][J], self.edges[2][K])
+                    self.origin[p] = (starts[0][I], starts[1][J], starts[2][K])
+                    for t, (ox, oy, oz) in enumerate(NB_OFFSETS):
+                        self.nb[p, t] = (((K + oz) % P2) * P1 + (J + oy) % P1) * P0 + (I + ox) % P0
+        self.boxes = [Box(tuple(int(v) for v in self.dims[p]), self.g) for p in range(self.np)]
+        self.fstride = np.array([b.field_stride for b in self.boxes], dtype=np.int64)
+        self.offset = np.concatenate([[0], np.cumsum(NFIELDS * self.fstride)[:-1]]).astype(np.int64)
+        self.arena_len = int(self.offset[-1] + NFIELDS * self.fstride[-1])
+        self.nvalid = np.array([b.ncells_valid for b in self.boxes], dtype=np.int64)
+        self.vbase = np.concatenate([[0], np.cumsum(self.nvalid)]).astype(np.int64)
+        self.global_n = tuple(int(sum(e)) for e in self.edges)
+
+    @property
+    def ncells_valid(self):
+        return int(self.vbase[-1])
+
+    @property
+    def ncells_padded(self):
+        return int(sum(b.ncells_padded for b in self.boxes))
+
+    def empty(self, fill=0.0):
+        a = np.empty(self.arena_len, dtype=np.float64)
+        a.fill(fill)
+        return a
+
+    def view(self, arena, p):
+        """(5, field_stride) view of patch p in an arena."""
+        o, fs = int(self.offset[p]), int(self.fstride[p])
+        return arena[o : o + NFIELDS * fs].reshape(NFIELDS, fs)
+
+    def grid(self, arena, p):
+        return self.boxes[p].grid(self.view(arena, p))
+
+    def valid(self, arena, p):
+        return self.boxes[p].valid(self.view(arena, p))
+
+    def to_global(self, arena):
+        """The valid cells of all patches assembled into (5, Nz, Ny, Nx)."""
+        Nx, Ny, Nz = self.global_n
+        out = np.empty((NFIELDS, Nz, Ny, Nx), dtype=arena.dtype)
+        for p in range(self.np):
+            (x0, y0, z0), (nx, ny, nz) = self.origin[p], self.dims[p]
+            out[:, z0 : z0 + nz, y0 : y0 + ny, x0 : x0 + nx] = self.valid(arena, p)
+        return out
+
+    def from_global(self, glob, fill=np.nan):
+        """An arena whose valid cells are taken from a (5, Nz, Ny, Nx) array."""
+        a = self.empty(fill)
+        for p in range(self.np):
+            (x0, y0, z0), (nx, ny, nz) = self.origin[p], self.dims[p]
+            self.valid(a, p)[...] = glob[:, z0 : z0 + nz, y0 : y0 + ny, x0 : x0 + nx]
+        return a
+
+
+def batch_gas_state(rng, batch, ghost_fill=np.nan):
+    """gas_state drawn patch after patch into one arena (ghosts = ghost_fill)."""
+    a = batch.empty(ghost_fill)
+    for p in range(batch.np):
+        batch.view(a, p)[...] = gas_state(rng, batch.boxes[p], ghost_fill=ghost_fill)
+    return a
+
+
+def power_law_counts(rng, npatch, xmax=20001.0):
+    """Per-patch counts n = floor(X) - 1 with density of X proportional to
+    X^-2 on [1, xmax) (inverse transform sampling)."""
+    u = rng.random(npatch)
+    x = 1.0 / (1.0 - u * (1.0 - 1.0 / xmax))
+    return np.floor(x).astype(np.int64) - 1
+
+
+def concat_particles(chunks):
+    keys = ("x", "y", "z", "m", "px", "py", "pz", "e")
+    return {k: np.ascontiguousarray(np.concatenate([c[k] for c in chunks])) for k in keys}
+
+
+def batch_particles(rng, batch, counts, kind):
+    """Particles of one kind, uniform in each patch (patch-local cell units),
+    stored patch after patch; returns (particles, first) with first[np] = total."""
+    chunks = [particles(rng, batch.boxes[p].n, int(counts[p]), kind) for p in range(batch.np)]
+    first = np.concatenate([[0], np.cumsum(counts)]).astype(np.int64)
+    return concat_particles(chunks), first
+
+
+BATCH_EDGES = (16, 24, 32, 48, 64)
+
+
+def make_batch_workload(supergrid=(8, 8, 8), edges=BATCH_EDGES, g=4, xmax=20001.0, sink_fraction=8, seed=None):
+    """Uneven AMR-like patches: per super-column edges drawn uniformly from
+    ``edges`` on each axis independently, lognormal gas, per-patch particle
+    counts from power_law_counts, each particle a sink with probability
+    1/sink_fraction, else a supernova.  Returns dict(batch, state, fb, fb_first,
+    sink, sink_first, fb_params, sink_params)."""
+    rng = np.random.default_rng(SEED_BASE + WORKLOAD_INDEX["c3_batched"] if seed is None else seed)
+    ed = tuple(tuple(int(v) for v in rng.choice(edges, size=supergrid[a])) for a in range(3))
+    batch = Batch(ed, g)
+    state = batch_gas_state(rng, batch)
+    total = power_law_counts(rng, batch.np, xmax)
+    nsk = rng.binomial(total, 1.0 / sink_fraction)
+    fb, fb_first = batch_particles(rng, batch, total - nsk, "feedback")
+    sk, sk_first = batch_particles(rng, batch, nsk, "sink")
+    return dict(batch=batch, state=state, fb=fb, fb_first=fb_first, sink=sk, sink_first=sk_first,
+                fb_params=feedback_params(), sink_params=sink_params())
