@@ -714,7 +714,17 @@ static int return_parts(const or_params *P, const or_mesh *S, const or_mesh *B, 
 /* U := U + eta Delta U^sum on every valid cell.  eta_out (optional, one value
  * per valid cell, x fastest) receives the momentum eta for feedback and the
  * common eta for sinks.  counts[0] = cells with eta < 1, counts[1] = cells
- * where no admissible lambda existed (feedback). */
+ * where no admissible lambda existed (feedback).
+ * Reading: a cell whose summed change is zero in every field receives
+ * nothing and is left as it is (eta = 1 there); the floating-point sum
+ * U + 0 would differ from U only by turning a -0 into +0. */
+static int all_zero(const double D[NF])
+{
+    for (int f = 0; f < NF; f++)
+        if (D[f] != 0.0) return 0;
+    return 1;
+}
+
 int or_apply(const or_params *P, or_mesh *S, const or_mesh *B, double *eta_out, int64_t *counts)
 {
     if (!P || !S || !B) return OR_ERR_ARG;
@@ -740,6 +750,7 @@ int or_apply(const or_params *P, or_mesh *S, const or_mesh *B, double *eta_out, 
                 }
                 if (eta[1] < 1.0) n_lim++;
                 if (eta_out) eta_out[v] = eta[1];
+                if (all_zero(D)) continue;
                 for (int f = 0; f < NF; f++) S->u[(int64_t)f * S->fstride + c] = U[f] + eta[f] * D[f];
             }
     if (counts) { counts[0] = n_lim; counts[1] = n_noroot; }
@@ -912,10 +923,11 @@ int or_cells_at(const or_params *P, const or_mesh *S, const or_particles *p, con
             double e = sink_eta(P, S->dx, U, D);
             for (int f = 0; f < NF; f++) eta[f] = e;
         }
+        int zero = all_zero(D);
         for (int f = 0; f < NF; f++) {
             out_sum[NF * t + f] = D[f];
             out_abs[NF * t + f] = A[f];
-            out_new[NF * t + f] = U[f] + eta[f] * D[f];
+            out_new[NF * t + f] = zero ? U[f] : U[f] + eta[f] * D[f];
         }
         if (out_eta) out_eta[t] = eta[1];
     }

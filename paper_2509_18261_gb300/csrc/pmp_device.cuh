@@ -383,6 +383,118 @@ constexpr int kRec = 6;
 enum { FB_MSNR = 0, FB_VSNR, FB_VX, FB_VY, FB_VZ, FB_NH, FB_RM, FB_PRAD, FB_Q, FB_E, FB_PV, FB_REGIME, FB_ROWS };
 enum { SK_RHO = 0, SK_VINF, SK_CINF, SK_MDOT, SK_RACC, SK_SUMW, SK_K, SK_NMEM, SK_ROWS };
 
+// ---------------------------------------------------------------------------
+// gathered rows from the kernel sums (shared by the single-box and batched
+// gathers; the order of every operation is the oracle's)
+// ---------------------------------------------------------------------------
+
+// Sec. 3.2.1 from the omega-weighted sums over the kernel: sw = sum omega,
+// sr = sum omega rho, sp = sum omega p.  Writes the 12 feedback rows of one
+// particle (G at its row 0, row stride gs); false if a result is not finite.
+__device__ __forceinline__ bool fb_gather_rows(const KParams &P, double sw, double sr, double sp0, double sp1,
+                                               double sp2, double m, double pe0, double pe1, double pe2, double Esn,
+                                               double *G, long long gs)
+{
+    const double V = P.V;
+    const double Vsnr = sw * V;
+    const double Mgas = sr * V;
+    const double Msnr = Mgas + m;
+    const double vc0 = (sp0 * V + pe0) / Msnr;
+    const double vc1 = (sp1 * V + pe1) / Msnr;
+    const double vc2 = (sp2 * V + pe2) / Msnr;
+    const double nH = Msnr / (P.mu_H * Vsnr);
+    const double Msf = P.A_sf * pmp_pow(nH, -0.26);
+    const double RM = Msnr / Msf;
+    double regime, prad;
+    if (RM <= P.RM_ej) {
+        regime = 0.0;
+        prad = 0.0;
+    } else if (RM <= P.RM_st) {
+        regime = 1.0;
+        prad = sqrt(((2.0 * m) * P.eps_K) * Esn);
+    } else {
+        regime = 2.0;
+        prad = P.A_p * pmp_pow(nH, -0.17);
+    }
+    const double vej2 = (pe0 * pe0 + pe1 * pe1) + pe2 * pe2;
+    const double Ekin = vej2 / (2.0 * m);
+    G[FB_MSNR * gs] = Msnr;
+    G[FB_VSNR * gs] = Vsnr;
+    G[FB_VX * gs] = vc0;
+    G[FB_VY * gs] = vc1;
+    G[FB_VZ * gs] = vc2;
+    G[FB_NH * gs] = nH;
+    G[FB_RM * gs] = RM;
+    G[FB_PRAD * gs] = prad;
+    G[FB_Q * gs] = m / Vsnr;
+    G[FB_E * gs] = (Esn + Ekin) / Vsnr;
+    G[FB_PV * gs] = prad / Vsnr;
+    G[FB_REGIME * gs] = regime;
+    return isfinite(Msnr) && isfinite(nH) && isfinite(prad) && isfinite(Ekin);
+}
+
+// Sec. 3.1.1, first half: from the kernel sums srho = sum rho, sp = sum p and
+// src = sum rho c_s over nk cells, the ambient state, r_BH, mdot_BH and
+// r_acc (cell units, clamped to [1/4, r_K / 2]).
+struct SinkAmbient {
+    double rho_inf, vinf2, c_inf, den, mdot, racc, ra2;
+};
+
+__device__ __forceinline__ SinkAmbient sink_ambient(const KParams &P, double srho, double sp0, double sp1, double sp2,
+                                                    double src, int nk, double ms, double ps0, double ps1, double ps2)
+{
+    SinkAmbient a;
+    a.rho_inf = srho / (double)nk;
+    a.c_inf = src / srho;
+    const double u0 = sp0 / srho - ps0 / ms;
+    const double u1 = sp1 / srho - ps1 / ms;
+    const double u2 = sp2 / srho - ps2 / ms;
+    a.vinf2 = (u0 * u0 + u1 * u1) + u2 * u2;
+    const double cinf2 = a.c_inf * a.c_inf;
+    a.den = a.vinf2 + cinf2;
+    const double r_bh = (P.G * ms) / a.den;
+    a.mdot = ((P.four_pi * a.rho_inf) * (r_bh * r_bh)) * sqrt(P.lam2 * cinf2 + a.vinf2);
+    double racc = r_bh / P.dx;
+    if (racc < 0.25) racc = 0.25;
+    if (racc > 0.5 * P.rK) racc = 0.5 * P.rK;
+    a.racc = racc;
+    a.ra2 = racc * racc;
+    return a;
+}
+
+// Per-axis Gaussian factor exp(-d^2 / r_acc^2) of the cell centred d away.
+__device__ __forceinline__ double sink_axis_weight(double d, double ra2) { return pmp_exp(-((d * d) / ra2)); }
+
+// Second half: K = mdot dt / (V sum w) and the 8 sink rows; false (and K = 0)
+// if a result is not finite.
+__device__ __forceinline__ bool sink_gather_rows(const KParams &P, const SinkAmbient &a, double sumw, int nk, double *G,
+                                                 long long gs)
+{
+    double K = ((a.mdot * P.dt) / P.V) / sumw;
+    const bool ok = (a.den > 0.0) && isfinite(a.mdot) && isfinite(K);
+    if (!ok) K = 0.0;
+    G[SK_RHO * gs] = a.rho_inf;
+    G[SK_VINF * gs] = sqrt(a.vinf2);
+    G[SK_CINF * gs] = a.c_inf;
+    G[SK_MDOT * gs] = a.mdot;
+    G[SK_RACC * gs] = a.racc;
+    G[SK_SUMW * gs] = sumw;
+    G[SK_K * gs] = K;
+    G[SK_NMEM * gs] = (double)nk;
+    return ok;
+}
+
+// True when every field of D is +0 or -0 (integer test; no FP64 instruction).
+// A cell whose summed change is zero in every field receives nothing in
+// Step 5 and is left as it is.
+__device__ __forceinline__ bool all_zero(const double D[NF])
+{
+    unsigned long long acc = 0;
+#pragma unroll
+    for (int f = 0; f < NF; ++f) acc |= (unsigned long long)__double_as_longlong(D[f]) << 1;
+    return acc == 0;
+}
+
 // Position check: 0 <= x < n on each axis (NaN fails).
 __device__ __forceinline__ int position_status(const Box &B, double x, double y, double z)
 {

@@ -117,17 +117,20 @@ __global__ void __launch_bounds__(256) k_apply_fb_fast(Box S, double *__restrict
         const long long cs = S.at(i, j, k), cb = B.at(i, j, k);
         double U[NF], D[NF];
 #pragma unroll
-        for (int f = 0; f < NF; ++f) {
-            U[f] = u[(long long)f * S.fs + cs];
-            D[f] = __ldg(b + (long long)f * B.fs + cb);
-        }
-        const bool nodp = D[1] == 0.0 && D[2] == 0.0 && D[3] == 0.0;
-        if (nodp || sn_lambda_holds_f32(U, D)) {
+        for (int f = 0; f < NF; ++f) D[f] = __ldg(b + (long long)f * B.fs + cb);
+        if (all_zero(D)) {
             if (eta_out) eta_out[v] = 1.0;
-#pragma unroll
-            for (int f = 0; f < NF; ++f) u[(long long)f * S.fs + cs] = U[f] + D[f];
         } else {
-            slow = true;
+#pragma unroll
+            for (int f = 0; f < NF; ++f) U[f] = u[(long long)f * S.fs + cs];
+            const bool nodp = D[1] == 0.0 && D[2] == 0.0 && D[3] == 0.0;
+            if (nodp || sn_lambda_holds_f32(U, D)) {
+                if (eta_out) eta_out[v] = 1.0;
+#pragma unroll
+                for (int f = 0; f < NF; ++f) u[(long long)f * S.fs + cs] = U[f] + D[f];
+            } else {
+                slow = true;
+            }
         }
     }
     const unsigned m = __ballot_sync(0xffffffffu, slow);
@@ -198,11 +201,13 @@ __global__ void __launch_bounds__(256) k_apply_fb(Box S, double *__restrict__ u,
         const double l = sn_lambda(U, D, nr);
         lim = l < 1.0;
         if (eta_out) eta_out[v] = l;
-        u[cs] = U[0] + D[0];
-        u[S.fs + cs] = U[1] + l * D[1];
-        u[2 * S.fs + cs] = U[2] + l * D[2];
-        u[3 * S.fs + cs] = U[3] + l * D[3];
-        u[4 * S.fs + cs] = U[4] + D[4];
+        if (!all_zero(D)) {
+            u[cs] = U[0] + D[0];
+            u[S.fs + cs] = U[1] + l * D[1];
+            u[2 * S.fs + cs] = U[2] + l * D[2];
+            u[3 * S.fs + cs] = U[3] + l * D[3];
+            u[4 * S.fs + cs] = U[4] + D[4];
+        }
     }
     const unsigned m1 = __ballot_sync(0xffffffffu, lim), m2 = __ballot_sync(0xffffffffu, nr);
     if ((threadIdx.x & 31) == 0) {
@@ -284,10 +289,13 @@ __global__ void __launch_bounds__(256) k_apply_sink(Box S, double *__restrict__ 
         const double e = __ldg(eta + v);
         lim = e < 1.0;
         if (eta_out) eta_out[v] = e;
+        double D[NF];
 #pragma unroll
-        for (int f = 0; f < NF; ++f) {
-            const double d = __ldg(b + (long long)f * B.fs + cb);
-            u[(long long)f * S.fs + cs] = u[(long long)f * S.fs + cs] + (e == 1.0 ? d : e * d);
+        for (int f = 0; f < NF; ++f) D[f] = __ldg(b + (long long)f * B.fs + cb);
+        if (!all_zero(D)) {
+#pragma unroll
+            for (int f = 0; f < NF; ++f)
+                u[(long long)f * S.fs + cs] = u[(long long)f * S.fs + cs] + (e == 1.0 ? D[f] : e * D[f]);
         }
     }
     const unsigned m1 = __ballot_sync(0xffffffffu, lim);

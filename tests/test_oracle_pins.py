@@ -549,3 +549,20 @@ def test_state_ghost_cells_are_never_read(orc):
     orc.cycle(w["sink_params"], w["box"], st, w["sink"])
     assert np.all(np.isfinite(w["box"].valid(st)))
     assert np.all(np.isfinite(w["sink"]["m"]))
+
+
+def test_cells_without_change_keep_their_bits(orc):
+    """Step 5 adds eta * Delta U^sum: a cell whose summed change is zero in
+    every field is left exactly as it was (a -0 momentum stays -0)."""
+    box = syn.Box((8, 8, 8), 2)
+    state = syn.uniform_gas(box, 1.0)
+    v = box.valid(state)
+    v[1] = -0.0
+    v[4] = 1.0
+    one = {"x": np.array([1.5]), "y": np.array([1.5]), "z": np.array([1.5]), "m": np.array([0.01]),
+           "px": np.array([0.0]), "py": np.array([0.0]), "pz": np.array([0.0]), "e": np.array([1.0])}
+    s = state.copy()
+    orc.cycle(syn.feedback_params(r_K=1.0), box, s, one)
+    far = box.valid(s)[:, 6, 6, 6]
+    assert np.signbit(far[1]) and far[1] == 0.0
+    assert box.valid(s)[0, 1, 1, 1] > 1.0
