@@ -12,8 +12,9 @@
  * the caller (for example the storage of a torch tensor), except where a
  * comment says "host".  The library borrows device pointers only for the work
  * it enqueues and never frees them.  It allocates device memory only in
- * pmp_create (a few hundred bytes for status words) and frees it in
- * pmp_destroy.  Scratch memory of a pass is the caller's: pmp_workspace_size
+ * pmp_create (a few hundred bytes for status words), pmp_batch_create and
+ * pmp_batch_set_particles (a batch's tables), and frees it in pmp_destroy /
+ * pmp_batch_destroy.  Scratch memory of a pass is the caller's: pmp_workspace_size
  * gives its size, pmp_gather writes the pass's plan into it (each particle's
  * kernel cells, found once), and pmp_deposit, pmp_apply_limited and
  * pmp_backward read it.
@@ -246,6 +247,116 @@ typedef struct {
 
 pmp_status pmp_timing_enable(pmp_ctx *ctx, int32_t on);
 pmp_status pmp_timing_read(pmp_ctx *ctx, pmp_kernel_time *out, int32_t max, int32_t *n);
+
+/* ------------------------------------------------------------------------ */
+/* Batched form: one pass over many uneven patches of one level             */
+/* ------------------------------------------------------------------------ */
+
+/* The patches of a batch tile a periodic domain as a rectilinear grid (every
+ * patch in a row of the grid has the row's extent across it), like the boxes
+ * of one AMR level in the paper's distributed setting (Sec. 2.2, Step 2).
+ * Each patch keeps its state and buffer, laid out like a pmp_mesh with the
+ * batch's ng, at `offset` of two caller-owned device arenas.  Its ghost cells
+ * are never filled by the caller: the state's are read from the neighbour
+ * patches, and the buffer's are summed into the neighbours' valid cells.
+ *
+ * neighbour[t]: the patch displaced by the t-th offset o = (ox, oy, oz) of
+ * {-1,0,1}^3 without (0,0,0), listed with oz slowest and ox fastest.  A
+ * ghost cell (i, j, k) of patch p is the valid cell of q = neighbour[o] at
+ * i + n_q (i < 0), i - n_p (i >= n_p), i (otherwise), likewise j and k, with
+ * o_a the sign of each case.  The summed buffer of a valid cell is
+ * ((B_c + B_img1) + B_img2) + ... over its ghost images in lexicographic
+ * order of the image offset (oz, oy, ox) (App. A.2); the image at offset o
+ * lies in neighbour[-o]. */
+typedef struct pmp_batch pmp_batch;
+
+typedef struct {
+    int32_t n[3];          /* valid cells per axis, >= ng */
+    int32_t neighbour[26]; /* patch index per offset, see above */
+    int64_t offset;        /* arena index of (field 0, padded cell 0) */
+    int64_t field_stride;  /* doubles between fields, >= padded cell count */
+} pmp_patch;
+
+/* How pmp_cycle_batched runs a pass.
+ * PERSISTENT: one cooperative launch of (SMs x resident blocks) blocks that
+ *   take work items from a queue per phase, with a grid-wide barrier between
+ *   phases whose waits end with PMP_ERR_TIMEOUT after a few seconds.
+ * PER_PATCH:  every phase launched once per patch (the plain form).
+ * GRAPH:      PERSISTENT captured once into a CUDA graph (per set of argument
+ *   pointers) and replayed; the first call captures on the context's stream,
+ *   which must not be capturing already. */
+typedef enum { PMP_BATCH_PERSISTENT = 0, PMP_BATCH_PER_PATCH = 1, PMP_BATCH_GRAPH = 2 } pmp_batch_launch;
+
+/* Step-1 strategy of a patch.
+ * OWNER_CUBE, OWNER_ROWS: each buffer cell of the patch (ghosts included) is
+ *   written once, as the sum of the patch's particles' contributions in
+ *   particle-index order; tiles of 8 x 8 x 8 cells, or of full padded rows x
+ *   8 x 4.  Deterministic: bit-for-bit the sum of the sorted mode.
+ * ATOMIC: the patch's buffer is zeroed, then FP64 atomic additions. */
+typedef enum {
+    PMP_STRATEGY_OWNER_CUBE = 0,
+    PMP_STRATEGY_OWNER_ROWS = 1,
+    PMP_STRATEGY_ATOMIC = 2
+} pmp_strategy;
+
+/* Autotuner bins: 4 patch-size bins (padded cells < 16384, < 65536,
+ * < 262144, larger) x 5 occupancy bins (no particles; particles per 1000
+ * valid cells < 1, < 10, < 100, larger); bin = size * 5 + occupancy. */
+#define PMP_BATCH_BINS 20
+
+/* Creates a batch of n_patches patches (host array `patches`) with ng ghost
+ * cells and cell size dx for the context's interaction kind, in arenas of
+ * arena_len doubles.  Checks: ng >= ceil(r_K) (else PMP_ERR_GHOST_TOO_THIN);
+ * every n >= ng; every patch inside the arena and disjoint from the others;
+ * neighbour entries in range, of matching extent across their offset, and
+ * reciprocal (the neighbour at -o of the neighbour at o is the patch).
+ * Allocates the batch's device tables; synchronous.  Particle ranges start
+ * empty; the strategy starts as OWNER_CUBE for every patch. */
+pmp_status pmp_batch_create(pmp_ctx *ctx, const pmp_patch *patches, int32_t n_patches, int32_t ng, double dx,
+                            int64_t arena_len, pmp_batch **out);
+
+/* Particle ranges: host array first[n_patches + 1], first[0] = 0,
+ * non-decreasing; patch p owns particles [first[p], first[p + 1]) of the
+ * particle arrays handed to pmp_cycle_batched, positions in that patch's
+ * cell units (0 <= x < n[0], likewise y, z).  Synchronises the context's
+ * stream; (re)allocates the per-particle tables. */
+pmp_status pmp_batch_set_particles(pmp_batch *batch, const int64_t *first);
+
+/* Sets one pmp_strategy for every patch (synchronises the stream). */
+pmp_status pmp_batch_set_strategy(pmp_batch *batch, int32_t strategy);
+
+/* Copies the strategy of every patch into per_patch (host, n_patches). */
+pmp_status pmp_batch_strategies(const pmp_batch *batch, int32_t *per_patch);
+
+/* Autotuner: for each bin holding patches, times the Step-1 deposit of those
+ * patches with every allowed strategy (OWNER_CUBE and OWNER_ROWS; ATOMIC too
+ * unless `deterministic`), best of `reps` runs, and keeps the fastest for the
+ * bin.  Runs the gather first; writes `gathered` and garbage into `buffer`;
+ * leaves `state` and the particles unchanged.  bin_choice (host, optional,
+ * PMP_BATCH_BINS entries) receives the chosen strategy per bin, -1 for empty
+ * bins.  Synchronous. */
+pmp_status pmp_batch_autotune(pmp_batch *batch, const double *state, double *buffer, pmp_particles *particles,
+                              double *gathered, int32_t deterministic, int32_t reps, int32_t *bin_choice);
+
+/* One pass (Steps 1-5 of Sec. 2.2; Step 4 for sinks) over every patch of the
+ * batch: gather, deposit into `buffer` (every padded cell of every patch is
+ * written), ghost summation across patches, limiter and update of the valid
+ * cells of `state`.  Afterwards `buffer` holds the deposits in ghost cells
+ * and the summed Delta U in valid cells, as the single-box calls leave it.
+ * particles: count = first[n_patches]; gathered: [rows][count]; eta_out
+ * (optional) one FP64 per valid cell, patch after patch, x fastest.  The
+ * limiter counters (pmp_limiter_counts) and device errors (pmp_get_error)
+ * are the context's.  `launch` is a pmp_batch_launch.  Enqueues on the
+ * context's stream (GRAPH: captures on the first call). */
+pmp_status pmp_cycle_batched(pmp_batch *batch, double *state, double *buffer, pmp_particles *particles,
+                             double *gathered, double *eta_out, int32_t launch);
+
+/* Persistent grid size (blocks) and item counts (host int64[3]: zeroing,
+ * deposit, apply items) of the batch's current plan. */
+pmp_status pmp_batch_info(const pmp_batch *batch, int32_t *grid, int64_t *items);
+
+/* Frees a batch's device tables (after its work has finished). */
+void pmp_batch_destroy(pmp_batch *batch);
 
 /* Size of the fixed device scratch of pmp_deposit_noalloc: 64 MiB, held on
  * every GPU that loads the library until the process exits. */

@@ -11,62 +11,7 @@
 #include "pmp.h"
 #include "pmp_device.cuh"
 #include "pmp_launch.h"
-
-struct pmp_ctx {
-    pmp_params p;
-    cudaStream_t stream;
-    pmp::DevStatus *st;  // device
-    int device;
-    // the plan recorded by the last pmp_gather
-    const void *plan_ws;
-    long long plan_n;
-    long long plan_nvalid;
-    int plan_mode;
-    // per-kernel CUDA-event timing (pmp_timing_enable)
-    bool timing;
-    struct Mark {
-        const char *name;
-        cudaEvent_t a, b;
-    };
-    std::vector<Mark> marks;
-    std::vector<cudaEvent_t> pool;
-};
-
-namespace {
-
-cudaEvent_t take_event(pmp_ctx *c)
-{
-    cudaEvent_t e;
-    if (!c->pool.empty()) {
-        e = c->pool.back();
-        c->pool.pop_back();
-    } else if (cudaEventCreate(&e) != cudaSuccess) {
-        e = nullptr;
-    }
-    return e;
-}
-
-// Brackets the kernel launched in its scope with two events on the context's
-// stream when timing is on.
-struct Timed {
-    pmp_ctx *c;
-    size_t idx;
-    Timed(pmp_ctx *ctx, const char *name) : c(ctx), idx((size_t)-1)
-    {
-        if (!c->timing) return;
-        pmp_ctx::Mark m{name, take_event(c), take_event(c)};
-        if (!m.a || !m.b) return;
-        cudaEventRecord(m.a, c->stream);
-        c->marks.push_back(m);
-        idx = c->marks.size() - 1;
-    }
-    ~Timed()
-    {
-        if (idx != (size_t)-1) cudaEventRecord(c->marks[idx].b, c->stream);
-    }
-};
-
-}  // namespace
+#include "pmp_ctx.h"
 
 namespace {
 
@@ -75,67 +20,6 @@ using pmp::KParams;
 using pmp::Parts;
 
 bool finite(double v) { return std::isfinite(v); }
-
-pmp_status check_params(const pmp_params *p)
-{
-    if (!p) return PMP_ERR_ARG;
-    if (p->kind != PMP_KIND_FEEDBACK && p->kind != PMP_KIND_SINK) return PMP_ERR_ARG;
-    if (!finite(p->r_K) || p->r_K < 1.0 || p->r_K > (double)pmp::kMaxR) return PMP_ERR_ARG;
-    if (!finite(p->gamma) || !(p->gamma > 1.0)) return PMP_ERR_ARG;
-    if (p->kind == PMP_KIND_FEEDBACK) {
-        if (p->subsample < 1 || p->subsample > pmp::kMaxS) return PMP_ERR_ARG;
-        if (!finite(p->A_sf) || !(p->A_sf > 0.0) || !finite(p->A_p) || p->A_p < 0.0) return PMP_ERR_ARG;
-        if (!finite(p->mu_H) || !(p->mu_H > 0.0) || !finite(p->eps_K) || p->eps_K < 0.0) return PMP_ERR_ARG;
-        if (!finite(p->RM_ej) || !finite(p->RM_st) || p->RM_ej > p->RM_st) return PMP_ERR_ARG;
-    } else {
-        if (!finite(p->G) || !(p->G > 0.0) || !finite(p->dt) || p->dt < 0.0) return PMP_ERR_ARG;
-        if (!finite(p->lambda_bh) || p->lambda_bh < 0.0 || !finite(p->J) || !(p->J > 0.0)) return PMP_ERR_ARG;
-        if (!finite(p->cap) || !(p->cap > 0.0) || p->cap > 1.0 || !finite(p->rho_min) || p->rho_min < 0.0)
-            return PMP_ERR_ARG;
-    }
-    return PMP_OK;
-}
-
-// Derived constants, each in the order the formulas state it.
-KParams make_kparams(const pmp_params &p, double dx)
-{
-    KParams k;
-    std::memset(&k, 0, sizeof(k));
-    k.rK = p.r_K;
-    k.r2 = p.r_K * p.r_K;
-    k.dt = p.dt;
-    k.G = p.G;
-    k.gg = p.gamma * (p.gamma - 1.0);
-    k.lam2 = p.lambda_bh * p.lambda_bh;
-    k.ctr = p.kind == PMP_KIND_SINK ? ((p.J * p.J) * pmp::kPi) / (p.G * (dx * dx)) : 0.0;
-    k.cap = p.cap;
-    k.rho_min = p.rho_min;
-    k.A_sf = p.A_sf;
-    k.A_p = p.A_p;
-    k.mu_H = p.mu_H;
-    k.RM_ej = p.RM_ej;
-    k.RM_st = p.RM_st;
-    k.eps_K = p.eps_K;
-    k.V = (dx * dx) * dx;
-    k.dx = dx;
-    k.four_pi = 4.0 * pmp::kPi;
-    k.S = p.kind == PMP_KIND_FEEDBACK ? p.subsample : 1;
-    k.S3 = k.S * k.S * k.S;
-    for (int a = 0; a < 8; ++a) k.frac[a] = a < k.S ? ((double)a + 0.5) / (double)k.S : 0.0;
-    k.Slog = -1;
-    for (int b = 0; b < 4; ++b)
-        if (k.S == (1 << b)) k.Slog = b;
-    for (int a = 0; a < 8; ++a) k.fracf[a] = (float)k.frac[a];
-    // FP32 band r2 (1 -/+ 2^-14), rounded outward
-    const double lo = k.r2 * (1.0 - 6.103515625e-05), hi = k.r2 * (1.0 + 6.103515625e-05);
-    k.band_lo = (float)lo;
-    if ((double)k.band_lo > lo) k.band_lo = std::nextafter(k.band_lo, 0.0f);
-    k.band_hi = (float)hi;
-    if ((double)k.band_hi < hi) k.band_hi = std::nextafter(k.band_hi, 3.0e38f);
-    k.R = (int)std::ceil(p.r_K);
-    k.kind = p.kind;
-    return k;
-}
 
 pmp_status make_box(const pmp_mesh *m, Box *b)
 {
@@ -325,6 +209,76 @@ pmp_status check_workspace(const Layout &L, const void *ws, size_t bytes)
 long long nvalid_of(const pmp_mesh *m) { return (long long)m->n[0] * m->n[1] * m->n[2]; }
 
 }  // namespace
+
+namespace pmp {
+
+pmp_status check_params(const pmp_params *p)
+{
+    if (!p) return PMP_ERR_ARG;
+    if (p->kind != PMP_KIND_FEEDBACK && p->kind != PMP_KIND_SINK) return PMP_ERR_ARG;
+    if (!std::isfinite(p->r_K) || p->r_K < 1.0 || p->r_K > (double)pmp::kMaxR) return PMP_ERR_ARG;
+    if (!std::isfinite(p->gamma) || !(p->gamma > 1.0)) return PMP_ERR_ARG;
+    if (p->kind == PMP_KIND_FEEDBACK) {
+        if (p->subsample < 1 || p->subsample > pmp::kMaxS) return PMP_ERR_ARG;
+        if (!std::isfinite(p->A_sf) || !(p->A_sf > 0.0) || !std::isfinite(p->A_p) || p->A_p < 0.0) return PMP_ERR_ARG;
+        if (!std::isfinite(p->mu_H) || !(p->mu_H > 0.0) || !std::isfinite(p->eps_K) || p->eps_K < 0.0) return PMP_ERR_ARG;
+        if (!std::isfinite(p->RM_ej) || !std::isfinite(p->RM_st) || p->RM_ej > p->RM_st) return PMP_ERR_ARG;
+    } else {
+        if (!std::isfinite(p->G) || !(p->G > 0.0) || !std::isfinite(p->dt) || p->dt < 0.0) return PMP_ERR_ARG;
+        if (!std::isfinite(p->lambda_bh) || p->lambda_bh < 0.0 || !std::isfinite(p->J) || !(p->J > 0.0)) return PMP_ERR_ARG;
+        if (!std::isfinite(p->cap) || !(p->cap > 0.0) || p->cap > 1.0 || !std::isfinite(p->rho_min) || p->rho_min < 0.0)
+            return PMP_ERR_ARG;
+    }
+    return PMP_OK;
+}
+
+// Derived constants, each in the order the formulas state it.
+KParams make_kparams(const pmp_params &p, double dx)
+{
+    KParams k;
+    std::memset(&k, 0, sizeof(k));
+    k.rK = p.r_K;
+    k.r2 = p.r_K * p.r_K;
+    k.dt = p.dt;
+    k.G = p.G;
+    k.gg = p.gamma * (p.gamma - 1.0);
+    k.lam2 = p.lambda_bh * p.lambda_bh;
+    k.ctr = p.kind == PMP_KIND_SINK ? ((p.J * p.J) * pmp::kPi) / (p.G * (dx * dx)) : 0.0;
+    k.cap = p.cap;
+    k.rho_min = p.rho_min;
+    k.A_sf = p.A_sf;
+    k.A_p = p.A_p;
+    k.mu_H = p.mu_H;
+    k.RM_ej = p.RM_ej;
+    k.RM_st = p.RM_st;
+    k.eps_K = p.eps_K;
+    k.V = (dx * dx) * dx;
+    k.dx = dx;
+    k.four_pi = 4.0 * pmp::kPi;
+    k.S = p.kind == PMP_KIND_FEEDBACK ? p.subsample : 1;
+    k.S3 = k.S * k.S * k.S;
+    for (int a = 0; a < 8; ++a) k.frac[a] = a < k.S ? ((double)a + 0.5) / (double)k.S : 0.0;
+    k.Slog = -1;
+    for (int b = 0; b < 4; ++b)
+        if (k.S == (1 << b)) k.Slog = b;
+    for (int a = 0; a < 8; ++a) k.fracf[a] = (float)k.frac[a];
+    // FP32 band r2 (1 -/+ 2^-14), rounded outward
+    const double lo = k.r2 * (1.0 - 6.103515625e-05), hi = k.r2 * (1.0 + 6.103515625e-05);
+    k.band_lo = (float)lo;
+    if ((double)k.band_lo > lo) k.band_lo = std::nextafter(k.band_lo, 0.0f);
+    k.band_hi = (float)hi;
+    if ((double)k.band_hi < hi) k.band_hi = std::nextafter(k.band_hi, 3.0e38f);
+    k.R = (int)std::ceil(p.r_K);
+    k.kind = p.kind;
+    return k;
+}
+
+}  // namespace pmp
+
+using pmp::check_params;
+using pmp::make_kparams;
+using pmp_detail::Timed;
+using pmp_detail::take_event;
 
 extern "C" {
 

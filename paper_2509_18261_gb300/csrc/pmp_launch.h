@@ -5,6 +5,17 @@
 
 #include "pmp_device.cuh"
 
+// Calls CALL with the compile-time constant RR = R_ (the stencil half-width).
+#define PMP_DISPATCH_R(R_, CALL)                         \
+    switch (R_) {                                        \
+    case 1: { constexpr int RR = 1; CALL; } break;       \
+    case 2: { constexpr int RR = 2; CALL; } break;       \
+    case 3: { constexpr int RR = 3; CALL; } break;       \
+    case 4: { constexpr int RR = 4; CALL; } break;       \
+    case 5: { constexpr int RR = 5; CALL; } break;       \
+    default: { constexpr int RR = 6; CALL; } break;      \
+    }
+
 namespace pmp {
 
 // Device pointers into a pass's workspace (the plan and the per-cell arrays).

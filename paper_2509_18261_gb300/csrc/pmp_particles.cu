@@ -281,42 +281,7 @@ __global__ void __launch_bounds__(128) k_gather_fb(KParams P, Box S, const doubl
             sp2 = sp2 + w * U[3];
         }
     }
-    const double V = P.V;
-    const double Vsnr = sw * V;
-    const double Mgas = sr * V;
-    const double Msnr = Mgas + m;
-    const double vc0 = (sp0 * V + pe0) / Msnr;
-    const double vc1 = (sp1 * V + pe1) / Msnr;
-    const double vc2 = (sp2 * V + pe2) / Msnr;
-    const double nH = Msnr / (P.mu_H * Vsnr);
-    const double Msf = P.A_sf * pmp_pow(nH, -0.26);
-    const double RM = Msnr / Msf;
-    double regime, prad;
-    if (RM <= P.RM_ej) {
-        regime = 0.0;
-        prad = 0.0;
-    } else if (RM <= P.RM_st) {
-        regime = 1.0;
-        prad = sqrt(((2.0 * m) * P.eps_K) * Esn);
-    } else {
-        regime = 2.0;
-        prad = P.A_p * pmp_pow(nH, -0.17);
-    }
-    const double vej2 = (pe0 * pe0 + pe1 * pe1) + pe2 * pe2;
-    const double Ekin = vej2 / (2.0 * m);
-    G[FB_MSNR * gs + s] = Msnr;
-    G[FB_VSNR * gs + s] = Vsnr;
-    G[FB_VX * gs + s] = vc0;
-    G[FB_VY * gs + s] = vc1;
-    G[FB_VZ * gs + s] = vc2;
-    G[FB_NH * gs + s] = nH;
-    G[FB_RM * gs + s] = RM;
-    G[FB_PRAD * gs + s] = prad;
-    G[FB_Q * gs + s] = m / Vsnr;
-    G[FB_E * gs + s] = (Esn + Ekin) / Vsnr;
-    G[FB_PV * gs + s] = prad / Vsnr;
-    G[FB_REGIME * gs + s] = regime;
-    if (!isfinite(Msnr) || !isfinite(nH) || !isfinite(prad) || !isfinite(Ekin)) report(st, PMP_ERR_NONFINITE, s);
+    if (!fb_gather_rows(P, sw, sr, sp0, sp1, sp2, m, pe0, pe1, pe2, Esn, G + s, gs)) report(st, PMP_ERR_NONFINITE, s);
 }
 
 // Sink gather.  Writes the particle's per-axis Gaussian factors
@@ -354,50 +319,22 @@ __global__ void __launch_bounds__(128) k_gather_sink(KParams P, Box S, const dou
         src = src + g2.x;
     }
     const int nk = (int)nc;
-    const double rho_inf = srho / (double)nk;
-    const double c_inf = src / srho;
-    const double u0 = sp0 / srho - ps0 / ms;
-    const double u1 = sp1 / srho - ps1 / ms;
-    const double u2 = sp2 / srho - ps2 / ms;
-    const double vinf2 = (u0 * u0 + u1 * u1) + u2 * u2;
-    const double cinf2 = c_inf * c_inf;
-    const double den = vinf2 + cinf2;
-    const double r_bh = (P.G * ms) / den;
-    const double mdot = ((P.four_pi * rho_inf) * (r_bh * r_bh)) * sqrt(P.lam2 * cinf2 + vinf2);
-    double racc = r_bh / P.dx;
-    if (racc < 0.25) racc = 0.25;
-    if (racc > 0.5 * P.rK) racc = 0.5 * P.rK;
-    const double ra2 = racc * racc;
+    const SinkAmbient am = sink_ambient(P, srho, sp0, sp1, sp2, src, nk, ms, ps0, ps1, ps2);
+    const double ra2 = am.ra2;
     const int hx = (int)floor(x), hy = (int)floor(y), hz = (int)floor(z);
     double *ws = pl.wts + s * (3 * W);
 #pragma unroll
     for (int o = 0; o < W; ++o) {
-        const double ax = ((double)(hx + o - R) + 0.5) - x;
-        const double ay = ((double)(hy + o - R) + 0.5) - y;
-        const double az = ((double)(hz + o - R) + 0.5) - z;
-        ws[o] = pmp_exp(-((ax * ax) / ra2));
-        ws[W + o] = pmp_exp(-((ay * ay) / ra2));
-        ws[2 * W + o] = pmp_exp(-((az * az) / ra2));
+        ws[o] = sink_axis_weight(((double)(hx + o - R) + 0.5) - x, ra2);
+        ws[W + o] = sink_axis_weight(((double)(hy + o - R) + 0.5) - y, ra2);
+        ws[2 * W + o] = sink_axis_weight(((double)(hz + o - R) + 0.5) - z, ra2);
     }
     double sumw = 0.0;
     for (unsigned q = 0; q < nc; ++q) {
         const PairCell c = unpack_pair(pl.slots[b0 + q], P.R);
         sumw = sumw + (ws[c.i - hx + R] * ws[W + c.j - hy + R]) * ws[2 * W + c.k - hz + R];
     }
-    double K = ((mdot * P.dt) / P.V) / sumw;
-    const bool ok = (den > 0.0) && isfinite(mdot) && isfinite(K);
-    if (!ok) {
-        K = 0.0;
-        report(st, PMP_ERR_NONFINITE, s);
-    }
-    G[SK_RHO * gs + s] = rho_inf;
-    G[SK_VINF * gs + s] = sqrt(vinf2);
-    G[SK_CINF * gs + s] = c_inf;
-    G[SK_MDOT * gs + s] = mdot;
-    G[SK_RACC * gs + s] = racc;
-    G[SK_SUMW * gs + s] = sumw;
-    G[SK_K * gs + s] = K;
-    G[SK_NMEM * gs + s] = (double)nk;
+    if (!sink_gather_rows(P, am, sumw, nk, G + s, gs)) report(st, PMP_ERR_NONFINITE, s);
 }
 
 // ---------------------------------------------------------------------------
@@ -660,16 +597,6 @@ __global__ void __launch_bounds__(128) k_return_sinks(KParams P, Box S, Parts p,
 // ---------------------------------------------------------------------------
 
 static inline unsigned blocks_for(long long n, int t) { return (unsigned)((n + t - 1) / t); }
-
-#define PMP_DISPATCH_R(R_, CALL)                         \
-    switch (R_) {                                        \
-    case 1: { constexpr int RR = 1; CALL; } break;       \
-    case 2: { constexpr int RR = 2; CALL; } break;       \
-    case 3: { constexpr int RR = 3; CALL; } break;       \
-    case 4: { constexpr int RR = 4; CALL; } break;       \
-    case 5: { constexpr int RR = 5; CALL; } break;       \
-    default: { constexpr int RR = 6; CALL; } break;      \
-    }
 
 void launch_prologue(const Box &S, const Parts &p, unsigned *keys, unsigned *ids, const PlanPtrs &pl, DevStatus *st,
                      cudaStream_t stream)

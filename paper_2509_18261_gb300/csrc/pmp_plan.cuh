@@ -76,14 +76,14 @@ __device__ __forceinline__ long long vidx(const Box &B, int i, int j, int k)
 }
 
 // Exact FP64 membership test of a cell centre, in the canonical order.
-__device__ __noinline__ bool centre_inside_exact(double r2, int ci, int cj, int ck, double x, double y, double z)
+static __device__ __noinline__ bool centre_inside_exact(double r2, int ci, int cj, int ck, double x, double y, double z)
 {
     const double d0 = ((double)ci + 0.5) - x, d1 = ((double)cj + 0.5) - y, d2 = ((double)ck + 0.5) - z;
     return (d0 * d0 + d1 * d1) + d2 * d2 < r2;
 }
 
 // Exact FP64 sub-point test, in the canonical order.
-__device__ __noinline__ bool subpoint_inside_exact(double r2, double fa, double fb, double fc, int ci, int cj, int ck,
+static __device__ __noinline__ bool subpoint_inside_exact(double r2, double fa, double fb, double fc, int ci, int cj, int ck,
                                                    double x, double y, double z)
 {
     const double sx = ((double)ci + fa) - x;

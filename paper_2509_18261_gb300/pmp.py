@@ -30,7 +30,14 @@ EXPORTS = [
     "pmp_create", "pmp_destroy", "pmp_set_stream", "pmp_gathered_rows", "pmp_workspace_size", "pmp_zero_buffer",
     "pmp_gather", "pmp_deposit", "pmp_fold_ghosts", "pmp_apply_limited", "pmp_backward", "pmp_get_error",
     "pmp_limiter_counts", "pmp_timing_enable", "pmp_timing_read", "pmp_deposit_noalloc",
+    "pmp_batch_create", "pmp_batch_set_particles", "pmp_batch_set_strategy", "pmp_batch_strategies",
+    "pmp_batch_autotune", "pmp_cycle_batched", "pmp_batch_info", "pmp_batch_destroy",
 ]
+PERSISTENT, PER_PATCH, GRAPH = 0, 1, 2
+LAUNCHES = {"persistent": PERSISTENT, "per_patch": PER_PATCH, "graph": GRAPH}
+OWNER_CUBE, OWNER_ROWS, STRAT_ATOMIC = 0, 1, 2
+STRATEGIES = {"owner_cube": OWNER_CUBE, "owner_rows": OWNER_ROWS, "atomic": STRAT_ATOMIC}
+BATCH_BINS = 20
 
 
 class PMPError(RuntimeError):
@@ -60,6 +67,11 @@ class _Mesh(ctypes.Structure):
 
 class _KernelTime(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 24), ("launches", ctypes.c_int64), ("ms", ctypes.c_double)]
+
+
+class _Patch(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32 * 3), ("neighbour", ctypes.c_int32 * 26), ("offset", ctypes.c_int64),
+                ("field_stride", ctypes.c_int64)]
 
 
 class _Particles(ctypes.Structure):
@@ -100,6 +112,14 @@ def load():
         "pmp_timing_enable": ([vp, i32], i32),
         "pmp_timing_read": ([vp, ctypes.POINTER(_KernelTime), i32, ctypes.POINTER(i32)], i32),
         "pmp_deposit_noalloc": ([P, M, Pa, vp, M, vp], i32),
+        "pmp_batch_create": ([vp, ctypes.POINTER(_Patch), i32, i32, ctypes.c_double, i64, ctypes.POINTER(vp)], i32),
+        "pmp_batch_set_particles": ([vp, ctypes.POINTER(i64)], i32),
+        "pmp_batch_set_strategy": ([vp, i32], i32),
+        "pmp_batch_strategies": ([vp, ctypes.POINTER(i32)], i32),
+        "pmp_batch_autotune": ([vp, vp, vp, Pa, vp, i32, i32, ctypes.POINTER(i32)], i32),
+        "pmp_cycle_batched": ([vp, vp, vp, Pa, vp, vp, i32], i32),
+        "pmp_batch_info": ([vp, ctypes.POINTER(i32), ctypes.POINTER(i64)], i32),
+        "pmp_batch_destroy": ([vp], None),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -293,6 +313,85 @@ def pmp_timing_read(ctx):
     return {buf[i].name.decode(): (buf[i].launches, buf[i].ms) for i in range(min(n.value, 64))}
 
 
+class BatchHandle:
+    """An opaque pmp_batch (pmp_batch_create / pmp_batch_destroy).
+
+    ``dims`` (np, 3), ``nb`` (np, 26), ``offset`` and ``field_stride`` (np)
+    describe the patches (host arrays); ``ctx`` fixes the interaction kind."""
+
+    def __init__(self, ctx, dims, nb, offset, field_stride, ng, arena_len, dx=1.0):
+        L = load()
+        n = len(dims)
+        arr = (_Patch * n)()
+        for p in range(n):
+            arr[p].n = (ctypes.c_int32 * 3)(*[int(v) for v in dims[p]])
+            arr[p].neighbour = (ctypes.c_int32 * 26)(*[int(v) for v in nb[p]])
+            arr[p].offset = int(offset[p])
+            arr[p].field_stride = int(field_stride[p])
+        ctx._sync_stream()
+        h = ctypes.c_void_p()
+        _check("pmp_batch_create", L.pmp_batch_create(ctx.h, arr, n, int(ng), float(dx), int(arena_len),
+                                                      ctypes.byref(h)))
+        self.h, self.ctx, self.np = h, ctx, n
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().pmp_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def pmp_batch_create(ctx, dims, nb, offset, field_stride, ng, arena_len, dx=1.0):
+    return BatchHandle(ctx, dims, nb, offset, field_stride, ng, arena_len, dx)
+
+
+def pmp_batch_set_particles(batch, first):
+    arr = (ctypes.c_int64 * len(first))(*[int(v) for v in first])
+    batch.ctx._sync_stream()
+    _check("pmp_batch_set_particles", load().pmp_batch_set_particles(batch.h, arr))
+
+
+def pmp_batch_set_strategy(batch, strategy):
+    batch.ctx._sync_stream()
+    _check("pmp_batch_set_strategy", load().pmp_batch_set_strategy(batch.h, STRATEGIES.get(strategy, strategy)))
+
+
+def pmp_batch_strategies(batch):
+    out = (ctypes.c_int32 * batch.np)()
+    _check("pmp_batch_strategies", load().pmp_batch_strategies(batch.h, out))
+    return list(out)
+
+
+def pmp_batch_autotune(batch, state, buffer, parts, gathered, deterministic=False, reps=3):
+    """Returns the chosen strategy per bin (-1: empty bin)."""
+    pp = _parts(parts)
+    out = (ctypes.c_int32 * BATCH_BINS)()
+    batch.ctx._sync_stream()
+    _check("pmp_batch_autotune", load().pmp_batch_autotune(batch.h, _ptr(state), _ptr(buffer), ctypes.byref(pp),
+                                                           _ptr(gathered), 1 if deterministic else 0, int(reps),
+                                                           out))
+    return list(out)
+
+
+def pmp_cycle_batched(batch, state, buffer, parts, gathered, eta_out=None, launch="persistent"):
+    pp = _parts(parts)
+    batch.ctx._sync_stream()
+    _check("pmp_cycle_batched", load().pmp_cycle_batched(batch.h, _ptr(state), _ptr(buffer), ctypes.byref(pp),
+                                                         _ptr(gathered), _ptr(eta_out), LAUNCHES.get(launch, launch)))
+
+
+def pmp_batch_info(batch):
+    g = ctypes.c_int32()
+    it = (ctypes.c_int64 * 3)()
+    _check("pmp_batch_info", load().pmp_batch_info(batch.h, ctypes.byref(g), it))
+    return g.value, tuple(it)
+
+
 # ---------------------------------------------------------------------------
 # conveniences built only from the calls above
 # ---------------------------------------------------------------------------
@@ -347,3 +446,34 @@ class Pass:
 def _EMPTY(device):
     z = torch.zeros(1, dtype=torch.float64, device=device)
     return {k: z[:0] for k in ("x", "y", "z", "m", "px", "py", "pz", "e")}
+
+
+class BatchPass:
+    """One pass of one kind over a synthetic.Batch of patches: state and
+    buffer arenas, particles (patch after patch), gathered rows, the batch
+    handle with its particle ranges set."""
+
+    def __init__(self, params, batch, state, parts, first, dx=1.0, want_eta=False):
+        self.ctx = Context(params)
+        dev = state.device
+        self.batch = batch
+        self.state = state
+        self.buffer = torch.zeros(batch.arena_len, dtype=torch.float64, device=dev)
+        self.parts = parts
+        n = int(parts["x"].numel())
+        self.n = n
+        self.gathered = torch.zeros((pmp_gathered_rows(params["kind"]), max(n, 1)), dtype=torch.float64, device=dev)
+        self.eta = torch.empty(batch.ncells_valid, dtype=torch.float64, device=dev) if want_eta else None
+        self.h = BatchHandle(self.ctx, batch.dims, batch.nb, batch.offset, batch.fstride, batch.g, batch.arena_len,
+                             dx)
+        pmp_batch_set_particles(self.h, first)
+
+    def gathered_view(self):
+        return self.gathered[:, : self.n]
+
+    def run(self, launch="persistent"):
+        pmp_cycle_batched(self.h, self.state, self.buffer, self.parts, self.gathered, self.eta, launch)
+
+    def close(self):
+        self.h.close()
+        self.ctx.close()
