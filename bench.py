@@ -49,6 +49,7 @@ def parse():
     ap.add_argument("--mode", default="atomic", choices=["atomic", "sorted"])
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--cpu-sample-n", type=int, default=128)
     ap.add_argument("--n", type=int, default=None,
                     help="shrink the box to n^3 at equal particle density (profiling captures)")
@@ -428,6 +429,8 @@ def run_ours(args, world, rank, local):
         "clocks": clk,
     }
     result["fwd_bwd_c4_128"] = fwd_bwd(args)
+    if not args.no_batched:
+        result["batched_c3"] = batched(args)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         result["cpu_baseline"] = cpu_baseline(args)
     if rank == 0:
@@ -475,6 +478,73 @@ def fwd_bwd(args):
     fm, bm = sum(f_ms) / len(f_ms), sum(b_ms) / len(b_ms)
     return {"fwd_ms": fm, "bwd_ms": bm, "total_ms": fm + bm, "particles": n,
             "workload": "c4_128: 128^3, 4 ghosts, 262,144 supernovae (half in 32 Plummer clusters)"}
+
+
+def batched(args):
+    """The batched form on the 512-patch workload (8x8x8 periodic super-grid,
+    edges from {16,24,32,48,64} per axis, power-law particle counts, 1/8
+    sinks): one mixed cycle (supernova pass, then sink pass) per step with the
+    autotuned per-bin strategies, run as one persistent launch per pass, as
+    that launch replayed from a CUDA graph, and as the plain per-patch launch
+    loop.  CUDA-event times of the two passes (the state restore before each
+    step is outside them), mean over `steps` after 3 warm-ups."""
+    import torch
+
+    from paper_2509_18261_gb300 import pmp
+    from paper_2509_18261_gb300 import synthetic as syn
+
+    w = syn.make_batch_workload()
+    batch = w["batch"]
+    st0 = torch.from_numpy(w["state"]).cuda()
+    st = st0.clone()
+    fb = pmp.parts_to_device(w["fb"])
+    sk = pmp.parts_to_device(w["sink"])
+    sk0 = {k: sk[k].clone() for k in ("m", "px", "py", "pz")}
+    passes = [pmp.BatchPass(w["fb_params"], batch, st, fb, w["fb_first"]),
+              pmp.BatchPass(w["sink_params"], batch, st, sk, w["sink_first"])]
+    chosen = []
+    for bp in passes:
+        chosen.append(pmp.pmp_batch_autotune(bp.h, st, bp.buffer, bp.parts, bp.gathered, deterministic=True))
+    stream = torch.cuda.current_stream()
+
+    def restore():
+        st.copy_(st0)
+        for k in sk0:
+            sk[k].copy_(sk0[k])
+
+    out = {}
+    for launch in ("persistent", "graph", "per_patch"):
+        times = []
+        for it in range(3 + max(args.steps, 1)):
+            restore()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for bp in passes:
+                bp.run(launch)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            if it >= 3:
+                times.append(e0.elapsed_time(e1))
+        out[launch] = sum(times) / len(times)
+    for bp in passes:
+        code, idx = pmp.pmp_get_error(bp.ctx)
+        if code:
+            raise RuntimeError(f"batched: device error {code} at {idx}")
+    grid, items = pmp.pmp_batch_info(passes[0].h)
+    for bp in passes:
+        bp.close()
+    n_particles = int(w["fb_first"][-1] + w["sink_first"][-1])
+    best = min(out["persistent"], out["graph"])
+    return {
+        "ms_per_cycle": {k: round(v, 4) for k, v in out.items()},
+        "speedup_vs_per_patch": out["per_patch"] / best,
+        "cells_per_s": batch.ncells_valid / (best * 1e-3),
+        "particles_per_s": n_particles / (best * 1e-3),
+        "strategy_per_bin": {"fb": chosen[0], "sink": chosen[1]},
+        "persistent_grid": grid,
+        "workload": (f"c3_batched: {batch.np} patches on an 8x8x8 periodic super-grid, {batch.ncells_valid} valid "
+                     f"cells, {int(w['fb_first'][-1])} supernovae + {int(w['sink_first'][-1])} sinks, 4 ghosts"),
+    }
 
 
 # ---------------------------------------------------------------------------
