@@ -1,9 +1,10 @@
 // pmp_particles.cu -- particle-side kernels.
 //
-//   plan      one warp per particle (spatial processing order): lanes test the
-//             (2R+1)^3 candidate cells; omega by a warp-wide ballot over the
-//             S^3 sub-points; kernel cells with omega > 0 written in canonical
-//             order (z slowest, x fastest) to the particle's fixed slot range
+//   plan      persistent; one warp per particle (spatial processing order):
+//             lanes classify the candidate cells, then count the S^3
+//             sub-points of the boundary cells (a lane per cell); kernel cells
+//             with omega > 0 written in canonical order (z slowest, x fastest)
+//             to the particle's fixed slot range
 //   gather    one thread per particle over its cells in that order, so every
 //             per-particle sum has one fixed summation order
 //   deposit   one warp per 8 consecutive particles, lanes over their pairs,
@@ -74,90 +75,142 @@ __global__ void __launch_bounds__(256) k_prologue(Box S, Parts p, int sh, unsign
 // plan
 // ---------------------------------------------------------------------------
 
-// shared memory per warp: floats edges [3][W+1], centre squares [3][W],
-// farthest-corner squares [3][W], sub-point squares [3][W*S], x-row extremes
-// [2][W]; ints: the kernel-cell code of each lane, the needing-lane list, the
-// per-lane sub-point counts
-__host__ __device__ constexpr int plan_warp_floats(int W, int S) { return 3 * (W + 1) + 8 * W + 3 * W * S; }
-constexpr int kPlanWarpInts = 96;
+// Candidate offsets of a kernel: (ox, oy, oz) in [0, W)^3, offset o - R per
+// axis, whose cell centre can come within r_K of some point of the host cell,
+// i.e. sum_a max(0, |o_a - R| - 1/2)^2 <= r_K^2 (1 + 1e-9) (the slack covers
+// rounding of the FP64 distance).  Kept in canonical order (z slowest, x
+// fastest); their number is the slot bound of a particle.  Built by one warp.
+__device__ __forceinline__ int build_candidates(double rK, int R, unsigned *cand)
+{
+    const int W = 2 * R + 1, W3 = W * W * W;
+    const int lane = threadIdx.x & 31;
+    const double lim = rK * rK * (1.0 + 1e-9);
+    int n = 0;
+    for (int k0 = 0; k0 < W3; k0 += 32) {
+        const int k = k0 + lane;
+        bool ok = false;
+        unsigned code = 0;
+        if (k < W3) {
+            const int oz = k / (W * W), oy = k / W - oz * W, ox = k - (k / W) * W;
+            const int o[3] = {ox - R, oy - R, oz - R};
+            double s = 0.0;
+            for (int a = 0; a < 3; ++a) {
+                const double m = fabs((double)o[a]) - 0.5;
+                if (m > 0.0) s += m * m;
+            }
+            ok = s <= lim;
+            code = (unsigned)ox | ((unsigned)oy << 8) | ((unsigned)oz << 16);
+        }
+        const unsigned msk = __ballot_sync(kFull, ok);
+        if (ok) cand[n + __popc(msk & ((1u << lane) - 1u))] = code;
+        n += __popc(msk);
+    }
+    return n;
+}
 
-template <int R, bool FB>
-__global__ void __launch_bounds__(256) k_plan(KParams P, Box S, Parts p, const unsigned *__restrict__ perm,
-                                              const unsigned long long *__restrict__ hosts,
-                                              const float4 *__restrict__ fr, unsigned cap,
-                                              unsigned *__restrict__ counts, unsigned long long *__restrict__ slots,
-                                              DevStatus *st)
+// Per-warp shared memory of the plan: FP32 squares per axis (sub-points
+// [3][W*S], centres [3][W], farthest corners [3][W]), then two u16 arrays of
+// W^3 entries (count per candidate, boundary-cell list).
+__host__ __device__ constexpr int plan_warp_bytes(int W, int S)
+{
+    return ((3 * W * S + 6 * W) * 4 + 15) / 16 * 16 + (4 * W * W * W + 15) / 16 * 16;
+}
+
+// Sub-point count of one boundary cell (centre inside, farthest corner not
+// surely inside): the S^3 FP32 sums are compared with both band edges; if no
+// sum falls inside the band the count below band_lo is the exact count,
+// otherwise the cell is recounted with the FP64 test for the in-band points.
+template <int SC>
+__device__ __forceinline__ int boundary_count(const KParams &P, const float *sx, const float *sy, const float *sz,
+                                              int cx, int cy, int cz, const Parts &p, long long s)
+{
+    constexpr int SM = SC ? SC : kMaxS;
+    const int Sn = SC ? SC : P.S;
+    const float blo = P.band_lo, bhi = P.band_hi;
+    float vx[SM];
+#pragma unroll
+    for (int a = 0; a < SM; ++a) vx[a] = (SC || a < Sn) ? sx[a] : 3.0e38f;
+    int lo = 0, hi = 0;
+#pragma unroll
+    for (int c = 0; c < SM; ++c) {
+        if (!SC && c >= Sn) break;
+        const float vzc = sz[c];
+#pragma unroll
+        for (int b = 0; b < SM; ++b) {
+            if (!SC && b >= Sn) break;
+            const float t = sy[b] + vzc;
+#pragma unroll
+            for (int a = 0; a < SM; ++a) {
+                const float v = t + vx[a];
+                lo += v < blo ? 1 : 0;
+                hi += v <= bhi ? 1 : 0;
+            }
+        }
+    }
+    if (lo == hi) return lo;
+    const double x = p.x[s], y = p.y[s], z = p.z[s];
+    int cnt = 0;
+    for (int c = 0; c < Sn; ++c)
+        for (int b = 0; b < Sn; ++b) {
+            const float t = sy[b] + sz[c];
+            for (int a = 0; a < Sn; ++a) {
+                const float v = t + sx[a];
+                if (v < blo) ++cnt;
+                else if (v <= bhi && subpoint_inside_exact(P.r2, P.frac[a], P.frac[b], P.frac[c], cx, cy, cz, x, y, z))
+                    ++cnt;
+            }
+        }
+    return cnt;
+}
+
+// Steps 1-4 of the plan for particle s (processing position t) by one warp.
+template <int R, bool FB, int SC>
+__device__ __forceinline__ void plan_particle(const KParams &P, const Box &S, const Parts &p, long long t, long long s,
+                                              unsigned long long hp, float4 f4, unsigned cap, int ncand,
+                                              const unsigned *cand, float *sub, float *csq, float *fc2,
+                                              unsigned short *stc, unsigned short *blist, unsigned *counts,
+                                              unsigned long long *slots, DevStatus *st)
 {
     constexpr int W = 2 * R + 1;
-    constexpr int W3 = W * W * W;
-    extern __shared__ float smem[];
-    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    const long long t = (long long)blockIdx.x * nw + wib;
-    const int Sn = FB ? P.S : 1;
-    const int wf = plan_warp_floats(W, Sn);
-    float *edge = smem + (size_t)wib * wf;  // [3][W+1]
-    float *csq = edge + 3 * (W + 1);        // [3][W]
-    float *fc2 = csq + 3 * W;               // [3][W]
-    float *xlo = fc2 + 3 * W;               // [W]
-    float *xhi = xlo + W;                   // [W]
-    float *sub = xhi + W;                   // [3][W*S]
-    int *ism = reinterpret_cast<int *>(smem + (size_t)nw * wf) + wib * kPlanWarpInts;
-    int *code = ism, *list = ism + 32, *csum = ism + 64;
-    if (t >= p.count) return;  // warp-uniform
-    const long long s = perm ? (long long)perm[t] : t;
-    const unsigned long long hp = hosts[s];
-    if (hp == kNoHost) {
-        if (lane == 0) counts[t] = 0;
-        return;
-    }
+    const int lane = threadIdx.x & 31;
+    const int Sn = FB ? (SC ? SC : P.S) : 1;
+    const float blo = P.band_lo, bhi = P.band_hi;
     int h0, h1, h2;
     unpack_host(hp, h0, h1, h2);
-    const float4 f4 = fr[s];
-    // FP32 offsets from the fractional position: e = (o - R) - frac
-    for (int i = lane; i < 3 * (W + 1); i += 32) {
-        const int a = i / (W + 1), o = i - a * (W + 1);
-        const float fa = a == 0 ? f4.x : (a == 1 ? f4.y : f4.z);
-        edge[i] = (float)(o - R) - fa;
-    }
+    // 1. per-axis squares from the FP32 edge offsets e = (o - R) - frac
     __syncwarp();
     for (int i = lane; i < 3 * W; i += 32) {
         const int a = i / W, o = i - a * W;
-        const float e0 = edge[a * (W + 1) + o], e1 = edge[a * (W + 1) + o + 1];
+        const float fa = a == 0 ? f4.x : (a == 1 ? f4.y : f4.z);
+        const float e0 = (float)(o - R) - fa, e1 = (float)(o + 1 - R) - fa;
         const float c = e0 + 0.5f;
         csq[i] = c * c;
-        const float m = fabsf(e0) > fabsf(e1) ? fabsf(e0) : fabsf(e1);
-        fc2[i] = m * m;
+        if (FB) {
+            const float m = fabsf(e0) > fabsf(e1) ? fabsf(e0) : fabsf(e1);
+            fc2[i] = m * m;
+        }
     }
     if (FB) {
         for (int i = lane; i < 3 * W * Sn; i += 32) {
             const int a = i / (W * Sn), r = i - a * (W * Sn), o = r / Sn, k = r - o * Sn;
-            const float u = edge[a * (W + 1) + o] + P.fracf[k];
+            const float fa = a == 0 ? f4.x : (a == 1 ? f4.y : f4.z);
+            const float u = ((float)(o - R) - fa) + P.fracf[k];
             sub[i] = u * u;
-        }
-        __syncwarp();
-        for (int o = lane; o < W; o += 32) {
-            float lo = 3.0e38f, hi = 0.0f;
-            for (int k = 0; k < Sn; ++k) {
-                const float v = sub[o * Sn + k];
-                lo = v < lo ? v : lo;
-                hi = v > hi ? v : hi;
-            }
-            xlo[o] = lo;
-            xhi[o] = hi;
         }
     }
     __syncwarp();
-    const float blo = P.band_lo, bhi = P.band_hi;
-    unsigned nout = 0;
+    // 2. classification
+    unsigned nout = 0, nb = 0;
     const unsigned long long base = (unsigned long long)t * cap;
-    for (int k0 = 0; k0 < W3; k0 += 32) {
+    for (int k0 = 0; k0 < ncand; k0 += 32) {
         const int k = k0 + lane;
         int ox = 0, oy = 0, oz = 0;
         bool mem = false, full = false;
-        if (k < W3) {
-            oz = k / (W * W);
-            oy = k / W - oz * W;
-            ox = k - (k / W) * W;
+        if (k < ncand) {
+            const unsigned code = cand[k];
+            ox = code & 0xff;
+            oy = (code >> 8) & 0xff;
+            oz = code >> 16;
             const int c0 = h0 + ox - R, c1 = h1 + oy - R, c2 = h2 + oz - R;
             const bool dom = (S.per0 || (c0 >= 0 && c0 < S.n0)) && (S.per1 || (c1 >= 0 && c1 < S.n1)) &&
                              (S.per2 || (c2 >= 0 && c2 < S.n2));
@@ -168,65 +221,121 @@ __global__ void __launch_bounds__(256) k_plan(KParams P, Box S, Parts p, const u
                 if (FB && mem) full = (fc2[ox] + fc2[W + oy]) + fc2[2 * W + oz] < blo;
             }
         }
-        int cnt = 0;
         if (FB) {
-            cnt = full ? P.S3 : 0;
-            const bool needs = mem && !full;
-            const unsigned need = __ballot_sync(kFull, needs);
-            if (need) {
-                // sub-point counts of the cells that need one: lanes take
-                // (cell, row) items, a row being the S sub-points along x at a
-                // fixed (y, z) sub-position
-                code[lane] = ox | (oy << 8) | (oz << 16);
-                csum[lane] = 0;
-                if (needs) list[__popc(need & ((1u << lane) - 1u))] = lane;
-                __syncwarp();
-                const int S2 = Sn * Sn;
-                const int items = __popc(need) * S2;
-                for (int f0 = 0; f0 < items; f0 += 32) {
-                    const int f = f0 + lane;
-                    if (f < items) {
-                        const int mi = P.Slog >= 0 ? (f >> (2 * P.Slog)) : f / S2;
-                        const int row = f - mi * S2;
-                        const int src = list[mi];
-                        const int pk = code[src];
-                        const int cx = pk & 0xff, cy = (pk >> 8) & 0xff, cz = pk >> 16;
-                        const int b = P.Slog >= 0 ? (row & (Sn - 1)) : row % Sn;
-                        const int c = P.Slog >= 0 ? (row >> P.Slog) : row / Sn;
-                        const float bs = sub[(W + cy) * Sn + b] + sub[(2 * W + cz) * Sn + c];
-                        int add = 0;
-                        if (bs + xlo[cx] > bhi) {
-                            add = 0;
-                        } else if (bs + xhi[cx] < blo) {
-                            add = Sn;
-                        } else {
-                            for (int a = 0; a < Sn; ++a) {
-                                const float tf = bs + sub[cx * Sn + a];
-                                if (tf < blo) ++add;
-                                else if (tf <= bhi &&
-                                         subpoint_inside_exact(P.r2, P.frac[a], P.frac[b], P.frac[c], h0 + cx - R,
-                                                               h1 + cy - R, h2 + cz - R, p.x[s], p.y[s], p.z[s]))
-                                    ++add;
-                            }
-                        }
-                        if (add) atomicAdd(csum + src, add);
-                    }
-                }
-                __syncwarp();
-                if (needs) cnt = csum[lane];
-                __syncwarp();
+            if (k < ncand) stc[k] = mem ? (full ? (unsigned short)P.S3 : 0) : 0;
+            const bool bnd = mem && !full;
+            const unsigned bm = __ballot_sync(kFull, bnd);
+            if (bnd) blist[nb + __popc(bm & ((1u << lane) - 1u))] = (unsigned short)k;
+            nb += __popc(bm);
+        } else {
+            const unsigned m = __ballot_sync(kFull, mem);
+            if (mem) {
+                const unsigned pos = nout + __popc(m & ((1u << lane) - 1u));
+                if (pos < cap) slots[base + pos] = pack_pair(h0 + ox - R, h1 + oy - R, h2 + oz - R, R, 0);
+                else report(st, PMP_ERR_WORKSPACE, s);
             }
-            mem = mem && cnt > 0;
+            nout += __popc(m);
         }
-        const unsigned m = __ballot_sync(kFull, mem);
-        if (mem) {
-            const unsigned pos = nout + __popc(m & ((1u << lane) - 1u));
-            if (pos < cap) slots[base + pos] = pack_pair(h0 + ox - R, h1 + oy - R, h2 + oz - R, R, cnt);
-            else report(st, PMP_ERR_WORKSPACE, s);
+    }
+    if (FB) {
+        __syncwarp();
+        // 3. sub-point counts of the boundary cells
+        for (unsigned j = lane; j < nb; j += 32) {
+            const int k = blist[j];
+            const unsigned code = cand[k];
+            const int ox = code & 0xff, oy = (code >> 8) & 0xff, oz = code >> 16;
+            stc[k] = (unsigned short)boundary_count<SC>(P, sub + ox * Sn, sub + (W + oy) * Sn,
+                                                        sub + (2 * W + oz) * Sn, h0 + ox - R, h1 + oy - R,
+                                                        h2 + oz - R, p, s);
         }
-        nout += __popc(m);
+        __syncwarp();
+        // 4. cells with omega > 0, in candidate order
+        for (int k0 = 0; k0 < ncand; k0 += 32) {
+            const int k = k0 + lane;
+            const int cnt = k < ncand ? stc[k] : 0;
+            const unsigned m = __ballot_sync(kFull, cnt > 0);
+            if (cnt > 0) {
+                const unsigned code = cand[k];
+                const int ox = code & 0xff, oy = (code >> 8) & 0xff, oz = code >> 16;
+                const unsigned pos = nout + __popc(m & ((1u << lane) - 1u));
+                if (pos < cap) slots[base + pos] = pack_pair(h0 + ox - R, h1 + oy - R, h2 + oz - R, R, cnt);
+                else report(st, PMP_ERR_WORKSPACE, s);
+            }
+            nout += __popc(m);
+        }
     }
     if (lane == 0) counts[t] = nout < cap ? nout : cap;
+}
+
+// The plan.  Persistent: each block builds the candidate table once, then its
+// warps take particles of the processing order.  For one particle a warp
+//   1. writes the per-axis FP32 squares;
+//   2. classifies the candidates (lane per candidate): member if the centre
+//      is inside (FP32 outside the band, else the FP64 test), full if the
+//      farthest corner is surely inside (omega = 1), else a boundary cell;
+//   3. (supernovae) counts the sub-points of the boundary cells, a lane per
+//      cell;
+//   4. writes the cells with omega > 0 (every member, for sinks) in
+//      candidate order to the particle's slots.
+template <int R, bool FB, int SC>
+__global__ void __launch_bounds__(256) k_plan(KParams P, Box S, Parts p, const unsigned *__restrict__ perm,
+                                              const unsigned long long *__restrict__ hosts,
+                                              const float4 *__restrict__ fr, unsigned cap,
+                                              unsigned *__restrict__ counts, unsigned long long *__restrict__ slots,
+                                              DevStatus *st)
+{
+    constexpr int W = 2 * R + 1;
+    constexpr int W3 = W * W * W;
+    extern __shared__ __align__(16) unsigned char psm[];
+    __shared__ int ncand_sh;
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int Sn = FB ? (SC ? SC : P.S) : 1;
+    unsigned *cand = reinterpret_cast<unsigned *>(psm);
+    const int wbytes = plan_warp_bytes(W, Sn);
+    unsigned char *wsm = psm + (W3 * 4 + 15) / 16 * 16 + (size_t)wib * wbytes;
+    float *sub = reinterpret_cast<float *>(wsm);  // [3][W*S]
+    float *csq = sub + 3 * W * Sn;                // [3][W]
+    float *fc2 = csq + 3 * W;                     // [3][W]
+    unsigned short *stc = reinterpret_cast<unsigned short *>(wsm + ((3 * W * Sn + 6 * W) * 4 + 15) / 16 * 16);
+    unsigned short *blist = stc + W3;
+    if (wib == 0) {
+        const int n = build_candidates(P.rK, R, cand);
+        if (lane == 0) ncand_sh = n;
+    }
+    __syncthreads();
+    const int ncand = ncand_sh;
+    const long long nwarps = (long long)gridDim.x * nw;
+    // The particle data of the next iteration and the index of the one after
+    // are requested one step ahead (their loads are random accesses).
+    long long t = (long long)blockIdx.x * nw + wib;
+    long long s = 0, s1 = 0;
+    unsigned long long hp = kNoHost;
+    float4 f4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (t < p.count) {
+        s = perm ? (long long)perm[t] : t;
+        hp = hosts[s];
+        f4 = fr[s];
+    }
+    if (t + nwarps < p.count) s1 = perm ? (long long)perm[t + nwarps] : t + nwarps;
+    for (; t < p.count; t += nwarps) {
+        unsigned long long hp1 = kNoHost;
+        float4 f41 = make_float4(0.f, 0.f, 0.f, 0.f);
+        long long s2 = 0;
+        if (t + nwarps < p.count) {
+            hp1 = hosts[s1];
+            f41 = fr[s1];
+        }
+        if (t + 2 * nwarps < p.count) s2 = perm ? (long long)perm[t + 2 * nwarps] : t + 2 * nwarps;
+        if (hp != kNoHost)
+            plan_particle<R, FB, SC>(P, S, p, t, s, hp, f4, cap, ncand, cand, sub, csq, fc2, stc, blist, counts,
+                                     slots, st);
+        else if (lane == 0)
+            counts[t] = 0;
+        s = s1;
+        hp = hp1;
+        f4 = f41;
+        s1 = s2;
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -235,6 +344,30 @@ __global__ void __launch_bounds__(256) k_plan(KParams P, Box S, Parts p, const u
 
 // Covered fractions omega = k / S^3 for k = 0..S^3, computed once per block.
 constexpr int kMaxS3 = kMaxS * kMaxS * kMaxS;
+
+// Pairs whose loads a per-particle loop issues together.
+constexpr int kUnroll = 4;
+
+// One kernel cell's terms of the supernova gather sums (omega = 1 skips the
+// products: 1 * v == v).
+__device__ __forceinline__ void fb_gather_add(const KParams &P, const double *wtab, int cnt, const double U[NF],
+                                              double &sw, double &sr, double &sp0, double &sp1, double &sp2)
+{
+    if (cnt == P.S3) {
+        sw = sw + 1.0;
+        sr = sr + U[0];
+        sp0 = sp0 + U[1];
+        sp1 = sp1 + U[2];
+        sp2 = sp2 + U[3];
+    } else {
+        const double w = wtab[cnt];
+        sw = sw + w;
+        sr = sr + w * U[0];
+        sp0 = sp0 + w * U[1];
+        sp1 = sp1 + w * U[2];
+        sp2 = sp2 + w * U[3];
+    }
+}
 
 __device__ __forceinline__ void fill_omega_table(const KParams &P, double *wtab)
 {
@@ -262,24 +395,24 @@ __global__ void __launch_bounds__(128) k_gather_fb(KParams P, Box S, const doubl
     double sw = 0.0, sr = 0.0, sp0 = 0.0, sp1 = 0.0, sp2 = 0.0;
     const unsigned long long b0 = (unsigned long long)t * pl.cap;
     const unsigned nc = pl.counts[t];
-    for (unsigned q = 0; q < nc; ++q) {
-        const PairCell c = unpack_pair(pl.slots[b0 + q], P.R);
+    // the cells' loads are issued kUnroll at a time, the sums stay in kernel order
+    unsigned q = 0;
+    for (; q + kUnroll <= nc; q += kUnroll) {
+        PairCell c[kUnroll];
+        double U[kUnroll][NF];
+#pragma unroll
+        for (int k = 0; k < kUnroll; ++k) c[k] = unpack_pair(__ldg(pl.slots + b0 + q + k), P.R);
+#pragma unroll
+        for (int k = 0; k < kUnroll; ++k)
+            load_cell(u, S, S.at(owner(c[k].i, S.n0), owner(c[k].j, S.n1), owner(c[k].k, S.n2)), U[k]);
+#pragma unroll
+        for (int k = 0; k < kUnroll; ++k) fb_gather_add(P, wtab, c[k].cnt, U[k], sw, sr, sp0, sp1, sp2);
+    }
+    for (; q < nc; ++q) {
+        const PairCell c = unpack_pair(__ldg(pl.slots + b0 + q), P.R);
         double U[NF];
         load_cell(u, S, S.at(owner(c.i, S.n0), owner(c.j, S.n1), owner(c.k, S.n2)), U);
-        if (c.cnt == P.S3) {
-            sw = sw + 1.0;
-            sr = sr + U[0];
-            sp0 = sp0 + U[1];
-            sp1 = sp1 + U[2];
-            sp2 = sp2 + U[3];
-        } else {
-            const double w = wtab[c.cnt];
-            sw = sw + w;
-            sr = sr + w * U[0];
-            sp0 = sp0 + w * U[1];
-            sp1 = sp1 + w * U[2];
-            sp2 = sp2 + w * U[3];
-        }
+        fb_gather_add(P, wtab, c.cnt, U, sw, sr, sp0, sp1, sp2);
     }
     if (!fb_gather_rows(P, sw, sr, sp0, sp1, sp2, m, pe0, pe1, pe2, Esn, G + s, gs)) report(st, PMP_ERR_NONFINITE, s);
 }
@@ -307,8 +440,29 @@ __global__ void __launch_bounds__(128) k_gather_sink(KParams P, Box S, const dou
     const unsigned long long b0 = (unsigned long long)t * pl.cap;
     const unsigned nc = pl.counts[t];
     double srho = 0.0, sp0 = 0.0, sp1 = 0.0, sp2 = 0.0, src = 0.0;
-    for (unsigned q = 0; q < nc; ++q) {
-        const PairCell c = unpack_pair(pl.slots[b0 + q], P.R);
+    unsigned q = 0;
+    for (; q + kUnroll <= nc; q += kUnroll) {
+        double2 g[kUnroll][3];
+#pragma unroll
+        for (int k = 0; k < kUnroll; ++k) {
+            const PairCell c = unpack_pair(__ldg(pl.slots + b0 + q + k), P.R);
+            const double2 *r = reinterpret_cast<const double2 *>(
+                pl.grec + vidx(S, owner(c.i, S.n0), owner(c.j, S.n1), owner(c.k, S.n2)) * kRec);
+            g[k][0] = __ldg(r);
+            g[k][1] = __ldg(r + 1);
+            g[k][2] = __ldg(r + 2);
+        }
+#pragma unroll
+        for (int k = 0; k < kUnroll; ++k) {
+            srho = srho + g[k][0].x;
+            sp0 = sp0 + g[k][0].y;
+            sp1 = sp1 + g[k][1].x;
+            sp2 = sp2 + g[k][1].y;
+            src = src + g[k][2].x;
+        }
+    }
+    for (; q < nc; ++q) {
+        const PairCell c = unpack_pair(__ldg(pl.slots + b0 + q), P.R);
         const double2 *g =
             reinterpret_cast<const double2 *>(pl.grec + vidx(S, owner(c.i, S.n0), owner(c.j, S.n1), owner(c.k, S.n2)) * kRec);
         const double2 g0 = __ldg(g), g1 = __ldg(g + 1), g2 = __ldg(g + 2);
@@ -555,6 +709,28 @@ __global__ void __launch_bounds__(128) k_segment_sum(KParams P, Box S, const dou
 // Step 4: limited changes returned to sinks
 // ---------------------------------------------------------------------------
 
+// One kernel cell's terms of the Step-4 sums: the pair's Delta U (mass and
+// momentum rows of sink_pair_delta, from D record d0 = (rho - rho_Tr, p_x/rho),
+// d1 = (p_y/rho, p_z/rho)) times the cell's eta e.
+__device__ __forceinline__ void sink_return_add(double K, double w, double2 d0, double2 d1, double e, double &a0,
+                                                double &a1, double &a2, double &a3)
+{
+    const double bh = K * w;
+    const double a = bh >= d0.x ? bh : d0.x;
+    const double u0 = -a, u1 = -(a * d0.y), u2 = -(a * d1.x), u3 = -(a * d1.y);
+    if (e == 1.0) {
+        a0 = a0 + u0;
+        a1 = a1 + u1;
+        a2 = a2 + u2;
+        a3 = a3 + u3;
+    } else {
+        a0 = a0 + e * u0;
+        a1 = a1 + e * u1;
+        a2 = a2 + e * u2;
+        a3 = a3 + e * u3;
+    }
+}
+
 template <int R>
 __global__ void __launch_bounds__(128) k_return_sinks(KParams P, Box S, Parts p, const double *__restrict__ G,
                                                       PlanPtrs pl, DevStatus *st)
@@ -567,24 +743,39 @@ __global__ void __launch_bounds__(128) k_return_sinks(KParams P, Box S, Parts p,
         report(st, bad, s);
         return;
     }
+    constexpr int W = 2 * R + 1;
     double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
     const unsigned long long b0 = (unsigned long long)t * pl.cap;
     const unsigned nc = pl.counts[t];
-    for (unsigned q = 0; q < nc; ++q) {
-        const PairCell c = unpack_pair(pl.slots[b0 + q], P.R);
-        double dU[NF], e;
-        sink_pair_delta<R>(P, S, p, G, pl, s, c, dU, e);
-        if (e == 1.0) {
-            a0 = a0 + dU[0];
-            a1 = a1 + dU[1];
-            a2 = a2 + dU[2];
-            a3 = a3 + dU[3];
-        } else {
-            a0 = a0 + e * dU[0];
-            a1 = a1 + e * dU[1];
-            a2 = a2 + e * dU[2];
-            a3 = a3 + e * dU[3];
+    int hx, hy, hz;
+    unpack_host(__ldg(pl.hosts + s), hx, hy, hz);
+    const double *ws = pl.wts + s * (3 * W);
+    const double K = __ldg(G + SK_K * p.count + s);
+    unsigned q = 0;
+    for (; q + kUnroll <= nc; q += kUnroll) {
+        double2 d0[kUnroll], d1[kUnroll];
+        double e[kUnroll], wx[kUnroll], wy[kUnroll], wz[kUnroll];
+#pragma unroll
+        for (int k = 0; k < kUnroll; ++k) {
+            const PairCell c = unpack_pair(__ldg(pl.slots + b0 + q + k), P.R);
+            const double *r = pl.drec + vidx(S, owner(c.i, S.n0), owner(c.j, S.n1), owner(c.k, S.n2)) * kRec;
+            d0[k] = __ldg(reinterpret_cast<const double2 *>(r));
+            d1[k] = __ldg(reinterpret_cast<const double2 *>(r) + 1);
+            e[k] = __ldg(r + 5);
+            wx[k] = __ldg(ws + c.i - hx + R);
+            wy[k] = __ldg(ws + W + c.j - hy + R);
+            wz[k] = __ldg(ws + 2 * W + c.k - hz + R);
         }
+#pragma unroll
+        for (int k = 0; k < kUnroll; ++k)
+            sink_return_add(K, (wx[k] * wy[k]) * wz[k], d0[k], d1[k], e[k], a0, a1, a2, a3);
+    }
+    for (; q < nc; ++q) {
+        const PairCell c = unpack_pair(__ldg(pl.slots + b0 + q), P.R);
+        const double *r = pl.drec + vidx(S, owner(c.i, S.n0), owner(c.j, S.n1), owner(c.k, S.n2)) * kRec;
+        const double w = (__ldg(ws + c.i - hx + R) * __ldg(ws + W + c.j - hy + R)) * __ldg(ws + 2 * W + c.k - hz + R);
+        sink_return_add(K, w, __ldg(reinterpret_cast<const double2 *>(r)),
+                        __ldg(reinterpret_cast<const double2 *>(r) + 1), __ldg(r + 5), a0, a1, a2, a3);
     }
     p.m[s] = p.m[s] - a0 * P.V;
     p.px[s] = p.px[s] - a1 * P.V;
@@ -610,15 +801,26 @@ void launch_prologue(const Box &S, const Parts &p, unsigned *keys, unsigned *ids
     k_prologue<<<blocks_for(p.count, 256), 256, 0, stream>>>(S, p, sh, keys, ids, pl.hosts, pl.fr, st);
 }
 
-template <int R, bool FB>
+template <int R, bool FB, int SC>
 static void plan_one(const KParams &P, const Box &S, const Parts &p, const PlanPtrs &pl, DevStatus *st,
                      cudaStream_t stream)
 {
     constexpr int W = 2 * R + 1;
-    const int warps = 8;
-    const size_t sm = (size_t)warps * (plan_warp_floats(W, FB ? P.S : 1) * sizeof(float) + kPlanWarpInts * sizeof(int));
-    k_plan<R, FB><<<blocks_for(p.count, warps), warps * 32, sm, stream>>>(P, S, p, pl.perm, pl.hosts, pl.fr,
-                                                                         (unsigned)pl.cap, pl.counts, pl.slots, st);
+    const int Sn = FB ? (SC ? SC : P.S) : 1;
+    const size_t head = (size_t)(W * W * W * 4 + 15) / 16 * 16;
+    const size_t wb = (size_t)plan_warp_bytes(W, Sn);
+    int warps = 8;
+    while (warps > 1 && head + warps * wb > 48 * 1024) --warps;
+    const size_t sm = head + warps * wb;
+    int dev = 0, nsm = 152, per_sm = 1;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_plan<R, FB, SC>, warps * 32, sm) != cudaSuccess ||
+        per_sm < 1)
+        per_sm = 1;
+    const long long need = (p.count + warps - 1) / warps;
+    const long long grid = need < (long long)nsm * per_sm ? need : (long long)nsm * per_sm;
+    k_plan<R, FB, SC><<<(unsigned)grid, warps * 32, sm, stream>>>(P, S, p, pl.perm, pl.hosts, pl.fr,
+                                                                   (unsigned)pl.cap, pl.counts, pl.slots, st);
 }
 
 void launch_plan(const KParams &P, const Box &S, const Parts &p, const PlanPtrs &pl, DevStatus *st,
@@ -626,9 +828,13 @@ void launch_plan(const KParams &P, const Box &S, const Parts &p, const PlanPtrs 
 {
     if (p.count == 0) return;
     if (P.kind == PMP_KIND_FEEDBACK) {
-        PMP_DISPATCH_R(P.R, (plan_one<RR, true>(P, S, p, pl, st, stream)));
+        if (P.S == 4) {
+            PMP_DISPATCH_R(P.R, (plan_one<RR, true, 4>(P, S, p, pl, st, stream)));
+        } else {
+            PMP_DISPATCH_R(P.R, (plan_one<RR, true, 0>(P, S, p, pl, st, stream)));
+        }
     } else {
-        PMP_DISPATCH_R(P.R, (plan_one<RR, false>(P, S, p, pl, st, stream)));
+        PMP_DISPATCH_R(P.R, (plan_one<RR, false, 0>(P, S, p, pl, st, stream)));
     }
 }
 
