@@ -22,7 +22,15 @@
  * cells.
  *
  * Build without fused multiply-add (gcc -ffp-contract=off): every product and
- * sum written below is rounded on its own, in the order written.
+ * sum written below is rounded on its own, in the order written, except where
+ * the code calls fma() (C99; x * y + z rounded once).
+ *
+ * Reading (evaluation): the paper fixes FP64 but no evaluation order.  A
+ * product that is added to a running sum or to another term is fused with
+ * that addition where the code says fma(): the gather sums of Sec. 3.2.1 and
+ * the sum of kernel weights of Eq. kernel_wgt, the momentum and energy rows of
+ * Eq. du, and the Step-4 sums of Sec. 2.2.  Everything else is rounded
+ * operation by operation.
  *
  * Readings of points the paper leaves open are marked "Reading:".  Parity of
  * the sub-sampled covered fraction omega and of the code-unit constants A_sf,
@@ -325,8 +333,8 @@ static int gather_feedback_one(const or_params *P, const or_mesh *S, const or_pa
         double U[NF];
         read_state(S, kc[t].wi, kc[t].wj, kc[t].wk, U);
         sw = sw + w;
-        sr = sr + w * U[0];
-        for (int a = 0; a < 3; a++) sp[a] = sp[a] + w * U[1 + a];
+        sr = fma(w, U[0], sr);
+        for (int a = 0; a < 3; a++) sp[a] = fma(w, U[1 + a], sp[a]);
     }
     double V = cell_volume(S->dx);
     double Vsnr = sw * V;
@@ -411,7 +419,8 @@ static int gather_sink_one(const or_params *P, const or_mesh *S, const or_partic
     if (racc > 0.5 * P->r_K) racc = 0.5 * P->r_K;
     double ra2 = racc * racc;
     double sumw = 0.0;
-    for (int t = 0; t < nk; t++) sumw = sumw + kernel_weight(&kc[t], ra2);
+    for (int t = 0; t < nk; t++)
+        sumw = fma(axis_weight(kc[t].d[0], ra2) * axis_weight(kc[t].d[1], ra2), axis_weight(kc[t].d[2], ra2), sumw);
     double V = cell_volume(S->dx);
     double K = ((mdot * P->dt) / V) / sumw;
     G[SK_RHO * stride] = rho_inf;
@@ -465,8 +474,8 @@ static void feedback_delta(double w, const double U[NF], const double *G, int64_
     double pr[3];
     for (int a = 0; a < 3; a++) pr[a] = s * c->d[a];
     dU[0] = w * q;
-    for (int a = 0; a < 3; a++) dU[1 + a] = w * (rn * vc[a] - U[1 + a]) + pr[a];
-    dU[4] = w * e + ((vc[0] * pr[0] + vc[1] * pr[1]) + vc[2] * pr[2]);
+    for (int a = 0; a < 3; a++) dU[1 + a] = fma(w, fma(rn, vc[a], -U[1 + a]), pr[a]);
+    dU[4] = fma(w, e, fma(vc[2], pr[2], fma(vc[1], pr[1], vc[0] * pr[0])));
 }
 
 /* Eq. accretion_function with the Truelove rate folded into the max:
@@ -662,6 +671,16 @@ static double sink_eta(const or_params *P, double dx, const double U[NF], const 
 /* Step 4: limited changes returned to sink particles                        */
 /* ------------------------------------------------------------------------ */
 
+/* One cell's terms of the Step-4 sums: with a = -Delta U_rho (the removal of
+ * Eq. accretion_function) and b = eta a, the mass sum takes -b and the
+ * momentum sums take -b v with v = p / rho, fused (Reading (evaluation)). */
+static void return_add(double eta, const double U[NF], const double dU[NF], double acc[4])
+{
+    double b = eta * (-dU[0]);
+    acc[0] = acc[0] - b;
+    for (int k = 0; k < 3; k++) acc[1 + k] = fma(-b, U[1 + k] / U[0], acc[1 + k]);
+}
+
 /* u_s := u_s - sum_c eta_c Delta U^s_c V, with Delta U^s recomputed exactly as
  * in Step 1 and eta from the pre-update state and the summed buffer of the
  * owning cell (eta at a ghost image is its owner's).  V is common to all
@@ -696,7 +715,7 @@ static int return_parts(const or_params *P, const or_mesh *S, const or_mesh *B, 
             int64_t o = cell_index(B, kc[t].wi, kc[t].wj, kc[t].wk);
             for (int f = 0; f < NF; f++) D[f] = B->u[(int64_t)f * B->fstride + o];
             double eta = sink_eta(P, S->dx, U, D);
-            for (int f = 0; f < 4; f++) acc[f] = acc[f] + eta * dU[f];
+            return_add(eta, U, dU, acc);
         }
         p->m[s] = p->m[s] - acc[0] * V;
         p->px[s] = p->px[s] - acc[1] * V;
@@ -959,7 +978,7 @@ int or_sinks_at(const or_params *P, const or_mesh *S, const or_particles *p, con
             st = folded_at(P, S, p, bins, g, kc2, kc[q].wi, kc[q].wj, kc[q].wk, D, A);
             if (st && !status) status = st;
             double eta = sink_eta(P, S->dx, U, D);
-            for (int f = 0; f < 4; f++) acc[f] = acc[f] + eta * dU[f];
+            return_add(eta, U, dU, acc);
         }
         out[4 * t + 0] = p->m[s] - acc[0] * V;
         out[4 * t + 1] = p->px[s] - acc[1] * V;

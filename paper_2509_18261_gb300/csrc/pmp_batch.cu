@@ -285,12 +285,12 @@ __device__ void gather_particle(const BArgs &a, long long s, SmemT<R> &sm)
                 double U[NF];
                 load5(a.u, o.c, o.fs, U);
                 if (FB) {
-                    const double w = (double)cnt / (double)P.S3;
-                    v0 = w;
-                    v1 = w * U[0];
-                    v2 = w * U[1];
-                    v3 = w * U[2];
-                    v4 = w * U[3];
+                    // omega and the cell's rho, p; lane 0 fuses the products into the sums
+                    v0 = (double)cnt / (double)P.S3;
+                    v1 = U[0];
+                    v2 = U[1];
+                    v3 = U[2];
+                    v4 = U[3];
                 } else {
                     double cs, rtr;
                     sink_cell(P, U, cs, rtr);
@@ -312,11 +312,20 @@ __device__ void gather_particle(const BArgs &a, long long s, SmemT<R> &sm)
         if (lane == 0) {
             for (int l = 0; l < 32; ++l) {
                 if (!((mem >> l) & 1u)) continue;
-                s0 = s0 + red[l][0];
-                s1 = s1 + red[l][1];
-                s2 = s2 + red[l][2];
-                s3 = s3 + red[l][3];
-                s4 = s4 + red[l][4];
+                if (FB) {
+                    const double w = red[l][0];
+                    s0 = s0 + w;
+                    s1 = fma(w, red[l][1], s1);
+                    s2 = fma(w, red[l][2], s2);
+                    s3 = fma(w, red[l][3], s3);
+                    s4 = fma(w, red[l][4], s4);
+                } else {
+                    s0 = s0 + red[l][0];
+                    s1 = s1 + red[l][1];
+                    s2 = s2 + red[l][2];
+                    s3 = s3 + red[l][3];
+                    s4 = s4 + red[l][4];
+                }
             }
             nk += __popc(mem);
         }
@@ -345,19 +354,21 @@ __device__ void gather_particle(const BArgs &a, long long s, SmemT<R> &sm)
     double sumw = 0.0;
     for (int k0 = 0; k0 < W3; k0 += 32) {
         const int k = k0 + lane;
-        double wv = 0.0;
+        double wxy = 0.0, wz = 0.0;
         bool mem = false;
         if (k < W3 && om[k]) {
             const int oz = k / (W * W), oy = (k / W) % W, ox = k % W;
-            wv = (ws[ox] * ws[W + oy]) * ws[2 * W + oz];
+            wxy = ws[ox] * ws[W + oy];
+            wz = ws[2 * W + oz];
             mem = true;
         }
         const unsigned mm = __ballot_sync(kFullMask, mem);
-        red[lane][0] = wv;
+        red[lane][0] = wxy;
+        red[lane][1] = wz;
         __syncwarp();
         if (lane == 0)
             for (int l = 0; l < 32; ++l)
-                if ((mm >> l) & 1u) sumw = sumw + red[l][0];
+                if ((mm >> l) & 1u) sumw = fma(red[l][0], red[l][1], sumw);
         __syncwarp();
     }
     if (lane == 0 && !sink_gather_rows(P, am, sumw, nk, a.G + s, N)) report(a.st, PMP_ERR_NONFINITE, s);
@@ -592,10 +603,11 @@ __device__ void return_sink(const BArgs &a, long long s, SmemT<R> &sm)
             bool img;
             folded_at(a, o.q, o.i, o.j, o.k, D, img);
             const double eta = sink_eta(P, U, D);
-            v0 = eta * dU[0];
-            v1 = eta * dU[1];
-            v2 = eta * dU[2];
-            v3 = eta * dU[3];
+            // b = eta a and v = p / rho; lane 0 fuses -b v into the sums
+            v0 = eta * (-dU[0]);
+            v1 = U[1] / U[0];
+            v2 = U[2] / U[0];
+            v3 = U[3] / U[0];
         }
         const unsigned mm = __ballot_sync(kFullMask, mem);
         red[lane][0] = v0;
@@ -606,10 +618,11 @@ __device__ void return_sink(const BArgs &a, long long s, SmemT<R> &sm)
         if (lane == 0)
             for (int l = 0; l < 32; ++l) {
                 if (!((mm >> l) & 1u)) continue;
-                c0 = c0 + red[l][0];
-                c1 = c1 + red[l][1];
-                c2 = c2 + red[l][2];
-                c3 = c3 + red[l][3];
+                const double b = red[l][0];
+                c0 = c0 - b;
+                c1 = fma(-b, red[l][1], c1);
+                c2 = fma(-b, red[l][2], c2);
+                c3 = fma(-b, red[l][3], c3);
             }
         __syncwarp();
     }

@@ -1,10 +1,14 @@
 // pmp_device.cuh -- device-side building blocks of the PMP library (sm_103a).
 //
 // Everything here is FP64 and is compiled with -fmad=false: each product and
-// sum is rounded on its own, in the order written, so that one quantity has
-// one value whichever kernel computes it (gather, deposit, sorted segment sum,
-// Step 4).  That fixed order is the contract that makes the sorted deposit
-// deterministic.
+// sum is rounded on its own, in the order written, except where the code calls
+// fma() (one rounding), so that one quantity has one value whichever kernel
+// computes it (gather, deposit, sorted segment sum, Step 4).  That fixed order
+// is the contract that makes the sorted deposit deterministic.  Products that
+// feed a running sum or another term are fused where the oracle fuses them:
+// the supernova gather sums, the sum of kernel weights, the momentum and
+// energy rows of Eq. du and the Step-4 sums (a DFMA costs the FP64 pipe what a
+// DADD or DMUL costs).
 #pragma once
 
 #include <cstdint>
@@ -353,10 +357,10 @@ __device__ __forceinline__ void feedback_delta(double w, const double U[NF], dou
     const double s = dd > 0.0 ? (w * Pv) / dist : 0.0;
     const double pr0 = s * d0, pr1 = s * d1, pr2 = s * d2;
     dU[0] = w * q;
-    dU[1] = w * (rn * vc[0] - U[1]) + pr0;
-    dU[2] = w * (rn * vc[1] - U[2]) + pr1;
-    dU[3] = w * (rn * vc[2] - U[3]) + pr2;
-    dU[4] = w * e + ((vc[0] * pr0 + vc[1] * pr1) + vc[2] * pr2);
+    dU[1] = fma(w, fma(rn, vc[0], -U[1]), pr0);
+    dU[2] = fma(w, fma(rn, vc[1], -U[2]), pr1);
+    dU[3] = fma(w, fma(rn, vc[2], -U[3]), pr2);
+    dU[4] = fma(w, e, fma(vc[2], pr2, fma(vc[1], pr1, vc[0] * pr0)));
 }
 
 // Sink deposition function (Eq. accretion_function with the Truelove rate in

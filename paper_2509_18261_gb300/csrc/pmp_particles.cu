@@ -348,8 +348,8 @@ constexpr int kMaxS3 = kMaxS * kMaxS * kMaxS;
 // Pairs whose loads a per-particle loop issues together.
 constexpr int kUnroll = 4;
 
-// One kernel cell's terms of the supernova gather sums (omega = 1 skips the
-// products: 1 * v == v).
+// One kernel cell's terms of the supernova gather sums, products fused into
+// the sums (omega = 1 skips the products: fma(1, v, s) == s + v).
 __device__ __forceinline__ void fb_gather_add(const KParams &P, const double *wtab, int cnt, const double U[NF],
                                               double &sw, double &sr, double &sp0, double &sp1, double &sp2)
 {
@@ -362,10 +362,10 @@ __device__ __forceinline__ void fb_gather_add(const KParams &P, const double *wt
     } else {
         const double w = wtab[cnt];
         sw = sw + w;
-        sr = sr + w * U[0];
-        sp0 = sp0 + w * U[1];
-        sp1 = sp1 + w * U[2];
-        sp2 = sp2 + w * U[3];
+        sr = fma(w, U[0], sr);
+        sp0 = fma(w, U[1], sp0);
+        sp1 = fma(w, U[2], sp1);
+        sp2 = fma(w, U[3], sp2);
     }
 }
 
@@ -486,7 +486,7 @@ __global__ void __launch_bounds__(128) k_gather_sink(KParams P, Box S, const dou
     double sumw = 0.0;
     for (unsigned q = 0; q < nc; ++q) {
         const PairCell c = unpack_pair(pl.slots[b0 + q], P.R);
-        sumw = sumw + (ws[c.i - hx + R] * ws[W + c.j - hy + R]) * ws[2 * W + c.k - hz + R];
+        sumw = fma(ws[c.i - hx + R] * ws[W + c.j - hy + R], ws[2 * W + c.k - hz + R], sumw);
     }
     if (!sink_gather_rows(P, am, sumw, nk, G + s, gs)) report(st, PMP_ERR_NONFINITE, s);
 }
@@ -709,26 +709,20 @@ __global__ void __launch_bounds__(128) k_segment_sum(KParams P, Box S, const dou
 // Step 4: limited changes returned to sinks
 // ---------------------------------------------------------------------------
 
-// One kernel cell's terms of the Step-4 sums: the pair's Delta U (mass and
-// momentum rows of sink_pair_delta, from D record d0 = (rho - rho_Tr, p_x/rho),
-// d1 = (p_y/rho, p_z/rho)) times the cell's eta e.
+// One kernel cell's terms of the Step-4 sums: the pair's removal a (as in
+// sink_pair_delta, from D record d0 = (rho - rho_Tr, p_x/rho), d1 = (p_y/rho,
+// p_z/rho)) limited by the cell's eta e, b = e a; the mass sum takes -b, the
+// momentum sums take -b v, fused.
 __device__ __forceinline__ void sink_return_add(double K, double w, double2 d0, double2 d1, double e, double &a0,
                                                 double &a1, double &a2, double &a3)
 {
     const double bh = K * w;
     const double a = bh >= d0.x ? bh : d0.x;
-    const double u0 = -a, u1 = -(a * d0.y), u2 = -(a * d1.x), u3 = -(a * d1.y);
-    if (e == 1.0) {
-        a0 = a0 + u0;
-        a1 = a1 + u1;
-        a2 = a2 + u2;
-        a3 = a3 + u3;
-    } else {
-        a0 = a0 + e * u0;
-        a1 = a1 + e * u1;
-        a2 = a2 + e * u2;
-        a3 = a3 + e * u3;
-    }
+    const double b = e == 1.0 ? a : e * a;
+    a0 = a0 - b;
+    a1 = fma(-b, d0.y, a1);
+    a2 = fma(-b, d1.x, a2);
+    a3 = fma(-b, d1.y, a3);
 }
 
 template <int R>
