@@ -47,7 +47,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--mode", default="atomic", choices=["atomic", "sorted"])
-    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--e2e-steps", type=int, default=4)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--cpu-sample-n", type=int, default=128)
@@ -359,33 +359,9 @@ def run_ours(args, world, rank, local):
     lim_fb = pmp.pmp_limiter_counts(P_fb.ctx)
     lim_sk = pmp.pmp_limiter_counts(P_sk.ctx)
 
-    # e2e: pinned host inputs -> device -> cycle -> results back to pinned host
-    h_state = torch.from_numpy(w["state"]).pin_memory()
-    h_fb = {k: torch.from_numpy(v).pin_memory() for k, v in w["fb"].items()}
-    h_sk = {k: torch.from_numpy(v).pin_memory() for k, v in w["sink"].items()}
-    o_state = torch.empty_like(h_state).pin_memory()
-    o_sk = {k: torch.empty_like(h_sk[k]).pin_memory() for k in ("m", "px", "py", "pz")}
-    bi = h_state.numel() * 8 + sum(v.numel() * 8 for v in h_fb.values()) + sum(v.numel() * 8 for v in h_sk.values())
-    bo = o_state.numel() * 8 + sum(v.numel() * 8 for v in o_sk.values())
-    barrier(world)
-    torch.cuda.synchronize()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(max(args.e2e_steps, 1)):
-        state.copy_(h_state, non_blocking=True)
-        for k in h_fb:
-            fb[k].copy_(h_fb[k], non_blocking=True)
-        for k in h_sk:
-            sk[k].copy_(h_sk[k], non_blocking=True)
-        cycle(restore_state=False)
-        o_state.copy_(state, non_blocking=True)
-        for k in o_sk:
-            o_sk[k].copy_(sk[k], non_blocking=True)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    barrier(world)
-    e2e_ms = max_over_ranks(world, e0.elapsed_time(e1) / max(args.e2e_steps, 1))
+    # e2e: pinned host inputs -> device -> cycle -> results back to pinned host,
+    # every step, through the public calls
+    e2e = end_to_end(args, w, world, state, fb, sk, P_fb, P_sk, cycle, stream)
 
     # roofline of the dominant kernel (per-launch time from the library's
     # CUDA events on the launching stream)
@@ -423,18 +399,161 @@ def run_ours(args, world, rank, local):
         "kernels_ms_per_launch": {k: round(v[1], 4) for k, v in sorted(kernel_ms.items())},
         "limiter": {"fb_cells_eta_lt_1": lim_fb[0], "fb_noroot": lim_fb[1], "sink_cells_eta_lt_1": lim_sk[0]},
         "roofline": roof,
-        "e2e": {"value": n_particles * world / (e2e_ms * 1e-3), "unit": "particles/s",
-                "ms_per_step": e2e_ms, "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo},
+        "e2e": e2e,
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clk,
     }
+    result["pm_deposit_c5_512"] = pm_deposit(args, w, state, fb, stream)
     result["fwd_bwd_c4_128"] = fwd_bwd(args)
     if not args.no_batched:
         result["batched_c3"] = batched(args)
+        result["deposit_modes_c2_256"] = deposit_modes(args)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         result["cpu_baseline"] = cpu_baseline(args)
     if rank == 0:
         print(json.dumps(result), flush=True)
+
+
+def end_to_end(args, w, world, state, fb, sk, P_fb, P_sk, cycle, stream):
+    """The cycle measured from pinned host memory to pinned host memory: every
+    step copies its inputs (gas state, both particle sets) to the device, runs
+    the two passes and copies the results (gas state, sink masses and
+    momenta) back.  Double-buffered: two device input sets; the copies of step
+    k+1 (in) and k-1 (out) run on two copy streams while step k computes, each
+    copy ordered after the work it depends on by events.  Also reported: the
+    same steps run one after another on one stream (serial_ms_per_step)."""
+    import torch
+
+    from paper_2509_18261_gb300 import pmp
+
+    h_state = torch.from_numpy(w["state"]).pin_memory()
+    h_fb = {k: torch.from_numpy(v).pin_memory() for k, v in w["fb"].items()}
+    h_sk = {k: torch.from_numpy(v).pin_memory() for k, v in w["sink"].items()}
+    outs = [dict(state=torch.empty_like(h_state).pin_memory(),
+                 sk={k: torch.empty_like(h_sk[k]).pin_memory() for k in ("m", "px", "py", "pz")}) for _ in range(2)]
+    bi = h_state.numel() * 8 + sum(v.numel() * 8 for v in h_fb.values()) + sum(v.numel() * 8 for v in h_sk.values())
+    bo = h_state.numel() * 8 + sum(v.numel() * 8 for v in outs[0]["sk"].values())
+    steps = max(args.e2e_steps, 2)
+
+    def copy_in(st, f, k_):
+        st.copy_(h_state, non_blocking=True)
+        for k in h_fb:
+            f[k].copy_(h_fb[k], non_blocking=True)
+        for k in h_sk:
+            k_[k].copy_(h_sk[k], non_blocking=True)
+
+    def copy_out(o, st, k_):
+        o["state"].copy_(st, non_blocking=True)
+        for k in o["sk"]:
+            o["sk"][k].copy_(k_[k], non_blocking=True)
+
+    def run_passes(ps):
+        for P, parts in ps:
+            c = P.ctx
+            pmp.pmp_zero_buffer(c, P.buffer)
+            pmp.pmp_gather(c, P.state, parts, P.gathered, args.mode, P.workspace)
+            pmp.pmp_deposit(c, P.state, parts, P.gathered, P.buffer, args.mode, P.workspace)
+            pmp.pmp_fold_ghosts(c, P.buffer)
+            pmp.pmp_apply_limited(c, P.state, P.buffer, parts, P.gathered, None, P.workspace)
+
+    # serial: copy in, cycle, copy out, all on the compute stream
+    barrier(world)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        copy_in(state, fb, sk)
+        run_passes(((P_fb, fb), (P_sk, sk)))
+        copy_out(outs[0], state, sk)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    serial_ms = max_over_ranks(world, e0.elapsed_time(e1) / steps)
+
+    # double-buffered: a second device input set with its own passes
+    st1 = torch.empty_like(state)
+    fb1 = {k: torch.empty_like(v) for k, v in fb.items()}
+    sk1 = {k: torch.empty_like(v) for k, v in sk.items()}
+    mode = args.mode
+    Q_fb = pmp.Pass(w["fb_params"], P_fb.box, st1, fb1, mode=mode)
+    Q_sk = pmp.Pass(w["sink_params"], P_sk.box, st1, sk1, mode=mode)
+    sets = [(state, fb, sk, ((P_fb, fb), (P_sk, sk))), (st1, fb1, sk1, ((Q_fb, fb1), (Q_sk, sk1)))]
+    s_in, s_out = torch.cuda.Stream(), torch.cuda.Stream()
+    ev_in = [torch.cuda.Event() for _ in range(2)]
+    ev_done = [torch.cuda.Event() for _ in range(2)]
+    ev_out = [torch.cuda.Event() for _ in range(2)]
+    out_used = [False, False]
+    barrier(world)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    s_in.wait_event(e0)
+    with torch.cuda.stream(s_in):
+        copy_in(*sets[0][:3])
+        ev_in[0].record(s_in)
+    for k in range(steps):
+        i, j = k % 2, (k + 1) % 2
+        if k + 1 < steps:
+            with torch.cuda.stream(s_in):
+                if out_used[j]:
+                    s_in.wait_event(ev_out[j])  # set j's results have left the device
+                copy_in(*sets[j][:3])
+                ev_in[j].record(s_in)
+        stream.wait_event(ev_in[i])
+        run_passes(sets[i][3])
+        ev_done[i].record(stream)
+        with torch.cuda.stream(s_out):
+            s_out.wait_event(ev_done[i])
+            copy_out(outs[i], sets[i][0], sets[i][2])
+            ev_out[i].record(s_out)
+        out_used[i] = True
+    for i in range(2):
+        if out_used[i]:
+            stream.wait_event(ev_out[i])
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = max_over_ranks(world, e0.elapsed_time(e1) / steps)
+    for P in (Q_fb, Q_sk):
+        code, idx = pmp.pmp_get_error(P.ctx)
+        if code:
+            raise RuntimeError(f"e2e: device error {code} at {idx}")
+        P.ctx.close()
+    n_particles = sum(v.numel() for v in (fb["x"], sk["x"]))
+    return {"value": n_particles * world / (ms * 1e-3), "unit": "particles/s", "ms_per_step": ms,
+            "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo, "steps": steps,
+            "serial_ms_per_step": serial_ms,
+            "overlap": "double-buffered: the copies of step k+1 (in) and k-1 (out) run on copy streams during step k"}
+
+
+def pm_deposit(args, w, state, fb, stream):
+    """The particle-mesh (PM/PIC) subset of the cycle, Steps 1, 2 and 5 of
+    Sec. 2.2: the 14,680,064 supernova particles of the 512^3 workload
+    deposited as mass, momentum and energy with the supernova kernel (r_K = 2,
+    S = 4) and added to the state without a limiter.  CUDA-event time of one
+    pass, mean over `steps` after 3 warm-ups (the state keeps accumulating;
+    the work per pass is the same)."""
+    import torch
+
+    from paper_2509_18261_gb300 import pmp
+    from paper_2509_18261_gb300 import synthetic as syn
+
+    P = pmp.Pass(syn.mass_params(), w["box"], state, fb, mode=args.mode)
+    times = []
+    for it in range(3 + max(args.steps, 1)):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        P.run()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if it >= 3:
+            times.append(e0.elapsed_time(e1))
+    code, idx = pmp.pmp_get_error(P.ctx)
+    if code:
+        raise RuntimeError(f"pm deposit: device error {code} at {idx}")
+    P.ctx.close()
+    ms = sum(times) / len(times)
+    n = fb["x"].numel()
+    return {"ms_per_pass": ms, "particles_per_s": n / (ms * 1e-3),
+            "cells_per_s": w["box"].ncells_valid / (ms * 1e-3), "particles": n, "mode": args.mode}
 
 
 def fwd_bwd(args):
@@ -478,6 +597,69 @@ def fwd_bwd(args):
     fm, bm = sum(f_ms) / len(f_ms), sum(b_ms) / len(b_ms)
     return {"fwd_ms": fm, "bwd_ms": bm, "total_ms": fm + bm, "particles": n,
             "workload": "c4_128: 128^3, 4 ghosts, 262,144 supernovae (half in 32 Plummer clusters)"}
+
+
+def deposit_modes(args):
+    """Step 1 on the 256^3 workload (1,048,576 supernovae, half in 32 Plummer
+    clusters) in the three accumulation modes: CUDA-event time of pmp_deposit
+    (ATOMIC; SORTED with its pair sort; ROUNDED with its error bound and the
+    rounding pass of App. A.1), mean of `steps` calls after 3 warm-ups.  Then
+    the reproducibility of each mode: buffer values (of cells some particle
+    reaches) that differ between two runs on the same input, and between the
+    input and the same particles in a seeded random order."""
+    import torch
+
+    from paper_2509_18261_gb300 import pmp
+    from paper_2509_18261_gb300 import synthetic as syn
+
+    w = syn.make_workload("c2_256")
+    box = w["box"]
+    st = torch.from_numpy(w["state"]).cuda()
+    parts = pmp.parts_to_device(w["fb"])
+    n = parts["x"].numel()
+    gen = torch.Generator(device="cuda").manual_seed(2509)
+    perm = torch.randperm(n, device="cuda", generator=gen)
+    parts2 = {k: v[perm].contiguous() for k, v in parts.items()}
+    stream = torch.cuda.current_stream()
+    out = {"workload": "c2_256: 256^3, 4 ghosts, 1,048,576 supernovae (half in 32 Plummer clusters), Step 1 only",
+           "ms": {}, "differing_values_between_orders": {}}
+    touched = None
+    out["differing_values_between_runs"] = {}
+    for mode, M in (("atomic", None), ("sorted", None), ("rounded", 28), ("rounded", 16), ("rounded", 8)):
+        bufs = []
+        for pp, timed in ((parts, M in (None, 28)), (parts, False), (parts2, False)):
+            ps = pmp.Pass(w["fb_params"], box, st, pp, mode=mode)
+            if M is not None:
+                pmp.pmp_set_rounding_margin(ps.ctx, M)
+            c = ps.ctx
+            pmp.pmp_gather(c, ps.state, pp, ps.gathered, mode, ps.workspace)
+            times = []
+            for it in range(3 + (max(args.steps, 1) if timed else 0)):
+                pmp.pmp_zero_buffer(c, ps.buffer)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                pmp.pmp_deposit(c, ps.state, pp, ps.gathered, ps.buffer, mode, ps.workspace)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                if it >= 3:
+                    times.append(e0.elapsed_time(e1))
+            code, idx = pmp.pmp_get_error(c)
+            if code:
+                raise RuntimeError(f"deposit modes: device error {code} at {idx}")
+            if times:
+                out["ms"][mode] = sum(times) / len(times)
+            bufs.append(ps.buffer.data.clone())
+            c.close()
+        a, a2, b = bufs
+        if touched is None:
+            touched = a != 0
+        key = mode if M is None else f"rounded_M{M}"
+        out["differing_values_between_runs"][key] = int(((a.view(torch.int64) != a2.view(torch.int64)) & touched)
+                                                        .sum().item())
+        out["differing_values_between_orders"][key] = int(((a.view(torch.int64) != b.view(torch.int64)) & touched)
+                                                          .sum().item())
+    out["touched_values"] = int(touched.sum().item())
+    return out
 
 
 def batched(args):

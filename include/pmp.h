@@ -57,11 +57,15 @@
  *                  regime (0 EJ, 1 ST, 2 MC)                     (Sec. 3.2.1)
  *   sink (8):      rho_inf, v_inf, c_inf, mdot_BH, r_acc (cell units), sum w,
  *                  K = mdot_BH dt / V / sum w, kernel cell count  (Sec. 3.1.1)
+ *   mass (6):      V_K = sum omega V, then m, p_x, p_y, p_z, e divided by V_K
  *
- * Numerics.  All arithmetic is FP64 with no fused multiply-add, in one fixed
- * order per quantity, so the sorted deposit is bit-for-bit reproducible
- * across runs and launch shapes.  exp and log are the library's own
- * (Cody & Waite reduction plus a Taylor / atanh series).
+ * Numerics.  All arithmetic is FP64 in one fixed order per quantity, so the
+ * sorted deposit is bit-for-bit reproducible across runs and launch shapes.
+ * Products are rounded on their own except in four places, where a product
+ * and the addition it feeds are fused (one rounding): the supernova gather
+ * sums, the sum of the sink kernel weights, the momentum and energy rows of
+ * Eq. du, and the Step-4 sums.  exp and log are the library's own (Cody &
+ * Waite reduction plus a Taylor / atanh series).
  */
 #ifndef PMP_H
 #define PMP_H
@@ -87,14 +91,31 @@ typedef enum {
     PMP_ERR_CUDA = 7              /* a CUDA runtime call failed */
 } pmp_status;
 
-typedef enum { PMP_KIND_FEEDBACK = 0, PMP_KIND_SINK = 1 } pmp_kind;
+/* Interaction kinds.  MASS is the particle-mesh (PM / PIC) deposit of Sec. 2.2,
+ * which needs Steps 1, 2 and 5 only: no limiter and no particle update.  A
+ * MASS particle spreads its mass, momentum and energy content (m, p, e) over
+ * its kernel cells in proportion to the covered fraction omega of the
+ * supernova kernel (r_K, subsample), Delta U_c = omega_c (m, p, e) / V_K with
+ * V_K = sum_c omega_c V, so sum_c Delta U_c V = (m, p, e).  (The paper names
+ * no assignment function for this use.)  `e` may be NULL (no energy). */
+typedef enum { PMP_KIND_FEEDBACK = 0, PMP_KIND_SINK = 1, PMP_KIND_MASS = 2 } pmp_kind;
 
 /* Step-1 accumulation strategy.
- * ATOMIC: FP64 atomic additions (Sec. 2.2, Step 1); per cell the sum equals
- *         the sorted one up to the order of additions.
- * SORTED: (cell, particle) pairs sorted by cell, then each cell summed in
- *         particle-index order; deterministic. */
-typedef enum { PMP_MODE_ATOMIC = 0, PMP_MODE_SORTED = 1 } pmp_mode;
+ * ATOMIC:  FP64 atomic additions (Sec. 2.2, Step 1); per cell the sum equals
+ *          the sorted one up to the order of additions.
+ * SORTED:  (cell, particle) pairs sorted by cell, then each cell summed in
+ *          particle-index order; deterministic.
+ * ROUNDED: the paper's reproducible atomics (App. A.1).  Each atomic
+ *          addition to a buffer value also adds eps |new value| (eps = 2^-52)
+ *          to an error bound E of that value; after the last particle every
+ *          buffer value v (ghost cells included) loses the low
+ *          N_bit = ceil(log2(E / |v|)) + 52 + M bits of its significand
+ *          (N_bit clamped to [0, 52]; truncation toward zero; v = 0 or E = 0
+ *          unchanged).  Two runs that add in different orders then agree bit
+ *          for bit except with probability about 2^-M per value that several
+ *          particles reach.  M is the context's (pmp_set_rounding_margin,
+ *          28 by default).  E lives in the workspace. */
+typedef enum { PMP_MODE_ATOMIC = 0, PMP_MODE_SORTED = 1, PMP_MODE_ROUNDED = 2 } pmp_mode;
 
 typedef struct {
     int32_t n[3];        /* valid cells per axis, >= 1 */
@@ -146,12 +167,18 @@ void pmp_destroy(pmp_ctx *ctx);
 /* Changes the stream later calls enqueue on. */
 pmp_status pmp_set_stream(pmp_ctx *ctx, pmp_stream stream);
 
-/* Number of gathered rows for a kind (12 feedback, 8 sink); 0 if unknown. */
+/* Sets the safety margin M of the ROUNDED deposit (App. A.1; 0 <= M <= 104,
+ * else PMP_ERR_ARG).  Host only; applies to later pmp_deposit calls. */
+pmp_status pmp_set_rounding_margin(pmp_ctx *ctx, int32_t M);
+
+/* Number of gathered rows for a kind (12 feedback, 8 sink, 6 mass); 0 if unknown. */
 int32_t pmp_gathered_rows(int32_t kind);
 
 /* Bytes of device workspace one pass needs for `n_particles` particles of
  * the context's kind on a mesh with the buffer's n, with the deposit
- * strategy `mode`.  Host only, no device work. */
+ * strategy `mode` (ROUNDED adds 5 x field_stride doubles for the error
+ * bound, so it depends on the buffer's field_stride too).  Host only, no
+ * device work. */
 pmp_status pmp_workspace_size(const pmp_ctx *ctx, const pmp_mesh *buffer, int64_t n_particles, int32_t mode,
                               size_t *bytes);
 
@@ -180,7 +207,9 @@ pmp_status pmp_gather(pmp_ctx *ctx, const pmp_mesh *state, const pmp_particles *
  * ghost zones included, on top of what the buffer holds.  `workspace` must
  * hold the plan of the preceding pmp_gather on these particles with the same
  * `mode` (else PMP_ERR_WORKSPACE).  ATOMIC uses FP64 atomics; SORTED
- * synchronises the stream once to read the pair count.  Kernel cells with
+ * synchronises the stream once to read the pair count; ROUNDED zeroes its
+ * error bound, adds with atomics and then rounds every buffer value, so the
+ * buffer should start from zero (pmp_zero_buffer).  Kernel cells with
  * omega = 0 receive nothing. */
 pmp_status pmp_deposit(pmp_ctx *ctx, const pmp_mesh *state, const pmp_particles *particles, const double *gathered,
                        pmp_mesh *buffer, int32_t mode, void *workspace, size_t workspace_bytes);
@@ -223,6 +252,28 @@ pmp_status pmp_apply_limited(pmp_ctx *ctx, pmp_mesh *state, const pmp_mesh *buff
 pmp_status pmp_backward(pmp_ctx *ctx, const pmp_mesh *state_in, const pmp_mesh *buffer, const pmp_particles *particles,
                         const double *gathered, const double *gU, double *g_out, void *workspace,
                         size_t workspace_bytes);
+
+/* Sink creation (Sec. 3.1.2), for a SINK context after its accretion pass,
+ * with that pass's summed buffer retained (Sec. 3.1, item 2).  A valid cell
+ * becomes a new sink when (a) rho > rho_Tr (Eq. truelove with the cell's own
+ * c_s), (b) rho is strictly larger than at every other cell whose centre
+ * lies within r_K (periodic images on periodic axes), and (c) the buffer is
+ * zero in every field at the cell, i.e. no sink's kernel reaches it (the
+ * paper's way of keeping new sinks out of r_K of existing ones).  All three
+ * are tested on the state as it was before any creation.  The qualifying
+ * cells, in cell order (z slowest, x fastest), give sinks 0, 1, ...: at the
+ * cell centre, with m_s = (rho - rho_Tr) V and p_s = m_s v (v = p / rho of
+ * the cell); the cell keeps its velocity and specific energy: rho := rho_Tr,
+ * p := rho_Tr v, E := rho_Tr E / rho.
+ * x..pz: device arrays of `capacity` entries receiving the new sinks; only
+ * the first `capacity` qualifying cells are created, the others are left
+ * as they are.  *count (device int64) receives the number of qualifying
+ * cells.  workspace: device, 256-byte aligned, at least
+ * pmp_create_sinks_workspace_size bytes.  Enqueued on the context's stream. */
+pmp_status pmp_create_sinks_workspace_size(const pmp_ctx *ctx, const pmp_mesh *state, size_t *bytes);
+pmp_status pmp_create_sinks(pmp_ctx *ctx, pmp_mesh *state, const pmp_mesh *buffer, int64_t capacity, double *x,
+                            double *y, double *z, double *m, double *px, double *py, double *pz, int64_t *count,
+                            void *workspace, size_t workspace_bytes);
 
 /* Synchronises the context's stream, then returns the first device error
  * since the last call (PMP_OK if none) in *code and the index of the

@@ -27,9 +27,10 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "pmp_oracle.c")
 _LIB = os.path.join(_HERE, "_build", "liboracle.so")
 
-KIND = {"feedback": 0, "sink": 1}
+KIND = {"feedback": 0, "sink": 1, "mass": 2}
 FB_ROWS = ["M_snr", "V_snr", "vcom_x", "vcom_y", "vcom_z", "n_H", "R_M", "p_rad", "q", "e", "Pv", "regime"]
 SK_ROWS = ["rho_inf", "v_inf", "c_inf", "mdot", "r_acc", "sum_w", "K", "n_mem"]
+MS_ROWS = ["V_K", "q_m", "q_px", "q_py", "q_pz", "q_e"]
 STATUS = {0: "ok", 1: "bad argument", 2: "particle outside", 3: "non-finite", 4: "out of memory"}
 
 
@@ -146,7 +147,7 @@ def _check(st, what, strict=True):
 
 
 def rows(kind):
-    return FB_ROWS if kind == "feedback" else SK_ROWS
+    return FB_ROWS if kind == "feedback" else (SK_ROWS if kind == "sink" else MS_ROWS)
 
 
 def exp(x):
@@ -178,6 +179,39 @@ def deposit(params, box, state, parts, gathered, buf, absbuf=None, dx=1.0, perio
     st = lib().or_deposit(ctypes.byref(P), ctypes.byref(S), ctypes.byref(pp), _dp(gathered), ctypes.byref(B),
                           _dp(absbuf))
     return _check(st, "deposit", strict)
+
+
+def deposit_rounded(params, box, state, parts, gathered, buf, M=28, dx=1.0, periodic=(1, 1, 1), strict=True):
+    """Step 1 with the reproducible atomics of App. A.1 (index order): adds
+    into ``buf``, then rounds every buffer value; returns the error bound E."""
+    P = make_params(params)
+    S = make_mesh(box, state, dx, periodic)
+    B = make_mesh(box, buf, dx, periodic)
+    pp = make_particles(parts)
+    E = np.zeros_like(buf)
+    st = lib().or_deposit_rounded(ctypes.byref(P), ctypes.byref(S), ctypes.byref(pp), _dp(gathered), ctypes.byref(B),
+                                  int(M), _dp(E))
+    _check(st, "deposit_rounded", strict)
+    return E
+
+
+def create_sinks(params, box, state, buf, cap=None, dx=1.0, periodic=(1, 1, 1)):
+    """Sink creation after an accretion pass (Sec. 3.1.2), ``state`` updated
+    in place; returns (count, new sinks dict x, y, z, m, px, py, pz)."""
+    P = make_params(params)
+    S = make_mesh(box, state, dx, periodic)
+    B = make_mesh(box, buf, dx, periodic)
+    if cap is None:
+        cap = box.ncells_valid
+    out = {k: np.zeros(max(cap, 1)) for k in ("x", "y", "z", "m", "px", "py", "pz")}
+    L = lib()
+    L.or_create_sinks.restype = ctypes.c_int64
+    n = L.or_create_sinks(ctypes.byref(P), ctypes.byref(S), ctypes.byref(B), ctypes.c_int64(cap),
+                          *[_dp(out[k]) for k in ("x", "y", "z", "m", "px", "py", "pz")])
+    if n < 0:
+        raise OracleError("create_sinks failed")
+    k = min(n, cap)
+    return n, {key: v[:k].copy() for key, v in out.items()}
 
 
 def fold(box, buf, absbuf=None, periodic=(1, 1, 1)):

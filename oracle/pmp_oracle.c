@@ -44,7 +44,7 @@
 #define NF 5
 #define OR_PI 3.141592653589793
 
-enum { KIND_FEEDBACK = 0, KIND_SINK = 1 };
+enum { KIND_FEEDBACK = 0, KIND_SINK = 1, KIND_MASS = 2 };
 
 /* status codes returned by every entry point */
 enum { OR_OK = 0, OR_ERR_ARG = 1, OR_ERR_OUTSIDE = 2, OR_ERR_NONFINITE = 3, OR_ERR_NOMEM = 4 };
@@ -292,10 +292,13 @@ static void sink_cell(const or_params *P, double dx, const double U[NF], double 
 /* Gathered rows, [rows][count] */
 #define FB_ROWS 12
 #define SK_ROWS 8
+#define MS_ROWS 6
+#define MAX_ROWS 12
 enum { FB_MSNR = 0, FB_VSNR, FB_VX, FB_VY, FB_VZ, FB_NH, FB_RM, FB_PRAD, FB_Q, FB_E, FB_PV, FB_REGIME };
 enum { SK_RHO = 0, SK_VINF, SK_CINF, SK_MDOT, SK_RACC, SK_SUMW, SK_K, SK_NMEM };
+enum { MS_VK = 0, MS_Q };  /* V_K, then the five per-volume amounts q_f */
 
-int or_gathered_rows(int kind) { return kind == KIND_FEEDBACK ? FB_ROWS : SK_ROWS; }
+int or_gathered_rows(int kind) { return kind == KIND_FEEDBACK ? FB_ROWS : (kind == KIND_SINK ? SK_ROWS : MS_ROWS); }
 
 static kcell *alloc_kcells(double rK)
 {
@@ -435,6 +438,44 @@ static int gather_sink_one(const or_params *P, const or_mesh *S, const or_partic
     return OR_OK;
 }
 
+/* Particle-mesh (PM/PIC) deposit, the step subset of Sec. 2.2 that uses Steps
+ * 1, 2 and 5 only: a particle spreads its mass, momentum and energy content
+ * over its kernel cells in proportion to the covered fraction omega.
+ * Reading: the paper names no assignment function for this use; the kernel
+ * and omega are those of the supernova deposit (Sec. 3.2.1), so that
+ * sum_c Delta U_c V returns (m, p, e) and no cell outside r_K is touched.
+ * V_K = sum omega V; q_f = (m, p_x, p_y, p_z, e)_f / V_K (e = 0 if the
+ * particles carry no energy). */
+static int gather_mass_one(const or_params *P, const or_mesh *S, const or_particles *p, int64_t s, kcell *kc,
+                           double *G, int64_t stride)
+{
+    double x = p->x[s], y = p->y[s], z = p->z[s];
+    int st = check_position(S, x, y, z);
+    if (st) return st;
+    int S3 = P->subsample * P->subsample * P->subsample;
+    double r2 = P->r_K * P->r_K;
+    int nk = kernel_cells(S, P->r_K, x, y, z, kc);
+    double sw = 0.0;
+    for (int t = 0; t < nk; t++) {
+        int64_t cnt = covered_subpoints(P->subsample, r2, kc[t].ci, kc[t].cj, kc[t].ck, x, y, z);
+        if (cnt == 0) continue;
+        sw = sw + (double)cnt / (double)S3;
+    }
+    double VK = sw * cell_volume(S->dx);
+    double u[NF] = {p->m[s], p->px[s], p->py[s], p->pz[s], p->e ? p->e[s] : 0.0};
+    G[MS_VK * stride] = VK;
+    for (int f = 0; f < NF; f++) G[(MS_Q + f) * stride] = u[f] / VK;
+    return OR_OK;
+}
+
+static int gather_one(const or_params *P, const or_mesh *S, const or_particles *p, int64_t s, kcell *kc, double *G,
+                      int64_t stride)
+{
+    if (P->kind == KIND_FEEDBACK) return gather_feedback_one(P, S, p, s, kc, G, stride);
+    if (P->kind == KIND_SINK) return gather_sink_one(P, S, p, s, kc, G, stride);
+    return gather_mass_one(P, S, p, s, kc, G, stride);
+}
+
 int or_gather(const or_params *P, const or_mesh *S, const or_particles *p, double *gathered)
 {
     if (!P || !S || !p || !gathered) return OR_ERR_ARG;
@@ -442,8 +483,7 @@ int or_gather(const or_params *P, const or_mesh *S, const or_particles *p, doubl
     if (!kc) return OR_ERR_NOMEM;
     int status = OR_OK;
     for (int64_t s = 0; s < p->count; s++) {
-        int st = P->kind == KIND_FEEDBACK ? gather_feedback_one(P, S, p, s, kc, gathered + s, p->count)
-                                          : gather_sink_one(P, S, p, s, kc, gathered + s, p->count);
+        int st = gather_one(P, S, p, s, kc, gathered + s, p->count);
         if (st && !status) status = st;
     }
     free(kc);
@@ -497,10 +537,25 @@ static void sink_delta(const or_params *P, double dx, const double U[NF], const 
     dU[4] = -(a * (U[4] / U[0]));
 }
 
+/* Particle-mesh deposit: Delta U_c = omega q (every row). */
+static void mass_delta(double w, const double *G, int64_t stride, double dU[NF])
+{
+    for (int f = 0; f < NF; f++) dU[f] = w * G[(MS_Q + f) * stride];
+}
+
+/* Delta U^s_c of the context's kind (w = omega; 1 for sinks). */
+static void kind_delta(const or_params *P, double dx, double w, const double U[NF], const double *G, int64_t stride,
+                       const kcell *c, double dU[NF])
+{
+    if (P->kind == KIND_FEEDBACK) feedback_delta(w, U, G, stride, c, dU);
+    else if (P->kind == KIND_SINK) sink_delta(P, dx, U, G, stride, c, dU);
+    else mass_delta(w, G, stride, dU);
+}
+
 /* Covered fraction of a kernel cell (1 for sinks). */
 static double cell_fraction(const or_params *P, const kcell *c, double x, double y, double z)
 {
-    if (P->kind != KIND_FEEDBACK) return 1.0;
+    if (P->kind == KIND_SINK) return 1.0;
     int S = P->subsample;
     int64_t cnt = covered_subpoints(S, P->r_K * P->r_K, c->ci, c->cj, c->ck, x, y, z);
     return (double)cnt / (double)(S * S * S);
@@ -517,6 +572,8 @@ static double cell_fraction(const or_params *P, const kcell *c, double x, double
  * with omega = 0 receive nothing. */
 static int deposit_parts(const or_params *P, const or_mesh *S, const or_particles *p, const double *gathered,
                          int64_t gstride, or_mesh *B, double *absbuf);
+static int deposit_parts_e(const or_params *P, const or_mesh *S, const or_particles *p, const double *gathered,
+                           int64_t gstride, or_mesh *B, double *absbuf, double *ebuf);
 
 int or_deposit(const or_params *P, const or_mesh *S, const or_particles *p, const double *gathered, or_mesh *B,
                double *absbuf)
@@ -526,9 +583,63 @@ int or_deposit(const or_params *P, const or_mesh *S, const or_particles *p, cons
     return deposit_parts(P, S, p, gathered, p->count, B, absbuf);
 }
 
+/* App. A.1, step 4: a buffer value v with error bound e keeps all but its
+ * least significant N_bit = log2(e / |v|) + 52 + M significand bits.
+ * Reading: log2 is rounded up to an integer (ceil, taken exactly from the
+ * binary exponent), N_bit is clamped to [0, 52], the dropped bits are set to
+ * zero (truncation toward zero), and v = 0 or e = 0 is left as it is. */
+static double repro_round(double v, double e, int M)
+{
+    if (v == 0.0 || !(e > 0.0)) return v;
+    double r = e / fabs(v);
+    if (!(r > 0.0)) return v;
+    int nbit;
+    if (r >= 1.0) {
+        nbit = 52;
+    } else {
+        int k;
+        double m = frexp(r, &k); /* r = m 2^k, 1/2 <= m < 1, so k - 1 <= log2 r < k */
+        int ceil_log2 = (m == 0.5) ? k - 1 : k;
+        nbit = ceil_log2 + 52 + M;
+        if (nbit < 0) nbit = 0;
+        if (nbit > 52) nbit = 52;
+    }
+    uint64_t bits;
+    memcpy(&bits, &v, sizeof bits);
+    if (nbit > 0) bits &= ~((((uint64_t)1) << nbit) - 1);
+    memcpy(&v, &bits, sizeof v);
+    return v;
+}
+
+/* App. A.1 (reproducible atomics), steps 1-4: Step 1 as or_deposit, with an
+ * error bound per buffer value, E := E + eps |Delta U^buf| after every
+ * addition (eps = 2^-52, the FP64 machine epsilon); then every buffer value
+ * (ghost cells included) rounded by repro_round with margin M.  ebuf (same
+ * layout as the buffer, zeroed by the caller) returns E. */
+int or_deposit_rounded(const or_params *P, const or_mesh *S, const or_particles *p, const double *gathered,
+                       or_mesh *B, int M, double *ebuf)
+{
+    if (!P || !S || !p || !gathered || !B || !ebuf || M < 0) return OR_ERR_ARG;
+    if (B->ng < stencil_halfwidth(P->r_K)) return OR_ERR_ARG;
+    int st = deposit_parts_e(P, S, p, gathered, p->count, B, NULL, ebuf);
+    int64_t ncell = (int64_t)(B->n[0] + 2 * B->ng) * (B->n[1] + 2 * B->ng) * (B->n[2] + 2 * B->ng);
+    for (int f = 0; f < NF; f++)
+        for (int64_t c = 0; c < ncell; c++) {
+            int64_t o = (int64_t)f * B->fstride + c;
+            B->u[o] = repro_round(B->u[o], ebuf[o], M);
+        }
+    return st;
+}
+
 /* or_deposit with particle s's gathered row r at gathered[r * gstride + s]. */
 static int deposit_parts(const or_params *P, const or_mesh *S, const or_particles *p, const double *gathered,
                          int64_t gstride, or_mesh *B, double *absbuf)
+{
+    return deposit_parts_e(P, S, p, gathered, gstride, B, absbuf, NULL);
+}
+
+static int deposit_parts_e(const or_params *P, const or_mesh *S, const or_particles *p, const double *gathered,
+                           int64_t gstride, or_mesh *B, double *absbuf, double *ebuf)
 {
     kcell *kc = alloc_kcells(P->r_K);
     if (!kc) return OR_ERR_NOMEM;
@@ -543,12 +654,13 @@ static int deposit_parts(const or_params *P, const or_mesh *S, const or_particle
             if (w == 0.0) continue;
             double U[NF], dU[NF];
             read_state(S, kc[t].wi, kc[t].wj, kc[t].wk, U);
-            if (P->kind == KIND_FEEDBACK) feedback_delta(w, U, gathered + s, gstride, &kc[t], dU);
-            else sink_delta(P, S->dx, U, gathered + s, gstride, &kc[t], dU);
+            kind_delta(P, S->dx, w, U, gathered + s, gstride, &kc[t], dU);
             int64_t b = cell_index(B, kc[t].ci, kc[t].cj, kc[t].ck);
             for (int f = 0; f < NF; f++) {
-                B->u[(int64_t)f * B->fstride + b] = B->u[(int64_t)f * B->fstride + b] + dU[f];
-                if (absbuf) absbuf[(int64_t)f * B->fstride + b] = absbuf[(int64_t)f * B->fstride + b] + fabs(dU[f]);
+                int64_t o = (int64_t)f * B->fstride + b;
+                B->u[o] = B->u[o] + dU[f];
+                if (absbuf) absbuf[o] = absbuf[o] + fabs(dU[f]);
+                if (ebuf) ebuf[o] = ebuf[o] + 2.220446049250313e-16 * fabs(B->u[o]);
             }
         }
     }
@@ -744,6 +856,23 @@ static int all_zero(const double D[NF])
     return 1;
 }
 
+/* Step 3 of the context's kind: eta per field of one cell (Eq. lambda for
+ * supernovae, the accretion limiter for sinks, 1 for the particle-mesh
+ * deposit, which Sec. 2.2 leaves unlimited). */
+static void kind_eta(const or_params *P, double dx, const double U[NF], const double D[NF], double eta[NF], int *nr)
+{
+    *nr = 0;
+    if (P->kind == KIND_FEEDBACK) {
+        double l = sn_lambda(U, D, nr);
+        eta[0] = 1.0; eta[1] = l; eta[2] = l; eta[3] = l; eta[4] = 1.0;
+    } else if (P->kind == KIND_SINK) {
+        double e = sink_eta(P, dx, U, D);
+        for (int f = 0; f < NF; f++) eta[f] = e;
+    } else {
+        for (int f = 0; f < NF; f++) eta[f] = 1.0;
+    }
+}
+
 int or_apply(const or_params *P, or_mesh *S, const or_mesh *B, double *eta_out, int64_t *counts)
 {
     if (!P || !S || !B) return OR_ERR_ARG;
@@ -758,15 +887,9 @@ int or_apply(const or_params *P, or_mesh *S, const or_mesh *B, double *eta_out, 
                     D[f] = B->u[(int64_t)f * B->fstride + b];
                 }
                 double eta[NF];
-                if (P->kind == KIND_FEEDBACK) {
-                    int nr;
-                    double l = sn_lambda(U, D, &nr);
-                    n_noroot += nr;
-                    eta[0] = 1.0; eta[1] = l; eta[2] = l; eta[3] = l; eta[4] = 1.0;
-                } else {
-                    double e = sink_eta(P, S->dx, U, D);
-                    for (int f = 0; f < NF; f++) eta[f] = e;
-                }
+                int nr;
+                kind_eta(P, S->dx, U, D, eta, &nr);
+                n_noroot += nr;
                 if (eta[1] < 1.0) n_lim++;
                 if (eta_out) eta_out[v] = eta[1];
                 if (all_zero(D)) continue;
@@ -774,6 +897,96 @@ int or_apply(const or_params *P, or_mesh *S, const or_mesh *B, double *eta_out, 
             }
     if (counts) { counts[0] = n_lim; counts[1] = n_noroot; }
     return OR_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Sink creation (Sec. 3.1.2)                                                */
+/* ------------------------------------------------------------------------ */
+
+/* After the accretion pass, with its summed buffer B retained (Sec. 3.1, item
+ * 2), a valid cell c becomes a new sink when
+ *   (a) rho_c > rho_Tr,c (Eq. truelove with the cell's own c_s);
+ *   (b) c is a local density maximum within r_K: rho_c > rho_c' for every
+ *       other valid cell c' whose centre lies within r_K of c's centre;
+ *   (c) no sink lies within r_K, enforced as the paper does: the summed
+ *       change of the accretion pass is zero in every field at c.
+ * Readings: "within r_K" is |x_c' - x_c|^2 < r_K^2 with the cell-centre
+ * offsets of Sec. 2.1, periodic images on periodic axes; the maximum is
+ * strict (equal neighbours create nothing); all conditions are evaluated on
+ * the state before any creation.  Then, in cell index order (z slowest), the
+ * sink gets position = the cell centre, m_s = (rho - rho_Tr) V and p_s =
+ * m_s v with v = p_c / rho_c; the cell keeps its velocity and specific
+ * energy: rho := rho_Tr, p := rho_Tr v, E := rho_Tr (E / rho).
+ * At most cap sinks are written (the cells beyond are left as they are);
+ * returns the number of cells that satisfy the conditions. */
+int64_t or_create_sinks(const or_params *P, or_mesh *S, const or_mesh *B, int64_t cap, double *x, double *y,
+                        double *z, double *m, double *px, double *py, double *pz)
+{
+    if (!P || !S || !B || P->kind != KIND_SINK) return -1;
+    int nx = S->n[0], ny = S->n[1], nz = S->n[2];
+    int R = stencil_halfwidth(P->r_K);
+    double r2 = P->r_K * P->r_K;
+    double V = cell_volume(S->dx);
+    int64_t nvalid = (int64_t)nx * ny * nz;
+    unsigned char *flag = (unsigned char *)calloc((size_t)(nvalid > 0 ? nvalid : 1), 1);
+    if (!flag) return -1;
+    int64_t v = 0;
+    for (int k = 0; k < nz; k++)
+        for (int j = 0; j < ny; j++)
+            for (int i = 0; i < nx; i++, v++) {
+                double U[NF], D[NF], cs, rtr;
+                read_state(S, i, j, k, U);
+                int64_t b = cell_index(B, i, j, k);
+                for (int f = 0; f < NF; f++) D[f] = B->u[(int64_t)f * B->fstride + b];
+                if (!all_zero(D)) continue;                       /* (c) */
+                sink_cell(P, S->dx, U, &cs, &rtr);
+                if (!(U[0] > rtr)) continue;                      /* (a) */
+                int ok = 1;
+                for (int oz = -R; oz <= R && ok; oz++)
+                    for (int oy = -R; oy <= R && ok; oy++)
+                        for (int ox = -R; ox <= R && ok; ox++) {
+                            if (!ox && !oy && !oz) continue;
+                            double d2 = (double)(ox * ox + oy * oy) + (double)(oz * oz);
+                            if (!(d2 < r2)) continue;
+                            int a = i + ox, bb = j + oy, c = k + oz;
+                            if (a < 0 || a >= nx) { if (!S->periodic[0]) continue; a = (a + nx) % nx; }
+                            if (bb < 0 || bb >= ny) { if (!S->periodic[1]) continue; bb = (bb + ny) % ny; }
+                            if (c < 0 || c >= nz) { if (!S->periodic[2]) continue; c = (c + nz) % nz; }
+                            if (a == i && bb == j && c == k) continue; /* a small periodic box wraps onto c */
+                            double rho2 = S->u[cell_index(S, a, bb, c)];
+                            if (!(U[0] > rho2)) ok = 0;          /* (b) */
+                        }
+                flag[v] = (unsigned char)ok;
+            }
+    int64_t n = 0;
+    v = 0;
+    for (int k = 0; k < nz; k++)
+        for (int j = 0; j < ny; j++)
+            for (int i = 0; i < nx; i++, v++) {
+                if (!flag[v]) continue;
+                if (n < cap) {
+                    double U[NF], cs, rtr;
+                    read_state(S, i, j, k, U);
+                    sink_cell(P, S->dx, U, &cs, &rtr);
+                    double vel[3] = {U[1] / U[0], U[2] / U[0], U[3] / U[0]};
+                    double es = U[4] / U[0];
+                    double ms = (U[0] - rtr) * V;
+                    x[n] = (double)i + 0.5;
+                    y[n] = (double)j + 0.5;
+                    z[n] = (double)k + 0.5;
+                    m[n] = ms;
+                    px[n] = ms * vel[0];
+                    py[n] = ms * vel[1];
+                    pz[n] = ms * vel[2];
+                    int64_t c = cell_index(S, i, j, k);
+                    S->u[c] = rtr;
+                    for (int a = 0; a < 3; a++) S->u[(int64_t)(1 + a) * S->fstride + c] = rtr * vel[a];
+                    S->u[(int64_t)4 * S->fstride + c] = rtr * es;
+                }
+                n++;
+            }
+    free(flag);
+    return n;
 }
 
 /* ------------------------------------------------------------------------ */
@@ -870,7 +1083,7 @@ static int deposit_at(const or_params *P, const or_mesh *S, const or_particles *
     int64_t *cand;
     int64_t nc = candidates(S, bins, R, bi, bj, bk, &cand);
     int rows = or_gathered_rows(P->kind);
-    double G[FB_ROWS > SK_ROWS ? FB_ROWS : SK_ROWS];
+    double G[MAX_ROWS];
     int status = OR_OK;
     for (int f = 0; f < NF; f++) { out[f] = 0.0; absout[f] = 0.0; }
     for (int64_t t = 0; t < nc; t++) {
@@ -882,16 +1095,14 @@ static int deposit_at(const or_params *P, const or_mesh *S, const or_particles *
             if (kc[q].ci == bi && kc[q].cj == bj && kc[q].ck == bk) { hit = q; break; }
         if (hit < 0) continue;
         kcell c = kc[hit];
-        int st = P->kind == KIND_FEEDBACK ? gather_feedback_one(P, S, p, s, kc, G, 1)
-                                          : gather_sink_one(P, S, p, s, kc, G, 1);
+        int st = gather_one(P, S, p, s, kc, G, 1);
         if (st && !status) status = st;
         (void)rows;
         double w = cell_fraction(P, &c, x, y, z);
         if (w == 0.0) continue;
         double U[NF], dU[NF];
         read_state(S, c.wi, c.wj, c.wk, U);
-        if (P->kind == KIND_FEEDBACK) feedback_delta(w, U, G, 1, &c, dU);
-        else sink_delta(P, S->dx, U, G, 1, &c, dU);
+        kind_delta(P, S->dx, w, U, G, 1, &c, dU);
         for (int f = 0; f < NF; f++) { out[f] = out[f] + dU[f]; absout[f] = absout[f] + fabs(dU[f]); }
     }
     free(cand);
@@ -934,14 +1145,8 @@ int or_cells_at(const or_params *P, const or_mesh *S, const or_particles *p, con
         if (st && !status) status = st;
         read_state(S, i, j, k, U);
         double eta[NF];
-        if (P->kind == KIND_FEEDBACK) {
-            int nr;
-            double l = sn_lambda(U, D, &nr);
-            eta[0] = 1.0; eta[1] = l; eta[2] = l; eta[3] = l; eta[4] = 1.0;
-        } else {
-            double e = sink_eta(P, S->dx, U, D);
-            for (int f = 0; f < NF; f++) eta[f] = e;
-        }
+        int nr;
+        kind_eta(P, S->dx, U, D, eta, &nr);
         int zero = all_zero(D);
         for (int f = 0; f < NF; f++) {
             out_sum[NF * t + f] = D[f];
@@ -998,8 +1203,7 @@ int or_gather_at(const or_params *P, const or_mesh *S, const or_particles *p, in
     if (!kc) return OR_ERR_NOMEM;
     int status = OR_OK;
     for (int64_t t = 0; t < nsel; t++) {
-        int st = P->kind == KIND_FEEDBACK ? gather_feedback_one(P, S, p, sel[t], kc, gathered + t, nsel)
-                                          : gather_sink_one(P, S, p, sel[t], kc, gathered + t, nsel);
+        int st = gather_one(P, S, p, sel[t], kc, gathered + t, nsel);
         if (st && !status) status = st;
     }
     free(kc);
@@ -1037,8 +1241,7 @@ int or_deltas(const or_params *P, const or_mesh *S, const or_particles *p, const
         if (w == 0.0) continue;
         double U[NF], d[NF];
         read_state(S, kc[t].wi, kc[t].wj, kc[t].wk, U);
-        if (P->kind == KIND_FEEDBACK) feedback_delta(w, U, G, 1, &kc[t], d);
-        else sink_delta(P, S->dx, U, G, 1, &kc[t], d);
+        kind_delta(P, S->dx, w, U, G, 1, &kc[t], d);
         ijk[3 * n] = kc[t].ci;
         ijk[3 * n + 1] = kc[t].cj;
         ijk[3 * n + 2] = kc[t].ck;
@@ -1175,7 +1378,7 @@ static int64_t batch_arena_len(const or_batch *T)
 
 static int batch_check(const or_params *P, const or_batch *T)
 {
-    if (!T || T->np <= 0 || T->ng < stencil_halfwidth(P->r_K)) return OR_ERR_ARG;
+    if (!T || T->np <= 0 || T->ng < stencil_halfwidth(P->r_K) || P->kind == KIND_MASS) return OR_ERR_ARG;
     for (int p = 0; p < T->np; p++)
         for (int a = 0; a < 3; a++)
             if (T->dims[3 * p + a] < T->ng) return OR_ERR_ARG;

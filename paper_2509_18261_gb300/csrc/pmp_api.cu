@@ -80,7 +80,7 @@ pmp_status make_parts(const pmp_ctx *ctx, const pmp_particles *p, Parts *q)
     if (!p || p->count < 0 || p->count > 0x7fffffffLL) return PMP_ERR_ARG;
     if (p->count > 0) {
         if (!p->x || !p->y || !p->z || !p->m || !p->px || !p->py || !p->pz) return PMP_ERR_ARG;
-        if (ctx->p.kind == PMP_KIND_FEEDBACK && !p->e) return PMP_ERR_ARG;
+        if (ctx->p.kind == PMP_KIND_FEEDBACK && !p->e) return PMP_ERR_ARG;  // MASS: e optional
     }
     q->count = p->count;
     q->x = p->x;
@@ -180,6 +180,13 @@ Layout layout(const pmp_params &p, long long n, long long nvalid, int mode)
 
 long long nvalid_rows(const Layout &L) { return L.aux_stride; }
 
+// ROUNDED mode: the error-bound buffer E of App. A.1 follows the rest of the
+// workspace, with the buffer mesh's layout ([5][field_stride] doubles).
+size_t ebuf_offset(const Layout &L) { return align256(L.total); }
+size_t ebuf_bytes(const pmp_mesh *buffer) { return sizeof(double) * 5 * (size_t)buffer->field_stride; }
+
+bool valid_mode(int32_t mode) { return mode == PMP_MODE_ATOMIC || mode == PMP_MODE_SORTED || mode == PMP_MODE_ROUNDED; }
+
 pmp::PlanPtrs plan_ptrs(const Layout &L, void *ws, const pmp_params &p, int mode)
 {
     char *w = static_cast<char *>(ws);
@@ -215,8 +222,9 @@ namespace pmp {
 pmp_status check_params(const pmp_params *p)
 {
     if (!p) return PMP_ERR_ARG;
-    if (p->kind != PMP_KIND_FEEDBACK && p->kind != PMP_KIND_SINK) return PMP_ERR_ARG;
+    if (p->kind != PMP_KIND_FEEDBACK && p->kind != PMP_KIND_SINK && p->kind != PMP_KIND_MASS) return PMP_ERR_ARG;
     if (!std::isfinite(p->r_K) || p->r_K < 1.0 || p->r_K > (double)pmp::kMaxR) return PMP_ERR_ARG;
+    if (p->kind == PMP_KIND_MASS) return p->subsample < 1 || p->subsample > pmp::kMaxS ? PMP_ERR_ARG : PMP_OK;
     if (!std::isfinite(p->gamma) || !(p->gamma > 1.0)) return PMP_ERR_ARG;
     if (p->kind == PMP_KIND_FEEDBACK) {
         if (p->subsample < 1 || p->subsample > pmp::kMaxS) return PMP_ERR_ARG;
@@ -255,7 +263,7 @@ KParams make_kparams(const pmp_params &p, double dx)
     k.V = (dx * dx) * dx;
     k.dx = dx;
     k.four_pi = 4.0 * pmp::kPi;
-    k.S = p.kind == PMP_KIND_FEEDBACK ? p.subsample : 1;
+    k.S = p.kind == PMP_KIND_SINK ? 1 : p.subsample;
     k.S3 = k.S * k.S * k.S;
     for (int a = 0; a < 8; ++a) k.frac[a] = a < k.S ? ((double)a + 0.5) / (double)k.S : 0.0;
     k.Slog = -1;
@@ -297,6 +305,7 @@ pmp_status pmp_create(pmp_ctx **out, const pmp_params *params, pmp_stream stream
     c->plan_n = -1;
     c->plan_nvalid = -1;
     c->plan_mode = PMP_MODE_ATOMIC;
+    c->repro_M = 28;
     c->timing = false;
     if (cudaGetDevice(&c->device) != cudaSuccess || cudaMalloc(&c->st, sizeof(pmp::DevStatus)) != cudaSuccess ||
         cudaMemset(c->st, 0, sizeof(pmp::DevStatus)) != cudaSuccess) {
@@ -319,6 +328,81 @@ void pmp_destroy(pmp_ctx *ctx)
     for (auto e : ctx->pool) cudaEventDestroy(e);
     cudaFree(ctx->st);
     delete ctx;
+}
+
+// Sink creation workspace: flags (4 B) and scan positions (8 B) per valid
+// cell, then the scan's temporary storage.
+struct CreateLayout {
+    size_t flags, pos, temp, temp_bytes, total;
+};
+
+static CreateLayout create_layout(long long nv)
+{
+    CreateLayout L;
+    const size_t n1 = (size_t)(nv > 0 ? nv : 1);
+    size_t off = 0;
+    L.flags = off;
+    off = align256(off + 4 * n1);
+    L.pos = off;
+    off = align256(off + 8 * n1);
+    L.temp = off;
+    L.temp_bytes = pmp::scan_temp_bytes(nv);
+    L.total = align256(off + L.temp_bytes);
+    return L;
+}
+
+pmp_status pmp_create_sinks_workspace_size(const pmp_ctx *ctx, const pmp_mesh *state, size_t *bytes)
+{
+    if (!ctx || !state || !bytes || ctx->p.kind != PMP_KIND_SINK) return PMP_ERR_ARG;
+    for (int a = 0; a < 3; ++a)
+        if (state->n[a] < 1) return PMP_ERR_ARG;
+    *bytes = create_layout(nvalid_of(state)).total;
+    return PMP_OK;
+}
+
+pmp_status pmp_create_sinks(pmp_ctx *ctx, pmp_mesh *state, const pmp_mesh *buffer, int64_t capacity, double *x,
+                            double *y, double *z, double *m, double *px, double *py, double *pz, int64_t *count,
+                            void *workspace, size_t workspace_bytes)
+{
+    if (!ctx || ctx->p.kind != PMP_KIND_SINK || !count || capacity < 0) return PMP_ERR_ARG;
+    if (capacity > 0 && (!x || !y || !z || !m || !px || !py || !pz)) return PMP_ERR_ARG;
+    Box S, B;
+    pmp_status s = make_box(state, &S);
+    if (s) return s;
+    s = make_box(buffer, &B);
+    if (s) return s;
+    for (int a = 0; a < 3; ++a)
+        if (state->n[a] != buffer->n[a] || state->periodic[a] != buffer->periodic[a]) return PMP_ERR_ARG;
+    if (state->dx != buffer->dx || overlaps(state, buffer)) return PMP_ERR_ARG;
+    const long long nv = nvalid_of(state);
+    if (nv > 0xfffffffeLL) return PMP_ERR_ARG;
+    const CreateLayout L = create_layout(nv);
+    if (!workspace || workspace_bytes < L.total || (reinterpret_cast<uintptr_t>(workspace) & 255))
+        return PMP_ERR_WORKSPACE;
+    const KParams P = make_kparams(ctx->p, state->dx);
+    char *w = static_cast<char *>(workspace);
+    unsigned *flags = reinterpret_cast<unsigned *>(w + L.flags);
+    unsigned long long *pos = reinterpret_cast<unsigned long long *>(w + L.pos);
+    cudaStream_t st = ctx->stream;
+    if (cudaMemsetAsync(count, 0, sizeof(int64_t), st) != cudaSuccess) return PMP_ERR_CUDA;
+    {
+        Timed tm(ctx, "create_flags");
+        pmp::launch_create_flags(P, S, state->data, B, buffer->data, flags, st);
+    }
+    if (pmp::scan_counts(w + L.temp, L.temp_bytes, flags, pos, nv, st) != cudaSuccess) return PMP_ERR_CUDA;
+    {
+        Timed tm(ctx, "create_apply");
+        pmp::launch_create_apply(P, S, state->data, flags, pos, capacity, x, y, z, m, px, py, pz,
+                                 reinterpret_cast<long long *>(count), st);
+    }
+    return last_launch();
+}
+
+pmp_status pmp_set_rounding_margin(pmp_ctx *ctx, int32_t M)
+{
+    if (!ctx || M < 0 || M > 104) return PMP_ERR_ARG;
+    ctx->repro_M = M;
+    return PMP_OK;
 }
 
 pmp_status pmp_timing_enable(pmp_ctx *ctx, int32_t on)
@@ -364,17 +448,22 @@ pmp_status pmp_set_stream(pmp_ctx *ctx, pmp_stream stream)
 
 int32_t pmp_gathered_rows(int32_t kind)
 {
-    return kind == PMP_KIND_FEEDBACK ? (int32_t)pmp::FB_ROWS : kind == PMP_KIND_SINK ? (int32_t)pmp::SK_ROWS : 0;
+    return kind == PMP_KIND_FEEDBACK ? (int32_t)pmp::FB_ROWS
+           : kind == PMP_KIND_SINK   ? (int32_t)pmp::SK_ROWS
+           : kind == PMP_KIND_MASS   ? (int32_t)pmp::MS_ROWS
+                                     : 0;
 }
 
 pmp_status pmp_workspace_size(const pmp_ctx *ctx, const pmp_mesh *buffer, int64_t n_particles, int32_t mode,
                               size_t *bytes)
 {
     if (!ctx || !buffer || !bytes || n_particles < 0 || n_particles > 0x7fffffffLL) return PMP_ERR_ARG;
-    if (mode != PMP_MODE_ATOMIC && mode != PMP_MODE_SORTED) return PMP_ERR_ARG;
+    if (!valid_mode(mode)) return PMP_ERR_ARG;
     for (int a = 0; a < 3; ++a)
         if (buffer->n[a] < 1) return PMP_ERR_ARG;
-    *bytes = layout(ctx->p, n_particles, nvalid_of(buffer), mode).total;
+    if (buffer->field_stride < 0) return PMP_ERR_ARG;
+    const Layout L = layout(ctx->p, n_particles, nvalid_of(buffer), mode);
+    *bytes = mode == PMP_MODE_ROUNDED ? ebuf_offset(L) + ebuf_bytes(buffer) : L.total;
     return PMP_OK;
 }
 
@@ -395,7 +484,7 @@ pmp_status pmp_gather(pmp_ctx *ctx, const pmp_mesh *state, const pmp_particles *
                       int32_t mode, void *workspace, size_t workspace_bytes)
 {
     if (!ctx || (!gathered && particles && particles->count > 0)) return PMP_ERR_ARG;
-    if (mode != PMP_MODE_ATOMIC && mode != PMP_MODE_SORTED) return PMP_ERR_ARG;
+    if (!valid_mode(mode)) return PMP_ERR_ARG;
     Box S;
     Parts q;
     pmp_status s = make_box(state, &S);
@@ -422,7 +511,7 @@ pmp_status pmp_gather(pmp_ctx *ctx, const pmp_mesh *state, const pmp_particles *
     void *temp = w + L.temp;
     cudaStream_t st = ctx->stream;
     if (q.count > 0) {
-        if (mode == PMP_MODE_ATOMIC) {
+        if (mode != PMP_MODE_SORTED) {
             unsigned *keys = reinterpret_cast<unsigned *>(w + L.keys), *ids = reinterpret_cast<unsigned *>(w + L.ids);
             unsigned *keys2 = reinterpret_cast<unsigned *>(w + L.keys2),
                      *ids2 = reinterpret_cast<unsigned *>(w + L.ids2);
@@ -467,7 +556,7 @@ pmp_status pmp_deposit(pmp_ctx *ctx, const pmp_mesh *state, const pmp_particles 
                        pmp_mesh *buffer, int32_t mode, void *workspace, size_t workspace_bytes)
 {
     if (!ctx || (!gathered && particles && particles->count > 0)) return PMP_ERR_ARG;
-    if (mode != PMP_MODE_ATOMIC && mode != PMP_MODE_SORTED) return PMP_ERR_ARG;
+    if (!valid_mode(mode)) return PMP_ERR_ARG;
     Box S, B;
     Parts q;
     pmp_status s = check_pair(ctx, state, buffer, &S, &B);
@@ -479,6 +568,7 @@ pmp_status pmp_deposit(pmp_ctx *ctx, const pmp_mesh *state, const pmp_particles 
     const Layout L = layout(ctx->p, q.count, nv, mode);
     s = check_workspace(L, workspace, workspace_bytes);
     if (s) return s;
+    if (mode == PMP_MODE_ROUNDED && workspace_bytes < ebuf_offset(L) + ebuf_bytes(buffer)) return PMP_ERR_WORKSPACE;
     s = check_plan(ctx, q.count, nv, workspace);
     if (s) return s;
     if (ctx->plan_mode != mode) return PMP_ERR_WORKSPACE;
@@ -488,7 +578,20 @@ pmp_status pmp_deposit(pmp_ctx *ctx, const pmp_mesh *state, const pmp_particles 
     if (mode == PMP_MODE_ATOMIC) {
         {
             Timed tm(ctx, "deposit");
-            pmp::launch_deposit_atomic(P, S, state->data, B, buffer->data, q, gathered, pl, st);
+            pmp::launch_deposit_atomic(P, S, state->data, B, buffer->data, q, gathered, pl, nullptr, st);
+        }
+        return last_launch();
+    }
+    if (mode == PMP_MODE_ROUNDED) {
+        double *E = reinterpret_cast<double *>(static_cast<char *>(workspace) + ebuf_offset(L));
+        if (cudaMemsetAsync(E, 0, ebuf_bytes(buffer), st) != cudaSuccess) return PMP_ERR_CUDA;
+        {
+            Timed tm(ctx, "deposit");
+            pmp::launch_deposit_atomic(P, S, state->data, B, buffer->data, q, gathered, pl, E, st);
+        }
+        {
+            Timed tm(ctx, "round");
+            pmp::launch_round(B, buffer->data, E, ctx->repro_M, st);
         }
         return last_launch();
     }

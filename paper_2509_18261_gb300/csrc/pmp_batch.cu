@@ -1263,6 +1263,7 @@ pmp_status pmp_batch_create(pmp_ctx *ctx, const pmp_patch *patches, int32_t n_pa
     *out = nullptr;
     if (!ctx || !patches || n_patches < 1 || ng < 0 || !std::isfinite(dx) || !(dx > 0.0) || arena_len < 1)
         return PMP_ERR_ARG;
+    if (ctx->p.kind == PMP_KIND_MASS) return PMP_ERR_ARG;  // the batched form covers supernovae and sinks
     const int R = (int)std::ceil(ctx->p.r_K);
     if (ng < R) return PMP_ERR_GHOST_TOO_THIN;
     // geometry checks: extents, arena bounds, disjoint patches, a consistent

@@ -19,6 +19,7 @@
 namespace pmp {
 
 constexpr int NF = 5;
+constexpr double kEpsMachine = 2.220446049250313e-16;  // 2^-52, the FP64 machine epsilon
 constexpr double kPi = 3.141592653589793;
 constexpr int kMaxR = 6;
 constexpr int kMaxS = 8;
@@ -386,6 +387,7 @@ constexpr int kRec = 6;
 // Gathered-row indices.
 enum { FB_MSNR = 0, FB_VSNR, FB_VX, FB_VY, FB_VZ, FB_NH, FB_RM, FB_PRAD, FB_Q, FB_E, FB_PV, FB_REGIME, FB_ROWS };
 enum { SK_RHO = 0, SK_VINF, SK_CINF, SK_MDOT, SK_RACC, SK_SUMW, SK_K, SK_NMEM, SK_ROWS };
+enum { MS_VK = 0, MS_Q, MS_ROWS = MS_Q + NF };  // V_K, then (m, p, e) / V_K
 
 // ---------------------------------------------------------------------------
 // gathered rows from the kernel sums (shared by the single-box and batched
@@ -497,6 +499,27 @@ __device__ __forceinline__ bool all_zero(const double D[NF])
 #pragma unroll
     for (int f = 0; f < NF; ++f) acc |= (unsigned long long)__double_as_longlong(D[f]) << 1;
     return acc == 0;
+}
+
+// App. A.1 rounding of one buffer value v with error bound e: r = e / |v|,
+// N_bit = ceil(log2 r) + 52 + M clamped to [0, 52], and the low N_bit bits of
+// the significand set to zero (truncation toward zero).  v = 0 or e = 0 is
+// left as it is.
+__device__ __forceinline__ double repro_round(double v, double e, int M)
+{
+    if (v == 0.0 || !(e > 0.0)) return v;
+    const double r = e / fabs(v);
+    if (!(r > 0.0)) return v;  // underflow: N_bit < 0
+    int nb = 52;
+    if (r < 1.0) {
+        int k;
+        const double m = frexp(r, &k);       // r = m 2^k, m in [1/2, 1)
+        const int c = m == 0.5 ? k - 1 : k;  // ceil(log2 r)
+        nb = c + 52 + M;
+        nb = nb < 0 ? 0 : (nb > 52 ? 52 : nb);
+    }
+    const unsigned long long bits = (unsigned long long)__double_as_longlong(v);
+    return __longlong_as_double((long long)(bits & ~((1ULL << nb) - 1ULL)));
 }
 
 // Position check: 0 <= x < n on each axis (NaN fails).

@@ -39,8 +39,9 @@ void launch_plan(const KParams &P, const Box &S, const Parts &p, const PlanPtrs 
                  cudaStream_t stream);
 void launch_gather(const KParams &P, const Box &S, const double *u, const Parts &p, const PlanPtrs &pl, double *G,
                    DevStatus *st, cudaStream_t stream);
+// E (optional): App. A.1 error-bound buffer, the buffer's layout, zeroed.
 void launch_deposit_atomic(const KParams &P, const Box &S, const double *u, const Box &B, double *b, const Parts &p,
-                           const double *G, const PlanPtrs &pl, cudaStream_t stream);
+                           const double *G, const PlanPtrs &pl, double *E, cudaStream_t stream);
 void launch_sort_keys(const KParams &P, const Box &B, const Parts &p, const PlanPtrs &pl,
                       const unsigned long long *offsets, unsigned *keys, unsigned *vals, cudaStream_t stream);
 void launch_segment_sum(const KParams &P, const Box &S, const double *u, const Box &B, double *b, const Parts &p,
@@ -56,6 +57,15 @@ void launch_pass_mask(const Box &S, const double *u, const Box &B, const double 
                       cudaStream_t stream);
 void launch_zero(const Box &B, double *b, cudaStream_t stream);
 void launch_fold(const Box &B, double *b, cudaStream_t stream);
+// Sink creation (Sec. 3.1.2): flags[v] = 1 for valid cells that qualify, then
+// the sinks written at their exclusive-scan positions (count -> *count).
+void launch_create_flags(const KParams &P, const Box &S, const double *u, const Box &B, const double *b,
+                         unsigned *flags, cudaStream_t stream);
+void launch_create_apply(const KParams &P, const Box &S, double *u, const unsigned *flags,
+                         const unsigned long long *pos, long long cap, double *x, double *y, double *z, double *m,
+                         double *px, double *py, double *pz, long long *count, cudaStream_t stream);
+// App. A.1 rounding of every buffer cell with its error bound E (margin M).
+void launch_round(const Box &B, double *b, const double *E, int M, cudaStream_t stream);
 void launch_sink_aux(const KParams &P, const Box &S, const double *u, double *grec, double *drec,
                      cudaStream_t stream);
 void launch_sink_eta(const KParams &P, const Box &S, const double *u, const Box &B, const double *b, double *drec,
@@ -69,6 +79,7 @@ void launch_apply(const KParams &P, const Box &S, double *u, const Box &B, const
 
 // CUB primitives, in pmp_sort.cu
 size_t cub_temp_bytes(long long n, long long max_pairs, bool sorted);
+size_t scan_temp_bytes(long long n);
 cudaError_t sort_host_keys(void *temp, size_t temp_bytes, const unsigned *kin, unsigned *kout, const unsigned *vin,
                            unsigned *vout, long long n, cudaStream_t stream);
 cudaError_t scan_counts(void *temp, size_t temp_bytes, const unsigned *counts, unsigned long long *offsets,

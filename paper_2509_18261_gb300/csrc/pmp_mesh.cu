@@ -341,6 +341,136 @@ void launch_zero(const Box &B, double *b, cudaStream_t stream)
     k_zero<<<152 * 8, 256, 0, stream>>>(b, B.fs, B.ncells);
 }
 
+// Sink creation (Sec. 3.1.2), pass 1: a valid cell qualifies when the
+// retained accretion buffer is zero in every field there (no sink within
+// r_K), rho > rho_Tr (Eq. truelove with the cell's c_s), and rho is strictly
+// larger than at every other cell whose centre lies within r_K (periodic
+// images on periodic axes).  Reads only.
+__global__ void __launch_bounds__(256) k_create_flags(KParams P, Box S, const double *__restrict__ u, Box B,
+                                                      const double *__restrict__ b, unsigned *__restrict__ flags)
+{
+    const long long nvalid = (long long)S.n0 * S.n1 * S.n2;
+    const long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= nvalid) return;
+    const int i = (int)(v % S.n0);
+    const long long r = v / S.n0;
+    const int j = (int)(r % S.n1), k = (int)(r / S.n1);
+    unsigned ok = 0;
+    double D[NF];
+    load_cell(b, B, B.at(i, j, k), D);
+    if (all_zero(D)) {
+        double U[NF];
+        load_cell(u, S, S.at(i, j, k), U);
+        if (U[0] > sink_rho_tr(P, U)) {
+            ok = 1;
+            const int R = P.R;
+            for (int oz = -R; oz <= R && ok; ++oz)
+                for (int oy = -R; oy <= R && ok; ++oy)
+                    for (int ox = -R; ox <= R && ok; ++ox) {
+                        if (!ox && !oy && !oz) continue;
+                        const double d2 = (double)(ox * ox + oy * oy) + (double)(oz * oz);
+                        if (!(d2 < P.r2)) continue;
+                        int a = i + ox, bb = j + oy, c = k + oz;
+                        if (a < 0 || a >= S.n0) {
+                            if (!S.per0) continue;
+                            a = wrapi(a, S.n0);
+                        }
+                        if (bb < 0 || bb >= S.n1) {
+                            if (!S.per1) continue;
+                            bb = wrapi(bb, S.n1);
+                        }
+                        if (c < 0 || c >= S.n2) {
+                            if (!S.per2) continue;
+                            c = wrapi(c, S.n2);
+                        }
+                        if (a == i && bb == j && c == k) continue;
+                        if (!(U[0] > __ldg(u + S.at(a, bb, c)))) ok = 0;
+                    }
+        }
+    }
+    flags[v] = ok;
+}
+
+// Pass 2: each qualifying cell with position p < cap (the exclusive scan of
+// the flags, so sinks come in cell order) becomes sink p at the cell centre
+// with m = (rho - rho_Tr) V and p = m v; the cell keeps v and E/rho with
+// rho := rho_Tr.  The last cell writes the total.
+__global__ void __launch_bounds__(256) k_create_apply(KParams P, Box S, double *__restrict__ u,
+                                                      const unsigned *__restrict__ flags,
+                                                      const unsigned long long *__restrict__ pos, long long cap,
+                                                      double *x, double *y, double *z, double *m, double *px,
+                                                      double *py, double *pz, long long *count)
+{
+    const long long nvalid = (long long)S.n0 * S.n1 * S.n2;
+    const long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= nvalid) return;
+    const unsigned f = flags[v];
+    const unsigned long long q = pos[v];
+    if (v == nvalid - 1) *count = (long long)(q + f);
+    if (!f || (long long)q >= cap) return;
+    const int i = (int)(v % S.n0);
+    const long long r = v / S.n0;
+    const int j = (int)(r % S.n1), k = (int)(r / S.n1);
+    const long long c = S.at(i, j, k);
+    double U[NF];
+    load_cell(u, S, c, U);
+    const double rtr = sink_rho_tr(P, U);
+    const double v0 = U[1] / U[0], v1 = U[2] / U[0], v2 = U[3] / U[0];
+    const double es = U[4] / U[0];
+    const double ms = (U[0] - rtr) * P.V;
+    x[q] = (double)i + 0.5;
+    y[q] = (double)j + 0.5;
+    z[q] = (double)k + 0.5;
+    m[q] = ms;
+    px[q] = ms * v0;
+    py[q] = ms * v1;
+    pz[q] = ms * v2;
+    u[c] = rtr;
+    u[S.fs + c] = rtr * v0;
+    u[2 * S.fs + c] = rtr * v1;
+    u[3 * S.fs + c] = rtr * v2;
+    u[4 * S.fs + c] = rtr * es;
+}
+
+void launch_create_flags(const KParams &P, const Box &S, const double *u, const Box &B, const double *b,
+                         unsigned *flags, cudaStream_t stream)
+{
+    const long long nvalid = (long long)S.n0 * S.n1 * S.n2;
+    k_create_flags<<<(unsigned)((nvalid + 255) / 256), 256, 0, stream>>>(P, S, u, B, b, flags);
+}
+
+void launch_create_apply(const KParams &P, const Box &S, double *u, const unsigned *flags,
+                         const unsigned long long *pos, long long cap, double *x, double *y, double *z, double *m,
+                         double *px, double *py, double *pz, long long *count, cudaStream_t stream)
+{
+    const long long nvalid = (long long)S.n0 * S.n1 * S.n2;
+    k_create_apply<<<(unsigned)((nvalid + 255) / 256), 256, 0, stream>>>(P, S, u, flags, pos, cap, x, y, z, m, px,
+                                                                         py, pz, count);
+}
+
+// App. A.1 rounding, every padded buffer cell and field (grid-stride).
+__global__ void __launch_bounds__(256) k_round(Box B, double *__restrict__ b, const double *__restrict__ E, int M)
+{
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < B.ncells; c += stride) {
+#pragma unroll
+        for (int f = 0; f < NF; ++f) {
+            const long long o = (long long)f * B.fs + c;
+            const double e = E[o];
+            if (e > 0.0) b[o] = repro_round(b[o], e, M);
+        }
+    }
+}
+
+void launch_round(const Box &B, double *b, const double *E, int M, cudaStream_t stream)
+{
+    int dev = 0, nsm = 152;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    const long long need = (B.ncells + 255) / 256;
+    const long long grid = need < (long long)nsm * 8 ? need : (long long)nsm * 8;
+    k_round<<<(unsigned)(grid > 0 ? grid : 1), 256, 0, stream>>>(B, b, E, M);
+}
+
 void launch_fold(const Box &B, double *b, cudaStream_t stream)
 {
     const long long nrows = (long long)B.n1 * B.n2;
@@ -375,12 +505,34 @@ void launch_apply_fb_slow(const Box &S, double *u, const Box &B, const double *b
     k_apply_fb_slow<<<152 * 8, 256, 0, stream>>>(S, u, B, b, eta_out, queue, qcount, st);
 }
 
+// Step 5 of the particle-mesh deposit (no Step 3 in Sec. 2.2's PM/PIC subset):
+// U += Delta U^sum, eta = 1.
+__global__ void __launch_bounds__(256) k_apply_add(Box S, double *__restrict__ u, Box B, const double *__restrict__ b,
+                                                   double *__restrict__ eta_out)
+{
+    const long long nvalid = (long long)S.n0 * S.n1 * S.n2;
+    const long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= nvalid) return;
+    const int i = (int)(v % S.n0);
+    const long long r = v / S.n0;
+    const int j = (int)(r % S.n1), k = (int)(r / S.n1);
+    const long long cs = S.at(i, j, k), cb = B.at(i, j, k);
+    double D[NF];
+#pragma unroll
+    for (int f = 0; f < NF; ++f) D[f] = __ldg(b + (long long)f * B.fs + cb);
+    if (eta_out) eta_out[v] = 1.0;
+    if (all_zero(D)) return;
+#pragma unroll
+    for (int f = 0; f < NF; ++f) u[(long long)f * S.fs + cs] = u[(long long)f * S.fs + cs] + D[f];
+}
+
 void launch_apply(const KParams &P, const Box &S, double *u, const Box &B, const double *b, const double *eta_in,
                   double *eta_out, DevStatus *st, cudaStream_t stream)
 {
     const long long nvalid = (long long)S.n0 * S.n1 * S.n2;
     const unsigned nb = (unsigned)((nvalid + 255) / 256);
-    if (P.kind == PMP_KIND_FEEDBACK) k_apply_fb<<<nb, 256, 0, stream>>>(S, u, B, b, eta_out, st);
+    if (P.kind == PMP_KIND_MASS) k_apply_add<<<nb, 256, 0, stream>>>(S, u, B, b, eta_out);
+    else if (P.kind == PMP_KIND_FEEDBACK) k_apply_fb<<<nb, 256, 0, stream>>>(S, u, B, b, eta_out, st);
     else k_apply_sink<<<nb, 256, 0, stream>>>(S, u, B, b, eta_in, eta_out, st);
 }
 

@@ -179,6 +179,6 @@ extern "C" pmp_status pmp_deposit_noalloc(const pmp_params *params, const pmp_me
     pmp::launch_prologue(S, q, nullptr, nullptr, pl, status, st);
     pmp::launch_plan(k, S, q, pl, status, st);
     pmp::launch_gather(k, S, state->data, q, pl, gathered, status, st);
-    pmp::launch_deposit_atomic(k, S, state->data, B, buffer->data, q, gathered, pl, st);
+    pmp::launch_deposit_atomic(k, S, state->data, B, buffer->data, q, gathered, pl, nullptr, st);
     return cudaGetLastError() == cudaSuccess ? PMP_OK : PMP_ERR_CUDA;
 }

@@ -348,6 +348,11 @@ constexpr int kMaxS3 = kMaxS * kMaxS * kMaxS;
 // Pairs whose loads a per-particle loop issues together.
 constexpr int kUnroll = 4;
 
+// Block size of the thread-per-sink kernels (gather, Step 4).  Step 4 keeps
+// each sink's 3(2R+1) Gaussian factors in a shared-memory column (the gather
+// does not: its cell-record loads need the L1 that the array would take).
+constexpr int kSinkThreads = 128;
+
 // One kernel cell's terms of the supernova gather sums, products fused into
 // the sums (omega = 1 skips the products: fma(1, v, s) == s + v).
 __device__ __forceinline__ void fb_gather_add(const KParams &P, const double *wtab, int cnt, const double U[NF],
@@ -417,10 +422,45 @@ __global__ void __launch_bounds__(128) k_gather_fb(KParams P, Box S, const doubl
     if (!fb_gather_rows(P, sw, sr, sp0, sp1, sp2, m, pe0, pe1, pe2, Esn, G + s, gs)) report(st, PMP_ERR_NONFINITE, s);
 }
 
+// Particle-mesh gather (MASS kind): V_K = V sum omega over the plan's cells in
+// kernel order, then (m, p, e) / V_K.
+__global__ void __launch_bounds__(128) k_gather_mass(KParams P, Box S, Parts p, PlanPtrs pl, double *__restrict__ G,
+                                                     DevStatus *st)
+{
+    __shared__ double wtab[kMaxS3 + 1];
+    fill_omega_table(P, wtab);
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= p.count) return;
+    const long long s = pl.perm ? (long long)pl.perm[t] : t;
+    const long long gs = p.count;
+    if (pl.hosts[s] == kNoHost) {
+        for (int r = 0; r < MS_ROWS; ++r) G[r * gs + s] = 0.0;
+        return;
+    }
+    double sw = 0.0;
+    const unsigned long long b0 = (unsigned long long)t * pl.cap;
+    const unsigned nc = pl.counts[t];
+    for (unsigned q = 0; q < nc; ++q) {
+        const int cnt = (int)(__ldg(pl.slots + b0 + q) >> 48);
+        sw = sw + (cnt == P.S3 ? 1.0 : wtab[cnt]);
+    }
+    const double VK = sw * P.V;
+    const double u[NF] = {p.m[s], p.px[s], p.py[s], p.pz[s], p.e ? p.e[s] : 0.0};
+    G[MS_VK * gs + s] = VK;
+    bool ok = isfinite(VK) && VK > 0.0;
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+        const double q = u[f] / VK;
+        G[(MS_Q + f) * gs + s] = q;
+        ok = ok && isfinite(q);
+    }
+    if (!ok) report(st, PMP_ERR_NONFINITE, s);
+}
+
 // Sink gather.  Writes the particle's per-axis Gaussian factors
 // exp(-d^2 / r_acc^2) to wts[s][3][W] for the deposit and Step 4.
 template <int R>
-__global__ void __launch_bounds__(128) k_gather_sink(KParams P, Box S, const double *__restrict__ u, Parts p,
+__global__ void __launch_bounds__(kSinkThreads) k_gather_sink(KParams P, Box S, const double *__restrict__ u, Parts p,
                                                      PlanPtrs pl, double *__restrict__ G, DevStatus *st)
 {
     constexpr int W = 2 * R + 1;
@@ -504,6 +544,11 @@ __device__ __forceinline__ void fb_pair_delta(const KParams &P, const Box &S, co
     const double d0 = ((double)c.i + 0.5) - x, d1 = ((double)c.j + 0.5) - y, d2 = ((double)c.k + 0.5) - z;
     const double dd = (d0 * d0 + d1 * d1) + d2 * d2;
     const double w = c.cnt == P.S3 ? 1.0 : (double)c.cnt / (double)P.S3;
+    if (P.kind == PMP_KIND_MASS) {
+#pragma unroll
+        for (int f = 0; f < NF; ++f) dU[f] = w * __ldg(G + (MS_Q + f) * gs + s);
+        return;
+    }
     double U[NF];
     load_cell(u, S, S.at(owner(c.i, S.n0), owner(c.j, S.n1), owner(c.k, S.n2)), U);
     const double vc[3] = {__ldg(G + FB_VX * gs + s), __ldg(G + FB_VY * gs + s), __ldg(G + FB_VZ * gs + s)};
@@ -558,16 +603,24 @@ __device__ __forceinline__ void fb_pair_delta_d(const double *__restrict__ u, co
 template <int R, bool FB>
 __global__ void __launch_bounds__(256) k_deposit_atomic(KParams P, Box S, const double *__restrict__ u, Box B,
                                                         double *__restrict__ b, Parts p,
-                                                        const double *__restrict__ G, PlanPtrs pl)
+                                                        const double *__restrict__ G, PlanPtrs pl,
+                                                        double *__restrict__ E)
 {
     constexpr int W = 2 * R + 1;
     constexpr int TAB = kPartsPerWarp * 3 * W;  // per warp: [8 particles][3 axes][W offsets]
     __shared__ double wtab[FB ? kMaxS3 + 1 : 1];
     __shared__ double dtab[FB ? 8 * TAB : 1], qtab[FB ? 8 * TAB : 1];
     __shared__ long long sidtab[8 * kPartsPerWarp];
+    // sinks: per warp the 8 particles' Gaussian factors [8][3W], K and host cells
+    __shared__ double swt[FB ? 1 : 8 * kPartsPerWarp * 3 * W];
+    __shared__ double sK[FB ? 1 : 8 * kPartsPerWarp];
+    __shared__ int shost[FB ? 1 : 8 * kPartsPerWarp * 3];
     if (FB) fill_omega_table(P, wtab);
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     double *dt = dtab + (FB ? wib * TAB : 0), *qt = qtab + (FB ? wib * TAB : 0);
+    double *wt = swt + (FB ? 0 : wib * kPartsPerWarp * 3 * W);
+    double *kt = sK + (FB ? 0 : wib * kPartsPerWarp);
+    int *ht = shost + (FB ? 0 : wib * kPartsPerWarp * 3);
     const long long nwarps = (long long)gridDim.x * (blockDim.x >> 5);
     for (long long t0 = ((long long)blockIdx.x * (blockDim.x >> 5) + wib) * kPartsPerWarp; t0 < p.count;
          t0 += nwarps * kPartsPerWarp) {
@@ -607,6 +660,23 @@ __global__ void __launch_bounds__(256) k_deposit_atomic(KParams P, Box S, const 
                 }
             }
             __syncwarp();
+        } else {
+            __syncwarp();
+            if (lane < kPartsPerWarp) sidtab[wib * kPartsPerWarp + lane] = sid;
+            __syncwarp();
+            for (int i = lane; i < kPartsPerWarp * 3 * W; i += 32) {
+                const int j = i / (3 * W);
+                if (t0 + j < p.count) wt[i] = __ldg(pl.wts + sidtab[wib * kPartsPerWarp + j] * (3 * W) + (i - j * 3 * W));
+            }
+            if (lane < kPartsPerWarp && t0 + lane < p.count) {
+                kt[lane] = __ldg(G + SK_K * p.count + sid);
+                int hx, hy, hz;
+                unpack_host(__ldg(pl.hosts + sid), hx, hy, hz);
+                ht[3 * lane] = hx;
+                ht[3 * lane + 1] = hy;
+                ht[3 * lane + 2] = hz;
+            }
+            __syncwarp();
         }
         for (unsigned g0 = 0; g0 < total; g0 += 32) {
             const unsigned g = g0 + lane;
@@ -626,7 +696,11 @@ __global__ void __launch_bounds__(256) k_deposit_atomic(KParams P, Box S, const 
                 const unsigned long long slot = (unsigned long long)(t0 + j) * pl.cap + (g - before);
                 const PairCell cell = unpack_pair(__ldg(pl.slots + slot), P.R);
                 double dU[NF];
-                if (FB) {
+                if (FB && P.kind == PMP_KIND_MASS) {
+                    const double w = cell.cnt == P.S3 ? 1.0 : wtab[cell.cnt];
+#pragma unroll
+                    for (int f = 0; f < NF; ++f) dU[f] = w * __ldg(G + (MS_Q + f) * p.count + s);
+                } else if (FB) {
                     int hx, hy, hz;
                     unpack_host(__ldg(pl.hosts + s), hx, hy, hz);
                     const int ix = j * 3 * W + (cell.i - hx + R), iy = j * 3 * W + W + (cell.j - hy + R),
@@ -635,12 +709,33 @@ __global__ void __launch_bounds__(256) k_deposit_atomic(KParams P, Box S, const 
                     const double w = cell.cnt == P.S3 ? 1.0 : wtab[cell.cnt];
                     fb_pair_delta_d(u, S, G, p.count, s, cell, w, dt[ix], dt[iy], dt[iz], dd, dU);
                 } else {
-                    double e;
-                    sink_pair_delta<R>(P, S, p, G, pl, s, cell, dU, e);
+                    const double *wj = wt + j * 3 * W;
+                    const double w = (wj[cell.i - ht[3 * j] + R] * wj[W + cell.j - ht[3 * j + 1] + R]) *
+                                     wj[2 * W + cell.k - ht[3 * j + 2] + R];
+                    const double2 *d = reinterpret_cast<const double2 *>(
+                        pl.drec + vidx(S, owner(cell.i, S.n0), owner(cell.j, S.n1), owner(cell.k, S.n2)) * kRec);
+                    const double2 d0 = __ldg(d), d1 = __ldg(d + 1), d2 = __ldg(d + 2);
+                    const double bh = kt[j] * w;
+                    const double a = bh >= d0.x ? bh : d0.x;
+                    dU[0] = -a;
+                    dU[1] = -(a * d0.y);
+                    dU[2] = -(a * d1.x);
+                    dU[3] = -(a * d1.y);
+                    dU[4] = -(a * d2.x);
                 }
                 const long long bc = B.at(cell.i, cell.j, cell.k);
+                if (E) {
+                    // App. A.1: the error bound of the cell grows by eps |buffer| after each addition
 #pragma unroll
-                for (int f = 0; f < NF; ++f) atomicAdd(b + (long long)f * B.fs + bc, dU[f]);
+                    for (int f = 0; f < NF; ++f) {
+                        const long long o = (long long)f * B.fs + bc;
+                        const double nv = atomicAdd(b + o, dU[f]) + dU[f];
+                        atomicAdd(E + o, kEpsMachine * fabs(nv));
+                    }
+                } else {
+#pragma unroll
+                    for (int f = 0; f < NF; ++f) atomicAdd(b + (long long)f * B.fs + bc, dU[f]);
+                }
             }
         }
     }
@@ -726,9 +821,12 @@ __device__ __forceinline__ void sink_return_add(double K, double w, double2 d0, 
 }
 
 template <int R>
-__global__ void __launch_bounds__(128) k_return_sinks(KParams P, Box S, Parts p, const double *__restrict__ G,
-                                                      PlanPtrs pl, DevStatus *st)
+__global__ void __launch_bounds__(kSinkThreads) k_return_sinks(KParams P, Box S, Parts p,
+                                                                const double *__restrict__ G, PlanPtrs pl,
+                                                                DevStatus *st)
 {
+    constexpr int W = 2 * R + 1;
+    __shared__ double wsm[3 * W * kSinkThreads];
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= p.count) return;
     const long long s = pl.perm ? (long long)pl.perm[t] : t;
@@ -737,13 +835,16 @@ __global__ void __launch_bounds__(128) k_return_sinks(KParams P, Box S, Parts p,
         report(st, bad, s);
         return;
     }
-    constexpr int W = 2 * R + 1;
     double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
     const unsigned long long b0 = (unsigned long long)t * pl.cap;
     const unsigned nc = pl.counts[t];
     int hx, hy, hz;
     unpack_host(__ldg(pl.hosts + s), hx, hy, hz);
-    const double *ws = pl.wts + s * (3 * W);
+    double *wc = wsm + threadIdx.x;
+    {
+        const double *ws = pl.wts + s * (3 * W);
+        for (int o = 0; o < 3 * W; ++o) wc[o * kSinkThreads] = __ldg(ws + o);
+    }
     const double K = __ldg(G + SK_K * p.count + s);
     unsigned q = 0;
     for (; q + kUnroll <= nc; q += kUnroll) {
@@ -756,9 +857,9 @@ __global__ void __launch_bounds__(128) k_return_sinks(KParams P, Box S, Parts p,
             d0[k] = __ldg(reinterpret_cast<const double2 *>(r));
             d1[k] = __ldg(reinterpret_cast<const double2 *>(r) + 1);
             e[k] = __ldg(r + 5);
-            wx[k] = __ldg(ws + c.i - hx + R);
-            wy[k] = __ldg(ws + W + c.j - hy + R);
-            wz[k] = __ldg(ws + 2 * W + c.k - hz + R);
+            wx[k] = wc[(c.i - hx + R) * kSinkThreads];
+            wy[k] = wc[(W + c.j - hy + R) * kSinkThreads];
+            wz[k] = wc[(2 * W + c.k - hz + R) * kSinkThreads];
         }
 #pragma unroll
         for (int k = 0; k < kUnroll; ++k)
@@ -767,7 +868,8 @@ __global__ void __launch_bounds__(128) k_return_sinks(KParams P, Box S, Parts p,
     for (; q < nc; ++q) {
         const PairCell c = unpack_pair(__ldg(pl.slots + b0 + q), P.R);
         const double *r = pl.drec + vidx(S, owner(c.i, S.n0), owner(c.j, S.n1), owner(c.k, S.n2)) * kRec;
-        const double w = (__ldg(ws + c.i - hx + R) * __ldg(ws + W + c.j - hy + R)) * __ldg(ws + 2 * W + c.k - hz + R);
+        const double w = (wc[(c.i - hx + R) * kSinkThreads] * wc[(W + c.j - hy + R) * kSinkThreads]) *
+                         wc[(2 * W + c.k - hz + R) * kSinkThreads];
         sink_return_add(K, w, __ldg(reinterpret_cast<const double2 *>(r)),
                         __ldg(reinterpret_cast<const double2 *>(r) + 1), __ldg(r + 5), a0, a1, a2, a3);
     }
@@ -821,7 +923,7 @@ void launch_plan(const KParams &P, const Box &S, const Parts &p, const PlanPtrs 
                  cudaStream_t stream)
 {
     if (p.count == 0) return;
-    if (P.kind == PMP_KIND_FEEDBACK) {
+    if (P.kind != PMP_KIND_SINK) {  // supernova and particle-mesh kernels both carry omega
         if (P.S == 4) {
             PMP_DISPATCH_R(P.R, (plan_one<RR, true, 4>(P, S, p, pl, st, stream)));
         } else {
@@ -839,22 +941,25 @@ void launch_gather(const KParams &P, const Box &S, const double *u, const Parts 
     const unsigned nb = blocks_for(p.count, 128);
     if (P.kind == PMP_KIND_FEEDBACK) {
         k_gather_fb<<<nb, 128, 0, stream>>>(P, S, u, p, pl, G, st);
+    } else if (P.kind == PMP_KIND_MASS) {
+        k_gather_mass<<<nb, 128, 0, stream>>>(P, S, p, pl, G, st);
     } else {
-        PMP_DISPATCH_R(P.R, (k_gather_sink<RR><<<nb, 128, 0, stream>>>(P, S, u, p, pl, G, st)));
+        PMP_DISPATCH_R(P.R, (k_gather_sink<RR><<<blocks_for(p.count, kSinkThreads), kSinkThreads, 0, stream>>>(
+                                 P, S, u, p, pl, G, st)));
     }
 }
 
 void launch_deposit_atomic(const KParams &P, const Box &S, const double *u, const Box &B, double *b, const Parts &p,
-                           const double *G, const PlanPtrs &pl, cudaStream_t stream)
+                           const double *G, const PlanPtrs &pl, double *E, cudaStream_t stream)
 {
     if (p.count == 0) return;
     const long long warps = (p.count + kPartsPerWarp - 1) / kPartsPerWarp;
     const long long blocks_needed = (warps + 7) / 8;
     const unsigned nb = (unsigned)(blocks_needed < 152LL * 64 ? blocks_needed : 152LL * 64);
-    if (P.kind == PMP_KIND_FEEDBACK) {
-        PMP_DISPATCH_R(P.R, (k_deposit_atomic<RR, true><<<nb, 256, 0, stream>>>(P, S, u, B, b, p, G, pl)));
+    if (P.kind != PMP_KIND_SINK) {
+        PMP_DISPATCH_R(P.R, (k_deposit_atomic<RR, true><<<nb, 256, 0, stream>>>(P, S, u, B, b, p, G, pl, E)));
     } else {
-        PMP_DISPATCH_R(P.R, (k_deposit_atomic<RR, false><<<nb, 256, 0, stream>>>(P, S, u, B, b, p, G, pl)));
+        PMP_DISPATCH_R(P.R, (k_deposit_atomic<RR, false><<<nb, 256, 0, stream>>>(P, S, u, B, b, p, G, pl, E)));
     }
 }
 
@@ -870,7 +975,7 @@ void launch_segment_sum(const KParams &P, const Box &S, const double *u, const B
                         const unsigned *vals, cudaStream_t stream)
 {
     const unsigned nb = 152u * 32u;
-    if (P.kind == PMP_KIND_FEEDBACK) {
+    if (P.kind != PMP_KIND_SINK) {
         k_segment_sum<1, true><<<nb, 128, 0, stream>>>(P, S, u, B, b, p, G, pl, total, keys, vals);
     } else {
         PMP_DISPATCH_R(P.R, (k_segment_sum<RR, false><<<nb, 128, 0, stream>>>(P, S, u, B, b, p, G, pl, total, keys,
@@ -882,8 +987,8 @@ void launch_return_sinks(const KParams &P, const Box &S, const Parts &p, const d
                          DevStatus *st, cudaStream_t stream)
 {
     if (p.count == 0) return;
-    const unsigned nb = blocks_for(p.count, 128);
-    PMP_DISPATCH_R(P.R, (k_return_sinks<RR><<<nb, 128, 0, stream>>>(P, S, p, G, pl, st)));
+    const unsigned nb = blocks_for(p.count, kSinkThreads);
+    PMP_DISPATCH_R(P.R, (k_return_sinks<RR><<<nb, kSinkThreads, 0, stream>>>(P, S, p, G, pl, st)));
 }
 
 }  // namespace pmp

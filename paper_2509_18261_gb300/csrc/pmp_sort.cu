@@ -32,6 +32,14 @@ cudaError_t sort_host_keys(void *temp, size_t temp_bytes, const unsigned *kin, u
 }
 
 // Exclusive prefix sum of 32-bit counts accumulated in 64 bits.
+size_t scan_temp_bytes(long long n)
+{
+    size_t b = 0;
+    cub::DeviceScan::ExclusiveScan(nullptr, b, (const unsigned *)nullptr, (unsigned long long *)nullptr,
+                                   cuda::std::plus<unsigned long long>(), 0ULL, n > 0 ? n : 1);
+    return b;
+}
+
 cudaError_t scan_counts(void *temp, size_t temp_bytes, const unsigned *counts, unsigned long long *offsets,
                         long long n, cudaStream_t stream)
 {

@@ -18,18 +18,19 @@ import torch
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_lib", "libpmp.so")
 
-FEEDBACK, SINK = 0, 1
-ATOMIC, SORTED = 0, 1
-KINDS = {"feedback": FEEDBACK, "sink": SINK}
-MODES = {"atomic": ATOMIC, "sorted": SORTED}
+FEEDBACK, SINK, MASS = 0, 1, 2
+ATOMIC, SORTED, ROUNDED = 0, 1, 2
+KINDS = {"feedback": FEEDBACK, "sink": SINK, "mass": MASS}
+MODES = {"atomic": ATOMIC, "sorted": SORTED, "rounded": ROUNDED}
 STATUS = {
     0: "PMP_OK", 1: "PMP_ERR_ARG", 2: "PMP_ERR_GHOST_TOO_THIN", 3: "PMP_ERR_PARTICLE_OUTSIDE",
     4: "PMP_ERR_NONFINITE", 5: "PMP_ERR_TIMEOUT", 6: "PMP_ERR_WORKSPACE", 7: "PMP_ERR_CUDA",
 }
 EXPORTS = [
-    "pmp_create", "pmp_destroy", "pmp_set_stream", "pmp_gathered_rows", "pmp_workspace_size", "pmp_zero_buffer",
+    "pmp_create", "pmp_destroy", "pmp_set_stream", "pmp_set_rounding_margin", "pmp_gathered_rows", "pmp_workspace_size", "pmp_zero_buffer",
     "pmp_gather", "pmp_deposit", "pmp_fold_ghosts", "pmp_apply_limited", "pmp_backward", "pmp_get_error",
     "pmp_limiter_counts", "pmp_timing_enable", "pmp_timing_read", "pmp_deposit_noalloc",
+    "pmp_create_sinks_workspace_size", "pmp_create_sinks",
     "pmp_batch_create", "pmp_batch_set_particles", "pmp_batch_set_strategy", "pmp_batch_strategies",
     "pmp_batch_autotune", "pmp_cycle_batched", "pmp_batch_info", "pmp_batch_destroy",
 ]
@@ -99,6 +100,7 @@ def load():
         "pmp_create": ([ctypes.POINTER(vp), P, vp], i32),
         "pmp_destroy": ([vp], None),
         "pmp_set_stream": ([vp, vp], i32),
+        "pmp_set_rounding_margin": ([vp, i32], i32),
         "pmp_gathered_rows": ([i32], i32),
         "pmp_workspace_size": ([vp, M, i64, i32, ctypes.POINTER(ctypes.c_size_t)], i32),
         "pmp_zero_buffer": ([vp, M], i32),
@@ -112,6 +114,8 @@ def load():
         "pmp_timing_enable": ([vp, i32], i32),
         "pmp_timing_read": ([vp, ctypes.POINTER(_KernelTime), i32, ctypes.POINTER(i32)], i32),
         "pmp_deposit_noalloc": ([P, M, Pa, vp, M, vp], i32),
+        "pmp_create_sinks_workspace_size": ([vp, M, ctypes.POINTER(ctypes.c_size_t)], i32),
+        "pmp_create_sinks": ([vp, M, M, i64, vp, vp, vp, vp, vp, vp, vp, vp, vp, ctypes.c_size_t], i32),
         "pmp_batch_create": ([vp, ctypes.POINTER(_Patch), i32, i32, ctypes.c_double, i64, ctypes.POINTER(vp)], i32),
         "pmp_batch_set_particles": ([vp, ctypes.POINTER(i64)], i32),
         "pmp_batch_set_strategy": ([vp, i32], i32),
@@ -202,6 +206,32 @@ class Context:
 
 def pmp_create(params):
     return Context(params)
+
+
+def pmp_create_sinks_workspace_size(ctx, state):
+    out = ctypes.c_size_t()
+    _check("pmp_create_sinks_workspace_size",
+           load().pmp_create_sinks_workspace_size(ctx.h, ctypes.byref(state.c()), ctypes.byref(out)))
+    return out.value
+
+
+def pmp_create_sinks(ctx, state, buffer, out, count, workspace):
+    """Sink creation (Sec. 3.1.2): ``out`` is a dict of device arrays x, y, z,
+    m, px, py, pz (their length is the capacity); ``count`` a device int64
+    tensor of one element receiving the number of qualifying cells."""
+    ctx._sync_stream()
+    cap = int(out["x"].numel())
+    ws, wsb = _ws(workspace)
+    args = [_ptr(out[k]) for k in ("x", "y", "z", "m", "px", "py", "pz")]
+    if not (isinstance(count, torch.Tensor) and count.is_cuda and count.dtype == torch.int64 and count.numel() >= 1):
+        raise TypeError("count must be a CUDA int64 tensor")
+    _check("pmp_create_sinks", load().pmp_create_sinks(ctx.h, ctypes.byref(state.c()), ctypes.byref(buffer.c()),
+                                                       cap, *args, ctypes.c_void_p(count.data_ptr()), ws, wsb))
+
+
+def pmp_set_rounding_margin(ctx, M):
+    """Safety margin M of the ROUNDED deposit (App. A.1)."""
+    _check("pmp_set_rounding_margin", load().pmp_set_rounding_margin(ctx.h, int(M)))
 
 
 def pmp_gathered_rows(kind):

@@ -179,6 +179,14 @@ def split_particles(p, idx):
 
 # --- parameter sets (code units; the values each workload uses) -------------
 
+def mass_params(**kw):
+    """Particle-mesh (PM/PIC) deposit: Steps 1, 2 and 5 of Sec. 2.2 with the
+    supernova kernel (r_K = 2, S = 4 sub-points per axis)."""
+    p = feedback_params(kind="mass")
+    p.update(kw)
+    return p
+
+
 def feedback_params(**kw):
     p = dict(
         kind="feedback",

@@ -128,3 +128,33 @@ def test_sorted_mode_is_reproducible(orc):
     a = gpu_pass(w["fb_params"], w["box"], w["state"], w["fb"], mode="sorted")
     b = gpu_pass(w["fb_params"], w["box"], w["state"], w["fb"], mode="sorted")
     assert_bits_equal(a["state"], b["state"], "two sorted runs")
+
+
+@pytest.mark.parametrize("mode", ["sorted", "atomic"])
+@pytest.mark.parametrize(
+    "n,g,rK,S,periodic",
+    [((12, 10, 9), 4, 2.0, 4, (1, 1, 1)), ((7, 8, 6), 3, 2.5, 3, (1, 0, 1)), ((5, 5, 5), 2, 1.0, 1, (0, 0, 0))],
+)
+def test_mass_deposit(orc, mode, n, g, rK, S, periodic):
+    """Particle-mesh kind (Steps 1, 2, 5): every row spread by omega."""
+    rng = np.random.default_rng(31 + g)
+    box = syn.Box(n, g)
+    state = syn.gas_state(rng, box)
+    parts = _cloud(rng, n, 40)
+    g_, ref = _check_pass(orc, syn.mass_params(r_K=rK, subsample=S), box, state, parts, mode, periodic=periodic)
+    assert ref["counts"][0] == 0
+    for k in parts:
+        assert_bits_equal(g_["parts"][k], parts[k], f"particle {k} unchanged")
+
+
+def test_mass_deposit_without_energy(orc):
+    rng = np.random.default_rng(5)
+    box = syn.Box((10, 10, 10), 4)
+    state = syn.gas_state(rng, box)
+    parts = _cloud(rng, box.n, 20)
+    no_e = {k: v for k, v in parts.items() if k != "e"}
+    g = gpu_pass(syn.mass_params(), box, state, no_e, mode="sorted")
+    zero_e = dict(parts, e=np.zeros(20))
+    ref = oracle_pass(orc, syn.mass_params(), box, state, zero_e)
+    assert_bits_equal(valid_flat(box, g["state"]), valid_flat(box, ref["state"]), "state")
+    assert np.all(box.valid(g["buf"])[4] == 0.0)
