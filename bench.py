@@ -53,6 +53,8 @@ def parse():
     ap.add_argument("--cpu-sample-n", type=int, default=128)
     ap.add_argument("--n", type=int, default=None,
                     help="shrink the box to n^3 at equal particle density (profiling captures)")
+    ap.add_argument("--keep-cluster-size", action="store_true",
+                    help="with --n: fewer clusters of the full size instead of as many smaller ones")
     return ap.parse_args()
 
 
@@ -260,7 +262,8 @@ def run_ours(args, world, rank, local):
 
     if args.n:
         full = syn.WORKLOADS[args.workload]["n"]
-        w = syn.make_workload(args.workload, n=args.n, count_scale=(args.n / full) ** 3)
+        w = syn.make_workload(args.workload, n=args.n, count_scale=(args.n / full) ** 3,
+                              keep_cluster_size=args.keep_cluster_size)
     else:
         w = syn.make_workload(args.workload)
     box = w["box"]
@@ -359,6 +362,8 @@ def run_ours(args, world, rank, local):
     lim_fb = pmp.pmp_limiter_counts(P_fb.ctx)
     lim_sk = pmp.pmp_limiter_counts(P_sk.ctx)
 
+    creation = sink_creation(P_sk, stream)
+
     # e2e: pinned host inputs -> device -> cycle -> results back to pinned host,
     # every step, through the public calls
     e2e = end_to_end(args, w, world, state, fb, sk, P_fb, P_sk, cycle, stream)
@@ -403,6 +408,7 @@ def run_ours(args, world, rank, local):
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clk,
     }
+    result["sink_creation_c5_512"] = creation
     result["pm_deposit_c5_512"] = pm_deposit(args, w, state, fb, stream)
     result["fwd_bwd_c4_128"] = fwd_bwd(args)
     if not args.no_batched:
@@ -522,6 +528,32 @@ def end_to_end(args, w, world, state, fb, sk, P_fb, P_sk, cycle, stream):
             "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo, "steps": steps,
             "serial_ms_per_step": serial_ms,
             "overlap": "double-buffered: the copies of step k+1 (in) and k-1 (out) run on copy streams during step k"}
+
+
+def sink_creation(P_sk, stream):
+    """Sink creation (Sec. 3.1.2) on the 512^3 state right after the timed
+    cycles, with the last sink pass's summed buffer: CUDA-event time of one
+    pmp_create_sinks (flags, scan, creation) and the number of new sinks."""
+    import torch
+
+    from paper_2509_18261_gb300 import pmp
+
+    ws = torch.empty(pmp.pmp_create_sinks_workspace_size(P_sk.ctx, P_sk.state), dtype=torch.uint8, device="cuda")
+    cap = 1 << 20
+    out = {k: torch.empty(cap, dtype=torch.float64, device="cuda") for k in ("x", "y", "z", "m", "px", "py", "pz")}
+    cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    pmp.pmp_create_sinks(P_sk.ctx, P_sk.state, P_sk.buffer, out, cnt, ws)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    code, idx = pmp.pmp_get_error(P_sk.ctx)
+    if code:
+        raise RuntimeError(f"sink creation: device error {code} at {idx}")
+    n = int(cnt.item())
+    return {"ms": e0.elapsed_time(e1), "new_sinks": n,
+            "new_mass": float(out["m"][:min(n, cap)].sum().item()) if n else 0.0,
+            "cells_per_s": P_sk.box.ncells_valid / (e0.elapsed_time(e1) * 1e-3)}
 
 
 def pm_deposit(args, w, state, fb, stream):

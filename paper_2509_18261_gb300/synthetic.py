@@ -252,11 +252,13 @@ WORKLOADS = {
 WORKLOAD_INDEX = {"c1_32": 0, "c2_256": 1, "c3_batched": 2, "c4_128": 3, "c5_512": 4}
 
 
-def make_workload(name, n=None, count_scale=1.0, ghost_fill=np.nan):
+def make_workload(name, n=None, count_scale=1.0, ghost_fill=np.nan, keep_cluster_size=False):
     """Build the named workload (optionally shrunk to box ``n``, counts scaled).
 
-    Returns dict(box, state, fb, sink, fb_params, sink_params); ``fb`` / ``sink``
-    are None when the workload has no particles of that kind.
+    With counts scaled, the clusters keep their number and shrink, or with
+    ``keep_cluster_size`` keep their size and become fewer.  Returns
+    dict(box, state, fb, sink, fb_params, sink_params); ``fb`` / ``sink`` are
+    None when the workload has no particles of that kind.
     """
     spec = WORKLOADS[name]
     rng = np.random.default_rng(SEED_BASE + WORKLOAD_INDEX[name])
@@ -282,7 +284,12 @@ def make_workload(name, n=None, count_scale=1.0, ghost_fill=np.nan):
         f = spec["mixed"]
         cnt = scaled(f["count"])
         ncl = f["nclusters"]
-        cl = scaled(f["clustered"]) // ncl * ncl
+        if keep_cluster_size:
+            size = f["clustered"] // ncl
+            ncl = max(1, int(round(ncl * count_scale)))
+            cl = ncl * size
+        else:
+            cl = scaled(f["clustered"]) // ncl * ncl
         allp = particles(rng, box.n, cnt, "feedback", clustered=cl, nclusters=ncl)
         nsink = cnt // f["sink_fraction"]
         fb = split_particles(allp, np.arange(0, cnt - nsink))
