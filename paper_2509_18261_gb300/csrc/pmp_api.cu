@@ -124,7 +124,7 @@ long long max_pairs_per_particle(double rK)
 
 struct Layout {
     size_t keys, ids, keys2, ids2, counts, slots, hosts, fr, wts, aux, eta, queue, qcount, offsets, skeys, skeys2,
-        svals, svals2;
+        svals, svals2, soffs, slong, scnt;
     size_t temp, temp_bytes, total;
     long long cap, aux_stride;
 };
@@ -171,6 +171,9 @@ Layout layout(const pmp_params &p, long long n, long long nvalid, int mode)
         L.skeys2 = take(4 * pairs);
         L.svals = take(4 * pairs);
         L.svals2 = take(4 * pairs);
+        L.soffs = take(4 * pairs);  // first pair of each run of equal cells
+        L.slong = take(4 * pairs);  // runs longer than a warp
+        L.scnt = take(16);          // number of runs, number of long runs
     }
     L.temp_bytes = pmp::cub_temp_bytes(n, (long long)pairs, sorted);
     L.temp = take(L.temp_bytes);
@@ -617,9 +620,18 @@ pmp_status pmp_deposit(pmp_ctx *ctx, const pmp_mesh *state, const pmp_particles 
     while (end_bit < 32 && (1LL << end_bit) < B.ncells) ++end_bit;
     if (pmp::sort_pairs(w + L.temp, L.temp_bytes, k1, k2, v1, v2, (long long)total, end_bit, st) != cudaSuccess)
         return PMP_ERR_CUDA;
+    // runs of equal cells: unique cells into k1, lengths into v1 (both free
+    // after the sort), first pairs into soffs
+    unsigned *offs = reinterpret_cast<unsigned *>(w + L.soffs), *longq = reinterpret_cast<unsigned *>(w + L.slong);
+    unsigned long long *nruns = reinterpret_cast<unsigned long long *>(w + L.scnt);
+    unsigned *nlong = reinterpret_cast<unsigned *>(w + L.scnt + 8);
+    if (pmp::encode_runs(w + L.temp, L.temp_bytes, k2, k1, v1, nruns, (long long)total, st) != cudaSuccess ||
+        pmp::scan_lengths(w + L.temp, L.temp_bytes, v1, offs, (long long)total, st) != cudaSuccess)
+        return PMP_ERR_CUDA;
     {
         Timed tm(ctx, "segment_sum");
-        pmp::launch_segment_sum(P, S, state->data, B, buffer->data, q, gathered, pl, offsets + q.count, k2, v2, st);
+        pmp::launch_segment_sum(P, S, state->data, B, buffer->data, q, gathered, pl, nruns, k1, v1, offs, v2, longq,
+                                nlong, st);
     }
     return last_launch();
 }

@@ -44,9 +44,13 @@ void launch_deposit_atomic(const KParams &P, const Box &S, const double *u, cons
                            const double *G, const PlanPtrs &pl, double *E, cudaStream_t stream);
 void launch_sort_keys(const KParams &P, const Box &B, const Parts &p, const PlanPtrs &pl,
                       const unsigned long long *offsets, unsigned *keys, unsigned *vals, cudaStream_t stream);
+// Sorted deposit, per run of equal buffer cells (uniq/lens/offs from
+// encode_runs and scan_lengths; nruns on the device): short runs one thread
+// each, runs longer than a warp one warp each (queued in longq/nlong).
 void launch_segment_sum(const KParams &P, const Box &S, const double *u, const Box &B, double *b, const Parts &p,
-                        const double *G, const PlanPtrs &pl, const unsigned long long *total, const unsigned *keys,
-                        const unsigned *vals, cudaStream_t stream);
+                        const double *G, const PlanPtrs &pl, const unsigned long long *nruns, const unsigned *uniq,
+                        const unsigned *lens, const unsigned *offs, const unsigned *vals, unsigned *longq,
+                        unsigned *nlong, cudaStream_t stream);
 void launch_return_sinks(const KParams &P, const Box &S, const Parts &p, const double *G, const PlanPtrs &pl,
                          DevStatus *st, cudaStream_t stream);
 
@@ -86,5 +90,11 @@ cudaError_t scan_counts(void *temp, size_t temp_bytes, const unsigned *counts, u
                         long long n, cudaStream_t stream);
 cudaError_t sort_pairs(void *temp, size_t temp_bytes, const unsigned *kin, unsigned *kout, const unsigned *vin,
                        unsigned *vout, long long n, int end_bit, cudaStream_t stream);
+// Runs of equal sorted keys: unique keys, run lengths and their count; the
+// exclusive sum of the lengths gives each run's first pair.
+cudaError_t encode_runs(void *temp, size_t temp_bytes, const unsigned *keys, unsigned *uniq, unsigned *lens,
+                        unsigned long long *nruns, long long n, cudaStream_t stream);
+cudaError_t scan_lengths(void *temp, size_t temp_bytes, const unsigned *lens, unsigned *offs, long long n,
+                         cudaStream_t stream);
 
 }  // namespace pmp

@@ -763,40 +763,108 @@ __global__ void __launch_bounds__(128) k_sort_keys(KParams P, Box B, long long n
     }
 }
 
-// One thread per run of equal keys (a buffer cell): the run's pairs, which the
-// stable sort kept in particle-index order, are added in that order on top of
-// what the buffer holds.
+// Deposition value of pair `slot` of the index-order plan (the sorted mode
+// plans in index order, so the slot's row is the particle).
 template <int R, bool FB>
-__global__ void __launch_bounds__(128) k_segment_sum(KParams P, Box S, const double *__restrict__ u, Box B,
-                                                     double *__restrict__ b, Parts p, const double *__restrict__ G,
-                                                     PlanPtrs pl, const unsigned long long *__restrict__ total_ptr,
-                                                     const unsigned *__restrict__ keys,
-                                                     const unsigned *__restrict__ vals)
+__device__ __forceinline__ void sorted_pair_delta(const KParams &P, const Box &S, const double *__restrict__ u,
+                                                  const Parts &p, const double *__restrict__ G, const PlanPtrs &pl,
+                                                  unsigned long long slot, double dU[NF])
 {
-    const unsigned long long total = *total_ptr;
+    const long long s = (long long)(slot / pl.cap);
+    const PairCell c = unpack_pair(pl.slots[slot], P.R);
+    if (FB) {
+        fb_pair_delta(P, S, u, p, G, s, c, dU);
+    } else {
+        double e;
+        sink_pair_delta<R>(P, S, p, G, pl, s, c, dU, e);
+    }
+}
+
+constexpr unsigned kLongRun = 32;  // runs longer than this get a warp
+
+// One thread per run of equal keys (a buffer cell) of at most kLongRun pairs:
+// the run's pairs, which the stable sort kept in particle-index order, are
+// added in that order on top of what the buffer holds.  Longer runs are
+// queued for k_segment_long.
+template <int R, bool FB>
+__global__ void __launch_bounds__(128) k_segment_runs(KParams P, Box S, const double *__restrict__ u, Box B,
+                                                      double *__restrict__ b, Parts p, const double *__restrict__ G,
+                                                      PlanPtrs pl, const unsigned long long *__restrict__ nruns_ptr,
+                                                      const unsigned *__restrict__ uniq,
+                                                      const unsigned *__restrict__ lens,
+                                                      const unsigned *__restrict__ offs,
+                                                      const unsigned *__restrict__ vals, unsigned *__restrict__ longq,
+                                                      unsigned *__restrict__ nlong)
+{
+    const unsigned long long nruns = *nruns_ptr;
     const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
-    for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += stride) {
-        const unsigned key = keys[i];
-        if (i > 0 && keys[i - 1] == key) continue;
+    for (unsigned long long r = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; r < nruns; r += stride) {
+        const unsigned len = lens[r];
+        if (len > kLongRun) {
+            longq[atomicAdd(nlong, 1u)] = (unsigned)r;
+            continue;
+        }
+        const unsigned key = uniq[r], o = offs[r];
         double acc[NF];
 #pragma unroll
         for (int f = 0; f < NF; ++f) acc[f] = b[(long long)f * B.fs + key];
-        for (unsigned long long j = i; j < total && keys[j] == key; ++j) {
-            const unsigned long long slot = vals[j];
-            const long long s = (long long)(slot / pl.cap);  // index-order plan: slot row = particle
-            const PairCell c = unpack_pair(pl.slots[slot], P.R);
+        for (unsigned j = 0; j < len; ++j) {
             double dU[NF];
-            if (FB) {
-                fb_pair_delta(P, S, u, p, G, s, c, dU);
-            } else {
-                double e;
-                sink_pair_delta<R>(P, S, p, G, pl, s, c, dU, e);
-            }
+            sorted_pair_delta<R, FB>(P, S, u, p, G, pl, vals[o + j], dU);
 #pragma unroll
             for (int f = 0; f < NF; ++f) acc[f] = acc[f] + dU[f];
         }
 #pragma unroll
         for (int f = 0; f < NF; ++f) b[(long long)f * B.fs + key] = acc[f];
+    }
+}
+
+// One warp per long run: the lanes compute 32 consecutive pairs' values at a
+// time, lane 0 adds them in run order (the same sequence of additions as a
+// single thread would make).
+template <int R, bool FB>
+__global__ void __launch_bounds__(128) k_segment_long(KParams P, Box S, const double *__restrict__ u, Box B,
+                                                      double *__restrict__ b, Parts p, const double *__restrict__ G,
+                                                      PlanPtrs pl, const unsigned *__restrict__ uniq,
+                                                      const unsigned *__restrict__ lens,
+                                                      const unsigned *__restrict__ offs,
+                                                      const unsigned *__restrict__ vals,
+                                                      const unsigned *__restrict__ longq,
+                                                      const unsigned *__restrict__ nlong_ptr)
+{
+    __shared__ double stage[4][32][NF + 1];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const unsigned nlong = *nlong_ptr;
+    const unsigned nw = gridDim.x * (blockDim.x >> 5);
+    for (unsigned q = blockIdx.x * (blockDim.x >> 5) + wib; q < nlong; q += nw) {
+        const unsigned r = longq[q];
+        const unsigned key = uniq[r], o = offs[r], len = lens[r];
+        double acc[NF];
+        if (lane == 0) {
+#pragma unroll
+            for (int f = 0; f < NF; ++f) acc[f] = b[(long long)f * B.fs + key];
+        }
+        for (unsigned c0 = 0; c0 < len; c0 += 32) {
+            if (c0 + lane < len) {
+                double dU[NF];
+                sorted_pair_delta<R, FB>(P, S, u, p, G, pl, vals[o + c0 + lane], dU);
+#pragma unroll
+                for (int f = 0; f < NF; ++f) stage[wib][lane][f] = dU[f];
+            }
+            __syncwarp();
+            if (lane == 0) {
+                const unsigned m = len - c0 < 32u ? len - c0 : 32u;
+                for (unsigned l = 0; l < m; ++l) {
+#pragma unroll
+                    for (int f = 0; f < NF; ++f) acc[f] = acc[f] + stage[wib][l][f];
+                }
+            }
+            __syncwarp();
+        }
+        if (lane == 0) {
+#pragma unroll
+            for (int f = 0; f < NF; ++f) b[(long long)f * B.fs + key] = acc[f];
+        }
     }
 }
 
@@ -971,15 +1039,23 @@ void launch_sort_keys(const KParams &P, const Box &B, const Parts &p, const Plan
 }
 
 void launch_segment_sum(const KParams &P, const Box &S, const double *u, const Box &B, double *b, const Parts &p,
-                        const double *G, const PlanPtrs &pl, const unsigned long long *total, const unsigned *keys,
-                        const unsigned *vals, cudaStream_t stream)
+                        const double *G, const PlanPtrs &pl, const unsigned long long *nruns, const unsigned *uniq,
+                        const unsigned *lens, const unsigned *offs, const unsigned *vals, unsigned *longq,
+                        unsigned *nlong, cudaStream_t stream)
 {
     const unsigned nb = 152u * 32u;
+    cudaMemsetAsync(nlong, 0, sizeof(unsigned), stream);
     if (P.kind != PMP_KIND_SINK) {
-        k_segment_sum<1, true><<<nb, 128, 0, stream>>>(P, S, u, B, b, p, G, pl, total, keys, vals);
+        k_segment_runs<1, true><<<nb, 128, 0, stream>>>(P, S, u, B, b, p, G, pl, nruns, uniq, lens, offs, vals, longq,
+                                                        nlong);
+        k_segment_long<1, true><<<152u * 8u, 128, 0, stream>>>(P, S, u, B, b, p, G, pl, uniq, lens, offs, vals, longq,
+                                                                nlong);
     } else {
-        PMP_DISPATCH_R(P.R, (k_segment_sum<RR, false><<<nb, 128, 0, stream>>>(P, S, u, B, b, p, G, pl, total, keys,
-                                                                               vals)));
+        PMP_DISPATCH_R(P.R, (k_segment_runs<RR, false><<<nb, 128, 0, stream>>>(P, S, u, B, b, p, G, pl, nruns, uniq,
+                                                                                lens, offs, vals, longq, nlong)));
+        PMP_DISPATCH_R(P.R, (k_segment_long<RR, false><<<152u * 8u, 128, 0, stream>>>(P, S, u, B, b, p, G, pl, uniq,
+                                                                                       lens, offs, vals, longq,
+                                                                                       nlong)));
     }
 }
 

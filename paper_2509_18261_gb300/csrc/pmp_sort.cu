@@ -2,6 +2,7 @@
 // sort of particles by host cell, the prefix sum of pair counts, and the
 // stable radix sort of (buffer cell, pair) keys.
 #include <cub/device/device_radix_sort.cuh>
+#include <cub/device/device_run_length_encode.cuh>
 #include <cub/device/device_scan.cuh>
 
 #include "pmp_launch.h"
@@ -17,12 +18,19 @@ size_t cub_temp_bytes(long long n, long long max_pairs, bool sorted)
     if (sorted)
         cub::DeviceScan::ExclusiveScan(nullptr, b, (const unsigned *)nullptr, (unsigned long long *)nullptr,
                                        cuda::std::plus<unsigned long long>(), 0ULL, nn + 1);
-    if (sorted)
+    size_t d = 0, e = 0;
+    if (sorted) {
+        const long long mp = max_pairs > 0 ? max_pairs : 1;
         cub::DeviceRadixSort::SortPairs(nullptr, c, (const unsigned *)nullptr, (unsigned *)nullptr,
-                                        (const unsigned *)nullptr, (unsigned *)nullptr,
-                                        max_pairs > 0 ? max_pairs : 1, 0, 32);
+                                        (const unsigned *)nullptr, (unsigned *)nullptr, mp, 0, 32);
+        cub::DeviceRunLengthEncode::Encode(nullptr, d, (const unsigned *)nullptr, (unsigned *)nullptr,
+                                           (unsigned *)nullptr, (unsigned long long *)nullptr, mp);
+        cub::DeviceScan::ExclusiveSum(nullptr, e, (const unsigned *)nullptr, (unsigned *)nullptr, mp);
+    }
     size_t m = a > b ? a : b;
-    return m > c ? m : c;
+    m = m > c ? m : c;
+    m = m > d ? m : d;
+    return m > e ? m : e;
 }
 
 cudaError_t sort_host_keys(void *temp, size_t temp_bytes, const unsigned *kin, unsigned *kout, const unsigned *vin,
@@ -45,6 +53,18 @@ cudaError_t scan_counts(void *temp, size_t temp_bytes, const unsigned *counts, u
 {
     return cub::DeviceScan::ExclusiveScan(temp, temp_bytes, counts, offsets, cuda::std::plus<unsigned long long>(),
                                           0ULL, n, stream);
+}
+
+cudaError_t encode_runs(void *temp, size_t temp_bytes, const unsigned *keys, unsigned *uniq, unsigned *lens,
+                        unsigned long long *nruns, long long n, cudaStream_t stream)
+{
+    return cub::DeviceRunLengthEncode::Encode(temp, temp_bytes, keys, uniq, lens, nruns, n, stream);
+}
+
+cudaError_t scan_lengths(void *temp, size_t temp_bytes, const unsigned *lens, unsigned *offs, long long n,
+                         cudaStream_t stream)
+{
+    return cub::DeviceScan::ExclusiveSum(temp, temp_bytes, lens, offs, n, stream);
 }
 
 cudaError_t sort_pairs(void *temp, size_t temp_bytes, const unsigned *kin, unsigned *kout, const unsigned *vin,

@@ -158,3 +158,26 @@ def test_mass_deposit_without_energy(orc):
     ref = oracle_pass(orc, syn.mass_params(), box, state, zero_e)
     assert_bits_equal(valid_flat(box, g["state"]), valid_flat(box, ref["state"]), "state")
     assert np.all(box.valid(g["buf"])[4] == 0.0)
+
+
+@pytest.mark.parametrize("kind", ["feedback", "sink"])
+def test_sorted_mode_long_runs(orc, kind):
+    """Clustered particles: many buffer cells take more contributions than a
+    warp has lanes, so the sorted mode's warp-per-run path runs; still the
+    oracle's bits."""
+    rng = np.random.default_rng(17)
+    box = syn.Box((16, 14, 12), 4)
+    state = syn.gas_state(rng, box)
+    parts = syn.particles(rng, box.n, 600, kind, clustered=600, nclusters=2)
+    params = syn.feedback_params() if kind == "feedback" else syn.sink_params(dt=0.01)
+    _, ref = _check_pass(orc, params, box, state, parts, "sorted")
+    # contributions per cell: at least one cell with more than 32
+    n = np.zeros(box.ncells_padded)
+    for s in range(len(parts["x"])):
+        one = {k: v[s:s + 1] for k, v in parts.items()}
+        ijk, _ = orc.deltas(params, box, state, one)
+        g = box.g
+        px, py = box.padded[0], box.padded[1]
+        for i, j, k in ijk:
+            n[((k + g) * py + (j + g)) * px + (i + g)] += 1
+    assert n.max() > 32
