@@ -253,6 +253,22 @@ pmp_status pmp_backward(pmp_ctx *ctx, const pmp_mesh *state_in, const pmp_mesh *
                         const double *gathered, const double *gU, double *g_out, void *workspace,
                         size_t workspace_bytes);
 
+/* Auxiliary conserved fields under accretion (Sec. 3.1.1, the extensions
+ * beyond minimal hydrodynamics): the dual-energy internal energy density and
+ * species (passive scalar) densities change at fixed specific value, as the
+ * paper prescribes (internal energy per unit mass in place of e_sp + v^2/2;
+ * Delta rho_sp = (rho_sp / rho) Delta rho).  Every pair's change of a field X
+ * is -a X/rho with the cell's X/rho, so the summed change is
+ * (X/rho) Delta rho^sum and the limited update is
+ *   X := X + eta ((X / rho) Delta rho^sum)
+ * with eta the cell's accretion limiter; X/rho is thus kept, to rounding.
+ * For a SINK context, after pmp_fold_ghosts and BEFORE pmp_apply_limited of
+ * the same pass (rho must be the pre-update density).  extra: device,
+ * n_extra fields of extra_stride doubles each, laid out like the state's
+ * cells (only valid cells are read or written). */
+pmp_status pmp_apply_extra(pmp_ctx *ctx, const pmp_mesh *state, const pmp_mesh *buffer, double *extra, int32_t n_extra,
+                           int64_t extra_stride);
+
 /* Sink creation (Sec. 3.1.2), for a SINK context after its accretion pass,
  * with that pass's summed buffer retained (Sec. 3.1, item 2).  A valid cell
  * becomes a new sink when (a) rho > rho_Tr (Eq. truelove with the cell's own

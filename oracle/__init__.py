@@ -195,6 +195,17 @@ def deposit_rounded(params, box, state, parts, gathered, buf, M=28, dx=1.0, peri
     return E
 
 
+def apply_extra(params, box, state, buf, extra, dx=1.0, periodic=(1, 1, 1)):
+    """Auxiliary fields (n, field_stride) at fixed specific value under
+    accretion, in place; call before the pass's apply."""
+    P = make_params(params)
+    S = make_mesh(box, state, dx, periodic)
+    B = make_mesh(box, buf, dx, periodic)
+    assert extra.dtype == np.float64 and extra.flags["C_CONTIGUOUS"] and extra.ndim == 2
+    _check(lib().or_apply_extra(ctypes.byref(P), ctypes.byref(S), ctypes.byref(B), _dp(extra),
+                                int(extra.shape[0]), ctypes.c_int64(extra.shape[1])), "apply_extra")
+
+
 def create_sinks(params, box, state, buf, cap=None, dx=1.0, periodic=(1, 1, 1)):
     """Sink creation after an accretion pass (Sec. 3.1.2), ``state`` updated
     in place; returns (count, new sinks dict x, y, z, m, px, py, pz)."""

@@ -900,6 +900,38 @@ int or_apply(const or_params *P, or_mesh *S, const or_mesh *B, double *eta_out, 
 }
 
 /* ------------------------------------------------------------------------ */
+/* Auxiliary conserved fields under accretion (Sec. 3.1.1, extensions)       */
+/* ------------------------------------------------------------------------ */
+
+/* The dual-energy internal energy density and species densities follow the
+ * accretion function with e_sp + v^2/2 replaced by their value per unit mass
+ * (Delta rho_sp = (rho_sp / rho) Delta rho): each pair's change is -a X/rho
+ * with the cell's X/rho.  Reading: that common factor is taken out of the sum
+ * over particles, Delta X^sum = (X/rho) Delta rho^sum, and the limiter's eta
+ * applies as to every other field: X := X + eta ((X / rho) Delta rho^sum), on
+ * the pre-update state (before Step 5).  X: [n][stride] with the state's cell
+ * layout. */
+int or_apply_extra(const or_params *P, const or_mesh *S, const or_mesh *B, double *X, int n, int64_t stride)
+{
+    if (!P || !S || !B || (n > 0 && !X) || P->kind != KIND_SINK) return OR_ERR_ARG;
+    for (int k = 0; k < S->n[2]; k++)
+        for (int j = 0; j < S->n[1]; j++)
+            for (int i = 0; i < S->n[0]; i++) {
+                double U[NF], D[NF];
+                read_state(S, i, j, k, U);
+                int64_t b = cell_index(B, i, j, k), c = cell_index(S, i, j, k);
+                for (int f = 0; f < NF; f++) D[f] = B->u[(int64_t)f * B->fstride + b];
+                if (all_zero(D)) continue;
+                double eta = sink_eta(P, S->dx, U, D);
+                for (int f = 0; f < n; f++) {
+                    double x = X[(int64_t)f * stride + c];
+                    X[(int64_t)f * stride + c] = x + eta * ((x / U[0]) * D[0]);
+                }
+            }
+    return OR_OK;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Sink creation (Sec. 3.1.2)                                                */
 /* ------------------------------------------------------------------------ */
 

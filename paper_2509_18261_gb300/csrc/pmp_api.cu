@@ -401,6 +401,28 @@ pmp_status pmp_create_sinks(pmp_ctx *ctx, pmp_mesh *state, const pmp_mesh *buffe
     return last_launch();
 }
 
+pmp_status pmp_apply_extra(pmp_ctx *ctx, const pmp_mesh *state, const pmp_mesh *buffer, double *extra, int32_t n_extra,
+                           int64_t extra_stride)
+{
+    if (!ctx || ctx->p.kind != PMP_KIND_SINK || n_extra < 0) return PMP_ERR_ARG;
+    Box S, B;
+    pmp_status s = make_box(state, &S);
+    if (s) return s;
+    s = make_box(buffer, &B);
+    if (s) return s;
+    for (int a = 0; a < 3; ++a)
+        if (state->n[a] != buffer->n[a] || state->periodic[a] != buffer->periodic[a]) return PMP_ERR_ARG;
+    if (overlaps(state, buffer)) return PMP_ERR_ARG;
+    if (n_extra == 0) return PMP_OK;
+    if (!extra || extra_stride < S.ncells || (reinterpret_cast<uintptr_t>(extra) & 7)) return PMP_ERR_ARG;
+    const KParams P = make_kparams(ctx->p, state->dx);
+    {
+        Timed tm(ctx, "apply_extra");
+        pmp::launch_apply_extra(P, S, state->data, B, buffer->data, extra, n_extra, extra_stride, ctx->stream);
+    }
+    return last_launch();
+}
+
 pmp_status pmp_set_rounding_margin(pmp_ctx *ctx, int32_t M)
 {
     if (!ctx || M < 0 || M > 104) return PMP_ERR_ARG;

@@ -68,6 +68,9 @@ void launch_create_flags(const KParams &P, const Box &S, const double *u, const 
 void launch_create_apply(const KParams &P, const Box &S, double *u, const unsigned *flags,
                          const unsigned long long *pos, long long cap, double *x, double *y, double *z, double *m,
                          double *px, double *py, double *pz, long long *count, cudaStream_t stream);
+// Auxiliary fields at fixed specific value under accretion (before Step 5).
+void launch_apply_extra(const KParams &P, const Box &S, const double *u, const Box &B, const double *b, double *X,
+                        int nx, long long xs, cudaStream_t stream);
 // App. A.1 rounding of every buffer cell with its error bound E (margin M).
 void launch_round(const Box &B, double *b, const double *E, int M, cudaStream_t stream);
 void launch_sink_aux(const KParams &P, const Box &S, const double *u, double *grec, double *drec,

@@ -341,6 +341,42 @@ void launch_zero(const Box &B, double *b, cudaStream_t stream)
     k_zero<<<152 * 8, 256, 0, stream>>>(b, B.fs, B.ncells);
 }
 
+// Auxiliary conserved fields under accretion (the extensions of Sec. 3.1.1
+// beyond minimal hydrodynamics: the dual-energy internal energy and species
+// densities), at fixed specific value: every pair's change of field X is
+// -a X/rho with the cell's X/rho, so the summed change is (X/rho) Delta rho^sum
+// and the limited update X := X + eta ((X / rho) Delta rho^sum), eta the
+// cell's accretion limiter.  Runs before Step 5 (rho is the pre-update one).
+__global__ void __launch_bounds__(256) k_apply_extra(KParams P, Box S, const double *__restrict__ u, Box B,
+                                                     const double *__restrict__ b, double *__restrict__ X, int nx,
+                                                     long long xs)
+{
+    const long long nvalid = (long long)S.n0 * S.n1 * S.n2;
+    const long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= nvalid) return;
+    const int i = (int)(v % S.n0);
+    const long long r = v / S.n0;
+    const int j = (int)(r % S.n1), k = (int)(r / S.n1);
+    double D[NF];
+    load_cell(b, B, B.at(i, j, k), D);
+    if (all_zero(D)) return;
+    double U[NF];
+    load_cell(u, S, S.at(i, j, k), U);
+    const double eta = sink_eta(P, U, D);
+    const long long c = S.at(i, j, k);
+    for (int f = 0; f < nx; ++f) {
+        const double x = X[(long long)f * xs + c];
+        X[(long long)f * xs + c] = x + eta * ((x / U[0]) * D[0]);
+    }
+}
+
+void launch_apply_extra(const KParams &P, const Box &S, const double *u, const Box &B, const double *b, double *X,
+                        int nx, long long xs, cudaStream_t stream)
+{
+    const long long nvalid = (long long)S.n0 * S.n1 * S.n2;
+    k_apply_extra<<<(unsigned)((nvalid + 255) / 256), 256, 0, stream>>>(P, S, u, B, b, X, nx, xs);
+}
+
 // Sink creation (Sec. 3.1.2), pass 1: a valid cell qualifies when the
 // retained accretion buffer is zero in every field there (no sink within
 // r_K), rho > rho_Tr (Eq. truelove with the cell's c_s), and rho is strictly

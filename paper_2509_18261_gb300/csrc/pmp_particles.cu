@@ -182,13 +182,8 @@ __device__ __forceinline__ void plan_particle(const KParams &P, const Box &S, co
     for (int i = lane; i < 3 * W; i += 32) {
         const int a = i / W, o = i - a * W;
         const float fa = a == 0 ? f4.x : (a == 1 ? f4.y : f4.z);
-        const float e0 = (float)(o - R) - fa, e1 = (float)(o + 1 - R) - fa;
-        const float c = e0 + 0.5f;
+        const float c = ((float)(o - R) - fa) + 0.5f;
         csq[i] = c * c;
-        if (FB) {
-            const float m = fabsf(e0) > fabsf(e1) ? fabsf(e0) : fabsf(e1);
-            fc2[i] = m * m;
-        }
     }
     if (FB) {
         for (int i = lane; i < 3 * W * Sn; i += 32) {
@@ -196,6 +191,13 @@ __device__ __forceinline__ void plan_particle(const KParams &P, const Box &S, co
             const float fa = a == 0 ? f4.x : (a == 1 ? f4.y : f4.z);
             const float u = ((float)(o - R) - fa) + P.fracf[k];
             sub[i] = u * u;
+        }
+        __syncwarp();
+        // the farthest sub-point of a cell along an axis is its first or last
+        // one: if the sum of those squares is surely inside, all S^3 are
+        for (int i = lane; i < 3 * W; i += 32) {
+            const float s0 = sub[i * Sn], s1 = sub[i * Sn + Sn - 1];
+            fc2[i] = s0 > s1 ? s0 : s1;
         }
     }
     __syncwarp();
@@ -272,7 +274,7 @@ __device__ __forceinline__ void plan_particle(const KParams &P, const Box &S, co
 //   1. writes the per-axis FP32 squares;
 //   2. classifies the candidates (lane per candidate): member if the centre
 //      is inside (FP32 outside the band, else the FP64 test), full if the
-//      farthest corner is surely inside (omega = 1), else a boundary cell;
+//      farthest sub-point is surely inside (omega = 1), else a boundary cell;
 //   3. (supernovae) counts the sub-points of the boundary cells, a lane per
 //      cell;
 //   4. writes the cells with omega > 0 (every member, for sinks) in

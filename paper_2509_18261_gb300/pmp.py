@@ -30,7 +30,7 @@ EXPORTS = [
     "pmp_create", "pmp_destroy", "pmp_set_stream", "pmp_set_rounding_margin", "pmp_gathered_rows", "pmp_workspace_size", "pmp_zero_buffer",
     "pmp_gather", "pmp_deposit", "pmp_fold_ghosts", "pmp_apply_limited", "pmp_backward", "pmp_get_error",
     "pmp_limiter_counts", "pmp_timing_enable", "pmp_timing_read", "pmp_deposit_noalloc",
-    "pmp_create_sinks_workspace_size", "pmp_create_sinks",
+    "pmp_create_sinks_workspace_size", "pmp_create_sinks", "pmp_apply_extra",
     "pmp_batch_create", "pmp_batch_set_particles", "pmp_batch_set_strategy", "pmp_batch_strategies",
     "pmp_batch_autotune", "pmp_cycle_batched", "pmp_batch_info", "pmp_batch_destroy",
 ]
@@ -115,6 +115,7 @@ def load():
         "pmp_timing_read": ([vp, ctypes.POINTER(_KernelTime), i32, ctypes.POINTER(i32)], i32),
         "pmp_deposit_noalloc": ([P, M, Pa, vp, M, vp], i32),
         "pmp_create_sinks_workspace_size": ([vp, M, ctypes.POINTER(ctypes.c_size_t)], i32),
+        "pmp_apply_extra": ([vp, M, M, vp, i32, i64], i32),
         "pmp_create_sinks": ([vp, M, M, i64, vp, vp, vp, vp, vp, vp, vp, vp, vp, ctypes.c_size_t], i32),
         "pmp_batch_create": ([vp, ctypes.POINTER(_Patch), i32, i32, ctypes.c_double, i64, ctypes.POINTER(vp)], i32),
         "pmp_batch_set_particles": ([vp, ctypes.POINTER(i64)], i32),
@@ -206,6 +207,16 @@ class Context:
 
 def pmp_create(params):
     return Context(params)
+
+
+def pmp_apply_extra(ctx, state, buffer, extra):
+    """Auxiliary fields at fixed specific value under accretion: ``extra`` is a
+    (n_extra, field_stride) float64 CUDA tensor laid out like the state."""
+    ctx._sync_stream()
+    n = int(extra.shape[0]) if extra.dim() == 2 else 1
+    stride = int(extra.shape[-1])
+    _check("pmp_apply_extra", load().pmp_apply_extra(ctx.h, ctypes.byref(state.c()), ctypes.byref(buffer.c()),
+                                                     _ptr(extra), n, stride))
 
 
 def pmp_create_sinks_workspace_size(ctx, state):

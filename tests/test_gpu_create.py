@@ -126,3 +126,53 @@ def test_create_rejects_wrong_kind_and_missing_arrays():
     with pytest.raises(pmp.PMPError):
         pmp.pmp_create_sinks(sk, S, B, out, cnt, ws[: ws.numel() // 2])
     sk.close()
+
+
+def test_auxiliary_fields_under_accretion(orc):
+    """pmp_apply_extra between Step 2 and Step 5 of a sink pass: the extra
+    fields, the state and the sinks equal the oracle's bit for bit."""
+    import torch
+
+    from paper_2509_18261_gb300 import pmp
+
+    rng = np.random.default_rng(12)
+    box = syn.Box((14, 12, 10), 4)
+    state = syn.gas_state(rng, box)
+    box.valid(state)[:] *= 3.0
+    parts = syn.particles(rng, box.n, 12, "sink")
+    params = syn.sink_params(dt=1.0)
+    X = np.zeros((3, box.field_stride))
+    X[0] = state[0] * rng.uniform(0.0, 1.0, box.field_stride)
+    X[1] = state[0] * 1.5
+    X[2] = state[0]
+    X = np.nan_to_num(X)
+    # oracle: gather, deposit, fold, extra, Step 4, Step 5
+    st_r, p_r, X_r = state.copy(), {k: v.copy() for k, v in parts.items()}, X.copy()
+    G = orc.gather(params, box, st_r, p_r)
+    buf = box.empty(0.0)
+    orc.deposit(params, box, st_r, p_r, G, buf)
+    orc.fold(box, buf)
+    orc.apply_extra(params, box, st_r, buf, X_r)
+    orc.return_sinks(params, box, st_r, buf, p_r, G)
+    orc.apply(params, box, st_r, buf)
+    # GPU, sorted deposit
+    st = torch.from_numpy(state.copy()).cuda()
+    pd = pmp.parts_to_device(parts)
+    Xd = torch.from_numpy(X.copy()).cuda()
+    ps = pmp.Pass(params, box, st, pd, mode="sorted")
+    c = ps.ctx
+    pmp.pmp_zero_buffer(c, ps.buffer)
+    pmp.pmp_gather(c, ps.state, pd, ps.gathered, "sorted", ps.workspace)
+    pmp.pmp_deposit(c, ps.state, pd, ps.gathered, ps.buffer, "sorted", ps.workspace)
+    pmp.pmp_fold_ghosts(c, ps.buffer)
+    pmp.pmp_apply_extra(c, ps.state, ps.buffer, Xd)
+    pmp.pmp_apply_limited(c, ps.state, ps.buffer, pd, ps.gathered, None, ps.workspace)
+    torch.cuda.synchronize()
+    assert pmp.pmp_get_error(c) == (0, -1)
+    got = Xd.cpu().numpy()
+    for f in range(3):
+        assert_bits_equal(box.valid(got[f:f + 1])[0], box.valid(X_r[f:f + 1])[0], f"extra field {f}")
+    assert_bits_equal(valid_flat(box, st.cpu().numpy()), valid_flat(box, st_r), "state")
+    for k in ("m", "px", "py", "pz"):
+        assert_bits_equal(pd[k].cpu().numpy(), p_r[k], f"sink {k}")
+    c.close()
