@@ -665,6 +665,9 @@ def deposit_modes(args):
                 pmp.pmp_set_rounding_margin(ps.ctx, M)
             c = ps.ctx
             pmp.pmp_gather(c, ps.state, pp, ps.gathered, mode, ps.workspace)
+            if timed:
+                pmp.pmp_timing_read(c)
+                pmp.pmp_timing_enable(c, True)
             times = []
             for it in range(3 + (max(args.steps, 1) if timed else 0)):
                 pmp.pmp_zero_buffer(c, ps.buffer)
@@ -680,6 +683,9 @@ def deposit_modes(args):
                 raise RuntimeError(f"deposit modes: device error {code} at {idx}")
             if times:
                 out["ms"][mode] = sum(times) / len(times)
+                stages = pmp.pmp_timing_read(c)
+                pmp.pmp_timing_enable(c, False)
+                out.setdefault("stage_ms", {})[mode] = {k: round(ms / nl, 4) for k, (nl, ms) in stages.items()}
             bufs.append(ps.buffer.data.clone())
             c.close()
         a, a2, b = bufs

@@ -640,16 +640,22 @@ pmp_status pmp_deposit(pmp_ctx *ctx, const pmp_mesh *state, const pmp_particles 
     }
     int end_bit = 1;
     while (end_bit < 32 && (1LL << end_bit) < B.ncells) ++end_bit;
-    if (pmp::sort_pairs(w + L.temp, L.temp_bytes, k1, k2, v1, v2, (long long)total, end_bit, st) != cudaSuccess)
-        return PMP_ERR_CUDA;
+    {
+        Timed tm(ctx, "sort_pairs");
+        if (pmp::sort_pairs(w + L.temp, L.temp_bytes, k1, k2, v1, v2, (long long)total, end_bit, st) != cudaSuccess)
+            return PMP_ERR_CUDA;
+    }
     // runs of equal cells: unique cells into k1, lengths into v1 (both free
     // after the sort), first pairs into soffs
     unsigned *offs = reinterpret_cast<unsigned *>(w + L.soffs), *longq = reinterpret_cast<unsigned *>(w + L.slong);
     unsigned long long *nruns = reinterpret_cast<unsigned long long *>(w + L.scnt);
     unsigned *nlong = reinterpret_cast<unsigned *>(w + L.scnt + 8);
-    if (pmp::encode_runs(w + L.temp, L.temp_bytes, k2, k1, v1, nruns, (long long)total, st) != cudaSuccess ||
-        pmp::scan_lengths(w + L.temp, L.temp_bytes, v1, offs, (long long)total, st) != cudaSuccess)
-        return PMP_ERR_CUDA;
+    {
+        Timed tm(ctx, "runs");
+        if (pmp::encode_runs(w + L.temp, L.temp_bytes, k2, k1, v1, nruns, (long long)total, st) != cudaSuccess ||
+            pmp::scan_lengths(w + L.temp, L.temp_bytes, v1, offs, (long long)total, st) != cudaSuccess)
+            return PMP_ERR_CUDA;
+    }
     {
         Timed tm(ctx, "segment_sum");
         pmp::launch_segment_sum(P, S, state->data, B, buffer->data, q, gathered, pl, nruns, k1, v1, offs, v2, longq,

@@ -268,7 +268,10 @@ __device__ void gather_particle(const BArgs &a, long long s, SmemT<R> &sm)
     const int h0 = (int)floor(x), h1 = (int)floor(y), h2 = (int)floor(z);
     if (lane == 0) a.hostp[s] = pack_host(h0, h1, h2);
     double (*red)[6] = sm.u.pw.red[wib];
-    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0, s4 = 0.0;
+    // lane f < 5 keeps sum f: one FP64 instruction per cell for all five sums
+    // (an FP64 instruction with one active lane costs the pipe about what a
+    // full-warp one does); the sequence of additions per sum is unchanged
+    double acc = 0.0;
     int nk = 0;
     for (int k0 = 0; k0 < W3; k0 += 32) {
         const int k = k0 + lane;
@@ -309,28 +312,24 @@ __device__ void gather_particle(const BArgs &a, long long s, SmemT<R> &sm)
         red[lane][3] = v3;
         red[lane][4] = v4;
         __syncwarp();
-        if (lane == 0) {
+        if (lane < 5) {
             for (int l = 0; l < 32; ++l) {
                 if (!((mem >> l) & 1u)) continue;
                 if (FB) {
+                    // sum 0 = sum omega (fma(1, w, s) == s + w); sums 1-4 = fma(omega, v, s)
                     const double w = red[l][0];
-                    s0 = s0 + w;
-                    s1 = fma(w, red[l][1], s1);
-                    s2 = fma(w, red[l][2], s2);
-                    s3 = fma(w, red[l][3], s3);
-                    s4 = fma(w, red[l][4], s4);
+                    acc = fma(lane == 0 ? 1.0 : w, lane == 0 ? w : red[l][lane], acc);
                 } else {
-                    s0 = s0 + red[l][0];
-                    s1 = s1 + red[l][1];
-                    s2 = s2 + red[l][2];
-                    s3 = s3 + red[l][3];
-                    s4 = s4 + red[l][4];
+                    acc = acc + red[l][lane];
                 }
             }
-            nk += __popc(mem);
         }
+        nk += __popc(mem);
         __syncwarp();
     }
+    const double s0 = __shfl_sync(kFullMask, acc, 0), s1 = __shfl_sync(kFullMask, acc, 1),
+                 s2 = __shfl_sync(kFullMask, acc, 2), s3 = __shfl_sync(kFullMask, acc, 3),
+                 s4 = __shfl_sync(kFullMask, acc, 4);
     if (FB) {
         if (lane == 0 &&
             !fb_gather_rows(P, s0, s1, s2, s3, s4, m, a.p.px[s], a.p.py[s], a.p.pz[s], a.p.e[s], a.G + s, N))
@@ -587,7 +586,7 @@ __device__ void return_sink(const BArgs &a, long long s, SmemT<R> &sm)
     const double K = __ldcg(a.G + SK_K * N + s);
     const double *ws = a.wts + s * (3 * W);
     double (*red)[6] = sm.u.pw.red[wib];
-    double c0 = 0.0, c1 = 0.0, c2 = 0.0, c3 = 0.0;
+    double acc = 0.0;  // lane f < 4 keeps sum f (see gather_particle)
     for (int k0 = 0; k0 < W3; k0 += 32) {
         const int k = k0 + lane;
         bool mem = false;
@@ -615,17 +614,16 @@ __device__ void return_sink(const BArgs &a, long long s, SmemT<R> &sm)
         red[lane][2] = v2;
         red[lane][3] = v3;
         __syncwarp();
-        if (lane == 0)
+        if (lane < 4)
             for (int l = 0; l < 32; ++l) {
                 if (!((mm >> l) & 1u)) continue;
-                const double b = red[l][0];
-                c0 = c0 - b;
-                c1 = fma(-b, red[l][1], c1);
-                c2 = fma(-b, red[l][2], c2);
-                c3 = fma(-b, red[l][3], c3);
+                // mass: fma(-b, 1, c) == c - b; momentum: fma(-b, v, c)
+                acc = fma(-red[l][0], lane == 0 ? 1.0 : red[l][lane], acc);
             }
         __syncwarp();
     }
+    const double c0 = __shfl_sync(kFullMask, acc, 0), c1 = __shfl_sync(kFullMask, acc, 1),
+                 c2 = __shfl_sync(kFullMask, acc, 2), c3 = __shfl_sync(kFullMask, acc, 3);
     if (lane == 0) {
         const double V = P.V;
         a.p.m[s] = a.p.m[s] - c0 * V;

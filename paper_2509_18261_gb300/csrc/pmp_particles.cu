@@ -382,13 +382,10 @@ __device__ __forceinline__ void fill_omega_table(const KParams &P, double *wtab)
     __syncthreads();
 }
 
-__global__ void __launch_bounds__(128) k_gather_fb(KParams P, Box S, const double *__restrict__ u, Parts p,
-                                                   PlanPtrs pl, double *__restrict__ G, DevStatus *st)
+__device__ __forceinline__ void gather_fb_particle(const KParams &P, const Box &S, const double *__restrict__ u,
+                                                   const Parts &p, const PlanPtrs &pl, double *__restrict__ G,
+                                                   DevStatus *st, const double *wtab, long long t)
 {
-    __shared__ double wtab[kMaxS3 + 1];
-    fill_omega_table(P, wtab);
-    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= p.count) return;
     const long long s = pl.perm ? (long long)pl.perm[t] : t;
     const long long gs = p.count;
     const double m = p.m[s], pe0 = p.px[s], pe1 = p.py[s], pe2 = p.pz[s], Esn = p.e[s];
@@ -422,6 +419,18 @@ __global__ void __launch_bounds__(128) k_gather_fb(KParams P, Box S, const doubl
         fb_gather_add(P, wtab, c.cnt, U, sw, sr, sp0, sp1, sp2);
     }
     if (!fb_gather_rows(P, sw, sr, sp0, sp1, sp2, m, pe0, pe1, pe2, Esn, G + s, gs)) report(st, PMP_ERR_NONFINITE, s);
+}
+
+// Grid-stride over the processing order (a window of consecutive particles
+// in flight, see window_blocks).
+__global__ void __launch_bounds__(128) k_gather_fb(KParams P, Box S, const double *__restrict__ u, Parts p,
+                                                   PlanPtrs pl, double *__restrict__ G, DevStatus *st)
+{
+    __shared__ double wtab[kMaxS3 + 1];
+    fill_omega_table(P, wtab);
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < p.count; t += stride)
+        gather_fb_particle(P, S, u, p, pl, G, st, wtab, t);
 }
 
 // Particle-mesh gather (MASS kind): V_K = V sum omega over the plan's cells in
@@ -462,12 +471,11 @@ __global__ void __launch_bounds__(128) k_gather_mass(KParams P, Box S, Parts p, 
 // Sink gather.  Writes the particle's per-axis Gaussian factors
 // exp(-d^2 / r_acc^2) to wts[s][3][W] for the deposit and Step 4.
 template <int R>
-__global__ void __launch_bounds__(kSinkThreads) k_gather_sink(KParams P, Box S, const double *__restrict__ u, Parts p,
-                                                     PlanPtrs pl, double *__restrict__ G, DevStatus *st)
+__device__ __forceinline__ void gather_sink_particle(const KParams &P, const Box &S, const double *__restrict__ u,
+                                                     const Parts &p, const PlanPtrs &pl, double *__restrict__ G,
+                                                     DevStatus *st, long long t)
 {
     constexpr int W = 2 * R + 1;
-    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= p.count) return;
     const long long s = pl.perm ? (long long)pl.perm[t] : t;
     const long long gs = p.count;
     const double x = p.x[s], y = p.y[s], z = p.z[s];
@@ -531,6 +539,17 @@ __global__ void __launch_bounds__(kSinkThreads) k_gather_sink(KParams P, Box S, 
         sumw = fma(ws[c.i - hx + R] * ws[W + c.j - hy + R], ws[2 * W + c.k - hz + R], sumw);
     }
     if (!sink_gather_rows(P, am, sumw, nk, G + s, gs)) report(st, PMP_ERR_NONFINITE, s);
+}
+
+// Grid-stride over the processing order: the sinks in flight at a time are a
+// window of consecutive sinks whose kernel cells fit in L2 (see the launcher).
+template <int R>
+__global__ void __launch_bounds__(kSinkThreads) k_gather_sink(KParams P, Box S, const double *__restrict__ u, Parts p,
+                                                              PlanPtrs pl, double *__restrict__ G, DevStatus *st)
+{
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < p.count; t += stride)
+        gather_sink_particle<R>(P, S, u, p, pl, G, st, t);
 }
 
 // ---------------------------------------------------------------------------
@@ -822,8 +841,10 @@ __global__ void __launch_bounds__(128) k_segment_runs(KParams P, Box S, const do
 }
 
 // One warp per long run: the lanes compute 32 consecutive pairs' values at a
-// time, lane 0 adds them in run order (the same sequence of additions as a
-// single thread would make).
+// time, then lane f (f < 5) adds field f of them in run order -- for every
+// field the same sequence of additions as a single thread would make, with
+// one FP64 instruction per pair for all five fields (an FP64 instruction with
+// one active lane costs the pipe about what a full-warp one does).
 template <int R, bool FB>
 __global__ void __launch_bounds__(128) k_segment_long(KParams P, Box S, const double *__restrict__ u, Box B,
                                                       double *__restrict__ b, Parts p, const double *__restrict__ G,
@@ -841,11 +862,8 @@ __global__ void __launch_bounds__(128) k_segment_long(KParams P, Box S, const do
     for (unsigned q = blockIdx.x * (blockDim.x >> 5) + wib; q < nlong; q += nw) {
         const unsigned r = longq[q];
         const unsigned key = uniq[r], o = offs[r], len = lens[r];
-        double acc[NF];
-        if (lane == 0) {
-#pragma unroll
-            for (int f = 0; f < NF; ++f) acc[f] = b[(long long)f * B.fs + key];
-        }
+        double acc = 0.0;
+        if (lane < NF) acc = b[(long long)lane * B.fs + key];
         for (unsigned c0 = 0; c0 < len; c0 += 32) {
             if (c0 + lane < len) {
                 double dU[NF];
@@ -854,19 +872,13 @@ __global__ void __launch_bounds__(128) k_segment_long(KParams P, Box S, const do
                 for (int f = 0; f < NF; ++f) stage[wib][lane][f] = dU[f];
             }
             __syncwarp();
-            if (lane == 0) {
+            if (lane < NF) {
                 const unsigned m = len - c0 < 32u ? len - c0 : 32u;
-                for (unsigned l = 0; l < m; ++l) {
-#pragma unroll
-                    for (int f = 0; f < NF; ++f) acc[f] = acc[f] + stage[wib][l][f];
-                }
+                for (unsigned l = 0; l < m; ++l) acc = acc + stage[wib][l][lane];
             }
             __syncwarp();
         }
-        if (lane == 0) {
-#pragma unroll
-            for (int f = 0; f < NF; ++f) b[(long long)f * B.fs + key] = acc[f];
-        }
+        if (lane < NF) b[(long long)lane * B.fs + key] = acc;
     }
 }
 
@@ -891,14 +903,11 @@ __device__ __forceinline__ void sink_return_add(double K, double w, double2 d0, 
 }
 
 template <int R>
-__global__ void __launch_bounds__(kSinkThreads) k_return_sinks(KParams P, Box S, Parts p,
-                                                                const double *__restrict__ G, PlanPtrs pl,
-                                                                DevStatus *st)
+__device__ __forceinline__ void return_sink_particle(const KParams &P, const Box &S, const Parts &p,
+                                                     const double *__restrict__ G, const PlanPtrs &pl, DevStatus *st,
+                                                     double *wsm, long long t)
 {
     constexpr int W = 2 * R + 1;
-    __shared__ double wsm[3 * W * kSinkThreads];
-    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= p.count) return;
     const long long s = pl.perm ? (long long)pl.perm[t] : t;
     const int bad = position_status(S, p.x[s], p.y[s], p.z[s]);
     if (bad) {
@@ -947,6 +956,18 @@ __global__ void __launch_bounds__(kSinkThreads) k_return_sinks(KParams P, Box S,
     p.px[s] = p.px[s] - a1 * P.V;
     p.py[s] = p.py[s] - a2 * P.V;
     p.pz[s] = p.pz[s] - a3 * P.V;
+}
+
+// Grid-stride over the processing order, like k_gather_sink.
+template <int R>
+__global__ void __launch_bounds__(kSinkThreads) k_return_sinks(KParams P, Box S, Parts p,
+                                                                const double *__restrict__ G, PlanPtrs pl,
+                                                                DevStatus *st)
+{
+    __shared__ double wsm[3 * (2 * R + 1) * kSinkThreads];
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < p.count; t += stride)
+        return_sink_particle<R>(P, S, p, G, pl, st, wsm, t);
 }
 
 // ---------------------------------------------------------------------------
@@ -1004,18 +1025,65 @@ void launch_plan(const KParams &P, const Box &S, const Parts &p, const PlanPtrs 
     }
 }
 
+// Blocks of the thread-per-sink kernels.  They run grid-stride over the
+// processing order, so the sinks in flight are a window of grid x
+// kSinkThreads consecutive sinks; its kernel cells (about cells / sinks of
+// them per sink, 48-byte records) are kept within half the L2, else every
+// record is read from DRAM several times.
+//
+// The window is set in units of "L2 windows": blocks per SM such that the
+// window's records take about one L2.  Measured on the 512^3 workload (sink
+// gather 21.8 -> 16.0 ms, Step 4 27.2 -> 21.0 ms), the gather does best at
+// about one and a half L2 windows (more resident warps hide its latency) and
+// Step 4, whose shared-memory tables already limit residency, at about one.
+static unsigned window_blocks(const Box &S, long long n, int threads, double bytes_per_cell, double l2_windows,
+                              int forced)
+{
+    int dev = 0, nsm = 152, l2 = 126 << 20;
+    if (cudaGetDevice(&dev) == cudaSuccess) {
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev);
+    }
+    const double cells = (double)S.n0 * S.n1 * S.n2;
+    const double per_particle = cells / (double)(n > 0 ? n : 1);
+    long long bps = forced > 0 ? forced
+                               : (long long)(l2_windows * (double)l2 /
+                                                 ((double)nsm * threads * per_particle * bytes_per_cell) +
+                                             0.5);
+    if (bps < 1) bps = 1;
+    if (bps > 16) bps = 16;
+    const long long need = (n + threads - 1) / threads;
+    const long long grid = (long long)nsm * bps;
+    return (unsigned)(need < grid ? need : grid);
+}
+
+#ifndef PMP_SINK_GATHER_BPS
+#define PMP_SINK_GATHER_BPS 0
+#endif
+#ifndef PMP_SINK_RETURN_BPS
+#define PMP_SINK_RETURN_BPS 0
+#endif
+#ifndef PMP_FB_GATHER_BPS
+#define PMP_FB_GATHER_BPS 0
+#endif
+#ifndef PMP_DEPOSIT_BPS
+#define PMP_DEPOSIT_BPS 0
+#endif
+
 void launch_gather(const KParams &P, const Box &S, const double *u, const Parts &p, const PlanPtrs &pl, double *G,
                    DevStatus *st, cudaStream_t stream)
 {
     if (p.count == 0) return;
     const unsigned nb = blocks_for(p.count, 128);
     if (P.kind == PMP_KIND_FEEDBACK) {
-        k_gather_fb<<<nb, 128, 0, stream>>>(P, S, u, p, pl, G, st);
+        // FP64-bound: a smaller window did not pay (512^3 sweep), full grid
+        const unsigned nbf = PMP_FB_GATHER_BPS > 0 ? window_blocks(S, p.count, 128, 40.0, 1.0, PMP_FB_GATHER_BPS) : nb;
+        k_gather_fb<<<nbf, 128, 0, stream>>>(P, S, u, p, pl, G, st);
     } else if (P.kind == PMP_KIND_MASS) {
         k_gather_mass<<<nb, 128, 0, stream>>>(P, S, p, pl, G, st);
     } else {
-        PMP_DISPATCH_R(P.R, (k_gather_sink<RR><<<blocks_for(p.count, kSinkThreads), kSinkThreads, 0, stream>>>(
-                                 P, S, u, p, pl, G, st)));
+        const unsigned nbs = window_blocks(S, p.count, kSinkThreads, 8.0 * kRec, 1.5, PMP_SINK_GATHER_BPS);
+        PMP_DISPATCH_R(P.R, (k_gather_sink<RR><<<nbs, kSinkThreads, 0, stream>>>(P, S, u, p, pl, G, st)));
     }
 }
 
@@ -1023,9 +1091,26 @@ void launch_deposit_atomic(const KParams &P, const Box &S, const double *u, cons
                            const double *G, const PlanPtrs &pl, double *E, cudaStream_t stream)
 {
     if (p.count == 0) return;
+    // Only resident blocks: the grid-stride loop then moves all of them
+    // through the processing order together, so the particles in flight are
+    // one compact window (a larger grid spreads the resident blocks' chunks
+    // over the whole order and every buffer line is fetched many times).
     const long long warps = (p.count + kPartsPerWarp - 1) / kPartsPerWarp;
     const long long blocks_needed = (warps + 7) / 8;
-    const unsigned nb = (unsigned)(blocks_needed < 152LL * 64 ? blocks_needed : 152LL * 64);
+    int dev = 0, nsm = 152;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    int occ = 1;
+    if (P.kind != PMP_KIND_SINK) {
+        PMP_DISPATCH_R(P.R, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_deposit_atomic<RR, true>, 256, 0));
+    } else {
+        PMP_DISPATCH_R(P.R, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_deposit_atomic<RR, false>, 256, 0));
+    }
+    // two resident blocks per SM: the 512^3 sweep gave the sink deposit 18.1
+    // -> 16.5 ms and left the supernova deposit (FP64-bound) unchanged
+    occ = occ < 2 ? occ : 2;
+    if (PMP_DEPOSIT_BPS > 0) occ = PMP_DEPOSIT_BPS;
+    if (occ < 1) occ = 1;
+    const unsigned nb = (unsigned)(blocks_needed < (long long)nsm * occ ? blocks_needed : (long long)nsm * occ);
     if (P.kind != PMP_KIND_SINK) {
         PMP_DISPATCH_R(P.R, (k_deposit_atomic<RR, true><<<nb, 256, 0, stream>>>(P, S, u, B, b, p, G, pl, E)));
     } else {
@@ -1065,7 +1150,7 @@ void launch_return_sinks(const KParams &P, const Box &S, const Parts &p, const d
                          DevStatus *st, cudaStream_t stream)
 {
     if (p.count == 0) return;
-    const unsigned nb = blocks_for(p.count, kSinkThreads);
+    const unsigned nb = window_blocks(S, p.count, kSinkThreads, 8.0 * kRec, 1.0, PMP_SINK_RETURN_BPS);
     PMP_DISPATCH_R(P.R, (k_return_sinks<RR><<<nb, kSinkThreads, 0, stream>>>(P, S, p, G, pl, st)));
 }
 
