@@ -356,24 +356,19 @@ constexpr int kUnroll = 4;
 constexpr int kSinkThreads = 128;
 
 // One kernel cell's terms of the supernova gather sums, products fused into
-// the sums (omega = 1 skips the products: fma(1, v, s) == s + v).
+// the sums.  No branch on omega = 1 (wtab[S^3] = 1 and fma(1, v, s) == s + v):
+// lanes of a warp mix full and partial cells, and a divergent branch would
+// issue both paths on the FP64 pipe.
 __device__ __forceinline__ void fb_gather_add(const KParams &P, const double *wtab, int cnt, const double U[NF],
                                               double &sw, double &sr, double &sp0, double &sp1, double &sp2)
 {
-    if (cnt == P.S3) {
-        sw = sw + 1.0;
-        sr = sr + U[0];
-        sp0 = sp0 + U[1];
-        sp1 = sp1 + U[2];
-        sp2 = sp2 + U[3];
-    } else {
-        const double w = wtab[cnt];
-        sw = sw + w;
-        sr = fma(w, U[0], sr);
-        sp0 = fma(w, U[1], sp0);
-        sp1 = fma(w, U[2], sp1);
-        sp2 = fma(w, U[3], sp2);
-    }
+    (void)P;
+    const double w = wtab[cnt];
+    sw = sw + w;
+    sr = fma(w, U[0], sr);
+    sp0 = fma(w, U[1], sp0);
+    sp1 = fma(w, U[2], sp1);
+    sp2 = fma(w, U[3], sp2);
 }
 
 __device__ __forceinline__ void fill_omega_table(const KParams &P, double *wtab)
@@ -558,13 +553,13 @@ __global__ void __launch_bounds__(kSinkThreads) k_gather_sink(KParams P, Box S, 
 
 __device__ __forceinline__ void fb_pair_delta(const KParams &P, const Box &S, const double *__restrict__ u,
                                               const Parts &p, const double *__restrict__ G, long long s,
-                                              const PairCell &c, double dU[NF])
+                                              const PairCell &c, const double *wtab, double dU[NF])
 {
     const long long gs = p.count;
     const double x = __ldg(p.x + s), y = __ldg(p.y + s), z = __ldg(p.z + s);
     const double d0 = ((double)c.i + 0.5) - x, d1 = ((double)c.j + 0.5) - y, d2 = ((double)c.k + 0.5) - z;
     const double dd = (d0 * d0 + d1 * d1) + d2 * d2;
-    const double w = c.cnt == P.S3 ? 1.0 : (double)c.cnt / (double)P.S3;
+    const double w = wtab[c.cnt];
     if (P.kind == PMP_KIND_MASS) {
 #pragma unroll
         for (int f = 0; f < NF; ++f) dU[f] = w * __ldg(G + (MS_Q + f) * gs + s);
@@ -789,12 +784,12 @@ __global__ void __launch_bounds__(128) k_sort_keys(KParams P, Box B, long long n
 template <int R, bool FB>
 __device__ __forceinline__ void sorted_pair_delta(const KParams &P, const Box &S, const double *__restrict__ u,
                                                   const Parts &p, const double *__restrict__ G, const PlanPtrs &pl,
-                                                  unsigned long long slot, double dU[NF])
+                                                  unsigned long long slot, const double *wtab, double dU[NF])
 {
     const long long s = (long long)(slot / pl.cap);
     const PairCell c = unpack_pair(pl.slots[slot], P.R);
     if (FB) {
-        fb_pair_delta(P, S, u, p, G, s, c, dU);
+        fb_pair_delta(P, S, u, p, G, s, c, wtab, dU);
     } else {
         double e;
         sink_pair_delta<R>(P, S, p, G, pl, s, c, dU, e);
@@ -817,6 +812,8 @@ __global__ void __launch_bounds__(128) k_segment_runs(KParams P, Box S, const do
                                                       const unsigned *__restrict__ vals, unsigned *__restrict__ longq,
                                                       unsigned *__restrict__ nlong)
 {
+    __shared__ double wtab[FB ? kMaxS3 + 1 : 1];
+    if (FB) fill_omega_table(P, wtab);
     const unsigned long long nruns = *nruns_ptr;
     const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
     for (unsigned long long r = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; r < nruns; r += stride) {
@@ -831,7 +828,7 @@ __global__ void __launch_bounds__(128) k_segment_runs(KParams P, Box S, const do
         for (int f = 0; f < NF; ++f) acc[f] = b[(long long)f * B.fs + key];
         for (unsigned j = 0; j < len; ++j) {
             double dU[NF];
-            sorted_pair_delta<R, FB>(P, S, u, p, G, pl, vals[o + j], dU);
+            sorted_pair_delta<R, FB>(P, S, u, p, G, pl, vals[o + j], wtab, dU);
 #pragma unroll
             for (int f = 0; f < NF; ++f) acc[f] = acc[f] + dU[f];
         }
@@ -856,6 +853,8 @@ __global__ void __launch_bounds__(128) k_segment_long(KParams P, Box S, const do
                                                       const unsigned *__restrict__ nlong_ptr)
 {
     __shared__ double stage[4][32][NF + 1];
+    __shared__ double wtab[FB ? kMaxS3 + 1 : 1];
+    if (FB) fill_omega_table(P, wtab);
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const unsigned nlong = *nlong_ptr;
     const unsigned nw = gridDim.x * (blockDim.x >> 5);
@@ -867,7 +866,7 @@ __global__ void __launch_bounds__(128) k_segment_long(KParams P, Box S, const do
         for (unsigned c0 = 0; c0 < len; c0 += 32) {
             if (c0 + lane < len) {
                 double dU[NF];
-                sorted_pair_delta<R, FB>(P, S, u, p, G, pl, vals[o + c0 + lane], dU);
+                sorted_pair_delta<R, FB>(P, S, u, p, G, pl, vals[o + c0 + lane], wtab, dU);
 #pragma unroll
                 for (int f = 0; f < NF; ++f) stage[wib][lane][f] = dU[f];
             }
