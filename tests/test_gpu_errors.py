@@ -79,3 +79,43 @@ def test_host_argument_errors_raise():
         pmp.pmp_deposit(ps2.ctx, ps2.state, parts, ps2.gathered, ps2.state, "sorted", ps2.workspace)
     assert e.value.code == 1
     assert pmp.pmp_get_error(ps2.ctx) == (0, -1)
+
+
+def test_new_entry_points_check_their_arguments():
+    """The rounded mode's workspace, pmp_apply_extra and the batched form's
+    kinds: host-side errors raise and enqueue nothing."""
+    import torch
+
+    from paper_2509_18261_gb300 import pmp
+
+    box = syn.Box((8, 8, 8), 4)
+    st = torch.from_numpy(syn.gas_state(np.random.default_rng(1), box)).cuda()
+    parts = pmp.parts_to_device(_cloud(box.n, 4))
+    # ROUNDED needs the error-bound part of the workspace (sized from the buffer)
+    ps = pmp.Pass(syn.feedback_params(), box, st, parts, mode="rounded")
+    n_atomic = pmp.pmp_workspace_size(ps.ctx, ps.buffer, 4, "atomic")
+    assert ps.workspace.numel() >= n_atomic + 5 * box.field_stride * 8
+    pmp.pmp_gather(ps.ctx, ps.state, parts, ps.gathered, "rounded", ps.workspace)
+    with pytest.raises(pmp.PMPError) as e:
+        pmp.pmp_deposit(ps.ctx, ps.state, parts, ps.gathered, ps.buffer, "rounded", ps.workspace[:n_atomic])
+    assert e.value.code == 6
+    # pmp_apply_extra: sink contexts only, and a stride covering the padded box
+    extra = torch.zeros((2, box.field_stride), dtype=torch.float64, device="cuda")
+    with pytest.raises(pmp.PMPError) as e:
+        pmp.pmp_apply_extra(ps.ctx, ps.state, ps.buffer, extra)
+    assert e.value.code == 1
+    sk = pmp.Pass(syn.sink_params(), box, st, parts)
+    with pytest.raises(pmp.PMPError) as e:
+        pmp.pmp_apply_extra(sk.ctx, sk.state, sk.buffer, extra[:, : box.ncells_padded // 2].contiguous())
+    assert e.value.code == 1
+    # the batched form covers supernovae and sinks, not the particle-mesh kind
+    w = syn.make_batch_workload(supergrid=(2, 2, 2), edges=(16,), xmax=50.0, seed=3)
+    b = w["batch"]
+    ctx = pmp.Context(syn.mass_params())
+    with pytest.raises(pmp.PMPError) as e:
+        pmp.BatchHandle(ctx, b.dims, b.nb, b.offset, b.fstride, b.g, b.arena_len)
+    assert e.value.code == 1
+    ctx.close()
+    assert pmp.pmp_get_error(ps.ctx) == (0, -1)
+    ps.ctx.close()
+    sk.ctx.close()

@@ -128,3 +128,33 @@ def test_rounding_margin_is_checked():
     pmp.pmp_set_rounding_margin(ctx, 0)
     pmp.pmp_set_rounding_margin(ctx, 104)
     ctx.close()
+
+
+def test_rounded_sink_deposit_against_oracle(orc):
+    """Sinks in the ROUNDED mode: single-contributor values bit for bit, the
+    rest within the dropped quantum of the oracle's plain sum."""
+    import torch
+
+    from paper_2509_18261_gb300 import pmp
+
+    rng = np.random.default_rng(21)
+    box = syn.Box((12, 12, 12), 4)
+    state = syn.gas_state(rng, box)
+    parts = syn.particles(rng, box.n, 24, "sink", clustered=12, nclusters=2)
+    params = syn.sink_params(dt=0.05)
+    st = torch.from_numpy(state.copy()).cuda()
+    pd = pmp.parts_to_device(parts)
+    ps = pmp.Pass(params, box, st, pd, mode="rounded")
+    ps.run(stop_after="deposit")
+    torch.cuda.synchronize()
+    got = ps.buffer.data.cpu().numpy()
+    assert pmp.pmp_get_error(ps.ctx) == (0, -1)
+    ps.ctx.close()
+    plain, absb, rounded, E = _oracle(orc, params, box, state, parts, 28)
+    single = (E > 0) & (E == EPS * np.abs(plain))
+    multi = (E > 0) & ~single
+    assert single.sum() > 100 and multi.sum() > 100
+    assert np.array_equal(got.view(np.uint64)[single], rounded.view(np.uint64)[single])
+    n = _contributions(orc, params, box, state, parts)
+    tol = _quantum(plain, n * EPS * absb, 28) + 1e-12 * absb
+    assert np.all(np.abs(got - plain)[multi] <= tol[multi])
