@@ -102,7 +102,11 @@ typedef enum { PMP_KIND_FEEDBACK = 0, PMP_KIND_SINK = 1, PMP_KIND_MASS = 2 } pmp
 
 /* Step-1 accumulation strategy.
  * ATOMIC:  FP64 atomic additions (Sec. 2.2, Step 1); per cell the sum equals
- *          the sorted one up to the order of additions.
+ *          the sorted one up to the order of additions.  For sinks every
+ *          pair's change is -a (1, p/rho, E/rho) with its cell's factors, so
+ *          the deposit adds only -a per pair into a one-field scratch and a
+ *          second pass adds (sum -a)(1, p/rho, E/rho) to each buffer cell: the
+ *          same sum up to the order of additions and one product per value.
  * SORTED:  (cell, particle) pairs sorted by cell, then each cell summed in
  *          particle-index order; deterministic.
  * ROUNDED: the paper's reproducible atomics (App. A.1).  Each atomic
@@ -177,8 +181,9 @@ int32_t pmp_gathered_rows(int32_t kind);
 /* Bytes of device workspace one pass needs for `n_particles` particles of
  * the context's kind on a mesh with the buffer's n, with the deposit
  * strategy `mode` (ROUNDED adds 5 x field_stride doubles for the error
- * bound, so it depends on the buffer's field_stride too).  Host only, no
- * device work. */
+ * bound, ATOMIC for sinks field_stride doubles for the deposit's scratch, so
+ * these depend on the buffer's field_stride too).  Host only, no device
+ * work. */
 pmp_status pmp_workspace_size(const pmp_ctx *ctx, const pmp_mesh *buffer, int64_t n_particles, int32_t mode,
                               size_t *bytes);
 

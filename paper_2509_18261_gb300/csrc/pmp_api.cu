@@ -183,10 +183,18 @@ Layout layout(const pmp_params &p, long long n, long long nvalid, int mode)
 
 long long nvalid_rows(const Layout &L) { return L.aux_stride; }
 
-// ROUNDED mode: the error-bound buffer E of App. A.1 follows the rest of the
-// workspace, with the buffer mesh's layout ([5][field_stride] doubles).
+// A tail with the buffer mesh's layout follows the rest of the workspace:
+// ROUNDED mode, the error-bound buffer E of App. A.1 ([5][field_stride]
+// doubles); ATOMIC mode for sinks, the one-field scratch of the deposit
+// ([field_stride] doubles).
 size_t ebuf_offset(const Layout &L) { return align256(L.total); }
 size_t ebuf_bytes(const pmp_mesh *buffer) { return sizeof(double) * 5 * (size_t)buffer->field_stride; }
+size_t tail_bytes(const pmp_params &p, int mode, const pmp_mesh *buffer)
+{
+    if (mode == PMP_MODE_ROUNDED) return ebuf_bytes(buffer);
+    if (mode == PMP_MODE_ATOMIC && p.kind == PMP_KIND_SINK) return sizeof(double) * (size_t)buffer->field_stride;
+    return 0;
+}
 
 bool valid_mode(int32_t mode) { return mode == PMP_MODE_ATOMIC || mode == PMP_MODE_SORTED || mode == PMP_MODE_ROUNDED; }
 
@@ -488,7 +496,8 @@ pmp_status pmp_workspace_size(const pmp_ctx *ctx, const pmp_mesh *buffer, int64_
         if (buffer->n[a] < 1) return PMP_ERR_ARG;
     if (buffer->field_stride < 0) return PMP_ERR_ARG;
     const Layout L = layout(ctx->p, n_particles, nvalid_of(buffer), mode);
-    *bytes = mode == PMP_MODE_ROUNDED ? ebuf_offset(L) + ebuf_bytes(buffer) : L.total;
+    const size_t tail = tail_bytes(ctx->p, mode, buffer);
+    *bytes = tail ? ebuf_offset(L) + tail : L.total;
     return PMP_OK;
 }
 
@@ -551,14 +560,19 @@ pmp_status pmp_gather(pmp_ctx *ctx, const pmp_mesh *state, const pmp_particles *
             Timed tm(ctx, "prologue");
             pmp::launch_prologue(S, q, nullptr, nullptr, pl, ctx->st, st);
         }
-        Timed tm(ctx, "plan");
-        pmp::launch_plan(P, S, q, pl, ctx->st, st);
+        if (ctx->p.kind == PMP_KIND_FEEDBACK) {
+            Timed tm(ctx, "plan_gather");
+            pmp::launch_plan_gather_fb(P, S, state->data, q, pl, gathered, ctx->st, st);
+        } else {
+            Timed tm(ctx, "plan");
+            pmp::launch_plan(P, S, q, pl, ctx->st, st);
+        }
     }
     if (ctx->p.kind == PMP_KIND_SINK) {
         Timed tm(ctx, "cell_records");
         pmp::launch_sink_aux(P, S, state->data, pl.grec, pl.drec, st);
     }
-    if (q.count > 0) {
+    if (q.count > 0 && ctx->p.kind != PMP_KIND_FEEDBACK) {
         Timed tm(ctx, "gather");
         pmp::launch_gather(P, S, state->data, q, pl, gathered, ctx->st, st);
     }
@@ -593,17 +607,32 @@ pmp_status pmp_deposit(pmp_ctx *ctx, const pmp_mesh *state, const pmp_particles 
     const Layout L = layout(ctx->p, q.count, nv, mode);
     s = check_workspace(L, workspace, workspace_bytes);
     if (s) return s;
-    if (mode == PMP_MODE_ROUNDED && workspace_bytes < ebuf_offset(L) + ebuf_bytes(buffer)) return PMP_ERR_WORKSPACE;
+    const size_t tail = tail_bytes(ctx->p, mode, buffer);
+    if (tail && workspace_bytes < ebuf_offset(L) + tail) return PMP_ERR_WORKSPACE;
     s = check_plan(ctx, q.count, nv, workspace);
     if (s) return s;
     if (ctx->plan_mode != mode) return PMP_ERR_WORKSPACE;
     const KParams P = make_kparams(ctx->p, state->dx);
     const pmp::PlanPtrs pl = plan_ptrs(L, workspace, ctx->p, mode);
     cudaStream_t st = ctx->stream;
+    if (mode == PMP_MODE_ATOMIC && ctx->p.kind == PMP_KIND_SINK) {
+        // one atomic per pair into the scratch, then the cells' factors
+        double *scr = reinterpret_cast<double *>(static_cast<char *>(workspace) + ebuf_offset(L));
+        if (cudaMemsetAsync(scr, 0, tail, st) != cudaSuccess) return PMP_ERR_CUDA;
+        {
+            Timed tm(ctx, "deposit");
+            pmp::launch_deposit_atomic(P, S, state->data, B, buffer->data, q, gathered, pl, nullptr, scr, st);
+        }
+        {
+            Timed tm(ctx, "spread");
+            pmp::launch_sink_spread(S, B, buffer->data, scr, pl.drec, st);
+        }
+        return last_launch();
+    }
     if (mode == PMP_MODE_ATOMIC) {
         {
             Timed tm(ctx, "deposit");
-            pmp::launch_deposit_atomic(P, S, state->data, B, buffer->data, q, gathered, pl, nullptr, st);
+            pmp::launch_deposit_atomic(P, S, state->data, B, buffer->data, q, gathered, pl, nullptr, nullptr, st);
         }
         return last_launch();
     }
@@ -612,7 +641,7 @@ pmp_status pmp_deposit(pmp_ctx *ctx, const pmp_mesh *state, const pmp_particles 
         if (cudaMemsetAsync(E, 0, ebuf_bytes(buffer), st) != cudaSuccess) return PMP_ERR_CUDA;
         {
             Timed tm(ctx, "deposit");
-            pmp::launch_deposit_atomic(P, S, state->data, B, buffer->data, q, gathered, pl, E, st);
+            pmp::launch_deposit_atomic(P, S, state->data, B, buffer->data, q, gathered, pl, E, nullptr, st);
         }
         {
             Timed tm(ctx, "round");

@@ -409,7 +409,9 @@ __device__ __forceinline__ bool fb_gather_rows(const KParams &P, double sw, doub
     const double vc1 = (sp1 * V + pe1) / Msnr;
     const double vc2 = (sp2 * V + pe2) / Msnr;
     const double nH = Msnr / (P.mu_H * Vsnr);
-    const double Msf = P.A_sf * pmp_pow(nH, -0.26);
+    // both powers of n_H are exp(a log n_H): the logarithm is taken once
+    const double lnH = pmp_log(nH);
+    const double Msf = P.A_sf * pmp_exp(-0.26 * lnH);
     const double RM = Msnr / Msf;
     double regime, prad;
     if (RM <= P.RM_ej) {
@@ -420,7 +422,7 @@ __device__ __forceinline__ bool fb_gather_rows(const KParams &P, double sw, doub
         prad = sqrt(((2.0 * m) * P.eps_K) * Esn);
     } else {
         regime = 2.0;
-        prad = P.A_p * pmp_pow(nH, -0.17);
+        prad = P.A_p * pmp_exp(-0.17 * lnH);
     }
     const double vej2 = (pe0 * pe0 + pe1 * pe1) + pe2 * pe2;
     const double Ekin = vej2 / (2.0 * m);

@@ -39,9 +39,16 @@ void launch_plan(const KParams &P, const Box &S, const Parts &p, const PlanPtrs 
                  cudaStream_t stream);
 void launch_gather(const KParams &P, const Box &S, const double *u, const Parts &p, const PlanPtrs &pl, double *G,
                    DevStatus *st, cudaStream_t stream);
+// Supernova kind: plan and gather in one launch (same slots, counts and rows
+// as launch_plan followed by launch_gather).
+void launch_plan_gather_fb(const KParams &P, const Box &S, const double *u, const Parts &p, const PlanPtrs &pl,
+                           double *G, DevStatus *st, cudaStream_t stream);
 // E (optional): App. A.1 error-bound buffer, the buffer's layout, zeroed.
+// scr (optional, sinks): one-field scratch with the buffer's layout, zeroed;
+// the deposit then sums only -a per cell into it and launch_sink_spread
+// completes Step 1.
 void launch_deposit_atomic(const KParams &P, const Box &S, const double *u, const Box &B, double *b, const Parts &p,
-                           const double *G, const PlanPtrs &pl, double *E, cudaStream_t stream);
+                           const double *G, const PlanPtrs &pl, double *E, double *scr, cudaStream_t stream);
 void launch_sort_keys(const KParams &P, const Box &B, const Parts &p, const PlanPtrs &pl,
                       const unsigned long long *offsets, unsigned *keys, unsigned *vals, cudaStream_t stream);
 // Sorted deposit, per run of equal buffer cells (uniq/lens/offs from
@@ -73,6 +80,10 @@ void launch_apply_extra(const KParams &P, const Box &S, const double *u, const B
                         int nx, long long xs, cudaStream_t stream);
 // App. A.1 rounding of every buffer cell with its error bound E (margin M).
 void launch_round(const Box &B, double *b, const double *E, int M, cudaStream_t stream);
+// Step 1 for sinks, second half of the scratch form: buffer += s (1, p/rho,
+// E/rho) per buffer cell, the factors of its owner cell's D record.
+void launch_sink_spread(const Box &S, const Box &B, double *b, const double *scr, const double *drec,
+                        cudaStream_t stream);
 void launch_sink_aux(const KParams &P, const Box &S, const double *u, double *grec, double *drec,
                      cudaStream_t stream);
 void launch_sink_eta(const KParams &P, const Box &S, const double *u, const Box &B, const double *b, double *drec,

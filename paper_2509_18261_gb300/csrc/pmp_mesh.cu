@@ -2,6 +2,7 @@
 // one GPU) and the limited apply (Steps 3 + 5).
 #include "pmp_device.cuh"
 #include "pmp_launch.h"
+#include "pmp_plan.cuh"
 
 namespace pmp {
 
@@ -239,6 +240,39 @@ __global__ void __launch_bounds__(256) k_sink_aux(KParams P, Box S, const double
     d[0] = make_double2(U[0] - rtr, U[1] / U[0]);
     d[1] = make_double2(U[2] / U[0], U[3] / U[0]);
     d[2] = make_double2(U[4] / U[0], 1.0);
+}
+
+// Step 1 for sinks in the ATOMIC mode, second half.  Every pair's change is
+// Delta U = -a (1, p/rho, E/rho) with the factors of its cell (the owner, for
+// a ghost image), so the deposit sums only s = sum(-a) per buffer cell into a
+// one-field scratch, and here the cell's buffer gains s (1, p/rho, E/rho)
+// from its owner's D record.  In real arithmetic this is the sum of the
+// pairs' five-field changes; in FP64 it differs from that sum by the order of
+// the additions and one rounding of the product, as any atomic order does.
+// A block takes padded rows (j, k), its threads the cells i of the row.
+__global__ void __launch_bounds__(256) k_sink_spread(Box S, Box B, double *__restrict__ b,
+                                                     const double *__restrict__ scr, const double *__restrict__ drec)
+{
+    const long long py = B.pxy / B.px;
+    const long long rows = B.ncells / B.px;
+    for (long long row = blockIdx.x; row < rows; row += gridDim.x) {
+        const int k = (int)(row / py) - B.g, j = (int)(row % py) - B.g;
+        const long long c0 = row * B.px;
+        for (int ii = threadIdx.x; ii < B.px; ii += blockDim.x) {
+            const long long c = c0 + ii;
+            const double sc = scr[c];
+            if (sc == 0.0) continue;
+            const int i = ii - B.g;
+            const double2 *d = reinterpret_cast<const double2 *>(
+                drec + vidx(S, owner(i, S.n0), owner(j, S.n1), owner(k, S.n2)) * kRec);
+            const double2 d0 = __ldg(d), d1 = __ldg(d + 1), d2 = __ldg(d + 2);
+            b[c] += sc;
+            b[B.fs + c] += sc * d0.y;
+            b[2 * B.fs + c] += sc * d1.x;
+            b[3 * B.fs + c] += sc * d1.y;
+            b[4 * B.fs + c] += sc * d2.x;
+        }
+    }
 }
 
 // Step 3 for sinks: eta per valid cell from the pre-update density, the summed
@@ -519,6 +553,16 @@ void launch_sink_aux(const KParams &P, const Box &S, const double *u, double *gr
 {
     const long long nvalid = (long long)S.n0 * S.n1 * S.n2;
     k_sink_aux<<<(unsigned)((nvalid + 255) / 256), 256, 0, stream>>>(P, S, u, grec, drec);
+}
+
+void launch_sink_spread(const Box &S, const Box &B, double *b, const double *scr, const double *drec,
+                        cudaStream_t stream)
+{
+    const long long rows = B.ncells / B.px;
+    int dev = 0, nsm = 152;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    const long long grid = rows < 8LL * nsm ? rows : 8LL * nsm;
+    if (grid > 0) k_sink_spread<<<(unsigned)grid, 256, 0, stream>>>(S, B, b, scr, drec);
 }
 
 void launch_sink_eta(const KParams &P, const Box &S, const double *u, const Box &B, const double *b, double *drec,

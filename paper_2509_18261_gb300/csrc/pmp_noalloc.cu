@@ -177,8 +177,7 @@ extern "C" pmp_status pmp_deposit_noalloc(const pmp_params *params, const pmp_me
     pl.fr = reinterpret_cast<float4 *>(w + o_fr);
     pl.cap = (unsigned long long)cap;
     pmp::launch_prologue(S, q, nullptr, nullptr, pl, status, st);
-    pmp::launch_plan(k, S, q, pl, status, st);
-    pmp::launch_gather(k, S, state->data, q, pl, gathered, status, st);
-    pmp::launch_deposit_atomic(k, S, state->data, B, buffer->data, q, gathered, pl, nullptr, st);
+    pmp::launch_plan_gather_fb(k, S, state->data, q, pl, gathered, status, st);
+    pmp::launch_deposit_atomic(k, S, state->data, B, buffer->data, q, gathered, pl, nullptr, nullptr, st);
     return cudaGetLastError() == cudaSuccess ? PMP_OK : PMP_ERR_CUDA;
 }

@@ -355,16 +355,31 @@ constexpr int kUnroll = 4;
 // does not: its cell-record loads need the L1 that the array would take).
 constexpr int kSinkThreads = 128;
 
+// A plan slot: through the read-only path (NC) when an earlier launch wrote
+// it, else (written by this warp in the same launch) a coherent load.
+template <bool NC>
+__device__ __forceinline__ unsigned long long slot_load(const unsigned long long *q)
+{
+    if (NC) return __ldg(q);
+    return *q;
+}
+
 // One kernel cell's terms of the supernova gather sums, products fused into
 // the sums.  No branch on omega = 1 (wtab[S^3] = 1 and fma(1, v, s) == s + v):
 // lanes of a warp mix full and partial cells, and a divergent branch would
-// issue both paths on the FP64 pipe.
-__device__ __forceinline__ void fb_gather_add(const KParams &P, const double *wtab, int cnt, const double U[NF],
-                                              double &sw, double &sr, double &sp0, double &sp1, double &sp2)
+// issue both paths on the FP64 pipe.  With IW (S a power of two) sum omega is
+// kept as the integer sum of the sub-point counts: every term k / S^3 and
+// every partial sum is a multiple of 2^-3log2(S) far below 2^53, so the FP64
+// sum in kernel order is exact and equals (sum k) / S^3 bit for bit.
+template <bool IW>
+__device__ __forceinline__ void fb_gather_add(const double *wtab, int cnt, const double U[NF], double &sw,
+                                              unsigned &isw, double &sr, double &sp0, double &sp1, double &sp2)
 {
-    (void)P;
     const double w = wtab[cnt];
-    sw = sw + w;
+    if (IW)
+        isw += (unsigned)cnt;
+    else
+        sw = sw + w;
     sr = fma(w, U[0], sr);
     sp0 = fma(w, U[1], sp0);
     sp1 = fma(w, U[2], sp1);
@@ -377,6 +392,7 @@ __device__ __forceinline__ void fill_omega_table(const KParams &P, double *wtab)
     __syncthreads();
 }
 
+template <bool IW, bool NC>
 __device__ __forceinline__ void gather_fb_particle(const KParams &P, const Box &S, const double *__restrict__ u,
                                                    const Parts &p, const PlanPtrs &pl, double *__restrict__ G,
                                                    DevStatus *st, const double *wtab, long long t)
@@ -392,6 +408,7 @@ __device__ __forceinline__ void gather_fb_particle(const KParams &P, const Box &
         return;
     }
     double sw = 0.0, sr = 0.0, sp0 = 0.0, sp1 = 0.0, sp2 = 0.0;
+    unsigned isw = 0;
     const unsigned long long b0 = (unsigned long long)t * pl.cap;
     const unsigned nc = pl.counts[t];
     // the cells' loads are issued kUnroll at a time, the sums stay in kernel order
@@ -400,19 +417,20 @@ __device__ __forceinline__ void gather_fb_particle(const KParams &P, const Box &
         PairCell c[kUnroll];
         double U[kUnroll][NF];
 #pragma unroll
-        for (int k = 0; k < kUnroll; ++k) c[k] = unpack_pair(__ldg(pl.slots + b0 + q + k), P.R);
+        for (int k = 0; k < kUnroll; ++k) c[k] = unpack_pair(slot_load<NC>(pl.slots + b0 + q + k), P.R);
 #pragma unroll
         for (int k = 0; k < kUnroll; ++k)
             load_cell(u, S, S.at(owner(c[k].i, S.n0), owner(c[k].j, S.n1), owner(c[k].k, S.n2)), U[k]);
 #pragma unroll
-        for (int k = 0; k < kUnroll; ++k) fb_gather_add(P, wtab, c[k].cnt, U[k], sw, sr, sp0, sp1, sp2);
+        for (int k = 0; k < kUnroll; ++k) fb_gather_add<IW>(wtab, c[k].cnt, U[k], sw, isw, sr, sp0, sp1, sp2);
     }
     for (; q < nc; ++q) {
-        const PairCell c = unpack_pair(__ldg(pl.slots + b0 + q), P.R);
+        const PairCell c = unpack_pair(slot_load<NC>(pl.slots + b0 + q), P.R);
         double U[NF];
         load_cell(u, S, S.at(owner(c.i, S.n0), owner(c.j, S.n1), owner(c.k, S.n2)), U);
-        fb_gather_add(P, wtab, c.cnt, U, sw, sr, sp0, sp1, sp2);
+        fb_gather_add<IW>(wtab, c.cnt, U, sw, isw, sr, sp0, sp1, sp2);
     }
+    if (IW) sw = (double)isw * wtab[1];  // wtab[1] = 2^-3log2(S): exact
     if (!fb_gather_rows(P, sw, sr, sp0, sp1, sp2, m, pe0, pe1, pe2, Esn, G + s, gs)) report(st, PMP_ERR_NONFINITE, s);
 }
 
@@ -424,8 +442,92 @@ __global__ void __launch_bounds__(128) k_gather_fb(KParams P, Box S, const doubl
     __shared__ double wtab[kMaxS3 + 1];
     fill_omega_table(P, wtab);
     const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < p.count; t += stride)
-        gather_fb_particle(P, S, u, p, pl, G, st, wtab, t);
+    if (P.Slog >= 0) {
+        for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < p.count; t += stride)
+            gather_fb_particle<true, true>(P, S, u, p, pl, G, st, wtab, t);
+    } else {
+        for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < p.count; t += stride)
+            gather_fb_particle<false, true>(P, S, u, p, pl, G, st, wtab, t);
+    }
+}
+
+// Resident blocks per SM the fused plan + gather is compiled for (its
+// register budget).  512^3 sweep: 2 -> 30.6 ms, 3 -> 26.4 ms (no spills),
+// 4 -> 25.0 ms (64 registers, 16 bytes spilled).
+#ifndef PMP_PLAN_GATHER_MINB
+#define PMP_PLAN_GATHER_MINB 4
+#endif
+
+// Plan and gather of the supernova kind in one persistent kernel.  A warp
+// takes 32 consecutive particles of the processing order, plans them one
+// after the other as k_plan does (warp-cooperative), then each lane gathers
+// one of them as k_gather_fb does (thread per particle).  The plan is bound
+// by instruction issue and the gather by the FP64 pipe, so warps in the two
+// phases share an SM's issue slots and FP64 pipe instead of running one
+// kernel after the other.  Slots and counts are the same as those of the two
+// kernels; the gather reads the slots its warp has just written through the
+// coherent path, after the warp's barrier.
+template <int R, int SC>
+__global__ void __launch_bounds__(256, PMP_PLAN_GATHER_MINB) k_plan_gather_fb(KParams P, Box S, const double *__restrict__ u, Parts p,
+                                                        PlanPtrs pl, double *__restrict__ G, DevStatus *st)
+{
+    constexpr int W = 2 * R + 1;
+    constexpr int W3 = W * W * W;
+    extern __shared__ __align__(16) unsigned char psm[];
+    __shared__ int ncand_sh;
+    __shared__ double wtab[kMaxS3 + 1];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int Sn = SC ? SC : P.S;
+    unsigned *cand = reinterpret_cast<unsigned *>(psm);
+    const int wbytes = plan_warp_bytes(W, Sn);
+    unsigned char *wsm = psm + (W3 * 4 + 15) / 16 * 16 + (size_t)wib * wbytes;
+    float *sub = reinterpret_cast<float *>(wsm);  // [3][W*S]
+    float *csq = sub + 3 * W * Sn;                // [3][W]
+    float *fc2 = csq + 3 * W;                     // [3][W]
+    unsigned short *stc = reinterpret_cast<unsigned short *>(wsm + ((3 * W * Sn + 6 * W) * 4 + 15) / 16 * 16);
+    unsigned short *blist = stc + W3;
+    for (int i = threadIdx.x; i <= P.S3; i += blockDim.x) wtab[i] = (double)i / (double)P.S3;
+    if (wib == 0) {
+        const int n = build_candidates(P.rK, R, cand);
+        if (lane == 0) ncand_sh = n;
+    }
+    __syncthreads();
+    const int ncand = ncand_sh;
+    const long long nwarps = (long long)gridDim.x * nw;
+    for (long long t0 = ((long long)blockIdx.x * nw + wib) * 32; t0 < p.count; t0 += nwarps * 32) {
+        // lane j loads particle t0 + j's index, host cell and offsets
+        const long long tl = t0 + lane;
+        long long sl = 0;
+        unsigned long long hl = kNoHost;
+        float4 fl = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (tl < p.count) {
+            sl = pl.perm ? (long long)pl.perm[tl] : tl;
+            hl = pl.hosts[sl];
+            fl = pl.fr[sl];
+        }
+        const int nj = p.count - t0 < 32 ? (int)(p.count - t0) : 32;
+        for (int j = 0; j < nj; ++j) {
+            const long long s = __shfl_sync(kFull, sl, j);
+            const unsigned long long hp = __shfl_sync(kFull, hl, j);
+            float4 f4;
+            f4.x = __shfl_sync(kFull, fl.x, j);
+            f4.y = __shfl_sync(kFull, fl.y, j);
+            f4.z = __shfl_sync(kFull, fl.z, j);
+            f4.w = 0.f;
+            if (hp != kNoHost)
+                plan_particle<R, true, SC>(P, S, p, t0 + j, s, hp, f4, (unsigned)pl.cap, ncand, cand, sub, csq, fc2,
+                                           stc, blist, pl.counts, pl.slots, st);
+            else if (lane == 0)
+                pl.counts[t0 + j] = 0;
+        }
+        __syncwarp();
+        if (tl < p.count) {
+            if (P.Slog >= 0)
+                gather_fb_particle<true, false>(P, S, u, p, pl, G, st, wtab, tl);
+            else
+                gather_fb_particle<false, false>(P, S, u, p, pl, G, st, wtab, tl);
+        }
+    }
 }
 
 // Particle-mesh gather (MASS kind): V_K = V sum omega over the plan's cells in
@@ -620,7 +722,7 @@ template <int R, bool FB>
 __global__ void __launch_bounds__(256) k_deposit_atomic(KParams P, Box S, const double *__restrict__ u, Box B,
                                                         double *__restrict__ b, Parts p,
                                                         const double *__restrict__ G, PlanPtrs pl,
-                                                        double *__restrict__ E)
+                                                        double *__restrict__ E, double *__restrict__ scr)
 {
     constexpr int W = 2 * R + 1;
     constexpr int TAB = kPartsPerWarp * 3 * W;  // per warp: [8 particles][3 axes][W offsets]
@@ -730,9 +832,15 @@ __global__ void __launch_bounds__(256) k_deposit_atomic(KParams P, Box S, const 
                                      wj[2 * W + cell.k - ht[3 * j + 2] + R];
                     const double2 *d = reinterpret_cast<const double2 *>(
                         pl.drec + vidx(S, owner(cell.i, S.n0), owner(cell.j, S.n1), owner(cell.k, S.n2)) * kRec);
-                    const double2 d0 = __ldg(d), d1 = __ldg(d + 1), d2 = __ldg(d + 2);
+                    const double2 d0 = __ldg(d);
                     const double bh = kt[j] * w;
                     const double a = bh >= d0.x ? bh : d0.x;
+                    if (scr) {
+                        // the cell's factors (1, p/rho, E/rho) are applied by k_sink_spread
+                        atomicAdd(scr + B.at(cell.i, cell.j, cell.k), -a);
+                        continue;
+                    }
+                    const double2 d1 = __ldg(d + 1), d2 = __ldg(d + 2);
                     dU[0] = -a;
                     dU[1] = -(a * d0.y);
                     dU[2] = -(a * d1.x);
@@ -1024,6 +1132,40 @@ void launch_plan(const KParams &P, const Box &S, const Parts &p, const PlanPtrs 
     }
 }
 
+template <int R, int SC>
+static void plan_gather_one(const KParams &P, const Box &S, const double *u, const Parts &p, const PlanPtrs &pl,
+                            double *G, DevStatus *st, cudaStream_t stream)
+{
+    constexpr int W = 2 * R + 1;
+    const int Sn = SC ? SC : P.S;
+    const size_t head = (size_t)(W * W * W * 4 + 15) / 16 * 16;
+    const size_t wb = (size_t)plan_warp_bytes(W, Sn);
+    int warps = 8;
+    while (warps > 1 && head + warps * wb > 40 * 1024) --warps;
+    const size_t sm = head + warps * wb;
+    int dev = 0, nsm = 152, per_sm = 1;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_plan_gather_fb<R, SC>, warps * 32, sm) !=
+            cudaSuccess ||
+        per_sm < 1)
+        per_sm = 1;
+    const long long per_block = 32LL * warps;
+    const long long need = (p.count + per_block - 1) / per_block;
+    const long long grid = need < (long long)nsm * per_sm ? need : (long long)nsm * per_sm;
+    k_plan_gather_fb<R, SC><<<(unsigned)grid, warps * 32, sm, stream>>>(P, S, u, p, pl, G, st);
+}
+
+void launch_plan_gather_fb(const KParams &P, const Box &S, const double *u, const Parts &p, const PlanPtrs &pl,
+                           double *G, DevStatus *st, cudaStream_t stream)
+{
+    if (p.count == 0) return;
+    if (P.S == 4) {
+        PMP_DISPATCH_R(P.R, (plan_gather_one<RR, 4>(P, S, u, p, pl, G, st, stream)));
+    } else {
+        PMP_DISPATCH_R(P.R, (plan_gather_one<RR, 0>(P, S, u, p, pl, G, st, stream)));
+    }
+}
+
 // Blocks of the thread-per-sink kernels.  They run grid-stride over the
 // processing order, so the sinks in flight are a window of grid x
 // kSinkThreads consecutive sinks; its kernel cells (about cells / sinks of
@@ -1087,7 +1229,7 @@ void launch_gather(const KParams &P, const Box &S, const double *u, const Parts 
 }
 
 void launch_deposit_atomic(const KParams &P, const Box &S, const double *u, const Box &B, double *b, const Parts &p,
-                           const double *G, const PlanPtrs &pl, double *E, cudaStream_t stream)
+                           const double *G, const PlanPtrs &pl, double *E, double *scr, cudaStream_t stream)
 {
     if (p.count == 0) return;
     // Only resident blocks: the grid-stride loop then moves all of them
@@ -1111,9 +1253,10 @@ void launch_deposit_atomic(const KParams &P, const Box &S, const double *u, cons
     if (occ < 1) occ = 1;
     const unsigned nb = (unsigned)(blocks_needed < (long long)nsm * occ ? blocks_needed : (long long)nsm * occ);
     if (P.kind != PMP_KIND_SINK) {
-        PMP_DISPATCH_R(P.R, (k_deposit_atomic<RR, true><<<nb, 256, 0, stream>>>(P, S, u, B, b, p, G, pl, E)));
+        PMP_DISPATCH_R(P.R,
+                       (k_deposit_atomic<RR, true><<<nb, 256, 0, stream>>>(P, S, u, B, b, p, G, pl, E, nullptr)));
     } else {
-        PMP_DISPATCH_R(P.R, (k_deposit_atomic<RR, false><<<nb, 256, 0, stream>>>(P, S, u, B, b, p, G, pl, E)));
+        PMP_DISPATCH_R(P.R, (k_deposit_atomic<RR, false><<<nb, 256, 0, stream>>>(P, S, u, B, b, p, G, pl, E, scr)));
     }
 }
 
