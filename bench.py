@@ -178,7 +178,8 @@ def kernel_cell_count(parts, n, rK, chunk=1 << 20):
 # Algorithmic work per kernel launch.  Particle kernels: canonical FP64
 # operations per (particle, kernel cell) pair; cell kernels: bytes a perfect
 # implementation moves.  See the kernel table of the design notes.
-FLOPS_PER_PAIR = {"fb_gather": 9, "fb_deposit": 29, "sink_gather": 8, "sink_deposit": 7, "sink_return": 14}
+FLOPS_PER_PAIR = {"fb_gather": 9, "fb_deposit": 29, "fb_gather_deposit": 9 + 29, "sink_gather": 8,
+                  "sink_deposit": 7, "sink_return": 14}
 FP32_PEAK_TOPS = 36.9  # measured FP32 instruction rate of this GB300 (dependent-free FFMA stream)
 
 
@@ -277,13 +278,16 @@ def run_ours(args, world, rank, local):
     P_sk = pmp.Pass(w["sink_params"], box, state, sk, mode=args.mode)
     stream = torch.cuda.current_stream()
 
-    phases = ["fb_zero", "fb_gather", "fb_deposit", "fb_fold", "fb_apply",
-              "sink_zero", "sink_gather", "sink_deposit", "sink_fold", "sink_apply"]
-    # own kernels per step.  Supernova pass: zero, prologue, plan, gather,
-    # deposit, fold, apply (fast + queued); sink pass: zero, prologue, plan,
-    # per-cell quantities, gather, deposit, fold, eta, Step-4 return, apply.
-    # The sorted deposit adds a key kernel and a segment kernel per pass.
-    launches_per_step = 18 if args.mode == "atomic" else 20
+    phases = ["fb_zero", "fb_gather_deposit", "fb_fold", "fb_apply",
+              "sink_zero", "sink_gather_deposit", "sink_fold", "sink_apply"]
+    # own kernels per step (the CUB sorts and scans are library kernels).
+    # ATOMIC: supernova pass zero, prologue, plan + gather + deposit, fold,
+    # apply (fast + queued) = 6; sink pass zero, prologue, plan, per-cell
+    # records, gather, deposit, spread, fold, eta, Step-4 return, apply = 11.
+    # SORTED: the supernova deposit is its own launches (plan + gather fused):
+    # key, run and long-run kernels per pass, no spread.  ROUNDED: a deposit
+    # and a rounding kernel per pass, no spread.
+    launches_per_step = {"atomic": 17, "sorted": 21, "rounded": 19}[args.mode]
     state0 = state.clone()
     sink0 = {k: sk[k].clone() for k in ("m", "px", "py", "pz")}
 
@@ -308,9 +312,7 @@ def run_ours(args, world, rank, local):
             mark()
             pmp.pmp_zero_buffer(c, ps.buffer)
             mark()
-            pmp.pmp_gather(c, ps.state, parts, ps.gathered, args.mode, ps.workspace)
-            mark()
-            pmp.pmp_deposit(c, ps.state, parts, ps.gathered, ps.buffer, args.mode, ps.workspace)
+            pmp.pmp_gather_deposit(c, ps.state, parts, ps.gathered, ps.buffer, args.mode, ps.workspace)
             mark()
             pmp.pmp_fold_ghosts(c, ps.buffer)
             mark()
@@ -348,11 +350,11 @@ def run_ours(args, world, rank, local):
     ms_per_step = max_over_ranks(world, ms_total / args.steps)
     phase_ms = {}
     for marks in events:
-        # marks per pass: zero|gather|deposit|fold|apply boundaries (6 marks each)
+        # marks per pass: zero|gather+deposit|fold|apply boundaries (5 marks each)
         for p in range(2):
-            m = marks[p * 6:(p + 1) * 6]
-            for i in range(5):
-                name = phases[p * 5 + i]
+            m = marks[p * 5:(p + 1) * 5]
+            for i in range(4):
+                name = phases[p * 4 + i]
                 phase_ms[name] = phase_ms.get(name, 0.0) + m[i].elapsed_time(m[i + 1]) / args.steps
     kernel_ms = {}
     for tag, ps in (("fb", P_fb), ("sink", P_sk)):
@@ -457,8 +459,7 @@ def end_to_end(args, w, world, state, fb, sk, P_fb, P_sk, cycle, stream):
         for P, parts in ps:
             c = P.ctx
             pmp.pmp_zero_buffer(c, P.buffer)
-            pmp.pmp_gather(c, P.state, parts, P.gathered, args.mode, P.workspace)
-            pmp.pmp_deposit(c, P.state, parts, P.gathered, P.buffer, args.mode, P.workspace)
+            pmp.pmp_gather_deposit(c, P.state, parts, P.gathered, P.buffer, args.mode, P.workspace)
             pmp.pmp_fold_ghosts(c, P.buffer)
             pmp.pmp_apply_limited(c, P.state, P.buffer, parts, P.gathered, None, P.workspace)
 

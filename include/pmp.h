@@ -219,6 +219,17 @@ pmp_status pmp_gather(pmp_ctx *ctx, const pmp_mesh *state, const pmp_particles *
 pmp_status pmp_deposit(pmp_ctx *ctx, const pmp_mesh *state, const pmp_particles *particles, const double *gathered,
                        pmp_mesh *buffer, int32_t mode, void *workspace, size_t workspace_bytes);
 
+/* pmp_gather followed by pmp_deposit (same arguments, same results: the
+ * gathered rows, the plan in `workspace` and Step 1 into `buffer`).  For
+ * supernovae in the ATOMIC mode the two run as one kernel: a warp plans,
+ * gathers and deposits 32 consecutive particles before it takes the next,
+ * so the deposit's FP64 work overlaps the plan's integer work and re-reads
+ * cells the gather has just read.  The buffer sums then differ from those
+ * of the two separate calls only by the order of the atomic additions.
+ * Other kinds and modes run the two calls one after the other. */
+pmp_status pmp_gather_deposit(pmp_ctx *ctx, const pmp_mesh *state, const pmp_particles *particles, double *gathered,
+                              pmp_mesh *buffer, int32_t mode, void *workspace, size_t workspace_bytes);
+
 /* Step 2 on one GPU (Sec. 2.2, Step 2): each ghost cell of the buffer is added
  * to the valid cell that owns it (periodic axes only); a valid cell with
  * several images sums them in the fixed order of App. A.2 taken as the

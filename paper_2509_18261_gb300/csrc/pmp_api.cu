@@ -514,8 +514,10 @@ pmp_status pmp_zero_buffer(pmp_ctx *ctx, pmp_mesh *buffer)
     return last_launch();
 }
 
-pmp_status pmp_gather(pmp_ctx *ctx, const pmp_mesh *state, const pmp_particles *particles, double *gathered,
-                      int32_t mode, void *workspace, size_t workspace_bytes)
+// pmp_gather; with `fused` (supernovae, ATOMIC, buffer checked by the caller)
+// also Step 1 into that buffer, in the same launch as plan and gather.
+static pmp_status gather_impl(pmp_ctx *ctx, const pmp_mesh *state, const pmp_particles *particles, double *gathered,
+                              int32_t mode, void *workspace, size_t workspace_bytes, pmp_mesh *fused)
 {
     if (!ctx || (!gathered && particles && particles->count > 0)) return PMP_ERR_ARG;
     if (!valid_mode(mode)) return PMP_ERR_ARG;
@@ -560,7 +562,13 @@ pmp_status pmp_gather(pmp_ctx *ctx, const pmp_mesh *state, const pmp_particles *
             Timed tm(ctx, "prologue");
             pmp::launch_prologue(S, q, nullptr, nullptr, pl, ctx->st, st);
         }
-        if (ctx->p.kind == PMP_KIND_FEEDBACK) {
+        if (fused) {
+            Box B;
+            s = make_box(fused, &B);
+            if (s) return s;
+            Timed tm(ctx, "gather_deposit");
+            pmp::launch_pass1_fb(P, S, state->data, B, fused->data, q, pl, gathered, ctx->st, st);
+        } else if (ctx->p.kind == PMP_KIND_FEEDBACK) {
             Timed tm(ctx, "plan_gather");
             pmp::launch_plan_gather_fb(P, S, state->data, q, pl, gathered, ctx->st, st);
         } else {
@@ -583,6 +591,29 @@ pmp_status pmp_gather(pmp_ctx *ctx, const pmp_mesh *state, const pmp_particles *
     ctx->plan_nvalid = nv;
     ctx->plan_mode = mode;
     return PMP_OK;
+}
+
+pmp_status pmp_gather(pmp_ctx *ctx, const pmp_mesh *state, const pmp_particles *particles, double *gathered,
+                      int32_t mode, void *workspace, size_t workspace_bytes)
+{
+    return gather_impl(ctx, state, particles, gathered, mode, workspace, workspace_bytes, nullptr);
+}
+
+pmp_status pmp_gather_deposit(pmp_ctx *ctx, const pmp_mesh *state, const pmp_particles *particles, double *gathered,
+                              pmp_mesh *buffer, int32_t mode, void *workspace, size_t workspace_bytes)
+{
+    if (!ctx || !valid_mode(mode)) return PMP_ERR_ARG;
+    if (ctx->p.kind == PMP_KIND_FEEDBACK && mode == PMP_MODE_ATOMIC) {
+        Box S, B;
+        pmp_status s = check_pair(ctx, state, buffer, &S, &B);
+        if (s) return s;
+        if (!particles || particles->count == 0)
+            return gather_impl(ctx, state, particles, gathered, mode, workspace, workspace_bytes, nullptr);
+        return gather_impl(ctx, state, particles, gathered, mode, workspace, workspace_bytes, buffer);
+    }
+    pmp_status s = gather_impl(ctx, state, particles, gathered, mode, workspace, workspace_bytes, nullptr);
+    if (s || !particles || particles->count == 0) return s;
+    return pmp_deposit(ctx, state, particles, gathered, buffer, mode, workspace, workspace_bytes);
 }
 
 static pmp_status check_plan(const pmp_ctx *ctx, long long n, long long nvalid, const void *ws)

@@ -28,7 +28,7 @@ STATUS = {
 }
 EXPORTS = [
     "pmp_create", "pmp_destroy", "pmp_set_stream", "pmp_set_rounding_margin", "pmp_gathered_rows", "pmp_workspace_size", "pmp_zero_buffer",
-    "pmp_gather", "pmp_deposit", "pmp_fold_ghosts", "pmp_apply_limited", "pmp_backward", "pmp_get_error",
+    "pmp_gather", "pmp_deposit", "pmp_gather_deposit", "pmp_fold_ghosts", "pmp_apply_limited", "pmp_backward", "pmp_get_error",
     "pmp_limiter_counts", "pmp_timing_enable", "pmp_timing_read", "pmp_deposit_noalloc",
     "pmp_create_sinks_workspace_size", "pmp_create_sinks", "pmp_apply_extra",
     "pmp_batch_create", "pmp_batch_set_particles", "pmp_batch_set_strategy", "pmp_batch_strategies",
@@ -106,6 +106,7 @@ def load():
         "pmp_zero_buffer": ([vp, M], i32),
         "pmp_gather": ([vp, M, Pa, vp, i32, vp, ctypes.c_size_t], i32),
         "pmp_deposit": ([vp, M, Pa, vp, M, i32, vp, ctypes.c_size_t], i32),
+        "pmp_gather_deposit": ([vp, M, Pa, vp, M, i32, vp, ctypes.c_size_t], i32),
         "pmp_fold_ghosts": ([vp, M], i32),
         "pmp_apply_limited": ([vp, M, M, Pa, vp, vp, vp, ctypes.c_size_t], i32),
         "pmp_backward": ([vp, M, M, Pa, vp, vp, vp, vp, ctypes.c_size_t], i32),
@@ -286,6 +287,15 @@ def pmp_deposit(ctx, state, parts, gathered, buffer, mode="atomic", workspace=No
                                              ctypes.byref(buffer.c()), MODES.get(mode, mode), ws, wsb))
 
 
+def pmp_gather_deposit(ctx, state, parts, gathered, buffer, mode="atomic", workspace=None):
+    ctx._sync_stream()
+    pp = _parts(parts)
+    ws, wsb = _ws(workspace)
+    _check("pmp_gather_deposit",
+           load().pmp_gather_deposit(ctx.h, ctypes.byref(state.c()), ctypes.byref(pp), _ptr(gathered),
+                                     ctypes.byref(buffer.c()), MODES.get(mode, mode), ws, wsb))
+
+
 def pmp_fold_ghosts(ctx, buffer):
     ctx._sync_stream()
     _check("pmp_fold_ghosts", load().pmp_fold_ghosts(ctx.h, ctypes.byref(buffer.c())))
@@ -447,11 +457,13 @@ def parts_to_device(p, device="cuda"):
 
 class Pass:
     """One PMP pass (zero, gather, deposit, fold, limited apply) of one kind
-    on one box, with its buffers allocated once."""
+    on one box, with its buffers allocated once.  `fused`: gather and deposit
+    through pmp_gather_deposit (else pmp_gather, then pmp_deposit)."""
 
-    def __init__(self, params, box, state, parts, mode="atomic", dx=1.0, periodic=(1, 1, 1), want_eta=False):
+    def __init__(self, params, box, state, parts, mode="atomic", dx=1.0, periodic=(1, 1, 1), want_eta=False,
+                 fused=True):
         self.ctx = Context(params)
-        self.box, self.mode = box, mode
+        self.box, self.mode, self.fused = box, mode, fused
         dev = state.device
         self.state = Mesh(state, box.n, box.g, periodic, dx)
         self.buffer = Mesh(torch.empty((5, box.field_stride), dtype=torch.float64, device=dev), box.n, box.g,
@@ -471,10 +483,13 @@ class Pass:
         c = self.ctx
         has = self.parts is not None and self.parts["x"].numel() > 0
         pmp_zero_buffer(c, self.buffer)
-        pmp_gather(c, self.state, self.parts if has else _EMPTY(self.state.data.device), self.gathered, self.mode,
-                   self.workspace)
-        if has:
-            pmp_deposit(c, self.state, self.parts, self.gathered, self.buffer, self.mode, self.workspace)
+        if has and self.fused:
+            pmp_gather_deposit(c, self.state, self.parts, self.gathered, self.buffer, self.mode, self.workspace)
+        else:
+            pmp_gather(c, self.state, self.parts if has else _EMPTY(self.state.data.device), self.gathered,
+                       self.mode, self.workspace)
+            if has:
+                pmp_deposit(c, self.state, self.parts, self.gathered, self.buffer, self.mode, self.workspace)
         if stop_after == "deposit":
             return
         pmp_fold_ghosts(c, self.buffer)

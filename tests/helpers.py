@@ -21,7 +21,8 @@ def cuda_ok():
 def gpu_pass(params, box, state_np, parts_np, mode="atomic", periodic=(1, 1, 1), dx=1.0, stop_after=None):
     """Runs one pass on the GPU.  Returns dict of numpy arrays: state (after),
     buf (after the requested stage), gathered, eta, parts (after), counts,
-    error."""
+    error.  Mode "atomic-split": the atomic mode through pmp_gather and
+    pmp_deposit (else gather and deposit go through pmp_gather_deposit)."""
     import torch
 
     from paper_2509_18261_gb300 import pmp
@@ -29,7 +30,9 @@ def gpu_pass(params, box, state_np, parts_np, mode="atomic", periodic=(1, 1, 1),
     dev = "cuda"
     st = torch.from_numpy(state_np.copy()).to(dev)
     parts = pmp.parts_to_device(parts_np, dev) if parts_np is not None else None
-    ps = pmp.Pass(params, box, st, parts, mode=mode, dx=dx, periodic=periodic, want_eta=True)
+    fused = mode != "atomic-split"
+    mode = "atomic" if mode == "atomic-split" else mode
+    ps = pmp.Pass(params, box, st, parts, mode=mode, dx=dx, periodic=periodic, want_eta=True, fused=fused)
     ps.run(stop_after=stop_after)
     torch.cuda.synchronize()
     out = dict(
