@@ -105,8 +105,9 @@ typedef enum { PMP_KIND_FEEDBACK = 0, PMP_KIND_SINK = 1, PMP_KIND_MASS = 2 } pmp
  *          the sorted one up to the order of additions.  For sinks every
  *          pair's change is -a (1, p/rho, E/rho) with its cell's factors, so
  *          the deposit adds only -a per pair into a one-field scratch and a
- *          second pass adds (sum -a)(1, p/rho, E/rho) to each buffer cell: the
- *          same sum up to the order of additions and one product per value.
+ *          second pass adds (sum -a)(1, p/rho, E/rho) to each buffer cell
+ *          (fused multiply-adds): the same sum up to the order of additions
+ *          and the rounding of one product per value.
  * SORTED:  (cell, particle) pairs sorted by cell, then each cell summed in
  *          particle-index order; deterministic.
  * ROUNDED: the paper's reproducible atomics (App. A.1).  Each atomic
@@ -221,12 +222,14 @@ pmp_status pmp_deposit(pmp_ctx *ctx, const pmp_mesh *state, const pmp_particles 
 
 /* pmp_gather followed by pmp_deposit (same arguments, same results: the
  * gathered rows, the plan in `workspace` and Step 1 into `buffer`).  For
- * supernovae in the ATOMIC mode the two run as one kernel: a warp plans,
- * gathers and deposits 32 consecutive particles before it takes the next,
- * so the deposit's FP64 work overlaps the plan's integer work and re-reads
- * cells the gather has just read.  The buffer sums then differ from those
- * of the two separate calls only by the order of the atomic additions.
- * Other kinds and modes run the two calls one after the other. */
+ * supernovae and sinks in the ATOMIC mode plan, gather and deposit run as
+ * one kernel: a warp plans, gathers and deposits 32 consecutive particles
+ * before it takes the next, so the FP64 work of gather and deposit overlaps
+ * the plan's integer work and the deposit re-reads cells the gather has
+ * just read (sinks: the per-cell records are written first, the scratch is
+ * spread after).  The buffer sums then differ from those of the two
+ * separate calls only by the order of the atomic additions.  Other kinds
+ * and modes run the two calls one after the other. */
 pmp_status pmp_gather_deposit(pmp_ctx *ctx, const pmp_mesh *state, const pmp_particles *particles, double *gathered,
                               pmp_mesh *buffer, int32_t mode, void *workspace, size_t workspace_bytes);
 

@@ -562,27 +562,41 @@ static pmp_status gather_impl(pmp_ctx *ctx, const pmp_mesh *state, const pmp_par
             Timed tm(ctx, "prologue");
             pmp::launch_prologue(S, q, nullptr, nullptr, pl, ctx->st, st);
         }
-        if (fused) {
-            Box B;
-            s = make_box(fused, &B);
-            if (s) return s;
-            Timed tm(ctx, "gather_deposit");
-            pmp::launch_pass1_fb(P, S, state->data, B, fused->data, q, pl, gathered, ctx->st, st);
-        } else if (ctx->p.kind == PMP_KIND_FEEDBACK) {
-            Timed tm(ctx, "plan_gather");
-            pmp::launch_plan_gather_fb(P, S, state->data, q, pl, gathered, ctx->st, st);
-        } else {
-            Timed tm(ctx, "plan");
-            pmp::launch_plan(P, S, q, pl, ctx->st, st);
-        }
     }
     if (ctx->p.kind == PMP_KIND_SINK) {
         Timed tm(ctx, "cell_records");
         pmp::launch_sink_aux(P, S, state->data, pl.grec, pl.drec, st);
     }
-    if (q.count > 0 && ctx->p.kind != PMP_KIND_FEEDBACK) {
-        Timed tm(ctx, "gather");
-        pmp::launch_gather(P, S, state->data, q, pl, gathered, ctx->st, st);
+    if (q.count > 0) {
+        if (fused) {
+            Box B;
+            s = make_box(fused, &B);
+            if (s) return s;
+            if (ctx->p.kind == PMP_KIND_FEEDBACK) {
+                Timed tm(ctx, "gather_deposit");
+                pmp::launch_pass1_fb(P, S, state->data, B, fused->data, q, pl, gathered, ctx->st, st);
+            } else {
+                // sinks: -a per pair into the scratch tail, then the cells' factors
+                double *scr = reinterpret_cast<double *>(w + ebuf_offset(L));
+                if (cudaMemsetAsync(scr, 0, tail_bytes(ctx->p, mode, fused), st) != cudaSuccess) return PMP_ERR_CUDA;
+                {
+                    Timed tm(ctx, "gather_deposit");
+                    pmp::launch_pass1_sink(P, S, state->data, B, scr, q, pl, gathered, ctx->st, st);
+                }
+                Timed tm(ctx, "spread");
+                pmp::launch_sink_spread(S, B, fused->data, scr, pl.drec, st);
+            }
+        } else if (ctx->p.kind == PMP_KIND_FEEDBACK) {
+            Timed tm(ctx, "plan_gather");
+            pmp::launch_plan_gather_fb(P, S, state->data, q, pl, gathered, ctx->st, st);
+        } else {
+            {
+                Timed tm(ctx, "plan");
+                pmp::launch_plan(P, S, q, pl, ctx->st, st);
+            }
+            Timed tm(ctx, "gather");
+            pmp::launch_gather(P, S, state->data, q, pl, gathered, ctx->st, st);
+        }
     }
     s = last_launch();
     if (s) return s;
@@ -602,13 +616,17 @@ pmp_status pmp_gather(pmp_ctx *ctx, const pmp_mesh *state, const pmp_particles *
 pmp_status pmp_gather_deposit(pmp_ctx *ctx, const pmp_mesh *state, const pmp_particles *particles, double *gathered,
                               pmp_mesh *buffer, int32_t mode, void *workspace, size_t workspace_bytes)
 {
-    if (!ctx || !valid_mode(mode)) return PMP_ERR_ARG;
-    if (ctx->p.kind == PMP_KIND_FEEDBACK && mode == PMP_MODE_ATOMIC) {
+    if (!ctx || !valid_mode(mode) || (particles && particles->count < 0)) return PMP_ERR_ARG;
+    if ((ctx->p.kind == PMP_KIND_FEEDBACK || ctx->p.kind == PMP_KIND_SINK) && mode == PMP_MODE_ATOMIC) {
         Box S, B;
         pmp_status s = check_pair(ctx, state, buffer, &S, &B);
         if (s) return s;
         if (!particles || particles->count == 0)
             return gather_impl(ctx, state, particles, gathered, mode, workspace, workspace_bytes, nullptr);
+        const size_t tail = tail_bytes(ctx->p, mode, buffer);
+        if (tail && (!workspace || workspace_bytes < ebuf_offset(layout(ctx->p, particles->count,
+                                                                         nvalid_of(state), mode)) + tail))
+            return PMP_ERR_WORKSPACE;
         return gather_impl(ctx, state, particles, gathered, mode, workspace, workspace_bytes, buffer);
     }
     pmp_status s = gather_impl(ctx, state, particles, gathered, mode, workspace, workspace_bytes, nullptr);

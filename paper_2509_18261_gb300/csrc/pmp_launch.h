@@ -48,6 +48,11 @@ void launch_plan_gather_fb(const KParams &P, const Box &S, const double *u, cons
 // launch_deposit_atomic, up to the order of the atomic additions).
 void launch_pass1_fb(const KParams &P, const Box &S, const double *u, const Box &B, double *b, const Parts &p,
                      const PlanPtrs &pl, double *G, DevStatus *st, cudaStream_t stream);
+// Sink kind, ATOMIC mode: plan, gather and the scratch deposit (-a per pair
+// into scr, zeroed) in one launch; the per-cell records must be written
+// first, launch_sink_spread completes Step 1.
+void launch_pass1_sink(const KParams &P, const Box &S, const double *u, const Box &B, double *scr, const Parts &p,
+                       const PlanPtrs &pl, double *G, DevStatus *st, cudaStream_t stream);
 // E (optional): App. A.1 error-bound buffer, the buffer's layout, zeroed.
 // scr (optional, sinks): one-field scratch with the buffer's layout, zeroed;
 // the deposit then sums only -a per cell into it and launch_sink_spread

@@ -246,9 +246,11 @@ __global__ void __launch_bounds__(256) k_sink_aux(KParams P, Box S, const double
 // Delta U = -a (1, p/rho, E/rho) with the factors of its cell (the owner, for
 // a ghost image), so the deposit sums only s = sum(-a) per buffer cell into a
 // one-field scratch, and here the cell's buffer gains s (1, p/rho, E/rho)
-// from its owner's D record.  In real arithmetic this is the sum of the
-// pairs' five-field changes; in FP64 it differs from that sum by the order of
-// the additions and one rounding of the product, as any atomic order does.
+// from its owner's D record (fused multiply-adds: this pass is bound by the
+// FP64 pipe, not by HBM, at five separate operations per cell).  In real
+// arithmetic this is the sum of the pairs' five-field changes; in FP64 it
+// differs from that sum by the order of the additions and the rounding of
+// the products, as any atomic order does.
 // A block takes padded rows (j, k), its threads the cells i of the row.
 __global__ void __launch_bounds__(256) k_sink_spread(Box S, Box B, double *__restrict__ b,
                                                      const double *__restrict__ scr, const double *__restrict__ drec)
@@ -267,10 +269,10 @@ __global__ void __launch_bounds__(256) k_sink_spread(Box S, Box B, double *__res
                 drec + vidx(S, owner(i, S.n0), owner(j, S.n1), owner(k, S.n2)) * kRec);
             const double2 d0 = __ldg(d), d1 = __ldg(d + 1), d2 = __ldg(d + 2);
             b[c] += sc;
-            b[B.fs + c] += sc * d0.y;
-            b[2 * B.fs + c] += sc * d1.x;
-            b[3 * B.fs + c] += sc * d1.y;
-            b[4 * B.fs + c] += sc * d2.x;
+            b[B.fs + c] = fma(sc, d0.y, b[B.fs + c]);
+            b[2 * B.fs + c] = fma(sc, d1.x, b[2 * B.fs + c]);
+            b[3 * B.fs + c] = fma(sc, d1.y, b[3 * B.fs + c]);
+            b[4 * B.fs + c] = fma(sc, d2.x, b[4 * B.fs + c]);
         }
     }
 }

@@ -750,7 +750,7 @@ __global__ void __launch_bounds__(128) k_gather_mass(KParams P, Box S, Parts p, 
 
 // Sink gather.  Writes the particle's per-axis Gaussian factors
 // exp(-d^2 / r_acc^2) to wts[s][3][W] for the deposit and Step 4.
-template <int R>
+template <int R, bool NC = true>
 __device__ __forceinline__ void gather_sink_particle(const KParams &P, const Box &S, const double *__restrict__ u,
                                                      const Parts &p, const PlanPtrs &pl, double *__restrict__ G,
                                                      DevStatus *st, long long t)
@@ -775,7 +775,7 @@ __device__ __forceinline__ void gather_sink_particle(const KParams &P, const Box
         double2 g[kUnroll][3];
 #pragma unroll
         for (int k = 0; k < kUnroll; ++k) {
-            const PairCell c = unpack_pair(__ldg(pl.slots + b0 + q + k), P.R);
+            const PairCell c = unpack_pair(slot_load<NC>(pl.slots + b0 + q + k), P.R);
             const double2 *r = reinterpret_cast<const double2 *>(
                 pl.grec + vidx(S, owner(c.i, S.n0), owner(c.j, S.n1), owner(c.k, S.n2)) * kRec);
             g[k][0] = __ldg(r);
@@ -792,7 +792,7 @@ __device__ __forceinline__ void gather_sink_particle(const KParams &P, const Box
         }
     }
     for (; q < nc; ++q) {
-        const PairCell c = unpack_pair(__ldg(pl.slots + b0 + q), P.R);
+        const PairCell c = unpack_pair(slot_load<NC>(pl.slots + b0 + q), P.R);
         const double2 *g =
             reinterpret_cast<const double2 *>(pl.grec + vidx(S, owner(c.i, S.n0), owner(c.j, S.n1), owner(c.k, S.n2)) * kRec);
         const double2 g0 = __ldg(g), g1 = __ldg(g + 1), g2 = __ldg(g + 2);
@@ -880,6 +880,148 @@ __device__ __forceinline__ void sink_pair_delta(const KParams &P, const Box &S, 
     dU[3] = -(a * d1.y);
     dU[4] = -(a * d2.x);
     eta = d2.y;
+}
+
+// Blocks per SM of the fused sink kernel (0: an L2 window of sinks in
+// flight, as the sink gather).
+#ifndef PMP_SINK_PASS1_BPS
+#define PMP_SINK_PASS1_BPS 0
+#endif
+
+// Per-warp shared memory of k_pass1_sink: the plan's FP32 centre squares
+// ([3][W], padded), then for 8 sinks their Gaussian factors ([8][3W]), K and
+// indices, and their host cells ([8][3]).
+__host__ __device__ constexpr int pass1_sink_warp_bytes(int W)
+{
+    return (3 * W * 4 + 15) / 16 * 16 + (kPartsPerWarp * 3 * W + 2 * kPartsPerWarp) * 8 + kPartsPerWarp * 3 * 4;
+}
+
+// Plan, gather and ATOMIC deposit of the sink kind in one persistent kernel
+// (pmp_gather_deposit; the per-cell records are written before it).  A warp
+// takes 32 consecutive sinks of the processing order and
+//   1. plans them one after the other (warp per sink, as k_plan);
+//   2. gathers them, a lane per sink (as k_gather_sink), which also writes
+//      each sink's Gaussian factors and K;
+//   3. adds -a of their pairs to the one-field scratch, 8 sinks at a time,
+//      lanes over the pairs (as k_deposit_atomic); k_sink_spread completes
+//      Step 1.
+template <int R>
+__global__ void __launch_bounds__(128) k_pass1_sink(KParams P, Box S, const double *__restrict__ u, Box B,
+                                                    double *__restrict__ scr, Parts p, PlanPtrs pl,
+                                                    double *__restrict__ G, DevStatus *st)
+{
+    constexpr int W = 2 * R + 1;
+    constexpr int W3 = W * W * W;
+    extern __shared__ __align__(16) unsigned char psm[];
+    __shared__ int ncand_sh;
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    unsigned *cand = reinterpret_cast<unsigned *>(psm);
+    const size_t head = (size_t)(W3 * 4 + 15) / 16 * 16;
+    unsigned char *wsm = psm + head + (size_t)wib * pass1_sink_warp_bytes(W);
+    float *csq = reinterpret_cast<float *>(wsm);  // [3][W]
+    double *wt = reinterpret_cast<double *>(wsm + (3 * W * 4 + 15) / 16 * 16);  // [8][3W]
+    double *kt = wt + kPartsPerWarp * 3 * W;                                   // [8]
+    long long *sidt = reinterpret_cast<long long *>(kt + kPartsPerWarp);       // [8]
+    int *ht = reinterpret_cast<int *>(sidt + kPartsPerWarp);                   // [8][3]
+    if (wib == 0) {
+        const int n = build_candidates(P.rK, R, cand);
+        if (lane == 0) ncand_sh = n;
+    }
+    __syncthreads();
+    const int ncand = ncand_sh;
+    const long long nwarps = (long long)gridDim.x * nw;
+    const long long gs = p.count;
+    for (long long t0 = ((long long)blockIdx.x * nw + wib) * 32; t0 < p.count; t0 += nwarps * 32) {
+        const long long tl = t0 + lane;
+        long long sl = 0;
+        unsigned long long hl = kNoHost;
+        float4 fl = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (tl < p.count) {
+            sl = pl.perm ? (long long)pl.perm[tl] : tl;
+            hl = pl.hosts[sl];
+            fl = pl.fr[sl];
+        }
+        const int nj = p.count - t0 < 32 ? (int)(p.count - t0) : 32;
+        // 1. plan
+        unsigned myc = 0;
+        for (int j = 0; j < nj; ++j) {
+            const long long s = __shfl_sync(kFull, sl, j);
+            const unsigned long long hp = __shfl_sync(kFull, hl, j);
+            float4 f4;
+            f4.x = __shfl_sync(kFull, fl.x, j);
+            f4.y = __shfl_sync(kFull, fl.y, j);
+            f4.z = __shfl_sync(kFull, fl.z, j);
+            f4.w = 0.f;
+            if (hp != kNoHost) {
+                const unsigned c = plan_particle<R, false, 0>(P, S, p, t0 + j, s, hp, f4, (unsigned)pl.cap, ncand,
+                                                              cand, nullptr, csq, nullptr, nullptr, nullptr, pl.counts,
+                                                              pl.slots, st);
+                if (lane == j) myc = c;
+            } else if (lane == 0) {
+                pl.counts[t0 + j] = 0;
+            }
+        }
+        __syncwarp();
+        // 2. gather, lane per sink
+        if (tl < p.count) gather_sink_particle<R, false>(P, S, u, p, pl, G, st, tl);
+        __syncwarp();
+        // 3. deposit of -a into the scratch, 8 sinks at a time
+        for (int jb = 0; jb < nj; jb += kPartsPerWarp) {
+            const int src = jb + (lane & (kPartsPerWarp - 1));
+            const unsigned cj = __shfl_sync(kFull, myc, src);
+            const long long sj = __shfl_sync(kFull, sl, src);
+            const unsigned long long hj = __shfl_sync(kFull, hl, src);
+            const bool mine = lane < kPartsPerWarp && jb + lane < nj;
+            unsigned incl = mine ? cj : 0;
+#pragma unroll
+            for (int d = 1; d < kPartsPerWarp; d <<= 1) {
+                const unsigned v = __shfl_up_sync(kFull, incl, d);
+                if (lane >= d) incl += v;
+            }
+            const unsigned total = __shfl_sync(kFull, incl, kPartsPerWarp - 1);
+            if (mine) {
+                sidt[lane] = sj;
+                kt[lane] = G[SK_K * gs + sj];
+                int hx, hy, hz;
+                unpack_host(hj, hx, hy, hz);
+                ht[3 * lane] = hx;
+                ht[3 * lane + 1] = hy;
+                ht[3 * lane + 2] = hz;
+            }
+            __syncwarp();
+            for (int i = lane; i < kPartsPerWarp * 3 * W; i += 32) {
+                const int j = i / (3 * W);
+                if (jb + j < nj) wt[i] = pl.wts[sidt[j] * (3 * W) + (i - j * 3 * W)];
+            }
+            __syncwarp();
+            for (unsigned g0 = 0; g0 < total; g0 += 32) {
+                const unsigned g = g0 + lane;
+                int j = 0;
+                unsigned before = 0;
+#pragma unroll
+                for (int k = 0; k < kPartsPerWarp - 1; ++k) {
+                    const unsigned ik = __shfl_sync(kFull, incl, k);
+                    if (g >= ik) {
+                        j = k + 1;
+                        before = ik;
+                    }
+                }
+                if (g < total) {
+                    const unsigned long long slot = (unsigned long long)(t0 + jb + j) * pl.cap + (g - before);
+                    const PairCell cell = unpack_pair(slot_load<false>(pl.slots + slot), P.R);
+                    const double *wj = wt + j * 3 * W;
+                    const double w = (wj[cell.i - ht[3 * j] + R] * wj[W + cell.j - ht[3 * j + 1] + R]) *
+                                     wj[2 * W + cell.k - ht[3 * j + 2] + R];
+                    const double d0x =
+                        __ldg(pl.drec + vidx(S, owner(cell.i, S.n0), owner(cell.j, S.n1), owner(cell.k, S.n2)) * kRec);
+                    const double bh = kt[j] * w;
+                    const double a = bh >= d0x ? bh : d0x;
+                    atomicAdd(scr + B.at(cell.i, cell.j, cell.k), -a);
+                }
+            }
+            __syncwarp();
+        }
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -1440,6 +1582,31 @@ void launch_gather(const KParams &P, const Box &S, const double *u, const Parts 
         const unsigned nbs = window_blocks(S, p.count, kSinkThreads, 8.0 * kRec, 1.5, PMP_SINK_GATHER_BPS);
         PMP_DISPATCH_R(P.R, (k_gather_sink<RR><<<nbs, kSinkThreads, 0, stream>>>(P, S, u, p, pl, G, st)));
     }
+}
+
+// The fused sink kernel: 4-warp blocks, each warp 32 sinks; a block has as
+// many sinks in flight as a 128-thread gather block, so an L2 window sets its
+// grid.  512^3 sweep (blocks per SM): 2 -> 45.7 ms, 3 -> 32.8 ms, 4 -> 27.5
+// ms, 6 -> 37.5 ms; two L2 windows give 4 (the separate plan, gather and
+// deposit took 2.6 + 16.2 + 9.6 ms).
+template <int R>
+static void pass1_sink_one(const KParams &P, const Box &S, const double *u, const Box &B, double *scr,
+                           const Parts &p, const PlanPtrs &pl, double *G, DevStatus *st, cudaStream_t stream)
+{
+    constexpr int W = 2 * R + 1;
+    constexpr int warps = 4;
+    const size_t sm = (size_t)(W * W * W * 4 + 15) / 16 * 16 + (size_t)warps * pass1_sink_warp_bytes(W);
+    const unsigned nb = window_blocks(S, (p.count + 31) / 32 * 32, 32 * warps, 8.0 * kRec, 2.0, PMP_SINK_PASS1_BPS);
+    const long long need = (p.count + 32LL * warps - 1) / (32LL * warps);
+    const unsigned grid = (unsigned)(need < (long long)nb ? need : (long long)nb);
+    k_pass1_sink<R><<<grid, 32 * warps, sm, stream>>>(P, S, u, B, scr, p, pl, G, st);
+}
+
+void launch_pass1_sink(const KParams &P, const Box &S, const double *u, const Box &B, double *scr, const Parts &p,
+                       const PlanPtrs &pl, double *G, DevStatus *st, cudaStream_t stream)
+{
+    if (p.count == 0) return;
+    PMP_DISPATCH_R(P.R, (pass1_sink_one<RR>(P, S, u, B, scr, p, pl, G, st, stream)));
 }
 
 void launch_deposit_atomic(const KParams &P, const Box &S, const double *u, const Box &B, double *b, const Parts &p,

@@ -99,7 +99,7 @@ def test_feedback_edge_boxes(orc, mode, n, g, rK, S, periodic):
     _check_pass(orc, syn.feedback_params(r_K=rK, subsample=S), box, state, parts, mode, periodic=periodic)
 
 
-@pytest.mark.parametrize("mode", ["sorted", "atomic"])
+@pytest.mark.parametrize("mode", ["sorted", "atomic", "atomic-split"])
 @pytest.mark.parametrize("n,g,rK,periodic,dt", [((9, 8, 10), 4, 4.0, (1, 1, 1), 0.5), ((7, 9, 6), 3, 2.7, (1, 0, 1), 2.0)])
 def test_sink_edge_boxes(orc, mode, n, g, rK, periodic, dt):
     rng = np.random.default_rng(7 + g)
