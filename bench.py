@@ -191,7 +191,6 @@ def roofline(kernel, ms, pairs, box, n_fb, n_sk, hbm_peak, peak_src):
         "fold": 120 * (box.ncells_padded - nvalid),
         "apply": 120 * nvalid + (8 * nvalid if kind == "sink" else 0),
         "cell_records": (40 + 96) * nvalid,
-        "eta": (8 + 8 + 8 + 16) * nvalid,
     }
     if stage == "plan":
         # FP32 decisions: 2 adds per candidate cell and per omega sub-point
@@ -215,6 +214,34 @@ def roofline(kernel, ms, pairs, box, n_fb, n_sk, hbm_peak, peak_src):
     r["ms_per_launch"] = ms
     r["traffic"] = profiled_traffic(kernel)
     return r
+
+
+def cell_pass_hbm(kernel_ms, box, hbm_peak):
+    """Per-launch HBM rate of the cell passes: algorithmic bytes (what a
+    perfect implementation moves) over the CUDA-event time of the launch, and
+    the fraction of the measured copy bandwidth.  The supernova apply is the
+    fast kernel plus the FP64 limiter on the queued cells (one phase, 120 B
+    per valid cell); the sink apply computes eta and updates the state in one
+    pass (128 B per valid cell with the eta it records for Step 4)."""
+    nvalid, npad = box.ncells_valid, box.ncells_padded
+    phases = {
+        "fb_zero": (("fb_zero",), 40 * npad),
+        "fb_fold": (("fb_fold",), 120 * (npad - nvalid)),
+        "fb_apply": (("fb_apply", "fb_apply_fp64"), 120 * nvalid),
+        "sink_zero": (("sink_zero",), 40 * npad),
+        "sink_cell_records": (("sink_cell_records",), (40 + 96) * nvalid),
+        "sink_spread": (("sink_spread",), 136 * npad),
+        "sink_fold": (("sink_fold",), 120 * (npad - nvalid)),
+        "sink_apply": (("sink_apply",), 128 * nvalid),
+    }
+    out = {}
+    for name, (kernels, nbytes) in phases.items():
+        if not all(k in kernel_ms for k in kernels):
+            continue
+        ms = sum(kernel_ms[k][1] for k in kernels)
+        gbs = nbytes / (ms * 1e-3) / 1e9
+        out[name] = {"ms": round(ms, 4), "bytes": nbytes, "GB/s": round(gbs, 1), "frac": round(gbs / hbm_peak, 4)}
+    return out
 
 
 def src_digest():
@@ -280,14 +307,15 @@ def run_ours(args, world, rank, local):
 
     phases = ["fb_zero", "fb_gather_deposit", "fb_fold", "fb_apply",
               "sink_zero", "sink_gather_deposit", "sink_fold", "sink_apply"]
-    # own kernels per step (the CUB sorts and scans are library kernels).
-    # ATOMIC: supernova pass zero, prologue, plan + gather + deposit, fold,
-    # apply (fast + queued) = 6; sink pass zero, prologue, plan, per-cell
-    # records, gather, deposit, spread, fold, eta, Step-4 return, apply = 11.
-    # SORTED: the supernova deposit is its own launches (plan + gather fused):
-    # key, run and long-run kernels per pass, no spread.  ROUNDED: a deposit
-    # and a rounding kernel per pass, no spread.
-    launches_per_step = {"atomic": 17, "sorted": 21, "rounded": 19}[args.mode]
+    # own kernels per step (the CUB sorts, scans and run encoding are library
+    # kernels).  ATOMIC: supernova pass zero, prologue, plan + gather +
+    # deposit, fold, apply (fast + queued) = 6; sink pass zero, prologue,
+    # per-cell records, plan + gather + deposit, spread, fold, eta + apply,
+    # Step-4 return = 8.  SORTED: plan + gather, keys, run and long-run
+    # kernels in place of the fused kernel (supernovae 9); sinks plan, gather,
+    # keys, runs, long runs, no spread (11).  ROUNDED: a deposit and a
+    # rounding kernel per pass (8 + 10).
+    launches_per_step = {"atomic": 14, "sorted": 20, "rounded": 18}[args.mode]
     state0 = state.clone()
     sink0 = {k: sk[k].clone() for k in ("m", "px", "py", "pz")}
 
@@ -379,6 +407,8 @@ def run_ours(args, world, rank, local):
     dominant = max(step_ms_by_kernel, key=step_ms_by_kernel.get)
     roof = roofline(dominant, kernel_ms[dominant][1], pairs, box, n_fb, n_sk, hbm_peak, peak_src)
 
+    hbm_passes = cell_pass_hbm(kernel_ms, box, hbm_peak)
+
     result = {
         "metric": METRIC,
         "value": n_particles * world / (ms_per_step * 1e-3),
@@ -406,6 +436,7 @@ def run_ours(args, world, rank, local):
         "kernels_ms_per_launch": {k: round(v[1], 4) for k, v in sorted(kernel_ms.items())},
         "limiter": {"fb_cells_eta_lt_1": lim_fb[0], "fb_noroot": lim_fb[1], "sink_cells_eta_lt_1": lim_sk[0]},
         "roofline": roof,
+        "hbm_passes": hbm_passes,
         "e2e": e2e,
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clk,

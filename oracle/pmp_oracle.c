@@ -276,14 +276,18 @@ static double cell_volume(double dx) { return (dx * dx) * dx; }
 
 /* Ideal-gas sound speed squared c_s^2 = gamma (gamma - 1) e_int / rho with
  * e_int = E - |p|^2 / (2 rho) (clamped at 0), and the Truelove density
- * rho_Tr = J^2 pi c_s^2 / (G dx^2) (Eq. truelove). */
+ * rho_Tr = J^2 pi c_s^2 / (G dx^2) (Eq. truelove).  Reading (evaluation):
+ * every quotient by rho in the sink formulas of Sec. 3.1.1 is a product with
+ * the cell's one reciprocal inv = 1/rho, so e_int = E - |p|^2 (inv/2) and
+ * c_s^2 = (gamma (gamma - 1) e_int) inv. */
 static void sink_cell(const or_params *P, double dx, const double U[NF], double *cs, double *rho_tr)
 {
+    double inv = 1.0 / U[0];
     double ke2 = (U[1] * U[1] + U[2] * U[2]) + U[3] * U[3];
-    double eint = U[4] - ke2 / (2.0 * U[0]);
+    double eint = U[4] - ke2 * (0.5 * inv);
     if (eint < 0.0) eint = 0.0;
     double gg = P->gamma * (P->gamma - 1.0);
-    double cs2 = (gg * eint) / U[0];
+    double cs2 = (gg * eint) * inv;
     double ctr = ((P->J * P->J) * OR_PI) / (P->G * (dx * dx));
     *cs = sqrt(cs2);
     *rho_tr = ctr * cs2;
@@ -521,7 +525,8 @@ static void feedback_delta(double w, const double U[NF], const double *G, int64_
 /* Eq. accretion_function with the Truelove rate folded into the max:
  * removal a = max(mdot_BH phi dt / V, rho - rho_Tr), written as
  * max(K w, rho - rho_Tr) with K = mdot_BH dt / V / sum w, and
- * Delta U = -a (1, v, e_sp + v^2/2) = -a (1, p/rho, E/rho). */
+ * Delta U = -a (1, v, e_sp + v^2/2) = -a (1, p/rho, E/rho), each quotient a
+ * product with inv = 1/rho (reading above). */
 static void sink_delta(const or_params *P, double dx, const double U[NF], const double *G, int64_t stride,
                        const kcell *c, double dU[NF])
 {
@@ -532,9 +537,10 @@ static void sink_delta(const or_params *P, double dx, const double U[NF], const 
     double bh = K * w;
     double tr = U[0] - rtr;
     double a = bh >= tr ? bh : tr;
+    double inv = 1.0 / U[0];
     dU[0] = -a;
-    for (int k = 0; k < 3; k++) dU[1 + k] = -(a * (U[1 + k] / U[0]));
-    dU[4] = -(a * (U[4] / U[0]));
+    for (int k = 0; k < 3; k++) dU[1 + k] = -(a * (U[1 + k] * inv));
+    dU[4] = -(a * (U[4] * inv));
 }
 
 /* Particle-mesh deposit: Delta U_c = omega q (every row). */
@@ -785,12 +791,14 @@ static double sink_eta(const or_params *P, double dx, const double U[NF], const 
 
 /* One cell's terms of the Step-4 sums: with a = -Delta U_rho (the removal of
  * Eq. accretion_function) and b = eta a, the mass sum takes -b and the
- * momentum sums take -b v with v = p / rho, fused (Reading (evaluation)). */
+ * momentum sums take -b v with v = p inv, inv = 1/rho, fused (Reading
+ * (evaluation)). */
 static void return_add(double eta, const double U[NF], const double dU[NF], double acc[4])
 {
     double b = eta * (-dU[0]);
+    double inv = 1.0 / U[0];
     acc[0] = acc[0] - b;
-    for (int k = 0; k < 3; k++) acc[1 + k] = fma(-b, U[1 + k] / U[0], acc[1 + k]);
+    for (int k = 0; k < 3; k++) acc[1 + k] = fma(-b, U[1 + k] * inv, acc[1 + k]);
 }
 
 /* u_s := u_s - sum_c eta_c Delta U^s_c V, with Delta U^s recomputed exactly as

@@ -123,7 +123,7 @@ long long max_pairs_per_particle(double rK)
 }
 
 struct Layout {
-    size_t keys, ids, keys2, ids2, counts, slots, hosts, fr, wts, aux, eta, queue, qcount, offsets, skeys, skeys2,
+    size_t keys, ids, keys2, ids2, counts, slots, hosts, fr, wts, aux, queue, qcount, offsets, skeys, skeys2,
         svals, svals2, soffs, slong, scnt;
     size_t temp, temp_bytes, total;
     long long cap, aux_stride;
@@ -160,7 +160,6 @@ Layout layout(const pmp_params &p, long long n, long long nvalid, int mode)
     if (sink) {
         L.wts = take(8 * n1 * 3 * (size_t)W);
         L.aux = take(8 * 2 * (size_t)pmp::kRec * (size_t)(nvalid > 0 ? nvalid : 1));
-        L.eta = take(8 * (size_t)(nvalid > 0 ? nvalid : 1));
     } else {
         L.queue = take(4 * (size_t)(nvalid > 0 ? nvalid : 1));
         L.qcount = take(8);
@@ -212,7 +211,6 @@ pmp::PlanPtrs plan_ptrs(const Layout &L, void *ws, const pmp_params &p, int mode
         pl.wts = reinterpret_cast<double *>(w + L.wts);
         pl.grec = reinterpret_cast<double *>(w + L.aux);
         pl.drec = pl.grec + (size_t)pmp::kRec * (size_t)(nvalid_rows(L) > 0 ? nvalid_rows(L) : 1);
-        pl.eta = reinterpret_cast<double *>(w + L.eta);
     }
     pl.cap = (unsigned long long)L.cap;
     return pl;
@@ -265,6 +263,11 @@ KParams make_kparams(const pmp_params &p, double dx)
     k.ctr = p.kind == PMP_KIND_SINK ? ((p.J * p.J) * pmp::kPi) / (p.G * (dx * dx)) : 0.0;
     k.cap = p.cap;
     k.rho_min = p.rho_min;
+    // cap rounded down and rho_min rounded up to FP32 (the sink limiter's FP32 pre-test)
+    k.cap_lo = (float)p.cap;
+    if ((double)k.cap_lo > p.cap) k.cap_lo = std::nextafter(k.cap_lo, 0.0f);
+    k.rho_min_hi = (float)p.rho_min;
+    if ((double)k.rho_min_hi < p.rho_min) k.rho_min_hi = std::nextafter(k.rho_min_hi, 3.0e38f);
     k.A_sf = p.A_sf;
     k.A_p = p.A_p;
     k.mu_H = p.mu_H;
@@ -771,7 +774,6 @@ pmp_status pmp_apply_limited(pmp_ctx *ctx, pmp_mesh *state, const pmp_mesh *buff
     if (overlaps(state, buffer)) return PMP_ERR_ARG;
     const KParams P = make_kparams(ctx->p, state->dx);
     cudaStream_t st = ctx->stream;
-    const double *eta_in = nullptr;
     if (ctx->p.kind == PMP_KIND_SINK) {
         const long long n = particles ? particles->count : 0;
         const long long nv = nvalid_of(state);
@@ -781,20 +783,24 @@ pmp_status pmp_apply_limited(pmp_ctx *ctx, pmp_mesh *state, const pmp_mesh *buff
         s = check_plan(ctx, n, nv, workspace);
         if (s) return s;
         const pmp::PlanPtrs pl = plan_ptrs(L, workspace, ctx->p, ctx->plan_mode);
-        {
-            Timed tm(ctx, "eta");
-            pmp::launch_sink_eta(P, S, state->data, B, buffer->data, pl.drec, pl.eta, st);
-        }
+        Parts q{};
         if (n > 0) {
             if (!gathered) return PMP_ERR_ARG;
-            Parts q;
             s = make_parts(ctx, particles, &q);
             if (s) return s;
+        }
+        if (cudaMemsetAsync(&ctx->st->n_limited, 0, 2 * sizeof(unsigned long long), st) != cudaSuccess)
+            return PMP_ERR_CUDA;
+        {
+            // Steps 3 + 5; Step 4 reads only the records and the particles
+            Timed tm(ctx, "apply");
+            pmp::launch_sink_eta_apply(P, S, state->data, B, buffer->data, pl.drec, eta_out, ctx->st, st);
+        }
+        if (n > 0) {
             Timed tm(ctx, "return");
             pmp::launch_return_sinks(P, S, q, gathered, pl, ctx->st, st);
         }
-        eta_in = pl.eta;
-        if (last_launch()) return PMP_ERR_CUDA;
+        return last_launch();
     }
     if (cudaMemsetAsync(&ctx->st->n_limited, 0, 2 * sizeof(unsigned long long), st) != cudaSuccess)
         return PMP_ERR_CUDA;
@@ -820,7 +826,7 @@ pmp_status pmp_apply_limited(pmp_ctx *ctx, pmp_mesh *state, const pmp_mesh *buff
     }
     {
         Timed tm(ctx, "apply");
-        pmp::launch_apply(P, S, state->data, B, buffer->data, eta_in, eta_out, ctx->st, st);
+        pmp::launch_apply(P, S, state->data, B, buffer->data, eta_out, ctx->st, st);
     }
     return last_launch();
 }

@@ -296,7 +296,7 @@ __device__ void gather_particle(const BArgs &a, long long s, SmemT<R> &sm)
                     v4 = U[3];
                 } else {
                     double cs, rtr;
-                    sink_cell(P, U, cs, rtr);
+                    sink_cell(P, U, 1.0 / U[0], cs, rtr);
                     v0 = U[0];
                     v1 = U[1];
                     v2 = U[2];
@@ -465,11 +465,12 @@ __device__ void deposit_tile(const BArgs &a, const DepItem &it, SmemT<R> &sm)
                     const Owner o = owner_of(a.T, p, i, j, k);
                     load5(a.u, o.c, o.fs, U);
                     if (!FB) {
-                        tr = U[0] - sink_rho_tr(P, U);
-                        q1 = U[1] / U[0];
-                        q2 = U[2] / U[0];
-                        q3 = U[3] / U[0];
-                        q4 = U[4] / U[0];
+                        const double inv = 1.0 / U[0];
+                        tr = U[0] - P.ctr * sink_cs2(P, U, inv);
+                        q1 = U[1] * inv;
+                        q2 = U[2] * inv;
+                        q3 = U[3] * inv;
+                        q4 = U[4] * inv;
                     }
                     haveU = true;
                 }
@@ -602,11 +603,12 @@ __device__ void return_sink(const BArgs &a, long long s, SmemT<R> &sm)
             bool img;
             folded_at(a, o.q, o.i, o.j, o.k, D, img);
             const double eta = sink_eta(P, U, D);
-            // b = eta a and v = p / rho; lane 0 fuses -b v into the sums
+            // b = eta a and v = p inv; lane 0 fuses -b v into the sums
+            const double inv = 1.0 / U[0];
             v0 = eta * (-dU[0]);
-            v1 = U[1] / U[0];
-            v2 = U[2] / U[0];
-            v3 = U[3] / U[0];
+            v1 = U[1] * inv;
+            v2 = U[2] * inv;
+            v3 = U[3] * inv;
         }
         const unsigned mm = __ballot_sync(kFullMask, mem);
         red[lane][0] = v0;

@@ -55,6 +55,7 @@ struct KParams {
     int Slog;        // log2(S) when S is a power of two, else -1
     float fracf[8];  // frac[] rounded to FP32
     float band_lo, band_hi;  // r2 (1 -/+ 2^-14) rounded outward to FP32
+    float cap_lo, rho_min_hi;  // cap rounded down, rho_min rounded up to FP32
 };
 
 struct Parts {
@@ -194,25 +195,32 @@ __device__ __forceinline__ void load_cell(const double *__restrict__ u, const Bo
     for (int f = 0; f < NF; ++f) U[f] = __ldg(u + (long long)f * B.fs + c);
 }
 
+// Every quotient by rho in the sink formulas is a product with the one
+// reciprocal inv = 1/rho of the cell (a division costs the GB300 FP64 pipe
+// about six of its operations, a product one).
 // Ideal-gas c_s^2 = gamma (gamma - 1) e_int / rho, e_int = E - |p|^2 / (2 rho)
-// clamped at 0; c_s; and rho_Tr = J^2 pi c_s^2 / (G dx^2) (Eq. truelove).
-__device__ __forceinline__ void sink_cell(const KParams &P, const double U[NF], double &cs, double &rho_tr)
+// clamped at 0, evaluated as e_int = E - |p|^2 (inv/2) and c_s^2 =
+// (gamma (gamma - 1) e_int) inv; c_s; and rho_Tr = J^2 pi c_s^2 / (G dx^2)
+// (Eq. truelove).
+__device__ __forceinline__ double sink_cs2(const KParams &P, const double U[NF], double inv)
 {
     const double ke2 = (U[1] * U[1] + U[2] * U[2]) + U[3] * U[3];
-    double eint = U[4] - ke2 / (2.0 * U[0]);
+    double eint = U[4] - ke2 * (0.5 * inv);
     if (eint < 0.0) eint = 0.0;
-    const double cs2 = (P.gg * eint) / U[0];
+    return (P.gg * eint) * inv;
+}
+
+__device__ __forceinline__ void sink_cell(const KParams &P, const double U[NF], double inv, double &cs,
+                                          double &rho_tr)
+{
+    const double cs2 = sink_cs2(P, U, inv);
     cs = sqrt(cs2);
     rho_tr = P.ctr * cs2;
 }
 
 __device__ __forceinline__ double sink_rho_tr(const KParams &P, const double U[NF])
 {
-    const double ke2 = (U[1] * U[1] + U[2] * U[2]) + U[3] * U[3];
-    double eint = U[4] - ke2 / (2.0 * U[0]);
-    if (eint < 0.0) eint = 0.0;
-    const double cs2 = (P.gg * eint) / U[0];
-    return P.ctr * cs2;
+    return P.ctr * sink_cs2(P, U, 1.0 / U[0]);
 }
 
 // Accretion limiter of Sec. 3.1.1 composed with the density floor, on the
@@ -365,23 +373,24 @@ __device__ __forceinline__ void feedback_delta(double w, const double U[NF], dou
 }
 
 // Sink deposition function (Eq. accretion_function with the Truelove rate in
-// the max): a = max(K w, rho - rho_Tr), Delta U = -a (1, p/rho, E/rho).
+// the max): a = max(K w, rho - rho_Tr), Delta U = -a (1, p inv, E inv).
 __device__ __forceinline__ void sink_delta(const KParams &P, const double U[NF], double K, double w, double dU[NF])
 {
-    const double rtr = sink_rho_tr(P, U);
+    const double inv = 1.0 / U[0];
+    const double rtr = P.ctr * sink_cs2(P, U, inv);
     const double bh = K * w;
     const double tr = U[0] - rtr;
     const double a = bh >= tr ? bh : tr;
     dU[0] = -a;
-    dU[1] = -(a * (U[1] / U[0]));
-    dU[2] = -(a * (U[2] / U[0]));
-    dU[3] = -(a * (U[3] / U[0]));
-    dU[4] = -(a * (U[4] / U[0]));
+    dU[1] = -(a * (U[1] * inv));
+    dU[2] = -(a * (U[2] * inv));
+    dU[3] = -(a * (U[3] * inv));
+    dU[4] = -(a * (U[4] * inv));
 }
 
 // Per-cell sink records (valid cells, x fastest), 6 doubles = 48 bytes each:
 //   G record (gather):          rho, p_x, p_y, p_z, rho c_s, 0
-//   D record (deposit, Step 4): rho - rho_Tr, p_x/rho, p_y/rho, p_z/rho, E/rho, eta
+//   D record (deposit, Step 4): rho - rho_Tr, p_x inv, p_y inv, p_z inv, E inv, 0 (inv = 1/rho)
 constexpr int kRec = 6;
 
 // Gathered-row indices.

@@ -29,7 +29,6 @@ struct PlanPtrs {
     double *wts;                      // sink: [n][3][2R+1] per-axis Gaussian factors
     double *grec;                     // sink: [valid cells][6] G records
     double *drec;                     // sink: [valid cells][6] D records
-    double *eta;                      // sink: [valid cells]
     unsigned long long cap;           // slots per particle
 };
 
@@ -96,14 +95,18 @@ void launch_sink_spread(const Box &S, const Box &B, double *b, const double *scr
                         cudaStream_t stream);
 void launch_sink_aux(const KParams &P, const Box &S, const double *u, double *grec, double *drec,
                      cudaStream_t stream);
-void launch_sink_eta(const KParams &P, const Box &S, const double *u, const Box &B, const double *b, double *drec,
-                     double *eta, cudaStream_t stream);
+// Steps 3 + 5 for sinks: eta per valid cell (into the D records, for Step 4)
+// and U += eta Delta U^sum, in one pass.
+void launch_sink_eta_apply(const KParams &P, const Box &S, double *u, const Box &B, const double *b, double *drec,
+                           double *eta_out, DevStatus *st, cudaStream_t stream);
 void launch_apply_fb_fast(const Box &S, double *u, const Box &B, const double *b, double *eta_out, unsigned *queue,
                           unsigned long long *qcount, cudaStream_t stream);
 void launch_apply_fb_slow(const Box &S, double *u, const Box &B, const double *b, double *eta_out,
                           const unsigned *queue, const unsigned long long *qcount, DevStatus *st, cudaStream_t stream);
-void launch_apply(const KParams &P, const Box &S, double *u, const Box &B, const double *b, const double *eta_in,
-                  double *eta_out, DevStatus *st, cudaStream_t stream);
+// Steps 3 + 5 without a plan workspace: feedback (FP64 limiter per cell) or
+// the particle-mesh kind (eta = 1).
+void launch_apply(const KParams &P, const Box &S, double *u, const Box &B, const double *b, double *eta_out,
+                  DevStatus *st, cudaStream_t stream);
 
 // CUB primitives, in pmp_sort.cu
 size_t cub_temp_bytes(long long n, long long max_pairs, bool sorted);

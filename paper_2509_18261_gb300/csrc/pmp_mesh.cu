@@ -100,64 +100,145 @@ __device__ __forceinline__ bool sn_lambda_holds_f32(const double U[NF], const do
     return dr >= 0.0f && M > 1e-30f && M < 1e30f && f < -6.103515625e-05f * M;
 }
 
+// Valid cell v (x fastest) -> (i, j, k), in 32-bit arithmetic when the box
+// has fewer than 2^32 valid cells (a 64-bit division costs several times the
+// instructions of a 32-bit one).
+__device__ __forceinline__ void cell_of(const Box &S, long long v, long long nvalid, int &i, int &j, int &k)
+{
+    if (nvalid <= 0xffffffffLL) {
+        const unsigned w = (unsigned)v, n0 = (unsigned)S.n0, n1 = (unsigned)S.n1;
+        const unsigned r = w / n0;
+        i = (int)(w - r * n0);
+        const unsigned kk = r / n1;
+        j = (int)(r - kk * n1);
+        k = (int)kk;
+    } else {
+        i = (int)(v % S.n0);
+        const long long r = v / S.n0;
+        j = (int)(r % S.n1);
+        k = (int)(r / S.n1);
+    }
+}
+
+// Adds the block's total of `mine` to *ctr with one atomic.  Every thread of
+// the block calls it (it holds a barrier); `sh` has a slot per warp.  One
+// atomic per warp on a single counter serialises at its L2 slice: millions
+// of them at 512^3.
+__device__ __forceinline__ void block_add(unsigned long long *ctr, unsigned mine, unsigned *sh)
+{
+    const unsigned w = __reduce_add_sync(0xffffffffu, mine);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = w;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long t = 0;
+        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += sh[q];
+        if (t) atomicAdd(ctr, t);
+    }
+}
+
+// True when the three momentum changes are zero (+0 or -0), tested on the
+// bits so that the FP64 pipe is left to the arithmetic.
+__device__ __forceinline__ bool no_dp(const double D[NF])
+{
+    const unsigned long long m = (unsigned long long)__double_as_longlong(D[1]) |
+                                 (unsigned long long)__double_as_longlong(D[2]) |
+                                 (unsigned long long)__double_as_longlong(D[3]);
+    return (m << 1) == 0;
+}
+
+constexpr int kApplyThreads = 256;
+constexpr int kApplyChunk = 4;  // cells per thread between two queue reservations
+
 // Steps 3 + 5 for feedback, first pass: cells whose Eq. lambda constraint
 // holds at lambda = 1 by the FP32 pre-check (or that receive no momentum) are
-// updated here; the others are queued for the FP64 limiter.
-__global__ void __launch_bounds__(256) k_apply_fb_fast(Box S, double *__restrict__ u, Box B,
-                                                       const double *__restrict__ b, double *__restrict__ eta_out,
-                                                       unsigned *__restrict__ queue,
-                                                       unsigned long long *__restrict__ qcount)
+// updated here; the others are queued for the FP64 limiter.  A block takes
+// chunks of kApplyThreads x kApplyChunk cells (grid-stride) and reserves the
+// queue slots of a chunk's queued cells with one atomic.  The queue's order
+// does not matter: each queued cell is updated on its own.
+__global__ void __launch_bounds__(kApplyThreads, 4) k_apply_fb_fast(Box S, double *__restrict__ u, Box B,
+                                                                 const double *__restrict__ b,
+                                                                 double *__restrict__ eta_out,
+                                                                 unsigned *__restrict__ queue,
+                                                                 unsigned long long *__restrict__ qcount)
 {
+    __shared__ unsigned wofs[kApplyThreads / 32];
+    __shared__ unsigned long long qbase;
     const long long nvalid = (long long)S.n0 * S.n1 * S.n2;
-    const long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    bool slow = false;
-    if (v < nvalid) {
-        const int i = (int)(v % S.n0);
-        const long long r = v / S.n0;
-        const int j = (int)(r % S.n1), k = (int)(r / S.n1);
-        const long long cs = S.at(i, j, k), cb = B.at(i, j, k);
-        double U[NF], D[NF];
+    constexpr long long per = (long long)kApplyThreads * kApplyChunk;
+    const long long nchunks = (nvalid + per - 1) / per;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (long long ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
+        const long long c0 = ch * per + threadIdx.x;
+        unsigned mask = 0;
 #pragma unroll
-        for (int f = 0; f < NF; ++f) D[f] = __ldg(b + (long long)f * B.fs + cb);
-        if (all_zero(D)) {
-            if (eta_out) eta_out[v] = 1.0;
-        } else {
+        for (int c = 0; c < kApplyChunk; ++c) {
+            const long long v = c0 + (long long)c * kApplyThreads;
+            if (v >= nvalid) break;
+            int i, j, k;
+            cell_of(S, v, nvalid, i, j, k);
+            const long long cs = S.at(i, j, k), cb = B.at(i, j, k);
+            double U[NF], D[NF];
 #pragma unroll
-            for (int f = 0; f < NF; ++f) U[f] = u[(long long)f * S.fs + cs];
-            const bool nodp = D[1] == 0.0 && D[2] == 0.0 && D[3] == 0.0;
-            if (nodp || sn_lambda_holds_f32(U, D)) {
+            for (int f = 0; f < NF; ++f) {
+                D[f] = __ldg(b + (long long)f * B.fs + cb);
+                U[f] = u[(long long)f * S.fs + cs];
+            }
+            if (all_zero(D)) {
+                if (eta_out) eta_out[v] = 1.0;
+            } else if (no_dp(D) || sn_lambda_holds_f32(U, D)) {
                 if (eta_out) eta_out[v] = 1.0;
 #pragma unroll
                 for (int f = 0; f < NF; ++f) u[(long long)f * S.fs + cs] = U[f] + D[f];
             } else {
-                slow = true;
+                mask |= 1u << c;
             }
         }
-    }
-    const unsigned m = __ballot_sync(0xffffffffu, slow);
-    if (m) {
-        const int lane = threadIdx.x & 31;
-        unsigned long long base = 0;
-        if (lane == __ffs(m) - 1) base = atomicAdd(qcount, (unsigned long long)__popc(m));
-        base = __shfl_sync(0xffffffffu, base, __ffs(m) - 1);
-        if (slow) queue[base + __popc(m & ((1u << lane) - 1u))] = (unsigned)v;
+        // queue slots: warp prefix of the per-thread counts, warp offsets in
+        // shared memory, one atomic for the chunk
+        const unsigned cnt = __popc(mask);
+        unsigned incl = cnt;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const unsigned t = __shfl_up_sync(0xffffffffu, incl, d);
+            if (lane >= d) incl += t;
+        }
+        if (lane == 31) wofs[wid] = incl;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            unsigned tot = 0;
+            for (int q = 0; q < kApplyThreads / 32; ++q) {
+                const unsigned t = wofs[q];
+                wofs[q] = tot;
+                tot += t;
+            }
+            qbase = tot ? atomicAdd(qcount, (unsigned long long)tot) : 0ULL;
+        }
+        __syncthreads();
+        unsigned long long pos = qbase + wofs[wid] + (incl - cnt);
+#pragma unroll
+        for (int c = 0; c < kApplyChunk; ++c)
+            if ((mask >> c) & 1u) queue[pos++] = (unsigned)(c0 + (long long)c * kApplyThreads);
+        __syncthreads();  // wofs and qbase are rewritten by the next chunk
     }
 }
 
 // Second pass: the queued cells through the FP64 limiter of Eq. lambda.
-__global__ void __launch_bounds__(256) k_apply_fb_slow(Box S, double *__restrict__ u, Box B,
-                                                       const double *__restrict__ b, double *__restrict__ eta_out,
-                                                       const unsigned *__restrict__ queue,
-                                                       const unsigned long long *__restrict__ qcount, DevStatus *st)
+__global__ void __launch_bounds__(kApplyThreads) k_apply_fb_slow(Box S, double *__restrict__ u, Box B,
+                                                                 const double *__restrict__ b,
+                                                                 double *__restrict__ eta_out,
+                                                                 const unsigned *__restrict__ queue,
+                                                                 const unsigned long long *__restrict__ qcount,
+                                                                 DevStatus *st)
 {
+    __shared__ unsigned sh[kApplyThreads / 32];
+    const long long nvalid = (long long)S.n0 * S.n1 * S.n2;
     const unsigned long long n = *qcount;
     const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
-    unsigned long long nl = 0, nr = 0;
+    unsigned nl = 0, nr = 0;
     for (unsigned long long q = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += stride) {
         const long long v = queue[q];
-        const int i = (int)(v % S.n0);
-        const long long r = v / S.n0;
-        const int j = (int)(r % S.n1), k = (int)(r / S.n1);
+        int i, j, k;
+        cell_of(S, v, nvalid, i, j, k);
         const long long cs = S.at(i, j, k), cb = B.at(i, j, k);
         double U[NF], D[NF];
 #pragma unroll
@@ -176,22 +257,24 @@ __global__ void __launch_bounds__(256) k_apply_fb_slow(Box S, double *__restrict
         u[3 * S.fs + cs] = U[3] + l * D[3];
         u[4 * S.fs + cs] = U[4] + D[4];
     }
-    if (nl) atomicAdd(&st->n_limited, nl);
-    if (nr) atomicAdd(&st->n_noroot, nr);
+    block_add(&st->n_limited, nl, sh);
+    __syncthreads();
+    block_add(&st->n_noroot, nr, sh);
 }
 
 // Steps 3 + 5 for feedback in one pass (used without a workspace): eta =
 // (1, l, l, l, 1) from Eq. lambda in FP64 for every cell.
-__global__ void __launch_bounds__(256) k_apply_fb(Box S, double *__restrict__ u, Box B, const double *__restrict__ b,
-                                                  double *__restrict__ eta_out, DevStatus *st)
+__global__ void __launch_bounds__(kApplyThreads) k_apply_fb(Box S, double *__restrict__ u, Box B,
+                                                            const double *__restrict__ b,
+                                                            double *__restrict__ eta_out, DevStatus *st)
 {
+    __shared__ unsigned sh[kApplyThreads / 32];
     const long long nvalid = (long long)S.n0 * S.n1 * S.n2;
-    const long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    int lim = 0, nr = 0;
-    if (v < nvalid) {
-        const int i = (int)(v % S.n0);
-        const long long r = v / S.n0;
-        const int j = (int)(r % S.n1), k = (int)(r / S.n1);
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    unsigned nl = 0, nr = 0;
+    for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < nvalid; v += stride) {
+        int i, j, k;
+        cell_of(S, v, nvalid, i, j, k);
         const long long cs = S.at(i, j, k), cb = B.at(i, j, k);
         double U[NF], D[NF];
 #pragma unroll
@@ -199,8 +282,10 @@ __global__ void __launch_bounds__(256) k_apply_fb(Box S, double *__restrict__ u,
             U[f] = u[(long long)f * S.fs + cs];
             D[f] = __ldg(b + (long long)f * B.fs + cb);
         }
-        const double l = sn_lambda(U, D, nr);
-        lim = l < 1.0;
+        int noroot;
+        const double l = sn_lambda(U, D, noroot);
+        nl += l < 1.0;
+        nr += noroot;
         if (eta_out) eta_out[v] = l;
         if (!all_zero(D)) {
             u[cs] = U[0] + D[0];
@@ -210,16 +295,14 @@ __global__ void __launch_bounds__(256) k_apply_fb(Box S, double *__restrict__ u,
             u[4 * S.fs + cs] = U[4] + D[4];
         }
     }
-    const unsigned m1 = __ballot_sync(0xffffffffu, lim), m2 = __ballot_sync(0xffffffffu, nr);
-    if ((threadIdx.x & 31) == 0) {
-        if (m1) atomicAdd(&st->n_limited, (unsigned long long)__popc(m1));
-        if (m2) atomicAdd(&st->n_noroot, (unsigned long long)__popc(m2));
-    }
+    block_add(&st->n_limited, nl, sh);
+    __syncthreads();
+    block_add(&st->n_noroot, nr, sh);
 }
 
 // Per-cell sink records, each value in the order the sink formulas state it:
 // G = (rho, p, rho c_s) for the gather; D = (rho - rho_Tr (Eq. truelove),
-// p/rho, E/rho, eta) for the deposit and Step 4 (eta filled in later).
+// p inv, E inv, 0) with inv = 1/rho for the deposit and Step 4.
 __global__ void __launch_bounds__(256) k_sink_aux(KParams P, Box S, const double *__restrict__ u,
                                                   double *__restrict__ grec, double *__restrict__ drec)
 {
@@ -231,21 +314,22 @@ __global__ void __launch_bounds__(256) k_sink_aux(KParams P, Box S, const double
     const int j = (int)(r % S.n1), k = (int)(r / S.n1);
     double U[NF], cs, rtr;
     load_cell(u, S, S.at(i, j, k), U);
-    sink_cell(P, U, cs, rtr);
+    const double inv = 1.0 / U[0];
+    sink_cell(P, U, inv, cs, rtr);
     double2 *g = reinterpret_cast<double2 *>(grec + v * kRec);
     g[0] = make_double2(U[0], U[1]);
     g[1] = make_double2(U[2], U[3]);
     g[2] = make_double2(U[0] * cs, 0.0);
     double2 *d = reinterpret_cast<double2 *>(drec + v * kRec);
-    d[0] = make_double2(U[0] - rtr, U[1] / U[0]);
-    d[1] = make_double2(U[2] / U[0], U[3] / U[0]);
-    d[2] = make_double2(U[4] / U[0], 1.0);
+    d[0] = make_double2(U[0] - rtr, U[1] * inv);
+    d[1] = make_double2(U[2] * inv, U[3] * inv);
+    d[2] = make_double2(U[4] * inv, 0.0);
 }
 
 // Step 1 for sinks in the ATOMIC mode, second half.  Every pair's change is
-// Delta U = -a (1, p/rho, E/rho) with the factors of its cell (the owner, for
+// Delta U = -a (1, p inv, E inv) with the factors of its cell (the owner, for
 // a ghost image), so the deposit sums only s = sum(-a) per buffer cell into a
-// one-field scratch, and here the cell's buffer gains s (1, p/rho, E/rho)
+// one-field scratch, and here the cell's buffer gains s (1, p inv, E inv)
 // from its owner's D record (fused multiply-adds: this pass is bound by the
 // FP64 pipe, not by HBM, at five separate operations per cell).  In real
 // arithmetic this is the sum of the pairs' five-field changes; in FP64 it
@@ -277,65 +361,92 @@ __global__ void __launch_bounds__(256) k_sink_spread(Box S, Box B, double *__res
     }
 }
 
-// Step 3 for sinks: eta per valid cell from the pre-update density, the summed
-// removal and rho - rho_Tr (accretion limiter of Sec. 3.1.1 with the floor);
-// written to the eta array and to the cell's D record.
-__global__ void __launch_bounds__(256) k_sink_eta(KParams P, Box S, const double *__restrict__ u, Box B,
-                                                  const double *__restrict__ b, double *__restrict__ drec,
-                                                  double *__restrict__ eta)
+// FP32 pre-test of the sink limiter's fast case: true only when the FP64
+// tests a <= RN(cap rho) and a <= RN(rho - rho_min) both hold, for a > 0.
+// af and rf are a and rho truncated to FP32 (within 2^-23 below), cap is
+// rounded down and rho_min up, and the comparison carries a 2^-16 relative
+// margin on each side: up = af (1 + 2^-16) exceeds a, and t1 = (cap rho) (1 -
+// 2^-16), t2 = (rho - rho_min) (1 - 2^-16), each with at most three FP32
+// roundings, stay below the FP64 values.  An operand outside the FP32 normal
+// range gives NaN or a subnormal bound, and so false; t1 is kept below 1e30
+// so that no product overflows.  False means "undecided": the caller runs
+// the FP64 tests.
+__device__ __forceinline__ bool sink_eta_one_f32(const KParams &P, double rho, double d0)
 {
-    const long long nvalid = (long long)S.n0 * S.n1 * S.n2;
-    const long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (v >= nvalid) return;
-    const int i = (int)(v % S.n0);
-    const long long r = v / S.n0;
-    const int j = (int)(r % S.n1), k = (int)(r / S.n1);
-    const double rho = __ldg(u + S.at(i, j, k));
-    const double a = -__ldg(b + B.at(i, j, k));
-    double e = 1.0;
-    if (a > 0.0) {
-        const double capr = P.cap * rho;
-        const double fl = rho - P.rho_min;
-        if (!(a <= capr && a <= fl)) {
-            double al = a < capr ? a : capr;
-            const double t = drec[v * kRec];
-            al = al > t ? al : t;
-            al = al < fl ? al : fl;
-            if (al < 0.0) al = 0.0;
-            e = al < a ? al / a : 1.0;
-        }
-    }
-    eta[v] = e;
-    drec[v * kRec + 5] = e;
+    const float af = -f32_trunc(d0), rf = f32_trunc(rho);
+    const float up = af * 1.0000152587890625f;
+    const float t1 = (P.cap_lo * rf) * 0.9999847412109375f;
+    const float t2 = (rf - P.rho_min_hi) * 0.9999847412109375f;
+    return up < t1 && up < t2 && t1 < 1e30f;
 }
 
-// Steps 3 + 5 for sinks: U += eta Delta U^sum, one eta for all five fields.
-__global__ void __launch_bounds__(256) k_apply_sink(Box S, double *__restrict__ u, Box B,
-                                                    const double *__restrict__ b, const double *__restrict__ eta,
-                                                    double *__restrict__ eta_out, DevStatus *st)
+// Steps 3 + 5 for sinks in one pass over the valid cells:
+// - eta from the pre-update density, the summed removal a = -Delta rho^sum and
+//   rho - rho_Tr (the accretion limiter of Sec. 3.1.1 composed with the
+//   density floor), written to the cell's D record for Step 4;
+// - U += eta Delta U^sum, one eta for all five fields.
+// The GB300 FP64 pipe, not HBM, bounds this pass unless the common case
+// (eta = 1) is decided without it: a <= 0 from the bits of Delta rho^sum,
+// then the FP32 pre-test above; only undecided cells run the FP64 tests
+// (reading rho - rho_Tr from the D record only where those fail).  Every
+// decision is the FP64 one.  Step 4 reads only the records, the particles
+// and the plan, never the state, so it can follow this pass.  Limited cells
+// are counted per block.
+__global__ void __launch_bounds__(kApplyThreads, 4) k_sink_eta_apply(KParams P, Box S, double *__restrict__ u, Box B,
+                                                                     const double *__restrict__ b,
+                                                                     double *__restrict__ drec,
+                                                                     double *__restrict__ eta_out, DevStatus *st)
 {
+    __shared__ unsigned sh[kApplyThreads / 32];
     const long long nvalid = (long long)S.n0 * S.n1 * S.n2;
-    const long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    int lim = 0;
-    if (v < nvalid) {
-        const int i = (int)(v % S.n0);
-        const long long r = v / S.n0;
-        const int j = (int)(r % S.n1), k = (int)(r / S.n1);
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    unsigned nl = 0;
+    for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < nvalid; v += stride) {
+        int i, j, k;
+        cell_of(S, v, nvalid, i, j, k);
         const long long cs = S.at(i, j, k), cb = B.at(i, j, k);
-        const double e = __ldg(eta + v);
-        lim = e < 1.0;
+        double U[NF], D[NF];
+#pragma unroll
+        for (int f = 0; f < NF; ++f) {
+            D[f] = __ldg(b + (long long)f * B.fs + cb);
+            U[f] = u[(long long)f * S.fs + cs];
+        }
+        // a = -D[0] > 0 exactly when D[0] is negative: sign set, not -0, not NaN
+        const unsigned long long b0 = (unsigned long long)__double_as_longlong(D[0]);
+        const unsigned long long mag2 = b0 << 1;
+        const bool pos_a = (b0 >> 63) != 0 && mag2 != 0 && mag2 <= (0x7ff0000000000000ULL << 1);
+        double e = 1.0;
+        bool one = true, lim = false;
+        if (pos_a && !sink_eta_one_f32(P, U[0], D[0])) {
+            const double rho = U[0];
+            const double a = -D[0];
+            const double capr = P.cap * rho;
+            const double fl = rho - P.rho_min;
+            if (!(a <= capr && a <= fl)) {
+                double al = a < capr ? a : capr;
+                const double t = __ldg(drec + v * kRec);
+                al = al > t ? al : t;
+                al = al < fl ? al : fl;
+                if (al < 0.0) al = 0.0;
+                e = al < a ? al / a : 1.0;
+                one = e == 1.0;
+                lim = e < 1.0;
+            }
+        }
+        drec[v * kRec + 5] = e;
         if (eta_out) eta_out[v] = e;
-        double D[NF];
-#pragma unroll
-        for (int f = 0; f < NF; ++f) D[f] = __ldg(b + (long long)f * B.fs + cb);
+        nl += lim;
         if (!all_zero(D)) {
+            if (one) {
 #pragma unroll
-            for (int f = 0; f < NF; ++f)
-                u[(long long)f * S.fs + cs] = u[(long long)f * S.fs + cs] + (e == 1.0 ? D[f] : e * D[f]);
+                for (int f = 0; f < NF; ++f) u[(long long)f * S.fs + cs] = U[f] + D[f];
+            } else {
+#pragma unroll
+                for (int f = 0; f < NF; ++f) u[(long long)f * S.fs + cs] = U[f] + e * D[f];
+            }
         }
     }
-    const unsigned m1 = __ballot_sync(0xffffffffu, lim);
-    if ((threadIdx.x & 31) == 0 && m1) atomicAdd(&st->n_limited, (unsigned long long)__popc(m1));
+    block_add(&st->n_limited, nl, sh);
 }
 
 // Adjoint of the limited apply: pass[c] = 1 where the supernova limiter left
@@ -567,24 +678,44 @@ void launch_sink_spread(const Box &S, const Box &B, double *b, const double *scr
     if (grid > 0) k_sink_spread<<<(unsigned)grid, 256, 0, stream>>>(S, B, b, scr, drec);
 }
 
-void launch_sink_eta(const KParams &P, const Box &S, const double *u, const Box &B, const double *b, double *drec,
-                     double *eta, cudaStream_t stream)
+// Resident grid of a grid-stride cell kernel: SMs x resident blocks, capped
+// by the blocks the work needs.
+template <typename K>
+static unsigned resident_grid(K kernel, int threads, long long need)
+{
+    int dev = 0, nsm = 152, per_sm = 1;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, 0) != cudaSuccess || per_sm < 1)
+        per_sm = 1;
+    const long long cap = (long long)nsm * per_sm;
+    const long long g = need < cap ? need : cap;
+    return (unsigned)(g > 0 ? g : 1);
+}
+
+void launch_sink_eta_apply(const KParams &P, const Box &S, double *u, const Box &B, const double *b, double *drec,
+                           double *eta_out, DevStatus *st, cudaStream_t stream)
 {
     const long long nvalid = (long long)S.n0 * S.n1 * S.n2;
-    k_sink_eta<<<(unsigned)((nvalid + 255) / 256), 256, 0, stream>>>(P, S, u, B, b, drec, eta);
+    if (nvalid == 0) return;
+    const unsigned grid = resident_grid(k_sink_eta_apply, kApplyThreads, (nvalid + kApplyThreads - 1) / kApplyThreads);
+    k_sink_eta_apply<<<grid, kApplyThreads, 0, stream>>>(P, S, u, B, b, drec, eta_out, st);
 }
 
 void launch_apply_fb_fast(const Box &S, double *u, const Box &B, const double *b, double *eta_out, unsigned *queue,
                           unsigned long long *qcount, cudaStream_t stream)
 {
     const long long nvalid = (long long)S.n0 * S.n1 * S.n2;
-    k_apply_fb_fast<<<(unsigned)((nvalid + 255) / 256), 256, 0, stream>>>(S, u, B, b, eta_out, queue, qcount);
+    if (nvalid == 0) return;
+    const long long per = (long long)kApplyThreads * kApplyChunk;
+    const unsigned grid = resident_grid(k_apply_fb_fast, kApplyThreads, (nvalid + per - 1) / per);
+    k_apply_fb_fast<<<grid, kApplyThreads, 0, stream>>>(S, u, B, b, eta_out, queue, qcount);
 }
 
 void launch_apply_fb_slow(const Box &S, double *u, const Box &B, const double *b, double *eta_out,
                           const unsigned *queue, const unsigned long long *qcount, DevStatus *st, cudaStream_t stream)
 {
-    k_apply_fb_slow<<<152 * 8, 256, 0, stream>>>(S, u, B, b, eta_out, queue, qcount, st);
+    const unsigned grid = resident_grid(k_apply_fb_slow, kApplyThreads, 1LL << 40);
+    k_apply_fb_slow<<<grid, kApplyThreads, 0, stream>>>(S, u, B, b, eta_out, queue, qcount, st);
 }
 
 // Step 5 of the particle-mesh deposit (no Step 3 in Sec. 2.2's PM/PIC subset):
@@ -608,14 +739,17 @@ __global__ void __launch_bounds__(256) k_apply_add(Box S, double *__restrict__ u
     for (int f = 0; f < NF; ++f) u[(long long)f * S.fs + cs] = u[(long long)f * S.fs + cs] + D[f];
 }
 
-void launch_apply(const KParams &P, const Box &S, double *u, const Box &B, const double *b, const double *eta_in,
-                  double *eta_out, DevStatus *st, cudaStream_t stream)
+void launch_apply(const KParams &P, const Box &S, double *u, const Box &B, const double *b, double *eta_out,
+                  DevStatus *st, cudaStream_t stream)
 {
     const long long nvalid = (long long)S.n0 * S.n1 * S.n2;
-    const unsigned nb = (unsigned)((nvalid + 255) / 256);
-    if (P.kind == PMP_KIND_MASS) k_apply_add<<<nb, 256, 0, stream>>>(S, u, B, b, eta_out);
-    else if (P.kind == PMP_KIND_FEEDBACK) k_apply_fb<<<nb, 256, 0, stream>>>(S, u, B, b, eta_out, st);
-    else k_apply_sink<<<nb, 256, 0, stream>>>(S, u, B, b, eta_in, eta_out, st);
+    if (nvalid == 0) return;
+    if (P.kind == PMP_KIND_MASS) {
+        k_apply_add<<<(unsigned)((nvalid + 255) / 256), 256, 0, stream>>>(S, u, B, b, eta_out);
+    } else {
+        const unsigned grid = resident_grid(k_apply_fb, kApplyThreads, (nvalid + kApplyThreads - 1) / kApplyThreads);
+        k_apply_fb<<<grid, kApplyThreads, 0, stream>>>(S, u, B, b, eta_out, st);
+    }
 }
 
 }  // namespace pmp

@@ -857,11 +857,11 @@ __device__ __forceinline__ void fb_pair_delta(const KParams &P, const Box &S, co
                    d2, dd, dU);
 }
 
-// Sink deposition value of one pair; also returns the cell's eta (D record).
+// Sink deposition value of one pair.
 template <int R>
 __device__ __forceinline__ void sink_pair_delta(const KParams &P, const Box &S, const Parts &p,
                                                 const double *__restrict__ G, const PlanPtrs &pl, long long s,
-                                                const PairCell &c, double dU[NF], double &eta)
+                                                const PairCell &c, double dU[NF])
 {
     constexpr int W = 2 * R + 1;
     int hx, hy, hz;
@@ -879,7 +879,6 @@ __device__ __forceinline__ void sink_pair_delta(const KParams &P, const Box &S, 
     dU[2] = -(a * d1.x);
     dU[3] = -(a * d1.y);
     dU[4] = -(a * d2.x);
-    eta = d2.y;
 }
 
 // Blocks per SM of the fused sink kernel (0: an L2 window of sinks in
@@ -1222,8 +1221,7 @@ __device__ __forceinline__ void sorted_pair_delta(const KParams &P, const Box &S
     if (FB) {
         fb_pair_delta(P, S, u, p, G, s, c, wtab, dU);
     } else {
-        double e;
-        sink_pair_delta<R>(P, S, p, G, pl, s, c, dU, e);
+        sink_pair_delta<R>(P, S, p, G, pl, s, c, dU);
     }
 }
 
