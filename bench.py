@@ -428,7 +428,7 @@ def run_ours(args, world, rank, local):
                          f"{n_fb} supernova particles (r_K=2, S=4) + {n_sk} sinks (r_K=4), "
                          "25% in 256 Plummer clusters (a=2 cells); supernova pass then sink pass"),
             "mode": args.mode,
-            "l2": "inputs larger than L2 (state + buffer 11.2 GB)",
+            "l2": f"inputs larger than L2 (state + buffer {2 * 8 * 5 * box.ncells_padded / 1e9:.1f} GB)",
             "parallelism": f"replicas x{world}",
             "kernel_pairs": pairs,
         },
