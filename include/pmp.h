@@ -441,6 +441,16 @@ pmp_status pmp_cycle_batched(pmp_batch *batch, double *state, double *buffer, pm
  * deposit, apply items) of the batch's current plan. */
 pmp_status pmp_batch_info(const pmp_batch *batch, int32_t *grid, int64_t *items);
 
+/* Fault injection for tests (no paper counterpart): the grid barriers of the
+ * persistent launch (PMP_LAUNCH_PERSISTENT and PMP_LAUNCH_GRAPH) wait for
+ * `arrivals` more blocks than the grid has, which never arrive.  Each wait is
+ * bounded in time, so the pass ends after about 4 s: the waiting blocks set
+ * PMP_ERR_TIMEOUT (first index -1, read with pmp_get_error) and the abort
+ * word, every block returns, and the context stays usable.  0, the default,
+ * restores normal operation.  arrivals must be 0 or 1 (else PMP_ERR_ARG).
+ * Synchronises the context's stream; drops a captured graph. */
+pmp_status pmp_batch_hold_barriers(pmp_batch *batch, int32_t arrivals);
+
 /* Frees a batch's device tables (after its work has finished). */
 void pmp_batch_destroy(pmp_batch *batch);
 

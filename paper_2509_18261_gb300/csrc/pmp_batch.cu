@@ -98,6 +98,7 @@ struct BArgs {
     const ZeroItem *zero;
     Ctl *ctl;
     DevStatus *st;
+    unsigned hold;  // arrivals a grid barrier waits for beyond the grid (0; 1 only to test the timeout)
 };
 
 // ---------------------------------------------------------------------------
@@ -730,7 +731,7 @@ __device__ bool grid_sync(const BArgs &a, SmemT<R> &sm)
         const unsigned g0 = *gen;
         __threadfence();
         const unsigned arrived = atomicAdd(&a.ctl->count, 1u) + 1u;
-        if (arrived == gridDim.x) {
+        if (arrived == gridDim.x + a.hold) {
             atomicExch(&a.ctl->count, 0u);
             __threadfence();
             atomicAdd(&a.ctl->gen, 1u);
@@ -917,6 +918,7 @@ struct pmp_batch {
     cudaGraphExec_t graph;
     cudaStream_t cap_stream;
     const void *gkey[8];
+    unsigned hold;  // see pmp_batch_hold_barriers
 };
 
 namespace {
@@ -1083,6 +1085,7 @@ BArgs make_args(pmp_batch *b, double *state, double *buffer, const pmp_particles
     a.zero = b->zero;
     a.ctl = b->ctl;
     a.st = b->ctx->st;
+    a.hold = b->hold;
     return a;
 }
 
@@ -1528,6 +1531,18 @@ pmp_status pmp_cycle_batched(pmp_batch *b, double *state, double *buffer, pmp_pa
         if (e == cudaSuccess) e = cudaGraphLaunch(b->graph, st);
     }
     return e == cudaSuccess ? PMP_OK : PMP_ERR_CUDA;
+}
+
+pmp_status pmp_batch_hold_barriers(pmp_batch *b, int32_t arrivals)
+{
+    if (!b || arrivals < 0 || arrivals > 1) return PMP_ERR_ARG;
+    if (cudaStreamSynchronize(b->ctx->stream) != cudaSuccess) return PMP_ERR_CUDA;
+    b->hold = (unsigned)arrivals;
+    if (b->graph) {  // the captured launch holds the old arguments
+        cudaGraphExecDestroy(b->graph);
+        b->graph = nullptr;
+    }
+    return PMP_OK;
 }
 
 pmp_status pmp_batch_info(const pmp_batch *b, int32_t *grid, int64_t *items)

@@ -32,7 +32,7 @@ EXPORTS = [
     "pmp_limiter_counts", "pmp_timing_enable", "pmp_timing_read", "pmp_deposit_noalloc",
     "pmp_create_sinks_workspace_size", "pmp_create_sinks", "pmp_apply_extra",
     "pmp_batch_create", "pmp_batch_set_particles", "pmp_batch_set_strategy", "pmp_batch_strategies",
-    "pmp_batch_autotune", "pmp_cycle_batched", "pmp_batch_info", "pmp_batch_destroy",
+    "pmp_batch_autotune", "pmp_cycle_batched", "pmp_batch_info", "pmp_batch_hold_barriers", "pmp_batch_destroy",
 ]
 PERSISTENT, PER_PATCH, GRAPH = 0, 1, 2
 LAUNCHES = {"persistent": PERSISTENT, "per_patch": PER_PATCH, "graph": GRAPH}
@@ -125,6 +125,7 @@ def load():
         "pmp_batch_autotune": ([vp, vp, vp, Pa, vp, i32, i32, ctypes.POINTER(i32)], i32),
         "pmp_cycle_batched": ([vp, vp, vp, Pa, vp, vp, i32], i32),
         "pmp_batch_info": ([vp, ctypes.POINTER(i32), ctypes.POINTER(i64)], i32),
+        "pmp_batch_hold_barriers": ([vp, i32], i32),
         "pmp_batch_destroy": ([vp], None),
     }
     for name, (args, res) in sig.items():
@@ -434,6 +435,10 @@ def pmp_cycle_batched(batch, state, buffer, parts, gathered, eta_out=None, launc
     batch.ctx._sync_stream()
     _check("pmp_cycle_batched", load().pmp_cycle_batched(batch.h, _ptr(state), _ptr(buffer), ctypes.byref(pp),
                                                          _ptr(gathered), _ptr(eta_out), LAUNCHES.get(launch, launch)))
+
+
+def pmp_batch_hold_barriers(batch, arrivals):
+    _check("pmp_batch_hold_barriers", load().pmp_batch_hold_barriers(batch.h, int(arrivals)))
 
 
 def pmp_batch_info(batch):

@@ -10,7 +10,9 @@ batched pass, through the C ABI.
 - the autotuner's choice (deterministic) still gives the oracle's bits;
 - the uneven 512-patch workload (8x8x8 super-grid, edges 16..64, power-law
   counts): the mixed cycle, supernovae then sinks, bit-exact;
-- argument checks of pmp_batch_create / pmp_batch_set_particles.
+- argument checks of pmp_batch_create / pmp_batch_set_particles;
+- a grid barrier held on purpose (pmp_batch_hold_barriers): the bounded wait
+  ends the pass with PMP_ERR_TIMEOUT, and the context stays usable.
 """
 import numpy as np
 import pytest
@@ -203,3 +205,38 @@ def test_c3_uneven_512_patches_mixed_cycle_bit_exact(orc):
         assert_bits_equal(ps[k].cpu().numpy(), sk_parts[k], f"sink {k}")
     fb.close()
     sk.close()
+
+
+def test_barrier_timeout_is_reported_and_the_context_recovers(orc):
+    """Failure detection without a GPU fault: pmp_batch_hold_barriers makes the
+    persistent launch's grid barriers wait for one block that never arrives.
+    Every wait gives up after its time limit, the pass reports
+    PMP_ERR_TIMEOUT (first index -1) and returns; with the hold released, the
+    next pass on the same context gives the oracle's bits."""
+    import torch
+
+    from paper_2509_18261_gb300 import pmp
+
+    batch, state, parts_np, first, params = _small("feedback")
+    ref = _oracle(orc, params, batch, state, parts_np, first)
+    st = torch.from_numpy(state.copy()).cuda()
+    parts = pmp.parts_to_device(parts_np)
+    bp = pmp.BatchPass(params, batch, st, parts, first, want_eta=True)
+    try:
+        pmp.pmp_batch_hold_barriers(bp.h, 1)
+        bp.run("persistent")
+        assert pmp.pmp_get_error(bp.ctx) == (5, -1)  # PMP_ERR_TIMEOUT
+        with pytest.raises(pmp.PMPError):
+            pmp.pmp_batch_hold_barriers(bp.h, 2)
+        pmp.pmp_batch_hold_barriers(bp.h, 0)
+        st.copy_(torch.from_numpy(state))
+        for k, v in parts_np.items():
+            parts[k].copy_(torch.from_numpy(v))
+        bp.run("persistent")
+        torch.cuda.synchronize()
+        got = dict(state=st.cpu().numpy(), buf=bp.buffer.cpu().numpy(), eta=bp.eta.cpu().numpy(),
+                   gathered=bp.gathered_view().cpu().numpy(), parts={k: v.cpu().numpy() for k, v in parts.items()},
+                   error=pmp.pmp_get_error(bp.ctx), counts=pmp.pmp_limiter_counts(bp.ctx))
+        _assert_same(got, ref, "feedback", "after the timeout")
+    finally:
+        bp.close()
