@@ -29,12 +29,17 @@
  * product that is added to a running sum or to another term is fused with
  * that addition where the code says fma(): the gather sums of Sec. 3.2.1 and
  * the sum of kernel weights of Eq. kernel_wgt, the momentum and energy rows of
- * Eq. du, and the Step-4 sums of Sec. 2.2.  Everything else is rounded
- * operation by operation.
+ * Eq. du, and the Step-4 sums of Sec. 2.2.  Every quotient by rho in the sink
+ * formulas of Sec. 3.1.1 (the Delta U rows, v in Step 4, c_s^2) is a product
+ * with the cell's one reciprocal 1/rho; the auxiliary fields and sink
+ * creation keep their divisions.  Everything else is rounded operation by
+ * operation.
  *
- * Readings of points the paper leaves open are marked "Reading:".  Parity of
- * the sub-sampled covered fraction omega and of the code-unit constants A_sf,
- * A_p is pinned only by self-consistency tests (no printed values exist).
+ * Readings of points the paper leaves open are marked "Reading:".
+ * Parity unpinned: the sub-sampled covered fraction omega and the code-unit
+ * constants A_sf, A_p have no values printed in the paper; the tests check
+ * them only by self-consistency (symmetry, convergence, conservation, the
+ * 0.46 E_sn calibration).
  */
 #include <math.h>
 #include <stdint.h>
