@@ -25,7 +25,11 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "pmp_oracle.c")
-_LIB = os.path.join(_HERE, "_build", "liboracle.so")
+# PMP_ORACLE_LIB names a prebuilt oracle library to load instead of building
+# this one: the pin-strength test (tests/test_oracle_mutants.py) builds copies
+# of the oracle with planted mistakes and runs the pins against each.
+_PREBUILT = os.environ.get("PMP_ORACLE_LIB")
+_LIB = _PREBUILT or os.path.join(_HERE, "_build", "liboracle.so")
 
 KIND = {"feedback": 0, "sink": 1, "mass": 2}
 FB_ROWS = ["M_snr", "V_snr", "vcom_x", "vcom_y", "vcom_z", "n_H", "R_M", "p_rad", "q", "e", "Pv", "regime"]
@@ -40,6 +44,8 @@ class OracleError(RuntimeError):
 
 def build(force=False):
     """Compile the oracle (no fused multiply-add, no fast-math)."""
+    if _PREBUILT:
+        return _LIB
     os.makedirs(os.path.dirname(_LIB), exist_ok=True)
     if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC):
         return _LIB

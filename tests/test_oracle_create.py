@@ -9,7 +9,8 @@
 - the cell keeps its velocity and specific energy, and the sink moves with
   the cell (Sec. 3.1.2);
 - two peaks closer than r_K make one sink (the higher), two peaks farther
-  apart make two, and a peak inside an accretion kernel makes none.
+  apart make two, two equal peaks closer than r_K make none (neither is a
+  strict maximum), and a peak inside an accretion kernel makes none.
 """
 import math
 
@@ -131,3 +132,10 @@ def test_peaks_and_kernels():
     cnt, new = oracle.create_sinks(params, box, st.copy(), buf)
     cells = set(zip(new["x"] - 0.5, new["y"] - 0.5, new["z"] - 0.5))
     assert (4.0, 4.0, 4.0) not in cells and (12.0, 4.0, 4.0) in cells
+    # two equal peaks 2 cells apart: neither is a strict local maximum, none
+    box, st = _state(1, n, peaks=[((4, 4, 4), 40.0), ((6, 4, 4), 40.0), ((12, 4, 4), 50.0)])
+    rho = box.valid(st)[0]
+    assert not _brute_local_max(rho, params["r_K"])[4, 4, 4]
+    cnt, new = oracle.create_sinks(params, box, st.copy(), box.empty(0.0))
+    cells = set(zip(new["x"] - 0.5, new["y"] - 0.5, new["z"] - 0.5))
+    assert (4.0, 4.0, 4.0) not in cells and (6.0, 4.0, 4.0) not in cells and (12.0, 4.0, 4.0) in cells

@@ -1,0 +1,146 @@
+"""Strength of the oracle's pins: planted mistakes must fail them.
+
+Each mutant below is the oracle with one plausible mistake planted in a copy
+of its source: a dropped term, a flipped sign, a transposed operand, a wrong
+index or bound, a wrong root.  The copy is compiled on the CPU and the
+oracle's pin tests run against it in a child process (PMP_ORACLE_LIB), with
+-x; a mutant passes this test only if some pin fails.  The oracle itself is
+never edited.  What each pin checks comes from the paper and the mathematics
+(closed forms, conservation, Fig. 1, brute force), so a mutant that survived
+would show a part of the oracle that only agrees with itself.
+"""
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = os.path.join(ROOT, "oracle", "pmp_oracle.c")
+PINS = ["tests/test_oracle_pins.py", "tests/test_oracle_create.py", "tests/test_oracle_extra.py",
+        "tests/test_oracle_mass.py", "tests/test_oracle_batch.py", "tests/test_oracle_repro.py"]
+
+# (name, the original text, its mutated form); the original occurs once.
+MUTANTS = [
+    ("accretion removes instead of adding to the buffer's density row",
+     "    dU[0] = -a;\n    for (int k = 0; k < 3; k++) dU[1 + k] = -(a * (U[1 + k] * inv));",
+     "    dU[0] = a;\n    for (int k = 0; k < 3; k++) dU[1 + k] = -(a * (U[1 + k] * inv));"),
+    ("internal energy without the kinetic term",
+     "double eint = U[4] - ke2 * (0.5 * inv);",
+     "double eint = U[4];"),
+    ("gamma (gamma - 1) written gamma - 1",
+     "double gg = P->gamma * (P->gamma - 1.0);",
+     "double gg = P->gamma - 1.0;"),
+    ("centre offset transposed (x_s - x_c)",
+     "static double centre_offset(int c, double x) { return ((double)c + 0.5) - x; }",
+     "static double centre_offset(int c, double x) { return x - ((double)c + 0.5); }"),
+    ("V_snr sums cells instead of covered fractions",
+     "        sw = sw + w;\n",
+     "        sw = sw + 1.0;\n"),
+    ("Bondi-Hoyle rate without lambda",
+     "sqrt(lam2 * cinf2 + vinf2)",
+     "sqrt(cinf2 + vinf2)"),
+    ("accretion limiter without the 25% cap",
+     "double al = a < P->cap * rho ? a : P->cap * rho;",
+     "double al = a;"),
+    ("Step 4 adds the removed mass to the sink with the wrong sign",
+     "    acc[0] = acc[0] - b;",
+     "    acc[0] = acc[0] + b;"),
+    ("ghost fold takes face images only",
+     "                            if (ox == 0 && oy == 0 && oz == 0) continue;\n"
+     "                            if ((ox && !B->periodic[0])",
+     "                            if ((ox != 0) + (oy != 0) + (oz != 0) != 1) continue;\n"
+     "                            if ((ox && !B->periodic[0])"),
+    ("momentum limiter takes the smaller root",
+     "    return hi < 1.0 ? hi : 1.0;",
+     "    if (lo > 0.0 && lo < 1.0) return lo;\n    return hi < 1.0 ? hi : 1.0;"),
+    ("ejecta kinetic energy dropped",
+     "G[FB_E * stride] = (Esn + Ekin) / Vsnr;",
+     "G[FB_E * stride] = Esn / Vsnr;"),
+    ("omega sub-points at the cell corner, not the mid-points",
+     "double sx = ((double)ci + ((double)a + 0.5) / (double)S) - x;",
+     "double sx = ((double)ci + ((double)a) / (double)S) - x;"),
+    ("kernel membership with <= instead of <",
+     "static int inside(double d2, double r2) { return d2 < r2; }",
+     "static int inside(double d2, double r2) { return d2 <= r2; }"),
+    ("momentum smoothing with rho instead of rho + q",
+     "    double rn = U[0] + q;",
+     "    double rn = U[0];"),
+    ("Truelove term with the sign of rho - rho_Tr flipped",
+     "    double tr = U[0] - rtr;\n    double a = bh >= tr ? bh : tr;\n    double inv",
+     "    double tr = rtr - U[0];\n    double a = bh >= tr ? bh : tr;\n    double inv"),
+    ("accretion energy row scaled by p_x instead of E",
+     "    dU[4] = -(a * (U[4] * inv));",
+     "    dU[4] = -(a * (U[1] * inv));"),
+    ("radial momentum scaled by |d| instead of divided",
+     "double s = c->d2 > 0.0 ? (w * Pv) / dist : 0.0;",
+     "double s = c->d2 > 0.0 ? (w * Pv) * dist : 0.0;"),
+    ("MC regime threshold compared with the wrong bound",
+     "else if (RM <= P->RM_st)",
+     "else if (RM <= P->RM_ej * 2.0)"),
+    ("density floor dropped from the accretion limiter",
+     "    double f = rho - P->rho_min;\n    al = al < f ? al : f;",
+     "    double f = rho;\n    al = al < f ? al : f;"),
+    ("sink gather mean density over one cell too many",
+     "    double rho_inf = srho / (double)nk;",
+     "    double rho_inf = srho / (double)(nk + 1);"),
+    ("exp with one Taylor term fewer",
+     "    double p = c[13];\n    for (int j = 12; j >= 0; j--) p = p * r + c[j];",
+     "    double p = c[12];\n    for (int j = 11; j >= 0; j--) p = p * r + c[j];"),
+    ("log without the low part of e ln2",
+     "return ed * LN2_HI - ((hf - (s * (hf + R) + ed * LN2_LO)) - f);",
+     "return ed * LN2_HI - ((hf - (s * (hf + R))) - f);"),
+    ("App. A.1 rounding without the margin M",
+     "        nbit = ceil_log2 + 52 + M;",
+     "        nbit = ceil_log2 + 52;"),
+    ("sink creation with a non-strict local maximum",
+     "                            if (!(U[0] > rho2)) ok = 0;          /* (b) */",
+     "                            if (!(U[0] >= rho2)) ok = 0;          /* (b) */"),
+    ("sink creation ignoring the retained accretion buffer",
+     "                if (!all_zero(D)) continue;                       /* (c) */",
+     "                (void)D;"),
+    ("particle-mesh deposit without omega",
+     "    for (int f = 0; f < NF; f++) dU[f] = w * G[(MS_Q + f) * stride];",
+     "    for (int f = 0; f < NF; f++) dU[f] = G[(MS_Q + f) * stride];"),
+    ("batched owner maps a low-side ghost with its own patch's size",
+     "w[a] = c[a] + (o[a] < 0 ? T->dims[3 * q + a] : 0) - (o[a] > 0 ? np_[a] : 0);",
+     "w[a] = c[a] + (o[a] < 0 ? np_[a] : 0) - (o[a] > 0 ? np_[a] : 0);"),
+]
+
+
+def _compile(tmp, i, text):
+    src = os.path.join(tmp, f"mutant_{i}.c")
+    lib = os.path.join(tmp, f"libmutant_{i}.so")
+    with open(src, "w") as f:
+        f.write(text)
+    subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math",
+                           "-fexcess-precision=standard", "-fPIC", "-shared", "-o", lib, src, "-lm"])
+    return lib
+
+
+def _pins_fail(lib):
+    env = dict(os.environ, PMP_ORACLE_LIB=lib)
+    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-m", "not gpu", "-p", "no:cacheprovider",
+                        *PINS], cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+    return r.returncode != 0, r.stdout[-400:]
+
+
+def test_mutants_are_well_formed():
+    src = open(SRC).read()
+    names = set()
+    for name, old, new in MUTANTS:
+        assert src.count(old) == 1, f"{name}: the original text must occur once"
+        assert old != new and name not in names
+        names.add(name)
+
+
+@pytest.mark.slow
+def test_every_planted_mistake_fails_a_pin(tmp_path):
+    src = open(SRC).read()
+    survivors = []
+    for i, (name, old, new) in enumerate(MUTANTS):
+        lib = _compile(str(tmp_path), i, src.replace(old, new))
+        failed, tail = _pins_fail(lib)
+        if not failed:
+            survivors.append(name)
+    assert not survivors, f"mistakes no pin catches: {survivors}"
