@@ -102,6 +102,35 @@ MUTANTS = [
     ("particle-mesh deposit without omega",
      "    for (int f = 0; f < NF; f++) dU[f] = w * G[(MS_Q + f) * stride];",
      "    for (int f = 0; f < NF; f++) dU[f] = G[(MS_Q + f) * stride];"),
+    ("v_COM adds gas momentum without the cell volume",
+     "vc[a] = (sp[a] * V + pe[a]) / Msnr;",
+     "vc[a] = (sp[a] + pe[a]) / Msnr;"),
+    ("M_sf with the exponent's sign flipped",
+     "double Msf = P->A_sf * or_pow(nH, -0.26);",
+     "double Msf = P->A_sf * or_pow(nH, 0.26);"),
+    ("P_snr with the exponent of M_sf",
+     "prad = P->A_p * or_pow(nH, -0.17);",
+     "prad = P->A_p * or_pow(nH, -0.26);"),
+    ("ST radial momentum without the factor 2",
+     "prad = sqrt(((2.0 * m) * P->eps_K) * Esn);",
+     "prad = sqrt((m * P->eps_K) * Esn);"),
+    ("accretion over the step without dt",
+     "double K = ((mdot * P->dt) / V) / sumw;",
+     "double K = (mdot / V) / sumw;"),
+    ("r_acc clamped at half a cell instead of a quarter",
+     "    if (racc < 0.25) racc = 0.25;",
+     "    if (racc < 0.5) racc = 0.5;"),
+    ("Step-4 momentum returned with the wrong sign",
+     "    for (int k = 0; k < 3; k++) acc[1 + k] = fma(-b, U[1 + k] * inv, acc[1 + k]);",
+     "    for (int k = 0; k < 3; k++) acc[1 + k] = fma(b, U[1 + k] * inv, acc[1 + k]);"),
+    ("Step 4 without the cell's eta",
+     "            double eta = sink_eta(P, S->dx, U, D);\n            return_add(eta, U, dU, acc);\n        }\n"
+     "        p->m[s] = p->m[s] - acc[0] * V;",
+     "            double eta = sink_eta(P, S->dx, U, D);\n            return_add(1.0, U, dU, acc);\n        }\n"
+     "        p->m[s] = p->m[s] - acc[0] * V;"),
+    ("App. A.1 ceil(log2 r) off by one at powers of two",
+     "        int ceil_log2 = (m == 0.5) ? k - 1 : k;",
+     "        int ceil_log2 = k;"),
     ("batched owner maps a low-side ghost with its own patch's size",
      "w[a] = c[a] + (o[a] < 0 ? T->dims[3 * q + a] : 0) - (o[a] > 0 ? np_[a] : 0);",
      "w[a] = c[a] + (o[a] < 0 ? np_[a] : 0) - (o[a] > 0 ? np_[a] : 0);"),

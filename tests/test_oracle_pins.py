@@ -145,8 +145,33 @@ def test_fig1_worked_example(orc):
 # Bondi / Bondi-Hoyle closed forms (Eq. rbh, Eq. mdot)
 # --------------------------------------------------------------------------
 
-@pytest.mark.parametrize("vel", [(0.0, 0.0, 0.0), (0.25, -0.5, 1.25)])
-def test_bondi_hoyle_closed_form(orc, vel):
+@pytest.mark.parametrize("Gm,r_acc", [(0.1, 0.25), (3.0, 2.0), (1.2, 1.2)])
+def test_accretion_kernel_shape(orc, Gm, r_acc):
+    """Gas at rest, one sink at rest, Bondi branch only: the removal per cell
+    follows the Gaussian of Eq. kernel, exp(-|x_c - x_s|^2 / r_acc^2), with
+    r_acc = r_BH = G m / c_s^2 kept between a quarter of a cell and r_K/2
+    (Sec. 3.1.1).  Ratios to the host cell, from cell centres computed here."""
+    params = syn.sink_params(r_K=4.0, gamma=2.0, G=0.01, dt=1e-9, rho_min=0.0)
+    box = syn.Box((16, 16, 16), 4)
+    state = syn.uniform_gas(box, 1.0, e_th=0.5)  # c_s = 1
+    xs = np.array([8.3, 7.6, 8.45])
+    sink = one(*xs, Gm / 0.01)
+    r = orc.cycle(params, box, state, sink)
+    assert r["counts"][0] == 0
+    drho = box.valid(r["buf"])[0]
+    k, j, i = np.nonzero(drho)
+    d2 = np.sum((np.stack([i + 0.5, j + 0.5, k + 0.5], axis=1) - xs) ** 2, axis=1)
+    assert np.all(d2 < 16.0)
+    h = np.argmin(d2)
+    want = np.exp(-(d2 - d2[h]) / (r_acc * r_acc))
+    got = drho[k, j, i] / drho[k[h], j[h], i[h]]
+    keep = want > 1e-250
+    assert keep.sum() > 6
+    assert np.allclose(got[keep], want[keep], rtol=1e-11, atol=0)
+
+
+@pytest.mark.parametrize("vel,dx", [((0.0, 0.0, 0.0), 1.0), ((0.25, -0.5, 1.25), 1.0), ((0.25, -0.5, 1.25), 0.5)])
+def test_bondi_hoyle_closed_form(orc, vel, dx):
     """Uniform gas (rho = 1, c_s = 1 exactly with gamma = 2 and e_th = 1/2)
     moving at vel past a sink at rest: the accreted mass over dt is the first
     line of Eq. mdot, 4 pi rho G^2 m^2 sqrt((lambda^2 c^2 + v^2)/(c^2 + v^2)^4)
@@ -158,14 +183,14 @@ def test_bondi_hoyle_closed_form(orc, vel):
     state = syn.uniform_gas(box, 1.0, vel=vel, e_th=0.5)
     sink = one(8.3, 7.6, 8.45, m)
     old = state.copy()
-    r = orc.cycle(params, box, state, sink)
+    r = orc.cycle(params, box, state, sink, dx=dx)
     assert r["counts"][0] == 0
     v2 = vel[0] ** 2 + vel[1] ** 2 + vel[2] ** 2
     lam = math.exp(1.5) / 4.0
     mdot = 4.0 * math.pi * 1.0 * G * G * m * m * math.sqrt((lam * lam + v2) / (1.0 + v2) ** 4)
     dm = sink["m"][0] - m
     assert dm == pytest.approx(mdot * dt, rel=1e-13)
-    dgas = math.fsum((box.valid(state)[0] - box.valid(old)[0]).ravel())
+    dgas = math.fsum((box.valid(state)[0] - box.valid(old)[0]).ravel()) * dx ** 3
     assert dgas == pytest.approx(-mdot * dt, rel=1e-10)
     # the sink keeps the momentum of the gas it swallowed (Eq. accretion_function row 2)
     for a in range(3):
@@ -185,22 +210,25 @@ def _fb_cloud(rng, box, count):
     return dict(x=x, y=y, z=z, m=m, px=m * v[0], py=m * v[1], pz=m * v[2], e=np.ones(count))
 
 
-def test_feedback_conservation_ej_regime(orc):
-    """EJ regime (|p_radial| = 0, Eq. dp): the summed buffer carries exactly the
-    ejecta mass, the ejecta momentum and E_sn + E_kin."""
+@pytest.mark.parametrize("dx", [1.0, 0.5])
+def test_feedback_conservation_ej_regime(orc, dx):
+    """EJ regime (|p_radial| = 0, Eq. dp): the summed buffer times the cell
+    volume V = dx^3 carries exactly the ejecta mass, the ejecta momentum and
+    E_sn + E_kin (Eq. conservation), for any cell size."""
     rng = np.random.default_rng(3)
     box = syn.Box((16, 16, 16), 2)
     state = syn.gas_state(rng, box)
     parts = _fb_cloud(rng, box, 40)
     params = syn.feedback_params(A_sf=1e9)
-    r = orc.cycle(params, box, state, parts)
+    r = orc.cycle(params, box, state, parts, dx=dx)
     assert np.all(r["gathered"][11] == 0.0)  # every particle in EJ
     D = box.valid(r["buf"]).reshape(5, -1)
-    assert math.fsum(D[0]) == pytest.approx(math.fsum(parts["m"]), rel=1e-13)
+    V = dx ** 3
+    assert math.fsum(D[0]) * V == pytest.approx(math.fsum(parts["m"]), rel=1e-13)
     for a, k in enumerate(("px", "py", "pz")):
-        assert math.fsum(D[1 + a]) == pytest.approx(math.fsum(parts[k]), rel=1e-12, abs=1e-15)
+        assert math.fsum(D[1 + a]) * V == pytest.approx(math.fsum(parts[k]), rel=1e-12, abs=1e-15)
     ekin = (parts["px"] ** 2 + parts["py"] ** 2 + parts["pz"] ** 2) / (2 * parts["m"])
-    assert math.fsum(D[4]) == pytest.approx(math.fsum(parts["e"] + ekin), rel=1e-13)
+    assert math.fsum(D[4]) * V == pytest.approx(math.fsum(parts["e"] + ekin), rel=1e-13)
 
 
 @pytest.mark.parametrize("regime_Asf", [(1, 100.0), (2, 1e-3)])
