@@ -17,6 +17,7 @@ import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 SRC = os.path.join(ROOT, "oracle", "pmp_oracle.c")
+DUAL = os.path.join(ROOT, "oracle", "dual.py")
 PINS = ["tests/test_oracle_pins.py", "tests/test_oracle_create.py", "tests/test_oracle_extra.py",
         "tests/test_oracle_mass.py", "tests/test_oracle_batch.py", "tests/test_oracle_repro.py"]
 
@@ -166,10 +167,74 @@ def test_mutants_are_well_formed():
 @pytest.mark.slow
 def test_every_planted_mistake_fails_a_pin(tmp_path):
     src = open(SRC).read()
+    # control: the unchanged source, built and run the same way, passes
+    failed, tail = _pins_fail(_compile(str(tmp_path), "control", src))
+    assert not failed, tail
     survivors = []
     for i, (name, old, new) in enumerate(MUTANTS):
         lib = _compile(str(tmp_path), i, src.replace(old, new))
         failed, tail = _pins_fail(lib)
         if not failed:
+            survivors.append(name)
+    assert not survivors, f"mistakes no pin catches: {survivors}"
+
+
+# The forward-mode restatement behind the adjoint tests (oracle/dual.py),
+# pinned by the C oracle's values and by central finite differences.
+DUAL_MUTANTS = [
+    ("quotient rule with the wrong sign",
+     "(self.t * o.v - self.v * o.t) / (o.v * o.v)",
+     "(self.t * o.v + self.v * o.t) / (o.v * o.v)"),
+    ("product rule with a dropped term",
+     "Dual(self.v * o.v, self.t * o.v + self.v * o.t)",
+     "Dual(self.v * o.v, self.t * o.v)"),
+    ("square-root derivative without the 2",
+     "a.t / (2.0 * r) if r > 0 else 0.0",
+     "a.t / r if r > 0 else 0.0"),
+    ("power derivative without the exponent",
+     "Dual(r, e * a.v ** (e - 1.0) * a.t)",
+     "Dual(r, a.v ** (e - 1.0) * a.t)"),
+    ("ST momentum without the ejecta energy's tangent",
+     "prad = dsqrt(2.0 * m * params[\"eps_K\"] * E)",
+     "prad = dsqrt(2.0 * m * params[\"eps_K\"] * E.v)"),
+    ("cell offset tangent dropped (positions carry no derivative)",
+     "d = [(float(cc) + 0.5) - xx for cc, xx in zip((i, j, k), xs)]",
+     "d = [(float(cc) + 0.5) - Dual(xx.v) for cc, xx in zip((i, j, k), xs)]"),
+]
+
+_DUAL_RUNNER = (
+    "import importlib.util, sys; sys.path.insert(0, {root!r});"
+    "import oracle;"
+    "spec = importlib.util.spec_from_file_location('oracle.dual', {path!r});"
+    "m = importlib.util.module_from_spec(spec); sys.modules['oracle.dual'] = m;"
+    "spec.loader.exec_module(m); oracle.dual = m;"
+    "import pytest; sys.exit(pytest.main(['-x', '-q', '-p', 'no:cacheprovider', 'tests/test_oracle_dual.py']))"
+)
+
+
+def test_dual_mutants_are_well_formed():
+    src = open(DUAL).read()
+    for name, old, new in DUAL_MUTANTS:
+        assert src.count(old) == 1, f"{name}: the original text must occur once"
+        assert old != new
+
+
+@pytest.mark.slow
+def test_every_planted_mistake_in_the_dual_oracle_fails_a_pin(tmp_path):
+    src = open(DUAL).read()
+
+    def run(i, text):
+        path = os.path.join(str(tmp_path), f"dual_mutant_{i}.py")
+        with open(path, "w") as f:
+            f.write(text)
+        return subprocess.run([sys.executable, "-c", _DUAL_RUNNER.format(root=ROOT, path=path)], cwd=ROOT,
+                              capture_output=True, text=True, timeout=600)
+
+    control = run("control", src)  # the unchanged module through the same runner passes
+    assert control.returncode == 0, control.stdout[-400:]
+    survivors = []
+    for i, (name, old, new) in enumerate(DUAL_MUTANTS):
+        r = run(i, src.replace(old, new))
+        if r.returncode == 0:
             survivors.append(name)
     assert not survivors, f"mistakes no pin catches: {survivors}"
