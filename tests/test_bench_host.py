@@ -1,0 +1,91 @@
+"""The bench's host-side arithmetic, on the CPU: the roofline object of the
+dominant kernel, the per-pass HBM figures and the clock record.  These are
+pure functions of timings, sizes and sampled text, so they are checked here
+with made-up inputs; the GPU only supplies the numbers."""
+import os
+import tempfile
+
+import pytest
+
+import bench
+from paper_2509_18261_gb300 import synthetic as syn
+
+
+def _box():
+    return syn.Box((512, 512, 512), 4)
+
+
+def test_alu_roofline_of_the_fused_supernova_kernel():
+    box = _box()
+    pairs = {"fb": 491_934_207, "sink": 562_210_341}
+    r = bench.roofline("fb_gather_deposit", 52.8, pairs, box, 14_680_064, 2_097_152, 6793.4, "measured")
+    flops = 38 * pairs["fb"]  # 9 (gather) + 29 (Eq. du) canonical FP64 operations per pair
+    assert r["bound"] == "alu" and r["unit"] == "TFLOP/s" and r["peak"] == bench.FP64_PEAK_TFLOPS
+    assert r["achieved"] == pytest.approx(flops / 52.8e-3 / 1e12, rel=1e-12)
+    assert r["frac"] == pytest.approx(r["achieved"] / r["peak"], rel=1e-12)
+    assert r["kernel"] == "fb_gather_deposit" and r["ms_per_launch"] == 52.8
+
+
+def test_hbm_roofline_of_the_sink_apply():
+    box = _box()
+    r = bench.roofline("sink_apply", 7.2, {"fb": 1, "sink": 1}, box, 1, 1, 6793.4, "measured")
+    assert r["bound"] == "hbm" and r["unit"] == "GB/s"
+    assert r["achieved"] == pytest.approx(128 * 512 ** 3 / 7.2e-3 / 1e9, rel=1e-12)
+    assert r["frac"] == pytest.approx(r["achieved"] / 6793.4, rel=1e-12)
+
+
+def test_traffic_is_reported_only_for_the_profiled_sources():
+    # the committed summary names the digest of the sources it was taken on
+    assert bench.profiled_traffic("fb_gather_deposit") is None or \
+        bench.profiled_traffic("fb_gather_deposit") > 1e10
+    assert bench.profiled_traffic("no_such_kernel") is None
+
+
+def test_cell_pass_hbm_sums_the_two_supernova_apply_kernels():
+    box = _box()
+    km = {"fb_apply": (1.0, 2.9), "fb_apply_fp64": (1.0, 6.3), "sink_apply": (1.0, 7.2), "fb_zero": (1.0, 0.86)}
+    out = bench.cell_pass_hbm(km, box, 6793.4)
+    assert out["fb_apply"]["ms"] == pytest.approx(9.2)
+    assert out["fb_apply"]["GB/s"] == pytest.approx(120 * 512 ** 3 / 9.2e-3 / 1e9, rel=1e-3)
+    assert out["sink_apply"]["bytes"] == 128 * 512 ** 3
+    assert out["fb_zero"]["bytes"] == 40 * box.ncells_padded
+    assert "sink_spread" not in out  # a pass that was not timed is left out
+
+
+class _Done:
+    def terminate(self):
+        pass
+
+    def wait(self, timeout=None):
+        return 0
+
+
+def _clocks_from(lines):
+    c = bench.Clocks(0)
+    fd, c.path = tempfile.mkstemp(suffix=".csv")
+    with os.fdopen(fd, "w") as f:
+        f.write("\n".join(lines) + "\n")
+    c.proc = _Done()
+    return c.stop()
+
+
+def test_clock_record_median_and_reasons():
+    rows = [
+        "0, 2070, 2070, 1100.5, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+        "0, 1980, 2070, 1390.2, 0x0000000000000004, Not Active, Not Active, Not Active, Active",
+        "0, 2070, 2070, 1200.0, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+    ]
+    r = _clocks_from(rows)
+    assert r["sm_mhz"] == 2070.0 and r["sm_max_mhz"] == 2070.0 and r["samples"] == 3
+    assert r["reasons"] == ["sw_power_cap"]
+
+
+def test_clock_record_flags_thermal_slowdown_and_skips_bad_rows():
+    rows = [
+        "0, 1500, 2070, 1400.0, 0x0000000000000040, Not Active, Active, Not Active, Not Active",
+        "0, [N/A], 2070, 1400.0, 0x0, Not Active, Not Active, Not Active, Not Active",
+        "garbage",
+    ]
+    r = _clocks_from(rows)
+    assert r["sm_mhz"] == 1500.0 and r["samples"] == 2
+    assert r["reasons"] == ["hw_thermal_slowdown"]
