@@ -253,7 +253,13 @@ pmp_status pmp_fold_ghosts(pmp_ctx *ctx, pmp_mesh *buffer);
  * eta_out: optional device array, one FP64 per valid cell (x fastest): the
  *   momentum eta (feedback) or the common eta (sink).
  * workspace: sinks need the one pmp_gather filled for this pass (its plan and
- *   per-cell quantities); feedback ignores it (may be NULL). */
+ *   per-cell quantities).  Feedback may pass NULL; with the workspace of this
+ *   pass's pmp_gather it queues the cells whose constraint an FP32 pre-test
+ *   cannot settle for the FP64 limiter (same results, fewer FP64 operations).
+ * Order of work (sinks): eta is computed and the state updated in one pass
+ *   over the cells, then Step 4 runs; Step 4 reads eta and the pre-update
+ *   per-cell quantities kept in the workspace, so the result is that of the
+ *   order the paper states (Step 4 before Step 5). */
 pmp_status pmp_apply_limited(pmp_ctx *ctx, pmp_mesh *state, const pmp_mesh *buffer, pmp_particles *particles,
                              const double *gathered, double *eta_out, void *workspace, size_t workspace_bytes);
 
