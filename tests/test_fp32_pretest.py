@@ -1,4 +1,7 @@
-"""Soundness of the sink limiter's FP32 pre-test (k_sink_eta_apply).
+"""Soundness of the limiters' FP32 pre-tests (k_sink_eta_apply and
+k_apply_fb_fast): whenever one decides eta = 1, the FP64 test agrees.
+
+Sink pre-test (accretion limiter of Sec. 3.1.1):
 
 The kernel decides the common case eta = 1 of the accretion limiter
 (Sec. 3.1.1) in FP32: a value truncated from FP64 to FP32, cap rounded down,
@@ -98,3 +101,60 @@ def test_pretest_takes_the_common_case():
     assert pretest(np.array([1.0]), np.array([-0.01]), F32(0.25), round_up_f32(1e-6))[0]
     # the Fig. 1 setting (cap 1, rho_min 0.2, a = 1) is left to FP64
     assert not pretest(np.array([1.0]), np.array([-1.0]), F32(1.0), round_up_f32(0.2))[0]
+
+
+# ---------------------------------------------------------------------------
+# the supernova apply's FP32 pre-check of Eq. lambda (k_apply_fb_fast)
+# ---------------------------------------------------------------------------
+
+def sn_pretest(U, D):
+    """The kernel's FP32 test that the constraint of Eq. lambda holds at
+    lambda = 1: f = e_int0 rho'/rho + |p + dp|^2/(2 rho') - E' < -2^-14 M,
+    on values truncated to FP32, with rho' >= rho and M in a safe range."""
+    with np.errstate(all="ignore"):
+        r, p0, p1, p2, E = (f32_trunc(U[i]) for i in range(5))
+        dr, d0, d1, d2, dE = (f32_trunc(D[i]) for i in range(5))
+        r1, E1 = r + dr, E + dE
+        pp = (p0 * p0 + p1 * p1) + p2 * p2
+        k0 = pp / (F32(2.0) * r)
+        q = r1 / r
+        n0, n1, n2 = p0 + d0, p1 + d1, p2 + d2
+        kn = ((n0 * n0 + n1 * n1) + n2 * n2) / (F32(2.0) * r1)
+        f = ((E - k0) * q + kn) - E1
+        M = (np.abs(E) + k0) * q + kn + np.abs(E1)
+        return (dr >= F32(0)) & (M > F32(1e-30)) & (M < F32(1e30)) & (f < F32(-6.103515625e-05) * M)
+
+
+def sn_holds_fp64(U, D):
+    """Eq. lambda's constraint at lambda = 1 in the FP64 order of the limiter."""
+    rho1 = U[0] + D[0]
+    E1 = U[4] + D[4]
+    p2 = (U[1] * U[1] + U[2] * U[2]) + U[3] * U[3]
+    eint0 = U[4] - p2 / (2.0 * U[0])
+    pn = [U[1] + D[1], U[2] + D[2], U[3] + D[3]]
+    pnn = (pn[0] * pn[0] + pn[1] * pn[1]) + pn[2] * pn[2]
+    therm = (eint0 * rho1) / U[0]
+    return therm + pnn / (2.0 * rho1) <= E1
+
+
+def test_supernova_pretest_never_accepts_what_fp64_rejects():
+    rng = np.random.default_rng(918261)
+    n = 300_000
+    rho = np.exp(rng.normal(-0.5, 2.0, n))
+    p = rng.normal(0, 0.5, (3, n)) * rho
+    eint = rho * np.exp(rng.normal(0.0, 2.0, n))
+    E = eint + (p * p).sum(0) / (2 * rho)
+    drho = rho * np.exp(rng.uniform(-12, 0, n))
+    dp = rng.normal(0, 1.0, (3, n)) * rho
+    U = np.stack([rho, p[0], p[1], p[2], E])
+    # energy deposit that puts the cell near the constraint's boundary
+    rho1 = rho + drho
+    pn = p + dp
+    need = eint * rho1 / rho + (pn * pn).sum(0) / (2 * rho1) - E
+    rel = rng.choice([-1.0, 1.0], n) * 2.0 ** -rng.uniform(3, 40, n)
+    dE = need * (1.0 + rel) + np.abs(need) * rel
+    D = np.stack([drho, dp[0], dp[1], dp[2], dE])
+    ok = sn_pretest(U, D)
+    exact = np.array([sn_holds_fp64(U[:, i], D[:, i]) for i in np.nonzero(ok)[0]])
+    assert exact.all(), "pre-check accepted a cell the FP64 test rejects"
+    assert ok.sum() > n // 10  # the fast case is taken often
