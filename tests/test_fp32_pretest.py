@@ -1,5 +1,8 @@
-"""Soundness of the limiters' FP32 pre-tests (k_sink_eta_apply and
-k_apply_fb_fast): whenever one decides eta = 1, the FP64 test agrees.
+"""Soundness of the FP32 decisions of the kernels: the limiters' pre-tests
+(k_sink_eta_apply and k_apply_fb_fast: whenever one decides eta = 1, the
+FP64 test agrees) and the plan's kernel-membership, full-cell and sub-point
+decisions (taken in FP32 outside a 2^-14 band around r_K^2, each equal to the
+FP64 decision of the canonical order).
 
 Sink pre-test (accretion limiter of Sec. 3.1.1):
 
@@ -12,7 +15,10 @@ round-to-nearest, like the GPU's FP32 pipe without contraction, so the
 pre-test restated here runs the same operations; the inputs crowd the two
 decision boundaries and the ends of the FP32 range.
 """
+import math
+
 import numpy as np
+import pytest
 
 F32 = np.float32
 
@@ -158,3 +164,87 @@ def test_supernova_pretest_never_accepts_what_fp64_rejects():
     exact = np.array([sn_holds_fp64(U[:, i], D[:, i]) for i in np.nonzero(ok)[0]])
     assert exact.all(), "pre-check accepted a cell the FP64 test rejects"
     assert ok.sum() > n // 10  # the fast case is taken often
+
+
+# ---------------------------------------------------------------------------
+# the plan's FP32 membership and sub-point decisions (plan_particle)
+# ---------------------------------------------------------------------------
+
+def _band(r2):
+    lo, hi = r2 * (1.0 - 2.0 ** -14), r2 * (1.0 + 2.0 ** -14)
+    blo, bhi = F32(lo), F32(hi)
+    if float(blo) > lo:
+        blo = np.nextafter(blo, F32(0))
+    if float(bhi) < hi:
+        bhi = np.nextafter(bhi, F32(3e38))
+    return blo, bhi
+
+
+def _plan_decisions(x, rK, S):
+    """For particles at x (n, 3), FP64: the kernel's FP32 decisions, restated
+    with the same operations: per-axis squares of ((o - R) - f) + 1/2 and of
+    ((o - R) - f) + (a + 1/2)/S, f = x - floor(x) rounded to FP32; a centre is
+    in when (sx + sy) + sz < band_lo, out when > band_hi; a sub-point is
+    summed as (sy + sz) + sx.  Returns the decisions with the FP64 truth for
+    every (particle, offset) and (particle, offset, sub-point)."""
+    R = int(math.ceil(rK))
+    W = 2 * R + 1
+    r2 = rK * rK
+    blo, bhi = _band(r2)
+    h = np.floor(x)
+    f = (x - h).astype(np.float32)                        # (n, 3)
+    o = (np.arange(W) - R).astype(np.float32)             # (W,)
+    e = (o[None, None, :] - f[:, :, None])                 # (n, 3, W), FP32
+    csq = (e + F32(0.5)) * (e + F32(0.5))
+    tf = (csq[:, 0, None, None, :] + csq[:, 1, None, :, None]) + csq[:, 2, :, None, None]  # (n, z, y, x)
+    # FP64 truth at the centres, in the canonical order
+    oo = np.arange(W) - R
+    d = (h[:, :, None] + oo[None, None, :] + 0.5) - x[:, :, None]    # (n, 3, W), FP64
+    d2 = (d[:, 0, None, None, :] ** 2 + d[:, 1, None, :, None] ** 2) + d[:, 2, :, None, None] ** 2
+    fr = np.array([(a + 0.5) / S for a in range(S)])
+    frf = fr.astype(np.float32)
+    u = e[:, :, :, None] + frf[None, None, None, :]        # (n, 3, W, S), FP32
+    sub = u * u
+    ds = (h[:, :, None, None] + oo[None, None, :, None] + fr[None, None, None, :]) - x[:, :, None, None]
+    return (tf, blo, bhi, d2, r2, sub, ds)
+
+
+@pytest.mark.parametrize("rK,S", [(2.0, 4), (4.0, 1), (2.5, 2), (3.0, 8)])
+def test_plan_fp32_decisions_equal_the_fp64_ones(rK, S):
+    rng = np.random.default_rng(int(rK * 10) + S)
+    n = 2000
+    R = int(math.ceil(rK))
+    # random particles, and particles placed so that one centre sits within
+    # 2^-30 .. 2^-10 (relative) of r_K
+    xr = rng.uniform(0, 64, (n, 3))
+    off = rng.integers(-R, R + 1, (n, 3)).astype(float)
+    dirs = rng.normal(size=(n, 3))
+    dirs /= np.linalg.norm(dirs, axis=1)[:, None]
+    rel = rng.choice([-1.0, 1.0], n) * 2.0 ** -rng.uniform(10, 30, n)
+    centre = 20.5 + off
+    xt = centre - dirs * (rK * (1.0 + rel))[:, None]
+    x = np.concatenate([xr, xt])
+    tf, blo, bhi, d2, r2, sub, ds = _plan_decisions(x, rK, S)
+    inside = d2 < r2
+    assert np.all(inside[tf < blo]), "FP32 'in' where FP64 says out"
+    assert not np.any(inside[tf > bhi]), "FP32 'out' where FP64 says in"
+    assert np.count_nonzero((tf >= blo) & (tf <= bhi)) > 0  # the band is exercised
+    # sub-points: (sy + sz) + sx against the band, on a subset (memory)
+    W = 2 * R + 1
+    m = max(64, int(2e7 // (W ** 3 * S ** 3)))
+    pick = np.concatenate([np.arange(min(m // 2, n)), n + np.arange(min(m // 2, n))])
+    sb, db = sub[pick], ds[pick]
+    v = (sb[:, 1][:, None, :, None, None, :, None] + sb[:, 2][:, :, None, None, :, None, None]) + \
+        sb[:, 0][:, None, None, :, None, None, :]
+    t64 = (db[:, 0][:, None, None, :, None, None, :] ** 2 + db[:, 1][:, None, :, None, None, :, None] ** 2) + \
+        db[:, 2][:, :, None, None, :, None, None] ** 2
+    sin = t64 < r2
+    assert np.all(sin[v < blo]), "FP32 sub-point 'in' where FP64 says out"
+    assert not np.any(sin[v > bhi]), "FP32 sub-point 'out' where FP64 says in"
+    # "full" cells (omega = 1 without counting): the per-axis larger of the
+    # first and last sub-point squares, summed, below band_lo
+    fc = np.maximum(sb[..., 0], sb[..., S - 1])          # (m, 3, W)
+    full = (fc[:, 0][:, None, None, :] + fc[:, 1][:, None, :, None]) + fc[:, 2][:, :, None, None] < blo
+    every = sin.reshape(sin.shape[:4] + (-1,)).all(axis=4)
+    assert np.all(every[full]), "a cell taken as full has a sub-point outside"
+    assert full.any()
