@@ -132,6 +132,17 @@ MUTANTS = [
     ("App. A.1 ceil(log2 r) off by one at powers of two",
      "        int ceil_log2 = (m == 0.5) ? k - 1 : k;",
      "        int ceil_log2 = k;"),
+    ("batched fold reads the image from the patch on the wrong side",
+     "int q = T->nb[26 * p + nb_slot(-ox, -oy, -oz)];",
+     "int q = T->nb[26 * p + nb_slot(ox, oy, oz)];"),
+    ("batched fold places a high-side image with the own patch's size",
+     "gi[a] = cc[a] + (o[a] > 0 ? nq : 0) - (o[a] < 0 ? npa : 0);",
+     "gi[a] = cc[a] + (o[a] > 0 ? npa : 0) - (o[a] < 0 ? npa : 0);"),
+    ("batched fold skips images at corners and edges",
+     "                                    if (ox == 0 && oy == 0 && oz == 0) continue;\n"
+     "                                    int q = T->nb",
+     "                                    if ((ox != 0) + (oy != 0) + (oz != 0) != 1) continue;\n"
+     "                                    int q = T->nb"),
     ("batched owner maps a low-side ghost with its own patch's size",
      "w[a] = c[a] + (o[a] < 0 ? T->dims[3 * q + a] : 0) - (o[a] > 0 ? np_[a] : 0);",
      "w[a] = c[a] + (o[a] < 0 ? np_[a] : 0) - (o[a] > 0 ? np_[a] : 0);"),
