@@ -832,7 +832,7 @@ def oracle_cycle_sample(n, seed_workload=WORKLOAD):
 
 def cpu_baseline(args):
     dt, npart, ncells = oracle_cycle_sample(args.cpu_sample_n)
-    return {"value": npart / dt, "unit": "particles/s", "cores": 1, "kind": "oracle",
+    return {"value": npart / dt, "unit": "particles/s", "cores": 1, "host_cpus": os.cpu_count(), "kind": "oracle",
             "cells_per_s": ncells / dt,
             "sample": f"one mixed cycle of the same workload shrunk to {args.cpu_sample_n}^3 at equal particle "
                       f"density ({npart} particles), single-threaded C oracle, {dt:.2f} s"}
@@ -866,7 +866,7 @@ def run_reference(args, world, rank):
         "dtype": "f64",
         "data": "synthetic",
         "config": {"workload": f"{args.workload} shrunk to {n}^3 at equal particle density ({npart} particles)"},
-        "cpu_baseline": {"value": value, "unit": "particles/s", "cores": 1, "kind": "oracle",
+        "cpu_baseline": {"value": value, "unit": "particles/s", "cores": 1, "host_cpus": os.cpu_count(), "kind": "oracle",
                          "sample": f"{n}^3 sample of {args.workload}, one mixed cycle per step"},
         "e2e": {"value": value, "unit": "particles/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
