@@ -89,3 +89,11 @@ def test_clock_record_flags_thermal_slowdown_and_skips_bad_rows():
     r = _clocks_from(rows)
     assert r["sm_mhz"] == 1500.0 and r["samples"] == 2
     assert r["reasons"] == ["hw_thermal_slowdown"]
+
+
+def test_cpu_baseline_leg_runs_the_oracle(orc):
+    import argparse
+
+    r = bench.cpu_baseline(argparse.Namespace(cpu_sample_n=16))
+    assert r["kind"] == "oracle" and r["cores"] == 1 and r["host_cpus"] >= 1
+    assert r["value"] > 0 and r["unit"] == "particles/s" and "16^3" in r["sample"]
