@@ -704,3 +704,46 @@ def test_cells_without_change_keep_their_bits(orc):
     far = box.valid(s)[:, 6, 6, 6]
     assert np.signbit(far[1]) and far[1] == 0.0
     assert box.valid(s)[0, 1, 1, 1] > 1.0
+
+
+# --------------------------------------------------------------------------
+# the plan's fixed slots: every kernel fits the per-particle bound C
+# --------------------------------------------------------------------------
+
+def _slot_bound(rK):
+    """Offsets o whose cell centre can come strictly within r_K of some point
+    of the host cell [0, 1)^3: the nearest such point is min(max(o + 1/2,
+    0), 1) per axis, so the distance is max(|o| - 1/2, 0) per axis."""
+    R = math.ceil(rK)
+    n = 0
+    for oz in range(-R, R + 1):
+        for oy in range(-R, R + 1):
+            for ox in range(-R, R + 1):
+                d2 = sum(max(abs(o) - 0.5, 0.0) ** 2 for o in (ox, oy, oz))
+                n += d2 < rK * rK
+    return n
+
+
+@pytest.mark.parametrize("rK,C", [(2.0, 81), (4.0, 461), (1.0, 27), (2.5, 117), (3.0, 251)])
+def test_every_kernel_fits_the_slot_bound(orc, rK, C):
+    """The workspace gives each particle C slots (81 at r_K = 2, 461 at
+    r_K = 4), the number of offsets whose centre can come within r_K of the
+    host cell: no position has more kernel cells, and the kernels of the
+    positions at the host cell's corners, edge and face midpoints (where each
+    offset's nearest point lies) cover exactly those C offsets."""
+    bound = _slot_bound(rK)
+    assert bound == C
+    box = syn.Box((24, 24, 24), 6)
+    params = syn.feedback_params(r_K=rK, subsample=1)
+    rng = np.random.default_rng(int(rK * 8))
+    eps = 1e-9
+    ends = (eps, 0.5, 1.0 - eps)
+    pos = [np.array([10.0 + a, 10.0 + b, 10.0 + c]) for a in ends for b in ends for c in ends]
+    pos += list(rng.uniform(10.0, 11.0, (200, 3)))
+    most, union = 0, set()
+    for x, y, z in pos:
+        ijk, _ = orc.kernel_of(params, box, float(x), float(y), float(z))
+        most = max(most, len(ijk))
+        union |= {(int(i) - 10, int(j) - 10, int(k) - 10) for i, j, k in ijk}
+    assert most <= bound
+    assert len(union) == bound
