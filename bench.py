@@ -265,7 +265,7 @@ def src_digest():
 def profiled_traffic(kernel):
     """DRAM bytes per launch of `kernel` from the committed ncu summary, if it
     was taken on the current kernel sources; else None."""
-    path = os.path.join(ROOT, "profiles", "traffic.md")
+    path = os.path.join(ROOT, "profiles", "dram_traffic_c5_512.md")
     if not os.path.exists(path):
         return None
     txt = open(path).read()
