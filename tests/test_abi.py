@@ -45,3 +45,16 @@ def test_binding_lists_every_export():
 def test_gathered_rows_without_gpu(lib):
     lib.pmp_gathered_rows.restype = ctypes.c_int32
     assert lib.pmp_gathered_rows(0) == 12 and lib.pmp_gathered_rows(1) == 8 and lib.pmp_gathered_rows(7) == 0
+
+
+def test_binding_fails_loudly_without_the_library(tmp_path, monkeypatch):
+    """No CPU fallback: with libpmp.so absent, the first call raises instead
+    of computing anything another way."""
+    from paper_2509_18261_gb300 import pmp
+
+    monkeypatch.setattr(pmp, "_lib", None)
+    monkeypatch.setattr(pmp, "LIB_PATH", str(tmp_path / "libpmp.so"))
+    with pytest.raises(RuntimeError, match="libpmp.so not found"):
+        pmp.load()
+    with pytest.raises(RuntimeError):
+        pmp.pmp_gathered_rows(0)
