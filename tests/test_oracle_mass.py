@@ -11,6 +11,7 @@ Sec. 2.2 that uses Steps 1, 2 and 5 only, to facts from outside the oracle:
 import math
 
 import numpy as np
+import pytest
 
 from paper_2509_18261_gb300 import synthetic as syn
 
@@ -23,12 +24,15 @@ def _case(seed=4, n=12, count=300):
     return box, state, parts
 
 
-def test_mass_momentum_energy_arrive_on_the_mesh(orc):
+@pytest.mark.parametrize("dx", [1.0, 0.5])
+def test_mass_momentum_energy_arrive_on_the_mesh(orc, dx):
+    """Sum over cells of Delta U times V = dx^3 returns each particle's (m, p,
+    e), for any cell size."""
     box, state, parts = _case()
     params = syn.mass_params()
     st = state.copy()
-    r = orc.cycle(params, box, st, {k: v.copy() for k, v in parts.items()})
-    V = 1.0
+    r = orc.cycle(params, box, st, {k: v.copy() for k, v in parts.items()}, dx=dx)
+    V = dx ** 3
     dU = box.valid(st) - box.valid(state)
     for f, key in enumerate(("m", "px", "py", "pz", "e")):
         got = math.fsum(float(v) for v in dU[f].ravel()) * V

@@ -132,6 +132,24 @@ MUTANTS = [
     ("App. A.1 ceil(log2 r) off by one at powers of two",
      "        int ceil_log2 = (m == 0.5) ? k - 1 : k;",
      "        int ceil_log2 = k;"),
+    ("Eq. lambda's thermal term without the rho'/rho factor",
+     "    double therm = (eint0 * rho1) / U[0];\n    double lhs",
+     "    double therm = eint0;\n    double lhs"),
+    ("Eq. lambda's constant term with rho' instead of 2 rho'",
+     "    double C = p2 - (2.0 * rho1) * (E1 - therm);",
+     "    double C = p2 - rho1 * (E1 - therm);"),
+    ("particle-mesh V_K without the cell volume",
+     "    double VK = sw * cell_volume(S->dx);",
+     "    double VK = sw;"),
+    ("omega sub-points of the y axis at the cell corner",
+     "double sy = ((double)cj + ((double)b + 0.5) / (double)S) - y;",
+     "double sy = ((double)cj + ((double)b) / (double)S) - y;"),
+    ("sink relative velocity without the sink's own velocity",
+     "    for (int a = 0; a < 3; a++) u[a] = sp[a] / srho - ps[a] / ms;",
+     "    for (int a = 0; a < 3; a++) u[a] = sp[a] / srho;"),
+    ("c_inf weighted by volume instead of mass",
+     "        src = src + U[0] * cs;",
+     "        src = src + cs;"),
     ("batched fold reads the image from the patch on the wrong side",
      "int q = T->nb[26 * p + nb_slot(-ox, -oy, -oz)];",
      "int q = T->nb[26 * p + nb_slot(ox, oy, oz)];"),

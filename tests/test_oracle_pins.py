@@ -170,6 +170,26 @@ def test_accretion_kernel_shape(orc, Gm, r_acc):
     assert np.allclose(got[keep], want[keep], rtol=1e-11, atol=0)
 
 
+def test_bondi_hoyle_depends_on_the_relative_velocity(orc):
+    """Eq. mdot uses the gas velocity relative to the sink: a sink moving at
+    -v through gas at rest accretes as a sink at rest in gas moving at v, and,
+    the swallowed gas being at rest, keeps its momentum."""
+    G, m, dt = 0.01, 10.0, 1e-3
+    vel = np.array([0.25, -0.5, 1.25])
+    params = syn.sink_params(r_K=4.0, gamma=2.0, G=G, dt=dt, rho_min=0.0)
+    box = syn.Box((16, 16, 16), 4)
+    state = syn.uniform_gas(box, 1.0, e_th=0.5)
+    sink = one(8.3, 7.6, 8.45, m, p=tuple(-m * vel))
+    r = orc.cycle(params, box, state, sink)
+    assert r["counts"][0] == 0
+    v2 = float(vel @ vel)
+    lam = math.exp(1.5) / 4.0
+    mdot = 4.0 * math.pi * G * G * m * m * math.sqrt((lam * lam + v2) / (1.0 + v2) ** 4)
+    assert sink["m"][0] - m == pytest.approx(mdot * dt, rel=1e-13)
+    for a, k in enumerate(("px", "py", "pz")):
+        assert sink[k][0] == -m * vel[a]
+
+
 @pytest.mark.parametrize("vel,dx", [((0.0, 0.0, 0.0), 1.0), ((0.25, -0.5, 1.25), 1.0), ((0.25, -0.5, 1.25), 0.5)])
 def test_bondi_hoyle_closed_form(orc, vel, dx):
     """Uniform gas (rho = 1, c_s = 1 exactly with gamma = 2 and e_th = 1/2)
