@@ -195,16 +195,21 @@ def test_mutants_are_well_formed():
 
 @pytest.mark.slow
 def test_every_planted_mistake_fails_a_pin(tmp_path):
+    from concurrent.futures import ThreadPoolExecutor
+
     src = open(SRC).read()
     # control: the unchanged source, built and run the same way, passes
     failed, tail = _pins_fail(_compile(str(tmp_path), "control", src))
     assert not failed, tail
-    survivors = []
-    for i, (name, old, new) in enumerate(MUTANTS):
-        lib = _compile(str(tmp_path), i, src.replace(old, new))
-        failed, tail = _pins_fail(lib)
-        if not failed:
-            survivors.append(name)
+
+    def one(item):
+        i, (name, old, new) = item
+        failed, _ = _pins_fail(_compile(str(tmp_path), i, src.replace(old, new)))
+        return name, failed
+
+    with ThreadPoolExecutor(max_workers=max(1, min(8, os.cpu_count() or 1))) as ex:
+        results = list(ex.map(one, enumerate(MUTANTS)))
+    survivors = [name for name, failed in results if not failed]
     assert not survivors, f"mistakes no pin catches: {survivors}"
 
 
