@@ -15,6 +15,7 @@
 import math
 
 import numpy as np
+import pytest
 
 from paper_2509_18261_gb300 import synthetic as syn
 
@@ -72,16 +73,17 @@ def test_created_cells_match_brute_force(orc):
     assert np.all(new["x"] % 1.0 == 0.5)
 
 
-def test_conservation_and_cell_velocity(orc):
+@pytest.mark.parametrize("dx", [1.0, 0.5])
+def test_conservation_and_cell_velocity(orc, dx):
     box, st = _state(5, 12)
-    params = syn.sink_params(G=0.3)
+    params = syn.sink_params(G=0.3 / dx ** 2)  # the same rho_Tr at either cell size
     buf = box.empty(0.0)
     before = box.valid(st).copy()
     st2 = st.copy()
-    n, new = orc.create_sinks(params, box, st2, buf)
+    n, new = orc.create_sinks(params, box, st2, buf, dx=dx)
     assert n > 0
     after = box.valid(st2)
-    V = 1.0
+    V = dx ** 3
     for f, key in ((0, "m"), (1, "px"), (2, "py"), (3, "pz")):
         lost = math.fsum(float(v) for v in (before[f] - after[f]).ravel()) * V
         gained = math.fsum(float(v) for v in new[key])

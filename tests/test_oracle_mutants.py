@@ -22,6 +22,9 @@ PINS = ["tests/test_oracle_pins.py", "tests/test_oracle_create.py", "tests/test_
         "tests/test_oracle_mass.py", "tests/test_oracle_batch.py", "tests/test_oracle_repro.py"]
 
 # (name, the original text, its mutated form); the original occurs once.
+# Equivalent mutants are left out: e.g. folding ghosts of a non-periodic axis
+# too changes nothing, because the kernel is cut at that face and those
+# ghosts only ever hold zeros.
 MUTANTS = [
     ("accretion removes instead of adding to the buffer's density row",
      "    dU[0] = -a;\n    for (int k = 0; k < 3; k++) dU[1 + k] = -(a * (U[1 + k] * inv));",
@@ -150,6 +153,23 @@ MUTANTS = [
     ("c_inf weighted by volume instead of mass",
      "        src = src + U[0] * cs;",
      "        src = src + cs;"),
+    ("periodic wrap with C's remainder (negative for low ghosts)",
+     "    int r = i % n;\n    return r < 0 ? r + n : r;",
+     "    int r = i % n;\n    return r;"),
+    ("kernel not cut at a non-periodic face",
+     "                if (!S->periodic[0] && (ci < 0 || ci >= S->n[0])) continue;\n",
+     ""),
+    ("Step 4 without the cell volume",
+     "        p->m[s] = p->m[s] - acc[0] * V;\n        p->px[s] = p->px[s] - acc[1] * V;\n"
+     "        p->py[s] = p->py[s] - acc[2] * V;\n        p->pz[s] = p->pz[s] - acc[3] * V;\n    }\n    free(kc);",
+     "        p->m[s] = p->m[s] - acc[0];\n        p->px[s] = p->px[s] - acc[1] * V;\n"
+     "        p->py[s] = p->py[s] - acc[2] * V;\n        p->pz[s] = p->pz[s] - acc[3] * V;\n    }\n    free(kc);"),
+    ("created sink mass without the cell volume",
+     "                    double ms = (U[0] - rtr) * V;",
+     "                    double ms = (U[0] - rtr);"),
+    ("created sink's cell keeps its momentum instead of its velocity",
+     "                    for (int a = 0; a < 3; a++) S->u[(int64_t)(1 + a) * S->fstride + c] = rtr * vel[a];",
+     "                    (void)vel;"),
     ("batched fold reads the image from the patch on the wrong side",
      "int q = T->nb[26 * p + nb_slot(-ox, -oy, -oz)];",
      "int q = T->nb[26 * p + nb_slot(ox, oy, oz)];"),

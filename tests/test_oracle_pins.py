@@ -230,6 +230,32 @@ def _fb_cloud(rng, box, count):
     return dict(x=x, y=y, z=z, m=m, px=m * v[0], py=m * v[1], pz=m * v[2], e=np.ones(count))
 
 
+def test_kernel_cut_at_a_non_periodic_face_keeps_the_ledger(orc):
+    """On a non-periodic axis the kernel stops at the domain face (reading R2):
+    no cell outside the domain is part of it, and the summed changes of the
+    valid cells carry exactly the ejecta mass, momentum and energy (EJ
+    regime), with nothing left in the buffer's ghost cells of that axis."""
+    box = syn.Box((12, 12, 12), 3)
+    rng = np.random.default_rng(17)
+    state = syn.gas_state(rng, box)
+    p = many([(0.3, 6.2, 5.7, 0.02, 0.001, -0.002, 0.0005, 1.0),
+              (11.6, 0.4, 11.8, 0.05, -0.003, 0.001, 0.002, 1.0)])
+    params = syn.feedback_params(A_sf=1e9)
+    for s in range(2):
+        ijk, _ = orc.kernel_of(params, box, p["x"][s], p["y"][s], p["z"][s], periodic=(0, 1, 1))
+        assert np.all((ijk[:, 0] >= 0) & (ijk[:, 0] < 12))
+        assert len(ijk) < len(orc.kernel_of(params, box, p["x"][s], p["y"][s], p["z"][s])[0])
+    r = orc.cycle(params, box, state, p, periodic=(0, 1, 1))
+    D = box.valid(r["buf"]).reshape(5, -1)
+    assert math.fsum(D[0]) == pytest.approx(math.fsum(p["m"]), rel=1e-13)
+    for a, k in enumerate(("px", "py", "pz")):
+        assert math.fsum(D[1 + a]) == pytest.approx(math.fsum(p[k]), rel=1e-12)
+    ekin = (p["px"] ** 2 + p["py"] ** 2 + p["pz"] ** 2) / (2 * p["m"])
+    assert math.fsum(D[4]) == pytest.approx(math.fsum(p["e"] + ekin), rel=1e-13)
+    g = box.grid(r["buf"])
+    assert np.all(g[:, :, :, :3] == 0) and np.all(g[:, :, :, -3:] == 0)
+
+
 @pytest.mark.parametrize("dx", [1.0, 0.5])
 def test_feedback_conservation_ej_regime(orc, dx):
     """EJ regime (|p_radial| = 0, Eq. dp): the summed buffer times the cell
