@@ -170,6 +170,24 @@ MUTANTS = [
     ("created sink's cell keeps its momentum instead of its velocity",
      "                    for (int a = 0; a < 3; a++) S->u[(int64_t)(1 + a) * S->fstride + c] = rtr * vel[a];",
      "                    (void)vel;"),
+    ("auxiliary field updated without the limiter's eta",
+     "X[(int64_t)f * stride + c] = x + eta * ((x / U[0]) * D[0]);",
+     "X[(int64_t)f * stride + c] = x + ((x / U[0]) * D[0]);"),
+    ("auxiliary field changed by its density, not its concentration",
+     "X[(int64_t)f * stride + c] = x + eta * ((x / U[0]) * D[0]);",
+     "X[(int64_t)f * stride + c] = x + eta * D[0];"),
+    ("sink apply scales only the density row",
+     "        double e = sink_eta(P, dx, U, D);\n        for (int f = 0; f < NF; f++) eta[f] = e;",
+     "        double e = sink_eta(P, dx, U, D);\n        for (int f = 0; f < NF; f++) eta[f] = f == 0 ? e : 1.0;"),
+    ("r_acc not clamped at r_K / 2",
+     "    if (racc > 0.5 * P->r_K) racc = 0.5 * P->r_K;\n",
+     ""),
+    ("Step 4 reads eta at the unwrapped (ghost) cell instead of its owner",
+     "            int64_t o = cell_index(B, kc[t].wi, kc[t].wj, kc[t].wk);\n            for (int f = 0; f < NF; f++) D[f] = B->u[(int64_t)f * B->fstride + o];\n            double eta = sink_eta(P, S->dx, U, D);\n            return_add(eta, U, dU, acc);\n        }\n        p->m[s]",
+     "            int64_t o = cell_index(B, kc[t].ci, kc[t].cj, kc[t].ck);\n            for (int f = 0; f < NF; f++) D[f] = B->u[(int64_t)f * B->fstride + o];\n            double eta = sink_eta(P, S->dx, U, D);\n            return_add(eta, U, dU, acc);\n        }\n        p->m[s]"),
+    ("Eq. mdot without rho_inf",
+     "double mdot = (((4.0 * OR_PI) * rho_inf) * (r_bh * r_bh))",
+     "double mdot = ((4.0 * OR_PI) * (r_bh * r_bh))"),
     ("batched fold reads the image from the patch on the wrong side",
      "int q = T->nb[26 * p + nb_slot(-ox, -oy, -oz)];",
      "int q = T->nb[26 * p + nb_slot(ox, oy, oz)];"),

@@ -190,24 +190,25 @@ def test_bondi_hoyle_depends_on_the_relative_velocity(orc):
         assert sink[k][0] == -m * vel[a]
 
 
-@pytest.mark.parametrize("vel,dx", [((0.0, 0.0, 0.0), 1.0), ((0.25, -0.5, 1.25), 1.0), ((0.25, -0.5, 1.25), 0.5)])
-def test_bondi_hoyle_closed_form(orc, vel, dx):
-    """Uniform gas (rho = 1, c_s = 1 exactly with gamma = 2 and e_th = 1/2)
+@pytest.mark.parametrize("vel,dx,rho0", [((0.0, 0.0, 0.0), 1.0, 1.0), ((0.25, -0.5, 1.25), 1.0, 1.0),
+                                         ((0.25, -0.5, 1.25), 0.5, 1.0), ((0.0, 0.0, 0.0), 1.0, 2.5)])
+def test_bondi_hoyle_closed_form(orc, vel, dx, rho0):
+    """Uniform gas (rho0, c_s = 1 exactly with gamma = 2 and e_th = 1/2)
     moving at vel past a sink at rest: the accreted mass over dt is the first
-    line of Eq. mdot, 4 pi rho G^2 m^2 sqrt((lambda^2 c^2 + v^2)/(c^2 + v^2)^4)
+    line of Eq. mdot, 4 pi rho0 G^2 m^2 sqrt((lambda^2 c^2 + v^2)/(c^2 + v^2)^4)
     dt, because the normalised weights of Eq. kernel_wgt sum to 1 and neither
     the Truelove branch nor the limiter is active."""
     G, m, dt = 0.01, 10.0, 1e-3
     params = syn.sink_params(r_K=4.0, gamma=2.0, G=G, dt=dt, rho_min=0.0)
     box = syn.Box((16, 16, 16), 4)
-    state = syn.uniform_gas(box, 1.0, vel=vel, e_th=0.5)
+    state = syn.uniform_gas(box, rho0, vel=vel, e_th=0.5)
     sink = one(8.3, 7.6, 8.45, m)
     old = state.copy()
     r = orc.cycle(params, box, state, sink, dx=dx)
     assert r["counts"][0] == 0
     v2 = vel[0] ** 2 + vel[1] ** 2 + vel[2] ** 2
     lam = math.exp(1.5) / 4.0
-    mdot = 4.0 * math.pi * 1.0 * G * G * m * m * math.sqrt((lam * lam + v2) / (1.0 + v2) ** 4)
+    mdot = 4.0 * math.pi * rho0 * G * G * m * m * math.sqrt((lam * lam + v2) / (1.0 + v2) ** 4)
     dm = sink["m"][0] - m
     assert dm == pytest.approx(mdot * dt, rel=1e-13)
     dgas = math.fsum((box.valid(state)[0] - box.valid(old)[0]).ravel()) * dx ** 3
