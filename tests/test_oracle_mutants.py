@@ -188,6 +188,18 @@ MUTANTS = [
     ("Eq. mdot without rho_inf",
      "double mdot = (((4.0 * OR_PI) * rho_inf) * (r_bh * r_bh))",
      "double mdot = ((4.0 * OR_PI) * (r_bh * r_bh))"),
+    ("App. A.1 error bound with half the machine epsilon",
+     "if (ebuf) ebuf[o] = ebuf[o] + 2.220446049250313e-16 * fabs(B->u[o]);",
+     "if (ebuf) ebuf[o] = ebuf[o] + 1.1102230246251565e-16 * fabs(B->u[o]);"),
+    ("App. A.1 error bound from the added value instead of the sum",
+     "if (ebuf) ebuf[o] = ebuf[o] + 2.220446049250313e-16 * fabs(B->u[o]);",
+     "if (ebuf) ebuf[o] = ebuf[o] + 2.220446049250313e-16 * fabs(dU[f]);"),
+    ("Eq. lambda's roots swapped when p . dp < 0",
+     "        double Q = sq - B;\n        hi = Q / A;\n        lo = C / Q;",
+     "        double Q = sq - B;\n        hi = C / Q;\n        lo = Q / A;"),
+    ("gathered gas mass without the cell volume",
+     "    double Mgas = sr * V;",
+     "    double Mgas = sr;"),
     ("batched fold reads the image from the patch on the wrong side",
      "int q = T->nb[26 * p + nb_slot(-ox, -oy, -oz)];",
      "int q = T->nb[26 * p + nb_slot(ox, oy, oz)];"),
