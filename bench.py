@@ -47,7 +47,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--mode", default="atomic", choices=["atomic", "sorted"])
-    ap.add_argument("--e2e-steps", type=int, default=4)
+    ap.add_argument("--e2e-steps", type=int, default=None, help="end-to-end steps (default: --steps)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--cpu-sample-n", type=int, default=128)
@@ -276,6 +276,62 @@ def profiled_traffic(kernel):
     return float(m.group(1)) if m else None
 
 
+def measure_fp64_and_atomics():
+    """FP64 fused-multiply-add and FP64 atomicAdd rates of this GPU, measured
+    with the library's probe kernels (CUDA events on the launching stream,
+    best of 5 after 3 warm-up launches)."""
+    import torch
+
+    from paper_2509_18261_gb300 import pmp
+
+    stream = torch.cuda.current_stream()
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    threads, chains = pmp.pmp_probe_threads(), pmp.pmp_probe_chains()
+
+    def best(fn, reps=5, warm=3):
+        for _ in range(warm):
+            fn()
+        ts = []
+        for _ in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            a.record(stream)
+            fn()
+            b.record(stream)
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+        return min(ts)
+
+    out = {}
+    blocks, iters = sms * 8, 4096
+    buf = torch.empty(blocks * threads, dtype=torch.float64, device="cuda")
+    ms = best(lambda: pmp.pmp_probe_fp64(buf, blocks, iters))
+    fmas = blocks * threads * chains * iters
+    out["fp64_tflops"] = 2.0 * fmas / (ms * 1e-3) / 1e12
+    out["fp64_dfma_per_clk_per_sm"] = None
+    out["fp64_probe"] = (f"{blocks} blocks x {threads} threads x {chains} chains x {iters} DFMA "
+                         f"(2 flops each), best of 5: {ms:.3f} ms")
+    del buf
+    for name, n_targets in (("atomic_l2_per_s", 1 << 20), ("atomic_hbm_per_s", 1 << 28)):
+        tgt = torch.zeros(n_targets, dtype=torch.float64, device="cuda")
+        n_adds = 1 << 28
+        ms = best(lambda: pmp.pmp_probe_atomic(tgt, n_adds, sms * 16))
+        out[name] = n_adds / (ms * 1e-3)
+        del tgt
+    out["atomic_probe"] = ("2^28 FP64 atomicAdd scattered over 2^20 doubles (8 MB, L2-resident) and over "
+                           "2^28 doubles (2 GB), best of 5")
+    torch.cuda.empty_cache()
+    return out
+
+
+def alg_bytes_fb_pass1(n_fb, touched_state, touched_buf):
+    """Algorithmic bytes of one launch of the fused supernova plan + gather +
+    deposit: the particles read once (64 B), their 12 gathered rows written
+    (96 B), every touched state cell read once (40 B) and every touched
+    buffer cell read and written once (80 B)."""
+    return 160 * n_fb + 40 * touched_state + 80 * touched_buf
+
+
 def peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -416,6 +472,20 @@ def run_ours(args, world, rank, local):
     step_ms_by_kernel = {k: nl * ms for k, (nl, ms) in kernel_ms.items()}
     dominant = max(step_ms_by_kernel, key=step_ms_by_kernel.get)
     roof = roofline(dominant, kernel_ms[dominant][1], pairs, box, n_fb, n_sk, hbm_peak, peak_src)
+    measured = measure_fp64_and_atomics()
+    if roof["bound"] == "alu" and roof["unit"] == "TFLOP/s":
+        roof["peak_measured"] = measured["fp64_tflops"]
+        roof["frac_measured"] = roof["achieved"] / measured["fp64_tflops"]
+        roof["peak_measured_source"] = "FP64 DFMA probe on this GPU, same run (pmp_probe_fp64)"
+    if dominant == "fb_gather_deposit":
+        # the same launch seen as an HBM kernel: algorithmic bytes over time
+        touched = touched_cells(P_fb, w["fb_params"], box, state0, fb)
+        ab = alg_bytes_fb_pass1(n_fb, touched["state"], touched["buffer"])
+        gbs = ab / (kernel_ms[dominant][1] * 1e-3) / 1e9
+        roof["hbm_view"] = {"algorithmic_bytes": ab, "GB/s": gbs, "frac": gbs / hbm_peak,
+                            "touched_cells": touched}
+        if roof.get("traffic"):
+            roof["traffic_ratio"] = roof["traffic"] / ab
 
     hbm_passes = cell_pass_hbm(kernel_ms, box, hbm_peak)
 
@@ -446,6 +516,7 @@ def run_ours(args, world, rank, local):
         "kernels_ms_per_launch": {k: round(v[1], 4) for k, v in sorted(kernel_ms.items())},
         "limiter": {"fb_cells_eta_lt_1": lim_fb[0], "fb_noroot": lim_fb[1], "sink_cells_eta_lt_1": lim_sk[0]},
         "roofline": roof,
+        "measured_peaks": measured,
         "hbm_passes": hbm_passes,
         "e2e": e2e,
         "gpu_launches": launches_per_step * args.steps,
@@ -482,7 +553,7 @@ def end_to_end(args, w, world, state, fb, sk, P_fb, P_sk, cycle, stream):
                  sk={k: torch.empty_like(h_sk[k]).pin_memory() for k in ("m", "px", "py", "pz")}) for _ in range(2)]
     bi = h_state.numel() * 8 + sum(v.numel() * 8 for v in h_fb.values()) + sum(v.numel() * 8 for v in h_sk.values())
     bo = h_state.numel() * 8 + sum(v.numel() * 8 for v in outs[0]["sk"].values())
-    steps = max(args.e2e_steps, 2)
+    steps = max(args.e2e_steps if args.e2e_steps else args.steps, 2)
 
     def copy_in(st, f, k_):
         st.copy_(h_state, non_blocking=True)
@@ -570,6 +641,29 @@ def end_to_end(args, w, world, state, fb, sk, P_fb, P_sk, cycle, stream):
             "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo, "steps": steps,
             "serial_ms_per_step": serial_ms,
             "overlap": "double-buffered: the copies of step k+1 (in) and k-1 (out) run on copy streams during step k"}
+
+
+def touched_cells(P_fb, params, box, state0, fb):
+    """Distinct buffer cells (ghosts included) and distinct state cells that
+    one supernova deposit touches: a deposit on the initial state, counted
+    from the buffer's density row before and after the fold."""
+    import torch
+
+    from paper_2509_18261_gb300 import pmp
+
+    ps = P_fb
+    ps.state.data.copy_(state0)
+    pmp.pmp_zero_buffer(ps.ctx, ps.buffer)
+    pmp.pmp_gather_deposit(ps.ctx, ps.state, fb, ps.gathered, ps.buffer, ps.mode, ps.workspace)
+    rho = ps.buffer.data[0, :box.ncells_padded]
+    tb = int(torch.count_nonzero(rho).item())
+    pmp.pmp_fold_ghosts(ps.ctx, ps.buffer)
+    g = box.g
+    px, py, pz = box.padded
+    v = ps.buffer.data[0, :box.ncells_padded].reshape(pz, py, px)[g:pz - g, g:py - g, g:px - g]
+    ts = int(torch.count_nonzero(v).item())
+    torch.cuda.synchronize()
+    return {"buffer": tb, "state": ts}
 
 
 def sink_creation(P_sk, stream):

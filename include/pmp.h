@@ -476,10 +476,14 @@ void pmp_batch_destroy(pmp_batch *batch);
  * particle count to about 99,000 at r_K = 2 (each particle needs 28 + 8 C
  * bytes, C the kernel-cell bound: 81 at r_K = 2, 461 at r_K = 4); larger
  * counts return PMP_ERR_WORKSPACE and enqueue nothing.  params->kind must be
- * PMP_KIND_FEEDBACK.
- * The first call on a device looks up the scratch's device address
- * (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture.  Every call shares the one scratch array, which
+ * PMP_KIND_FEEDBACK.  The meshes are checked as pmp_deposit checks them
+ * (PMP_ERR_ARG for a misaligned or NULL data pointer, a periodic flag other
+ * than 0 or 1, a non-finite dx, meshes of different boxes, or a state that
+ * overlaps the buffer; PMP_ERR_GHOST_TOO_THIN for buffer ng < ceil(r_K)).
+ * Every call looks up the scratch's device address on the current device
+ * (cudaGetSymbolAddress, which allocates nothing), so a call after a device
+ * reset or on another device uses that device's copy; make the first call
+ * on a device before any stream capture.  Every call shares the one scratch array, which
  * keeps the last call's contents: calls whose work overlaps on the GPU (two
  * streams, or two threads) race and corrupt each other; serialise them.
  * Particles outside the box are skipped; no device errors are reported (there
@@ -487,6 +491,26 @@ void pmp_batch_destroy(pmp_batch *batch);
  * library routine; enqueues on `stream` and returns. */
 pmp_status pmp_deposit_noalloc(const pmp_params *params, const pmp_mesh *state, const pmp_particles *particles,
                                double *gathered, pmp_mesh *buffer, pmp_stream stream);
+
+/* ------------------------------------------------------------------------ */
+/* Measurement kernels (no paper counterpart)                               */
+/* ------------------------------------------------------------------------ */
+
+/* The peaks the particle kernels are measured against, taken on the GPU the
+ * library runs on.  Both enqueue one launch on `stream` and return; the
+ * caller times it (CUDA events on that stream).
+ * pmp_probe_fp64: `blocks` blocks of pmp_probe_threads() threads, each running
+ *   pmp_probe_chains() independent chains of `iters` FP64 fused multiply-adds
+ *   (2 flops each); out (device) receives one double per thread, so it needs
+ *   blocks * pmp_probe_threads() entries.
+ * pmp_probe_atomic: n_adds FP64 atomicAdd of 1.0 spread over n_targets
+ *   doubles of `target` (device), addition t to index (t * 2654435761) mod
+ *   n_targets; grid-stride over `blocks` blocks.
+ * PMP_ERR_ARG for NULL pointers or non-positive sizes. */
+int32_t pmp_probe_threads(void);
+int32_t pmp_probe_chains(void);
+pmp_status pmp_probe_fp64(double *out, int32_t blocks, int32_t iters, pmp_stream stream);
+pmp_status pmp_probe_atomic(double *target, int64_t n_targets, int64_t n_adds, int32_t blocks, pmp_stream stream);
 
 #ifdef __cplusplus
 }

@@ -16,46 +16,12 @@
 namespace {
 
 using pmp::Box;
+using pmp::make_box;
+using pmp::overlaps;
 using pmp::KParams;
 using pmp::Parts;
 
 bool finite(double v) { return std::isfinite(v); }
-
-pmp_status make_box(const pmp_mesh *m, Box *b)
-{
-    if (!m || !m->data) return PMP_ERR_ARG;
-    for (int a = 0; a < 3; ++a) {
-        if (m->n[a] < 1) return PMP_ERR_ARG;
-        if (m->periodic[a] != 0 && m->periodic[a] != 1) return PMP_ERR_ARG;
-    }
-    if (m->ng < 0 || !finite(m->dx) || !(m->dx > 0.0)) return PMP_ERR_ARG;
-    const long long px = (long long)m->n[0] + 2LL * m->ng, py = (long long)m->n[1] + 2LL * m->ng,
-                    pz = (long long)m->n[2] + 2LL * m->ng;
-    const long long nc = px * py * pz;
-    if (m->field_stride < nc) return PMP_ERR_ARG;
-    if ((reinterpret_cast<uintptr_t>(m->data) & 7) != 0) return PMP_ERR_ARG;
-    b->n0 = m->n[0];
-    b->n1 = m->n[1];
-    b->n2 = m->n[2];
-    b->g = m->ng;
-    b->per0 = m->periodic[0];
-    b->per1 = m->periodic[1];
-    b->per2 = m->periodic[2];
-    b->pad_ = 0;
-    b->px = px;
-    b->pxy = px * py;
-    b->fs = m->field_stride;
-    b->ncells = nc;
-    return PMP_OK;
-}
-
-bool overlaps(const pmp_mesh *a, const pmp_mesh *b)
-{
-    const char *a0 = reinterpret_cast<const char *>(a->data), *b0 = reinterpret_cast<const char *>(b->data);
-    const char *a1 = a0 + sizeof(double) * (size_t)(4 * a->field_stride + 1);
-    const char *b1 = b0 + sizeof(double) * (size_t)(4 * b->field_stride + 1);
-    return a0 < b1 && b0 < a1;
-}
 
 // State/buffer compatibility and the ghost-width rule (Sec. 2.2, Step 1: the
 // buffer's ghost zones must contain the kernel).
@@ -227,6 +193,42 @@ long long nvalid_of(const pmp_mesh *m) { return (long long)m->n[0] * m->n[1] * m
 }  // namespace
 
 namespace pmp {
+
+pmp_status make_box(const pmp_mesh *m, Box *b)
+{
+    if (!m || !m->data) return PMP_ERR_ARG;
+    for (int a = 0; a < 3; ++a) {
+        if (m->n[a] < 1) return PMP_ERR_ARG;
+        if (m->periodic[a] != 0 && m->periodic[a] != 1) return PMP_ERR_ARG;
+    }
+    if (m->ng < 0 || !std::isfinite(m->dx) || !(m->dx > 0.0)) return PMP_ERR_ARG;
+    const long long px = (long long)m->n[0] + 2LL * m->ng, py = (long long)m->n[1] + 2LL * m->ng,
+                    pz = (long long)m->n[2] + 2LL * m->ng;
+    const long long nc = px * py * pz;
+    if (m->field_stride < nc) return PMP_ERR_ARG;
+    if ((reinterpret_cast<uintptr_t>(m->data) & 7) != 0) return PMP_ERR_ARG;
+    b->n0 = m->n[0];
+    b->n1 = m->n[1];
+    b->n2 = m->n[2];
+    b->g = m->ng;
+    b->per0 = m->periodic[0];
+    b->per1 = m->periodic[1];
+    b->per2 = m->periodic[2];
+    b->pad_ = 0;
+    b->px = px;
+    b->pxy = px * py;
+    b->fs = m->field_stride;
+    b->ncells = nc;
+    return PMP_OK;
+}
+
+bool overlaps(const pmp_mesh *a, const pmp_mesh *b)
+{
+    const char *a0 = reinterpret_cast<const char *>(a->data), *b0 = reinterpret_cast<const char *>(b->data);
+    const char *a1 = a0 + sizeof(double) * (size_t)(4 * a->field_stride + 1);
+    const char *b1 = b0 + sizeof(double) * (size_t)(4 * b->field_stride + 1);
+    return a0 < b1 && b0 < a1;
+}
 
 pmp_status check_params(const pmp_params *p)
 {

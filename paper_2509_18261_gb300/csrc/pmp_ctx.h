@@ -69,6 +69,12 @@ struct Timed {
 
 namespace pmp {
 
+// Geometry of a mesh for the kernels, after checking it: n >= 1, periodic
+// flags 0 or 1, ng >= 0, dx finite and positive, field_stride at least the
+// padded cell count, data non-NULL and 8-byte aligned (else PMP_ERR_ARG).
+pmp_status make_box(const pmp_mesh *m, Box *b);
+// True when the five-field extents of two meshes share a byte.
+bool overlaps(const pmp_mesh *a, const pmp_mesh *b);
 // Validates a parameter set (PMP_OK or PMP_ERR_ARG).
 pmp_status check_params(const pmp_params *p);
 // Derived constants of a parameter set for cell size dx.

@@ -33,6 +33,7 @@ EXPORTS = [
     "pmp_create_sinks_workspace_size", "pmp_create_sinks", "pmp_apply_extra",
     "pmp_batch_create", "pmp_batch_set_particles", "pmp_batch_set_strategy", "pmp_batch_strategies",
     "pmp_batch_autotune", "pmp_cycle_batched", "pmp_batch_info", "pmp_batch_hold_barriers", "pmp_batch_destroy",
+    "pmp_probe_threads", "pmp_probe_chains", "pmp_probe_fp64", "pmp_probe_atomic",
 ]
 PERSISTENT, PER_PATCH, GRAPH = 0, 1, 2
 LAUNCHES = {"persistent": PERSISTENT, "per_patch": PER_PATCH, "graph": GRAPH}
@@ -127,6 +128,10 @@ def load():
         "pmp_batch_info": ([vp, ctypes.POINTER(i32), ctypes.POINTER(i64)], i32),
         "pmp_batch_hold_barriers": ([vp, i32], i32),
         "pmp_batch_destroy": ([vp], None),
+        "pmp_probe_threads": ([], i32),
+        "pmp_probe_chains": ([], i32),
+        "pmp_probe_fp64": ([vp, i32, i32, vp], i32),
+        "pmp_probe_atomic": ([vp, i64, i64, i32, vp], i32),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -350,6 +355,24 @@ def pmp_deposit_noalloc(params, state, parts, gathered, buffer):
     _check("pmp_deposit_noalloc", load().pmp_deposit_noalloc(ctypes.byref(cp), ctypes.byref(state.c()),
                                                              ctypes.byref(pp), _ptr(gathered),
                                                              ctypes.byref(buffer.c()), _stream()))
+
+
+def pmp_probe_threads():
+    return load().pmp_probe_threads()
+
+
+def pmp_probe_chains():
+    return load().pmp_probe_chains()
+
+
+def pmp_probe_fp64(out, blocks, iters):
+    """Enqueues the FP64 fused multiply-add probe on the current stream."""
+    _check("pmp_probe_fp64", load().pmp_probe_fp64(_ptr(out), blocks, iters, _stream()))
+
+
+def pmp_probe_atomic(target, n_adds, blocks):
+    """Enqueues n_adds FP64 atomicAdd over the doubles of `target`."""
+    _check("pmp_probe_atomic", load().pmp_probe_atomic(_ptr(target), target.numel(), n_adds, blocks, _stream()))
 
 
 def pmp_timing_enable(ctx, on=True):

@@ -10,7 +10,8 @@ from paper_2509_18261_gb300 import pmp
 from paper_2509_18261_gb300 import synthetic as syn
 
 OK, ARG, THIN, WORKSPACE, CUDA = 0, 1, 2, 6, 7
-FAKE = 0x1000  # a non-NULL address that nothing dereferences on the host
+FAKE = 0x1000  # non-NULL addresses that nothing dereferences on the host
+FAKE_BUF = 0x40000000  # far from FAKE: a state at FAKE and a buffer here do not overlap
 
 
 @pytest.fixture(scope="module")
@@ -72,24 +73,67 @@ def _noalloc(lib, params, state, parts, buffer, gathered=FAKE):
                                    ctypes.byref(buffer), None)
 
 
+def _buf(n=(32, 32, 32), ng=4, data=FAKE_BUF):
+    return _mesh(n, ng, data)
+
+
 def test_noalloc_checks_its_arguments_on_the_host(lib):
     fb = pmp._params_struct(syn.feedback_params())
     m = _mesh((32, 32, 32), 4)
     # sinks are not offered
-    assert _noalloc(lib, pmp._params_struct(syn.sink_params()), m, _parts(10), _mesh((32, 32, 32), 4)) == ARG
+    assert _noalloc(lib, pmp._params_struct(syn.sink_params()), m, _parts(10), _buf()) == ARG
     # no gathered rows for a non-empty set
-    assert _noalloc(lib, fb, m, _parts(10), _mesh((32, 32, 32), 4), gathered=None) == ARG
+    assert _noalloc(lib, fb, m, _parts(10), _buf(), gathered=None) == ARG
     # state and buffer of different boxes
-    assert _noalloc(lib, fb, m, _parts(10), _mesh((32, 32, 16), 4)) == ARG
+    assert _noalloc(lib, fb, m, _parts(10), _buf((32, 32, 16))) == ARG
     # a buffer ghost layer thinner than ceil(r_K)
-    assert _noalloc(lib, fb, m, _parts(10), _mesh((32, 32, 32), 1)) == THIN
+    assert _noalloc(lib, fb, m, _parts(10), _buf(ng=1)) == THIN
     # NULL mesh data
-    assert _noalloc(lib, fb, _mesh((32, 32, 32), 4, data=None), _parts(10), _mesh((32, 32, 32), 4)) == ARG
+    assert _noalloc(lib, fb, _mesh((32, 32, 32), 4, data=None), _parts(10), _buf()) == ARG
+
+
+def test_noalloc_rejects_a_state_that_overlaps_the_buffer(lib):
+    fb = pmp._params_struct(syn.feedback_params())
+    m = _mesh((32, 32, 32), 4)
+    assert _noalloc(lib, fb, m, _parts(10), _buf(data=FAKE)) == ARG  # the same array
+    assert _noalloc(lib, fb, m, _parts(10), _buf(data=FAKE + 8 * 1000)) == ARG  # inside the state's fields
+    inside = _mesh((32, 32, 32), 4, data=FAKE_BUF + 8 * 64000 * 4)  # state inside the buffer's last field
+    assert _noalloc(lib, fb, inside, _parts(10), _buf()) == ARG
+
+
+@pytest.mark.parametrize("what", ["misaligned state", "misaligned buffer", "periodic 2", "dx inf", "dx nan",
+                                  "negative ng"])
+def test_noalloc_checks_its_meshes_as_the_context_calls_do(lib, what):
+    fb = pmp._params_struct(syn.feedback_params())
+    m, b = _mesh((32, 32, 32), 4), _buf()
+    if what == "misaligned state":
+        m.data = FAKE + 4
+    elif what == "misaligned buffer":
+        b.data = FAKE_BUF + 4
+    elif what == "periodic 2":
+        m.periodic[1] = 2
+        b.periodic[1] = 2
+    elif what == "dx inf":
+        m.dx = b.dx = float("inf")
+    elif what == "dx nan":
+        m.dx = b.dx = float("nan")
+    else:
+        m.ng = -1
+    assert _noalloc(lib, fb, m, _parts(10), b) == ARG
+
+
+@pytest.mark.parametrize("field,value", [("A_p", float("nan")), ("eps_K", float("nan")), ("RM_ej", float("nan")),
+                                         ("RM_st", float("nan")), ("gamma", float("inf")), ("A_sf", float("inf")),
+                                         ("mu_H", float("inf")), ("r_K", 0.5), ("subsample", 0)])
+def test_noalloc_checks_parameters_as_pmp_create_does(lib, field, value):
+    fb = pmp._params_struct(syn.feedback_params())
+    setattr(fb, field, value)
+    assert _noalloc(lib, fb, _mesh((32, 32, 32), 4), _parts(10), _buf()) == ARG
 
 
 def test_noalloc_rejects_counts_beyond_its_fixed_scratch(lib):
     # 64 MiB at 28 + 8 * 81 bytes per particle (r_K = 2): about 99,000 particles
     fb = pmp._params_struct(syn.feedback_params())
-    m, b = _mesh((64, 64, 64), 4), _mesh((64, 64, 64), 4)
+    m, b = _mesh((64, 64, 64), 4), _buf((64, 64, 64))
     assert _noalloc(lib, fb, m, _parts(120_000), b) == WORKSPACE
     assert _noalloc(lib, fb, m, _parts(10_000_000), b) == WORKSPACE

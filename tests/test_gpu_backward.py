@@ -2,9 +2,10 @@
 
 - dot-product identity <J dtheta, v> = <dtheta, J^T v> against the dual-number
   oracle (forward mode), to 1e-8 relative;
-- central finite differences of the C oracle's deposition function on 64
-  particles of the 128^3 workload whose kernels touch no limiter-active cell
-  (h = 1e-6 max(1, |theta|));
+- fourth-order central finite differences of the C oracle's deposition
+  function on 64 particles of the 128^3 workload whose kernels touch no
+  limiter-active cell, at 1e-8 relative plus the quotient's rounding
+  allowance;
 - cells where the limiter acted pass no gradient;
 - the autograd Function returns exactly pmp_backward's gradients.
 """
@@ -14,6 +15,7 @@ import numpy as np
 import pytest
 
 from paper_2509_18261_gb300 import synthetic as syn
+from helpers import fd_derivative
 
 pytestmark = pytest.mark.gpu
 FIELDS = ("m", "e", "px", "py", "pz", "x", "y", "z")
@@ -67,6 +69,10 @@ def test_adjoint_dot_product_identity(orc):
 
 
 def test_adjoint_matches_finite_differences_128(orc):
+    """64 particles of the 128^3 workload whose kernels touch no
+    limiter-active cell: each of the 8 gradients within 1e-8 of the
+    fourth-order central difference of the oracle's deposition function,
+    plus the difference quotient's own rounding allowance (helpers.fd_derivative)."""
     w = syn.make_workload("c4_128")
     box, state, parts, params = w["box"], w["state"], w["fb"], w["fb_params"]
     rng = np.random.default_rng(41)
@@ -77,8 +83,9 @@ def test_adjoint_matches_finite_differences_128(orc):
     nx, ny, nz = box.n
     active = (eta < 1.0).reshape(nz, ny, nx)
     Rv = box.valid(R)
+    G = orc.gather(params, box, state, parts)
     order = rng.permutation(len(parts["x"]))
-    checked = 0
+    checked = decided = total = 0
     for s in order:
         if checked >= 64:
             break
@@ -86,32 +93,21 @@ def test_adjoint_matches_finite_differences_128(orc):
         ijk, _ = orc.kernel_of(params, box, one["x"][0], one["y"][0], one["z"][0])
         if any(active[k % nz, j % ny, i % nx] for (i, j, k) in ijk):
             continue
-        ok = True
         for i, f in enumerate(FIELDS):
-            x0 = one[f][0]
-            h = 1e-6 * max(1.0, abs(x0))
-            if f in ("x", "y", "z"):
-                a, b = dict(one), dict(one)
-                a[f] = np.array([x0 + h]); b[f] = np.array([x0 - h])
-                ka = orc.kernel_of(params, box, a["x"][0], a["y"][0], a["z"][0])
-                kb = orc.kernel_of(params, box, b["x"][0], b["y"][0], b["z"][0])
-                if not (np.array_equal(ka[0], kb[0]) and np.array_equal(ka[1], kb[1])):
-                    continue
-
-            def L(val):
-                o = {k: arr.copy() for k, arr in one.items()}
-                o[f][0] = val
-                cells, dU = orc.deltas(params, box, state, o)
-                return math.fsum(float(Rv[c, kk % nz, jj % ny, ii % nx] * dU[q, c])
-                                 for q, (ii, jj, kk) in enumerate(cells) for c in range(5))
-
-            fd = (L(x0 + h) - L(x0 - h)) / (2 * h)
+            r = fd_derivative(orc, params, box, state, one, Rv, f, G[0, s])
+            if r is None:
+                continue
+            fd, floor = r
+            total += 1
+            decided += floor <= 1e-9 * abs(fd)
             gi = g[i, s]
-            if not abs(gi - fd) <= 1e-6 * abs(fd) + 1e-9 * (1.0 + np.abs(g[:, s]).max()):
-                ok = False
-                raise AssertionError(f"particle {s} d/d{f}: adjoint {gi!r} vs finite difference {fd!r}")
-        checked += ok
+            assert abs(gi - fd) <= 1e-8 * abs(fd) + floor, (
+                f"particle {s} d/d{f}: adjoint {gi!r} vs finite difference {fd!r} "
+                f"(rel {abs(gi - fd) / abs(fd):.2e}, floor {floor / abs(fd):.2e})")
+        checked += 1
     assert checked == 64
+    assert total >= 64 * 7
+    assert decided >= total // 2  # most checks are settled by the 1e-8 term, not the floor
 
 
 def test_limiter_active_cells_pass_no_gradient(orc):

@@ -12,7 +12,7 @@ import numpy as np
 import pytest
 
 from paper_2509_18261_gb300 import synthetic as syn
-from helpers import assert_bits_equal, assert_within_abs, gpu_pass, oracle_pass, valid_flat
+from helpers import assert_bits_equal, assert_state_within_bound, gpu_pass, oracle_pass, sink_return_bound, valid_flat
 
 pytestmark = pytest.mark.gpu
 
@@ -55,11 +55,11 @@ def test_half_cell_size(orc, kind, mode):
                 assert_bits_equal(g["parts"][k], ref["parts"][k], f"sink {k} after Step 4")
     else:
         A = valid_flat(box, ref["absbuf"])
-        U0 = np.abs(valid_flat(box, state))
-        d = np.abs(valid_flat(box, g["state"]) - valid_flat(box, ref["state"]))
-        lim = (ref["eta"] < 1.0) | (g["eta"] < 1.0)
-        ok = d <= 1e-12 * A + 4 * 2.0 ** -52 * U0
-        ok[:, lim] |= d[:, lim] <= 1e-9 * (A[:, lim] + U0[:, lim])
-        assert np.all(ok), f"state after Step 5: {np.count_nonzero(~ok)} cells off"
+        assert_state_within_bound(params, valid_flat(box, state), valid_flat(box, ref["buf"]), A, ref["eta"],
+                                  valid_flat(box, g["state"]), valid_flat(box, ref["state"]))
+        if kind == "sink":
+            for k in ("m", "px", "py", "pz"):
+                tol = sink_return_bound(params, box, state, parts, ref["parts"], k)
+                assert np.all(np.abs(g["parts"][k] - ref["parts"][k]) <= tol), k
     if kind == "sink":
         assert ref["counts"][0] > 0

@@ -67,3 +67,38 @@ def test_dual_tangent_matches_central_differences(orc, field):
                 continue  # omega or the kernel cells change inside [x - h, x + h]
         fd = (L(x0 + h) - L(x0 - h)) / (2 * h)
         assert fd == pytest.approx(want, rel=2e-6, abs=1e-9 * (abs(want) + 1e-3))
+
+
+def test_fourth_order_differences_agree_with_the_dual_tangents_at_1e8(orc):
+    """The finite-difference procedure of the GPU adjoint test
+    (helpers.fd_derivative) against the dual-number tangents on a clustered
+    box: within 1e-8 relative plus the quotient's rounding allowance, for all
+    eight variables; and that allowance settles at most half the checks."""
+    from oracle import dual
+
+    from helpers import fd_derivative
+
+    rng = np.random.default_rng(23)
+    box = syn.Box((24, 24, 24), 2)
+    state = syn.gas_state(rng, box)
+    parts = syn.particles(rng, box.n, 16, "feedback", clustered=8, nclusters=1)
+    params = syn.feedback_params()
+    R = rng.standard_normal((5,) + box.n[::-1])
+    G = orc.gather(params, box, state, parts)
+    total = decided = 0
+    for s in range(len(parts["x"])):
+        one = {k: parts[k][s:s + 1].copy() for k in FIELDS}
+        for f in FIELDS:
+            r = fd_derivative(orc, params, box, state, one, R, f, G[0, s])
+            if r is None:
+                continue
+            fd, floor = r
+            tang = {k: np.zeros(1) for k in FIELDS}
+            tang[f][0] = 1.0
+            _, tan = dual.pass_tangent(orc, params, box, state, one, tang, np.ones(box.n[::-1], bool))
+            want = math.fsum((R * tan).ravel())
+            total += 1
+            decided += floor <= 1e-9 * abs(fd)
+            assert abs(fd - want) <= 1e-8 * abs(want) + floor, (s, f, fd, want, floor)
+    assert total >= 16 * 7
+    assert decided >= total // 2

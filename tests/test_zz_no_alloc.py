@@ -73,3 +73,36 @@ def test_noalloc_rejects_more_particles_than_its_scratch_holds():
         pmp.pmp_deposit_noalloc(params, st, big, g, buf)
     assert e.value.code == 6
     assert torch.count_nonzero(buf.data).item() == 0
+
+
+def test_noalloc_skips_particles_outside_the_box(orc):
+    """Particles outside [0, n) (or with a NaN position) receive zero gathered
+    rows and deposit nothing; the others deposit as if alone."""
+    import torch
+
+    from paper_2509_18261_gb300 import pmp
+
+    box, state, parts, params = _inputs()
+    inside = {k: v[:500].copy() for k, v in parts.items()}
+    mixed = {k: v[:520].copy() for k, v in parts.items()}
+    n = box.n
+    bad = [(n[0] + 0.5, 1.0, 1.0), (-0.25, 3.0, 3.0), (1.0, float(n[1]), 1.0), (2.0, 2.0, -1e-300),
+           (float("nan"), 1.0, 1.0)]
+    for r in range(20):
+        x, y, z = bad[r % len(bad)]
+        mixed["x"][500 + r], mixed["y"][500 + r], mixed["z"][500 + r] = x, y, z
+    G_ref = orc.gather(params, box, state, inside)
+    buf_ref, abs_ref = box.empty(0.0), box.empty(0.0)
+    orc.deposit(params, box, state, inside, G_ref, buf_ref, abs_ref)
+    st = pmp.Mesh(torch.from_numpy(state).cuda(), box.n, box.g)
+    pd = pmp.parts_to_device(mixed)
+    for call in range(2):
+        buf = pmp.Mesh(torch.zeros((5, box.field_stride), dtype=torch.float64, device="cuda"), box.n, box.g)
+        g = torch.full((12, 520), float("nan"), dtype=torch.float64, device="cuda")
+        pmp.pmp_deposit_noalloc(params, st, pd, g, buf)
+        torch.cuda.synchronize()
+        gn = g.cpu().numpy()
+        assert_bits_equal(gn[:, :500], G_ref, f"gathered rows of the particles inside, call {call + 1}")
+        assert np.all(gn[:, 500:] == 0.0), "particles outside get zero rows"
+        assert_within_abs(box.grid(buf.data.cpu().numpy()), box.grid(buf_ref), box.grid(abs_ref),
+                          f"buffer: only the particles inside deposit, call {call + 1}")
