@@ -89,7 +89,7 @@ long long max_pairs_per_particle(double rK)
 }
 
 struct Layout {
-    size_t keys, ids, keys2, ids2, counts, slots, hosts, fr, wts, aux, queue, qcount, offsets, skeys, skeys2,
+    size_t keys, ids, keys2, ids2, counts, slots, hosts, fr, wts, aux, pa, queue, qcount, offsets, skeys, skeys2,
         svals, svals2, soffs, slong, scnt;
     size_t temp, temp_bytes, total;
     long long cap, aux_stride;
@@ -126,6 +126,8 @@ Layout layout(const pmp_params &p, long long n, long long nvalid, int mode)
     if (sink) {
         L.wts = take(8 * n1 * 3 * (size_t)W);
         L.aux = take(8 * 2 * (size_t)pmp::kRec * (size_t)(nvalid > 0 ? nvalid : 1));
+        // ATOMIC: each pair's removal a, stored by the fused deposit for Step 4
+        if (mode == PMP_MODE_ATOMIC) L.pa = take(8 * pairs);
     } else {
         L.queue = take(4 * (size_t)(nvalid > 0 ? nvalid : 1));
         L.qcount = take(8);
@@ -177,6 +179,7 @@ pmp::PlanPtrs plan_ptrs(const Layout &L, void *ws, const pmp_params &p, int mode
         pl.wts = reinterpret_cast<double *>(w + L.wts);
         pl.grec = reinterpret_cast<double *>(w + L.aux);
         pl.drec = pl.grec + (size_t)pmp::kRec * (size_t)(nvalid_rows(L) > 0 ? nvalid_rows(L) : 1);
+        pl.pa = mode == PMP_MODE_ATOMIC ? reinterpret_cast<double *>(w + L.pa) : nullptr;
     }
     pl.cap = (unsigned long long)L.cap;
     return pl;
@@ -321,6 +324,7 @@ pmp_status pmp_create(pmp_ctx **out, const pmp_params *params, pmp_stream stream
     c->plan_n = -1;
     c->plan_nvalid = -1;
     c->plan_mode = PMP_MODE_ATOMIC;
+    c->plan_has_a = false;
     c->repro_M = 28;
     c->timing = false;
     if (cudaGetDevice(&c->device) != cudaSuccess || cudaMalloc(&c->st, sizeof(pmp::DevStatus)) != cudaSuccess ||
@@ -546,6 +550,7 @@ static pmp_status gather_impl(pmp_ctx *ctx, const pmp_mesh *state, const pmp_par
     s = check_workspace(L, workspace, workspace_bytes);
     if (s) return s;
     ctx->plan_ws = nullptr;
+    ctx->plan_has_a = false;
     const KParams P = make_kparams(ctx->p, state->dx);
     const pmp::PlanPtrs pl = plan_ptrs(L, workspace, ctx->p, mode);
     char *w = static_cast<char *>(workspace);
@@ -609,6 +614,8 @@ static pmp_status gather_impl(pmp_ctx *ctx, const pmp_mesh *state, const pmp_par
     ctx->plan_n = q.count;
     ctx->plan_nvalid = nv;
     ctx->plan_mode = mode;
+    // the fused sink deposit stored each pair's removal for Step 4
+    ctx->plan_has_a = fused && ctx->p.kind == PMP_KIND_SINK && mode == PMP_MODE_ATOMIC && q.count > 0;
     return PMP_OK;
 }
 
@@ -798,7 +805,10 @@ pmp_status pmp_apply_limited(pmp_ctx *ctx, pmp_mesh *state, const pmp_mesh *buff
             Timed tm(ctx, "apply");
             pmp::launch_sink_eta_apply(P, S, state->data, B, buffer->data, pl.drec, eta_out, ctx->st, st);
         }
-        if (n > 0) {
+        if (n > 0 && ctx->plan_has_a) {
+            Timed tm(ctx, "return");
+            pmp::launch_return_sinks_stored(P, S, q, pl, ctx->st, st);
+        } else if (n > 0) {
             Timed tm(ctx, "return");
             pmp::launch_return_sinks(P, S, q, gathered, pl, ctx->st, st);
         }

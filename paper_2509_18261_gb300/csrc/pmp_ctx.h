@@ -19,6 +19,7 @@ struct pmp_ctx {
     long long plan_n;
     long long plan_nvalid;
     int plan_mode;
+    bool plan_has_a;  // the plan's workspace holds each sink pair's removal (fused ATOMIC deposit)
     int repro_M;  // App. A.1 safety margin M of the ROUNDED mode
     // per-kernel CUDA-event timing (pmp_timing_enable)
     bool timing;

@@ -29,6 +29,7 @@ struct PlanPtrs {
     double *wts;                      // sink: [n][3][2R+1] per-axis Gaussian factors
     double *grec;                     // sink: [valid cells][6] G records
     double *drec;                     // sink: [valid cells][6] D records
+    double *pa;                       // sink, fused ATOMIC deposit: [n * cap] each pair's removal a, by slot
     unsigned long long cap;           // slots per particle
 };
 
@@ -69,6 +70,12 @@ void launch_segment_sum(const KParams &P, const Box &S, const double *u, const B
                         unsigned *nlong, cudaStream_t stream);
 void launch_return_sinks(const KParams &P, const Box &S, const Parts &p, const double *G, const PlanPtrs &pl,
                          DevStatus *st, cudaStream_t stream);
+// Step 4 from the removals the fused ATOMIC deposit stored (pl.pa): a warp
+// per sink, lanes over its kernel cells, the sums reduced across the warp
+// (their order is not the canonical one; the ATOMIC mode has no bit-exact
+// contract).
+void launch_return_sinks_stored(const KParams &P, const Box &S, const Parts &p, const PlanPtrs &pl, DevStatus *st,
+                                cudaStream_t stream);
 
 void launch_backward_fb(const KParams &P, const Box &S, const double *u, const double *gU, const Parts &p,
                         const PlanPtrs &pl, const unsigned char *pass, const double *G, double *gout,

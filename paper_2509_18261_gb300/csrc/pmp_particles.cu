@@ -670,7 +670,7 @@ __global__ void __launch_bounds__(256, PMP_PASS1_MINB) k_pass1_fb(KParams P, Box
                         const double xa = a == 0 ? p.x[sjj] : (a == 1 ? p.y[sjj] : p.z[sjj]);
                         const double d = ((double)(h + o - R) + 0.5) - xa;
                         dt[i] = d;
-                        qt[i] = d * d;
+                        qt[i] = (0.5 * d) * d;  // half squares: exact halves of d * d
                     }
                 }
             }
@@ -696,13 +696,13 @@ __global__ void __launch_bounds__(256, PMP_PASS1_MINB) k_pass1_fb(KParams P, Box
                     unpack_host(pl.hosts[s], hx, hy, hz);
                     const int ix = j * 3 * W + (cell.i - hx + R), iy = j * 3 * W + W + (cell.j - hy + R),
                               iz = j * 3 * W + 2 * W + (cell.k - hz + R);
-                    const double dd = (qt[ix] + qt[iy]) + qt[iz];
+                    const double hd = (qt[ix] + qt[iy]) + qt[iz];
                     double U[NF], dU[NF];
                     load_cell(u, S, S.at(owner(cell.i, S.n0), owner(cell.j, S.n1), owner(cell.k, S.n2)), U);
                     const int jj = jb + j;
                     const double vc[3] = {rows[jj], rows[32 + jj], rows[64 + jj]};
-                    feedback_delta(wtab[cell.cnt], U, rows[96 + jj], rows[128 + jj], rows[160 + jj], vc, dt[ix],
-                                   dt[iy], dt[iz], dd, dU);
+                    feedback_delta_fast(wtab[cell.cnt], U, rows[96 + jj], rows[128 + jj], rows[160 + jj], vc,
+                                        dt[ix], dt[iy], dt[iz], hd, dU);
                     const long long bc = B.at(cell.i, cell.j, cell.k);
 #pragma unroll
                     for (int f = 0; f < NF; ++f) atomicAdd(b + (long long)f * B.fs + bc, dU[f]);
@@ -1016,6 +1016,7 @@ __global__ void __launch_bounds__(128) k_pass1_sink(KParams P, Box S, const doub
                     const double bh = kt[j] * w;
                     const double a = bh >= d0x ? bh : d0x;
                     atomicAdd(scr + B.at(cell.i, cell.j, cell.k), -a);
+                    if (pl.pa) pl.pa[slot] = a;  // Step 4 reads it back (launch_return_sinks_stored)
                 }
             }
             __syncwarp();
@@ -1028,16 +1029,21 @@ __global__ void __launch_bounds__(128) k_pass1_sink(KParams P, Box S, const doub
 // processing order and spreads their pairs over its lanes
 // ---------------------------------------------------------------------------
 
-// Feedback deposition value of one pair from precomputed centre offsets.
+// Feedback deposition value of one pair from precomputed centre offsets and
+// the half square hd = |d|^2 / 2: the canonical evaluation (feedback_delta)
+// or, for the plain atomic sums, feedback_delta_fast.
 __device__ __forceinline__ void fb_pair_delta_d(const double *__restrict__ u, const Box &S, const double *__restrict__ G,
                                                 long long gs, long long s, const PairCell &c, double w, double d0,
-                                                double d1, double d2, double dd, double dU[NF])
+                                                double d1, double d2, double hd, bool canonical, double dU[NF])
 {
     double U[NF];
     load_cell(u, S, S.at(owner(c.i, S.n0), owner(c.j, S.n1), owner(c.k, S.n2)), U);
     const double vc[3] = {__ldg(G + FB_VX * gs + s), __ldg(G + FB_VY * gs + s), __ldg(G + FB_VZ * gs + s)};
-    feedback_delta(w, U, __ldg(G + FB_Q * gs + s), __ldg(G + FB_E * gs + s), __ldg(G + FB_PV * gs + s), vc, d0, d1,
-                   d2, dd, dU);
+    const double q = __ldg(G + FB_Q * gs + s), e = __ldg(G + FB_E * gs + s), Pv = __ldg(G + FB_PV * gs + s);
+    if (canonical)
+        feedback_delta(w, U, q, e, Pv, vc, d0, d1, d2, hd + hd, dU);
+    else
+        feedback_delta_fast(w, U, q, e, Pv, vc, d0, d1, d2, hd, dU);
 }
 
 template <int R, bool FB>
@@ -1095,7 +1101,7 @@ __global__ void __launch_bounds__(256) k_deposit_atomic(KParams P, Box S, const 
                         const double xa = a == 0 ? __ldg(p.x + sj) : (a == 1 ? __ldg(p.y + sj) : __ldg(p.z + sj));
                         const double d = ((double)(h + o - R) + 0.5) - xa;
                         dt[i] = d;
-                        qt[i] = d * d;
+                        qt[i] = (0.5 * d) * d;  // half squares: exact halves of d * d
                     }
                 }
             }
@@ -1145,9 +1151,10 @@ __global__ void __launch_bounds__(256) k_deposit_atomic(KParams P, Box S, const 
                     unpack_host(__ldg(pl.hosts + s), hx, hy, hz);
                     const int ix = j * 3 * W + (cell.i - hx + R), iy = j * 3 * W + W + (cell.j - hy + R),
                               iz = j * 3 * W + 2 * W + (cell.k - hz + R);
-                    const double dd = (qt[ix] + qt[iy]) + qt[iz];
+                    const double hd = (qt[ix] + qt[iy]) + qt[iz];
                     const double w = cell.cnt == P.S3 ? 1.0 : wtab[cell.cnt];
-                    fb_pair_delta_d(u, S, G, p.count, s, cell, w, dt[ix], dt[iy], dt[iz], dd, dU);
+                    // ROUNDED (App. A.1) keeps the canonical evaluation; hd + hd is d . d exactly
+                    fb_pair_delta_d(u, S, G, p.count, s, cell, w, dt[ix], dt[iy], dt[iz], hd, E != nullptr, dU);
                 } else {
                     const double *wj = wt + j * 3 * W;
                     const double w = (wj[cell.i - ht[3 * j] + R] * wj[W + cell.j - ht[3 * j + 1] + R]) *
@@ -1396,6 +1403,50 @@ __global__ void __launch_bounds__(kSinkThreads) k_return_sinks(KParams P, Box S,
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < p.count; t += stride)
         return_sink_particle<R>(P, S, p, G, pl, st, wsm, t);
+}
+
+// Step 4 from the stored removals: a warp per sink of the processing order,
+// lane l over the sink's kernel cells l, l + 32, ...; each lane sums
+// b = eta a and b v of its cells (the D record holds v = p / rho and, after
+// Step 3, eta), then the warp adds the 32 partial sums.  Per pair: one
+// product and four additions of FP64 work, and loads of neighbouring cells'
+// records by neighbouring lanes.
+__global__ void __launch_bounds__(256) k_return_sinks_stored(KParams P, Box S, Parts p, PlanPtrs pl)
+{
+    const int lane = threadIdx.x & 31;
+    const long long nwarps = (long long)gridDim.x * (blockDim.x >> 5);
+    for (long long t = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); t < p.count; t += nwarps) {
+        const long long s = pl.perm ? (long long)pl.perm[t] : t;
+        if (pl.hosts[s] == kNoHost) continue;  // reported by the prologue
+        const unsigned long long b0 = (unsigned long long)t * pl.cap;
+        const unsigned nc = pl.counts[t];
+        double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+        for (unsigned q = lane; q < nc; q += 32) {
+            const PairCell c = unpack_pair(__ldg(pl.slots + b0 + q), P.R);
+            const double a = __ldg(pl.pa + b0 + q);
+            const double *r = pl.drec + vidx(S, owner(c.i, S.n0), owner(c.j, S.n1), owner(c.k, S.n2)) * kRec;
+            const double2 d0 = __ldg(reinterpret_cast<const double2 *>(r));
+            const double2 d1 = __ldg(reinterpret_cast<const double2 *>(r) + 1);
+            const double b = __ldg(r + 5) * a;
+            a0 = a0 - b;
+            a1 = fma(-b, d0.y, a1);
+            a2 = fma(-b, d1.x, a2);
+            a3 = fma(-b, d1.y, a3);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            a0 = a0 + __shfl_xor_sync(kFull, a0, o);
+            a1 = a1 + __shfl_xor_sync(kFull, a1, o);
+            a2 = a2 + __shfl_xor_sync(kFull, a2, o);
+            a3 = a3 + __shfl_xor_sync(kFull, a3, o);
+        }
+        if (lane == 0) {
+            p.m[s] = p.m[s] - a0 * P.V;
+            p.px[s] = p.px[s] - a1 * P.V;
+            p.py[s] = p.py[s] - a2 * P.V;
+            p.pz[s] = p.pz[s] - a3 * P.V;
+        }
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -1665,6 +1716,28 @@ void launch_segment_sum(const KParams &P, const Box &S, const double *u, const B
                                                                                        lens, offs, vals, longq,
                                                                                        nlong)));
     }
+}
+
+#ifndef PMP_SINK_RETURN_STORED_BPS
+#define PMP_SINK_RETURN_STORED_BPS 0
+#endif
+
+void launch_return_sinks_stored(const KParams &P, const Box &S, const Parts &p, const PlanPtrs &pl, DevStatus *st,
+                                cudaStream_t stream)
+{
+    (void)st;
+    if (p.count == 0) return;
+    // resident blocks only, so the sinks in flight are one window of the
+    // processing order; the window (8 sinks per block) is also kept near the
+    // L2's size in cell records
+    int dev = 0, nsm = 152, occ = 1;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_return_sinks_stored, 256, 0) != cudaSuccess || occ < 1)
+        occ = 1;
+    const unsigned nb = window_blocks(S, p.count, 8, 8.0 * kRec, 1.0, PMP_SINK_RETURN_STORED_BPS);
+    const long long cap = (long long)nsm * occ;
+    const unsigned grid = (unsigned)((long long)nb < cap ? (long long)nb : cap);
+    k_return_sinks_stored<<<grid, 256, 0, stream>>>(P, S, p, pl);
 }
 
 void launch_return_sinks(const KParams &P, const Box &S, const Parts &p, const double *G, const PlanPtrs &pl,
