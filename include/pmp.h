@@ -259,7 +259,11 @@ pmp_status pmp_fold_ghosts(pmp_ctx *ctx, pmp_mesh *buffer);
  * Order of work (sinks): eta is computed and the state updated in one pass
  *   over the cells, then Step 4 runs; Step 4 reads eta and the pre-update
  *   per-cell quantities kept in the workspace, so the result is that of the
- *   order the paper states (Step 4 before Step 5). */
+ *   order the paper states (Step 4 before Step 5).  Step 4 sums a sink's
+ *   kernel cells in canonical order, except after pmp_gather_deposit in the
+ *   ATOMIC mode: that deposit stores each pair's removal a in the workspace,
+ *   and Step 4 adds eta a over the cells in an order of its own (32 partial
+ *   sums per sink, then their sum), like the ATOMIC buffer sums. */
 pmp_status pmp_apply_limited(pmp_ctx *ctx, pmp_mesh *state, const pmp_mesh *buffer, pmp_particles *particles,
                              const double *gathered, double *eta_out, void *workspace, size_t workspace_bytes);
 

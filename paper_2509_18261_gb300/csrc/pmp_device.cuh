@@ -372,60 +372,6 @@ __device__ __forceinline__ void feedback_delta(double w, const double U[NF], dou
     dU[4] = fma(w, e, fma(vc[2], pr2, fma(vc[1], pr1, vc[0] * pr0)));
 }
 
-// FP32 -> FP64 of a normal FP32 value by integer operations (exact).
-__device__ __forceinline__ double f64_of_f32(float f)
-{
-    const unsigned b = __float_as_uint(f);
-    const unsigned long long e = (unsigned long long)(((b >> 23) & 0xffu) - 127u + 1023u);
-    return __longlong_as_double((long long)(((unsigned long long)(b & 0x80000000u) << 32) | (e << 52) |
-                                            ((unsigned long long)(b & 0x7fffffu) << 29)));
-}
-
-// 1 / sqrt(2 h) for h = |d|^2 / 2 in the normal FP32 range, for the atomic
-// deposit (no bit-exact contract there).  Seed: rsqrtf of h truncated to
-// FP32, times 1/sqrt(2) (relative error below 2^-21); then two Newton steps
-// y := y + y (1/2 - h y^2) in FP64, 3 operations each (the error squares:
-// about 2^-41, then a few units of the last place).  It replaces a square
-// root and a division, which take the FP64 pipe about 17 operations.
-__device__ __forceinline__ double rsqrt2_newton(double h)
-{
-    const float hf = f32_trunc(h);
-    double y = f64_of_f32(rsqrtf(hf) * 0.70710678f);
-#pragma unroll
-    for (int it = 0; it < 2; ++it) {
-        const double t = h * y;
-        const double r = fma(-t, y, 0.5);
-        y = fma(y, r, y);
-    }
-    return y;
-}
-
-// Eq. du as feedback_delta computes it, with the radial unit vector d/|d|
-// taken from rsqrt2_newton of hd = |d|^2 / 2 (summed from halved squares)
-// instead of sqrt and a division: the same value to a few units of the last
-// place.  For the ATOMIC deposit, whose sums carry no bit-exact contract;
-// the SORTED deposit keeps feedback_delta.  |d|^2 below the FP32 normal range
-// (a particle within 1e-19 cells of a cell centre) takes the division form.
-__device__ __forceinline__ void feedback_delta_fast(double w, const double U[NF], double q, double e, double Pv,
-                                                    const double vc[3], double d0, double d1, double d2, double hd,
-                                                    double dU[NF])
-{
-    const double rn = U[0] + q;
-    double s;
-    // hd >= 2^-126, tested on the bits (hd is a sum of squares, never -0 or
-    // NaN here): an FP64 comparison would take the FP64 pipe
-    if (__double_as_longlong(hd) >= 0x3810000000000000LL)
-        s = (w * Pv) * rsqrt2_newton(hd);
-    else
-        s = hd > 0.0 ? (w * Pv) / sqrt(hd + hd) : 0.0;
-    const double pr0 = s * d0, pr1 = s * d1, pr2 = s * d2;
-    dU[0] = w * q;
-    dU[1] = fma(w, fma(rn, vc[0], -U[1]), pr0);
-    dU[2] = fma(w, fma(rn, vc[1], -U[2]), pr1);
-    dU[3] = fma(w, fma(rn, vc[2], -U[3]), pr2);
-    dU[4] = fma(w, e, fma(vc[2], pr2, fma(vc[1], pr1, vc[0] * pr0)));
-}
-
 // Sink deposition function (Eq. accretion_function with the Truelove rate in
 // the max): a = max(K w, rho - rho_Tr), Delta U = -a (1, p inv, E inv).
 __device__ __forceinline__ void sink_delta(const KParams &P, const double U[NF], double K, double w, double dU[NF])

@@ -670,7 +670,7 @@ __global__ void __launch_bounds__(256, PMP_PASS1_MINB) k_pass1_fb(KParams P, Box
                         const double xa = a == 0 ? p.x[sjj] : (a == 1 ? p.y[sjj] : p.z[sjj]);
                         const double d = ((double)(h + o - R) + 0.5) - xa;
                         dt[i] = d;
-                        qt[i] = (0.5 * d) * d;  // half squares: exact halves of d * d
+                        qt[i] = d * d;
                     }
                 }
             }
@@ -696,13 +696,13 @@ __global__ void __launch_bounds__(256, PMP_PASS1_MINB) k_pass1_fb(KParams P, Box
                     unpack_host(pl.hosts[s], hx, hy, hz);
                     const int ix = j * 3 * W + (cell.i - hx + R), iy = j * 3 * W + W + (cell.j - hy + R),
                               iz = j * 3 * W + 2 * W + (cell.k - hz + R);
-                    const double hd = (qt[ix] + qt[iy]) + qt[iz];
+                    const double dd = (qt[ix] + qt[iy]) + qt[iz];
                     double U[NF], dU[NF];
                     load_cell(u, S, S.at(owner(cell.i, S.n0), owner(cell.j, S.n1), owner(cell.k, S.n2)), U);
                     const int jj = jb + j;
                     const double vc[3] = {rows[jj], rows[32 + jj], rows[64 + jj]};
-                    feedback_delta_fast(wtab[cell.cnt], U, rows[96 + jj], rows[128 + jj], rows[160 + jj], vc,
-                                        dt[ix], dt[iy], dt[iz], hd, dU);
+                    feedback_delta(wtab[cell.cnt], U, rows[96 + jj], rows[128 + jj], rows[160 + jj], vc, dt[ix],
+                                   dt[iy], dt[iz], dd, dU);
                     const long long bc = B.at(cell.i, cell.j, cell.k);
 #pragma unroll
                     for (int f = 0; f < NF; ++f) atomicAdd(b + (long long)f * B.fs + bc, dU[f]);
@@ -1029,21 +1029,16 @@ __global__ void __launch_bounds__(128) k_pass1_sink(KParams P, Box S, const doub
 // processing order and spreads their pairs over its lanes
 // ---------------------------------------------------------------------------
 
-// Feedback deposition value of one pair from precomputed centre offsets and
-// the half square hd = |d|^2 / 2: the canonical evaluation (feedback_delta)
-// or, for the plain atomic sums, feedback_delta_fast.
+// Feedback deposition value of one pair from precomputed centre offsets.
 __device__ __forceinline__ void fb_pair_delta_d(const double *__restrict__ u, const Box &S, const double *__restrict__ G,
                                                 long long gs, long long s, const PairCell &c, double w, double d0,
-                                                double d1, double d2, double hd, bool canonical, double dU[NF])
+                                                double d1, double d2, double dd, double dU[NF])
 {
     double U[NF];
     load_cell(u, S, S.at(owner(c.i, S.n0), owner(c.j, S.n1), owner(c.k, S.n2)), U);
     const double vc[3] = {__ldg(G + FB_VX * gs + s), __ldg(G + FB_VY * gs + s), __ldg(G + FB_VZ * gs + s)};
-    const double q = __ldg(G + FB_Q * gs + s), e = __ldg(G + FB_E * gs + s), Pv = __ldg(G + FB_PV * gs + s);
-    if (canonical)
-        feedback_delta(w, U, q, e, Pv, vc, d0, d1, d2, hd + hd, dU);
-    else
-        feedback_delta_fast(w, U, q, e, Pv, vc, d0, d1, d2, hd, dU);
+    feedback_delta(w, U, __ldg(G + FB_Q * gs + s), __ldg(G + FB_E * gs + s), __ldg(G + FB_PV * gs + s), vc, d0, d1,
+                   d2, dd, dU);
 }
 
 template <int R, bool FB>
@@ -1101,7 +1096,7 @@ __global__ void __launch_bounds__(256) k_deposit_atomic(KParams P, Box S, const 
                         const double xa = a == 0 ? __ldg(p.x + sj) : (a == 1 ? __ldg(p.y + sj) : __ldg(p.z + sj));
                         const double d = ((double)(h + o - R) + 0.5) - xa;
                         dt[i] = d;
-                        qt[i] = (0.5 * d) * d;  // half squares: exact halves of d * d
+                        qt[i] = d * d;
                     }
                 }
             }
@@ -1151,10 +1146,9 @@ __global__ void __launch_bounds__(256) k_deposit_atomic(KParams P, Box S, const 
                     unpack_host(__ldg(pl.hosts + s), hx, hy, hz);
                     const int ix = j * 3 * W + (cell.i - hx + R), iy = j * 3 * W + W + (cell.j - hy + R),
                               iz = j * 3 * W + 2 * W + (cell.k - hz + R);
-                    const double hd = (qt[ix] + qt[iy]) + qt[iz];
+                    const double dd = (qt[ix] + qt[iy]) + qt[iz];
                     const double w = cell.cnt == P.S3 ? 1.0 : wtab[cell.cnt];
-                    // ROUNDED (App. A.1) keeps the canonical evaluation; hd + hd is d . d exactly
-                    fb_pair_delta_d(u, S, G, p.count, s, cell, w, dt[ix], dt[iy], dt[iz], hd, E != nullptr, dU);
+                    fb_pair_delta_d(u, S, G, p.count, s, cell, w, dt[ix], dt[iy], dt[iz], dd, dU);
                 } else {
                     const double *wj = wt + j * 3 * W;
                     const double w = (wj[cell.i - ht[3 * j] + R] * wj[W + cell.j - ht[3 * j + 1] + R]) *

@@ -139,12 +139,13 @@ def sn_lambda_bound(U, D, dD):
     return lam, bound, amb, noroot
 
 
-def feedback_state_tolerance(U, D, A, tau=1e-12):
+def feedback_state_tolerance(U, D, A, tau=1e-12, dD=None):
     """Per cell and field, the largest |U_new(GPU) - U_new(oracle)| after
     Step 5 of a supernova pass when both buffers lie within tau * A of the
-    exact sum.  U, D, A: arrays (5, n) of the pre-update state, the oracle's
-    summed buffer and the oracle's sum of |Delta U|.  Returns (tol, ambiguous)."""
-    dD = tau * A
+    exact sum (or within dD, when given).  U, D, A: arrays (5, n) of the
+    pre-update state, the oracle's summed buffer and the oracle's sum of
+    |Delta U|.  Returns (tol, ambiguous)."""
+    dD = tau * A if dD is None else dD
     lam, bl, amb, _ = sn_lambda_bound(U, D, dD)
     unew = np.abs(U) + np.abs(D)
     tol = dD + 2.0 * U_ROUND * unew + 2.0 * U_ROUND * np.abs(D)
@@ -154,13 +155,17 @@ def feedback_state_tolerance(U, D, A, tau=1e-12):
     return tol, amb
 
 
-def sink_state_tolerance(U, D, A, eta, tau=1e-12):
+def sink_state_tolerance(U, D, A, eta, tau=1e-12, dD=None, dlim=None):
     """As feedback_state_tolerance for a sink pass.  eta (n,) is the oracle's.
     Where the limiter acts, eta = a_lim / a with a_lim a function of the
     state alone and a = -D_rho, whose relative error is tau (every term of
-    D_rho is negative, so A_rho = a): eta moves by at most eta (tau + 2u)."""
-    dD = tau * A
-    deta = eta * (tau + 4.0 * U_ROUND)
+    D_rho is negative, so A_rho = a): eta moves by at most eta (tau + 2u)
+    (plus dlim / a when a_lim is itself known only to within dlim)."""
+    dD = tau * A if dD is None else dD
+    deta = eta * (np.max(dD[0:1] / np.maximum(A[0:1], 1e-300), axis=0) + 4.0 * U_ROUND)
+    if dlim is not None:
+        # a_lim itself known only to within dlim (two evaluations of rho_Tr)
+        deta = deta + dlim / np.maximum(np.abs(D[0]), 1e-300)
     unew = np.abs(U) + np.abs(D)
     tol = eta * dD + np.abs(D) * deta + 4.0 * U_ROUND * (unew + np.abs(D))
     return tol

@@ -88,7 +88,7 @@ def valid_flat(box, arr):
     return box.valid(arr).reshape(5, -1)
 
 
-def state_tolerance(params, U0, D, A, eta, tau=1e-12, chunk=1 << 20):
+def state_tolerance(params, U0, D, A, eta, tau=1e-12, chunk=1 << 20, dD=None, dlim=None):
     """Per cell and field bound on |U_new(GPU atomic) - U_new(oracle)| after
     Step 5 (tests/bounds.py): U0 the pre-update state, D, A and eta the
     oracle's summed buffer, sum of |dU| and eta, as (5, n), (5, n), (n,).
@@ -100,12 +100,15 @@ def state_tolerance(params, U0, D, A, eta, tau=1e-12, chunk=1 << 20):
     amb = np.zeros(n, dtype=bool)
     for a in range(0, n, chunk):
         b = min(n, a + chunk)
+        dd = None if dD is None else dD[:, a:b]
         if params["kind"] == "feedback":
-            tol[:, a:b], amb[a:b] = feedback_state_tolerance(U0[:, a:b], D[:, a:b], A[:, a:b], tau)
+            tol[:, a:b], amb[a:b] = feedback_state_tolerance(U0[:, a:b], D[:, a:b], A[:, a:b], tau, dd)
         elif params["kind"] == "sink":
-            tol[:, a:b] = sink_state_tolerance(U0[:, a:b], D[:, a:b], A[:, a:b], eta[a:b], tau)
+            tol[:, a:b] = sink_state_tolerance(U0[:, a:b], D[:, a:b], A[:, a:b], eta[a:b], tau, dd,
+                                               None if dlim is None else dlim[a:b])
         else:
-            tol[:, a:b] = tau * A[:, a:b] + 4.0 * U_ROUND * (np.abs(U0[:, a:b]) + np.abs(D[:, a:b]))
+            tol[:, a:b] = (tau * A[:, a:b] if dd is None else dd) + \
+                4.0 * U_ROUND * (np.abs(U0[:, a:b]) + np.abs(D[:, a:b]))
     return tol, amb
 
 
