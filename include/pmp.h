@@ -464,6 +464,104 @@ pmp_status pmp_batch_hold_barriers(pmp_batch *batch, int32_t arrivals);
 /* Frees a batch's device tables (after its work has finished). */
 void pmp_batch_destroy(pmp_batch *batch);
 
+/* ------------------------------------------------------------------------ */
+/* The batched form on several ranks (Sec. 2.2, Step 2 across ranks)        */
+/* ------------------------------------------------------------------------ */
+
+/* Assigns the patches of one level to n_ranks ranks along a space-filling
+ * curve (Sec. 2.2 distributes boxes this way): patches ordered by the Morton
+ * (Z-order) code of pos[p] (host, [n][3], each 0 <= v < 2^20: the patch's
+ * place in the super-grid), ties by index, then cut into runs of consecutive
+ * patches of about equal total cost (cost[p] >= 1, e.g. valid cells plus a
+ * weight per particle); rank_of (host, n entries) receives the rank of each
+ * patch.  A patch costlier than a rank's share can leave a rank without
+ * patches.  Host only; PMP_ERR_ARG on a bad argument. */
+pmp_status pmp_partition_sfc(int32_t n_patches, const int32_t *pos, const int64_t *cost, int32_t n_ranks,
+                             int32_t *rank_of);
+
+/* What one rank holds and exchanges in a pass.  Its local patches are its
+ * owned patches (in global index order), one proxy per patch of another rank
+ * that neighbours an owned patch (global index order), and one zero patch
+ * (extents the largest of all patches) whose cells must stay zero.  A proxy
+ * carries, each pass, the neighbour's valid state cells that lie in an owned
+ * patch's ghost zone (exchange STATE, before the pass), the neighbour's
+ * buffer ghost cells that lie on owned cells (GHOST, after Step 1: the images
+ * App. A.2 adds, so the owned cells' sums have the one-rank order), and for
+ * sinks the neighbour's folded sums next to owned patches (FOLDED, after
+ * GHOST: Step 4 of an owned sink reads eta there).  Proxies and the zero patch
+ * have the zero patch as every neighbour.  Local patches lie patch after
+ * patch in a local arena, field strides rounded up to 32 doubles.
+ * A region is a box of cells of one local patch, lo <= c < hi per axis in its
+ * padded coordinates (-ng .. n + ng); a message to or from one peer is the
+ * concatenation of its regions, each [5][volume] doubles (field slowest, x
+ * fastest).  The messages of one exchange lie peer after peer (increasing
+ * rank) in one buffer; `offset` is the region's first double there.  The
+ * regions a rank sends to a peer are, in order, those the peer receives from
+ * it.  pmp_plan_* is host code (no GPU needed). */
+enum { PMP_XCH_STATE = 0, PMP_XCH_GHOST = 1, PMP_XCH_FOLDED = 2 };
+
+typedef struct {
+    int32_t peer;   /* the other rank */
+    int32_t patch;  /* local patch index on this rank */
+    int32_t lo[3], hi[3];
+    int64_t offset; /* first double of the region in the exchange's buffer */
+} pmp_region;
+
+typedef struct pmp_plan pmp_plan;
+
+/* Plan of rank `rank` for the global patches (neighbour tables as for
+ * pmp_batch_create; offsets and strides ignored) with ng ghost cells and the
+ * partition rank_of (host, n entries). */
+pmp_status pmp_plan_create(const pmp_patch *patches, int32_t n_patches, int32_t ng, const int32_t *rank_of,
+                           int32_t n_ranks, int32_t rank, pmp_plan **out);
+
+/* The rank's local patches: counts, and (each optional, n_local entries) the
+ * patches (extents, local neighbour table, local arena offsets and strides)
+ * and their global indices (-1 for the zero patch); the local arena length. */
+pmp_status pmp_plan_local(const pmp_plan *plan, int32_t *n_owned, int32_t *n_local, pmp_patch *local,
+                          int32_t *global_id, int64_t *arena_len);
+
+/* The regions of exchange `kind` that the rank sends (send = 1) or receives
+ * (send = 0); *n receives their number, at most `max` are written to out. */
+pmp_status pmp_plan_regions(const pmp_plan *plan, int32_t kind, int32_t send, pmp_region *out, int32_t max,
+                            int32_t *n);
+
+void pmp_plan_destroy(pmp_plan *plan);
+
+/* A batch of a rank's local patches: patches [0, n_owned) are worked on (the
+ * neighbour tables of these are checked as pmp_batch_create checks them,
+ * except that a neighbour that is not owned need not list the patch back);
+ * the others are proxies and the zero patch, only read.  Particles belong to
+ * owned patches (pmp_batch_set_particles: empty ranges for the others). */
+pmp_status pmp_batch_create_partial(pmp_ctx *ctx, const pmp_patch *patches, int32_t n_patches, int32_t n_owned,
+                                    int32_t ng, double dx, int64_t arena_len, pmp_batch **out);
+
+/* Parts of pmp_cycle_batched, for a pass whose exchanges run between them:
+ * PMP_BATCH_PART_DEPOSIT is Step 1 (gather and deposit), PMP_BATCH_PART_FINISH
+ * Steps 2-5 (the ghost sum, Step 4 for sinks, limiter and update).  Between
+ * the two the caller unpacks the GHOST (and for sinks FOLDED) exchanges into
+ * the buffer.  launch: PERSISTENT or PER_PATCH (PMP_ERR_ARG for GRAPH).
+ * Arguments and results otherwise as pmp_cycle_batched, for owned patches. */
+enum { PMP_BATCH_PART_ALL = 0, PMP_BATCH_PART_DEPOSIT = 1, PMP_BATCH_PART_FINISH = 2 };
+pmp_status pmp_cycle_batched_part(pmp_batch *batch, double *state, double *buffer, pmp_particles *particles,
+                                  double *gathered, double *eta_out, int32_t launch, int32_t part);
+
+/* Region lists on the device for packing and unpacking (slot 0..5, a list per
+ * slot; allocates device memory, synchronises the context's stream).  The
+ * regions' patches are local patches of the batch. */
+pmp_status pmp_batch_set_regions(pmp_batch *batch, int32_t slot, const pmp_region *regions, int32_t n);
+
+/* Packs the slot's regions of `arena` (a state or buffer arena of the batch)
+ * into msg (device, indexed by the regions' offsets).  folded = 1 packs the
+ * folded sums (App. A.2 order, as Step 2 forms them) of the buffer `arena`
+ * at valid cells of owned patches instead of the stored values.  Enqueued on
+ * the context's stream. */
+pmp_status pmp_batch_pack(pmp_batch *batch, int32_t slot, const double *arena, double *msg, int32_t folded);
+
+/* Writes the slot's regions of msg into `arena`.  Enqueued on the context's
+ * stream. */
+pmp_status pmp_batch_unpack(pmp_batch *batch, int32_t slot, const double *msg, double *arena);
+
 /* Size of the fixed device scratch of pmp_deposit_noalloc: 64 MiB, held on
  * every GPU that loads the library until the process exits. */
 #define PMP_NOALLOC_SCRATCH_BYTES (64u << 20)

@@ -381,6 +381,8 @@ def _batch_lib():
         dp = ctypes.POINTER(ctypes.c_double)
         L.or_batch_cycle.argtypes = [ctypes.POINTER(Params), ctypes.POINTER(BatchT), dp, dp, dp,
                                      ctypes.POINTER(Particles), dp, dp, ctypes.c_void_p]
+        L.or_batch_part.argtypes = [ctypes.POINTER(Params), ctypes.POINTER(BatchT), ctypes.c_int32, ctypes.c_int32,
+                                    dp, dp, ctypes.POINTER(Particles), dp, dp, ctypes.c_void_p]
         L.or_batch_fill_ghosts.argtypes = [ctypes.POINTER(BatchT), dp]
         L.or_batch_fold.argtypes = [ctypes.POINTER(BatchT), dp]
         L._batch_ready = True
@@ -417,3 +419,18 @@ def batch_cycle(params, batch, state, parts, first, dx=1.0, want_abs=False, want
                                      ctypes.byref(pp), _dp(G), _dp(eta), counts.ctypes.data_as(ctypes.c_void_p))
     _check(st, "batch_cycle")
     return dict(gathered=G, buf=buf, absbuf=absbuf, eta=eta, counts=counts)
+
+
+def batch_part(params, batch, owned, part, state, buf, parts, first, gathered, eta=None, dx=1.0):
+    """One part of a pass over the first `owned` patches of a batch (part 0:
+    Step 1; part 1: Steps 2-5), the other patches only read as neighbours;
+    state, buf: arenas, mutated in place; gathered: [rows][total count].
+    Returns the limiter counts of part 1."""
+    T, keep = _batch_struct(batch, first, dx)
+    counts = np.zeros(2, dtype=np.int64)
+    P = make_params(params)
+    pp = make_particles(parts)
+    st = _batch_lib().or_batch_part(ctypes.byref(P), ctypes.byref(T), int(owned), int(part), _dp(state), _dp(buf),
+                                    ctypes.byref(pp), _dp(gathered), _dp(eta), counts.ctypes.data_as(ctypes.c_void_p))
+    _check(st, "batch_part")
+    return counts

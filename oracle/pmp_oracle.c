@@ -1354,11 +1354,12 @@ static int batch_owner(const or_batch *T, int p, const int c[3], int w[3])
     return q;
 }
 
-/* Every ghost cell of every patch := the cell it stands for (all 5 fields). */
-static void batch_fill_ghosts(const or_batch *T, double *arena)
+/* Every ghost cell of the first `owned` patches := the cell it stands for
+ * (all 5 fields). */
+static void batch_fill_ghosts_n(const or_batch *T, int owned, double *arena)
 {
     int g = T->ng;
-    for (int p = 0; p < T->np; p++) {
+    for (int p = 0; p < owned; p++) {
         or_mesh M = batch_view(T, p, arena);
         for (int k = -g; k < M.n[2] + g; k++)
             for (int j = -g; j < M.n[1] + g; j++)
@@ -1380,10 +1381,10 @@ static void batch_fill_ghosts(const or_batch *T, double *arena)
  * c_a - n_p,a (o_a = -1) or c_a (o_a = 0), when that is inside q's padded
  * box.  With one patch whose neighbours are all itself this is the fold of a
  * periodic box.  Ghost cells are only read, so the fold runs in place. */
-static void batch_fold_arena(const or_batch *T, double *arena)
+static void batch_fold_arena_n(const or_batch *T, int owned, double *arena)
 {
     int g = T->ng;
-    for (int p = 0; p < T->np; p++) {
+    for (int p = 0; p < owned; p++) {
         or_mesh M = batch_view(T, p, arena);
         for (int f = 0; f < NF; f++)
             for (int k = 0; k < M.n[2]; k++)
@@ -1411,6 +1412,9 @@ static void batch_fold_arena(const or_batch *T, double *arena)
     }
 }
 
+static void batch_fill_ghosts(const or_batch *T, double *arena) { batch_fill_ghosts_n(T, T->np, arena); }
+static void batch_fold_arena(const or_batch *T, double *arena) { batch_fold_arena_n(T, T->np, arena); }
+
 static int64_t batch_arena_len(const or_batch *T)
 {
     int64_t len = 0;
@@ -1435,27 +1439,32 @@ static int batch_check(const or_params *P, const or_batch *T)
 void or_batch_fill_ghosts(const or_batch *T, double *arena) { batch_fill_ghosts(T, arena); }
 void or_batch_fold(const or_batch *T, double *arena) { batch_fold_arena(T, arena); }
 
-/* One PMP pass (Sec. 2.2) over a batch: Steps 1-5 with every patch's ghost
- * cells read through its neighbours (a private copy of the state with filled
- * ghosts; the caller's ghost cells are never read), particles of patch 0, 1,
- * ... each in index order, the cross-patch fold above, Step 4 with eta at a
- * ghost image taken from the cell it stands for, and the limited update of
- * every valid cell.  buf (and absbuf) receive the deposits including ghosts,
- * then the folded sums in valid cells.  eta_out gets one value per valid cell,
- * patch after patch (x fastest).  counts as for or_apply, summed. */
-int or_batch_cycle(const or_params *P, const or_batch *T, double *state, double *buf, double *absbuf,
-                   or_particles *p, double *gathered, double *eta_out, int64_t *counts)
+/* A private copy of the state whose first `owned` patches have their ghost
+ * cells filled from the cells they stand for (the caller's ghost cells are
+ * never read). */
+static double *batch_state_scratch(const or_batch *T, int owned, const double *state)
 {
-    int st = batch_check(P, T);
-    if (st) return st;
-    if (!p || !gathered || !state || !buf || p->count != T->first[T->np]) return OR_ERR_ARG;
     int64_t len = batch_arena_len(T);
     double *scratch = (double *)malloc(sizeof(double) * (size_t)len);
+    if (!scratch) return NULL;
+    memcpy(scratch, state, sizeof(double) * (size_t)len);
+    batch_fill_ghosts_n(T, owned, scratch);
+    return scratch;
+}
+
+/* First part of a pass over the first `owned` patches of a batch (Step 1):
+ * their buffers (and absbuf) zeroed, ghosts included, then the particles of
+ * patch 0, 1, ... each in index order gathered and deposited.  The other
+ * patches of the batch are only read, as neighbours (they stand for patches
+ * that another rank owns: their valid state cells must hold what those
+ * patches hold). */
+static int batch_part_deposit(const or_params *P, const or_batch *T, int owned, const double *state, double *buf,
+                              double *absbuf, or_particles *p, double *gathered)
+{
+    double *scratch = batch_state_scratch(T, owned, state);
     kcell *kc = alloc_kcells(P->r_K);
     if (!scratch || !kc) { free(scratch); free(kc); return OR_ERR_NOMEM; }
-    memcpy(scratch, state, sizeof(double) * (size_t)len);
-    batch_fill_ghosts(T, scratch);
-    for (int q = 0; q < T->np; q++) {
+    for (int q = 0; q < owned; q++) {
         or_mesh B = batch_view(T, q, buf);
         int64_t pc = (int64_t)(B.n[0] + 2 * B.ng) * (B.n[1] + 2 * B.ng) * (B.n[2] + 2 * B.ng);
         for (int f = 0; f < NF; f++)
@@ -1466,7 +1475,7 @@ int or_batch_cycle(const or_params *P, const or_batch *T, double *state, double 
     }
     int status = OR_OK;
     int64_t N = T->first[T->np];
-    for (int q = 0; q < T->np && !status; q++) {
+    for (int q = 0; q < owned && !status; q++) {
         or_mesh S = batch_view(T, q, scratch), B = batch_view(T, q, buf);
         int64_t f0 = T->first[q];
         or_particles pp = {T->first[q + 1] - f0, p->x + f0, p->y + f0, p->z + f0,
@@ -1480,29 +1489,45 @@ int or_batch_cycle(const or_params *P, const or_batch *T, double *state, double 
         int r = deposit_parts(P, &S, &pp, gathered + f0, N, &B, absbuf ? absbuf + T->offset[q] : NULL);
         if (r && !status) status = r;
     }
-    if (!status) {
-        batch_fold_arena(T, buf);
-        if (absbuf) batch_fold_arena(T, absbuf);
-    }
-    if (!status && P->kind == KIND_SINK) {
+    free(scratch);
+    free(kc);
+    return status;
+}
+
+/* Second part (Steps 2-5) over the first `owned` patches: the cross-patch
+ * fold of their buffers (images read from every neighbour's ghost cells),
+ * for sinks Step 4 with eta at a ghost image taken from the cell it stands
+ * for (a neighbour that stands for another rank's patch must hold that
+ * patch's folded sums in its valid buffer cells), and the limited update of
+ * their valid cells.  eta_out: one value per valid cell of those patches. */
+static int batch_part_finish(const or_params *P, const or_batch *T, int owned, double *state, double *buf,
+                             double *absbuf, or_particles *p, const double *gathered, double *eta_out, int64_t *counts)
+{
+    int status = OR_OK;
+    int64_t len = batch_arena_len(T), N = T->first[T->np];
+    batch_fold_arena_n(T, owned, buf);
+    if (absbuf) batch_fold_arena_n(T, owned, absbuf);
+    if (P->kind == KIND_SINK) {
+        double *scratch = batch_state_scratch(T, owned, state);
         double *bcopy = (double *)malloc(sizeof(double) * (size_t)len);
-        if (!bcopy) status = OR_ERR_NOMEM;
+        if (!scratch || !bcopy) status = OR_ERR_NOMEM;
         else {
             memcpy(bcopy, buf, sizeof(double) * (size_t)len);
-            batch_fill_ghosts(T, bcopy);
-            for (int q = 0; q < T->np && !status; q++) {
+            batch_fill_ghosts_n(T, owned, bcopy);
+            for (int q = 0; q < owned && !status; q++) {
                 or_mesh S = batch_view(T, q, scratch), B = batch_view(T, q, bcopy);
                 int64_t f0 = T->first[q];
                 or_particles pp = {T->first[q + 1] - f0, p->x + f0, p->y + f0, p->z + f0,
                                    p->m + f0, p->px + f0, p->py + f0, p->pz + f0, NULL};
                 status = return_parts(P, &S, &B, &pp, gathered + f0, N);
             }
-            free(bcopy);
         }
+        free(scratch);
+        free(bcopy);
     }
     if (!status) {
         int64_t tot[2] = {0, 0}, v = 0;
-        for (int q = 0; q < T->np; q++) {
+        for (int q = 0; q < owned; q++) {
             or_mesh S = batch_view(T, q, state), B = batch_view(T, q, buf);
             int64_t c2[2];
             or_apply(P, &S, &B, eta_out ? eta_out + v : NULL, c2);
@@ -1512,7 +1537,42 @@ int or_batch_cycle(const or_params *P, const or_batch *T, double *state, double 
         }
         if (counts) { counts[0] = tot[0]; counts[1] = tot[1]; }
     }
-    free(scratch);
-    free(kc);
     return status;
+}
+
+/* One PMP pass (Sec. 2.2) over a batch: Steps 1-5 with every patch's ghost
+ * cells read through its neighbours, particles of patch 0, 1, ... each in
+ * index order, the cross-patch fold above, Step 4 with eta at a ghost image
+ * taken from the cell it stands for, and the limited update of every valid
+ * cell.  buf (and absbuf) receive the deposits including ghosts, then the
+ * folded sums in valid cells.  eta_out gets one value per valid cell, patch
+ * after patch (x fastest).  counts as for or_apply, summed. */
+int or_batch_cycle(const or_params *P, const or_batch *T, double *state, double *buf, double *absbuf,
+                   or_particles *p, double *gathered, double *eta_out, int64_t *counts)
+{
+    int st = batch_check(P, T);
+    if (st) return st;
+    if (!p || !gathered || !state || !buf || p->count != T->first[T->np]) return OR_ERR_ARG;
+    st = batch_part_deposit(P, T, T->np, state, buf, absbuf, p, gathered);
+    if (!st) st = batch_part_finish(P, T, T->np, state, buf, absbuf, p, gathered, eta_out, counts);
+    return st;
+}
+
+/* The two parts of a pass over the first `owned` patches of a batch, for a
+ * rank of a decomposition whose other patches stand for neighbours owned
+ * elsewhere: part 0 is Step 1 (gather and deposit), part 1 Steps 2-5.
+ * Between them the caller brings in the ghost cells of those neighbours'
+ * buffers (their deposits that fall on owned cells) and, for sinks, their
+ * folded sums; before part 0 their valid state cells.  Run on one rank that
+ * owns every patch, part 0 then part 1 is or_batch_cycle. */
+int or_batch_part(const or_params *P, const or_batch *T, int32_t owned, int32_t part, double *state, double *buf,
+                  or_particles *p, double *gathered, double *eta_out, int64_t *counts)
+{
+    int st = batch_check(P, T);
+    if (st) return st;
+    if (!p || !gathered || !state || !buf || p->count != T->first[T->np] || owned < 0 || owned > T->np)
+        return OR_ERR_ARG;
+    if (part == 0) return batch_part_deposit(P, T, owned, state, buf, NULL, p, gathered);
+    if (part == 1) return batch_part_finish(P, T, owned, state, buf, NULL, p, gathered, eta_out, counts);
+    return OR_ERR_ARG;
 }

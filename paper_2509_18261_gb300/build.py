@@ -19,7 +19,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIBDIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIBDIR, "libpmp.so")
-SOURCES = ["pmp_api.cu", "pmp_particles.cu", "pmp_mesh.cu", "pmp_sort.cu", "pmp_noalloc.cu", "pmp_batch.cu", "pmp_probe.cu"]
+SOURCES = ["pmp_api.cu", "pmp_particles.cu", "pmp_mesh.cu", "pmp_sort.cu", "pmp_noalloc.cu", "pmp_batch.cu", "pmp_probe.cu", "pmp_exchange.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

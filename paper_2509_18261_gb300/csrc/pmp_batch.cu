@@ -48,6 +48,8 @@ constexpr int kCap = 512;  // candidate particles staged per chunk of a tile
 constexpr unsigned kFullMask = 0xffffffffu;
 constexpr unsigned long long kNoHostB = ~0ULL;
 constexpr unsigned long long kWaitNs = 4000000000ULL;  // grid-barrier wait limit
+constexpr int kPackThreads = 256;  // cells per pack item and block
+constexpr int kRegionSlots = 6;    // region lists a batch keeps for packing
 
 struct PatchDev {
     int n[3];
@@ -99,6 +101,7 @@ struct BArgs {
     Ctl *ctl;
     DevStatus *st;
     unsigned hold;  // arrivals a grid barrier waits for beyond the grid (0; 1 only to test the timeout)
+    int ph0, ph1;   // the phases [ph0, ph1] this launch runs (0 gather, 1 deposit, 2 Step 4, 3 apply)
 };
 
 // ---------------------------------------------------------------------------
@@ -774,41 +777,48 @@ __global__ void __launch_bounds__(kThreads, 2) k_batch_persistent(BArgs a)
     SmemT<R> &sm = *reinterpret_cast<SmemT<R> *>(smem_raw);
     const int wib = threadIdx.x >> 5;
     if (FB) fill_wtab(a.P, sm);
-    // phase 0: zeroing for the atomic strategy, then the gather (8 particles per item)
     const long long N = a.p.count;
     const long long ngrp = (N + kWarps - 1) / kWarps;
-    for (;;) {
-        const int it = next_item(&a.ctl->q[0], sm);
-        if (it >= a.nzero + ngrp) break;
-        if (it < a.nzero) {
-            zero_item(a, a.zero[it]);
-        } else {
-            const long long s = (long long)(it - a.nzero) * kWarps + wib;
-            if (s < N) gather_particle<R, FB>(a, s, sm);
+    // a grid barrier only between two phases this launch runs
+    const int last = FB && a.ph1 == 2 ? 1 : a.ph1;
+    // phase 0: zeroing for the atomic strategy, then the gather (8 particles per item)
+    if (a.ph0 <= 0) {
+        for (;;) {
+            const int it = next_item(&a.ctl->q[0], sm);
+            if (it >= a.nzero + ngrp) break;
+            if (it < a.nzero) {
+                zero_item(a, a.zero[it]);
+            } else {
+                const long long s = (long long)(it - a.nzero) * kWarps + wib;
+                if (s < N) gather_particle<R, FB>(a, s, sm);
+            }
         }
+        if (last == 0 || !grid_sync(a, sm)) return;
     }
-    if (!grid_sync(a, sm)) return;
     // phase 1: deposit
-    for (;;) {
-        const int it = next_item(&a.ctl->q[1], sm);
-        if (it >= a.ndep) break;
-        const DepItem d = a.dep[it];
-        if (d.strat == STRAT_ATOMIC) {
-            for (long long s = d.lo[0] + wib; s < d.hi[0]; s += kWarps) deposit_atomic_particle<R, FB>(a, d.patch, s, sm);
-        } else {
-            deposit_tile<R, FB>(a, d, sm);
+    if (a.ph0 <= 1) {
+        for (;;) {
+            const int it = next_item(&a.ctl->q[1], sm);
+            if (it >= a.ndep) break;
+            const DepItem d = a.dep[it];
+            if (d.strat == STRAT_ATOMIC) {
+                for (long long s = d.lo[0] + wib; s < d.hi[0]; s += kWarps)
+                    deposit_atomic_particle<R, FB>(a, d.patch, s, sm);
+            } else {
+                deposit_tile<R, FB>(a, d, sm);
+            }
         }
+        if (last == 1 || !grid_sync(a, sm)) return;
     }
-    if (!grid_sync(a, sm)) return;
     // phase 2: Step 4 (sinks)
-    if (!FB) {
+    if (!FB && a.ph0 <= 2) {
         for (;;) {
             const int it = next_item(&a.ctl->q[2], sm);
             if (it >= ngrp) break;
             const long long s = (long long)it * kWarps + wib;
             if (s < N) return_sink<R>(a, s, sm);
         }
-        if (!grid_sync(a, sm)) return;
+        if (last == 2 || !grid_sync(a, sm)) return;
     }
     // phase 3: summation, limiter, update
     unsigned nl = 0, nr = 0;
@@ -871,6 +881,65 @@ __global__ void __launch_bounds__(kThreads) k_batch_apply(BArgs a, int i0)
     flush_counts(a, nl, nr);
 }
 
+// ---------------------------------------------------------------------------
+// packing and unpacking of exchange regions (the batched form on several ranks)
+// ---------------------------------------------------------------------------
+
+// A region of one local patch: cells lo <= c < hi (padded coordinates), its
+// five fields at msg[off + f * vol + cell] (x fastest).
+struct PackRegion {
+    int patch;
+    int lo[3], hi[3];
+    int pad_;
+    long long off, vol;
+};
+// kPackCells consecutive cells of one region.
+struct PackItem {
+    int region, pad_;
+    long long c0;
+};
+
+__device__ __forceinline__ void region_cell(const PackRegion &r, long long c, int &i, int &j, int &k)
+{
+    const int nx = r.hi[0] - r.lo[0], ny = r.hi[1] - r.lo[1];
+    i = r.lo[0] + (int)(c % nx);
+    const long long t = c / nx;
+    j = r.lo[1] + (int)(t % ny);
+    k = r.lo[2] + (int)(t / ny);
+}
+
+// pack (to_msg) or unpack one item per block; folded: the folded sums of the
+// buffer (App. A.2 order) instead of the stored values (valid cells only)
+__global__ void __launch_bounds__(kPackThreads) k_batch_pack(BArgs a, const PackRegion *__restrict__ regs,
+                                                             const PackItem *__restrict__ items, const double *src,
+                                                             double *dst, int to_msg, int folded)
+{
+    const PackItem it = items[blockIdx.x];
+    const PackRegion r = regs[it.region];
+    const long long c = it.c0 + threadIdx.x;
+    if (c >= r.vol) return;
+    int i, j, k;
+    region_cell(r, c, i, j, k);
+    const PatchDev *T = a.T + r.patch;
+    const long long pc = pcell(T, i, j, k);
+    if (folded) {
+        double D[NF];
+        bool img;
+        folded_at(a, r.patch, i, j, k, D, img);
+#pragma unroll
+        for (int f = 0; f < NF; ++f) dst[r.off + (long long)f * r.vol + c] = D[f];
+        return;
+    }
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+        const long long m = r.off + (long long)f * r.vol + c, e = pc + (long long)f * T->fs;
+        if (to_msg)
+            dst[m] = src[e];
+        else
+            dst[e] = src[m];
+    }
+}
+
 }  // namespace
 }  // namespace pmp
 
@@ -919,6 +988,13 @@ struct pmp_batch {
     cudaStream_t cap_stream;
     const void *gkey[8];
     unsigned hold;  // see pmp_batch_hold_barriers
+    int n_owned;    // patches [0, n_owned) are worked on; the rest are only read
+    // region lists for pack / unpack (pmp_batch_set_regions), per slot: the
+    // regions and work items of up to kPackCells cells each
+    pmp::PackRegion *reg[pmp::kRegionSlots];
+    pmp::PackItem *pitem[pmp::kRegionSlots];
+    int nreg[pmp::kRegionSlots], npitem[pmp::kRegionSlots];
+    std::vector<pmp::PackRegion> reg_h[pmp::kRegionSlots];
 };
 
 namespace {
@@ -978,7 +1054,7 @@ void tiles(const pmp_patch &pp, int g, int p, int strat, std::vector<DepItem> &o
 pmp_status build_items(pmp_batch *b)
 {
     const int np = b->np, g = b->ng;
-    std::vector<int> order(np);
+    std::vector<int> order(b->n_owned);
     std::iota(order.begin(), order.end(), 0);
     std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
         return (b->first[x + 1] - b->first[x]) > (b->first[y + 1] - b->first[y]);
@@ -1086,6 +1162,8 @@ BArgs make_args(pmp_batch *b, double *state, double *buffer, const pmp_particles
     a.ctl = b->ctl;
     a.st = b->ctx->st;
     a.hold = b->hold;
+    a.ph0 = 0;
+    a.ph1 = 3;
     return a;
 }
 
@@ -1169,17 +1247,20 @@ cudaError_t per_patch(pmp_batch *b, const BArgs &a, cudaStream_t st)
 {
     using namespace pmp;
     const size_t sm = b->smem;
-    for (int p = 0; p < b->np; ++p)
-        if (b->zero_hi[p] > b->zero_lo[p])
-            k_batch_zero<<<(unsigned)(b->zero_hi[p] - b->zero_lo[p]), kThreads, 0, st>>>(a, b->zero_lo[p]);
-    for (int p = 0; p < b->np; ++p) {
-        const long long s0 = b->first[p], s1 = b->first[p + 1];
-        if (s1 > s0)
-            k_batch_gather<R, FB><<<(unsigned)((s1 - s0 + kWarps - 1) / kWarps), kThreads, sm, st>>>(a, s0, s1);
+    if (a.ph0 <= 1) {
+        for (int p = 0; p < b->np; ++p)
+            if (b->zero_hi[p] > b->zero_lo[p])
+                k_batch_zero<<<(unsigned)(b->zero_hi[p] - b->zero_lo[p]), kThreads, 0, st>>>(a, b->zero_lo[p]);
+        for (int p = 0; p < b->np; ++p) {
+            const long long s0 = b->first[p], s1 = b->first[p + 1];
+            if (s1 > s0)
+                k_batch_gather<R, FB><<<(unsigned)((s1 - s0 + kWarps - 1) / kWarps), kThreads, sm, st>>>(a, s0, s1);
+        }
+        for (int p = 0; p < b->np; ++p)
+            if (b->dep_hi[p] > b->dep_lo[p])
+                k_batch_deposit<R, FB><<<(unsigned)(b->dep_hi[p] - b->dep_lo[p]), kThreads, sm, st>>>(a, b->dep_lo[p]);
     }
-    for (int p = 0; p < b->np; ++p)
-        if (b->dep_hi[p] > b->dep_lo[p])
-            k_batch_deposit<R, FB><<<(unsigned)(b->dep_hi[p] - b->dep_lo[p]), kThreads, sm, st>>>(a, b->dep_lo[p]);
+    if (a.ph1 < 2) return cudaGetLastError();
     if (!FB) {
         for (int p = 0; p < b->np; ++p) {
             const long long s0 = b->first[p], s1 = b->first[p + 1];
@@ -1259,13 +1340,14 @@ int bin_of(const pmp_batch *b, int p)
 
 extern "C" {
 
-pmp_status pmp_batch_create(pmp_ctx *ctx, const pmp_patch *patches, int32_t n_patches, int32_t ng, double dx,
-                            int64_t arena_len, pmp_batch **out)
+static pmp_status batch_create(pmp_ctx *ctx, const pmp_patch *patches, int32_t n_patches, int32_t n_owned, int32_t ng,
+                               double dx, int64_t arena_len, pmp_batch **out)
 {
     if (!out) return PMP_ERR_ARG;
     *out = nullptr;
     if (!ctx || !patches || n_patches < 1 || ng < 0 || !std::isfinite(dx) || !(dx > 0.0) || arena_len < 1)
         return PMP_ERR_ARG;
+    if (n_owned < 0 || n_owned > n_patches) return PMP_ERR_ARG;
     if (ctx->p.kind == PMP_KIND_MASS) return PMP_ERR_ARG;  // the batched form covers supernovae and sinks
     const int R = (int)std::ceil(ctx->p.r_K);
     if (ng < R) return PMP_ERR_GHOST_TOO_THIN;
@@ -1297,21 +1379,22 @@ pmp_status pmp_batch_create(pmp_ctx *ctx, const pmp_patch *patches, int32_t n_pa
             for (int oy = -1; oy <= 1; ++oy)
                 for (int ox = -1; ox <= 1; ++ox) {
                     if (!ox && !oy && !oz) continue;
-                    const int q = pp.neighbour[t];
+                    const int q = pp.neighbour[t++];
                     if (q < 0 || q >= n_patches) return PMP_ERR_ARG;
+                    if (p >= n_owned) continue;  // proxies and the zero patch: only read
                     const int o[3] = {ox, oy, oz};
                     for (int a = 0; a < 3; ++a)
                         if (o[a] == 0 && patches[q].n[a] != pp.n[a]) return PMP_ERR_ARG;
-                    // the reverse offset leads back
+                    // the reverse offset leads back (between owned patches)
                     const int rt = ((1 - oz) * 3 + (1 - oy)) * 3 + (1 - ox);
-                    if (patches[q].neighbour[rt > 13 ? rt - 1 : rt] != p) return PMP_ERR_ARG;
-                    ++t;
+                    if (q < n_owned && patches[q].neighbour[rt > 13 ? rt - 1 : rt] != p) return PMP_ERR_ARG;
                 }
     }
     pmp_batch *b = new (std::nothrow) pmp_batch();
     if (!b) return PMP_ERR_ARG;
     b->ctx = ctx;
     b->np = n_patches;
+    b->n_owned = n_owned;
     b->ng = ng;
     b->R = R;
     b->W3 = (2 * R + 1) * (2 * R + 1) * (2 * R + 1);
@@ -1355,9 +1438,25 @@ pmp_status pmp_batch_create(pmp_ctx *ctx, const pmp_patch *patches, int32_t n_pa
     return PMP_OK;
 }
 
+pmp_status pmp_batch_create(pmp_ctx *ctx, const pmp_patch *patches, int32_t n_patches, int32_t ng, double dx,
+                            int64_t arena_len, pmp_batch **out)
+{
+    return batch_create(ctx, patches, n_patches, n_patches, ng, dx, arena_len, out);
+}
+
+pmp_status pmp_batch_create_partial(pmp_ctx *ctx, const pmp_patch *patches, int32_t n_patches, int32_t n_owned,
+                                    int32_t ng, double dx, int64_t arena_len, pmp_batch **out)
+{
+    return batch_create(ctx, patches, n_patches, n_owned, ng, dx, arena_len, out);
+}
+
 void pmp_batch_destroy(pmp_batch *b)
 {
     if (!b) return;
+    for (int k = 0; k < pmp::kRegionSlots; ++k) {
+        cudaFree(b->reg[k]);
+        cudaFree(b->pitem[k]);
+    }
     if (b->graph) cudaGraphExecDestroy(b->graph);
     if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
     cudaFree(b->T);
@@ -1531,6 +1630,107 @@ pmp_status pmp_cycle_batched(pmp_batch *b, double *state, double *buffer, pmp_pa
         if (e == cudaSuccess) e = cudaGraphLaunch(b->graph, st);
     }
     return e == cudaSuccess ? PMP_OK : PMP_ERR_CUDA;
+}
+
+pmp_status pmp_cycle_batched_part(pmp_batch *b, double *state, double *buffer, pmp_particles *particles,
+                                  double *gathered, double *eta_out, int32_t launch, int32_t part)
+{
+    if (part == PMP_BATCH_PART_ALL) return pmp_cycle_batched(b, state, buffer, particles, gathered, eta_out, launch);
+    if (!b || !state || !buffer) return PMP_ERR_ARG;
+    if (part != PMP_BATCH_PART_DEPOSIT && part != PMP_BATCH_PART_FINISH) return PMP_ERR_ARG;
+    if (launch != PMP_BATCH_PERSISTENT && launch != PMP_BATCH_PER_PATCH) return PMP_ERR_ARG;
+    if (((reinterpret_cast<uintptr_t>(state) | reinterpret_cast<uintptr_t>(buffer)) & 7) != 0) return PMP_ERR_ARG;
+    {
+        const double *s0 = state, *s1 = state + b->arena_len, *b0 = buffer, *b1 = buffer + b->arena_len;
+        if (s0 < b1 && b0 < s1) return PMP_ERR_ARG;
+    }
+    pmp_status s = check_particles(b, particles, gathered);
+    if (s) return s;
+    if (b->first[b->np] > 0 && !b->om) return PMP_ERR_ARG;
+    BArgs a = make_args(b, state, buffer, particles, gathered, eta_out);
+    a.ph0 = part == PMP_BATCH_PART_DEPOSIT ? 0 : 2;
+    a.ph1 = part == PMP_BATCH_PART_DEPOSIT ? 1 : 3;
+    const cudaError_t e = launch == PMP_BATCH_PER_PATCH ? enqueue_per_patch(b, a, b->ctx->stream)
+                                                        : enqueue_persistent(b, a, b->ctx->stream);
+    return e == cudaSuccess ? PMP_OK : PMP_ERR_CUDA;
+}
+
+pmp_status pmp_batch_set_regions(pmp_batch *b, int32_t slot, const pmp_region *regions, int32_t n)
+{
+    if (!b || slot < 0 || slot >= pmp::kRegionSlots || n < 0 || (n > 0 && !regions)) return PMP_ERR_ARG;
+    std::vector<pmp::PackRegion> R(n);
+    std::vector<pmp::PackItem> I;
+    for (int r = 0; r < n; ++r) {
+        const pmp_region &g = regions[r];
+        if (g.patch < 0 || g.patch >= b->np || g.offset < 0) return PMP_ERR_ARG;
+        const pmp_patch &pp = b->patches[g.patch];
+        pmp::PackRegion &d = R[r];
+        std::memset(&d, 0, sizeof(d));
+        d.patch = g.patch;
+        for (int a = 0; a < 3; ++a) {
+            if (g.lo[a] < -b->ng || g.hi[a] > pp.n[a] + b->ng || g.lo[a] >= g.hi[a]) return PMP_ERR_ARG;
+            d.lo[a] = g.lo[a];
+            d.hi[a] = g.hi[a];
+        }
+        d.off = g.offset;
+        d.vol = (long long)(g.hi[0] - g.lo[0]) * (g.hi[1] - g.lo[1]) * (g.hi[2] - g.lo[2]);
+        for (long long c = 0; c < d.vol; c += pmp::kPackThreads) {
+            pmp::PackItem it;
+            it.region = r;
+            it.pad_ = 0;
+            it.c0 = c;
+            I.push_back(it);
+        }
+    }
+    if (cudaStreamSynchronize(b->ctx->stream) != cudaSuccess) return PMP_ERR_CUDA;
+    cudaFree(b->reg[slot]);
+    cudaFree(b->pitem[slot]);
+    b->reg[slot] = nullptr;
+    b->pitem[slot] = nullptr;
+    b->nreg[slot] = b->npitem[slot] = 0;
+    b->reg_h[slot].clear();
+    if (n == 0) return PMP_OK;
+    if (cudaMalloc(&b->reg[slot], sizeof(pmp::PackRegion) * R.size()) != cudaSuccess ||
+        cudaMalloc(&b->pitem[slot], sizeof(pmp::PackItem) * I.size()) != cudaSuccess ||
+        cudaMemcpy(b->reg[slot], R.data(), sizeof(pmp::PackRegion) * R.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(b->pitem[slot], I.data(), sizeof(pmp::PackItem) * I.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+        return PMP_ERR_CUDA;
+    b->nreg[slot] = n;
+    b->npitem[slot] = (int)I.size();
+    b->reg_h[slot] = R;
+    return PMP_OK;
+}
+
+static pmp_status pack_impl(pmp_batch *b, int32_t slot, const double *src, double *dst, int to_msg, int folded)
+{
+    if (!b || slot < 0 || slot >= pmp::kRegionSlots || !src || !dst) return PMP_ERR_ARG;
+    if (b->npitem[slot] == 0) return PMP_OK;
+    pmp_particles none;
+    std::memset(&none, 0, sizeof(none));
+    const double *arena = to_msg ? src : dst;
+    BArgs a = make_args(b, const_cast<double *>(arena), const_cast<double *>(arena), &none, nullptr, nullptr);
+    pmp::k_batch_pack<<<(unsigned)b->npitem[slot], pmp::kPackThreads, 0, b->ctx->stream>>>(
+        a, b->reg[slot], b->pitem[slot], src, dst, to_msg, folded);
+    return cudaGetLastError() == cudaSuccess ? PMP_OK : PMP_ERR_CUDA;
+}
+
+pmp_status pmp_batch_pack(pmp_batch *b, int32_t slot, const double *arena, double *msg, int32_t folded)
+{
+    if (folded != 0 && folded != 1) return PMP_ERR_ARG;
+    if (b && folded && slot >= 0 && slot < pmp::kRegionSlots) {
+        // folded sums are formed at valid cells of owned patches only
+        for (const auto &r : b->reg_h[slot]) {
+            if (r.patch >= b->n_owned) return PMP_ERR_ARG;
+            for (int a = 0; a < 3; ++a)
+                if (r.lo[a] < 0 || r.hi[a] > b->patches[r.patch].n[a]) return PMP_ERR_ARG;
+        }
+    }
+    return pack_impl(b, slot, arena, msg, 1, folded);
+}
+
+pmp_status pmp_batch_unpack(pmp_batch *b, int32_t slot, const double *msg, double *arena)
+{
+    return pack_impl(b, slot, msg, arena, 0, 0);
 }
 
 pmp_status pmp_batch_hold_barriers(pmp_batch *b, int32_t arrivals)

@@ -34,7 +34,12 @@ EXPORTS = [
     "pmp_batch_create", "pmp_batch_set_particles", "pmp_batch_set_strategy", "pmp_batch_strategies",
     "pmp_batch_autotune", "pmp_cycle_batched", "pmp_batch_info", "pmp_batch_hold_barriers", "pmp_batch_destroy",
     "pmp_probe_threads", "pmp_probe_chains", "pmp_probe_fp64", "pmp_probe_atomic",
+    "pmp_partition_sfc", "pmp_plan_create", "pmp_plan_local", "pmp_plan_regions", "pmp_plan_destroy",
+    "pmp_batch_create_partial", "pmp_cycle_batched_part", "pmp_batch_set_regions", "pmp_batch_pack",
+    "pmp_batch_unpack",
 ]
+PART_ALL, PART_DEPOSIT, PART_FINISH = 0, 1, 2
+XCH_STATE, XCH_GHOST, XCH_FOLDED = 0, 1, 2
 PERSISTENT, PER_PATCH, GRAPH = 0, 1, 2
 LAUNCHES = {"persistent": PERSISTENT, "per_patch": PER_PATCH, "graph": GRAPH}
 OWNER_CUBE, OWNER_ROWS, STRAT_ATOMIC = 0, 1, 2
@@ -74,6 +79,11 @@ class _KernelTime(ctypes.Structure):
 class _Patch(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int32 * 3), ("neighbour", ctypes.c_int32 * 26), ("offset", ctypes.c_int64),
                 ("field_stride", ctypes.c_int64)]
+
+
+class _Region(ctypes.Structure):
+    _fields_ = [("peer", ctypes.c_int32), ("patch", ctypes.c_int32), ("lo", ctypes.c_int32 * 3),
+                ("hi", ctypes.c_int32 * 3), ("offset", ctypes.c_int64)]
 
 
 class _Particles(ctypes.Structure):
@@ -132,6 +142,19 @@ def load():
         "pmp_probe_chains": ([], i32),
         "pmp_probe_fp64": ([vp, i32, i32, vp], i32),
         "pmp_probe_atomic": ([vp, i64, i64, i32, vp], i32),
+        "pmp_partition_sfc": ([i32, ctypes.POINTER(i32), ctypes.POINTER(i64), i32, ctypes.POINTER(i32)], i32),
+        "pmp_plan_create": ([ctypes.POINTER(_Patch), i32, i32, ctypes.POINTER(i32), i32, i32, ctypes.POINTER(vp)],
+                            i32),
+        "pmp_plan_local": ([vp, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(_Patch),
+                            ctypes.POINTER(i32), ctypes.POINTER(i64)], i32),
+        "pmp_plan_regions": ([vp, i32, i32, ctypes.POINTER(_Region), i32, ctypes.POINTER(i32)], i32),
+        "pmp_plan_destroy": ([vp], None),
+        "pmp_batch_create_partial": ([vp, ctypes.POINTER(_Patch), i32, i32, i32, ctypes.c_double, i64,
+                                      ctypes.POINTER(vp)], i32),
+        "pmp_cycle_batched_part": ([vp, vp, vp, Pa, vp, vp, i32, i32], i32),
+        "pmp_batch_set_regions": ([vp, i32, ctypes.POINTER(_Region), i32], i32),
+        "pmp_batch_pack": ([vp, i32, vp, vp, i32], i32),
+        "pmp_batch_unpack": ([vp, i32, vp, vp], i32),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -394,19 +417,19 @@ class BatchHandle:
     ``dims`` (np, 3), ``nb`` (np, 26), ``offset`` and ``field_stride`` (np)
     describe the patches (host arrays); ``ctx`` fixes the interaction kind."""
 
-    def __init__(self, ctx, dims, nb, offset, field_stride, ng, arena_len, dx=1.0):
+    def __init__(self, ctx, dims, nb, offset, field_stride, ng, arena_len, dx=1.0, n_owned=None):
         L = load()
         n = len(dims)
-        arr = (_Patch * n)()
-        for p in range(n):
-            arr[p].n = (ctypes.c_int32 * 3)(*[int(v) for v in dims[p]])
-            arr[p].neighbour = (ctypes.c_int32 * 26)(*[int(v) for v in nb[p]])
-            arr[p].offset = int(offset[p])
-            arr[p].field_stride = int(field_stride[p])
+        arr = _patch_array(dims, nb, offset, field_stride)
         ctx._sync_stream()
         h = ctypes.c_void_p()
-        _check("pmp_batch_create", L.pmp_batch_create(ctx.h, arr, n, int(ng), float(dx), int(arena_len),
-                                                      ctypes.byref(h)))
+        if n_owned is None:
+            _check("pmp_batch_create", L.pmp_batch_create(ctx.h, arr, n, int(ng), float(dx), int(arena_len),
+                                                          ctypes.byref(h)))
+        else:
+            _check("pmp_batch_create_partial", L.pmp_batch_create_partial(ctx.h, arr, n, int(n_owned), int(ng),
+                                                                          float(dx), int(arena_len),
+                                                                          ctypes.byref(h)))
         self.h, self.ctx, self.np = h, ctx, n
 
     def close(self):
@@ -421,8 +444,124 @@ class BatchHandle:
             pass
 
 
+def _patch_array(dims, nb, offset=None, field_stride=None):
+    n = len(dims)
+    arr = (_Patch * n)()
+    for p in range(n):
+        arr[p].n = (ctypes.c_int32 * 3)(*[int(v) for v in dims[p]])
+        arr[p].neighbour = (ctypes.c_int32 * 26)(*[int(v) for v in nb[p]])
+        arr[p].offset = int(offset[p]) if offset is not None else 0
+        arr[p].field_stride = int(field_stride[p]) if field_stride is not None else 0
+    return arr
+
+
 def pmp_batch_create(ctx, dims, nb, offset, field_stride, ng, arena_len, dx=1.0):
     return BatchHandle(ctx, dims, nb, offset, field_stride, ng, arena_len, dx)
+
+
+def pmp_batch_create_partial(ctx, dims, nb, offset, field_stride, n_owned, ng, arena_len, dx=1.0):
+    return BatchHandle(ctx, dims, nb, offset, field_stride, ng, arena_len, dx, n_owned=n_owned)
+
+
+def pmp_cycle_batched_part(batch, state, buffer, parts, gathered, eta_out=None, launch="persistent", part=PART_ALL):
+    pp = _parts(parts)
+    batch.ctx._sync_stream()
+    _check("pmp_cycle_batched_part", load().pmp_cycle_batched_part(batch.h, _ptr(state), _ptr(buffer),
+                                                                   ctypes.byref(pp), _ptr(gathered), _ptr(eta_out),
+                                                                   LAUNCHES.get(launch, launch), int(part)))
+
+
+def _region_array(regions):
+    arr = (_Region * max(len(regions), 1))()
+    for i, r in enumerate(regions):
+        arr[i].peer, arr[i].patch = int(r["peer"]), int(r["patch"])
+        arr[i].lo = (ctypes.c_int32 * 3)(*[int(v) for v in r["lo"]])
+        arr[i].hi = (ctypes.c_int32 * 3)(*[int(v) for v in r["hi"]])
+        arr[i].offset = int(r["offset"])
+    return arr
+
+
+def pmp_batch_set_regions(batch, slot, regions):
+    batch.ctx._sync_stream()
+    _check("pmp_batch_set_regions", load().pmp_batch_set_regions(batch.h, int(slot), _region_array(regions),
+                                                                 len(regions)))
+
+
+def pmp_batch_pack(batch, slot, arena, msg, folded=False):
+    batch.ctx._sync_stream()
+    _check("pmp_batch_pack", load().pmp_batch_pack(batch.h, int(slot), _ptr(arena), _ptr(msg), 1 if folded else 0))
+
+
+def pmp_batch_unpack(batch, slot, msg, arena):
+    batch.ctx._sync_stream()
+    _check("pmp_batch_unpack", load().pmp_batch_unpack(batch.h, int(slot), _ptr(msg), _ptr(arena)))
+
+
+# host-only plan calls (no GPU needed)
+
+def pmp_partition_sfc(pos, cost, n_ranks):
+    """rank_of per patch (list) from super-grid positions (n, 3) and costs."""
+    n = len(pos)
+    P = (ctypes.c_int32 * (3 * n))(*[int(v) for row in pos for v in row])
+    C = (ctypes.c_int64 * n)(*[int(v) for v in cost])
+    out = (ctypes.c_int32 * n)()
+    _check("pmp_partition_sfc", load().pmp_partition_sfc(n, P, C, int(n_ranks), out))
+    return list(out)
+
+
+class PlanHandle:
+    """An opaque pmp_plan (pmp_plan_create / pmp_plan_destroy)."""
+
+    def __init__(self, dims, nb, ng, rank_of, n_ranks, rank):
+        n = len(dims)
+        arr = _patch_array(dims, nb)
+        ro = (ctypes.c_int32 * n)(*[int(v) for v in rank_of])
+        h = ctypes.c_void_p()
+        _check("pmp_plan_create", load().pmp_plan_create(arr, n, int(ng), ro, int(n_ranks), int(rank),
+                                                         ctypes.byref(h)))
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().pmp_plan_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def pmp_plan_create(dims, nb, ng, rank_of, n_ranks, rank):
+    return PlanHandle(dims, nb, ng, rank_of, n_ranks, rank)
+
+
+def pmp_plan_local(plan):
+    """dict(n_owned, dims (n, 3), nb (n, 26), offset, field_stride, global_id, arena_len)."""
+    L = load()
+    no, nl, al = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int64()
+    _check("pmp_plan_local", L.pmp_plan_local(plan.h, ctypes.byref(no), ctypes.byref(nl), None, None,
+                                              ctypes.byref(al)))
+    arr = (_Patch * nl.value)()
+    gid = (ctypes.c_int32 * nl.value)()
+    _check("pmp_plan_local", L.pmp_plan_local(plan.h, None, None, arr, gid, None))
+    return dict(n_owned=no.value, dims=[tuple(arr[i].n) for i in range(nl.value)],
+                nb=[tuple(arr[i].neighbour) for i in range(nl.value)],
+                offset=[arr[i].offset for i in range(nl.value)],
+                field_stride=[arr[i].field_stride for i in range(nl.value)],
+                global_id=list(gid), arena_len=al.value)
+
+
+def pmp_plan_regions(plan, kind, send):
+    """List of dict(peer, patch, lo, hi, offset)."""
+    L = load()
+    n = ctypes.c_int32()
+    _check("pmp_plan_regions", L.pmp_plan_regions(plan.h, int(kind), int(send), None, 0, ctypes.byref(n)))
+    arr = (_Region * max(n.value, 1))()
+    _check("pmp_plan_regions", L.pmp_plan_regions(plan.h, int(kind), int(send), arr, n.value, ctypes.byref(n)))
+    return [dict(peer=arr[i].peer, patch=arr[i].patch, lo=tuple(arr[i].lo), hi=tuple(arr[i].hi),
+                 offset=arr[i].offset) for i in range(n.value)]
 
 
 def pmp_batch_set_particles(batch, first):
