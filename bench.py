@@ -213,7 +213,8 @@ def roofline(kernel, ms, pairs, box, n_fb, n_sk, hbm_peak, peak_src):
              "frac": achieved / FP64_PEAK_TFLOPS, "peak_source": "nominal FP64, 152 SMs x 2 DFMA/clk x 2.07 GHz"}
     r["kernel"] = kernel
     r["ms_per_launch"] = ms
-    r["traffic"] = profiled_traffic(kernel)
+    units = pairs.get(kind) if stage not in hbm_bytes and stage != "plan" else nvalid
+    r["traffic"] = profiled_traffic(kernel, units)
     return r
 
 
@@ -222,8 +223,9 @@ def cell_pass_hbm(kernel_ms, box, hbm_peak):
     perfect implementation moves) over the CUDA-event time of the launch, and
     the fraction of the measured copy bandwidth.  The supernova apply is the
     fast kernel plus the FP64 limiter on the queued cells (one phase, 120 B
-    per valid cell); the sink apply computes eta and updates the state in one
-    pass (128 B per valid cell with the eta it records for Step 4)."""
+    per valid cell); the sink apply likewise (its common pass and the FP64
+    limiter on the queued cells; 128 B per valid cell with the eta it records
+    for Step 4)."""
     nvalid, npad = box.ncells_valid, box.ncells_padded
     phases = {
         "fb_zero": (("fb_zero",), 40 * npad),
@@ -233,7 +235,7 @@ def cell_pass_hbm(kernel_ms, box, hbm_peak):
         "sink_cell_records": (("sink_cell_records",), (40 + 96) * nvalid),
         "sink_spread": (("sink_spread",), 136 * npad),
         "sink_fold": (("sink_fold",), 120 * (npad - nvalid)),
-        "sink_apply": (("sink_apply",), 128 * nvalid),
+        "sink_apply": (("sink_apply", "sink_apply_fp64"), 128 * nvalid),
     }
     out = {}
     for name, (kernels, nbytes) in phases.items():
@@ -246,8 +248,9 @@ def cell_pass_hbm(kernel_ms, box, hbm_peak):
 
 
 # Sources that neither define nor launch the single-box kernels the traffic
-# figures are taken from: the batched form and the allocation-free entry point.
-DIGEST_EXCLUDES = ("pmp_batch.cu", "pmp_noalloc.cu")
+# figures are taken from: the batched form and its exchange plan, the
+# allocation-free entry point and the peak probes.
+DIGEST_EXCLUDES = ("pmp_batch.cu", "pmp_noalloc.cu", "pmp_probe.cu", "pmp_exchange.cu")
 
 
 def src_digest():
@@ -262,18 +265,24 @@ def src_digest():
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(kernel):
-    """DRAM bytes per launch of `kernel` from the committed ncu summary, if it
-    was taken on the current kernel sources; else None."""
-    path = os.path.join(ROOT, "profiles", "dram_traffic_c5_512.md")
-    if not os.path.exists(path):
+def profiled_traffic(kernel, units):
+    """DRAM bytes of one launch of `kernel` processing `units` (pairs or
+    cells): the DRAM bytes per unit of the committed one-kernel ncu capture
+    on the 192^3 shrink of the workload times `units`, if the capture was
+    taken on the current kernel sources; else None.  (Traffic per pair is
+    taken to scale with the pairs at equal particle density.)"""
+    path = os.path.join(ROOT, "profiles", "counters_c5_192.md")
+    if not os.path.exists(path) or not units:
         return None
     txt = open(path).read()
     m = re.search(r"csrc_sha:\s*([0-9a-f]+)", txt)
     if not m or m.group(1) != src_digest():
         return None
-    m = re.search(rf"^\|\s*{re.escape(kernel)}\s*\|\s*([0-9.eE+]+)\s*\|", txt, re.M)
-    return float(m.group(1)) if m else None
+    for line in txt.splitlines():
+        cols = [c.strip() for c in line.strip().strip("|").split("|")]
+        if len(cols) == 13 and cols[1] == kernel:
+            return float(cols[12]) * units
+    return None
 
 
 def measure_fp64_and_atomics():
@@ -376,12 +385,13 @@ def run_ours(args, world, rank, local):
     # own kernels per step (the CUB sorts, scans and run encoding are library
     # kernels).  ATOMIC: supernova pass zero, prologue, plan + gather +
     # deposit, fold, apply (fast + queued) = 6; sink pass zero, prologue,
-    # per-cell records, plan + gather + deposit, spread, fold, eta + apply,
-    # Step-4 return = 8.  SORTED: plan + gather, keys, run and long-run
-    # kernels in place of the fused kernel (supernovae 9); sinks plan, gather,
-    # keys, runs, long runs, no spread (11).  ROUNDED: a deposit and a
-    # rounding kernel per pass (8 + 10).
-    launches_per_step = {"atomic": 14, "sorted": 20, "rounded": 18}[args.mode]
+    # per-cell records, plan + gather + deposit, spread, fold, eta + apply
+    # (common + queued), Step-4 return = 9.  SORTED: plan + gather, pair
+    # values, keys, run and long-run kernels in place of the fused kernel
+    # (supernovae 10); sinks plan, gather, pair values, keys, runs, long runs,
+    # no spread (13).  ROUNDED: a deposit and a rounding kernel per pass
+    # (8 + 11).
+    launches_per_step = {"atomic": 15, "sorted": 23, "rounded": 19}[args.mode]
     state0 = state.clone()
     sink0 = {k: sk[k].clone() for k in ("m", "px", "py", "pz")}
 
@@ -833,6 +843,44 @@ def deposit_modes(args):
         out["differing_values_between_orders"][key] = int(((a.view(torch.int64) != b.view(torch.int64)) & touched)
                                                           .sum().item())
     out["touched_values"] = int(touched.sum().item())
+    out["full_cycle"] = c2_full_cycle(args, w, st, parts)
+    return out
+
+
+def c2_full_cycle(args, w, st0, parts):
+    """One whole supernova pass on the 256^3 workload -- zero, gather +
+    deposit, fold, limited apply -- in the ATOMIC and SORTED modes: CUDA-event
+    time per pass (mean of `steps` passes after 3 warm-ups, each from the
+    initial state), particles/s and cells/s."""
+    import torch
+
+    from paper_2509_18261_gb300 import pmp
+
+    box = w["box"]
+    stream = torch.cuda.current_stream()
+    out = {}
+    n = parts["x"].numel()
+    for mode in ("atomic", "sorted"):
+        st = st0.clone()
+        ps = pmp.Pass(w["fb_params"], box, st, parts, mode=mode)
+        times = []
+        for it in range(3 + max(args.steps, 1)):
+            st.copy_(st0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ps.run()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            if it >= 3:
+                times.append(e0.elapsed_time(e1))
+        code, idx = pmp.pmp_get_error(ps.ctx)
+        if code:
+            raise RuntimeError(f"c2 full cycle: device error {code} at {idx}")
+        ms = sum(times) / len(times)
+        out[mode] = {"ms": ms, "particles_per_s": n / (ms * 1e-3), "cells_per_s": box.ncells_valid / (ms * 1e-3)}
+        ps.ctx.close()
+        del ps, st
+    torch.cuda.empty_cache()
     return out
 
 

@@ -102,7 +102,10 @@ typedef struct {
 
 /* ln 2 split for Cody & Waite (1980) argument reduction: LN2_HI keeps the top
  * 32 significant bits of ln 2 (so k*LN2_HI is exact for |k| < 2^21) and
- * LN2_LO is the next 53 bits of ln 2 = 0.693147180559945309417232121458... */
+ * LN2_LO is the next 53 bits of ln 2 = 0.693147180559945309417232121458...
+ * The published fdlibm library prints the same split (and the log
+ * arrangement f - (hf - s (hf + R)) used below); the polynomials are this
+ * oracle's own. */
 static const double LN2_HI = 6.93147180369123816490e-01;
 static const double LN2_LO = 1.90821492927058770002e-10;
 static const double INV_LN2 = 1.44269504088896338700e+00;

@@ -90,7 +90,7 @@ long long max_pairs_per_particle(double rK)
 
 struct Layout {
     size_t keys, ids, keys2, ids2, counts, slots, hosts, fr, wts, aux, pa, queue, qcount, offsets, skeys, skeys2,
-        svals, svals2, soffs, slong, scnt;
+        svals, svals2, soffs, slong, scnt, spv;
     size_t temp, temp_bytes, total;
     long long cap, aux_stride;
 };
@@ -128,6 +128,9 @@ Layout layout(const pmp_params &p, long long n, long long nvalid, int mode)
         L.aux = take(8 * 2 * (size_t)pmp::kRec * (size_t)(nvalid > 0 ? nvalid : 1));
         // ATOMIC: each pair's removal a, stored by the fused deposit for Step 4
         if (mode == PMP_MODE_ATOMIC) L.pa = take(8 * pairs);
+        // cells whose eta the sink apply's first pass leaves to the FP64 limiter
+        L.queue = take(4 * (size_t)(nvalid > 0 ? nvalid : 1));
+        L.qcount = take(8);
     } else {
         L.queue = take(4 * (size_t)(nvalid > 0 ? nvalid : 1));
         L.qcount = take(8);
@@ -141,6 +144,7 @@ Layout layout(const pmp_params &p, long long n, long long nvalid, int mode)
         L.soffs = take(4 * pairs);  // first pair of each run of equal cells
         L.slong = take(4 * pairs);  // runs longer than a warp
         L.scnt = take(16);          // number of runs, number of long runs
+        L.spv = take(8 * 5 * pairs);  // every pair's deposition value, index order
     }
     L.temp_bytes = pmp::cub_temp_bytes(n, (long long)pairs, sorted);
     L.temp = take(L.temp_bytes);
@@ -566,7 +570,12 @@ static pmp_status gather_impl(pmp_ctx *ctx, const pmp_mesh *state, const pmp_par
                 pmp::launch_prologue(S, q, keys, ids, pl, ctx->st, st);
             }
             Timed tm(ctx, "order_sort");
-            if (pmp::sort_host_keys(temp, L.temp_bytes, keys, keys2, ids, ids2, q.count, st) != cudaSuccess)
+            int nmax = state->n[0] > state->n[1] ? state->n[0] : state->n[1];
+            nmax = nmax > state->n[2] ? nmax : state->n[2];
+            int bits = 0;
+            while ((1 << bits) < nmax) ++bits;
+            const int end_bit = 3 * (bits < 10 ? (bits > 0 ? bits : 1) : 10);
+            if (pmp::sort_host_keys(temp, L.temp_bytes, keys, keys2, ids, ids2, q.count, end_bit, st) != cudaSuccess)
                 return PMP_ERR_CUDA;
         } else {
             Timed tm(ctx, "prologue");
@@ -724,6 +733,11 @@ pmp_status pmp_deposit(pmp_ctx *ctx, const pmp_mesh *state, const pmp_particles 
     if (total == 0) return PMP_OK;
     unsigned *k1 = reinterpret_cast<unsigned *>(w + L.skeys), *k2 = reinterpret_cast<unsigned *>(w + L.skeys2);
     unsigned *v1 = reinterpret_cast<unsigned *>(w + L.svals), *v2 = reinterpret_cast<unsigned *>(w + L.svals2);
+    double *pv = reinterpret_cast<double *>(w + L.spv);
+    {
+        Timed tm(ctx, "pair_values");
+        pmp::launch_pair_values(P, S, state->data, q, gathered, pl, offsets, pv, st);
+    }
     {
         Timed tm(ctx, "sort_keys");
         pmp::launch_sort_keys(P, B, q, pl, offsets, k1, v1, st);
@@ -748,8 +762,7 @@ pmp_status pmp_deposit(pmp_ctx *ctx, const pmp_mesh *state, const pmp_particles 
     }
     {
         Timed tm(ctx, "segment_sum");
-        pmp::launch_segment_sum(P, S, state->data, B, buffer->data, q, gathered, pl, nruns, k1, v1, offs, v2, longq,
-                                nlong, st);
+        pmp::launch_segment_sum(B, buffer->data, pv, nruns, k1, v1, offs, v2, longq, nlong, st);
     }
     return last_launch();
 }
@@ -802,8 +815,17 @@ pmp_status pmp_apply_limited(pmp_ctx *ctx, pmp_mesh *state, const pmp_mesh *buff
             return PMP_ERR_CUDA;
         {
             // Steps 3 + 5; Step 4 reads only the records and the particles
-            Timed tm(ctx, "apply");
-            pmp::launch_sink_eta_apply(P, S, state->data, B, buffer->data, pl.drec, eta_out, ctx->st, st);
+            char *w = static_cast<char *>(workspace);
+            unsigned *queue = reinterpret_cast<unsigned *>(w + L.queue);
+            unsigned long long *qc = reinterpret_cast<unsigned long long *>(w + L.qcount);
+            if (cudaMemsetAsync(qc, 0, sizeof(unsigned long long), st) != cudaSuccess) return PMP_ERR_CUDA;
+            {
+                Timed tm(ctx, "apply");
+                pmp::launch_sink_eta_apply(P, S, state->data, B, buffer->data, pl.drec, eta_out, queue, qc, st);
+            }
+            Timed tm(ctx, "apply_fp64");
+            pmp::launch_sink_eta_apply_slow(P, S, state->data, B, buffer->data, pl.drec, eta_out, queue, qc, ctx->st,
+                                            st);
         }
         if (n > 0 && ctx->plan_has_a) {
             Timed tm(ctx, "return");

@@ -91,7 +91,10 @@ __device__ __forceinline__ int wrapi(int i, int n)
 
 // ln 2 = 0.6931471805599453094172321...: kLn2Hi holds its leading 32
 // significant bits (so k * kLn2Hi is exact for |k| < 2^21), kLn2Lo the rest
-// rounded to double.
+// rounded to double.  This two-part split of ln 2 (and 1/ln 2) is the one
+// Cody & Waite's reduction uses; the published fdlibm library prints the
+// same digits.  The log arrangement f - (hf - s (hf + R)) below also follows
+// fdlibm's published e_log; the polynomials are this library's own.
 constexpr double kLn2Hi = 6.93147180369123816490e-01;
 constexpr double kLn2Lo = 1.90821492927058770002e-10;
 constexpr double kInvLn2 = 1.44269504088896338700e+00;

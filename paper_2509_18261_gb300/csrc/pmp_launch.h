@@ -61,13 +61,18 @@ void launch_deposit_atomic(const KParams &P, const Box &S, const double *u, cons
                            const double *G, const PlanPtrs &pl, double *E, double *scr, cudaStream_t stream);
 void launch_sort_keys(const KParams &P, const Box &B, const Parts &p, const PlanPtrs &pl,
                       const unsigned long long *offsets, unsigned *keys, unsigned *vals, cudaStream_t stream);
-// Sorted deposit, per run of equal buffer cells (uniq/lens/offs from
-// encode_runs and scan_lengths; nruns on the device): short runs one thread
-// each, runs longer than a warp one warp each (queued in longq/nlong).
-void launch_segment_sum(const KParams &P, const Box &S, const double *u, const Box &B, double *b, const Parts &p,
-                        const double *G, const PlanPtrs &pl, const unsigned long long *nruns, const unsigned *uniq,
-                        const unsigned *lens, const unsigned *offs, const unsigned *vals, unsigned *longq,
-                        unsigned *nlong, cudaStream_t stream);
+// Sorted deposit, first part: every pair's deposition value (the same
+// function and operations as the atomic deposit) stored at
+// pv[(offsets[s] + q) * 5 + f] for pair q of particle s (index order).
+void launch_pair_values(const KParams &P, const Box &S, const double *u, const Parts &p, const double *G,
+                        const PlanPtrs &pl, const unsigned long long *offsets, double *pv, cudaStream_t stream);
+// Sorted deposit, second part, per run of equal buffer cells (uniq/lens/offs
+// from encode_runs and scan_lengths; nruns on the device): the run's stored
+// pair values added in list order on top of the buffer value; short runs one
+// thread each, runs longer than a warp one warp each (queued in longq/nlong).
+void launch_segment_sum(const Box &B, double *b, const double *pv, const unsigned long long *nruns,
+                        const unsigned *uniq, const unsigned *lens, const unsigned *offs, const unsigned *vals,
+                        unsigned *longq, unsigned *nlong, cudaStream_t stream);
 void launch_return_sinks(const KParams &P, const Box &S, const Parts &p, const double *G, const PlanPtrs &pl,
                          DevStatus *st, cudaStream_t stream);
 // Step 4 from the removals the fused ATOMIC deposit stored (pl.pa): a warp
@@ -102,10 +107,16 @@ void launch_sink_spread(const Box &S, const Box &B, double *b, const double *scr
                         cudaStream_t stream);
 void launch_sink_aux(const KParams &P, const Box &S, const double *u, double *grec, double *drec,
                      cudaStream_t stream);
-// Steps 3 + 5 for sinks: eta per valid cell (into the D records, for Step 4)
-// and U += eta Delta U^sum, in one pass.
+// Steps 3 + 5 for sinks, first pass: eta = 1 and U += Delta U^sum where no
+// FP64 work decides it (eta into the D records, for Step 4); the other cells
+// queued for the second pass.
 void launch_sink_eta_apply(const KParams &P, const Box &S, double *u, const Box &B, const double *b, double *drec,
-                           double *eta_out, DevStatus *st, cudaStream_t stream);
+                           double *eta_out, unsigned *queue, unsigned long long *qcount, cudaStream_t stream);
+// The cells the first pass queued, through the FP64 limiter (counts limited
+// cells in st->n_limited).
+void launch_sink_eta_apply_slow(const KParams &P, const Box &S, double *u, const Box &B, const double *b,
+                                double *drec, double *eta_out, const unsigned *queue,
+                                const unsigned long long *qcount, DevStatus *st, cudaStream_t stream);
 void launch_apply_fb_fast(const Box &S, double *u, const Box &B, const double *b, double *eta_out, unsigned *queue,
                           unsigned long long *qcount, cudaStream_t stream);
 void launch_apply_fb_slow(const Box &S, double *u, const Box &B, const double *b, double *eta_out,
@@ -118,8 +129,13 @@ void launch_apply(const KParams &P, const Box &S, double *u, const Box &B, const
 // CUB primitives, in pmp_sort.cu
 size_t cub_temp_bytes(long long n, long long max_pairs, bool sorted);
 size_t scan_temp_bytes(long long n);
+// Sorts the processing-order keys on bits [0, end_bit): the Morton codes of a
+// box whose largest extent needs b bits (b <= 10 after the shift) fill bits
+// [0, 3b).  Invalid particles (all-ones keys) then sort among the last
+// cell's particles; where they fall in the order does not matter, as they
+// have no kernel cells.
 cudaError_t sort_host_keys(void *temp, size_t temp_bytes, const unsigned *kin, unsigned *kout, const unsigned *vin,
-                           unsigned *vout, long long n, cudaStream_t stream);
+                           unsigned *vout, long long n, int end_bit, cudaStream_t stream);
 cudaError_t scan_counts(void *temp, size_t temp_bytes, const unsigned *counts, unsigned long long *offsets,
                         long long n, cudaStream_t stream);
 cudaError_t sort_pairs(void *temp, size_t temp_bytes, const unsigned *kin, unsigned *kout, const unsigned *vin,

@@ -380,28 +380,126 @@ __device__ __forceinline__ bool sink_eta_one_f32(const KParams &P, double rho, d
     return up < t1 && up < t2 && t1 < 1e30f;
 }
 
-// Steps 3 + 5 for sinks in one pass over the valid cells:
-// - eta from the pre-update density, the summed removal a = -Delta rho^sum and
-//   rho - rho_Tr (the accretion limiter of Sec. 3.1.1 composed with the
-//   density floor), written to the cell's D record for Step 4;
-// - U += eta Delta U^sum, one eta for all five fields.
-// The GB300 FP64 pipe, not HBM, bounds this pass unless the common case
-// (eta = 1) is decided without it: a <= 0 from the bits of Delta rho^sum,
-// then the FP32 pre-test above; only undecided cells run the FP64 tests
-// (reading rho - rho_Tr from the D record only where those fail).  Every
-// decision is the FP64 one.  Step 4 reads only the records, the particles
-// and the plan, never the state, so it can follow this pass.  Limited cells
-// are counted per block.
+// Sink limiter (Sec. 3.1.1 with the density floor) in FP64 for a cell with
+// removal a = -D[0] > 0 that the FP32 pre-test left undecided; t is rho -
+// rho_Tr from the cell's D record.  Same operations as sink_eta.
+__device__ __forceinline__ double sink_eta_fp64(const KParams &P, double rho, double d0, double t)
+{
+    const double a = -d0;
+    const double capr = P.cap * rho;
+    const double fl = rho - P.rho_min;
+    if (a <= capr && a <= fl) return 1.0;
+    double al = a < capr ? a : capr;
+    al = al > t ? al : t;
+    al = al < fl ? al : fl;
+    if (al < 0.0) al = 0.0;
+    return al < a ? al / a : 1.0;
+}
+
+// a = -D[0] > 0 exactly when D[0] is negative: sign set, not -0, not NaN
+// (decided on the bits, no FP64 instruction).
+__device__ __forceinline__ bool removal_positive(double d0)
+{
+    const unsigned long long b0 = (unsigned long long)__double_as_longlong(d0);
+    const unsigned long long mag2 = b0 << 1;
+    return (b0 >> 63) != 0 && mag2 != 0 && mag2 <= (0x7ff0000000000000ULL << 1);
+}
+
+// Steps 3 + 5 for sinks, first pass over the valid cells: eta = 1 wherever
+// it is decided without FP64 work -- no removal (from the bits of
+// Delta rho^sum) or the FP32 pre-test above -- and those cells are updated,
+// U += Delta U^sum, with eta = 1 written to the cell's D record for Step 4.
+// The other cells are queued for k_sink_eta_apply_slow, so that the FP64
+// branch of the limiter, which about one cell in twenty takes, is issued for
+// full warps of such cells rather than for every warp in which one lane takes
+// it.  Queue slots are reserved per chunk of a block, as in k_apply_fb_fast;
+// the queue's order does not matter.  Step 4 reads only the records, the
+// particles and the plan, never the state, so it can follow these passes.
 __global__ void __launch_bounds__(kApplyThreads, 4) k_sink_eta_apply(KParams P, Box S, double *__restrict__ u, Box B,
                                                                      const double *__restrict__ b,
                                                                      double *__restrict__ drec,
-                                                                     double *__restrict__ eta_out, DevStatus *st)
+                                                                     double *__restrict__ eta_out,
+                                                                     unsigned *__restrict__ queue,
+                                                                     unsigned long long *__restrict__ qcount)
+{
+    __shared__ unsigned wofs[kApplyThreads / 32];
+    __shared__ unsigned long long qbase;
+    const long long nvalid = (long long)S.n0 * S.n1 * S.n2;
+    constexpr long long per = (long long)kApplyThreads * kApplyChunk;
+    const long long nchunks = (nvalid + per - 1) / per;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (long long ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
+        const long long c0 = ch * per + threadIdx.x;
+        unsigned mask = 0;
+#pragma unroll
+        for (int c = 0; c < kApplyChunk; ++c) {
+            const long long v = c0 + (long long)c * kApplyThreads;
+            if (v >= nvalid) break;
+            int i, j, k;
+            cell_of(S, v, nvalid, i, j, k);
+            const long long cs = S.at(i, j, k), cb = B.at(i, j, k);
+            double U[NF], D[NF];
+#pragma unroll
+            for (int f = 0; f < NF; ++f) {
+                D[f] = __ldg(b + (long long)f * B.fs + cb);
+                U[f] = u[(long long)f * S.fs + cs];
+            }
+            if (removal_positive(D[0]) && !sink_eta_one_f32(P, U[0], D[0])) {
+                mask |= 1u << c;
+                continue;
+            }
+            drec[v * kRec + 5] = 1.0;
+            if (eta_out) eta_out[v] = 1.0;
+            if (!all_zero(D)) {
+#pragma unroll
+                for (int f = 0; f < NF; ++f) u[(long long)f * S.fs + cs] = U[f] + D[f];
+            }
+        }
+        const unsigned cnt = __popc(mask);
+        unsigned incl = cnt;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const unsigned t = __shfl_up_sync(0xffffffffu, incl, d);
+            if (lane >= d) incl += t;
+        }
+        if (lane == 31) wofs[wid] = incl;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            unsigned tot = 0;
+            for (int q = 0; q < kApplyThreads / 32; ++q) {
+                const unsigned t = wofs[q];
+                wofs[q] = tot;
+                tot += t;
+            }
+            qbase = tot ? atomicAdd(qcount, (unsigned long long)tot) : 0ULL;
+        }
+        __syncthreads();
+        unsigned long long pos = qbase + wofs[wid] + (incl - cnt);
+#pragma unroll
+        for (int c = 0; c < kApplyChunk; ++c)
+            if ((mask >> c) & 1u) queue[pos++] = (unsigned)(c0 + (long long)c * kApplyThreads);
+        __syncthreads();  // wofs and qbase are rewritten by the next chunk
+    }
+}
+
+// Second pass: the queued cells through the FP64 limiter, then U += eta
+// Delta U^sum (one eta for all five fields), eta to the D record; limited
+// cells are counted per block.
+__global__ void __launch_bounds__(kApplyThreads) k_sink_eta_apply_slow(KParams P, Box S, double *__restrict__ u, Box B,
+                                                                       const double *__restrict__ b,
+                                                                       double *__restrict__ drec,
+                                                                       double *__restrict__ eta_out,
+                                                                       const unsigned *__restrict__ queue,
+                                                                       const unsigned long long *__restrict__ qcount,
+                                                                       DevStatus *st)
 {
     __shared__ unsigned sh[kApplyThreads / 32];
     const long long nvalid = (long long)S.n0 * S.n1 * S.n2;
-    const long long stride = (long long)gridDim.x * blockDim.x;
+    const unsigned long long n = *qcount;
+    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
     unsigned nl = 0;
-    for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < nvalid; v += stride) {
+    for (unsigned long long q = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += stride) {
+        const long long v = queue[q];
         int i, j, k;
         cell_of(S, v, nvalid, i, j, k);
         const long long cs = S.at(i, j, k), cb = B.at(i, j, k);
@@ -411,39 +509,16 @@ __global__ void __launch_bounds__(kApplyThreads, 4) k_sink_eta_apply(KParams P, 
             D[f] = __ldg(b + (long long)f * B.fs + cb);
             U[f] = u[(long long)f * S.fs + cs];
         }
-        // a = -D[0] > 0 exactly when D[0] is negative: sign set, not -0, not NaN
-        const unsigned long long b0 = (unsigned long long)__double_as_longlong(D[0]);
-        const unsigned long long mag2 = b0 << 1;
-        const bool pos_a = (b0 >> 63) != 0 && mag2 != 0 && mag2 <= (0x7ff0000000000000ULL << 1);
-        double e = 1.0;
-        bool one = true, lim = false;
-        if (pos_a && !sink_eta_one_f32(P, U[0], D[0])) {
-            const double rho = U[0];
-            const double a = -D[0];
-            const double capr = P.cap * rho;
-            const double fl = rho - P.rho_min;
-            if (!(a <= capr && a <= fl)) {
-                double al = a < capr ? a : capr;
-                const double t = __ldg(drec + v * kRec);
-                al = al > t ? al : t;
-                al = al < fl ? al : fl;
-                if (al < 0.0) al = 0.0;
-                e = al < a ? al / a : 1.0;
-                one = e == 1.0;
-                lim = e < 1.0;
-            }
-        }
+        const double e = sink_eta_fp64(P, U[0], D[0], __ldg(drec + v * kRec));
         drec[v * kRec + 5] = e;
         if (eta_out) eta_out[v] = e;
-        nl += lim;
-        if (!all_zero(D)) {
-            if (one) {
+        nl += e < 1.0;
+        if (e == 1.0) {
 #pragma unroll
-                for (int f = 0; f < NF; ++f) u[(long long)f * S.fs + cs] = U[f] + D[f];
-            } else {
+            for (int f = 0; f < NF; ++f) u[(long long)f * S.fs + cs] = U[f] + D[f];
+        } else {
 #pragma unroll
-                for (int f = 0; f < NF; ++f) u[(long long)f * S.fs + cs] = U[f] + e * D[f];
-            }
+            for (int f = 0; f < NF; ++f) u[(long long)f * S.fs + cs] = U[f] + e * D[f];
         }
     }
     block_add(&st->n_limited, nl, sh);
@@ -693,12 +768,21 @@ static unsigned resident_grid(K kernel, int threads, long long need)
 }
 
 void launch_sink_eta_apply(const KParams &P, const Box &S, double *u, const Box &B, const double *b, double *drec,
-                           double *eta_out, DevStatus *st, cudaStream_t stream)
+                           double *eta_out, unsigned *queue, unsigned long long *qcount, cudaStream_t stream)
 {
     const long long nvalid = (long long)S.n0 * S.n1 * S.n2;
     if (nvalid == 0) return;
-    const unsigned grid = resident_grid(k_sink_eta_apply, kApplyThreads, (nvalid + kApplyThreads - 1) / kApplyThreads);
-    k_sink_eta_apply<<<grid, kApplyThreads, 0, stream>>>(P, S, u, B, b, drec, eta_out, st);
+    const long long per = (long long)kApplyThreads * kApplyChunk;
+    const unsigned grid = resident_grid(k_sink_eta_apply, kApplyThreads, (nvalid + per - 1) / per);
+    k_sink_eta_apply<<<grid, kApplyThreads, 0, stream>>>(P, S, u, B, b, drec, eta_out, queue, qcount);
+}
+
+void launch_sink_eta_apply_slow(const KParams &P, const Box &S, double *u, const Box &B, const double *b,
+                                double *drec, double *eta_out, const unsigned *queue,
+                                const unsigned long long *qcount, DevStatus *st, cudaStream_t stream)
+{
+    const unsigned grid = resident_grid(k_sink_eta_apply_slow, kApplyThreads, 1LL << 40);
+    k_sink_eta_apply_slow<<<grid, kApplyThreads, 0, stream>>>(P, S, u, B, b, drec, eta_out, queue, qcount, st);
 }
 
 void launch_apply_fb_fast(const Box &S, double *u, const Box &B, const double *b, double *eta_out, unsigned *queue,

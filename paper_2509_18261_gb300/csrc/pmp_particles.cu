@@ -832,55 +832,6 @@ __global__ void __launch_bounds__(kSinkThreads) k_gather_sink(KParams P, Box S, 
         gather_sink_particle<R>(P, S, u, p, pl, G, st, t);
 }
 
-// ---------------------------------------------------------------------------
-// per-pair deposition values
-// ---------------------------------------------------------------------------
-
-__device__ __forceinline__ void fb_pair_delta(const KParams &P, const Box &S, const double *__restrict__ u,
-                                              const Parts &p, const double *__restrict__ G, long long s,
-                                              const PairCell &c, const double *wtab, double dU[NF])
-{
-    const long long gs = p.count;
-    const double x = __ldg(p.x + s), y = __ldg(p.y + s), z = __ldg(p.z + s);
-    const double d0 = ((double)c.i + 0.5) - x, d1 = ((double)c.j + 0.5) - y, d2 = ((double)c.k + 0.5) - z;
-    const double dd = (d0 * d0 + d1 * d1) + d2 * d2;
-    const double w = wtab[c.cnt];
-    if (P.kind == PMP_KIND_MASS) {
-#pragma unroll
-        for (int f = 0; f < NF; ++f) dU[f] = w * __ldg(G + (MS_Q + f) * gs + s);
-        return;
-    }
-    double U[NF];
-    load_cell(u, S, S.at(owner(c.i, S.n0), owner(c.j, S.n1), owner(c.k, S.n2)), U);
-    const double vc[3] = {__ldg(G + FB_VX * gs + s), __ldg(G + FB_VY * gs + s), __ldg(G + FB_VZ * gs + s)};
-    feedback_delta(w, U, __ldg(G + FB_Q * gs + s), __ldg(G + FB_E * gs + s), __ldg(G + FB_PV * gs + s), vc, d0, d1,
-                   d2, dd, dU);
-}
-
-// Sink deposition value of one pair.
-template <int R>
-__device__ __forceinline__ void sink_pair_delta(const KParams &P, const Box &S, const Parts &p,
-                                                const double *__restrict__ G, const PlanPtrs &pl, long long s,
-                                                const PairCell &c, double dU[NF])
-{
-    constexpr int W = 2 * R + 1;
-    int hx, hy, hz;
-    unpack_host(__ldg(pl.hosts + s), hx, hy, hz);
-    const double *ws = pl.wts + s * (3 * W);
-    const double w = (__ldg(ws + c.i - hx + R) * __ldg(ws + W + c.j - hy + R)) * __ldg(ws + 2 * W + c.k - hz + R);
-    const double2 *d =
-        reinterpret_cast<const double2 *>(pl.drec + vidx(S, owner(c.i, S.n0), owner(c.j, S.n1), owner(c.k, S.n2)) * kRec);
-    const double2 d0 = __ldg(d), d1 = __ldg(d + 1), d2 = __ldg(d + 2);
-    const double bh = __ldg(G + SK_K * p.count + s) * w;
-    const double tr = d0.x;
-    const double a = bh >= tr ? bh : tr;
-    dU[0] = -a;
-    dU[1] = -(a * d0.y);
-    dU[2] = -(a * d1.x);
-    dU[3] = -(a * d1.y);
-    dU[4] = -(a * d2.x);
-}
-
 // Blocks per SM of the fused sink kernel (0: an L2 window of sinks in
 // flight, as the sink gather).
 #ifndef PMP_SINK_PASS1_BPS
@@ -1041,11 +992,15 @@ __device__ __forceinline__ void fb_pair_delta_d(const double *__restrict__ u, co
                    d2, dd, dU);
 }
 
+// With pv (sorted mode: index order, no perm), each pair's value is stored
+// at pv[(offs[t] + q) * 5 + f] instead of added into the buffer.
 template <int R, bool FB>
 __global__ void __launch_bounds__(256) k_deposit_atomic(KParams P, Box S, const double *__restrict__ u, Box B,
                                                         double *__restrict__ b, Parts p,
                                                         const double *__restrict__ G, PlanPtrs pl,
-                                                        double *__restrict__ E, double *__restrict__ scr)
+                                                        double *__restrict__ E, double *__restrict__ scr,
+                                                        double *__restrict__ pv,
+                                                        const unsigned long long *__restrict__ offs)
 {
     constexpr int W = 2 * R + 1;
     constexpr int TAB = kPartsPerWarp * 3 * W;  // per warp: [8 particles][3 axes][W offsets]
@@ -1170,6 +1125,12 @@ __global__ void __launch_bounds__(256) k_deposit_atomic(KParams P, Box S, const 
                     dU[3] = -(a * d1.y);
                     dU[4] = -(a * d2.x);
                 }
+                if (pv) {
+                    double *o = pv + (offs[t0 + j] + (g - before)) * NF;
+#pragma unroll
+                    for (int f = 0; f < NF; ++f) o[f] = dU[f];
+                    continue;
+                }
                 const long long bc = B.at(cell.i, cell.j, cell.k);
                 if (E) {
                     // App. A.1: the error bound of the cell grows by eps |buffer| after each addition
@@ -1192,8 +1153,9 @@ __global__ void __launch_bounds__(256) k_deposit_atomic(KParams P, Box S, const 
 // Step 1, sorted accumulation
 // ---------------------------------------------------------------------------
 
-// Compact (buffer cell, slot) lists in particle-index order (the sorted mode
-// plans in index order); offsets from the exclusive scan of the counts.
+// Compact (buffer cell, pair) lists in particle-index order (the sorted mode
+// plans in index order); offsets from the exclusive scan of the counts.  A
+// pair is named by its place o + q in that list, where its value is stored.
 __global__ void __launch_bounds__(128) k_sort_keys(KParams P, Box B, long long n, PlanPtrs pl,
                                                    const unsigned long long *__restrict__ offsets,
                                                    unsigned *__restrict__ keys, unsigned *__restrict__ vals)
@@ -1206,25 +1168,10 @@ __global__ void __launch_bounds__(128) k_sort_keys(KParams P, Box B, long long n
     for (unsigned q = 0; q < nc; ++q) {
         const PairCell c = unpack_pair(pl.slots[b0 + q], P.R);
         keys[o + q] = (unsigned)B.at(c.i, c.j, c.k);
-        vals[o + q] = (unsigned)(b0 + q);
+        vals[o + q] = (unsigned)(o + q);  // the pair's place in the index-order list (its value's row)
     }
 }
 
-// Deposition value of pair `slot` of the index-order plan (the sorted mode
-// plans in index order, so the slot's row is the particle).
-template <int R, bool FB>
-__device__ __forceinline__ void sorted_pair_delta(const KParams &P, const Box &S, const double *__restrict__ u,
-                                                  const Parts &p, const double *__restrict__ G, const PlanPtrs &pl,
-                                                  unsigned long long slot, const double *wtab, double dU[NF])
-{
-    const long long s = (long long)(slot / pl.cap);
-    const PairCell c = unpack_pair(pl.slots[slot], P.R);
-    if (FB) {
-        fb_pair_delta(P, S, u, p, G, s, c, wtab, dU);
-    } else {
-        sink_pair_delta<R>(P, S, p, G, pl, s, c, dU);
-    }
-}
 
 constexpr unsigned kLongRun = 32;  // runs longer than this get a warp
 
@@ -1232,18 +1179,14 @@ constexpr unsigned kLongRun = 32;  // runs longer than this get a warp
 // the run's pairs, which the stable sort kept in particle-index order, are
 // added in that order on top of what the buffer holds.  Longer runs are
 // queued for k_segment_long.
-template <int R, bool FB>
-__global__ void __launch_bounds__(128) k_segment_runs(KParams P, Box S, const double *__restrict__ u, Box B,
-                                                      double *__restrict__ b, Parts p, const double *__restrict__ G,
-                                                      PlanPtrs pl, const unsigned long long *__restrict__ nruns_ptr,
+__global__ void __launch_bounds__(128) k_segment_runs(Box B, double *__restrict__ b, const double *__restrict__ pv,
+                                                      const unsigned long long *__restrict__ nruns_ptr,
                                                       const unsigned *__restrict__ uniq,
                                                       const unsigned *__restrict__ lens,
                                                       const unsigned *__restrict__ offs,
                                                       const unsigned *__restrict__ vals, unsigned *__restrict__ longq,
                                                       unsigned *__restrict__ nlong)
 {
-    __shared__ double wtab[FB ? kMaxS3 + 1 : 1];
-    if (FB) fill_omega_table(P, wtab);
     const unsigned long long nruns = *nruns_ptr;
     const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
     for (unsigned long long r = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; r < nruns; r += stride) {
@@ -1257,10 +1200,9 @@ __global__ void __launch_bounds__(128) k_segment_runs(KParams P, Box S, const do
 #pragma unroll
         for (int f = 0; f < NF; ++f) acc[f] = b[(long long)f * B.fs + key];
         for (unsigned j = 0; j < len; ++j) {
-            double dU[NF];
-            sorted_pair_delta<R, FB>(P, S, u, p, G, pl, vals[o + j], wtab, dU);
+            const double *v = pv + (unsigned long long)vals[o + j] * NF;
 #pragma unroll
-            for (int f = 0; f < NF; ++f) acc[f] = acc[f] + dU[f];
+            for (int f = 0; f < NF; ++f) acc[f] = acc[f] + __ldg(v + f);
         }
 #pragma unroll
         for (int f = 0; f < NF; ++f) b[(long long)f * B.fs + key] = acc[f];
@@ -1272,10 +1214,8 @@ __global__ void __launch_bounds__(128) k_segment_runs(KParams P, Box S, const do
 // field the same sequence of additions as a single thread would make, with
 // one FP64 instruction per pair for all five fields (an FP64 instruction with
 // one active lane costs the pipe about what a full-warp one does).
-template <int R, bool FB>
-__global__ void __launch_bounds__(128) k_segment_long(KParams P, Box S, const double *__restrict__ u, Box B,
-                                                      double *__restrict__ b, Parts p, const double *__restrict__ G,
-                                                      PlanPtrs pl, const unsigned *__restrict__ uniq,
+__global__ void __launch_bounds__(128) k_segment_long(Box B, double *__restrict__ b, const double *__restrict__ pv,
+                                                      const unsigned *__restrict__ uniq,
                                                       const unsigned *__restrict__ lens,
                                                       const unsigned *__restrict__ offs,
                                                       const unsigned *__restrict__ vals,
@@ -1283,8 +1223,6 @@ __global__ void __launch_bounds__(128) k_segment_long(KParams P, Box S, const do
                                                       const unsigned *__restrict__ nlong_ptr)
 {
     __shared__ double stage[4][32][NF + 1];
-    __shared__ double wtab[FB ? kMaxS3 + 1 : 1];
-    if (FB) fill_omega_table(P, wtab);
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const unsigned nlong = *nlong_ptr;
     const unsigned nw = gridDim.x * (blockDim.x >> 5);
@@ -1295,10 +1233,9 @@ __global__ void __launch_bounds__(128) k_segment_long(KParams P, Box S, const do
         if (lane < NF) acc = b[(long long)lane * B.fs + key];
         for (unsigned c0 = 0; c0 < len; c0 += 32) {
             if (c0 + lane < len) {
-                double dU[NF];
-                sorted_pair_delta<R, FB>(P, S, u, p, G, pl, vals[o + c0 + lane], wtab, dU);
+                const double *v = pv + (unsigned long long)vals[o + c0 + lane] * NF;
 #pragma unroll
-                for (int f = 0; f < NF; ++f) stage[wib][lane][f] = dU[f];
+                for (int f = 0; f < NF; ++f) stage[wib][lane][f] = __ldg(v + f);
             }
             __syncwarp();
             if (lane < NF) {
@@ -1316,7 +1253,7 @@ __global__ void __launch_bounds__(128) k_segment_long(KParams P, Box S, const do
 // ---------------------------------------------------------------------------
 
 // One kernel cell's terms of the Step-4 sums: the pair's removal a (as in
-// sink_pair_delta, from D record d0 = (rho - rho_Tr, p_x/rho), d1 = (p_y/rho,
+// the deposit, from D record d0 = (rho - rho_Tr, p_x/rho), d1 = (p_y/rho,
 // p_z/rho)) limited by the cell's eta e, b = e a; the mass sum takes -b, the
 // momentum sums take -b v, fused.
 __device__ __forceinline__ void sink_return_add(double K, double w, double2 d0, double2 d1, double e, double &a0,
@@ -1652,8 +1589,9 @@ void launch_pass1_sink(const KParams &P, const Box &S, const double *u, const Bo
     PMP_DISPATCH_R(P.R, (pass1_sink_one<RR>(P, S, u, B, scr, p, pl, G, st, stream)));
 }
 
-void launch_deposit_atomic(const KParams &P, const Box &S, const double *u, const Box &B, double *b, const Parts &p,
-                           const double *G, const PlanPtrs &pl, double *E, double *scr, cudaStream_t stream)
+static void launch_pair_kernel(const KParams &P, const Box &S, const double *u, const Box &B, double *b,
+                               const Parts &p, const double *G, const PlanPtrs &pl, double *E, double *scr,
+                               double *pv, const unsigned long long *offs, cudaStream_t stream)
 {
     if (p.count == 0) return;
     // Only resident blocks: the grid-stride loop then moves all of them
@@ -1677,11 +1615,24 @@ void launch_deposit_atomic(const KParams &P, const Box &S, const double *u, cons
     if (occ < 1) occ = 1;
     const unsigned nb = (unsigned)(blocks_needed < (long long)nsm * occ ? blocks_needed : (long long)nsm * occ);
     if (P.kind != PMP_KIND_SINK) {
-        PMP_DISPATCH_R(P.R,
-                       (k_deposit_atomic<RR, true><<<nb, 256, 0, stream>>>(P, S, u, B, b, p, G, pl, E, nullptr)));
+        PMP_DISPATCH_R(P.R, (k_deposit_atomic<RR, true><<<nb, 256, 0, stream>>>(P, S, u, B, b, p, G, pl, E, nullptr,
+                                                                                 pv, offs)));
     } else {
-        PMP_DISPATCH_R(P.R, (k_deposit_atomic<RR, false><<<nb, 256, 0, stream>>>(P, S, u, B, b, p, G, pl, E, scr)));
+        PMP_DISPATCH_R(P.R, (k_deposit_atomic<RR, false><<<nb, 256, 0, stream>>>(P, S, u, B, b, p, G, pl, E, scr,
+                                                                                  pv, offs)));
     }
+}
+
+void launch_deposit_atomic(const KParams &P, const Box &S, const double *u, const Box &B, double *b, const Parts &p,
+                           const double *G, const PlanPtrs &pl, double *E, double *scr, cudaStream_t stream)
+{
+    launch_pair_kernel(P, S, u, B, b, p, G, pl, E, scr, nullptr, nullptr, stream);
+}
+
+void launch_pair_values(const KParams &P, const Box &S, const double *u, const Parts &p, const double *G,
+                        const PlanPtrs &pl, const unsigned long long *offsets, double *pv, cudaStream_t stream)
+{
+    launch_pair_kernel(P, S, u, S, nullptr, p, G, pl, nullptr, nullptr, pv, offsets, stream);
 }
 
 void launch_sort_keys(const KParams &P, const Box &B, const Parts &p, const PlanPtrs &pl,
@@ -1691,25 +1642,14 @@ void launch_sort_keys(const KParams &P, const Box &B, const Parts &p, const Plan
     k_sort_keys<<<blocks_for(p.count, 128), 128, 0, stream>>>(P, B, p.count, pl, offsets, keys, vals);
 }
 
-void launch_segment_sum(const KParams &P, const Box &S, const double *u, const Box &B, double *b, const Parts &p,
-                        const double *G, const PlanPtrs &pl, const unsigned long long *nruns, const unsigned *uniq,
-                        const unsigned *lens, const unsigned *offs, const unsigned *vals, unsigned *longq,
-                        unsigned *nlong, cudaStream_t stream)
+void launch_segment_sum(const Box &B, double *b, const double *pv, const unsigned long long *nruns,
+                        const unsigned *uniq, const unsigned *lens, const unsigned *offs, const unsigned *vals,
+                        unsigned *longq, unsigned *nlong, cudaStream_t stream)
 {
     const unsigned nb = 152u * 32u;
     cudaMemsetAsync(nlong, 0, sizeof(unsigned), stream);
-    if (P.kind != PMP_KIND_SINK) {
-        k_segment_runs<1, true><<<nb, 128, 0, stream>>>(P, S, u, B, b, p, G, pl, nruns, uniq, lens, offs, vals, longq,
-                                                        nlong);
-        k_segment_long<1, true><<<152u * 8u, 128, 0, stream>>>(P, S, u, B, b, p, G, pl, uniq, lens, offs, vals, longq,
-                                                                nlong);
-    } else {
-        PMP_DISPATCH_R(P.R, (k_segment_runs<RR, false><<<nb, 128, 0, stream>>>(P, S, u, B, b, p, G, pl, nruns, uniq,
-                                                                                lens, offs, vals, longq, nlong)));
-        PMP_DISPATCH_R(P.R, (k_segment_long<RR, false><<<152u * 8u, 128, 0, stream>>>(P, S, u, B, b, p, G, pl, uniq,
-                                                                                       lens, offs, vals, longq,
-                                                                                       nlong)));
-    }
+    k_segment_runs<<<nb, 128, 0, stream>>>(B, b, pv, nruns, uniq, lens, offs, vals, longq, nlong);
+    k_segment_long<<<152u * 8u, 128, 0, stream>>>(B, b, pv, uniq, lens, offs, vals, longq, nlong);
 }
 
 #ifndef PMP_SINK_RETURN_STORED_BPS

@@ -34,9 +34,9 @@ size_t cub_temp_bytes(long long n, long long max_pairs, bool sorted)
 }
 
 cudaError_t sort_host_keys(void *temp, size_t temp_bytes, const unsigned *kin, unsigned *kout, const unsigned *vin,
-                           unsigned *vout, long long n, cudaStream_t stream)
+                           unsigned *vout, long long n, int end_bit, cudaStream_t stream)
 {
-    return cub::DeviceRadixSort::SortPairs(temp, temp_bytes, kin, kout, vin, vout, n, 0, 32, stream);
+    return cub::DeviceRadixSort::SortPairs(temp, temp_bytes, kin, kout, vin, vout, n, 0, end_bit, stream);
 }
 
 // Exclusive prefix sum of 32-bit counts accumulated in 64 bits.

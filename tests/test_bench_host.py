@@ -34,20 +34,30 @@ def test_hbm_roofline_of_the_sink_apply():
     assert r["frac"] == pytest.approx(r["achieved"] / 6793.4, rel=1e-12)
 
 
-def test_traffic_is_reported_only_for_the_profiled_sources():
+def test_traffic_is_reported_only_for_the_profiled_sources(monkeypatch):
     # the committed summary names the digest of the sources it was taken on
-    assert bench.profiled_traffic("fb_gather_deposit") is None or \
-        bench.profiled_traffic("fb_gather_deposit") > 1e10
-    assert bench.profiled_traffic("no_such_kernel") is None
+    t = bench.profiled_traffic("fb_gather_deposit", 491934207)
+    assert t is None or t > 1e10
+    assert bench.profiled_traffic("no_such_kernel", 1000) is None
+    # with the digest of the capture, the per-pair bytes scale with the pairs
+    import re
+
+    txt = open(bench.os.path.join(bench.ROOT, "profiles", "counters_c5_192.md")).read()
+    monkeypatch.setattr(bench, "src_digest", lambda: re.search(r"csrc_sha:\s*([0-9a-f]+)", txt).group(1))
+    a = bench.profiled_traffic("fb_gather_deposit", 1000)
+    assert a is not None and bench.profiled_traffic("fb_gather_deposit", 2000) == pytest.approx(2 * a)
+    assert 100.0 < a / 1000 < 400.0  # bytes per pair of the 192^3 capture
 
 
 def test_cell_pass_hbm_sums_the_two_supernova_apply_kernels():
     box = _box()
-    km = {"fb_apply": (1.0, 2.9), "fb_apply_fp64": (1.0, 6.3), "sink_apply": (1.0, 7.2), "fb_zero": (1.0, 0.86)}
+    km = {"fb_apply": (1.0, 2.9), "fb_apply_fp64": (1.0, 6.3), "sink_apply": (1.0, 6.2), "sink_apply_fp64": (1.0, 1.0),
+          "fb_zero": (1.0, 0.86)}
     out = bench.cell_pass_hbm(km, box, 6793.4)
     assert out["fb_apply"]["ms"] == pytest.approx(9.2)
     assert out["fb_apply"]["GB/s"] == pytest.approx(120 * 512 ** 3 / 9.2e-3 / 1e9, rel=1e-3)
     assert out["sink_apply"]["bytes"] == 128 * 512 ** 3
+    assert out["sink_apply"]["ms"] == pytest.approx(7.2)
     assert out["fb_zero"]["bytes"] == 40 * box.ncells_padded
     assert "sink_spread" not in out  # a pass that was not timed is left out
 
