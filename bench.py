@@ -223,9 +223,8 @@ def cell_pass_hbm(kernel_ms, box, hbm_peak):
     perfect implementation moves) over the CUDA-event time of the launch, and
     the fraction of the measured copy bandwidth.  The supernova apply is the
     fast kernel plus the FP64 limiter on the queued cells (one phase, 120 B
-    per valid cell); the sink apply likewise (its common pass and the FP64
-    limiter on the queued cells; 128 B per valid cell with the eta it records
-    for Step 4)."""
+    per valid cell); the sink apply computes eta and updates the state in one
+    pass (128 B per valid cell with the eta it records for Step 4)."""
     nvalid, npad = box.ncells_valid, box.ncells_padded
     phases = {
         "fb_zero": (("fb_zero",), 40 * npad),
@@ -235,7 +234,7 @@ def cell_pass_hbm(kernel_ms, box, hbm_peak):
         "sink_cell_records": (("sink_cell_records",), (40 + 96) * nvalid),
         "sink_spread": (("sink_spread",), 136 * npad),
         "sink_fold": (("sink_fold",), 120 * (npad - nvalid)),
-        "sink_apply": (("sink_apply", "sink_apply_fp64"), 128 * nvalid),
+        "sink_apply": (("sink_apply",), 128 * nvalid),
     }
     out = {}
     for name, (kernels, nbytes) in phases.items():
@@ -385,13 +384,12 @@ def run_ours(args, world, rank, local):
     # own kernels per step (the CUB sorts, scans and run encoding are library
     # kernels).  ATOMIC: supernova pass zero, prologue, plan + gather +
     # deposit, fold, apply (fast + queued) = 6; sink pass zero, prologue,
-    # per-cell records, plan + gather + deposit, spread, fold, eta + apply
-    # (common + queued), Step-4 return = 9.  SORTED: plan + gather, pair
-    # values, keys, run and long-run kernels in place of the fused kernel
-    # (supernovae 10); sinks plan, gather, pair values, keys, runs, long runs,
-    # no spread (13).  ROUNDED: a deposit and a rounding kernel per pass
-    # (8 + 11).
-    launches_per_step = {"atomic": 15, "sorted": 23, "rounded": 19}[args.mode]
+    # per-cell records, plan + gather + deposit, spread, fold, eta + apply,
+    # Step-4 return = 8.  SORTED: plan + gather, pair values, keys, run and
+    # long-run kernels in place of the fused kernel (supernovae 10); sinks
+    # plan, gather, pair values, keys, runs, long runs, no spread (12).
+    # ROUNDED: a deposit and a rounding kernel per pass (8 + 10).
+    launches_per_step = {"atomic": 14, "sorted": 22, "rounded": 18}[args.mode]
     state0 = state.clone()
     sink0 = {k: sk[k].clone() for k in ("m", "px", "py", "pz")}
 

@@ -128,9 +128,6 @@ Layout layout(const pmp_params &p, long long n, long long nvalid, int mode)
         L.aux = take(8 * 2 * (size_t)pmp::kRec * (size_t)(nvalid > 0 ? nvalid : 1));
         // ATOMIC: each pair's removal a, stored by the fused deposit for Step 4
         if (mode == PMP_MODE_ATOMIC) L.pa = take(8 * pairs);
-        // cells whose eta the sink apply's first pass leaves to the FP64 limiter
-        L.queue = take(4 * (size_t)(nvalid > 0 ? nvalid : 1));
-        L.qcount = take(8);
     } else {
         L.queue = take(4 * (size_t)(nvalid > 0 ? nvalid : 1));
         L.qcount = take(8);
@@ -815,17 +812,8 @@ pmp_status pmp_apply_limited(pmp_ctx *ctx, pmp_mesh *state, const pmp_mesh *buff
             return PMP_ERR_CUDA;
         {
             // Steps 3 + 5; Step 4 reads only the records and the particles
-            char *w = static_cast<char *>(workspace);
-            unsigned *queue = reinterpret_cast<unsigned *>(w + L.queue);
-            unsigned long long *qc = reinterpret_cast<unsigned long long *>(w + L.qcount);
-            if (cudaMemsetAsync(qc, 0, sizeof(unsigned long long), st) != cudaSuccess) return PMP_ERR_CUDA;
-            {
-                Timed tm(ctx, "apply");
-                pmp::launch_sink_eta_apply(P, S, state->data, B, buffer->data, pl.drec, eta_out, queue, qc, st);
-            }
-            Timed tm(ctx, "apply_fp64");
-            pmp::launch_sink_eta_apply_slow(P, S, state->data, B, buffer->data, pl.drec, eta_out, queue, qc, ctx->st,
-                                            st);
+            Timed tm(ctx, "apply");
+            pmp::launch_sink_eta_apply(P, S, state->data, B, buffer->data, pl.drec, eta_out, ctx->st, st);
         }
         if (n > 0 && ctx->plan_has_a) {
             Timed tm(ctx, "return");

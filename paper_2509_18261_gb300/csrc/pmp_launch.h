@@ -107,16 +107,10 @@ void launch_sink_spread(const Box &S, const Box &B, double *b, const double *scr
                         cudaStream_t stream);
 void launch_sink_aux(const KParams &P, const Box &S, const double *u, double *grec, double *drec,
                      cudaStream_t stream);
-// Steps 3 + 5 for sinks, first pass: eta = 1 and U += Delta U^sum where no
-// FP64 work decides it (eta into the D records, for Step 4); the other cells
-// queued for the second pass.
+// Steps 3 + 5 for sinks: eta per valid cell (into the D records, for Step 4)
+// and U += eta Delta U^sum, in one pass.
 void launch_sink_eta_apply(const KParams &P, const Box &S, double *u, const Box &B, const double *b, double *drec,
-                           double *eta_out, unsigned *queue, unsigned long long *qcount, cudaStream_t stream);
-// The cells the first pass queued, through the FP64 limiter (counts limited
-// cells in st->n_limited).
-void launch_sink_eta_apply_slow(const KParams &P, const Box &S, double *u, const Box &B, const double *b,
-                                double *drec, double *eta_out, const unsigned *queue,
-                                const unsigned long long *qcount, DevStatus *st, cudaStream_t stream);
+                           double *eta_out, DevStatus *st, cudaStream_t stream);
 void launch_apply_fb_fast(const Box &S, double *u, const Box &B, const double *b, double *eta_out, unsigned *queue,
                           unsigned long long *qcount, cudaStream_t stream);
 void launch_apply_fb_slow(const Box &S, double *u, const Box &B, const double *b, double *eta_out,

@@ -405,122 +405,107 @@ __device__ __forceinline__ bool removal_positive(double d0)
     return (b0 >> 63) != 0 && mag2 != 0 && mag2 <= (0x7ff0000000000000ULL << 1);
 }
 
-// Steps 3 + 5 for sinks, first pass over the valid cells: eta = 1 wherever
-// it is decided without FP64 work -- no removal (from the bits of
-// Delta rho^sum) or the FP32 pre-test above -- and those cells are updated,
-// U += Delta U^sum, with eta = 1 written to the cell's D record for Step 4.
-// The other cells are queued for k_sink_eta_apply_slow, so that the FP64
-// branch of the limiter, which about one cell in twenty takes, is issued for
-// full warps of such cells rather than for every warp in which one lane takes
-// it.  Queue slots are reserved per chunk of a block, as in k_apply_fb_fast;
-// the queue's order does not matter.  Step 4 reads only the records, the
-// particles and the plan, never the state, so it can follow these passes.
-__global__ void __launch_bounds__(kApplyThreads, 4) k_sink_eta_apply(KParams P, Box S, double *__restrict__ u, Box B,
+// One cell's Steps 3 + 5 for sinks once eta is known: eta to the D record
+// (Step 4 reads it there) and to eta_out, U += eta Delta U^sum (one eta for
+// every field; a cell whose change is zero in every field is left as it is).
+__device__ __forceinline__ void sink_update(const Box &S, double *__restrict__ u, long long v, long long cs,
+                                            const double U[NF], const double D[NF], double e,
+                                            double *__restrict__ drec, double *__restrict__ eta_out)
+{
+    drec[v * kRec + 5] = e;
+    if (eta_out) eta_out[v] = e;
+    if (all_zero(D)) return;
+    if (e == 1.0) {
+#pragma unroll
+        for (int f = 0; f < NF; ++f) u[(long long)f * S.fs + cs] = U[f] + D[f];
+    } else {
+#pragma unroll
+        for (int f = 0; f < NF; ++f) u[(long long)f * S.fs + cs] = U[f] + e * D[f];
+    }
+}
+
+constexpr int kSinkPend = 64;  // cells a warp holds back for its FP64 limiter batch
+
+// Steps 3 + 5 for sinks in one pass over the valid cells, a warp taking 32
+// consecutive cells at a time.  eta = 1 wherever it is decided without FP64
+// work -- no removal (from the bits of Delta rho^sum) or the FP32 pre-test
+// above -- and those cells are updated at once.  The cells left undecided
+// (about one in twenty) are held back, with their loaded state and summed
+// change, in the warp's shared-memory list; whenever it holds 32 of them the
+// warp runs the FP64 limiter on all 32 lanes.  Issued cell by cell in place,
+// that branch would take the FP64 pipe for every warp in which one lane
+// takes it.  Every decision is the FP64 one.  Step 4 reads only the records,
+// the particles and the plan, never the state, so it can follow this pass.
+// Limited cells are counted per block.
+__global__ void __launch_bounds__(kApplyThreads, 3) k_sink_eta_apply(KParams P, Box S, double *__restrict__ u, Box B,
                                                                      const double *__restrict__ b,
                                                                      double *__restrict__ drec,
-                                                                     double *__restrict__ eta_out,
-                                                                     unsigned *__restrict__ queue,
-                                                                     unsigned long long *__restrict__ qcount)
+                                                                     double *__restrict__ eta_out, DevStatus *st)
 {
-    __shared__ unsigned wofs[kApplyThreads / 32];
-    __shared__ unsigned long long qbase;
+    constexpr int kW = kApplyThreads / 32;
+    __shared__ double pend[kW][kSinkPend][2 * NF];
+    __shared__ long long pcell[kW][kSinkPend];
+    __shared__ unsigned sh[kW];
     const long long nvalid = (long long)S.n0 * S.n1 * S.n2;
-    constexpr long long per = (long long)kApplyThreads * kApplyChunk;
-    const long long nchunks = (nvalid + per - 1) / per;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    for (long long ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
-        const long long c0 = ch * per + threadIdx.x;
-        unsigned mask = 0;
+    const unsigned lt = (1u << lane) - 1u;
+    unsigned nl = 0;
+    int npend = 0;  // the same in every lane
+    // the limiter on pending entry q (one lane)
+    auto limit = [&](int q) {
+        const long long v = pcell[wid][q];
+        const double *e_ = pend[wid][q];
+        double U[NF], D[NF];
 #pragma unroll
-        for (int c = 0; c < kApplyChunk; ++c) {
-            const long long v = c0 + (long long)c * kApplyThreads;
-            if (v >= nvalid) break;
+        for (int f = 0; f < NF; ++f) {
+            U[f] = e_[f];
+            D[f] = e_[NF + f];
+        }
+        int i, j, k;
+        cell_of(S, v, nvalid, i, j, k);
+        const double e = sink_eta_fp64(P, U[0], D[0], __ldg(drec + v * kRec));
+        nl += e < 1.0;
+        sink_update(S, u, v, S.at(i, j, k), U, D, e, drec, eta_out);
+    };
+    const long long step = (long long)gridDim.x * kApplyThreads;
+    for (long long v0 = ((long long)blockIdx.x * kW + wid) * 32; v0 < nvalid; v0 += step) {
+        const long long v = v0 + lane;
+        bool need = false;
+        long long cs = 0;
+        double U[NF], D[NF];
+        if (v < nvalid) {
             int i, j, k;
             cell_of(S, v, nvalid, i, j, k);
-            const long long cs = S.at(i, j, k), cb = B.at(i, j, k);
-            double U[NF], D[NF];
+            cs = S.at(i, j, k);
+            const long long cb = B.at(i, j, k);
 #pragma unroll
             for (int f = 0; f < NF; ++f) {
                 D[f] = __ldg(b + (long long)f * B.fs + cb);
                 U[f] = u[(long long)f * S.fs + cs];
             }
-            if (removal_positive(D[0]) && !sink_eta_one_f32(P, U[0], D[0])) {
-                mask |= 1u << c;
-                continue;
+            need = removal_positive(D[0]) && !sink_eta_one_f32(P, U[0], D[0]);
+        }
+        const unsigned m = __ballot_sync(0xffffffffu, need);
+        if (need) {
+            const int q = npend + __popc(m & lt);
+            pcell[wid][q] = v;
+#pragma unroll
+            for (int f = 0; f < NF; ++f) {
+                pend[wid][q][f] = U[f];
+                pend[wid][q][NF + f] = D[f];
             }
-            drec[v * kRec + 5] = 1.0;
-            if (eta_out) eta_out[v] = 1.0;
-            if (!all_zero(D)) {
-#pragma unroll
-                for (int f = 0; f < NF; ++f) u[(long long)f * S.fs + cs] = U[f] + D[f];
-            }
+        } else if (v < nvalid) {
+            sink_update(S, u, v, cs, U, D, 1.0, drec, eta_out);
         }
-        const unsigned cnt = __popc(mask);
-        unsigned incl = cnt;
-#pragma unroll
-        for (int d = 1; d < 32; d <<= 1) {
-            const unsigned t = __shfl_up_sync(0xffffffffu, incl, d);
-            if (lane >= d) incl += t;
-        }
-        if (lane == 31) wofs[wid] = incl;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            unsigned tot = 0;
-            for (int q = 0; q < kApplyThreads / 32; ++q) {
-                const unsigned t = wofs[q];
-                wofs[q] = tot;
-                tot += t;
-            }
-            qbase = tot ? atomicAdd(qcount, (unsigned long long)tot) : 0ULL;
-        }
-        __syncthreads();
-        unsigned long long pos = qbase + wofs[wid] + (incl - cnt);
-#pragma unroll
-        for (int c = 0; c < kApplyChunk; ++c)
-            if ((mask >> c) & 1u) queue[pos++] = (unsigned)(c0 + (long long)c * kApplyThreads);
-        __syncthreads();  // wofs and qbase are rewritten by the next chunk
-    }
-}
-
-// Second pass: the queued cells through the FP64 limiter, then U += eta
-// Delta U^sum (one eta for all five fields), eta to the D record; limited
-// cells are counted per block.
-__global__ void __launch_bounds__(kApplyThreads) k_sink_eta_apply_slow(KParams P, Box S, double *__restrict__ u, Box B,
-                                                                       const double *__restrict__ b,
-                                                                       double *__restrict__ drec,
-                                                                       double *__restrict__ eta_out,
-                                                                       const unsigned *__restrict__ queue,
-                                                                       const unsigned long long *__restrict__ qcount,
-                                                                       DevStatus *st)
-{
-    __shared__ unsigned sh[kApplyThreads / 32];
-    const long long nvalid = (long long)S.n0 * S.n1 * S.n2;
-    const unsigned long long n = *qcount;
-    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
-    unsigned nl = 0;
-    for (unsigned long long q = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += stride) {
-        const long long v = queue[q];
-        int i, j, k;
-        cell_of(S, v, nvalid, i, j, k);
-        const long long cs = S.at(i, j, k), cb = B.at(i, j, k);
-        double U[NF], D[NF];
-#pragma unroll
-        for (int f = 0; f < NF; ++f) {
-            D[f] = __ldg(b + (long long)f * B.fs + cb);
-            U[f] = u[(long long)f * S.fs + cs];
-        }
-        const double e = sink_eta_fp64(P, U[0], D[0], __ldg(drec + v * kRec));
-        drec[v * kRec + 5] = e;
-        if (eta_out) eta_out[v] = e;
-        nl += e < 1.0;
-        if (e == 1.0) {
-#pragma unroll
-            for (int f = 0; f < NF; ++f) u[(long long)f * S.fs + cs] = U[f] + D[f];
-        } else {
-#pragma unroll
-            for (int f = 0; f < NF; ++f) u[(long long)f * S.fs + cs] = U[f] + e * D[f];
+        npend += __popc(m);
+        __syncwarp();
+        if (npend >= 32) {
+            limit(npend - 32 + lane);
+            npend -= 32;
+            __syncwarp();
         }
     }
+    if (lane < npend) limit(lane);
     block_add(&st->n_limited, nl, sh);
 }
 
@@ -768,21 +753,12 @@ static unsigned resident_grid(K kernel, int threads, long long need)
 }
 
 void launch_sink_eta_apply(const KParams &P, const Box &S, double *u, const Box &B, const double *b, double *drec,
-                           double *eta_out, unsigned *queue, unsigned long long *qcount, cudaStream_t stream)
+                           double *eta_out, DevStatus *st, cudaStream_t stream)
 {
     const long long nvalid = (long long)S.n0 * S.n1 * S.n2;
     if (nvalid == 0) return;
-    const long long per = (long long)kApplyThreads * kApplyChunk;
-    const unsigned grid = resident_grid(k_sink_eta_apply, kApplyThreads, (nvalid + per - 1) / per);
-    k_sink_eta_apply<<<grid, kApplyThreads, 0, stream>>>(P, S, u, B, b, drec, eta_out, queue, qcount);
-}
-
-void launch_sink_eta_apply_slow(const KParams &P, const Box &S, double *u, const Box &B, const double *b,
-                                double *drec, double *eta_out, const unsigned *queue,
-                                const unsigned long long *qcount, DevStatus *st, cudaStream_t stream)
-{
-    const unsigned grid = resident_grid(k_sink_eta_apply_slow, kApplyThreads, 1LL << 40);
-    k_sink_eta_apply_slow<<<grid, kApplyThreads, 0, stream>>>(P, S, u, B, b, drec, eta_out, queue, qcount, st);
+    const unsigned grid = resident_grid(k_sink_eta_apply, kApplyThreads, (nvalid + kApplyThreads - 1) / kApplyThreads);
+    k_sink_eta_apply<<<grid, kApplyThreads, 0, stream>>>(P, S, u, B, b, drec, eta_out, st);
 }
 
 void launch_apply_fb_fast(const Box &S, double *u, const Box &B, const double *b, double *eta_out, unsigned *queue,
