@@ -352,12 +352,41 @@ def peaks():
 # our arm
 # ---------------------------------------------------------------------------
 
+def gpu_local_cpus(local):
+    """CPUs of the NUMA node the GPU hangs off (sysfs local_cpulist of its
+    PCI function), or None.  Pinned host buffers allocated by a thread on
+    those CPUs are placed in that node's memory."""
+    try:
+        out = subprocess.run(["nvidia-smi", "-i", str(local), "--query-gpu=pci.bus_id", "--format=csv,noheader"],
+                             capture_output=True, text=True, timeout=30).stdout.strip().lower()
+        if not out:
+            return None
+        dom, rest = out.split(":", 1)
+        bdf = f"{int(dom, 16) & 0xffff:04x}:{rest}"
+        spec = open(f"/sys/bus/pci/devices/{bdf}/local_cpulist").read().strip()
+        cpus = set()
+        for part in spec.split(","):
+            a, _, b = part.partition("-")
+            cpus.update(range(int(a), int(b or a) + 1))
+        return cpus or None
+    except Exception:
+        return None
+
+
 def run_ours(args, world, rank, local):
     import numpy as np
     import torch
 
     import __graft_entry__
 
+    # keep the host side (and the pinned buffers of the end-to-end leg) next
+    # to the GPU's memory controller
+    cpus = gpu_local_cpus(local)
+    if cpus:
+        try:
+            os.sched_setaffinity(0, cpus & os.sched_getaffinity(0) or cpus)
+        except OSError:
+            pass
     __graft_entry__.build()
     from paper_2509_18261_gb300 import pmp
     from paper_2509_18261_gb300 import synthetic as syn
@@ -529,6 +558,7 @@ def run_ours(args, world, rank, local):
         "e2e": e2e,
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clk,
+        "host_affinity": (f"{len(cpus)} CPUs local to the GPU" if cpus else "unchanged"),
     }
     result["sink_creation_c5_512"] = creation
     result["pm_deposit_c5_512"] = pm_deposit(args, w, state, fb, stream)

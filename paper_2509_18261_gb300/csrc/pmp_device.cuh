@@ -409,13 +409,7 @@ enum { MS_VK = 0, MS_Q, MS_ROWS = MS_Q + NF };  // V_K, then (m, p, e) / V_K
 // Sec. 3.2.1 from the omega-weighted sums over the kernel: sw = sum omega,
 // sr = sum omega rho, sp = sum omega p.  Writes the 12 feedback rows of one
 // particle (G at its row 0, row stride gs); false if a result is not finite.
-// Inlining of the per-particle finishing of the supernova gather (a
-// compile-time choice: the fused kernels' instruction footprint).
-#ifndef PMP_ROWS_INLINE
-#define PMP_ROWS_INLINE __forceinline__
-#endif
-
-__device__ PMP_ROWS_INLINE bool fb_gather_rows(const KParams &P, double sw, double sr, double sp0, double sp1,
+__device__ __forceinline__ bool fb_gather_rows(const KParams &P, double sw, double sr, double sp0, double sp1,
                                                double sp2, double m, double pe0, double pe1, double pe2, double Esn,
                                                double *G, long long gs)
 {
