@@ -264,6 +264,24 @@ def src_digest():
     return h.hexdigest()[:16]
 
 
+def profiled_row(kernel):
+    """The row of `kernel` (bench name) in the committed one-kernel ncu
+    capture on the 192^3 shrink, if it was taken on the current kernel
+    sources: dict(fp64_per_unit, bytes_per_unit), else None."""
+    path = os.path.join(ROOT, "profiles", "counters_c5_192.md")
+    if not os.path.exists(path):
+        return None
+    txt = open(path).read()
+    m = re.search(r"csrc_sha:\s*([0-9a-f]+)", txt)
+    if not m or m.group(1) != src_digest():
+        return None
+    for line in txt.splitlines():
+        cols = [c.strip() for c in line.strip().strip("|").split("|")]
+        if len(cols) == 13 and cols[1] == kernel:
+            return {"fp64_per_unit": float(cols[11]), "bytes_per_unit": float(cols[12])}
+    return None
+
+
 def profiled_traffic(kernel, units):
     """DRAM bytes of one launch of `kernel` processing `units` (pairs or
     cells): the DRAM bytes per unit of the committed one-kernel ncu capture
@@ -514,6 +532,13 @@ def run_ours(args, world, rank, local):
         roof["peak_measured"] = measured["fp64_tflops"]
         roof["frac_measured"] = roof["achieved"] / measured["fp64_tflops"]
         roof["peak_measured_source"] = "FP64 DFMA probe on this GPU, same run (pmp_probe_fp64)"
+        row = profiled_row(dominant)
+        kind = dominant.split("_", 1)[0]
+        if row and pairs.get(kind):
+            # issued FP64 lane-operations (ncu, 192^3) over the FP64 issue peak (a DFMA = 2 flops)
+            rate = row["fp64_per_unit"] * pairs[kind] / (kernel_ms[dominant][1] * 1e-3) / 1e12
+            roof["fp64_issue"] = {"lane_ops_per_pair": row["fp64_per_unit"], "T_lane_ops_per_s": rate,
+                                  "peak": measured["fp64_tflops"] / 2.0, "frac": rate / (measured["fp64_tflops"] / 2.0)}
     if dominant == "fb_gather_deposit":
         # the same launch seen as an HBM kernel: algorithmic bytes over time
         touched = touched_cells(P_fb, w["fb_params"], box, state0, fb)

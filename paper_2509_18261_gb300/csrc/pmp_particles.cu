@@ -833,9 +833,10 @@ __global__ void __launch_bounds__(kSinkThreads) k_gather_sink(KParams P, Box S, 
 }
 
 // Blocks per SM of the fused sink kernel (0: an L2 window of sinks in
-// flight, as the sink gather).
+// flight, as the sink gather; the default 6 is the measured best, see
+// PMP_SINK_PASS1_MINB).
 #ifndef PMP_SINK_PASS1_BPS
-#define PMP_SINK_PASS1_BPS 0
+#define PMP_SINK_PASS1_BPS 6
 #endif
 
 // Per-warp shared memory of k_pass1_sink: the plan's FP32 centre squares
@@ -856,7 +857,15 @@ __host__ __device__ constexpr int pass1_sink_warp_bytes(int W)
 //      lanes over the pairs (as k_deposit_atomic); k_sink_spread completes
 //      Step 1.
 template <int R>
-__global__ void __launch_bounds__(128) k_pass1_sink(KParams P, Box S, const double *__restrict__ u, Box B,
+// Resident blocks per SM the fused sink kernel is compiled for (78
+// registers, no spills) and launched with.  512^3 sweep of (compiled for,
+// launched): (any, 4) 24.6 ms, (6, 6) 23.7 ms, (6, 5) 24.8 ms, (8, 8) 31.9 ms,
+// (any, 3) 30.8 ms: more sinks in flight than about one L2 of cell records
+// costs more than the extra warps gain.
+#ifndef PMP_SINK_PASS1_MINB
+#define PMP_SINK_PASS1_MINB 6
+#endif
+__global__ void __launch_bounds__(128, PMP_SINK_PASS1_MINB) k_pass1_sink(KParams P, Box S, const double *__restrict__ u, Box B,
                                                     double *__restrict__ scr, Parts p, PlanPtrs pl,
                                                     double *__restrict__ G, DevStatus *st)
 {

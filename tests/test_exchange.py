@@ -145,6 +145,33 @@ def test_decomposed_pass_equals_the_one_rank_pass(orc, kind, n_ranks):
         assert ref["counts"][0] > 0  # the limiter acted
 
 
+@pytest.mark.parametrize("supergrid,n_ranks", [((1, 2, 3), 2), ((2, 2, 2), 3), ((2, 1, 1), 2), ((3, 1, 2), 3)])
+@pytest.mark.parametrize("kind", KINDS)
+def test_decomposition_of_thin_super_grids(orc, kind, supergrid, n_ranks):
+    """Super-grids one or two patches wide: a patch is its own neighbour
+    across an axis, or the same remote patch is the neighbour on both sides
+    (two different slabs of one proxy)."""
+    rng, batch, state = mr.small_batch(11 + sum(supergrid), supergrid=supergrid)
+    if kind == "sink":
+        for p in range(batch.np):
+            v = batch.valid(state, p)
+            v[0] *= 4.0
+            v[4] *= 4.0
+    parts, first = mr.boundary_particles(rng, batch, kind)
+    params = _params(kind)
+    rank_of, plans = _plans(batch, first, n_ranks)
+    ranks = [mr.OracleRank(orc, params, pl, batch, state, parts, first) for pl in plans]
+    mr.exchange_in_process(ranks, xch.STATE)
+    for r in ranks:
+        r.deposit()
+    mr.exchange_in_process(ranks, xch.GHOST)
+    if kind == "sink":
+        mr.exchange_in_process(ranks, xch.FOLDED)
+    for r in ranks:
+        r.finish()
+    _compare(orc, kind, batch, state, parts, first, ranks, rank_of)
+
+
 def _gloo_rank(rank, world, port, kind, out_dir):
     import torch
     import torch.distributed as dist
