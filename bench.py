@@ -432,11 +432,12 @@ def run_ours(args, world, rank, local):
     # kernels).  ATOMIC: supernova pass zero, prologue, plan + gather +
     # deposit, fold, apply (fast + queued) = 6; sink pass zero, prologue,
     # per-cell records, plan + gather + deposit, spread, fold, eta + apply,
-    # Step-4 return = 8.  SORTED: plan + gather, pair values, keys, run and
-    # long-run kernels in place of the fused kernel (supernovae 10); sinks
-    # plan, gather, pair values, keys, runs, long runs, no spread (12).
-    # ROUNDED: a deposit and a rounding kernel per pass (8 + 10).
-    launches_per_step = {"atomic": 14, "sorted": 22, "rounded": 18}[args.mode]
+    # Step-4 return = 8.  SORTED: plan + gather, pair values (with the sort's
+    # keys), run and long-run kernels in place of the fused kernel
+    # (supernovae 9); sinks plan, gather, pair values, runs, long runs, no
+    # spread (11).  ROUNDED: a deposit and a rounding kernel per pass
+    # (8 + 10).
+    launches_per_step = {"atomic": 14, "sorted": 20, "rounded": 18}[args.mode]
     state0 = state.clone()
     sink0 = {k: sk[k].clone() for k in ("m", "px", "py", "pz")}
 

@@ -733,11 +733,7 @@ pmp_status pmp_deposit(pmp_ctx *ctx, const pmp_mesh *state, const pmp_particles 
     double *pv = reinterpret_cast<double *>(w + L.spv);
     {
         Timed tm(ctx, "pair_values");
-        pmp::launch_pair_values(P, S, state->data, q, gathered, pl, offsets, pv, st);
-    }
-    {
-        Timed tm(ctx, "sort_keys");
-        pmp::launch_sort_keys(P, B, q, pl, offsets, k1, v1, st);
+        pmp::launch_pair_values(P, S, state->data, B, q, gathered, pl, offsets, pv, k1, v1, st);
     }
     int end_bit = 1;
     while (end_bit < 32 && (1LL << end_bit) < B.ncells) ++end_bit;

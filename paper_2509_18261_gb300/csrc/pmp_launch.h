@@ -59,13 +59,14 @@ void launch_pass1_sink(const KParams &P, const Box &S, const double *u, const Bo
 // completes Step 1.
 void launch_deposit_atomic(const KParams &P, const Box &S, const double *u, const Box &B, double *b, const Parts &p,
                            const double *G, const PlanPtrs &pl, double *E, double *scr, cudaStream_t stream);
-void launch_sort_keys(const KParams &P, const Box &B, const Parts &p, const PlanPtrs &pl,
-                      const unsigned long long *offsets, unsigned *keys, unsigned *vals, cudaStream_t stream);
 // Sorted deposit, first part: every pair's deposition value (the same
 // function and operations as the atomic deposit) stored at
-// pv[(offsets[s] + q) * 5 + f] for pair q of particle s (index order).
-void launch_pair_values(const KParams &P, const Box &S, const double *u, const Parts &p, const double *G,
-                        const PlanPtrs &pl, const unsigned long long *offsets, double *pv, cudaStream_t stream);
+// pv[(offsets[s] + q) * 5 + f] for pair q of particle s (index order), with
+// its buffer cell in keys[offsets[s] + q] and offsets[s] + q in vals (the
+// pair sort's input).
+void launch_pair_values(const KParams &P, const Box &S, const double *u, const Box &B, const Parts &p,
+                        const double *G, const PlanPtrs &pl, const unsigned long long *offsets, double *pv,
+                        unsigned *keys, unsigned *vals, cudaStream_t stream);
 // Sorted deposit, second part, per run of equal buffer cells (uniq/lens/offs
 // from encode_runs and scan_lengths; nruns on the device): the run's stored
 // pair values added in list order on top of the buffer value; short runs one

@@ -1001,15 +1001,19 @@ __device__ __forceinline__ void fb_pair_delta_d(const double *__restrict__ u, co
                    d2, dd, dU);
 }
 
-// With pv (sorted mode: index order, no perm), each pair's value is stored
-// at pv[(offs[t] + q) * 5 + f] instead of added into the buffer.
+// With pv (sorted mode: index order, no perm), pair q of particle t, the
+// (offs[t] + q)-th of the index-order list, stores its value at
+// pv[(offs[t] + q) * 5 + f], its buffer cell at skeys[offs[t] + q] and its
+// place offs[t] + q at svals[offs[t] + q] (the sort's keys and values)
+// instead of adding into the buffer.
 template <int R, bool FB>
 __global__ void __launch_bounds__(256) k_deposit_atomic(KParams P, Box S, const double *__restrict__ u, Box B,
                                                         double *__restrict__ b, Parts p,
                                                         const double *__restrict__ G, PlanPtrs pl,
                                                         double *__restrict__ E, double *__restrict__ scr,
                                                         double *__restrict__ pv,
-                                                        const unsigned long long *__restrict__ offs)
+                                                        const unsigned long long *__restrict__ offs,
+                                                        unsigned *__restrict__ skeys, unsigned *__restrict__ svals)
 {
     constexpr int W = 2 * R + 1;
     constexpr int TAB = kPartsPerWarp * 3 * W;  // per warp: [8 particles][3 axes][W offsets]
@@ -1135,9 +1139,12 @@ __global__ void __launch_bounds__(256) k_deposit_atomic(KParams P, Box S, const 
                     dU[4] = -(a * d2.x);
                 }
                 if (pv) {
-                    double *o = pv + (offs[t0 + j] + (g - before)) * NF;
+                    const unsigned long long idx = offs[t0 + j] + (g - before);
+                    double *o = pv + idx * NF;
 #pragma unroll
                     for (int f = 0; f < NF; ++f) o[f] = dU[f];
+                    skeys[idx] = (unsigned)B.at(cell.i, cell.j, cell.k);
+                    svals[idx] = (unsigned)idx;
                     continue;
                 }
                 const long long bc = B.at(cell.i, cell.j, cell.k);
@@ -1162,24 +1169,6 @@ __global__ void __launch_bounds__(256) k_deposit_atomic(KParams P, Box S, const 
 // Step 1, sorted accumulation
 // ---------------------------------------------------------------------------
 
-// Compact (buffer cell, pair) lists in particle-index order (the sorted mode
-// plans in index order); offsets from the exclusive scan of the counts.  A
-// pair is named by its place o + q in that list, where its value is stored.
-__global__ void __launch_bounds__(128) k_sort_keys(KParams P, Box B, long long n, PlanPtrs pl,
-                                                   const unsigned long long *__restrict__ offsets,
-                                                   unsigned *__restrict__ keys, unsigned *__restrict__ vals)
-{
-    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= n) return;
-    const unsigned long long o = offsets[t];
-    const unsigned nc = pl.counts[t];
-    const unsigned long long b0 = (unsigned long long)t * pl.cap;
-    for (unsigned q = 0; q < nc; ++q) {
-        const PairCell c = unpack_pair(pl.slots[b0 + q], P.R);
-        keys[o + q] = (unsigned)B.at(c.i, c.j, c.k);
-        vals[o + q] = (unsigned)(o + q);  // the pair's place in the index-order list (its value's row)
-    }
-}
 
 
 constexpr unsigned kLongRun = 32;  // runs longer than this get a warp
@@ -1600,7 +1589,8 @@ void launch_pass1_sink(const KParams &P, const Box &S, const double *u, const Bo
 
 static void launch_pair_kernel(const KParams &P, const Box &S, const double *u, const Box &B, double *b,
                                const Parts &p, const double *G, const PlanPtrs &pl, double *E, double *scr,
-                               double *pv, const unsigned long long *offs, cudaStream_t stream)
+                               double *pv, const unsigned long long *offs, unsigned *skeys, unsigned *svals,
+                               cudaStream_t stream)
 {
     if (p.count == 0) return;
     // Only resident blocks: the grid-stride loop then moves all of them
@@ -1625,31 +1615,26 @@ static void launch_pair_kernel(const KParams &P, const Box &S, const double *u, 
     const unsigned nb = (unsigned)(blocks_needed < (long long)nsm * occ ? blocks_needed : (long long)nsm * occ);
     if (P.kind != PMP_KIND_SINK) {
         PMP_DISPATCH_R(P.R, (k_deposit_atomic<RR, true><<<nb, 256, 0, stream>>>(P, S, u, B, b, p, G, pl, E, nullptr,
-                                                                                 pv, offs)));
+                                                                                 pv, offs, skeys, svals)));
     } else {
         PMP_DISPATCH_R(P.R, (k_deposit_atomic<RR, false><<<nb, 256, 0, stream>>>(P, S, u, B, b, p, G, pl, E, scr,
-                                                                                  pv, offs)));
+                                                                                  pv, offs, skeys, svals)));
     }
 }
 
 void launch_deposit_atomic(const KParams &P, const Box &S, const double *u, const Box &B, double *b, const Parts &p,
                            const double *G, const PlanPtrs &pl, double *E, double *scr, cudaStream_t stream)
 {
-    launch_pair_kernel(P, S, u, B, b, p, G, pl, E, scr, nullptr, nullptr, stream);
+    launch_pair_kernel(P, S, u, B, b, p, G, pl, E, scr, nullptr, nullptr, nullptr, nullptr, stream);
 }
 
-void launch_pair_values(const KParams &P, const Box &S, const double *u, const Parts &p, const double *G,
-                        const PlanPtrs &pl, const unsigned long long *offsets, double *pv, cudaStream_t stream)
+void launch_pair_values(const KParams &P, const Box &S, const double *u, const Box &B, const Parts &p,
+                        const double *G, const PlanPtrs &pl, const unsigned long long *offsets, double *pv,
+                        unsigned *keys, unsigned *vals, cudaStream_t stream)
 {
-    launch_pair_kernel(P, S, u, S, nullptr, p, G, pl, nullptr, nullptr, pv, offsets, stream);
+    launch_pair_kernel(P, S, u, B, nullptr, p, G, pl, nullptr, nullptr, pv, offsets, keys, vals, stream);
 }
 
-void launch_sort_keys(const KParams &P, const Box &B, const Parts &p, const PlanPtrs &pl,
-                      const unsigned long long *offsets, unsigned *keys, unsigned *vals, cudaStream_t stream)
-{
-    if (p.count == 0) return;
-    k_sort_keys<<<blocks_for(p.count, 128), 128, 0, stream>>>(P, B, p.count, pl, offsets, keys, vals);
-}
 
 void launch_segment_sum(const Box &B, double *b, const double *pv, const unsigned long long *nruns,
                         const unsigned *uniq, const unsigned *lens, const unsigned *offs, const unsigned *vals,
