@@ -179,7 +179,7 @@ def kernel_cell_count(parts, n, rK, chunk=1 << 20):
 # Algorithmic work per kernel launch.  Particle kernels: canonical FP64
 # operations per (particle, kernel cell) pair; cell kernels: bytes a perfect
 # implementation moves.  See the kernel table of the design notes.
-FLOPS_PER_PAIR = {"fb_gather": 9, "fb_deposit": 29, "fb_gather_deposit": 9 + 29, "sink_gather": 8,
+FLOPS_PER_PAIR = {"fb_gather": 9, "fb_plan_gather": 9, "fb_deposit": 29, "sink_gather": 8,
                   "sink_deposit": 7, "sink_return": 14}
 FP32_PEAK_TOPS = 36.9  # measured FP32 instruction rate of this GB300 (dependent-free FFMA stream)
 
@@ -350,12 +350,17 @@ def measure_fp64_and_atomics():
     return out
 
 
-def alg_bytes_fb_pass1(n_fb, touched_state, touched_buf):
-    """Algorithmic bytes of one launch of the fused supernova plan + gather +
-    deposit: the particles read once (64 B), their 12 gathered rows written
-    (96 B), every touched state cell read once (40 B) and every touched
-    buffer cell read and written once (80 B)."""
-    return 160 * n_fb + 40 * touched_state + 80 * touched_buf
+def alg_bytes_fb(stage, n_fb, pairs, touched_state, touched_buf):
+    """Algorithmic bytes of one launch of the supernova plan + gather or
+    deposit kernel.  plan_gather: the particles read once (64 B), their 12
+    gathered rows written (96 B), every touched state cell read once (40 B)
+    and the plan written (8 B per pair).  deposit: positions and the six rows
+    it uses read (72 B per particle), the plan read (8 B per pair), every
+    touched state cell read once (40 B) and every touched buffer cell read
+    and written once (80 B)."""
+    if stage == "plan_gather":
+        return 160 * n_fb + 8 * pairs + 40 * touched_state
+    return 72 * n_fb + 8 * pairs + 40 * touched_state + 80 * touched_buf
 
 
 def peaks():
@@ -429,15 +434,14 @@ def run_ours(args, world, rank, local):
     phases = ["fb_zero", "fb_gather_deposit", "fb_fold", "fb_apply",
               "sink_zero", "sink_gather_deposit", "sink_fold", "sink_apply"]
     # own kernels per step (the CUB sorts, scans and run encoding are library
-    # kernels).  ATOMIC: supernova pass zero, prologue, plan + gather +
-    # deposit, fold, apply (fast + queued) = 6; sink pass zero, prologue,
+    # kernels).  ATOMIC: supernova pass zero, prologue, plan + gather,
+    # deposit, fold, apply (fast + queued) = 7; sink pass zero, prologue,
     # per-cell records, plan + gather + deposit, spread, fold, eta + apply,
-    # Step-4 return = 8.  SORTED: plan + gather, pair values (with the sort's
-    # keys), run and long-run kernels in place of the fused kernel
-    # (supernovae 9); sinks plan, gather, pair values, runs, long runs, no
-    # spread (11).  ROUNDED: a deposit and a rounding kernel per pass
-    # (8 + 10).
-    launches_per_step = {"atomic": 14, "sorted": 20, "rounded": 18}[args.mode]
+    # Step-4 return = 8.  SORTED: pair values (with the sort's keys), run and
+    # long-run kernels in place of the deposit (supernovae 9); sinks plan,
+    # gather, pair values, runs, long runs, no spread (11).  ROUNDED: a
+    # deposit and a rounding kernel per pass (8 + 10).
+    launches_per_step = {"atomic": 15, "sorted": 20, "rounded": 18}[args.mode]
     state0 = state.clone()
     sink0 = {k: sk[k].clone() for k in ("m", "px", "py", "pz")}
 
@@ -540,10 +544,10 @@ def run_ours(args, world, rank, local):
             rate = row["fp64_per_unit"] * pairs[kind] / (kernel_ms[dominant][1] * 1e-3) / 1e12
             roof["fp64_issue"] = {"lane_ops_per_pair": row["fp64_per_unit"], "T_lane_ops_per_s": rate,
                                   "peak": measured["fp64_tflops"] / 2.0, "frac": rate / (measured["fp64_tflops"] / 2.0)}
-    if dominant == "fb_gather_deposit":
+    if dominant in ("fb_plan_gather", "fb_deposit"):
         # the same launch seen as an HBM kernel: algorithmic bytes over time
         touched = touched_cells(P_fb, w["fb_params"], box, state0, fb)
-        ab = alg_bytes_fb_pass1(n_fb, touched["state"], touched["buffer"])
+        ab = alg_bytes_fb(dominant.split("_", 1)[1], n_fb, pairs["fb"], touched["state"], touched["buffer"])
         gbs = ab / (kernel_ms[dominant][1] * 1e-3) / 1e9
         roof["hbm_view"] = {"algorithmic_bytes": ab, "GB/s": gbs, "frac": gbs / hbm_peak,
                             "touched_cells": touched}

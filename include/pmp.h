@@ -222,14 +222,14 @@ pmp_status pmp_deposit(pmp_ctx *ctx, const pmp_mesh *state, const pmp_particles 
 
 /* pmp_gather followed by pmp_deposit (same arguments, same results: the
  * gathered rows, the plan in `workspace` and Step 1 into `buffer`).  For
- * supernovae and sinks in the ATOMIC mode plan, gather and deposit run as
- * one kernel: a warp plans, gathers and deposits 32 consecutive particles
- * before it takes the next, so the FP64 work of gather and deposit overlaps
- * the plan's integer work and the deposit re-reads cells the gather has
- * just read (sinks: the per-cell records are written first, the scratch is
- * spread after).  The buffer sums then differ from those of the two
- * separate calls only by the order of the atomic additions.  Other kinds
- * and modes run the two calls one after the other. */
+ * sinks in the ATOMIC mode plan, gather and deposit run as one kernel: a
+ * warp plans, gathers and deposits 32 consecutive sinks before it takes the
+ * next, so the FP64 work of gather and deposit overlaps the plan's integer
+ * work and the deposit re-reads cells the gather has just read (the
+ * per-cell records are written first, the scratch is spread after).  The
+ * buffer sums then differ from those of the two separate calls only by the
+ * order of the atomic additions.  Other kinds and modes run the two calls
+ * one after the other. */
 pmp_status pmp_gather_deposit(pmp_ctx *ctx, const pmp_mesh *state, const pmp_particles *particles, double *gathered,
                               pmp_mesh *buffer, int32_t mode, void *workspace, size_t workspace_bytes);
 
@@ -613,6 +613,18 @@ int32_t pmp_probe_threads(void);
 int32_t pmp_probe_chains(void);
 pmp_status pmp_probe_fp64(double *out, int32_t blocks, int32_t iters, pmp_stream stream);
 pmp_status pmp_probe_atomic(double *target, int64_t n_targets, int64_t n_adds, int32_t blocks, pmp_stream stream);
+
+/* The library's correctly rounded FP64 quotient and square root, computed
+ * from integer and FP32 instructions by digit recurrence (no paper
+ * counterpart: the kernels use them for the divisions and square roots of the
+ * formulas of Sec. 3.1-3.2, whose results they equal bit for bit).  For
+ * i < n: quot[i] = a[i] / b[i] and root[i] = sqrt(a[i]), rounded to nearest
+ * even as IEEE 754 binary64 prescribes (zero, subnormal, infinite and NaN
+ * operands included).  All four arrays are device memory of n doubles, owned
+ * by the caller; one launch is enqueued on `stream`.  PMP_ERR_ARG for n < 0 or
+ * a NULL array with n > 0; PMP_ERR_CUDA if the launch fails. */
+pmp_status pmp_exact_math(const double *a, const double *b, int64_t n, double *quot, double *root,
+                          pmp_stream stream);
 
 #ifdef __cplusplus
 }

@@ -524,7 +524,7 @@ pmp_status pmp_zero_buffer(pmp_ctx *ctx, pmp_mesh *buffer)
     return last_launch();
 }
 
-// pmp_gather; with `fused` (supernovae, ATOMIC, buffer checked by the caller)
+// pmp_gather; with `fused` (sinks, ATOMIC, buffer checked by the caller)
 // also Step 1 into that buffer, in the same launch as plan and gather.
 static pmp_status gather_impl(pmp_ctx *ctx, const pmp_mesh *state, const pmp_particles *particles, double *gathered,
                               int32_t mode, void *workspace, size_t workspace_bytes, pmp_mesh *fused)
@@ -588,20 +588,15 @@ static pmp_status gather_impl(pmp_ctx *ctx, const pmp_mesh *state, const pmp_par
             Box B;
             s = make_box(fused, &B);
             if (s) return s;
-            if (ctx->p.kind == PMP_KIND_FEEDBACK) {
+            // sinks: -a per pair into the scratch tail, then the cells' factors
+            double *scr = reinterpret_cast<double *>(w + ebuf_offset(L));
+            if (cudaMemsetAsync(scr, 0, tail_bytes(ctx->p, mode, fused), st) != cudaSuccess) return PMP_ERR_CUDA;
+            {
                 Timed tm(ctx, "gather_deposit");
-                pmp::launch_pass1_fb(P, S, state->data, B, fused->data, q, pl, gathered, ctx->st, st);
-            } else {
-                // sinks: -a per pair into the scratch tail, then the cells' factors
-                double *scr = reinterpret_cast<double *>(w + ebuf_offset(L));
-                if (cudaMemsetAsync(scr, 0, tail_bytes(ctx->p, mode, fused), st) != cudaSuccess) return PMP_ERR_CUDA;
-                {
-                    Timed tm(ctx, "gather_deposit");
-                    pmp::launch_pass1_sink(P, S, state->data, B, scr, q, pl, gathered, ctx->st, st);
-                }
-                Timed tm(ctx, "spread");
-                pmp::launch_sink_spread(S, B, fused->data, scr, pl.drec, st);
+                pmp::launch_pass1_sink(P, S, state->data, B, scr, q, pl, gathered, ctx->st, st);
             }
+            Timed tm(ctx, "spread");
+            pmp::launch_sink_spread(S, B, fused->data, scr, pl.drec, st);
         } else if (ctx->p.kind == PMP_KIND_FEEDBACK) {
             Timed tm(ctx, "plan_gather");
             pmp::launch_plan_gather_fb(P, S, state->data, q, pl, gathered, ctx->st, st);
@@ -635,7 +630,11 @@ pmp_status pmp_gather_deposit(pmp_ctx *ctx, const pmp_mesh *state, const pmp_par
                               pmp_mesh *buffer, int32_t mode, void *workspace, size_t workspace_bytes)
 {
     if (!ctx || !valid_mode(mode) || (particles && particles->count < 0)) return PMP_ERR_ARG;
-    if ((ctx->p.kind == PMP_KIND_FEEDBACK || ctx->p.kind == PMP_KIND_SINK) && mode == PMP_MODE_ATOMIC) {
+    // Sinks in the ATOMIC mode: plan, gather and deposit in one kernel.  The
+    // supernova kind runs plan + gather, then the deposit: since the square
+    // root and the division of Eq. du moved off the FP64 pipe, a kernel of all
+    // three phases is bound by instruction fetch and is slower than the two.
+    if (ctx->p.kind == PMP_KIND_SINK && mode == PMP_MODE_ATOMIC) {
         Box S, B;
         pmp_status s = check_pair(ctx, state, buffer, &S, &B);
         if (s) return s;

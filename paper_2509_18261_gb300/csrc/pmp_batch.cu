@@ -300,7 +300,7 @@ __device__ void gather_particle(const BArgs &a, long long s, SmemT<R> &sm)
                     v4 = U[3];
                 } else {
                     double cs, rtr;
-                    sink_cell(P, U, 1.0 / U[0], cs, rtr);
+                    sink_cell(P, U, exact::div_rn(1.0, U[0]), cs, rtr);
                     v0 = U[0];
                     v1 = U[1];
                     v2 = U[2];
@@ -469,7 +469,7 @@ __device__ void deposit_tile(const BArgs &a, const DepItem &it, SmemT<R> &sm)
                     const Owner o = owner_of(a.T, p, i, j, k);
                     load5(a.u, o.c, o.fs, U);
                     if (!FB) {
-                        const double inv = 1.0 / U[0];
+                        const double inv = exact::div_rn(1.0, U[0]);
                         tr = U[0] - P.ctr * sink_cs2(P, U, inv);
                         q1 = U[1] * inv;
                         q2 = U[2] * inv;
@@ -608,7 +608,7 @@ __device__ void return_sink(const BArgs &a, long long s, SmemT<R> &sm)
             folded_at(a, o.q, o.i, o.j, o.k, D, img);
             const double eta = sink_eta(P, U, D);
             // b = eta a and v = p inv; lane 0 fuses -b v into the sums
-            const double inv = 1.0 / U[0];
+            const double inv = exact::div_rn(1.0, U[0]);
             v0 = eta * (-dU[0]);
             v1 = U[1] * inv;
             v2 = U[2] * inv;

@@ -15,6 +15,7 @@
 #include <cuda_runtime.h>
 
 #include "pmp.h"
+#include "pmp_exact.cuh"
 
 namespace pmp {
 
@@ -199,8 +200,7 @@ __device__ __forceinline__ void load_cell(const double *__restrict__ u, const Bo
 }
 
 // Every quotient by rho in the sink formulas is a product with the one
-// reciprocal inv = 1/rho of the cell (a division costs the GB300 FP64 pipe
-// about six of its operations, a product one).
+// reciprocal inv = 1/rho of the cell (one division per cell instead of five).
 // Ideal-gas c_s^2 = gamma (gamma - 1) e_int / rho, e_int = E - |p|^2 / (2 rho)
 // clamped at 0, evaluated as e_int = E - |p|^2 (inv/2) and c_s^2 =
 // (gamma (gamma - 1) e_int) inv; c_s; and rho_Tr = J^2 pi c_s^2 / (G dx^2)
@@ -217,13 +217,13 @@ __device__ __forceinline__ void sink_cell(const KParams &P, const double U[NF], 
                                           double &rho_tr)
 {
     const double cs2 = sink_cs2(P, U, inv);
-    cs = sqrt(cs2);
+    cs = exact::sqrt_rn(cs2);
     rho_tr = P.ctr * cs2;
 }
 
 __device__ __forceinline__ double sink_rho_tr(const KParams &P, const double U[NF])
 {
-    return P.ctr * sink_cs2(P, U, 1.0 / U[0]);
+    return P.ctr * sink_cs2(P, U, exact::div_rn(1.0, U[0]));
 }
 
 // Accretion limiter of Sec. 3.1.1 composed with the density floor, on the
@@ -245,7 +245,7 @@ __device__ __forceinline__ double sink_eta(const KParams &P, const double U[NF],
     al = al > t ? al : t;
     al = al < fl ? al : fl;
     if (al < 0.0) al = 0.0;
-    return al < a ? al / a : 1.0;
+    return al < a ? exact::div_rn(al, a) : 1.0;
 }
 
 // Supernova momentum limiter (Eq. lambda) with T the pre-deposit temperature:
@@ -260,11 +260,11 @@ __device__ __forceinline__ double sn_lambda(const double U[NF], const double D[N
     const double rho1 = U[0] + D[0];
     const double E1 = U[4] + D[4];
     const double p2 = (U[1] * U[1] + U[2] * U[2]) + U[3] * U[3];
-    const double eint0 = U[4] - p2 / (2.0 * U[0]);
+    const double eint0 = U[4] - exact::div_rn(p2, 2.0 * U[0]);
     const double pn0 = U[1] + D[1], pn1 = U[2] + D[2], pn2 = U[3] + D[3];
     const double pnn = (pn0 * pn0 + pn1 * pn1) + pn2 * pn2;
-    const double therm = (eint0 * rho1) / U[0];
-    const double lhs = therm + pnn / (2.0 * rho1);
+    const double therm = exact::div_rn(eint0 * rho1, U[0]);
+    const double lhs = therm + exact::div_rn(pnn, 2.0 * rho1);
     if (lhs <= E1) return 1.0;
     const double A = (D[1] * D[1] + D[2] * D[2]) + D[3] * D[3];
     if (!(A > 0.0)) return 1.0;
@@ -275,16 +275,16 @@ __device__ __forceinline__ double sn_lambda(const double U[NF], const double D[N
         noroot = 1;
         return 0.0;
     }
-    const double sq = sqrt(disc);
+    const double sq = exact::sqrt_rn(disc);
     double hi, lo;
     if (B >= 0.0) {
         const double Q = -(B + sq);
-        hi = Q != 0.0 ? C / Q : 0.0;
-        lo = Q / A;
+        hi = Q != 0.0 ? exact::div_rn(C, Q) : 0.0;
+        lo = exact::div_rn(Q, A);
     } else {
         const double Q = sq - B;
-        hi = Q / A;
-        lo = C / Q;
+        hi = exact::div_rn(Q, A);
+        lo = exact::div_rn(C, Q);
     }
     if (hi < 0.0 || lo > 1.0) {
         noroot = 1;
@@ -365,8 +365,9 @@ __device__ __forceinline__ void feedback_delta(double w, const double U[NF], dou
                                                double dU[NF])
 {
     const double rn = U[0] + q;
-    const double dist = sqrt(dd);
-    const double s = dd > 0.0 ? (w * Pv) / dist : 0.0;
+    // sqrt and the quotient by integer digit recurrence (pmp_exact.cuh): the
+    // same correctly rounded values, off the FP64 pipe
+    const double s = exact::positive(dd) ? exact::div_rn(w * Pv, exact::sqrt_rn(dd)) : 0.0;
     const double pr0 = s * d0, pr1 = s * d1, pr2 = s * d2;
     dU[0] = w * q;
     dU[1] = fma(w, fma(rn, vc[0], -U[1]), pr0);
@@ -379,7 +380,7 @@ __device__ __forceinline__ void feedback_delta(double w, const double U[NF], dou
 // the max): a = max(K w, rho - rho_Tr), Delta U = -a (1, p inv, E inv).
 __device__ __forceinline__ void sink_delta(const KParams &P, const double U[NF], double K, double w, double dU[NF])
 {
-    const double inv = 1.0 / U[0];
+    const double inv = exact::div_rn(1.0, U[0]);
     const double rtr = P.ctr * sink_cs2(P, U, inv);
     const double bh = K * w;
     const double tr = U[0] - rtr;
@@ -405,6 +406,12 @@ enum { MS_VK = 0, MS_Q, MS_ROWS = MS_Q + NF };  // V_K, then (m, p, e) / V_K
 // gathered rows from the kernel sums (shared by the single-box and batched
 // gathers; the order of every operation is the oracle's)
 // ---------------------------------------------------------------------------
+
+// The per-particle formulas keep the compiler's FP64 division and sqrt: they
+// run once per particle, and the integer forms of pmp_exact.cuh inlined at
+// their dozen call sites made the fused plan + gather kernels' code large
+// enough to stall on instruction fetch (512^3: 25.0 -> 29.0 ms).  The
+// per-pair and per-cell formulas use the integer forms.
 
 // Sec. 3.2.1 from the omega-weighted sums over the kernel: sw = sum omega,
 // sr = sum omega rho, sp = sum omega p.  Writes the 12 feedback rows of one
@@ -522,7 +529,7 @@ __device__ __forceinline__ bool all_zero(const double D[NF])
 __device__ __forceinline__ double repro_round(double v, double e, int M)
 {
     if (v == 0.0 || !(e > 0.0)) return v;
-    const double r = e / fabs(v);
+    const double r = exact::div_rn(e, fabs(v));
     if (!(r > 0.0)) return v;  // underflow: N_bit < 0
     int nb = 52;
     if (r < 1.0) {

@@ -43,11 +43,6 @@ void launch_gather(const KParams &P, const Box &S, const double *u, const Parts 
 // as launch_plan followed by launch_gather).
 void launch_plan_gather_fb(const KParams &P, const Box &S, const double *u, const Parts &p, const PlanPtrs &pl,
                            double *G, DevStatus *st, cudaStream_t stream);
-// Supernova kind, ATOMIC mode: plan, gather and deposit in one launch (the
-// plan, rows and buffer of launch_plan_gather_fb followed by
-// launch_deposit_atomic, up to the order of the atomic additions).
-void launch_pass1_fb(const KParams &P, const Box &S, const double *u, const Box &B, double *b, const Parts &p,
-                     const PlanPtrs &pl, double *G, DevStatus *st, cudaStream_t stream);
 // Sink kind, ATOMIC mode: plan, gather and the scratch deposit (-a per pair
 // into scr, zeroed) in one launch; the per-cell records must be written
 // first, launch_sink_spread completes Step 1.

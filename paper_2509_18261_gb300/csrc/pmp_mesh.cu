@@ -314,7 +314,7 @@ __global__ void __launch_bounds__(256) k_sink_aux(KParams P, Box S, const double
     const int j = (int)(r % S.n1), k = (int)(r / S.n1);
     double U[NF], cs, rtr;
     load_cell(u, S, S.at(i, j, k), U);
-    const double inv = 1.0 / U[0];
+    const double inv = exact::div_rn(1.0, U[0]);
     sink_cell(P, U, inv, cs, rtr);
     double2 *g = reinterpret_cast<double2 *>(grec + v * kRec);
     g[0] = make_double2(U[0], U[1]);
@@ -658,8 +658,8 @@ __global__ void __launch_bounds__(256) k_create_apply(KParams P, Box S, double *
     double U[NF];
     load_cell(u, S, c, U);
     const double rtr = sink_rho_tr(P, U);
-    const double v0 = U[1] / U[0], v1 = U[2] / U[0], v2 = U[3] / U[0];
-    const double es = U[4] / U[0];
+    const double v0 = exact::div_rn(U[1], U[0]), v1 = exact::div_rn(U[2], U[0]), v2 = exact::div_rn(U[3], U[0]);
+    const double es = exact::div_rn(U[4], U[0]);
     const double ms = (U[0] - rtr) * P.V;
     x[q] = (double)i + 0.5;
     y[q] = (double)j + 0.5;

@@ -536,183 +536,6 @@ __global__ void __launch_bounds__(256, PMP_PLAN_GATHER_MINB) k_plan_gather_fb(KP
     }
 }
 
-// Resident blocks per SM the fused plan + gather + deposit is compiled for.
-// 512^3 sweep: 2 -> 58.5 ms, 3 -> 54.6 ms (80 registers, no spills), 4 ->
-// 52.9 ms (64 registers, 132 bytes spilled).
-#ifndef PMP_PASS1_MINB
-#define PMP_PASS1_MINB 4
-#endif
-
-// Per-warp shared memory of the deposit phase of k_pass1_fb: the deposit's
-// six per-particle quantities of the warp's 32 particles ([6][32]), the
-// centre offsets and their squares of 8 particles ([8][3][W] each), their
-// indices.
-__host__ __device__ constexpr int pass1_warp_bytes(int W)
-{
-    return (6 * 32 + 2 * kPartsPerWarp * 3 * W) * 8 + kPartsPerWarp * 8;
-}
-
-// Plan, gather and ATOMIC deposit of the supernova kind in one persistent
-// kernel (pmp_gather_deposit).  A warp takes 32 consecutive particles of the
-// processing order and
-//   1. plans them one after the other (warp per particle, as k_plan);
-//   2. gathers them, a lane per particle (as k_gather_fb), and keeps the
-//      deposit's quantities (v_COM, q, e, |p_radial| / V_snr) in shared memory;
-//   3. deposits their pairs 8 particles at a time, lanes over the pairs (as
-//      k_deposit_atomic).
-// The plan is bound by instruction issue, gather and deposit by the FP64
-// pipe: warps in different phases share an SM.  The deposit reads the cells
-// the gather has just read, and the slots the warp has just written (through
-// the coherent path, after the warp's barrier).
-template <int R, int SC>
-__global__ void __launch_bounds__(256, PMP_PASS1_MINB) k_pass1_fb(KParams P, Box S, const double *__restrict__ u, Box B,
-                                                                 double *__restrict__ b, Parts p, PlanPtrs pl,
-                                                                 double *__restrict__ G, DevStatus *st)
-{
-    constexpr int W = 2 * R + 1;
-    constexpr int W3 = W * W * W;
-    constexpr int TAB = kPartsPerWarp * 3 * W;
-    extern __shared__ __align__(16) unsigned char psm[];
-    __shared__ int ncand_sh;
-    __shared__ double wtab[kMaxS3 + 1];
-    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    const int Sn = SC ? SC : P.S;
-    unsigned *cand = reinterpret_cast<unsigned *>(psm);
-    const int wbytes = plan_warp_bytes(W, Sn);
-    const size_t head = (size_t)(W3 * 4 + 15) / 16 * 16;
-    unsigned char *wsm = psm + head + (size_t)wib * wbytes;
-    float *sub = reinterpret_cast<float *>(wsm);  // [3][W*S]
-    float *csq = sub + 3 * W * Sn;                // [3][W]
-    float *fc2 = csq + 3 * W;                     // [3][W]
-    unsigned short *stc = reinterpret_cast<unsigned short *>(wsm + ((3 * W * Sn + 6 * W) * 4 + 15) / 16 * 16);
-    unsigned short *blist = stc + W3;
-    double *rows = reinterpret_cast<double *>(psm + head + (size_t)nw * wbytes + (size_t)wib * pass1_warp_bytes(W));
-    double *dt = rows + 6 * 32, *qt = dt + TAB;
-    long long *sidt = reinterpret_cast<long long *>(qt + TAB);
-    for (int i = threadIdx.x; i <= P.S3; i += blockDim.x) wtab[i] = (double)i / (double)P.S3;
-    if (wib == 0) {
-        const int n = build_candidates(P.rK, R, cand);
-        if (lane == 0) ncand_sh = n;
-    }
-    __syncthreads();
-    const int ncand = ncand_sh;
-    const long long nwarps = (long long)gridDim.x * nw;
-    const long long gs = p.count;
-    for (long long t0 = ((long long)blockIdx.x * nw + wib) * 32; t0 < p.count; t0 += nwarps * 32) {
-        const long long tl = t0 + lane;
-        long long sl = 0;
-        unsigned long long hl = kNoHost;
-        float4 fl = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (tl < p.count) {
-            sl = pl.perm ? (long long)pl.perm[tl] : tl;
-            hl = pl.hosts[sl];
-            fl = pl.fr[sl];
-        }
-        const int nj = p.count - t0 < 32 ? (int)(p.count - t0) : 32;
-        // 1. plan
-        unsigned myc = 0;
-        for (int j = 0; j < nj; ++j) {
-            const long long s = __shfl_sync(kFull, sl, j);
-            const unsigned long long hp = __shfl_sync(kFull, hl, j);
-            float4 f4;
-            f4.x = __shfl_sync(kFull, fl.x, j);
-            f4.y = __shfl_sync(kFull, fl.y, j);
-            f4.z = __shfl_sync(kFull, fl.z, j);
-            f4.w = 0.f;
-            if (hp != kNoHost) {
-                const unsigned c = plan_particle<R, true, SC>(P, S, p, t0 + j, s, hp, f4, (unsigned)pl.cap, ncand, cand,
-                                                              sub, csq, fc2, stc, blist, pl.counts, pl.slots, st);
-                if (lane == j) myc = c;
-            } else if (lane == 0) {
-                pl.counts[t0 + j] = 0;
-            }
-        }
-        __syncwarp();
-        // 2. gather, lane per particle
-        if (tl < p.count) {
-            if (P.Slog >= 0)
-                gather_fb_particle<true, false>(P, S, u, p, pl, G, st, wtab, tl);
-            else
-                gather_fb_particle<false, false>(P, S, u, p, pl, G, st, wtab, tl);
-            rows[lane] = G[FB_VX * gs + sl];
-            rows[32 + lane] = G[FB_VY * gs + sl];
-            rows[64 + lane] = G[FB_VZ * gs + sl];
-            rows[96 + lane] = G[FB_Q * gs + sl];
-            rows[128 + lane] = G[FB_E * gs + sl];
-            rows[160 + lane] = G[FB_PV * gs + sl];
-        }
-        __syncwarp();
-        // 3. deposit, 8 particles at a time
-        for (int jb = 0; jb < nj; jb += kPartsPerWarp) {
-            const int src = jb + (lane & (kPartsPerWarp - 1));
-            const unsigned cj = __shfl_sync(kFull, myc, src);
-            const long long sj = __shfl_sync(kFull, sl, src);
-            const bool mine = lane < kPartsPerWarp && jb + lane < nj;
-            unsigned incl = mine ? cj : 0;
-#pragma unroll
-            for (int d = 1; d < kPartsPerWarp; d <<= 1) {
-                const unsigned v = __shfl_up_sync(kFull, incl, d);
-                if (lane >= d) incl += v;
-            }
-            const unsigned total = __shfl_sync(kFull, incl, kPartsPerWarp - 1);
-            if (mine) sidt[lane] = sj;
-            __syncwarp();
-            // centre offsets (c + 1/2) - x and their squares of the 8 particles
-            for (int i = lane; i < TAB; i += 32) {
-                const int j = i / (3 * W), r = i - j * (3 * W), a = r / W, o = r - a * W;
-                if (jb + j < nj) {
-                    const long long sjj = sidt[j];
-                    const unsigned long long hp = pl.hosts[sjj];
-                    if (hp != kNoHost) {
-                        int hx, hy, hz;
-                        unpack_host(hp, hx, hy, hz);
-                        const int h = a == 0 ? hx : (a == 1 ? hy : hz);
-                        const double xa = a == 0 ? p.x[sjj] : (a == 1 ? p.y[sjj] : p.z[sjj]);
-                        const double d = ((double)(h + o - R) + 0.5) - xa;
-                        dt[i] = d;
-                        qt[i] = d * d;
-                    }
-                }
-            }
-            __syncwarp();
-            for (unsigned g0 = 0; g0 < total; g0 += 32) {
-                const unsigned g = g0 + lane;
-                // particle j of this pair: the first whose inclusive prefix exceeds g
-                int j = 0;
-                unsigned before = 0;
-#pragma unroll
-                for (int k = 0; k < kPartsPerWarp - 1; ++k) {
-                    const unsigned ik = __shfl_sync(kFull, incl, k);
-                    if (g >= ik) {
-                        j = k + 1;
-                        before = ik;
-                    }
-                }
-                if (g < total) {
-                    const long long s = sidt[j];
-                    const unsigned long long slot = (unsigned long long)(t0 + jb + j) * pl.cap + (g - before);
-                    const PairCell cell = unpack_pair(slot_load<false>(pl.slots + slot), P.R);
-                    int hx, hy, hz;
-                    unpack_host(pl.hosts[s], hx, hy, hz);
-                    const int ix = j * 3 * W + (cell.i - hx + R), iy = j * 3 * W + W + (cell.j - hy + R),
-                              iz = j * 3 * W + 2 * W + (cell.k - hz + R);
-                    const double dd = (qt[ix] + qt[iy]) + qt[iz];
-                    double U[NF], dU[NF];
-                    load_cell(u, S, S.at(owner(cell.i, S.n0), owner(cell.j, S.n1), owner(cell.k, S.n2)), U);
-                    const int jj = jb + j;
-                    const double vc[3] = {rows[jj], rows[32 + jj], rows[64 + jj]};
-                    feedback_delta(wtab[cell.cnt], U, rows[96 + jj], rows[128 + jj], rows[160 + jj], vc, dt[ix],
-                                   dt[iy], dt[iz], dd, dU);
-                    const long long bc = B.at(cell.i, cell.j, cell.k);
-#pragma unroll
-                    for (int f = 0; f < NF; ++f) atomicAdd(b + (long long)f * B.fs + bc, dU[f]);
-                }
-            }
-            __syncwarp();
-        }
-    }
-}
-
 // Particle-mesh gather (MASS kind): V_K = V sum omega over the plan's cells in
 // kernel order, then (m, p, e) / V_K.
 __global__ void __launch_bounds__(128) k_gather_mass(KParams P, Box S, Parts p, PlanPtrs pl, double *__restrict__ G,
@@ -741,7 +564,7 @@ __global__ void __launch_bounds__(128) k_gather_mass(KParams P, Box S, Parts p, 
     bool ok = isfinite(VK) && VK > 0.0;
 #pragma unroll
     for (int f = 0; f < NF; ++f) {
-        const double q = u[f] / VK;
+        const double q = exact::div_rn(u[f], VK);
         G[(MS_Q + f) * gs + s] = q;
         ok = ok && isfinite(q);
     }
@@ -1007,7 +830,10 @@ __device__ __forceinline__ void fb_pair_delta_d(const double *__restrict__ u, co
 // place offs[t] + q at svals[offs[t] + q] (the sort's keys and values)
 // instead of adding into the buffer.
 template <int R, bool FB>
-__global__ void __launch_bounds__(256) k_deposit_atomic(KParams P, Box S, const double *__restrict__ u, Box B,
+#ifndef PMP_DEPOSIT_MINB
+#define PMP_DEPOSIT_MINB 1
+#endif
+__global__ void __launch_bounds__(256, PMP_DEPOSIT_MINB) k_deposit_atomic(KParams P, Box S, const double *__restrict__ u, Box B,
                                                         double *__restrict__ b, Parts p,
                                                         const double *__restrict__ G, PlanPtrs pl,
                                                         double *__restrict__ E, double *__restrict__ scr,
@@ -1172,6 +998,7 @@ __global__ void __launch_bounds__(256) k_deposit_atomic(KParams P, Box S, const 
 
 
 constexpr unsigned kLongRun = 32;  // runs longer than this get a warp
+constexpr int kSegChunk = 4;       // pairs whose loads a run's thread issues together
 
 // One thread per run of equal keys (a buffer cell) of at most kLongRun pairs:
 // the run's pairs, which the stable sort kept in particle-index order, are
@@ -1197,10 +1024,27 @@ __global__ void __launch_bounds__(128) k_segment_runs(Box B, double *__restrict_
         double acc[NF];
 #pragma unroll
         for (int f = 0; f < NF; ++f) acc[f] = b[(long long)f * B.fs + key];
-        for (unsigned j = 0; j < len; ++j) {
-            const double *v = pv + (unsigned long long)vals[o + j] * NF;
+        // kSegChunk pairs' indices, then all their values, are loaded before
+        // they are added (in run order): the loads of a chunk are in flight
+        // together
+        for (unsigned j0 = 0; j0 < len; j0 += kSegChunk) {
+            unsigned idx[kSegChunk];
 #pragma unroll
-            for (int f = 0; f < NF; ++f) acc[f] = acc[f] + __ldg(v + f);
+            for (int k = 0; k < kSegChunk; ++k) idx[k] = j0 + k < len ? __ldg(vals + o + j0 + k) : 0u;
+            double v[kSegChunk][NF];
+#pragma unroll
+            for (int k = 0; k < kSegChunk; ++k) {
+                const double *pk = pv + (unsigned long long)idx[k] * NF;
+#pragma unroll
+                for (int f = 0; f < NF; ++f) v[k][f] = j0 + k < len ? __ldg(pk + f) : 0.0;
+            }
+#pragma unroll
+            for (int k = 0; k < kSegChunk; ++k) {
+                if (j0 + k < len) {
+#pragma unroll
+                    for (int f = 0; f < NF; ++f) acc[f] = acc[f] + v[k][f];
+                }
+            }
         }
 #pragma unroll
         for (int f = 0; f < NF; ++f) b[(long long)f * B.fs + key] = acc[f];
@@ -1362,18 +1206,21 @@ __global__ void __launch_bounds__(256) k_return_sinks_stored(KParams P, Box S, P
             a2 = fma(-b, d1.x, a2);
             a3 = fma(-b, d1.y, a3);
         }
+        // The warp's 32 partial sums of the four fields, reduced with the
+        // fields spread over the lanes: after the first exchange each half
+        // warp keeps two fields, after the second each quarter one, so a
+        // lane makes 6 additions instead of 20 (each FP64 instruction costs
+        // the pipe the same whatever the lanes hold).
+        const bool hi16 = (lane & 16) != 0, hi8 = (lane & 8) != 0;
+        const double x = (hi16 ? a2 : a0) + __shfl_xor_sync(kFull, hi16 ? a0 : a2, 16);
+        const double y = (hi16 ? a3 : a1) + __shfl_xor_sync(kFull, hi16 ? a1 : a3, 16);
+        double z = (hi8 ? y : x) + __shfl_xor_sync(kFull, hi8 ? x : y, 8);
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            a0 = a0 + __shfl_xor_sync(kFull, a0, o);
-            a1 = a1 + __shfl_xor_sync(kFull, a1, o);
-            a2 = a2 + __shfl_xor_sync(kFull, a2, o);
-            a3 = a3 + __shfl_xor_sync(kFull, a3, o);
-        }
-        if (lane == 0) {
-            p.m[s] = p.m[s] - a0 * P.V;
-            p.px[s] = p.px[s] - a1 * P.V;
-            p.py[s] = p.py[s] - a2 * P.V;
-            p.pz[s] = p.pz[s] - a3 * P.V;
+        for (int o = 4; o > 0; o >>= 1) z = z + __shfl_xor_sync(kFull, z, o);
+        // lane 8f holds field f: m, p_x, p_y, p_z
+        if ((lane & 7) == 0) {
+            double *dst = lane == 0 ? p.m : (lane == 8 ? p.px : (lane == 16 ? p.py : p.pz));
+            dst[s] = dst[s] - z * P.V;
         }
     }
 }
@@ -1464,39 +1311,6 @@ void launch_plan_gather_fb(const KParams &P, const Box &S, const double *u, cons
         PMP_DISPATCH_R(P.R, (plan_gather_one<RR, 4>(P, S, u, p, pl, G, st, stream)));
     } else {
         PMP_DISPATCH_R(P.R, (plan_gather_one<RR, 0>(P, S, u, p, pl, G, st, stream)));
-    }
-}
-
-template <int R, int SC>
-static void pass1_one(const KParams &P, const Box &S, const double *u, const Box &B, double *b, const Parts &p,
-                      const PlanPtrs &pl, double *G, DevStatus *st, cudaStream_t stream)
-{
-    constexpr int W = 2 * R + 1;
-    const int Sn = SC ? SC : P.S;
-    const size_t head = (size_t)(W * W * W * 4 + 15) / 16 * 16;
-    const size_t wb = (size_t)plan_warp_bytes(W, Sn) + (size_t)pass1_warp_bytes(W);
-    int warps = 8;
-    while (warps > 1 && head + warps * wb > 40 * 1024) --warps;
-    const size_t sm = head + warps * wb;
-    int dev = 0, nsm = 152, per_sm = 1;
-    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pass1_fb<R, SC>, warps * 32, sm) != cudaSuccess ||
-        per_sm < 1)
-        per_sm = 1;
-    const long long per_block = 32LL * warps;
-    const long long need = (p.count + per_block - 1) / per_block;
-    const long long grid = need < (long long)nsm * per_sm ? need : (long long)nsm * per_sm;
-    k_pass1_fb<R, SC><<<(unsigned)grid, warps * 32, sm, stream>>>(P, S, u, B, b, p, pl, G, st);
-}
-
-void launch_pass1_fb(const KParams &P, const Box &S, const double *u, const Box &B, double *b, const Parts &p,
-                     const PlanPtrs &pl, double *G, DevStatus *st, cudaStream_t stream)
-{
-    if (p.count == 0) return;
-    if (P.S == 4) {
-        PMP_DISPATCH_R(P.R, (pass1_one<RR, 4>(P, S, u, B, b, p, pl, G, st, stream)));
-    } else {
-        PMP_DISPATCH_R(P.R, (pass1_one<RR, 0>(P, S, u, B, b, p, pl, G, st, stream)));
     }
 }
 
@@ -1740,15 +1554,15 @@ __global__ void __launch_bounds__(128) k_backward_fb(KParams P, Box S, const dou
         const double d0 = ((double)c.i + 0.5) - x, d1 = ((double)c.j + 0.5) - y, d2 = ((double)c.k + 0.5) - z;
         const double dd = d0 * d0 + d1 * d1 + d2 * d2;
         if (dd > 0.0) {
-            const double dist = sqrt(dd);
-            const double h0 = d0 / dist, h1 = d1 / dist, h2 = d2 / dist;
+            const double dist = exact::sqrt_rn(dd);
+            const double h0 = exact::div_rn(d0, dist), h1 = exact::div_rn(d1, dist), h2 = exact::div_rn(d2, dist);
             Sgpd += w * (ap0 * h0 + ap1 * h1 + ap2 * h2);
             SgEd0 += w * aE * h0;
             SgEd1 += w * aE * h1;
             SgEd2 += w * aE * h2;
             const double t0 = ap0 + aE * vc0, t1 = ap1 + aE * vc1, t2 = ap2 + aE * vc2;
             const double th = t0 * h0 + t1 * h1 + t2 * h2;
-            const double f = w / dist;
+            const double f = exact::div_rn(w, dist);
             X0 += f * (t0 - h0 * th);
             X1 += f * (t1 - h1 * th);
             X2 += f * (t2 - h2 * th);

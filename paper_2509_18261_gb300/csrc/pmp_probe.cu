@@ -5,6 +5,7 @@
 #include <cstdint>
 
 #include "pmp.h"
+#include "pmp_exact.cuh"
 
 namespace {
 
@@ -42,6 +43,20 @@ __global__ void __launch_bounds__(kProbeThreads) k_probe_atomic(double *__restri
     }
 }
 
+// Element-wise quotient and square root by the library's integer / FP32
+// forms (pmp_exact.cuh), the ones the particle and cell kernels use.
+__global__ void __launch_bounds__(kProbeThreads) k_exact_math(const double *__restrict__ a,
+                                                             const double *__restrict__ b, long long n,
+                                                             double *__restrict__ quot, double *__restrict__ root)
+{
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const double x = a[i];
+        quot[i] = pmp::exact::div_rn(x, b[i]);
+        root[i] = pmp::exact::sqrt_rn(x);
+    }
+}
+
 }  // namespace
 
 extern "C" {
@@ -63,6 +78,17 @@ pmp_status pmp_probe_atomic(double *target, int64_t n_targets, int64_t n_adds, i
     if (!target || n_targets < 1 || n_adds < 0 || blocks < 1) return PMP_ERR_ARG;
     k_probe_atomic<<<blocks, kProbeThreads, 0, reinterpret_cast<cudaStream_t>(stream)>>>(target, n_targets,
                                                                                        n_adds);
+    return cudaGetLastError() == cudaSuccess ? PMP_OK : PMP_ERR_CUDA;
+}
+
+pmp_status pmp_exact_math(const double *a, const double *b, int64_t n, double *quot, double *root,
+                          pmp_stream stream)
+{
+    if (n < 0 || (n > 0 && (!a || !b || !quot || !root))) return PMP_ERR_ARG;
+    if (n == 0) return PMP_OK;
+    const long long blocks = (n + kProbeThreads - 1) / kProbeThreads;
+    k_exact_math<<<(unsigned)(blocks < 152LL * 16 ? blocks : 152LL * 16), kProbeThreads, 0,
+                   reinterpret_cast<cudaStream_t>(stream)>>>(a, b, n, quot, root);
     return cudaGetLastError() == cudaSuccess ? PMP_OK : PMP_ERR_CUDA;
 }
 

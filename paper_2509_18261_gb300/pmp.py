@@ -33,7 +33,7 @@ EXPORTS = [
     "pmp_create_sinks_workspace_size", "pmp_create_sinks", "pmp_apply_extra",
     "pmp_batch_create", "pmp_batch_set_particles", "pmp_batch_set_strategy", "pmp_batch_strategies",
     "pmp_batch_autotune", "pmp_cycle_batched", "pmp_batch_info", "pmp_batch_hold_barriers", "pmp_batch_destroy",
-    "pmp_probe_threads", "pmp_probe_chains", "pmp_probe_fp64", "pmp_probe_atomic",
+    "pmp_probe_threads", "pmp_probe_chains", "pmp_probe_fp64", "pmp_probe_atomic", "pmp_exact_math",
     "pmp_partition_sfc", "pmp_plan_create", "pmp_plan_local", "pmp_plan_regions", "pmp_plan_destroy",
     "pmp_batch_create_partial", "pmp_cycle_batched_part", "pmp_batch_set_regions", "pmp_batch_pack",
     "pmp_batch_unpack",
@@ -142,6 +142,7 @@ def load():
         "pmp_probe_chains": ([], i32),
         "pmp_probe_fp64": ([vp, i32, i32, vp], i32),
         "pmp_probe_atomic": ([vp, i64, i64, i32, vp], i32),
+        "pmp_exact_math": ([vp, vp, i64, vp, vp, vp], i32),
         "pmp_partition_sfc": ([i32, ctypes.POINTER(i32), ctypes.POINTER(i64), i32, ctypes.POINTER(i32)], i32),
         "pmp_plan_create": ([ctypes.POINTER(_Patch), i32, i32, ctypes.POINTER(i32), i32, i32, ctypes.POINTER(vp)],
                             i32),
@@ -396,6 +397,15 @@ def pmp_probe_fp64(out, blocks, iters):
 def pmp_probe_atomic(target, n_adds, blocks):
     """Enqueues n_adds FP64 atomicAdd over the doubles of `target`."""
     _check("pmp_probe_atomic", load().pmp_probe_atomic(_ptr(target), target.numel(), n_adds, blocks, _stream()))
+
+
+def pmp_exact_math(a, b, quot, root):
+    """quot = a / b and root = sqrt(a), element-wise, by the library's integer
+    forms (device tensors of float64, same length)."""
+    n = a.numel()
+    if not (b.numel() == quot.numel() == root.numel() == n):
+        raise ValueError("pmp_exact_math: arrays of different lengths")
+    _check("pmp_exact_math", load().pmp_exact_math(_ptr(a), _ptr(b), n, _ptr(quot), _ptr(root), _stream()))
 
 
 def pmp_timing_enable(ctx, on=True):

@@ -15,15 +15,22 @@ def _box():
     return syn.Box((512, 512, 512), 4)
 
 
-def test_alu_roofline_of_the_fused_supernova_kernel():
+def test_alu_roofline_of_the_supernova_kernels():
     box = _box()
     pairs = {"fb": 491_934_207, "sink": 562_210_341}
-    r = bench.roofline("fb_gather_deposit", 52.8, pairs, box, 14_680_064, 2_097_152, 6793.4, "measured")
-    flops = 38 * pairs["fb"]  # 9 (gather) + 29 (Eq. du) canonical FP64 operations per pair
-    assert r["bound"] == "alu" and r["unit"] == "TFLOP/s" and r["peak"] == bench.FP64_PEAK_TFLOPS
-    assert r["achieved"] == pytest.approx(flops / 52.8e-3 / 1e12, rel=1e-12)
-    assert r["frac"] == pytest.approx(r["achieved"] / r["peak"], rel=1e-12)
-    assert r["kernel"] == "fb_gather_deposit" and r["ms_per_launch"] == 52.8
+    for kernel, per_pair in (("fb_deposit", 29), ("fb_plan_gather", 9)):  # Eq. du; the gather sums
+        r = bench.roofline(kernel, 24.2, pairs, box, 14_680_064, 2_097_152, 6793.4, "measured")
+        flops = per_pair * pairs["fb"]  # canonical FP64 operations per pair
+        assert r["bound"] == "alu" and r["unit"] == "TFLOP/s" and r["peak"] == bench.FP64_PEAK_TFLOPS
+        assert r["achieved"] == pytest.approx(flops / 24.2e-3 / 1e12, rel=1e-12)
+        assert r["frac"] == pytest.approx(r["achieved"] / r["peak"], rel=1e-12)
+        assert r["kernel"] == kernel and r["ms_per_launch"] == 24.2
+
+
+def test_algorithmic_bytes_of_the_supernova_kernels():
+    n, pairs, ts, tb = 1000, 33_000, 20_000, 21_000
+    assert bench.alg_bytes_fb("plan_gather", n, pairs, ts, tb) == 160 * n + 8 * pairs + 40 * ts
+    assert bench.alg_bytes_fb("deposit", n, pairs, ts, tb) == 72 * n + 8 * pairs + 40 * ts + 80 * tb
 
 
 def test_hbm_roofline_of_the_sink_apply():
@@ -36,17 +43,19 @@ def test_hbm_roofline_of_the_sink_apply():
 
 def test_traffic_is_reported_only_for_the_profiled_sources(monkeypatch):
     # the committed summary names the digest of the sources it was taken on
-    t = bench.profiled_traffic("fb_gather_deposit", 491934207)
-    assert t is None or t > 1e10
-    assert bench.profiled_traffic("no_such_kernel", 1000) is None
-    # with the digest of the capture, the per-pair bytes scale with the pairs
     import re
 
     txt = open(bench.os.path.join(bench.ROOT, "profiles", "counters_c5_192.md")).read()
+    rows = [[c.strip() for c in line.strip().strip("|").split("|")] for line in txt.splitlines()]
+    kernel = next(r[1] for r in rows if len(r) == 13 and r[1].startswith("fb_"))
+    t = bench.profiled_traffic(kernel, 491934207)
+    assert t is None or t > 1e10
+    assert bench.profiled_traffic("no_such_kernel", 1000) is None
+    # with the digest of the capture, the per-pair bytes scale with the pairs
     monkeypatch.setattr(bench, "src_digest", lambda: re.search(r"csrc_sha:\s*([0-9a-f]+)", txt).group(1))
-    a = bench.profiled_traffic("fb_gather_deposit", 1000)
-    assert a is not None and bench.profiled_traffic("fb_gather_deposit", 2000) == pytest.approx(2 * a)
-    assert 100.0 < a / 1000 < 400.0  # bytes per pair of the 192^3 capture
+    a = bench.profiled_traffic(kernel, 1000)
+    assert a is not None and bench.profiled_traffic(kernel, 2000) == pytest.approx(2 * a)
+    assert 20.0 < a / 1000 < 400.0  # bytes per pair of the 192^3 capture
 
 
 def test_cell_pass_hbm_sums_the_two_supernova_apply_kernels():
