@@ -253,9 +253,10 @@ pmp_status pmp_fold_ghosts(pmp_ctx *ctx, pmp_mesh *buffer);
  * eta_out: optional device array, one FP64 per valid cell (x fastest): the
  *   momentum eta (feedback) or the common eta (sink).
  * workspace: sinks need the one pmp_gather filled for this pass (its plan and
- *   per-cell quantities).  Feedback may pass NULL; with the workspace of this
- *   pass's pmp_gather it queues the cells whose constraint an FP32 pre-test
- *   cannot settle for the FP64 limiter (same results, fewer FP64 operations).
+ *   per-cell quantities).  Feedback does not read it (NULL is accepted): one
+ *   pass over the cells settles most of them with an FP32 pre-test of the
+ *   constraint and runs the FP64 limiter on the rest, with the same results
+ *   as the FP64 limiter on every cell.
  * Order of work (sinks): eta is computed and the state updated in one pass
  *   over the cells, then Step 4 runs; Step 4 reads eta and the pre-update
  *   per-cell quantities kept in the workspace, so the result is that of the

@@ -72,7 +72,8 @@ def build(force=False, verbose=False):
         with concurrent.futures.ThreadPoolExecutor(max_workers=min(8, len(jobs))) as ex:
             logs = list(ex.map(run, jobs))
     if force or jobs or _stale(LIB, objs):
-        run([nvcc()] + ARCH + ["-shared", "-o", LIB] + objs)
+        # every symbol resolved at link time: a missing definition fails the build, not the first load
+        run([nvcc()] + ARCH + ["-shared", "-Xlinker", "--no-undefined", "-o", LIB] + objs)
     if verbose:
         for line in logs:
             print(line)

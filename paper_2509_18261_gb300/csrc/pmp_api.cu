@@ -13,6 +13,11 @@
 #include "pmp_launch.h"
 #include "pmp_ctx.h"
 
+// The supernova plan and gather as one kernel (1) or as two (0).
+#ifndef PMP_FB_PLAN_GATHER_FUSED
+#define PMP_FB_PLAN_GATHER_FUSED 1
+#endif
+
 namespace {
 
 using pmp::Box;
@@ -89,7 +94,7 @@ long long max_pairs_per_particle(double rK)
 }
 
 struct Layout {
-    size_t keys, ids, keys2, ids2, counts, slots, hosts, fr, wts, aux, pa, queue, qcount, offsets, skeys, skeys2,
+    size_t keys, ids, keys2, ids2, counts, slots, hosts, fr, wts, aux, pa, mask, offsets, koffsets, kcounts, skeys, skeys2,
         svals, svals2, soffs, slong, scnt, spv;
     size_t temp, temp_bytes, total;
     long long cap, aux_stride;
@@ -113,12 +118,10 @@ Layout layout(const pmp_params &p, long long n, long long nvalid, int mode)
     };
     const size_t n1 = (size_t)(n > 0 ? n : 1);
     const size_t pairs = n1 * (size_t)L.cap;
-    if (!sorted) {
-        L.keys = take(4 * n1);
-        L.ids = take(4 * n1);
-        L.keys2 = take(4 * n1);
-        L.ids2 = take(4 * n1);
-    }
+    L.keys = take(4 * n1);
+    L.ids = take(4 * n1);
+    L.keys2 = take(4 * n1);
+    L.ids2 = take(4 * n1);
     L.counts = take(4 * (n1 + 1));
     L.slots = take(8 * pairs);
     L.hosts = take(8 * n1);
@@ -129,11 +132,12 @@ Layout layout(const pmp_params &p, long long n, long long nvalid, int mode)
         // ATOMIC: each pair's removal a, stored by the fused deposit for Step 4
         if (mode == PMP_MODE_ATOMIC) L.pa = take(8 * pairs);
     } else {
-        L.queue = take(4 * (size_t)(nvalid > 0 ? nvalid : 1));
-        L.qcount = take(8);
+        L.mask = take((size_t)(nvalid > 0 ? nvalid : 1));  // the adjoint's per-cell pass mask
     }
     if (sorted) {
         L.offsets = take(8 * (n1 + 1));
+        L.koffsets = take(8 * (n1 + 1));
+        L.kcounts = take(4 * (n1 + 1));
         L.skeys = take(4 * pairs);
         L.skeys2 = take(4 * pairs);
         L.svals = take(4 * pairs);
@@ -171,7 +175,8 @@ pmp::PlanPtrs plan_ptrs(const Layout &L, void *ws, const pmp_params &p, int mode
     char *w = static_cast<char *>(ws);
     pmp::PlanPtrs pl;
     std::memset(&pl, 0, sizeof(pl));
-    pl.perm = mode == PMP_MODE_SORTED ? nullptr : reinterpret_cast<const unsigned *>(w + L.ids2);
+    (void)mode;
+    pl.perm = reinterpret_cast<const unsigned *>(w + L.ids2);
     pl.counts = reinterpret_cast<unsigned *>(w + L.counts);
     pl.slots = reinterpret_cast<unsigned long long *>(w + L.slots);
     pl.hosts = reinterpret_cast<unsigned long long *>(w + L.hosts);
@@ -558,26 +563,22 @@ static pmp_status gather_impl(pmp_ctx *ctx, const pmp_mesh *state, const pmp_par
     void *temp = w + L.temp;
     cudaStream_t st = ctx->stream;
     if (q.count > 0) {
-        if (mode != PMP_MODE_SORTED) {
-            unsigned *keys = reinterpret_cast<unsigned *>(w + L.keys), *ids = reinterpret_cast<unsigned *>(w + L.ids);
-            unsigned *keys2 = reinterpret_cast<unsigned *>(w + L.keys2),
-                     *ids2 = reinterpret_cast<unsigned *>(w + L.ids2);
-            {
-                Timed tm(ctx, "prologue");
-                pmp::launch_prologue(S, q, keys, ids, pl, ctx->st, st);
-            }
-            Timed tm(ctx, "order_sort");
-            int nmax = state->n[0] > state->n[1] ? state->n[0] : state->n[1];
-            nmax = nmax > state->n[2] ? nmax : state->n[2];
-            int bits = 0;
-            while ((1 << bits) < nmax) ++bits;
-            const int end_bit = 3 * (bits < 10 ? (bits > 0 ? bits : 1) : 10);
-            if (pmp::sort_host_keys(temp, L.temp_bytes, keys, keys2, ids, ids2, q.count, end_bit, st) != cudaSuccess)
-                return PMP_ERR_CUDA;
-        } else {
+        // processing order: particles sorted by the Morton code of their host
+        // cell (every mode; results do not depend on it)
+        unsigned *keys = reinterpret_cast<unsigned *>(w + L.keys), *ids = reinterpret_cast<unsigned *>(w + L.ids);
+        unsigned *keys2 = reinterpret_cast<unsigned *>(w + L.keys2), *ids2 = reinterpret_cast<unsigned *>(w + L.ids2);
+        {
             Timed tm(ctx, "prologue");
-            pmp::launch_prologue(S, q, nullptr, nullptr, pl, ctx->st, st);
+            pmp::launch_prologue(S, q, keys, ids, pl, ctx->st, st);
         }
+        Timed tm(ctx, "order_sort");
+        int nmax = state->n[0] > state->n[1] ? state->n[0] : state->n[1];
+        nmax = nmax > state->n[2] ? nmax : state->n[2];
+        int bits = 0;
+        while ((1 << bits) < nmax) ++bits;
+        const int end_bit = 3 * (bits < 10 ? (bits > 0 ? bits : 1) : 10);
+        if (pmp::sort_host_keys(temp, L.temp_bytes, keys, keys2, ids, ids2, q.count, end_bit, st) != cudaSuccess)
+            return PMP_ERR_CUDA;
     }
     if (ctx->p.kind == PMP_KIND_SINK) {
         Timed tm(ctx, "cell_records");
@@ -597,7 +598,7 @@ static pmp_status gather_impl(pmp_ctx *ctx, const pmp_mesh *state, const pmp_par
             }
             Timed tm(ctx, "spread");
             pmp::launch_sink_spread(S, B, fused->data, scr, pl.drec, st);
-        } else if (ctx->p.kind == PMP_KIND_FEEDBACK) {
+        } else if (ctx->p.kind == PMP_KIND_FEEDBACK && PMP_FB_PLAN_GATHER_FUSED) {
             Timed tm(ctx, "plan_gather");
             pmp::launch_plan_gather_fb(P, S, state->data, q, pl, gathered, ctx->st, st);
         } else {
@@ -721,6 +722,12 @@ pmp_status pmp_deposit(pmp_ctx *ctx, const pmp_mesh *state, const pmp_particles 
     if (cudaMemsetAsync(pl.counts + q.count, 0, sizeof(unsigned), st) != cudaSuccess) return PMP_ERR_CUDA;
     if (pmp::scan_counts(w + L.temp, L.temp_bytes, pl.counts, offsets, q.count + 1, st) != cudaSuccess)
         return PMP_ERR_CUDA;
+    // the same counts in particle-index order, for the pair sort's input lists
+    unsigned *kcounts = reinterpret_cast<unsigned *>(w + L.kcounts);
+    unsigned long long *koffsets = reinterpret_cast<unsigned long long *>(w + L.koffsets);
+    pmp::launch_counts_by_index(pl, q.count, kcounts, st);
+    if (pmp::scan_counts(w + L.temp, L.temp_bytes, kcounts, koffsets, q.count + 1, st) != cudaSuccess)
+        return PMP_ERR_CUDA;
     unsigned long long total = 0;
     if (cudaMemcpyAsync(&total, offsets + q.count, sizeof(total), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
         cudaStreamSynchronize(st) != cudaSuccess)
@@ -732,7 +739,7 @@ pmp_status pmp_deposit(pmp_ctx *ctx, const pmp_mesh *state, const pmp_particles 
     double *pv = reinterpret_cast<double *>(w + L.spv);
     {
         Timed tm(ctx, "pair_values");
-        pmp::launch_pair_values(P, S, state->data, B, q, gathered, pl, offsets, pv, k1, v1, st);
+        pmp::launch_pair_values(P, S, state->data, B, q, gathered, pl, offsets, koffsets, pv, k1, v1, st);
     }
     int end_bit = 1;
     while (end_bit < 32 && (1LL << end_bit) < B.ncells) ++end_bit;
@@ -821,26 +828,6 @@ pmp_status pmp_apply_limited(pmp_ctx *ctx, pmp_mesh *state, const pmp_mesh *buff
     }
     if (cudaMemsetAsync(&ctx->st->n_limited, 0, 2 * sizeof(unsigned long long), st) != cudaSuccess)
         return PMP_ERR_CUDA;
-    const long long nv = nvalid_of(state);
-    if (ctx->p.kind == PMP_KIND_FEEDBACK && workspace && ctx->plan_ws == workspace && ctx->plan_nvalid == nv) {
-        // scratch for the queue of cells that need the FP64 limiter
-        const Layout L = layout(ctx->p, ctx->plan_n, nv, ctx->plan_mode);
-        s = check_workspace(L, workspace, workspace_bytes);
-        if (s) return s;
-        char *w = static_cast<char *>(workspace);
-        unsigned *queue = reinterpret_cast<unsigned *>(w + L.queue);
-        unsigned long long *qc = reinterpret_cast<unsigned long long *>(w + L.qcount);
-        if (cudaMemsetAsync(qc, 0, sizeof(unsigned long long), st) != cudaSuccess) return PMP_ERR_CUDA;
-        {
-            Timed tm(ctx, "apply");
-            pmp::launch_apply_fb_fast(S, state->data, B, buffer->data, eta_out, queue, qc, st);
-        }
-        {
-            Timed tm(ctx, "apply_fp64");
-            pmp::launch_apply_fb_slow(S, state->data, B, buffer->data, eta_out, queue, qc, ctx->st, st);
-        }
-        return last_launch();
-    }
     {
         Timed tm(ctx, "apply");
         pmp::launch_apply(P, S, state->data, B, buffer->data, eta_out, ctx->st, st);
@@ -873,7 +860,7 @@ pmp_status pmp_backward(pmp_ctx *ctx, const pmp_mesh *state_in, const pmp_mesh *
     if (q.count == 0) return PMP_OK;
     const KParams P = make_kparams(ctx->p, state_in->dx);
     const pmp::PlanPtrs pl = plan_ptrs(L, workspace, ctx->p, ctx->plan_mode);
-    unsigned char *pass = reinterpret_cast<unsigned char *>(static_cast<char *>(workspace) + L.queue);
+    unsigned char *pass = reinterpret_cast<unsigned char *>(static_cast<char *>(workspace) + L.mask);
     {
         Timed tm(ctx, "backward_mask");
         pmp::launch_pass_mask(S, state_in->data, B, buffer->data, pass, ctx->stream);

@@ -55,13 +55,20 @@ void launch_pass1_sink(const KParams &P, const Box &S, const double *u, const Bo
 void launch_deposit_atomic(const KParams &P, const Box &S, const double *u, const Box &B, double *b, const Parts &p,
                            const double *G, const PlanPtrs &pl, double *E, double *scr, cudaStream_t stream);
 // Sorted deposit, first part: every pair's deposition value (the same
-// function and operations as the atomic deposit) stored at
-// pv[(offsets[s] + q) * 5 + f] for pair q of particle s (index order), with
-// its buffer cell in keys[offsets[s] + q] and offsets[s] + q in vals (the
-// pair sort's input).
+// function and operations as the atomic deposit).  Pair q of the particle at
+// processing position t (particle s = perm[t]) is stored at
+// pv[(offsets[t] + q) * 5 + f], so that the values of nearby particles lie
+// together; the pair sort's input lists are in particle-index order: its
+// buffer cell at keys[koffsets[s] + q] and offsets[t] + q at vals[koffsets[s]
+// + q].  offsets / koffsets: exclusive prefix sums of the pair counts in
+// processing / index order.
 void launch_pair_values(const KParams &P, const Box &S, const double *u, const Box &B, const Parts &p,
-                        const double *G, const PlanPtrs &pl, const unsigned long long *offsets, double *pv,
-                        unsigned *keys, unsigned *vals, cudaStream_t stream);
+                        const double *G, const PlanPtrs &pl, const unsigned long long *offsets,
+                        const unsigned long long *koffsets, double *pv, unsigned *keys, unsigned *vals,
+                        cudaStream_t stream);
+// counts_idx[perm[t]] = counts[t] for t < n, counts_idx[n] = 0 (the pair
+// counts in particle-index order).
+void launch_counts_by_index(const PlanPtrs &pl, long long n, unsigned *counts_idx, cudaStream_t stream);
 // Sorted deposit, second part, per run of equal buffer cells (uniq/lens/offs
 // from encode_runs and scan_lengths; nruns on the device): the run's stored
 // pair values added in list order on top of the buffer value; short runs one
@@ -107,10 +114,8 @@ void launch_sink_aux(const KParams &P, const Box &S, const double *u, double *gr
 // and U += eta Delta U^sum, in one pass.
 void launch_sink_eta_apply(const KParams &P, const Box &S, double *u, const Box &B, const double *b, double *drec,
                            double *eta_out, DevStatus *st, cudaStream_t stream);
-void launch_apply_fb_fast(const Box &S, double *u, const Box &B, const double *b, double *eta_out, unsigned *queue,
-                          unsigned long long *qcount, cudaStream_t stream);
-void launch_apply_fb_slow(const Box &S, double *u, const Box &B, const double *b, double *eta_out,
-                          const unsigned *queue, const unsigned long long *qcount, DevStatus *st, cudaStream_t stream);
+void launch_apply_fb_stream(const Box &S, double *u, const Box &B, const double *b, double *eta_out, DevStatus *st,
+                            cudaStream_t stream);
 // Steps 3 + 5 without a plan workspace: feedback (FP64 limiter per cell) or
 // the particle-mesh kind (eta = 1).
 void launch_apply(const KParams &P, const Box &S, double *u, const Box &B, const double *b, double *eta_out,

@@ -147,37 +147,64 @@ __device__ __forceinline__ bool no_dp(const double D[NF])
 }
 
 constexpr int kApplyThreads = 256;
-constexpr int kApplyChunk = 4;  // cells per thread between two queue reservations
+constexpr int kFbPend = 64;  // cells a warp holds back for its FP64 limiter batch
 
-// Steps 3 + 5 for feedback, first pass: cells whose Eq. lambda constraint
-// holds at lambda = 1 by the FP32 pre-check (or that receive no momentum) are
-// updated here; the others are queued for the FP64 limiter.  A block takes
-// chunks of kApplyThreads x kApplyChunk cells (grid-stride) and reserves the
-// queue slots of a chunk's queued cells with one atomic.  The queue's order
-// does not matter: each queued cell is updated on its own.
-__global__ void __launch_bounds__(kApplyThreads, 4) k_apply_fb_fast(Box S, double *__restrict__ u, Box B,
-                                                                 const double *__restrict__ b,
-                                                                 double *__restrict__ eta_out,
-                                                                 unsigned *__restrict__ queue,
-                                                                 unsigned long long *__restrict__ qcount)
+// Steps 3 + 5 for feedback in one streaming pass.  Cells that receive
+// nothing, receive no momentum, or whose Eq. lambda constraint holds at
+// lambda = 1 by the FP32 pre-check are updated at once; a warp keeps the
+// others, with the state and summed change it has just loaded, in a
+// shared-memory list and runs the FP64 limiter on 32 of them whenever that
+// many are pending (a full-warp FP64 branch, overlapped with the other warps'
+// streaming; no cell is read twice).
+#ifndef PMP_FB_APPLY_MINB
+#define PMP_FB_APPLY_MINB 3
+#endif
+__global__ void __launch_bounds__(kApplyThreads, PMP_FB_APPLY_MINB) k_apply_fb_stream(Box S, double *__restrict__ u, Box B,
+                                                                      const double *__restrict__ b,
+                                                                      double *__restrict__ eta_out, DevStatus *st)
 {
-    __shared__ unsigned wofs[kApplyThreads / 32];
-    __shared__ unsigned long long qbase;
+    constexpr int kW = kApplyThreads / 32;
+    __shared__ double pend[kW][kFbPend][2 * NF];
+    __shared__ long long pcell[kW][kFbPend];
+    __shared__ unsigned sh[kW];
     const long long nvalid = (long long)S.n0 * S.n1 * S.n2;
-    constexpr long long per = (long long)kApplyThreads * kApplyChunk;
-    const long long nchunks = (nvalid + per - 1) / per;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    for (long long ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
-        const long long c0 = ch * per + threadIdx.x;
-        unsigned mask = 0;
+    const unsigned lt = (1u << lane) - 1u;
+    unsigned nl = 0, nr = 0;
+    int npend = 0;  // the same in every lane
+    // the limiter on pending entry q (one lane)
+    auto limit = [&](int q) {
+        const long long v = pcell[wid][q];
+        const double *e_ = pend[wid][q];
+        double U[NF], D[NF];
 #pragma unroll
-        for (int c = 0; c < kApplyChunk; ++c) {
-            const long long v = c0 + (long long)c * kApplyThreads;
-            if (v >= nvalid) break;
+        for (int f = 0; f < NF; ++f) {
+            U[f] = e_[f];
+            D[f] = e_[NF + f];
+        }
+        int i, j, k;
+        cell_of(S, v, nvalid, i, j, k);
+        const long long cs = S.at(i, j, k);
+        int noroot;
+        const double l = sn_lambda(U, D, noroot);
+        nl += l < 1.0;
+        nr += noroot;
+        if (eta_out) eta_out[v] = l;
+        u[cs] = U[0] + D[0];
+        u[S.fs + cs] = U[1] + l * D[1];
+        u[2 * S.fs + cs] = U[2] + l * D[2];
+        u[3 * S.fs + cs] = U[3] + l * D[3];
+        u[4 * S.fs + cs] = U[4] + D[4];
+    };
+    const long long step = (long long)gridDim.x * kApplyThreads;
+    for (long long v0 = ((long long)blockIdx.x * kW + wid) * 32; v0 < nvalid; v0 += step) {
+        const long long v = v0 + lane;
+        bool need = false;
+        double U[NF], D[NF];
+        if (v < nvalid) {
             int i, j, k;
             cell_of(S, v, nvalid, i, j, k);
             const long long cs = S.at(i, j, k), cb = B.at(i, j, k);
-            double U[NF], D[NF];
 #pragma unroll
             for (int f = 0; f < NF; ++f) {
                 D[f] = __ldg(b + (long long)f * B.fs + cb);
@@ -190,111 +217,28 @@ __global__ void __launch_bounds__(kApplyThreads, 4) k_apply_fb_fast(Box S, doubl
 #pragma unroll
                 for (int f = 0; f < NF; ++f) u[(long long)f * S.fs + cs] = U[f] + D[f];
             } else {
-                mask |= 1u << c;
+                need = true;
             }
         }
-        // queue slots: warp prefix of the per-thread counts, warp offsets in
-        // shared memory, one atomic for the chunk
-        const unsigned cnt = __popc(mask);
-        unsigned incl = cnt;
+        const unsigned m = __ballot_sync(0xffffffffu, need);
+        if (need) {
+            const int q = npend + __popc(m & lt);
+            pcell[wid][q] = v;
 #pragma unroll
-        for (int d = 1; d < 32; d <<= 1) {
-            const unsigned t = __shfl_up_sync(0xffffffffu, incl, d);
-            if (lane >= d) incl += t;
-        }
-        if (lane == 31) wofs[wid] = incl;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            unsigned tot = 0;
-            for (int q = 0; q < kApplyThreads / 32; ++q) {
-                const unsigned t = wofs[q];
-                wofs[q] = tot;
-                tot += t;
+            for (int f = 0; f < NF; ++f) {
+                pend[wid][q][f] = U[f];
+                pend[wid][q][NF + f] = D[f];
             }
-            qbase = tot ? atomicAdd(qcount, (unsigned long long)tot) : 0ULL;
         }
-        __syncthreads();
-        unsigned long long pos = qbase + wofs[wid] + (incl - cnt);
-#pragma unroll
-        for (int c = 0; c < kApplyChunk; ++c)
-            if ((mask >> c) & 1u) queue[pos++] = (unsigned)(c0 + (long long)c * kApplyThreads);
-        __syncthreads();  // wofs and qbase are rewritten by the next chunk
-    }
-}
-
-// Second pass: the queued cells through the FP64 limiter of Eq. lambda.
-__global__ void __launch_bounds__(kApplyThreads) k_apply_fb_slow(Box S, double *__restrict__ u, Box B,
-                                                                 const double *__restrict__ b,
-                                                                 double *__restrict__ eta_out,
-                                                                 const unsigned *__restrict__ queue,
-                                                                 const unsigned long long *__restrict__ qcount,
-                                                                 DevStatus *st)
-{
-    __shared__ unsigned sh[kApplyThreads / 32];
-    const long long nvalid = (long long)S.n0 * S.n1 * S.n2;
-    const unsigned long long n = *qcount;
-    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
-    unsigned nl = 0, nr = 0;
-    for (unsigned long long q = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += stride) {
-        const long long v = queue[q];
-        int i, j, k;
-        cell_of(S, v, nvalid, i, j, k);
-        const long long cs = S.at(i, j, k), cb = B.at(i, j, k);
-        double U[NF], D[NF];
-#pragma unroll
-        for (int f = 0; f < NF; ++f) {
-            U[f] = u[(long long)f * S.fs + cs];
-            D[f] = __ldg(b + (long long)f * B.fs + cb);
-        }
-        int noroot;
-        const double l = sn_lambda(U, D, noroot);
-        nl += l < 1.0;
-        nr += noroot;
-        if (eta_out) eta_out[v] = l;
-        u[cs] = U[0] + D[0];
-        u[S.fs + cs] = U[1] + l * D[1];
-        u[2 * S.fs + cs] = U[2] + l * D[2];
-        u[3 * S.fs + cs] = U[3] + l * D[3];
-        u[4 * S.fs + cs] = U[4] + D[4];
-    }
-    block_add(&st->n_limited, nl, sh);
-    __syncthreads();
-    block_add(&st->n_noroot, nr, sh);
-}
-
-// Steps 3 + 5 for feedback in one pass (used without a workspace): eta =
-// (1, l, l, l, 1) from Eq. lambda in FP64 for every cell.
-__global__ void __launch_bounds__(kApplyThreads) k_apply_fb(Box S, double *__restrict__ u, Box B,
-                                                            const double *__restrict__ b,
-                                                            double *__restrict__ eta_out, DevStatus *st)
-{
-    __shared__ unsigned sh[kApplyThreads / 32];
-    const long long nvalid = (long long)S.n0 * S.n1 * S.n2;
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    unsigned nl = 0, nr = 0;
-    for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < nvalid; v += stride) {
-        int i, j, k;
-        cell_of(S, v, nvalid, i, j, k);
-        const long long cs = S.at(i, j, k), cb = B.at(i, j, k);
-        double U[NF], D[NF];
-#pragma unroll
-        for (int f = 0; f < NF; ++f) {
-            U[f] = u[(long long)f * S.fs + cs];
-            D[f] = __ldg(b + (long long)f * B.fs + cb);
-        }
-        int noroot;
-        const double l = sn_lambda(U, D, noroot);
-        nl += l < 1.0;
-        nr += noroot;
-        if (eta_out) eta_out[v] = l;
-        if (!all_zero(D)) {
-            u[cs] = U[0] + D[0];
-            u[S.fs + cs] = U[1] + l * D[1];
-            u[2 * S.fs + cs] = U[2] + l * D[2];
-            u[3 * S.fs + cs] = U[3] + l * D[3];
-            u[4 * S.fs + cs] = U[4] + D[4];
+        npend += __popc(m);
+        __syncwarp();
+        if (npend >= 32) {
+            limit(npend - 32 + lane);
+            npend -= 32;
+            __syncwarp();
         }
     }
+    if (lane < npend) limit(lane);
     block_add(&st->n_limited, nl, sh);
     __syncthreads();
     block_add(&st->n_noroot, nr, sh);
@@ -761,21 +705,13 @@ void launch_sink_eta_apply(const KParams &P, const Box &S, double *u, const Box 
     k_sink_eta_apply<<<grid, kApplyThreads, 0, stream>>>(P, S, u, B, b, drec, eta_out, st);
 }
 
-void launch_apply_fb_fast(const Box &S, double *u, const Box &B, const double *b, double *eta_out, unsigned *queue,
-                          unsigned long long *qcount, cudaStream_t stream)
+void launch_apply_fb_stream(const Box &S, double *u, const Box &B, const double *b, double *eta_out, DevStatus *st,
+                            cudaStream_t stream)
 {
     const long long nvalid = (long long)S.n0 * S.n1 * S.n2;
     if (nvalid == 0) return;
-    const long long per = (long long)kApplyThreads * kApplyChunk;
-    const unsigned grid = resident_grid(k_apply_fb_fast, kApplyThreads, (nvalid + per - 1) / per);
-    k_apply_fb_fast<<<grid, kApplyThreads, 0, stream>>>(S, u, B, b, eta_out, queue, qcount);
-}
-
-void launch_apply_fb_slow(const Box &S, double *u, const Box &B, const double *b, double *eta_out,
-                          const unsigned *queue, const unsigned long long *qcount, DevStatus *st, cudaStream_t stream)
-{
-    const unsigned grid = resident_grid(k_apply_fb_slow, kApplyThreads, 1LL << 40);
-    k_apply_fb_slow<<<grid, kApplyThreads, 0, stream>>>(S, u, B, b, eta_out, queue, qcount, st);
+    const unsigned grid = resident_grid(k_apply_fb_stream, kApplyThreads, (nvalid + kApplyThreads - 1) / kApplyThreads);
+    k_apply_fb_stream<<<grid, kApplyThreads, 0, stream>>>(S, u, B, b, eta_out, st);
 }
 
 // Step 5 of the particle-mesh deposit (no Step 3 in Sec. 2.2's PM/PIC subset):
@@ -807,8 +743,7 @@ void launch_apply(const KParams &P, const Box &S, double *u, const Box &B, const
     if (P.kind == PMP_KIND_MASS) {
         k_apply_add<<<(unsigned)((nvalid + 255) / 256), 256, 0, stream>>>(S, u, B, b, eta_out);
     } else {
-        const unsigned grid = resident_grid(k_apply_fb, kApplyThreads, (nvalid + kApplyThreads - 1) / kApplyThreads);
-        k_apply_fb<<<grid, kApplyThreads, 0, stream>>>(S, u, B, b, eta_out, st);
+        launch_apply_fb_stream(S, u, B, b, eta_out, st, stream);
     }
 }
 

@@ -824,11 +824,10 @@ __device__ __forceinline__ void fb_pair_delta_d(const double *__restrict__ u, co
                    d2, dd, dU);
 }
 
-// With pv (sorted mode: index order, no perm), pair q of particle t, the
-// (offs[t] + q)-th of the index-order list, stores its value at
-// pv[(offs[t] + q) * 5 + f], its buffer cell at skeys[offs[t] + q] and its
-// place offs[t] + q at svals[offs[t] + q] (the sort's keys and values)
-// instead of adding into the buffer.
+// With pv (sorted mode), pair q of the particle at processing position t
+// (particle s) stores its value at pv[(offs[t] + q) * 5 + f], and its buffer
+// cell and that place offs[t] + q at position koffs[s] + q of the sort's key
+// and value lists (particle-index order), instead of adding into the buffer.
 template <int R, bool FB>
 #ifndef PMP_DEPOSIT_MINB
 #define PMP_DEPOSIT_MINB 1
@@ -839,6 +838,7 @@ __global__ void __launch_bounds__(256, PMP_DEPOSIT_MINB) k_deposit_atomic(KParam
                                                         double *__restrict__ E, double *__restrict__ scr,
                                                         double *__restrict__ pv,
                                                         const unsigned long long *__restrict__ offs,
+                                                        const unsigned long long *__restrict__ koffs,
                                                         unsigned *__restrict__ skeys, unsigned *__restrict__ svals)
 {
     constexpr int W = 2 * R + 1;
@@ -969,8 +969,9 @@ __global__ void __launch_bounds__(256, PMP_DEPOSIT_MINB) k_deposit_atomic(KParam
                     double *o = pv + idx * NF;
 #pragma unroll
                     for (int f = 0; f < NF; ++f) o[f] = dU[f];
-                    skeys[idx] = (unsigned)B.at(cell.i, cell.j, cell.k);
-                    svals[idx] = (unsigned)idx;
+                    const unsigned long long kpos = koffs[s] + (g - before);
+                    skeys[kpos] = (unsigned)B.at(cell.i, cell.j, cell.k);
+                    svals[kpos] = (unsigned)idx;
                     continue;
                 }
                 const long long bc = B.at(cell.i, cell.j, cell.k);
@@ -1051,11 +1052,14 @@ __global__ void __launch_bounds__(128) k_segment_runs(Box B, double *__restrict_
     }
 }
 
-// One warp per long run: the lanes compute 32 consecutive pairs' values at a
-// time, then lane f (f < 5) adds field f of them in run order -- for every
-// field the same sequence of additions as a single thread would make, with
-// one FP64 instruction per pair for all five fields (an FP64 instruction with
-// one active lane costs the pipe about what a full-warp one does).
+constexpr int kLongPerWarp = 6;  // long runs a warp sums side by side (lanes 5 r + f)
+
+// Long runs, kLongPerWarp per warp: for 32 consecutive pairs of each of its
+// runs at a time, the lanes load the pairs' stored values into shared
+// memory, then lane 5 r + f adds field f of run r's pairs in run order -- for
+// every run and field the same sequence of additions as a single thread
+// would make.  An FP64 instruction costs the pipe the same with 5 or 30
+// active lanes, so six runs per warp take the time of one.
 __global__ void __launch_bounds__(128) k_segment_long(Box B, double *__restrict__ b, const double *__restrict__ pv,
                                                       const unsigned *__restrict__ uniq,
                                                       const unsigned *__restrict__ lens,
@@ -1064,29 +1068,53 @@ __global__ void __launch_bounds__(128) k_segment_long(Box B, double *__restrict_
                                                       const unsigned *__restrict__ longq,
                                                       const unsigned *__restrict__ nlong_ptr)
 {
-    __shared__ double stage[4][32][NF + 1];
+    __shared__ double stage[4][kLongPerWarp][32][NF];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int rme = lane / NF, fme = lane - rme * NF;  // lanes 0..29: run rme, field fme
     const unsigned nlong = *nlong_ptr;
+    const unsigned ngroups = (nlong + kLongPerWarp - 1) / kLongPerWarp;
     const unsigned nw = gridDim.x * (blockDim.x >> 5);
-    for (unsigned q = blockIdx.x * (blockDim.x >> 5) + wib; q < nlong; q += nw) {
-        const unsigned r = longq[q];
-        const unsigned key = uniq[r], o = offs[r], len = lens[r];
-        double acc = 0.0;
-        if (lane < NF) acc = b[(long long)lane * B.fs + key];
-        for (unsigned c0 = 0; c0 < len; c0 += 32) {
-            if (c0 + lane < len) {
-                const double *v = pv + (unsigned long long)vals[o + c0 + lane] * NF;
+    for (unsigned g = blockIdx.x * (blockDim.x >> 5) + wib; g < ngroups; g += nw) {
+        unsigned key[kLongPerWarp], o[kLongPerWarp], len[kLongPerWarp];
+        unsigned maxlen = 0, mylen = 0, mykey = 0;
 #pragma unroll
-                for (int f = 0; f < NF; ++f) stage[wib][lane][f] = __ldg(v + f);
+        for (int r = 0; r < kLongPerWarp; ++r) {
+            const unsigned q = g * kLongPerWarp + r;
+            len[r] = 0;
+            key[r] = 0;
+            o[r] = 0;
+            if (q < nlong) {
+                const unsigned rr = longq[q];
+                key[r] = uniq[rr];
+                o[r] = offs[rr];
+                len[r] = lens[rr];
+            }
+            maxlen = len[r] > maxlen ? len[r] : maxlen;
+            if (r == rme) {
+                mylen = len[r];
+                mykey = key[r];
+            }
+        }
+        const bool mine = rme < kLongPerWarp && mylen > 0;
+        double acc = 0.0;
+        if (mine) acc = b[(long long)fme * B.fs + mykey];
+        for (unsigned c0 = 0; c0 < maxlen; c0 += 32) {
+#pragma unroll
+            for (int r = 0; r < kLongPerWarp; ++r) {
+                if (c0 + lane < len[r]) {
+                    const double *v = pv + (unsigned long long)__ldg(vals + o[r] + c0 + lane) * NF;
+#pragma unroll
+                    for (int f = 0; f < NF; ++f) stage[wib][r][lane][f] = __ldg(v + f);
+                }
             }
             __syncwarp();
-            if (lane < NF) {
-                const unsigned m = len - c0 < 32u ? len - c0 : 32u;
-                for (unsigned l = 0; l < m; ++l) acc = acc + stage[wib][l][lane];
+            if (mine && mylen > c0) {
+                const unsigned m = mylen - c0 < 32u ? mylen - c0 : 32u;
+                for (unsigned l = 0; l < m; ++l) acc = acc + stage[wib][rme][l][fme];
             }
             __syncwarp();
         }
-        if (lane < NF) b[(long long)lane * B.fs + key] = acc;
+        if (mine) b[(long long)fme * B.fs + mykey] = acc;
     }
 }
 
@@ -1403,8 +1431,8 @@ void launch_pass1_sink(const KParams &P, const Box &S, const double *u, const Bo
 
 static void launch_pair_kernel(const KParams &P, const Box &S, const double *u, const Box &B, double *b,
                                const Parts &p, const double *G, const PlanPtrs &pl, double *E, double *scr,
-                               double *pv, const unsigned long long *offs, unsigned *skeys, unsigned *svals,
-                               cudaStream_t stream)
+                               double *pv, const unsigned long long *offs, const unsigned long long *koffs,
+                               unsigned *skeys, unsigned *svals, cudaStream_t stream)
 {
     if (p.count == 0) return;
     // Only resident blocks: the grid-stride loop then moves all of them
@@ -1421,32 +1449,49 @@ static void launch_pair_kernel(const KParams &P, const Box &S, const double *u, 
     } else {
         PMP_DISPATCH_R(P.R, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_deposit_atomic<RR, false>, 256, 0));
     }
-    // two resident blocks per SM: the 512^3 sweep gave the sink deposit 18.1
-    // -> 16.5 ms and left the supernova deposit (FP64-bound) unchanged
-    occ = occ < 2 ? occ : 2;
+    // resident blocks per SM (512^3 sweeps): the sink deposit does best with
+    // two (18.1 -> 16.5 ms), the supernova deposit with three (23.9 -> 22.2
+    // ms against two; more warps hide its loads' latency)
+    const int cap = P.kind == PMP_KIND_SINK ? 2 : 3;
+    occ = occ < cap ? occ : cap;
     if (PMP_DEPOSIT_BPS > 0) occ = PMP_DEPOSIT_BPS;
     if (occ < 1) occ = 1;
     const unsigned nb = (unsigned)(blocks_needed < (long long)nsm * occ ? blocks_needed : (long long)nsm * occ);
     if (P.kind != PMP_KIND_SINK) {
         PMP_DISPATCH_R(P.R, (k_deposit_atomic<RR, true><<<nb, 256, 0, stream>>>(P, S, u, B, b, p, G, pl, E, nullptr,
-                                                                                 pv, offs, skeys, svals)));
+                                                                                 pv, offs, koffs, skeys, svals)));
     } else {
         PMP_DISPATCH_R(P.R, (k_deposit_atomic<RR, false><<<nb, 256, 0, stream>>>(P, S, u, B, b, p, G, pl, E, scr,
-                                                                                  pv, offs, skeys, svals)));
+                                                                                  pv, offs, koffs, skeys, svals)));
     }
 }
 
 void launch_deposit_atomic(const KParams &P, const Box &S, const double *u, const Box &B, double *b, const Parts &p,
                            const double *G, const PlanPtrs &pl, double *E, double *scr, cudaStream_t stream)
 {
-    launch_pair_kernel(P, S, u, B, b, p, G, pl, E, scr, nullptr, nullptr, nullptr, nullptr, stream);
+    launch_pair_kernel(P, S, u, B, b, p, G, pl, E, scr, nullptr, nullptr, nullptr, nullptr, nullptr, stream);
 }
 
 void launch_pair_values(const KParams &P, const Box &S, const double *u, const Box &B, const Parts &p,
-                        const double *G, const PlanPtrs &pl, const unsigned long long *offsets, double *pv,
-                        unsigned *keys, unsigned *vals, cudaStream_t stream)
+                        const double *G, const PlanPtrs &pl, const unsigned long long *offsets,
+                        const unsigned long long *koffsets, double *pv, unsigned *keys, unsigned *vals,
+                        cudaStream_t stream)
 {
-    launch_pair_kernel(P, S, u, B, nullptr, p, G, pl, nullptr, nullptr, pv, offsets, keys, vals, stream);
+    launch_pair_kernel(P, S, u, B, nullptr, p, G, pl, nullptr, nullptr, pv, offsets, koffsets, keys, vals, stream);
+}
+
+__global__ void __launch_bounds__(256) k_counts_by_index(const unsigned *__restrict__ perm,
+                                                         const unsigned *__restrict__ counts, long long n,
+                                                         unsigned *__restrict__ counts_idx)
+{
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < n) counts_idx[perm ? perm[t] : t] = counts[t];
+    if (t == n) counts_idx[n] = 0;
+}
+
+void launch_counts_by_index(const PlanPtrs &pl, long long n, unsigned *counts_idx, cudaStream_t stream)
+{
+    k_counts_by_index<<<blocks_for(n + 1, 256), 256, 0, stream>>>(pl.perm, pl.counts, n, counts_idx);
 }
 
 
