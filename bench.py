@@ -221,15 +221,15 @@ def roofline(kernel, ms, pairs, box, n_fb, n_sk, hbm_peak, peak_src):
 def cell_pass_hbm(kernel_ms, box, hbm_peak):
     """Per-launch HBM rate of the cell passes: algorithmic bytes (what a
     perfect implementation moves) over the CUDA-event time of the launch, and
-    the fraction of the measured copy bandwidth.  The supernova apply is the
-    fast kernel plus the FP64 limiter on the queued cells (one phase, 120 B
-    per valid cell); the sink apply computes eta and updates the state in one
-    pass (128 B per valid cell with the eta it records for Step 4)."""
+    the fraction of the measured copy bandwidth.  The supernova apply reads
+    the state and the summed change and writes the state (120 B per valid
+    cell); the sink apply computes eta and updates the state in one pass (128
+    B per valid cell with the eta it records for Step 4)."""
     nvalid, npad = box.ncells_valid, box.ncells_padded
     phases = {
         "fb_zero": (("fb_zero",), 40 * npad),
         "fb_fold": (("fb_fold",), 120 * (npad - nvalid)),
-        "fb_apply": (("fb_apply", "fb_apply_fp64"), 120 * nvalid),
+        "fb_apply": (("fb_apply",), 120 * nvalid),
         "sink_zero": (("sink_zero",), 40 * npad),
         "sink_cell_records": (("sink_cell_records",), (40 + 96) * nvalid),
         "sink_spread": (("sink_spread",), 136 * npad),
@@ -435,13 +435,13 @@ def run_ours(args, world, rank, local):
               "sink_zero", "sink_gather_deposit", "sink_fold", "sink_apply"]
     # own kernels per step (the CUB sorts, scans and run encoding are library
     # kernels).  ATOMIC: supernova pass zero, prologue, plan + gather,
-    # deposit, fold, apply (fast + queued) = 7; sink pass zero, prologue,
-    # per-cell records, plan + gather + deposit, spread, fold, eta + apply,
-    # Step-4 return = 8.  SORTED: pair values (with the sort's keys), run and
-    # long-run kernels in place of the deposit (supernovae 9); sinks plan,
-    # gather, pair values, runs, long runs, no spread (11).  ROUNDED: a
-    # deposit and a rounding kernel per pass (8 + 10).
-    launches_per_step = {"atomic": 15, "sorted": 20, "rounded": 18}[args.mode]
+    # deposit, fold, apply = 6; sink pass zero, prologue, per-cell records,
+    # plan + gather + deposit, spread, fold, eta + apply, Step-4 return = 8.
+    # SORTED: the pair counts in index order, pair values (with the sort's
+    # lists), run and long-run kernels in place of the deposit (supernovae
+    # 9); sinks plan, gather, the same four, no spread (12).  ROUNDED: a
+    # deposit and a rounding kernel per pass (7 + 10).
+    launches_per_step = {"atomic": 14, "sorted": 21, "rounded": 17}[args.mode]
     state0 = state.clone()
     sink0 = {k: sk[k].clone() for k in ("m", "px", "py", "pz")}
 
@@ -606,10 +606,10 @@ def end_to_end(args, w, world, state, fb, sk, P_fb, P_sk, cycle, stream):
     """The cycle measured from pinned host memory to pinned host memory: every
     step copies its inputs (gas state, both particle sets) to the device, runs
     the two passes and copies the results (gas state, sink masses and
-    momenta) back.  Double-buffered: two device input sets; the copies of step
-    k+1 (in) and k-1 (out) run on two copy streams while step k computes, each
-    copy ordered after the work it depends on by events.  Also reported: the
-    same steps run one after another on one stream (serial_ms_per_step)."""
+    momenta) back.  Pipelined over three device input sets: the copies of
+    step k+1 (in) and k-1 (out) run on two copy streams while step k computes,
+    each copy ordered after the work it depends on by events.  Also reported:
+    the same steps run one after another on one stream (serial_ms_per_step)."""
     import torch
 
     from paper_2509_18261_gb300 import pmp
@@ -617,8 +617,10 @@ def end_to_end(args, w, world, state, fb, sk, P_fb, P_sk, cycle, stream):
     h_state = torch.from_numpy(w["state"]).pin_memory()
     h_fb = {k: torch.from_numpy(v).pin_memory() for k, v in w["fb"].items()}
     h_sk = {k: torch.from_numpy(v).pin_memory() for k, v in w["sink"].items()}
+    NSETS = 3  # device input sets of the pipelined form (below)
     outs = [dict(state=torch.empty_like(h_state).pin_memory(),
-                 sk={k: torch.empty_like(h_sk[k]).pin_memory() for k in ("m", "px", "py", "pz")}) for _ in range(2)]
+                 sk={k: torch.empty_like(h_sk[k]).pin_memory() for k in ("m", "px", "py", "pz")})
+            for _ in range(NSETS)]
     bi = h_state.numel() * 8 + sum(v.numel() * 8 for v in h_fb.values()) + sum(v.numel() * 8 for v in h_sk.values())
     bo = h_state.numel() * 8 + sum(v.numel() * 8 for v in outs[0]["sk"].values())
     steps = max(args.e2e_steps if args.e2e_steps else args.steps, 2)
@@ -656,19 +658,27 @@ def end_to_end(args, w, world, state, fb, sk, P_fb, P_sk, cycle, stream):
     torch.cuda.synchronize()
     serial_ms = max_over_ranks(world, e0.elapsed_time(e1) / steps)
 
-    # double-buffered: a second device input set with its own passes
-    st1 = torch.empty_like(state)
-    fb1 = {k: torch.empty_like(v) for k, v in fb.items()}
-    sk1 = {k: torch.empty_like(v) for k, v in sk.items()}
+    # pipelined over NSETS device input sets, each with its own passes: the
+    # copy of step k+1's inputs (in) and of step k-1's results (out) run on
+    # two copy streams while step k computes; with three sets an in-copy
+    # never waits for the out-copy of the same set (two sets chain the two
+    # copies of every step one after the other)
     mode = args.mode
-    Q_fb = pmp.Pass(w["fb_params"], P_fb.box, st1, fb1, mode=mode)
-    Q_sk = pmp.Pass(w["sink_params"], P_sk.box, st1, sk1, mode=mode)
-    sets = [(state, fb, sk, ((P_fb, fb), (P_sk, sk))), (st1, fb1, sk1, ((Q_fb, fb1), (Q_sk, sk1)))]
+    sets = [(state, fb, sk, ((P_fb, fb), (P_sk, sk)))]
+    extra = []
+    for _ in range(NSETS - 1):
+        st1 = torch.empty_like(state)
+        fb1 = {k: torch.empty_like(v) for k, v in fb.items()}
+        sk1 = {k: torch.empty_like(v) for k, v in sk.items()}
+        Q_fb = pmp.Pass(w["fb_params"], P_fb.box, st1, fb1, mode=mode)
+        Q_sk = pmp.Pass(w["sink_params"], P_sk.box, st1, sk1, mode=mode)
+        extra += [Q_fb, Q_sk]
+        sets.append((st1, fb1, sk1, ((Q_fb, fb1), (Q_sk, sk1))))
     s_in, s_out = torch.cuda.Stream(), torch.cuda.Stream()
-    ev_in = [torch.cuda.Event() for _ in range(2)]
-    ev_done = [torch.cuda.Event() for _ in range(2)]
-    ev_out = [torch.cuda.Event() for _ in range(2)]
-    out_used = [False, False]
+    ev_in = [torch.cuda.Event() for _ in range(NSETS)]
+    ev_done = [torch.cuda.Event() for _ in range(NSETS)]
+    ev_out = [torch.cuda.Event() for _ in range(NSETS)]
+    out_used = [False] * NSETS
     barrier(world)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -678,7 +688,7 @@ def end_to_end(args, w, world, state, fb, sk, P_fb, P_sk, cycle, stream):
         copy_in(*sets[0][:3])
         ev_in[0].record(s_in)
     for k in range(steps):
-        i, j = k % 2, (k + 1) % 2
+        i, j = k % NSETS, (k + 1) % NSETS
         if k + 1 < steps:
             with torch.cuda.stream(s_in):
                 if out_used[j]:
@@ -693,13 +703,13 @@ def end_to_end(args, w, world, state, fb, sk, P_fb, P_sk, cycle, stream):
             copy_out(outs[i], sets[i][0], sets[i][2])
             ev_out[i].record(s_out)
         out_used[i] = True
-    for i in range(2):
+    for i in range(NSETS):
         if out_used[i]:
             stream.wait_event(ev_out[i])
     e1.record(stream)
     torch.cuda.synchronize()
     ms = max_over_ranks(world, e0.elapsed_time(e1) / steps)
-    for P in (Q_fb, Q_sk):
+    for P in extra:
         code, idx = pmp.pmp_get_error(P.ctx)
         if code:
             raise RuntimeError(f"e2e: device error {code} at {idx}")
@@ -708,7 +718,8 @@ def end_to_end(args, w, world, state, fb, sk, P_fb, P_sk, cycle, stream):
     return {"value": n_particles * world / (ms * 1e-3), "unit": "particles/s", "ms_per_step": ms,
             "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo, "steps": steps,
             "serial_ms_per_step": serial_ms,
-            "overlap": "double-buffered: the copies of step k+1 (in) and k-1 (out) run on copy streams during step k"}
+            "overlap": "three device input sets: the copies of step k+1 (in) and k-1 (out) run on two copy streams "
+                       "during step k"}
 
 
 def touched_cells(P_fb, params, box, state0, fb):

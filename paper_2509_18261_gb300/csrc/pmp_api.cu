@@ -26,8 +26,6 @@ using pmp::overlaps;
 using pmp::KParams;
 using pmp::Parts;
 
-bool finite(double v) { return std::isfinite(v); }
-
 // State/buffer compatibility and the ghost-width rule (Sec. 2.2, Step 1: the
 // buffer's ghost zones must contain the kernel).
 pmp_status check_pair(const pmp_ctx *ctx, const pmp_mesh *state, const pmp_mesh *buffer, Box *S, Box *B)

@@ -376,6 +376,21 @@ __device__ __forceinline__ void feedback_delta(double w, const double U[NF], dou
     dU[4] = fma(w, e, fma(vc[2], pr2, fma(vc[1], pr1, vc[0] * pr0)));
 }
 
+// max(b, x) for b >= +0 and x not NaN, as a comparison of the 64-bit
+// patterns: non-negative doubles order like their patterns, and a negative x
+// (or -0) has a negative pattern.  The same value as b >= x ? b : x, off the
+// FP64 pipe (an FP64 comparison occupies it like an addition).
+__device__ __forceinline__ double max_nonneg(double b, double x)
+{
+    return __double_as_longlong(b) >= __double_as_longlong(x) ? b : x;
+}
+
+// -x by flipping the sign bit (exact, off the FP64 pipe).
+__device__ __forceinline__ double neg_bits(double x)
+{
+    return __longlong_as_double(__double_as_longlong(x) ^ (long long)0x8000000000000000ULL);
+}
+
 // Sink deposition function (Eq. accretion_function with the Truelove rate in
 // the max): a = max(K w, rho - rho_Tr), Delta U = -a (1, p inv, E inv).
 __device__ __forceinline__ void sink_delta(const KParams &P, const double U[NF], double K, double w, double dU[NF])
@@ -412,6 +427,15 @@ enum { MS_VK = 0, MS_Q, MS_ROWS = MS_Q + NF };  // V_K, then (m, p, e) / V_K
 // their dozen call sites made the fused plan + gather kernels' code large
 // enough to stall on instruction fetch (512^3: 25.0 -> 29.0 ms).  The
 // per-pair and per-cell formulas use the integer forms.
+
+// Quotients and square roots of the per-sink formulas: the integer forms of
+// pmp_exact.cuh (the same correctly rounded values, off the FP64 pipe)
+// through one out-of-line copy each, so that their dozen call sites do not
+// enlarge the kernels' code (512^3: sink plan + gather + deposit 23.5 -> 23.2
+// ms).  The supernova rows keep the compiler's FP64 sequences: the integer
+// forms made the supernova plan + gather slower (25.0 -> 26.5 ms).
+static __device__ __noinline__ double row_div(double a, double b) { return exact::div_rn(a, b); }
+static __device__ __noinline__ double row_sqrt(double x) { return exact::sqrt_rn(x); }
 
 // Sec. 3.2.1 from the omega-weighted sums over the kernel: sw = sum omega,
 // sr = sum omega rho, sp = sum omega p.  Writes the 12 feedback rows of one
@@ -471,17 +495,17 @@ __device__ __forceinline__ SinkAmbient sink_ambient(const KParams &P, double srh
                                                     double src, int nk, double ms, double ps0, double ps1, double ps2)
 {
     SinkAmbient a;
-    a.rho_inf = srho / (double)nk;
-    a.c_inf = src / srho;
-    const double u0 = sp0 / srho - ps0 / ms;
-    const double u1 = sp1 / srho - ps1 / ms;
-    const double u2 = sp2 / srho - ps2 / ms;
+    a.rho_inf = row_div(srho, (double)nk);
+    a.c_inf = row_div(src, srho);
+    const double u0 = row_div(sp0, srho) - row_div(ps0, ms);
+    const double u1 = row_div(sp1, srho) - row_div(ps1, ms);
+    const double u2 = row_div(sp2, srho) - row_div(ps2, ms);
     a.vinf2 = (u0 * u0 + u1 * u1) + u2 * u2;
     const double cinf2 = a.c_inf * a.c_inf;
     a.den = a.vinf2 + cinf2;
-    const double r_bh = (P.G * ms) / a.den;
-    a.mdot = ((P.four_pi * a.rho_inf) * (r_bh * r_bh)) * sqrt(P.lam2 * cinf2 + a.vinf2);
-    double racc = r_bh / P.dx;
+    const double r_bh = row_div(P.G * ms, a.den);
+    a.mdot = ((P.four_pi * a.rho_inf) * (r_bh * r_bh)) * row_sqrt(P.lam2 * cinf2 + a.vinf2);
+    double racc = row_div(r_bh, P.dx);
     if (racc < 0.25) racc = 0.25;
     if (racc > 0.5 * P.rK) racc = 0.5 * P.rK;
     a.racc = racc;
@@ -490,18 +514,18 @@ __device__ __forceinline__ SinkAmbient sink_ambient(const KParams &P, double srh
 }
 
 // Per-axis Gaussian factor exp(-d^2 / r_acc^2) of the cell centred d away.
-__device__ __forceinline__ double sink_axis_weight(double d, double ra2) { return pmp_exp(-((d * d) / ra2)); }
+__device__ __forceinline__ double sink_axis_weight(double d, double ra2) { return pmp_exp(-row_div(d * d, ra2)); }
 
 // Second half: K = mdot dt / (V sum w) and the 8 sink rows; false (and K = 0)
 // if a result is not finite.
 __device__ __forceinline__ bool sink_gather_rows(const KParams &P, const SinkAmbient &a, double sumw, int nk, double *G,
                                                  long long gs)
 {
-    double K = ((a.mdot * P.dt) / P.V) / sumw;
+    double K = row_div(row_div(a.mdot * P.dt, P.V), sumw);
     const bool ok = (a.den > 0.0) && isfinite(a.mdot) && isfinite(K);
     if (!ok) K = 0.0;
     G[SK_RHO * gs] = a.rho_inf;
-    G[SK_VINF * gs] = sqrt(a.vinf2);
+    G[SK_VINF * gs] = row_sqrt(a.vinf2);
     G[SK_CINF * gs] = a.c_inf;
     G[SK_MDOT * gs] = a.mdot;
     G[SK_RACC * gs] = a.racc;

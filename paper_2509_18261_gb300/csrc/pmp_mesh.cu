@@ -291,7 +291,7 @@ __global__ void __launch_bounds__(256) k_sink_spread(Box S, Box B, double *__res
         for (int ii = threadIdx.x; ii < B.px; ii += blockDim.x) {
             const long long c = c0 + ii;
             const double sc = scr[c];
-            if (sc == 0.0) continue;
+            if ((__double_as_longlong(sc) << 1) == 0) continue;  // +-0: no pair reached the cell
             const int i = ii - B.g;
             const double2 *d = reinterpret_cast<const double2 *>(
                 drec + vidx(S, owner(i, S.n0), owner(j, S.n1), owner(k, S.n2)) * kRec);

@@ -796,9 +796,9 @@ __global__ void __launch_bounds__(128, PMP_SINK_PASS1_MINB) k_pass1_sink(KParams
                                      wj[2 * W + cell.k - ht[3 * j + 2] + R];
                     const double d0x =
                         __ldg(pl.drec + vidx(S, owner(cell.i, S.n0), owner(cell.j, S.n1), owner(cell.k, S.n2)) * kRec);
-                    const double bh = kt[j] * w;
-                    const double a = bh >= d0x ? bh : d0x;
-                    atomicAdd(scr + B.at(cell.i, cell.j, cell.k), -a);
+                    const double bh = kt[j] * w;  // >= +0: K and w are
+                    const double a = max_nonneg(bh, d0x);
+                    atomicAdd(scr + B.at(cell.i, cell.j, cell.k), neg_bits(a));
                     if (pl.pa) pl.pa[slot] = a;  // Step 4 reads it back (launch_return_sinks_stored)
                 }
             }
@@ -951,10 +951,10 @@ __global__ void __launch_bounds__(256, PMP_DEPOSIT_MINB) k_deposit_atomic(KParam
                         pl.drec + vidx(S, owner(cell.i, S.n0), owner(cell.j, S.n1), owner(cell.k, S.n2)) * kRec);
                     const double2 d0 = __ldg(d);
                     const double bh = kt[j] * w;
-                    const double a = bh >= d0.x ? bh : d0.x;
+                    const double a = max_nonneg(bh, d0.x);
                     if (scr) {
                         // the cell's factors (1, p/rho, E/rho) are applied by k_sink_spread
-                        atomicAdd(scr + B.at(cell.i, cell.j, cell.k), -a);
+                        atomicAdd(scr + B.at(cell.i, cell.j, cell.k), neg_bits(a));
                         continue;
                     }
                     const double2 d1 = __ldg(d + 1), d2 = __ldg(d + 2);
@@ -998,13 +998,16 @@ __global__ void __launch_bounds__(256, PMP_DEPOSIT_MINB) k_deposit_atomic(KParam
 
 
 
-constexpr unsigned kLongRun = 32;  // runs longer than this get a warp
+constexpr unsigned kLongRun = 32;  // runs longer than this are summed by k_segment_long
 constexpr int kSegChunk = 4;       // pairs whose loads a run's thread issues together
 
 // One thread per run of equal keys (a buffer cell) of at most kLongRun pairs:
 // the run's pairs, which the stable sort kept in particle-index order, are
 // added in that order on top of what the buffer holds.  Longer runs are
-// queued for k_segment_long.
+// queued for k_segment_long.  (Runs handed to the lanes as they finish, or
+// sorted by length within blocks of 128, issue fewer FP64 additions but were
+// slower: 0.67 ms here, 0.89 and 0.71 ms those, at 256^3; the kernel waits
+// on its chain of dependent loads.)
 __global__ void __launch_bounds__(128) k_segment_runs(Box B, double *__restrict__ b, const double *__restrict__ pv,
                                                       const unsigned long long *__restrict__ nruns_ptr,
                                                       const unsigned *__restrict__ uniq,
@@ -1055,11 +1058,14 @@ __global__ void __launch_bounds__(128) k_segment_runs(Box B, double *__restrict_
 constexpr int kLongPerWarp = 6;  // long runs a warp sums side by side (lanes 5 r + f)
 
 // Long runs, kLongPerWarp per warp: for 32 consecutive pairs of each of its
-// runs at a time, the lanes load the pairs' stored values into shared
-// memory, then lane 5 r + f adds field f of run r's pairs in run order -- for
-// every run and field the same sequence of additions as a single thread
-// would make.  An FP64 instruction costs the pipe the same with 5 or 30
-// active lanes, so six runs per warp take the time of one.
+// runs at a time, the lanes stage the pairs' stored values in shared memory,
+// then lane 5 r + f adds field f of run r's pairs in run order -- for every
+// run and field the same sequence of additions as a single thread would
+// make.  An FP64 instruction costs the pipe the same with 5 or 30 active
+// lanes, so six runs per warp take the time of one.  The loads are
+// software-pipelined: the next chunk's values and the chunk after that's
+// list indices are in flight while a chunk is summed, so a run of thousands
+// of pairs (a Plummer core) costs about one load latency per 32 pairs.
 __global__ void __launch_bounds__(128) k_segment_long(Box B, double *__restrict__ b, const double *__restrict__ pv,
                                                       const unsigned *__restrict__ uniq,
                                                       const unsigned *__restrict__ lens,
@@ -1068,18 +1074,19 @@ __global__ void __launch_bounds__(128) k_segment_long(Box B, double *__restrict_
                                                       const unsigned *__restrict__ longq,
                                                       const unsigned *__restrict__ nlong_ptr)
 {
-    __shared__ double stage[4][kLongPerWarp][32][NF];
+    constexpr int G = kLongPerWarp;
+    __shared__ double stage[4][G][32][NF];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int rme = lane / NF, fme = lane - rme * NF;  // lanes 0..29: run rme, field fme
     const unsigned nlong = *nlong_ptr;
-    const unsigned ngroups = (nlong + kLongPerWarp - 1) / kLongPerWarp;
+    const unsigned ngroups = (nlong + G - 1) / G;
     const unsigned nw = gridDim.x * (blockDim.x >> 5);
     for (unsigned g = blockIdx.x * (blockDim.x >> 5) + wib; g < ngroups; g += nw) {
-        unsigned key[kLongPerWarp], o[kLongPerWarp], len[kLongPerWarp];
+        unsigned key[G], o[G], len[G];
         unsigned maxlen = 0, mylen = 0, mykey = 0;
 #pragma unroll
-        for (int r = 0; r < kLongPerWarp; ++r) {
-            const unsigned q = g * kLongPerWarp + r;
+        for (int r = 0; r < G; ++r) {
+            const unsigned q = g * G + r;
             len[r] = 0;
             key[r] = 0;
             o[r] = 0;
@@ -1095,22 +1102,52 @@ __global__ void __launch_bounds__(128) k_segment_long(Box B, double *__restrict_
                 mykey = key[r];
             }
         }
-        const bool mine = rme < kLongPerWarp && mylen > 0;
+        const bool mine = rme < G && mylen > 0;
         double acc = 0.0;
         if (mine) acc = b[(long long)fme * B.fs + mykey];
+        // chunk 0's values, chunk 1's indices
+        unsigned id[G];
+        double v[G][NF];
+#pragma unroll
+        for (int r = 0; r < G; ++r) id[r] = lane < (int)len[r] ? __ldg(vals + o[r] + lane) : 0u;
+#pragma unroll
+        for (int r = 0; r < G; ++r) {
+#pragma unroll
+            for (int f = 0; f < NF; ++f)
+                v[r][f] = lane < (int)len[r] ? __ldg(pv + (unsigned long long)id[r] * NF + f) : 0.0;
+        }
+#pragma unroll
+        for (int r = 0; r < G; ++r) id[r] = 32u + lane < len[r] ? __ldg(vals + o[r] + 32u + lane) : 0u;
         for (unsigned c0 = 0; c0 < maxlen; c0 += 32) {
 #pragma unroll
-            for (int r = 0; r < kLongPerWarp; ++r) {
+            for (int r = 0; r < G; ++r) {
                 if (c0 + lane < len[r]) {
-                    const double *v = pv + (unsigned long long)__ldg(vals + o[r] + c0 + lane) * NF;
 #pragma unroll
-                    for (int f = 0; f < NF; ++f) stage[wib][r][lane][f] = __ldg(v + f);
+                    for (int f = 0; f < NF; ++f) stage[wib][r][lane][f] = v[r][f];
                 }
             }
             __syncwarp();
+            // in flight during the sums: chunk c0 + 32's values, chunk c0 + 64's indices
+            const unsigned c1 = c0 + 32u, c2 = c0 + 64u;
+#pragma unroll
+            for (int r = 0; r < G; ++r) {
+#pragma unroll
+                for (int f = 0; f < NF; ++f)
+                    v[r][f] = c1 + lane < len[r] ? __ldg(pv + (unsigned long long)id[r] * NF + f) : 0.0;
+            }
+#pragma unroll
+            for (int r = 0; r < G; ++r) id[r] = c2 + lane < len[r] ? __ldg(vals + o[r] + c2 + lane) : 0u;
             if (mine && mylen > c0) {
+                // eight staged values at a time in registers, then added in order
                 const unsigned m = mylen - c0 < 32u ? mylen - c0 : 32u;
-                for (unsigned l = 0; l < m; ++l) acc = acc + stage[wib][rme][l][fme];
+                for (unsigned l0 = 0; l0 < m; l0 += 8) {
+                    double x[8];
+#pragma unroll
+                    for (int k = 0; k < 8; ++k) x[k] = stage[wib][rme][l0 + k][fme];
+#pragma unroll
+                    for (int k = 0; k < 8; ++k)
+                        if (l0 + k < m) acc = acc + x[k];
+                }
             }
             __syncwarp();
         }
@@ -1495,6 +1532,10 @@ void launch_counts_by_index(const PlanPtrs &pl, long long n, unsigned *counts_id
 }
 
 
+#ifndef PMP_SEG_LONG_BPS
+#define PMP_SEG_LONG_BPS 2
+#endif
+
 void launch_segment_sum(const Box &B, double *b, const double *pv, const unsigned long long *nruns,
                         const unsigned *uniq, const unsigned *lens, const unsigned *offs, const unsigned *vals,
                         unsigned *longq, unsigned *nlong, cudaStream_t stream)
@@ -1502,7 +1543,15 @@ void launch_segment_sum(const Box &B, double *b, const double *pv, const unsigne
     const unsigned nb = 152u * 32u;
     cudaMemsetAsync(nlong, 0, sizeof(unsigned), stream);
     k_segment_runs<<<nb, 128, 0, stream>>>(B, b, pv, nruns, uniq, lens, offs, vals, longq, nlong);
-    k_segment_long<<<152u * 8u, 128, 0, stream>>>(B, b, pv, uniq, lens, offs, vals, longq, nlong);
+    // long runs: two four-warp blocks per SM.  The runs of one Plummer core
+    // are neighbours in the queue; with few warps per SM the grid-stride
+    // order deals them out over all SMs, and the FP64 pipe of an SM is
+    // shared by few sequential chains (with 16 warps per SM the core's
+    // chains shared a few SMs' pipes: 0.68 ms at 256^3)
+    int dev = 0, nsm = 152;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    k_segment_long<<<(unsigned)nsm * PMP_SEG_LONG_BPS, 128, 0, stream>>>(B, b, pv, uniq, lens, offs, vals, longq,
+                                                                        nlong);
 }
 
 #ifndef PMP_SINK_RETURN_STORED_BPS

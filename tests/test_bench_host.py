@@ -58,12 +58,13 @@ def test_traffic_is_reported_only_for_the_profiled_sources(monkeypatch):
     assert 20.0 < a / 1000 < 400.0  # bytes per pair of the 192^3 capture
 
 
-def test_cell_pass_hbm_sums_the_two_supernova_apply_kernels():
+def test_cell_pass_hbm_rates():
     box = _box()
-    km = {"fb_apply": (1.0, 2.9), "fb_apply_fp64": (1.0, 6.3), "sink_apply": (1.0, 7.2), "fb_zero": (1.0, 0.86)}
+    km = {"fb_apply": (1.0, 5.2), "sink_apply": (1.0, 7.2), "fb_zero": (1.0, 0.86)}
     out = bench.cell_pass_hbm(km, box, 6793.4)
-    assert out["fb_apply"]["ms"] == pytest.approx(9.2)
-    assert out["fb_apply"]["GB/s"] == pytest.approx(120 * 512 ** 3 / 9.2e-3 / 1e9, rel=1e-3)
+    assert out["fb_apply"]["ms"] == pytest.approx(5.2)
+    assert out["fb_apply"]["GB/s"] == pytest.approx(120 * 512 ** 3 / 5.2e-3 / 1e9, rel=1e-3)
+    assert out["fb_apply"]["frac"] == pytest.approx(out["fb_apply"]["GB/s"] / 6793.4, rel=1e-3)
     assert out["sink_apply"]["bytes"] == 128 * 512 ** 3
     assert out["sink_apply"]["ms"] == pytest.approx(7.2)
     assert out["fb_zero"]["bytes"] == 40 * box.ncells_padded
