@@ -252,13 +252,15 @@ __device__ __forceinline__ double sink_eta(const KParams &P, const double U[NF],
 // lambda = 1 if the constraint holds at 1; otherwise the largest root in
 // [0, 1] of |dp|^2 l^2 + 2 (p . dp) l + |p|^2 - 2 rho' (E' - e_int0 rho'/rho),
 // from the cancellation-free quadratic formula (Press et al., Numerical
-// Recipes, Sec. 5.6); 0 if there is none (noroot set).
-__device__ __forceinline__ double sn_lambda(const double U[NF], const double D[NF], int &noroot)
+// Recipes, Sec. 5.6); 0 if there is none (noroot set).  sn_lambda_dp is the
+// limiter for a change whose momentum is not zero (no test for Delta p = 0),
+// and returns rho' = U_0 + D_0 and E' = U_4 + D_4 for the update.
+__device__ __forceinline__ double sn_lambda_dp(const double U[NF], const double D[NF], int &noroot, double &rho1,
+                                               double &E1)
 {
     noroot = 0;
-    if (D[1] == 0.0 && D[2] == 0.0 && D[3] == 0.0) return 1.0;
-    const double rho1 = U[0] + D[0];
-    const double E1 = U[4] + D[4];
+    rho1 = U[0] + D[0];
+    E1 = U[4] + D[4];
     const double p2 = (U[1] * U[1] + U[2] * U[2]) + U[3] * U[3];
     const double eint0 = U[4] - exact::div_rn(p2, 2.0 * U[0]);
     const double pn0 = U[1] + D[1], pn1 = U[2] + D[2], pn2 = U[3] + D[3];
@@ -267,30 +269,38 @@ __device__ __forceinline__ double sn_lambda(const double U[NF], const double D[N
     const double lhs = therm + exact::div_rn(pnn, 2.0 * rho1);
     if (lhs <= E1) return 1.0;
     const double A = (D[1] * D[1] + D[2] * D[2]) + D[3] * D[3];
-    if (!(A > 0.0)) return 1.0;
+    if (!exact::positive(A)) return 1.0;  // !(A > 0)
     const double B = (U[1] * D[1] + U[2] * D[2]) + U[3] * D[3];
     const double C = p2 - (2.0 * rho1) * (E1 - therm);
     const double disc = B * B - A * C;
-    if (!(disc >= 0.0)) {
+    if (!exact::ge0(disc)) {
         noroot = 1;
         return 0.0;
     }
     const double sq = exact::sqrt_rn(disc);
     double hi, lo;
-    if (B >= 0.0) {
+    if (exact::ge0(B)) {
         const double Q = -(B + sq);
-        hi = Q != 0.0 ? exact::div_rn(C, Q) : 0.0;
+        hi = exact::ne0(Q) ? exact::div_rn(C, Q) : 0.0;
         lo = exact::div_rn(Q, A);
     } else {
         const double Q = sq - B;
         hi = exact::div_rn(Q, A);
         lo = exact::div_rn(C, Q);
     }
-    if (hi < 0.0 || lo > 1.0) {
+    if (exact::lt0(hi) || exact::gt1(lo)) {
         noroot = 1;
         return 0.0;
     }
-    return hi < 1.0 ? hi : 1.0;
+    return exact::lt1(hi) ? hi : 1.0;
+}
+
+__device__ __forceinline__ double sn_lambda(const double U[NF], const double D[NF], int &noroot)
+{
+    noroot = 0;
+    if (((exact::bits_of(D[1]) | exact::bits_of(D[2]) | exact::bits_of(D[3])) << 1) == 0) return 1.0;  // Delta p = 0
+    double rho1, E1;
+    return sn_lambda_dp(U, D, noroot, rho1, E1);
 }
 
 // ---------------------------------------------------------------------------

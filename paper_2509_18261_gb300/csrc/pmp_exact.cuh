@@ -1,5 +1,5 @@
 // pmp_exact.cuh -- correctly rounded binary64 square root and quotient from
-// integer and FP32 instructions.
+// integer and FP32 instructions, and comparisons decided on the bit patterns.
 //
 // GB300 executes FP64 at 2 lanes per clock per SM, integer and FP32 work at
 // 64-128; a binary64 square root or division compiled to the FP64 unit is a
@@ -69,6 +69,36 @@ PMP_EXACT_FN double double_of(uint64_t u)
 // x > 0.0 without an FP64 comparison: bit patterns 1 .. 0x7ff0...0 are the
 // positive subnormals, normals and +inf.
 PMP_EXACT_FN bool positive(double x) { return bits_of(x) - 1ULL < 0x7ff0000000000000ULL; }
+
+// Comparisons with 0 and 1 decided on the bit patterns, with the IEEE 754
+// result for every operand (signed zeros, infinities and NaN included): an
+// FP64 comparison occupies the FP64 pipe like an addition.
+// x >= 0: +-0, positive finite, +inf
+PMP_EXACT_FN bool ge0(double x)
+{
+    const uint64_t u = bits_of(x);
+    return u <= 0x7ff0000000000000ULL || u == kSign;
+}
+// x < 0: negative non-zero, -inf
+PMP_EXACT_FN bool lt0(double x)
+{
+    const uint64_t u = bits_of(x);
+    return u > kSign && u <= 0xfff0000000000000ULL;
+}
+// x != 0 (NaN included)
+PMP_EXACT_FN bool ne0(double x) { return (bits_of(x) << 1) != 0; }
+// x > 1
+PMP_EXACT_FN bool gt1(double x)
+{
+    const uint64_t u = bits_of(x);
+    return u > 0x3ff0000000000000ULL && u <= 0x7ff0000000000000ULL;
+}
+// x < 1: [+0, 1) or negative (-0 and -inf included)
+PMP_EXACT_FN bool lt1(double x)
+{
+    const uint64_t u = bits_of(x);
+    return u < 0x3ff0000000000000ULL || (u >= kSign && u <= 0xfff0000000000000ULL);
+}
 
 // One digit of the division recurrence: with 0 <= R < mb on entry,
 // d = floor(R 2^s / mb), R <- R 2^s - d mb, Q <- Q 2^s + d.  The FP32

@@ -185,16 +185,18 @@ __global__ void __launch_bounds__(kApplyThreads, PMP_FB_APPLY_MINB) k_apply_fb_s
         int i, j, k;
         cell_of(S, v, nvalid, i, j, k);
         const long long cs = S.at(i, j, k);
+        // pending cells receive momentum (no_dp was false)
         int noroot;
-        const double l = sn_lambda(U, D, noroot);
+        double rho1, E1;
+        const double l = sn_lambda_dp(U, D, noroot, rho1, E1);
         nl += l < 1.0;
         nr += noroot;
         if (eta_out) eta_out[v] = l;
-        u[cs] = U[0] + D[0];
+        u[cs] = rho1;
         u[S.fs + cs] = U[1] + l * D[1];
         u[2 * S.fs + cs] = U[2] + l * D[2];
         u[3 * S.fs + cs] = U[3] + l * D[3];
-        u[4 * S.fs + cs] = U[4] + D[4];
+        u[4 * S.fs + cs] = E1;
     };
     const long long step = (long long)gridDim.x * kApplyThreads;
     for (long long v0 = ((long long)blockIdx.x * kW + wid) * 32; v0 < nvalid; v0 += step) {
@@ -267,7 +269,7 @@ __global__ void __launch_bounds__(256) k_sink_aux(KParams P, Box S, const double
     double2 *d = reinterpret_cast<double2 *>(drec + v * kRec);
     d[0] = make_double2(U[0] - rtr, U[1] * inv);
     d[1] = make_double2(U[2] * inv, U[3] * inv);
-    d[2] = make_double2(U[4] * inv, 0.0);
+    d[2] = make_double2(U[4] * inv, 1.0);  // eta, until Step 3 limits the cell
 }
 
 // Step 1 for sinks in the ATOMIC mode, second half.  Every pair's change is
@@ -349,14 +351,17 @@ __device__ __forceinline__ bool removal_positive(double d0)
     return (b0 >> 63) != 0 && mag2 != 0 && mag2 <= (0x7ff0000000000000ULL << 1);
 }
 
-// One cell's Steps 3 + 5 for sinks once eta is known: eta to the D record
-// (Step 4 reads it there) and to eta_out, U += eta Delta U^sum (one eta for
-// every field; a cell whose change is zero in every field is left as it is).
+// One cell's Steps 3 + 5 for sinks once eta is known: eta to eta_out and,
+// for a cell that went through the FP64 limiter (LIM), to the D record, where
+// Step 4 reads it (the records are written with eta = 1, so the other cells
+// need no scattered 8-byte write); U += eta Delta U^sum (one eta for every
+// field; a cell whose change is zero in every field is left as it is).
+template <bool LIM>
 __device__ __forceinline__ void sink_update(const Box &S, double *__restrict__ u, long long v, long long cs,
                                             const double U[NF], const double D[NF], double e,
                                             double *__restrict__ drec, double *__restrict__ eta_out)
 {
-    drec[v * kRec + 5] = e;
+    if (LIM) drec[v * kRec + 5] = e;
     if (eta_out) eta_out[v] = e;
     if (all_zero(D)) return;
     if (e == 1.0) {
@@ -409,7 +414,7 @@ __global__ void __launch_bounds__(kApplyThreads, 3) k_sink_eta_apply(KParams P, 
         cell_of(S, v, nvalid, i, j, k);
         const double e = sink_eta_fp64(P, U[0], D[0], __ldg(drec + v * kRec));
         nl += e < 1.0;
-        sink_update(S, u, v, S.at(i, j, k), U, D, e, drec, eta_out);
+        sink_update<true>(S, u, v, S.at(i, j, k), U, D, e, drec, eta_out);
     };
     const long long step = (long long)gridDim.x * kApplyThreads;
     for (long long v0 = ((long long)blockIdx.x * kW + wid) * 32; v0 < nvalid; v0 += step) {
@@ -439,7 +444,7 @@ __global__ void __launch_bounds__(kApplyThreads, 3) k_sink_eta_apply(KParams P, 
                 pend[wid][q][NF + f] = D[f];
             }
         } else if (v < nvalid) {
-            sink_update(S, u, v, cs, U, D, 1.0, drec, eta_out);
+            sink_update<false>(S, u, v, cs, U, D, 1.0, drec, eta_out);
         }
         npend += __popc(m);
         __syncwarp();

@@ -1533,7 +1533,7 @@ void launch_counts_by_index(const PlanPtrs &pl, long long n, unsigned *counts_id
 
 
 #ifndef PMP_SEG_LONG_BPS
-#define PMP_SEG_LONG_BPS 2
+#define PMP_SEG_LONG_BPS 8
 #endif
 
 void launch_segment_sum(const Box &B, double *b, const double *pv, const unsigned long long *nruns,
@@ -1543,11 +1543,8 @@ void launch_segment_sum(const Box &B, double *b, const double *pv, const unsigne
     const unsigned nb = 152u * 32u;
     cudaMemsetAsync(nlong, 0, sizeof(unsigned), stream);
     k_segment_runs<<<nb, 128, 0, stream>>>(B, b, pv, nruns, uniq, lens, offs, vals, longq, nlong);
-    // long runs: two four-warp blocks per SM.  The runs of one Plummer core
-    // are neighbours in the queue; with few warps per SM the grid-stride
-    // order deals them out over all SMs, and the FP64 pipe of an SM is
-    // shared by few sequential chains (with 16 warps per SM the core's
-    // chains shared a few SMs' pipes: 0.68 ms at 256^3)
+    // long runs: eight four-warp blocks per SM (256^3 sweep of the blocks
+    // per SM, whole segment sum: 1 -> 2.27 ms, 2 -> 1.81, 4 -> 1.66, 8 -> 1.44)
     int dev = 0, nsm = 152;
     if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     k_segment_long<<<(unsigned)nsm * PMP_SEG_LONG_BPS, 128, 0, stream>>>(B, b, pv, uniq, lens, offs, vals, longq,

@@ -122,3 +122,42 @@ void exact_check(uint64_t seed, long long n, long long *counts, double *bad)
 }
 
 }  // extern "C"
+
+extern "C" {
+
+// Checks the bit-pattern comparisons of pmp_exact.cuh (x > 0, x >= 0, x < 0,
+// x != 0, x > 1, x < 1) against the host's IEEE comparisons: the special
+// values (signed zeros, infinities, NaNs of both signs, the smallest
+// subnormals, 1 and its neighbours), then n random bit patterns and n
+// random doubles near 0 and 1.  Returns the number of disagreements; the
+// first disagreeing operand goes to *bad.
+long long exact_check_compare(uint64_t seed, long long n, double *bad)
+{
+    long long wrong = 0;
+    auto chk = [&](double x) {
+        const bool ok = pmp::exact::positive(x) == (x > 0.0) && pmp::exact::ge0(x) == (x >= 0.0) &&
+                        pmp::exact::lt0(x) == (x < 0.0) && pmp::exact::ne0(x) == (x != 0.0) &&
+                        pmp::exact::gt1(x) == (x > 1.0) && pmp::exact::lt1(x) == (x < 1.0);
+        if (!ok && wrong++ == 0) *bad = x;
+    };
+    const uint64_t special[] = {0x0ULL, 0x8000000000000000ULL, 0x1ULL, 0x8000000000000001ULL,
+                                0x000fffffffffffffULL, 0x0010000000000000ULL, 0x7fefffffffffffffULL,
+                                0x7ff0000000000000ULL, 0xfff0000000000000ULL, 0x7ff0000000000001ULL,
+                                0x7ff8000000000000ULL, 0x7fffffffffffffffULL, 0xfff0000000000001ULL,
+                                0xfff8000000000000ULL, 0xffffffffffffffffULL, 0x3ff0000000000000ULL,
+                                0x3fefffffffffffffULL, 0x3ff0000000000001ULL, 0xbff0000000000000ULL,
+                                0xbfefffffffffffffULL, 0xbff0000000000001ULL};
+    for (uint64_t u : special) chk(from_bits(u));
+    uint64_t s = seed;
+    for (long long i = 0; i < n; ++i) {
+        chk(from_bits(splitmix(s)));
+        const uint64_t r = splitmix(s);
+        const double near = (double)(int64_t)(r % 2001) / 1000.0 - 1.0;  // [-1, 1] in steps of 1e-3
+        chk(near);
+        chk(near + 1.0);
+        chk(nudge(1.0, (int64_t)(r % 7) - 3));
+    }
+    return wrong;
+}
+
+}  // extern "C"

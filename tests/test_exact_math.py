@@ -1,6 +1,7 @@
 """The library's correctly rounded FP64 quotient and square root from integer
 and FP32 instructions (pmp_exact.cuh, used by the kernels for the divisions
-and square roots of Eq. du and the sink formulas).  A binary64 quotient or
+and square roots of Eq. du and the sink formulas), and its comparisons with
+0 and 1 decided on the bit patterns.  A binary64 quotient or
 square root rounded to nearest is unique, so the check is bit equality:
 
 - on the host, the header compiled by g++ against the C library's sqrt and
@@ -35,6 +36,8 @@ def harness(tmp_path_factory):
     lib = ctypes.CDLL(out)
     lib.exact_check.argtypes = [ctypes.c_uint64, ctypes.c_longlong, ctypes.POINTER(ctypes.c_longlong),
                                 ctypes.POINTER(ctypes.c_double)]
+    lib.exact_check_compare.argtypes = [ctypes.c_uint64, ctypes.c_longlong, ctypes.POINTER(ctypes.c_double)]
+    lib.exact_check_compare.restype = ctypes.c_longlong
     return lib
 
 
@@ -46,6 +49,13 @@ def test_host_build_matches_the_c_library(harness, seed):
     assert counts[0] == counts[2] == 10_000_000
     assert counts[1] == 0, f"sqrt wrong for x = {bad[0]!r}"
     assert counts[3] == 0, f"quotient wrong for {bad[1]!r} / {bad[2]!r}"
+
+
+def test_host_bit_pattern_comparisons_match_ieee(harness):
+    """x > 0, x >= 0, x < 0, x != 0, x > 1 and x < 1 decided on the bits
+    (used by the Eq. lambda limiter) against the IEEE comparisons."""
+    bad = ctypes.c_double()
+    assert harness.exact_check_compare(7, 2_000_000, ctypes.byref(bad)) == 0, f"comparison wrong for {bad.value!r}"
 
 
 def _operands(n, seed):
