@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--mode", default="atomic", choices=["atomic", "sorted"])
     ap.add_argument("--e2e-steps", type=int, default=None, help="end-to-end steps (default: --steps)")
+    ap.add_argument("--copy-streams", type=int, default=4,
+                    help="copy streams per direction in the pipelined end-to-end leg")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--cpu-sample-n", type=int, default=128)
@@ -616,9 +618,10 @@ def end_to_end(args, w, world, state, fb, sk, P_fb, P_sk, cycle, stream):
     step copies its inputs (gas state, both particle sets) to the device, runs
     the two passes and copies the results (gas state, sink masses and
     momenta) back.  Pipelined over three device input sets: the copies of
-    step k+1 (in) and k-1 (out) run on two copy streams while step k computes,
-    each copy ordered after the work it depends on by events.  Also reported:
-    the same steps run one after another on one stream (serial_ms_per_step)."""
+    step k+1 (in) and k-1 (out) run while step k computes, each direction
+    split over --copy-streams copy streams, each copy ordered after the work
+    it depends on by events.  Also reported: the same steps run one after another on one
+    stream (serial_ms_per_step)."""
     import torch
 
     from paper_2509_18261_gb300 import pmp
@@ -668,10 +671,10 @@ def end_to_end(args, w, world, state, fb, sk, P_fb, P_sk, cycle, stream):
     serial_ms = max_over_ranks(world, e0.elapsed_time(e1) / steps)
 
     # pipelined over NSETS device input sets, each with its own passes: the
-    # copy of step k+1's inputs (in) and of step k-1's results (out) run on
-    # two copy streams while step k computes; with three sets an in-copy
-    # never waits for the out-copy of the same set (two sets chain the two
-    # copies of every step one after the other)
+    # copy of step k+1's inputs (in) and of step k-1's results (out) run
+    # while step k computes; with three sets an in-copy never waits for the
+    # out-copy of the same set (two sets chain the two copies of every step
+    # one after the other)
     mode = args.mode
     sets = [(state, fb, sk, ((P_fb, fb), (P_sk, sk)))]
     extra = []
@@ -683,38 +686,74 @@ def end_to_end(args, w, world, state, fb, sk, P_fb, P_sk, cycle, stream):
         Q_sk = pmp.Pass(w["sink_params"], P_sk.box, st1, sk1, mode=mode)
         extra += [Q_fb, Q_sk]
         sets.append((st1, fb1, sk1, ((Q_fb, fb1), (Q_sk, sk1))))
-    s_in, s_out = torch.cuda.Stream(), torch.cuda.Stream()
-    ev_in = [torch.cuda.Event() for _ in range(NSETS)]
-    ev_done = [torch.cuda.Event() for _ in range(NSETS)]
-    ev_out = [torch.cuda.Event() for _ in range(NSETS)]
-    out_used = [False] * NSETS
+    # each direction's copies are split over NCOPY streams (a single copy
+    # moves at the rate of one copy engine)
+    NCOPY = max(1, args.copy_streams)
+    s_in = [torch.cuda.Stream() for _ in range(NCOPY)]
+    s_out = [torch.cuda.Stream() for _ in range(NCOPY)]
+
+    def pieces(t):
+        flat = t.view(-1)
+        n = flat.numel()
+        step = (n + NCOPY - 1) // NCOPY
+        return [flat[i * step:min(n, (i + 1) * step)] for i in range(NCOPY)]
+
+    h_pieces = pieces(h_state)
+    o_pieces = [pieces(o["state"]) for o in outs]
+    d_pieces = [pieces(st_[0]) for st_ in sets]
+
+    def copy_in_split(j, after):
+        evs = []
+        for i, s_ in enumerate(s_in):
+            with torch.cuda.stream(s_):
+                for e in after:
+                    s_.wait_event(e)
+                d_pieces[j][i].copy_(h_pieces[i], non_blocking=True)
+                if i == 0:
+                    for k in h_fb:
+                        sets[j][1][k].copy_(h_fb[k], non_blocking=True)
+                    for k in h_sk:
+                        sets[j][2][k].copy_(h_sk[k], non_blocking=True)
+                ev = torch.cuda.Event()
+                ev.record(s_)
+                evs.append(ev)
+        return evs
+
+    def copy_out_split(i_, after):
+        evs = []
+        for i, s_ in enumerate(s_out):
+            with torch.cuda.stream(s_):
+                s_.wait_event(after)
+                o_pieces[i_][i].copy_(d_pieces[i_][i], non_blocking=True)
+                if i == 0:
+                    for k in outs[i_]["sk"]:
+                        outs[i_]["sk"][k].copy_(sets[i_][2][k], non_blocking=True)
+                ev = torch.cuda.Event()
+                ev.record(s_)
+                evs.append(ev)
+        return evs
+
+    ev_in = [[] for _ in range(NSETS)]
+    ev_out = [[] for _ in range(NSETS)]
     barrier(world)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    s_in.wait_event(e0)
-    with torch.cuda.stream(s_in):
-        copy_in(*sets[0][:3])
-        ev_in[0].record(s_in)
+    ev_in[0] = copy_in_split(0, [e0])
     for k in range(steps):
         i, j = k % NSETS, (k + 1) % NSETS
         if k + 1 < steps:
-            with torch.cuda.stream(s_in):
-                if out_used[j]:
-                    s_in.wait_event(ev_out[j])  # set j's results have left the device
-                copy_in(*sets[j][:3])
-                ev_in[j].record(s_in)
-        stream.wait_event(ev_in[i])
+            # set j's results of an earlier step have left the device
+            ev_in[j] = copy_in_split(j, ev_out[j])
+        for e in ev_in[i]:
+            stream.wait_event(e)
         run_passes(sets[i][3])
-        ev_done[i].record(stream)
-        with torch.cuda.stream(s_out):
-            s_out.wait_event(ev_done[i])
-            copy_out(outs[i], sets[i][0], sets[i][2])
-            ev_out[i].record(s_out)
-        out_used[i] = True
+        done = torch.cuda.Event()
+        done.record(stream)
+        ev_out[i] = copy_out_split(i, done)
     for i in range(NSETS):
-        if out_used[i]:
-            stream.wait_event(ev_out[i])
+        for e in ev_out[i]:
+            stream.wait_event(e)
     e1.record(stream)
     torch.cuda.synchronize()
     ms = max_over_ranks(world, e0.elapsed_time(e1) / steps)
@@ -727,8 +766,8 @@ def end_to_end(args, w, world, state, fb, sk, P_fb, P_sk, cycle, stream):
     return {"value": n_particles * world / (ms * 1e-3), "unit": "particles/s", "ms_per_step": ms,
             "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo, "steps": steps,
             "serial_ms_per_step": serial_ms,
-            "overlap": "three device input sets: the copies of step k+1 (in) and k-1 (out) run on two copy streams "
-                       "during step k"}
+            "overlap": f"three device input sets: the copies of step k+1 (in) and k-1 (out) run during step k, each "
+                       f"direction split over {NCOPY} copy streams"}
 
 
 def touched_cells(P_fb, params, box, state0, fb):

@@ -209,7 +209,7 @@ __device__ __forceinline__ double sink_cs2(const KParams &P, const double U[NF],
 {
     const double ke2 = (U[1] * U[1] + U[2] * U[2]) + U[3] * U[3];
     double eint = U[4] - ke2 * (0.5 * inv);
-    if (eint < 0.0) eint = 0.0;
+    if (exact::lt0(eint)) eint = 0.0;  // eint < 0, decided on the bits
     return (P.gg * eint) * inv;
 }
 

@@ -386,7 +386,10 @@ constexpr int kSinkPend = 64;  // cells a warp holds back for its FP64 limiter b
 // takes it.  Every decision is the FP64 one.  Step 4 reads only the records,
 // the particles and the plan, never the state, so it can follow this pass.
 // Limited cells are counted per block.
-__global__ void __launch_bounds__(kApplyThreads, 3) k_sink_eta_apply(KParams P, Box S, double *__restrict__ u, Box B,
+#ifndef PMP_SINK_APPLY_MINB
+#define PMP_SINK_APPLY_MINB 3
+#endif
+__global__ void __launch_bounds__(kApplyThreads, PMP_SINK_APPLY_MINB) k_sink_eta_apply(KParams P, Box S, double *__restrict__ u, Box B,
                                                                      const double *__restrict__ b,
                                                                      double *__restrict__ drec,
                                                                      double *__restrict__ eta_out, DevStatus *st)

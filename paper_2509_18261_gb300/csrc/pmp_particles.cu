@@ -353,8 +353,19 @@ __global__ void __launch_bounds__(256) k_plan(KParams P, Box S, Parts p, const u
 // Covered fractions omega = k / S^3 for k = 0..S^3, computed once per block.
 constexpr int kMaxS3 = kMaxS * kMaxS * kMaxS;
 
-// Pairs whose loads a per-particle loop issues together.
-constexpr int kUnroll = 4;
+// Pairs whose loads a per-particle gather loop issues together (512^3
+// sweeps: supernova plan + gather 1 -> 24.0 ms, 2 -> 24.2, 3 -> 25.1, 4 ->
+// 25.0, 8 -> 27.7: the fused kernel is bound by instruction issue and fetch,
+// not by its loads; sink plan + gather + deposit 2 -> 24.0 ms, 4 -> 23.1-23.4,
+// 8 -> 23.1).
+#ifndef PMP_GATHER_UNROLL_FB
+#define PMP_GATHER_UNROLL_FB 1
+#endif
+#ifndef PMP_GATHER_UNROLL_SINK
+#define PMP_GATHER_UNROLL_SINK 4
+#endif
+constexpr int kUnrollFb = PMP_GATHER_UNROLL_FB;
+constexpr int kUnroll = PMP_GATHER_UNROLL_SINK;
 
 // Block size of the thread-per-sink kernels (gather, Step 4).  Step 4 keeps
 // each sink's 3(2R+1) Gaussian factors in a shared-memory column (the gather
@@ -417,18 +428,18 @@ __device__ __forceinline__ void gather_fb_particle(const KParams &P, const Box &
     unsigned isw = 0;
     const unsigned long long b0 = (unsigned long long)t * pl.cap;
     const unsigned nc = pl.counts[t];
-    // the cells' loads are issued kUnroll at a time, the sums stay in kernel order
+    // the cells' loads are issued kUnrollFb at a time, the sums stay in kernel order
     unsigned q = 0;
-    for (; q + kUnroll <= nc; q += kUnroll) {
-        PairCell c[kUnroll];
-        double U[kUnroll][NF];
+    for (; q + kUnrollFb <= nc; q += kUnrollFb) {
+        PairCell c[kUnrollFb];
+        double U[kUnrollFb][NF];
 #pragma unroll
-        for (int k = 0; k < kUnroll; ++k) c[k] = unpack_pair(slot_load<NC>(pl.slots + b0 + q + k), P.R);
+        for (int k = 0; k < kUnrollFb; ++k) c[k] = unpack_pair(slot_load<NC>(pl.slots + b0 + q + k), P.R);
 #pragma unroll
-        for (int k = 0; k < kUnroll; ++k)
+        for (int k = 0; k < kUnrollFb; ++k)
             load_cell(u, S, S.at(owner(c[k].i, S.n0), owner(c[k].j, S.n1), owner(c[k].k, S.n2)), U[k]);
 #pragma unroll
-        for (int k = 0; k < kUnroll; ++k) fb_gather_add<IW>(wtab, c[k].cnt, U[k], sw, isw, sr, sp0, sp1, sp2);
+        for (int k = 0; k < kUnrollFb; ++k) fb_gather_add<IW>(wtab, c[k].cnt, U[k], sw, isw, sr, sp0, sp1, sp2);
     }
     for (; q < nc; ++q) {
         const PairCell c = unpack_pair(slot_load<NC>(pl.slots + b0 + q), P.R);
@@ -573,23 +584,63 @@ __global__ void __launch_bounds__(128) k_gather_mass(KParams P, Box S, Parts p, 
 
 // Sink gather.  Writes the particle's per-axis Gaussian factors
 // exp(-d^2 / r_acc^2) to wts[s][3][W] for the deposit and Step 4.
-template <int R, bool NC = true>
-__device__ __forceinline__ void gather_sink_particle(const KParams &P, const Box &S, const double *__restrict__ u,
-                                                     const Parts &p, const PlanPtrs &pl, double *__restrict__ G,
-                                                     DevStatus *st, long long t)
+// The rest of one sink's gather once the sums over its kernel cells (in
+// kernel order) are known: Sec. 3.1.1's ambient quantities, the per-axis
+// Gaussian factors, sum w and the gathered rows (row stride gs).
+template <int R>
+__device__ __forceinline__ void gather_sink_finish(const KParams &P, const PlanPtrs &pl, double *__restrict__ G,
+                                                   long long gs, DevStatus *st, long long t, long long s, double x,
+                                                   double y, double z, double ms, double ps0, double ps1,
+                                                   double ps2, unsigned nc, double srho, double sp0, double sp1,
+                                                   double sp2, double src)
 {
     constexpr int W = 2 * R + 1;
-    const long long s = pl.perm ? (long long)pl.perm[t] : t;
-    const long long gs = p.count;
-    const double x = p.x[s], y = p.y[s], z = p.z[s];
-    const double ms = p.m[s], ps0 = p.px[s], ps1 = p.py[s], ps2 = p.pz[s];
+    const unsigned long long b0 = (unsigned long long)t * pl.cap;
+    const int nk = (int)nc;
+    const SinkAmbient am = sink_ambient(P, srho, sp0, sp1, sp2, src, nk, ms, ps0, ps1, ps2);
+    const double ra2 = am.ra2;
+    const int hx = (int)floor(x), hy = (int)floor(y), hz = (int)floor(z);
+    double *ws = pl.wts + s * (3 * W);
+#pragma unroll
+    for (int o = 0; o < W; ++o) {
+        ws[o] = sink_axis_weight(((double)(hx + o - R) + 0.5) - x, ra2);
+        ws[W + o] = sink_axis_weight(((double)(hy + o - R) + 0.5) - y, ra2);
+        ws[2 * W + o] = sink_axis_weight(((double)(hz + o - R) + 0.5) - z, ra2);
+    }
+    double sumw = 0.0;
+    for (unsigned q = 0; q < nc; ++q) {
+        const PairCell c = unpack_pair(pl.slots[b0 + q], P.R);
+        sumw = fma(ws[c.i - hx + R] * ws[W + c.j - hy + R], ws[2 * W + c.k - hz + R], sumw);
+    }
+    if (!sink_gather_rows(P, am, sumw, nk, G + s, gs)) report(st, PMP_ERR_NONFINITE, s);
+}
+
+// The validity test of a sink before its gather: false (rows zeroed, the
+// error reported) for a position outside the box or a mass that is not
+// positive.
+__device__ __forceinline__ bool sink_gather_ok(const Box &S, double x, double y, double z, double ms,
+                                               double *__restrict__ G, long long gs, long long s, DevStatus *st)
+{
     int bad = position_status(S, x, y, z);
     if (!bad && !(ms > 0.0)) bad = PMP_ERR_NONFINITE;
     if (bad) {
         report(st, bad, s);
         for (int r = 0; r < SK_ROWS; ++r) G[r * gs + s] = 0.0;
-        return;
+        return false;
     }
+    return true;
+}
+
+template <int R, bool NC = true>
+__device__ __forceinline__ void gather_sink_particle(const KParams &P, const Box &S, const double *__restrict__ u,
+                                                     const Parts &p, const PlanPtrs &pl, double *__restrict__ G,
+                                                     DevStatus *st, long long t)
+{
+    const long long s = pl.perm ? (long long)pl.perm[t] : t;
+    const long long gs = p.count;
+    const double x = p.x[s], y = p.y[s], z = p.z[s];
+    const double ms = p.m[s], ps0 = p.px[s], ps1 = p.py[s], ps2 = p.pz[s];
+    if (!sink_gather_ok(S, x, y, z, ms, G, gs, s, st)) return;
     const unsigned long long b0 = (unsigned long long)t * pl.cap;
     const unsigned nc = pl.counts[t];
     double srho = 0.0, sp0 = 0.0, sp1 = 0.0, sp2 = 0.0, src = 0.0;
@@ -625,23 +676,7 @@ __device__ __forceinline__ void gather_sink_particle(const KParams &P, const Box
         sp2 = sp2 + g1.y;
         src = src + g2.x;
     }
-    const int nk = (int)nc;
-    const SinkAmbient am = sink_ambient(P, srho, sp0, sp1, sp2, src, nk, ms, ps0, ps1, ps2);
-    const double ra2 = am.ra2;
-    const int hx = (int)floor(x), hy = (int)floor(y), hz = (int)floor(z);
-    double *ws = pl.wts + s * (3 * W);
-#pragma unroll
-    for (int o = 0; o < W; ++o) {
-        ws[o] = sink_axis_weight(((double)(hx + o - R) + 0.5) - x, ra2);
-        ws[W + o] = sink_axis_weight(((double)(hy + o - R) + 0.5) - y, ra2);
-        ws[2 * W + o] = sink_axis_weight(((double)(hz + o - R) + 0.5) - z, ra2);
-    }
-    double sumw = 0.0;
-    for (unsigned q = 0; q < nc; ++q) {
-        const PairCell c = unpack_pair(pl.slots[b0 + q], P.R);
-        sumw = fma(ws[c.i - hx + R] * ws[W + c.j - hy + R], ws[2 * W + c.k - hz + R], sumw);
-    }
-    if (!sink_gather_rows(P, am, sumw, nk, G + s, gs)) report(st, PMP_ERR_NONFINITE, s);
+    gather_sink_finish<R>(P, pl, G, gs, st, t, s, x, y, z, ms, ps0, ps1, ps2, nc, srho, sp0, sp1, sp2, src);
 }
 
 // Grid-stride over the processing order: the sinks in flight at a time are a
@@ -744,7 +779,10 @@ __global__ void __launch_bounds__(128, PMP_SINK_PASS1_MINB) k_pass1_sink(KParams
             }
         }
         __syncwarp();
-        // 2. gather, lane per sink
+        // 2. gather, lane per sink (a lane's loop keeps the loads of four
+        // cells' records in flight; staging the records of six sinks at a time
+        // in shared memory, with lanes over (sink, field) for the sums, left
+        // fewer loads in flight and was slower: 23.1 -> 35.5 ms at 512^3)
         if (tl < p.count) gather_sink_particle<R, false>(P, S, u, p, pl, G, st, tl);
         __syncwarp();
         // 3. deposit of -a into the scratch, 8 sinks at a time

@@ -27,6 +27,15 @@ def test_alu_roofline_of_the_supernova_kernels():
         assert r["kernel"] == kernel and r["ms_per_launch"] == 24.2
 
 
+def test_alu_roofline_of_the_fused_sink_kernel():
+    # Sec. 3.1.1 gather sums and weights (8) plus the accretion deposit (7) per pair
+    box = _box()
+    pairs = {"fb": 491_934_207, "sink": 562_210_341}
+    r = bench.roofline("sink_gather_deposit", 23.3, pairs, box, 14_680_064, 2_097_152, 6793.4, "measured")
+    assert r["bound"] == "alu" and r["unit"] == "TFLOP/s"
+    assert r["achieved"] == pytest.approx(15 * pairs["sink"] / 23.3e-3 / 1e12, rel=1e-12)
+
+
 def test_algorithmic_bytes_of_the_supernova_kernels():
     n, pairs, ts, tb = 1000, 33_000, 20_000, 21_000
     assert bench.alg_bytes_fb("plan_gather", n, pairs, ts, tb) == 160 * n + 8 * pairs + 40 * ts
