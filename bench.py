@@ -280,7 +280,9 @@ def profiled_row(kernel):
     for line in txt.splitlines():
         cols = [c.strip() for c in line.strip().strip("|").split("|")]
         if len(cols) == 13 and cols[1] == kernel:
-            return {"fp64_per_unit": float(cols[11]), "bytes_per_unit": float(cols[12])}
+            return {"fp64_per_unit": float(cols[11]), "bytes_per_unit": float(cols[12]),
+                    "dram_pct": float(cols[5]), "fp64_pipe_pct": float(cols[6]), "issue_pct": float(cols[7]),
+                    "warps_active_pct": float(cols[8])}
     return None
 
 
@@ -544,6 +546,10 @@ def run_ours(args, world, rank, local):
             r["peak_measured_source"] = "FP64 DFMA probe on this GPU, same run (pmp_probe_fp64)"
             row = profiled_row(name)
             kind = name.split("_", 1)[0]
+            if row:
+                # what binds it: the one-kernel counters of the 192^3 capture
+                r["counters_192"] = {k: row[k] for k in ("issue_pct", "fp64_pipe_pct", "dram_pct",
+                                                         "warps_active_pct")}
             if row and pairs.get(kind):
                 # issued FP64 lane-operations (ncu, 192^3) over the FP64 issue peak (a DFMA = 2 flops)
                 rate = row["fp64_per_unit"] * pairs[kind] / (kernel_ms[name][1] * 1e-3) / 1e12

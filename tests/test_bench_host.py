@@ -67,6 +67,22 @@ def test_traffic_is_reported_only_for_the_profiled_sources(monkeypatch):
     assert 20.0 < a / 1000 < 400.0  # bytes per pair of the 192^3 capture
 
 
+def test_profiled_row_reads_the_binding_counters(monkeypatch):
+    import re
+
+    txt = open(bench.os.path.join(bench.ROOT, "profiles", "counters_c5_192.md")).read()
+    monkeypatch.setattr(bench, "src_digest", lambda: re.search(r"csrc_sha:\s*([0-9a-f]+)", txt).group(1))
+    rows = [[c.strip() for c in line.strip().strip("|").split("|")] for line in txt.splitlines()]
+    names = [r[1] for r in rows if len(r) == 13 and r[1] != "bench name" and not r[1].startswith("---")]
+    assert "fb_plan_gather" in names and "fb_deposit" in names
+    for name in names:
+        row = bench.profiled_row(name)
+        assert row is not None
+        for k in ("issue_pct", "fp64_pipe_pct", "dram_pct", "warps_active_pct"):
+            assert 0.0 < row[k] <= 100.0
+        assert row["fp64_per_unit"] >= 0.0 and row["bytes_per_unit"] > 0.0
+
+
 def test_cell_pass_hbm_rates():
     box = _box()
     km = {"fb_apply": (1.0, 5.2), "sink_apply": (1.0, 7.2), "fb_zero": (1.0, 0.86)}
