@@ -100,6 +100,22 @@ PMP_EXACT_FN bool lt1(double x)
     return u < 0x3ff0000000000000ULL || (u >= kSign && u <= 0xfff0000000000000ULL);
 }
 
+// m / 2 for an odd integer m (|m| < 2^31), i.e. the double (m - 1) / 2 + 0.5
+// that a cell centre c + 1/2 is, built from its bits without an FP64
+// conversion or addition (exact: the value has at most 32 significant bits).
+PMP_EXACT_FN double half_odd(int m)
+{
+    const uint32_t a = m < 0 ? (uint32_t)(-(int64_t)m) : (uint32_t)m;  // odd, >= 1
+#if defined(__CUDA_ARCH__)
+    const int e = 31 - __clz(a);
+#else
+    const int e = 31 - __builtin_clz(a);
+#endif
+    // a = 1.f 2^e, so m / 2 = 1.f 2^(e - 1): biased exponent 1022 + e
+    const uint64_t mant = ((uint64_t)a << (52 - e)) & kMant;
+    return double_of((m < 0 ? kSign : 0) | ((uint64_t)(1022 + e) << 52) | mant);
+}
+
 // One digit of the division recurrence: with 0 <= R < mb on entry,
 // d = floor(R 2^s / mb), R <- R 2^s - d mb, Q <- Q 2^s + d.  The FP32
 // estimate R 2^s / mb (R and mb truncated to 32 bits, rb = RN(1 / (mb >> 21)))

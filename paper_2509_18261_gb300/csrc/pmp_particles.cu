@@ -926,7 +926,8 @@ __global__ void __launch_bounds__(256, PMP_DEPOSIT_MINB) k_deposit_atomic(KParam
                         unpack_host(hp, hx, hy, hz);
                         const int h = a == 0 ? hx : (a == 1 ? hy : hz);
                         const double xa = a == 0 ? __ldg(p.x + sj) : (a == 1 ? __ldg(p.y + sj) : __ldg(p.z + sj));
-                        const double d = ((double)(h + o - R) + 0.5) - xa;
+                        // (c + 1/2) - x, c + 1/2 built on the integer pipes (exact)
+                        const double d = exact::half_odd(2 * (h + o - R) + 1) - xa;
                         dt[i] = d;
                         qt[i] = d * d;
                     }

@@ -161,3 +161,19 @@ long long exact_check_compare(uint64_t seed, long long n, double *bad)
 }
 
 }  // extern "C"
+
+extern "C" {
+
+// half_odd(2c + 1) against the host's (double)c + 0.5 for every c in
+// [lo, hi]; returns the number of disagreements, the first c in *bad.
+long long exact_check_half_odd(long long lo, long long hi, long long *bad)
+{
+    long long wrong = 0;
+    for (long long c = lo; c <= hi; ++c) {
+        const double want = (double)c + 0.5;
+        if (to_bits(pmp::exact::half_odd((int)(2 * c + 1))) != to_bits(want) && wrong++ == 0) *bad = c;
+    }
+    return wrong;
+}
+
+}  // extern "C"

@@ -38,6 +38,8 @@ def harness(tmp_path_factory):
                                 ctypes.POINTER(ctypes.c_double)]
     lib.exact_check_compare.argtypes = [ctypes.c_uint64, ctypes.c_longlong, ctypes.POINTER(ctypes.c_double)]
     lib.exact_check_compare.restype = ctypes.c_longlong
+    lib.exact_check_half_odd.argtypes = [ctypes.c_longlong, ctypes.c_longlong, ctypes.POINTER(ctypes.c_longlong)]
+    lib.exact_check_half_odd.restype = ctypes.c_longlong
     return lib
 
 
@@ -56,6 +58,16 @@ def test_host_bit_pattern_comparisons_match_ieee(harness):
     (used by the Eq. lambda limiter) against the IEEE comparisons."""
     bad = ctypes.c_double()
     assert harness.exact_check_compare(7, 2_000_000, ctypes.byref(bad)) == 0, f"comparison wrong for {bad.value!r}"
+
+
+def test_host_cell_centre_from_bits_matches_the_conversion(harness):
+    """c + 1/2 built from the bits of 2c + 1 (the deposit's offset table)
+    against (double)c + 0.5, for every cell index of boxes up to 2^22 cells
+    per axis and the ends of the int range."""
+    bad = ctypes.c_longlong()
+    assert harness.exact_check_half_odd(-(1 << 22), 1 << 22, ctypes.byref(bad)) == 0, f"wrong for c = {bad.value}"
+    assert harness.exact_check_half_odd(-(1 << 30), -(1 << 30) + 1000, ctypes.byref(bad)) == 0, bad.value
+    assert harness.exact_check_half_odd((1 << 30) - 1001, (1 << 30) - 1, ctypes.byref(bad)) == 0, bad.value
 
 
 def _operands(n, seed):
