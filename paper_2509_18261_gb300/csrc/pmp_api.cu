@@ -126,7 +126,8 @@ Layout layout(const pmp_params &p, long long n, long long nvalid, int mode)
     L.fr = take(16 * n1);
     if (sink) {
         L.wts = take(8 * n1 * 3 * (size_t)W);
-        L.aux = take(8 * 2 * (size_t)pmp::kRec * (size_t)(nvalid > 0 ? nvalid : 1));
+        // G records, D records, rho - rho_Tr, eta
+        L.aux = take(8 * (size_t)(pmp::kRec + pmp::kDRec + 2) * (size_t)(nvalid > 0 ? nvalid : 1));
         // ATOMIC: each pair's removal a, stored by the fused deposit for Step 4
         if (mode == PMP_MODE_ATOMIC) L.pa = take(8 * pairs);
     } else {
@@ -181,8 +182,13 @@ pmp::PlanPtrs plan_ptrs(const Layout &L, void *ws, const pmp_params &p, int mode
     pl.fr = reinterpret_cast<float4 *>(w + L.fr);
     if (p.kind == PMP_KIND_SINK) {
         pl.wts = reinterpret_cast<double *>(w + L.wts);
-        pl.grec = reinterpret_cast<double *>(w + L.aux);
-        pl.drec = pl.grec + (size_t)pmp::kRec * (size_t)(nvalid_rows(L) > 0 ? nvalid_rows(L) : 1);
+        // D records first: at the region's 256-byte-aligned start, every
+        // 32-byte record is one sector
+        const size_t nv = (size_t)(nvalid_rows(L) > 0 ? nvalid_rows(L) : 1);
+        pl.drec = reinterpret_cast<double *>(w + L.aux);
+        pl.grec = pl.drec + (size_t)pmp::kDRec * nv;
+        pl.dtr = pl.grec + (size_t)pmp::kRec * nv;
+        pl.deta = pl.dtr + nv;
         pl.pa = mode == PMP_MODE_ATOMIC ? reinterpret_cast<double *>(w + L.pa) : nullptr;
     }
     pl.cap = (unsigned long long)L.cap;
@@ -580,7 +586,7 @@ static pmp_status gather_impl(pmp_ctx *ctx, const pmp_mesh *state, const pmp_par
     }
     if (ctx->p.kind == PMP_KIND_SINK) {
         Timed tm(ctx, "cell_records");
-        pmp::launch_sink_aux(P, S, state->data, pl.grec, pl.drec, st);
+        pmp::launch_sink_aux(P, S, state->data, pl.grec, pl.drec, pl.dtr, pl.deta, st);
     }
     if (q.count > 0) {
         if (fused) {
@@ -813,7 +819,7 @@ pmp_status pmp_apply_limited(pmp_ctx *ctx, pmp_mesh *state, const pmp_mesh *buff
         {
             // Steps 3 + 5; Step 4 reads only the records and the particles
             Timed tm(ctx, "apply");
-            pmp::launch_sink_eta_apply(P, S, state->data, B, buffer->data, pl.drec, eta_out, ctx->st, st);
+            pmp::launch_sink_eta_apply(P, S, state->data, B, buffer->data, pl.dtr, pl.deta, eta_out, ctx->st, st);
         }
         if (n > 0 && ctx->plan_has_a) {
             Timed tm(ctx, "return");

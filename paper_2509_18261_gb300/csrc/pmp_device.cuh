@@ -417,10 +417,13 @@ __device__ __forceinline__ void sink_delta(const KParams &P, const double U[NF],
     dU[4] = -(a * (U[4] * inv));
 }
 
-// Per-cell sink records (valid cells, x fastest), 6 doubles = 48 bytes each:
-//   G record (gather):          rho, p_x, p_y, p_z, rho c_s, 0
-//   D record (deposit, Step 4): rho - rho_Tr, p_x inv, p_y inv, p_z inv, E inv, 0 (inv = 1/rho)
+// Per-cell sink quantities (valid cells, x fastest), inv = 1/rho:
+//   G record (gather), 6 doubles = 48 bytes:  rho, p_x, p_y, p_z, rho c_s, 0
+//   D record (spread, Step 4), 4 doubles = 32 bytes (one sector):  p_x inv, p_y inv, p_z inv, E inv
+//   rho - rho_Tr (deposit, limiter) and eta (Step 4) in dense arrays of their own, so that a
+//   kernel that needs one of them reads 8 bytes per cell, not a record
 constexpr int kRec = 6;
+constexpr int kDRec = 4;
 
 // Gathered-row indices.
 enum { FB_MSNR = 0, FB_VSNR, FB_VX, FB_VY, FB_VZ, FB_NH, FB_RM, FB_PRAD, FB_Q, FB_E, FB_PV, FB_REGIME, FB_ROWS };

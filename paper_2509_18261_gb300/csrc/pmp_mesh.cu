@@ -247,10 +247,12 @@ __global__ void __launch_bounds__(kApplyThreads, PMP_FB_APPLY_MINB) k_apply_fb_s
 }
 
 // Per-cell sink records, each value in the order the sink formulas state it:
-// G = (rho, p, rho c_s) for the gather; D = (rho - rho_Tr (Eq. truelove),
-// p inv, E inv, 0) with inv = 1/rho for the deposit and Step 4.
+// G = (rho, p, rho c_s) for the gather; D = (p inv, E inv) with inv = 1/rho
+// for the spread and Step 4; rho - rho_Tr (Eq. truelove) for the deposit and
+// the limiter; eta = 1 until Step 3 limits the cell.
 __global__ void __launch_bounds__(256) k_sink_aux(KParams P, Box S, const double *__restrict__ u,
-                                                  double *__restrict__ grec, double *__restrict__ drec)
+                                                  double *__restrict__ grec, double *__restrict__ drec,
+                                                  double *__restrict__ dtr, double *__restrict__ deta)
 {
     const long long nvalid = (long long)S.n0 * S.n1 * S.n2;
     const long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -266,10 +268,11 @@ __global__ void __launch_bounds__(256) k_sink_aux(KParams P, Box S, const double
     g[0] = make_double2(U[0], U[1]);
     g[1] = make_double2(U[2], U[3]);
     g[2] = make_double2(U[0] * cs, 0.0);
-    double2 *d = reinterpret_cast<double2 *>(drec + v * kRec);
-    d[0] = make_double2(U[0] - rtr, U[1] * inv);
-    d[1] = make_double2(U[2] * inv, U[3] * inv);
-    d[2] = make_double2(U[4] * inv, 1.0);  // eta, until Step 3 limits the cell
+    double2 *d = reinterpret_cast<double2 *>(drec + v * kDRec);
+    d[0] = make_double2(U[1] * inv, U[2] * inv);
+    d[1] = make_double2(U[3] * inv, U[4] * inv);
+    dtr[v] = U[0] - rtr;
+    deta[v] = 1.0;
 }
 
 // Step 1 for sinks in the ATOMIC mode, second half.  Every pair's change is
@@ -296,13 +299,13 @@ __global__ void __launch_bounds__(256) k_sink_spread(Box S, Box B, double *__res
             if ((__double_as_longlong(sc) << 1) == 0) continue;  // +-0: no pair reached the cell
             const int i = ii - B.g;
             const double2 *d = reinterpret_cast<const double2 *>(
-                drec + vidx(S, owner(i, S.n0), owner(j, S.n1), owner(k, S.n2)) * kRec);
-            const double2 d0 = __ldg(d), d1 = __ldg(d + 1), d2 = __ldg(d + 2);
+                drec + vidx(S, owner(i, S.n0), owner(j, S.n1), owner(k, S.n2)) * kDRec);
+            const double2 d0 = __ldg(d), d1 = __ldg(d + 1);
             b[c] += sc;
-            b[B.fs + c] = fma(sc, d0.y, b[B.fs + c]);
-            b[2 * B.fs + c] = fma(sc, d1.x, b[2 * B.fs + c]);
-            b[3 * B.fs + c] = fma(sc, d1.y, b[3 * B.fs + c]);
-            b[4 * B.fs + c] = fma(sc, d2.x, b[4 * B.fs + c]);
+            b[B.fs + c] = fma(sc, d0.x, b[B.fs + c]);
+            b[2 * B.fs + c] = fma(sc, d0.y, b[2 * B.fs + c]);
+            b[3 * B.fs + c] = fma(sc, d1.x, b[3 * B.fs + c]);
+            b[4 * B.fs + c] = fma(sc, d1.y, b[4 * B.fs + c]);
         }
     }
 }
@@ -352,16 +355,16 @@ __device__ __forceinline__ bool removal_positive(double d0)
 }
 
 // One cell's Steps 3 + 5 for sinks once eta is known: eta to eta_out and,
-// for a cell that went through the FP64 limiter (LIM), to the D record, where
-// Step 4 reads it (the records are written with eta = 1, so the other cells
-// need no scattered 8-byte write); U += eta Delta U^sum (one eta for every
-// field; a cell whose change is zero in every field is left as it is).
+// for a cell that went through the FP64 limiter (LIM), to deta, where Step 4
+// reads it (the cell records pass writes eta = 1 for every cell, so the other
+// cells need no write here); U += eta Delta U^sum (one eta for every field; a
+// cell whose change is zero in every field is left as it is).
 template <bool LIM>
 __device__ __forceinline__ void sink_update(const Box &S, double *__restrict__ u, long long v, long long cs,
                                             const double U[NF], const double D[NF], double e,
-                                            double *__restrict__ drec, double *__restrict__ eta_out)
+                                            double *__restrict__ deta, double *__restrict__ eta_out)
 {
-    if (LIM) drec[v * kRec + 5] = e;
+    if (LIM) deta[v] = e;
     if (eta_out) eta_out[v] = e;
     if (all_zero(D)) return;
     if (e == 1.0) {
@@ -391,7 +394,8 @@ constexpr int kSinkPend = 64;  // cells a warp holds back for its FP64 limiter b
 #endif
 __global__ void __launch_bounds__(kApplyThreads, PMP_SINK_APPLY_MINB) k_sink_eta_apply(KParams P, Box S, double *__restrict__ u, Box B,
                                                                      const double *__restrict__ b,
-                                                                     double *__restrict__ drec,
+                                                                     const double *__restrict__ dtr,
+                                                                     double *__restrict__ deta,
                                                                      double *__restrict__ eta_out, DevStatus *st)
 {
     constexpr int kW = kApplyThreads / 32;
@@ -415,9 +419,9 @@ __global__ void __launch_bounds__(kApplyThreads, PMP_SINK_APPLY_MINB) k_sink_eta
         }
         int i, j, k;
         cell_of(S, v, nvalid, i, j, k);
-        const double e = sink_eta_fp64(P, U[0], D[0], __ldg(drec + v * kRec));
+        const double e = sink_eta_fp64(P, U[0], D[0], __ldg(dtr + v));
         nl += e < 1.0;
-        sink_update<true>(S, u, v, S.at(i, j, k), U, D, e, drec, eta_out);
+        sink_update<true>(S, u, v, S.at(i, j, k), U, D, e, deta, eta_out);
     };
     const long long step = (long long)gridDim.x * kApplyThreads;
     for (long long v0 = ((long long)blockIdx.x * kW + wid) * 32; v0 < nvalid; v0 += step) {
@@ -447,7 +451,7 @@ __global__ void __launch_bounds__(kApplyThreads, PMP_SINK_APPLY_MINB) k_sink_eta
                 pend[wid][q][NF + f] = D[f];
             }
         } else if (v < nvalid) {
-            sink_update<false>(S, u, v, cs, U, D, 1.0, drec, eta_out);
+            sink_update<false>(S, u, v, cs, U, D, 1.0, deta, eta_out);
         }
         npend += __popc(m);
         __syncwarp();
@@ -673,11 +677,11 @@ void launch_fold(const Box &B, double *b, cudaStream_t stream)
     k_fold<<<(unsigned)((threads + 255) / 256), 256, 0, stream>>>(B, b);
 }
 
-void launch_sink_aux(const KParams &P, const Box &S, const double *u, double *grec, double *drec,
-                     cudaStream_t stream)
+void launch_sink_aux(const KParams &P, const Box &S, const double *u, double *grec, double *drec, double *dtr,
+                     double *deta, cudaStream_t stream)
 {
     const long long nvalid = (long long)S.n0 * S.n1 * S.n2;
-    k_sink_aux<<<(unsigned)((nvalid + 255) / 256), 256, 0, stream>>>(P, S, u, grec, drec);
+    k_sink_aux<<<(unsigned)((nvalid + 255) / 256), 256, 0, stream>>>(P, S, u, grec, drec, dtr, deta);
 }
 
 void launch_sink_spread(const Box &S, const Box &B, double *b, const double *scr, const double *drec,
@@ -704,13 +708,13 @@ static unsigned resident_grid(K kernel, int threads, long long need)
     return (unsigned)(g > 0 ? g : 1);
 }
 
-void launch_sink_eta_apply(const KParams &P, const Box &S, double *u, const Box &B, const double *b, double *drec,
-                           double *eta_out, DevStatus *st, cudaStream_t stream)
+void launch_sink_eta_apply(const KParams &P, const Box &S, double *u, const Box &B, const double *b, const double *dtr,
+                           double *deta, double *eta_out, DevStatus *st, cudaStream_t stream)
 {
     const long long nvalid = (long long)S.n0 * S.n1 * S.n2;
     if (nvalid == 0) return;
     const unsigned grid = resident_grid(k_sink_eta_apply, kApplyThreads, (nvalid + kApplyThreads - 1) / kApplyThreads);
-    k_sink_eta_apply<<<grid, kApplyThreads, 0, stream>>>(P, S, u, B, b, drec, eta_out, st);
+    k_sink_eta_apply<<<grid, kApplyThreads, 0, stream>>>(P, S, u, B, b, dtr, deta, eta_out, st);
 }
 
 void launch_apply_fb_stream(const Box &S, double *u, const Box &B, const double *b, double *eta_out, DevStatus *st,

@@ -833,7 +833,7 @@ __global__ void __launch_bounds__(128, PMP_SINK_PASS1_MINB) k_pass1_sink(KParams
                     const double w = (wj[cell.i - ht[3 * j] + R] * wj[W + cell.j - ht[3 * j + 1] + R]) *
                                      wj[2 * W + cell.k - ht[3 * j + 2] + R];
                     const double d0x =
-                        __ldg(pl.drec + vidx(S, owner(cell.i, S.n0), owner(cell.j, S.n1), owner(cell.k, S.n2)) * kRec);
+                        __ldg(pl.dtr + vidx(S, owner(cell.i, S.n0), owner(cell.j, S.n1), owner(cell.k, S.n2)));
                     const double bh = kt[j] * w;  // >= +0: K and w are
                     const double a = max_nonneg(bh, d0x);
                     atomicAdd(scr + B.at(cell.i, cell.j, cell.k), neg_bits(a));
@@ -986,22 +986,21 @@ __global__ void __launch_bounds__(256, PMP_DEPOSIT_MINB) k_deposit_atomic(KParam
                     const double *wj = wt + j * 3 * W;
                     const double w = (wj[cell.i - ht[3 * j] + R] * wj[W + cell.j - ht[3 * j + 1] + R]) *
                                      wj[2 * W + cell.k - ht[3 * j + 2] + R];
-                    const double2 *d = reinterpret_cast<const double2 *>(
-                        pl.drec + vidx(S, owner(cell.i, S.n0), owner(cell.j, S.n1), owner(cell.k, S.n2)) * kRec);
-                    const double2 d0 = __ldg(d);
+                    const long long vc = vidx(S, owner(cell.i, S.n0), owner(cell.j, S.n1), owner(cell.k, S.n2));
                     const double bh = kt[j] * w;
-                    const double a = max_nonneg(bh, d0.x);
+                    const double a = max_nonneg(bh, __ldg(pl.dtr + vc));
                     if (scr) {
                         // the cell's factors (1, p/rho, E/rho) are applied by k_sink_spread
                         atomicAdd(scr + B.at(cell.i, cell.j, cell.k), neg_bits(a));
                         continue;
                     }
-                    const double2 d1 = __ldg(d + 1), d2 = __ldg(d + 2);
+                    const double2 *d = reinterpret_cast<const double2 *>(pl.drec + vc * kDRec);
+                    const double2 d0 = __ldg(d), d1 = __ldg(d + 1);
                     dU[0] = -a;
-                    dU[1] = -(a * d0.y);
-                    dU[2] = -(a * d1.x);
-                    dU[3] = -(a * d1.y);
-                    dU[4] = -(a * d2.x);
+                    dU[1] = -(a * d0.x);
+                    dU[2] = -(a * d0.y);
+                    dU[3] = -(a * d1.x);
+                    dU[4] = -(a * d1.y);
                 }
                 if (pv) {
                     const unsigned long long idx = offs[t0 + j] + (g - before);
@@ -1199,19 +1198,19 @@ __global__ void __launch_bounds__(128) k_segment_long(Box B, double *__restrict_
 // ---------------------------------------------------------------------------
 
 // One kernel cell's terms of the Step-4 sums: the pair's removal a (as in
-// the deposit, from D record d0 = (rho - rho_Tr, p_x/rho), d1 = (p_y/rho,
-// p_z/rho)) limited by the cell's eta e, b = e a; the mass sum takes -b, the
-// momentum sums take -b v, fused.
-__device__ __forceinline__ void sink_return_add(double K, double w, double2 d0, double2 d1, double e, double &a0,
-                                                double &a1, double &a2, double &a3)
+// the deposit, from the cell's rho - rho_Tr) limited by the cell's eta e,
+// b = e a; the mass sum takes -b, the momentum sums take -b v (v = p/rho from
+// the D record), fused.
+__device__ __forceinline__ void sink_return_add(double K, double w, double tr, double2 v01, double v2, double e,
+                                                double &a0, double &a1, double &a2, double &a3)
 {
     const double bh = K * w;
-    const double a = bh >= d0.x ? bh : d0.x;
+    const double a = bh >= tr ? bh : tr;
     const double b = e == 1.0 ? a : e * a;
     a0 = a0 - b;
-    a1 = fma(-b, d0.y, a1);
-    a2 = fma(-b, d1.x, a2);
-    a3 = fma(-b, d1.y, a3);
+    a1 = fma(-b, v01.x, a1);
+    a2 = fma(-b, v01.y, a2);
+    a3 = fma(-b, v2, a3);
 }
 
 template <int R>
@@ -1239,30 +1238,33 @@ __device__ __forceinline__ void return_sink_particle(const KParams &P, const Box
     const double K = __ldg(G + SK_K * p.count + s);
     unsigned q = 0;
     for (; q + kUnroll <= nc; q += kUnroll) {
-        double2 d0[kUnroll], d1[kUnroll];
-        double e[kUnroll], wx[kUnroll], wy[kUnroll], wz[kUnroll];
+        double2 v01[kUnroll];
+        double tr[kUnroll], v2[kUnroll], e[kUnroll], wx[kUnroll], wy[kUnroll], wz[kUnroll];
 #pragma unroll
         for (int k = 0; k < kUnroll; ++k) {
             const PairCell c = unpack_pair(__ldg(pl.slots + b0 + q + k), P.R);
-            const double *r = pl.drec + vidx(S, owner(c.i, S.n0), owner(c.j, S.n1), owner(c.k, S.n2)) * kRec;
-            d0[k] = __ldg(reinterpret_cast<const double2 *>(r));
-            d1[k] = __ldg(reinterpret_cast<const double2 *>(r) + 1);
-            e[k] = __ldg(r + 5);
+            const long long vc = vidx(S, owner(c.i, S.n0), owner(c.j, S.n1), owner(c.k, S.n2));
+            const double *r = pl.drec + vc * kDRec;
+            v01[k] = __ldg(reinterpret_cast<const double2 *>(r));
+            v2[k] = __ldg(r + 2);
+            tr[k] = __ldg(pl.dtr + vc);
+            e[k] = __ldg(pl.deta + vc);
             wx[k] = wc[(c.i - hx + R) * kSinkThreads];
             wy[k] = wc[(W + c.j - hy + R) * kSinkThreads];
             wz[k] = wc[(2 * W + c.k - hz + R) * kSinkThreads];
         }
 #pragma unroll
         for (int k = 0; k < kUnroll; ++k)
-            sink_return_add(K, (wx[k] * wy[k]) * wz[k], d0[k], d1[k], e[k], a0, a1, a2, a3);
+            sink_return_add(K, (wx[k] * wy[k]) * wz[k], tr[k], v01[k], v2[k], e[k], a0, a1, a2, a3);
     }
     for (; q < nc; ++q) {
         const PairCell c = unpack_pair(__ldg(pl.slots + b0 + q), P.R);
-        const double *r = pl.drec + vidx(S, owner(c.i, S.n0), owner(c.j, S.n1), owner(c.k, S.n2)) * kRec;
+        const long long vc = vidx(S, owner(c.i, S.n0), owner(c.j, S.n1), owner(c.k, S.n2));
+        const double *r = pl.drec + vc * kDRec;
         const double w = (wc[(c.i - hx + R) * kSinkThreads] * wc[(W + c.j - hy + R) * kSinkThreads]) *
                          wc[(2 * W + c.k - hz + R) * kSinkThreads];
-        sink_return_add(K, w, __ldg(reinterpret_cast<const double2 *>(r)),
-                        __ldg(reinterpret_cast<const double2 *>(r) + 1), __ldg(r + 5), a0, a1, a2, a3);
+        sink_return_add(K, w, __ldg(pl.dtr + vc), __ldg(reinterpret_cast<const double2 *>(r)), __ldg(r + 2),
+                        __ldg(pl.deta + vc), a0, a1, a2, a3);
     }
     p.m[s] = p.m[s] - a0 * P.V;
     p.px[s] = p.px[s] - a1 * P.V;
@@ -1284,8 +1286,8 @@ __global__ void __launch_bounds__(kSinkThreads) k_return_sinks(KParams P, Box S,
 
 // Step 4 from the stored removals: a warp per sink of the processing order,
 // lane l over the sink's kernel cells l, l + 32, ...; each lane sums
-// b = eta a and b v of its cells (the D record holds v = p / rho and, after
-// Step 3, eta), then the warp adds the 32 partial sums.  Per pair: one
+// b = eta a and b v of its cells (v = p / rho from the D record, eta from
+// deta), then the warp adds the 32 partial sums.  Per pair: one
 // product and four additions of FP64 work, and loads of neighbouring cells'
 // records by neighbouring lanes.
 __global__ void __launch_bounds__(256) k_return_sinks_stored(KParams P, Box S, Parts p, PlanPtrs pl)
@@ -1301,14 +1303,15 @@ __global__ void __launch_bounds__(256) k_return_sinks_stored(KParams P, Box S, P
         for (unsigned q = lane; q < nc; q += 32) {
             const PairCell c = unpack_pair(__ldg(pl.slots + b0 + q), P.R);
             const double a = __ldg(pl.pa + b0 + q);
-            const double *r = pl.drec + vidx(S, owner(c.i, S.n0), owner(c.j, S.n1), owner(c.k, S.n2)) * kRec;
-            const double2 d0 = __ldg(reinterpret_cast<const double2 *>(r));
-            const double2 d1 = __ldg(reinterpret_cast<const double2 *>(r) + 1);
-            const double b = __ldg(r + 5) * a;
+            const long long vc = vidx(S, owner(c.i, S.n0), owner(c.j, S.n1), owner(c.k, S.n2));
+            const double *r = pl.drec + vc * kDRec;
+            const double2 v01 = __ldg(reinterpret_cast<const double2 *>(r));
+            const double v2 = __ldg(r + 2);
+            const double b = __ldg(pl.deta + vc) * a;
             a0 = a0 - b;
-            a1 = fma(-b, d0.y, a1);
-            a2 = fma(-b, d1.x, a2);
-            a3 = fma(-b, d1.y, a3);
+            a1 = fma(-b, v01.x, a1);
+            a2 = fma(-b, v01.y, a2);
+            a3 = fma(-b, v2, a3);
         }
         // The warp's 32 partial sums of the four fields, reduced with the
         // fields spread over the lanes: after the first exchange each half
