@@ -193,7 +193,7 @@ def roofline(kernel, ms, pairs, box, n_fb, n_sk, hbm_peak, peak_src):
         "zero": 40 * box.ncells_padded,
         "fold": 120 * (box.ncells_padded - nvalid),
         "apply": 120 * nvalid + (8 * nvalid if kind == "sink" else 0),
-        "cell_records": (40 + 96) * nvalid,
+        "cell_records": (40 + 88) * nvalid,
     }
     if stage == "plan":
         # FP32 decisions: 2 adds per candidate cell and per omega sub-point
@@ -233,7 +233,7 @@ def cell_pass_hbm(kernel_ms, box, hbm_peak):
         "fb_fold": (("fb_fold",), 120 * (npad - nvalid)),
         "fb_apply": (("fb_apply",), 120 * nvalid),
         "sink_zero": (("sink_zero",), 40 * npad),
-        "sink_cell_records": (("sink_cell_records",), (40 + 96) * nvalid),
+        "sink_cell_records": (("sink_cell_records",), (40 + 88) * nvalid),
         "sink_spread": (("sink_spread",), 136 * npad),
         "sink_fold": (("sink_fold",), 120 * (npad - nvalid)),
         "sink_apply": (("sink_apply",), 128 * nvalid),

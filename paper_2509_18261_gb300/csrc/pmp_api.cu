@@ -127,7 +127,7 @@ Layout layout(const pmp_params &p, long long n, long long nvalid, int mode)
     if (sink) {
         L.wts = take(8 * n1 * 3 * (size_t)W);
         // G records, D records, rho - rho_Tr, eta
-        L.aux = take(8 * (size_t)(pmp::kRec + pmp::kDRec + 2) * (size_t)(nvalid > 0 ? nvalid : 1));
+        L.aux = take(8 * (size_t)(pmp::kDRec + pmp::kGRec + 3) * (size_t)(nvalid > 0 ? nvalid : 1));
         // ATOMIC: each pair's removal a, stored by the fused deposit for Step 4
         if (mode == PMP_MODE_ATOMIC) L.pa = take(8 * pairs);
     } else {
@@ -182,12 +182,13 @@ pmp::PlanPtrs plan_ptrs(const Layout &L, void *ws, const pmp_params &p, int mode
     pl.fr = reinterpret_cast<float4 *>(w + L.fr);
     if (p.kind == PMP_KIND_SINK) {
         pl.wts = reinterpret_cast<double *>(w + L.wts);
-        // D records first: at the region's 256-byte-aligned start, every
-        // 32-byte record is one sector
+        // the two 32-byte records first: at the region's 256-byte-aligned
+        // start, every record is one sector
         const size_t nv = (size_t)(nvalid_rows(L) > 0 ? nvalid_rows(L) : 1);
         pl.drec = reinterpret_cast<double *>(w + L.aux);
         pl.grec = pl.drec + (size_t)pmp::kDRec * nv;
-        pl.dtr = pl.grec + (size_t)pmp::kRec * nv;
+        pl.gcs = pl.grec + (size_t)pmp::kGRec * nv;
+        pl.dtr = pl.gcs + nv;
         pl.deta = pl.dtr + nv;
         pl.pa = mode == PMP_MODE_ATOMIC ? reinterpret_cast<double *>(w + L.pa) : nullptr;
     }
@@ -586,7 +587,7 @@ static pmp_status gather_impl(pmp_ctx *ctx, const pmp_mesh *state, const pmp_par
     }
     if (ctx->p.kind == PMP_KIND_SINK) {
         Timed tm(ctx, "cell_records");
-        pmp::launch_sink_aux(P, S, state->data, pl.grec, pl.drec, pl.dtr, pl.deta, st);
+        pmp::launch_sink_aux(P, S, state->data, pl.grec, pl.gcs, pl.drec, pl.dtr, pl.deta, st);
     }
     if (q.count > 0) {
         if (fused) {

@@ -418,12 +418,15 @@ __device__ __forceinline__ void sink_delta(const KParams &P, const double U[NF],
 }
 
 // Per-cell sink quantities (valid cells, x fastest), inv = 1/rho:
-//   G record (gather), 6 doubles = 48 bytes:  rho, p_x, p_y, p_z, rho c_s, 0
+//   G record (gather), 4 doubles = 32 bytes (one sector):  rho, p_x, p_y, p_z
 //   D record (spread, Step 4), 4 doubles = 32 bytes (one sector):  p_x inv, p_y inv, p_z inv, E inv
-//   rho - rho_Tr (deposit, limiter) and eta (Step 4) in dense arrays of their own, so that a
-//   kernel that needs one of them reads 8 bytes per cell, not a record
-constexpr int kRec = 6;
+//   rho c_s (gather), rho - rho_Tr (deposit, limiter) and eta (Step 4) in dense arrays of their
+//   own, so that a kernel reads 8 bytes per cell for each of them, not a record
+constexpr int kGRec = 4;
 constexpr int kDRec = 4;
+// Bytes per cell the L2 windows of the sink kernels are sized with (the
+// launch shapes were measured with this figure).
+constexpr double kWindowBytesPerCell = 48.0;
 
 // Gathered-row indices.
 enum { FB_MSNR = 0, FB_VSNR, FB_VX, FB_VY, FB_VZ, FB_NH, FB_RM, FB_PRAD, FB_Q, FB_E, FB_PV, FB_REGIME, FB_ROWS };

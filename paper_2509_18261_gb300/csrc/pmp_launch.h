@@ -27,7 +27,8 @@ struct PlanPtrs {
     unsigned long long *hosts;        // [n] packed host cell, by particle index
     float4 *fr;                       // [n] fractional position in the host cell (FP32)
     double *wts;                      // sink: [n][3][2R+1] per-axis Gaussian factors
-    double *grec;                     // sink: [valid cells][6] G records
+    double *grec;                     // sink: [valid cells][4] G records
+    double *gcs;                      // sink: [valid cells] rho c_s
     double *drec;                     // sink: [valid cells][4] D records
     double *dtr;                      // sink: [valid cells] rho - rho_Tr
     double *deta;                     // sink: [valid cells] eta (1 until Step 3 limits the cell)
@@ -110,8 +111,8 @@ void launch_round(const Box &B, double *b, const double *E, int M, cudaStream_t 
 // E/rho) per buffer cell, the factors of its owner cell's D record.
 void launch_sink_spread(const Box &S, const Box &B, double *b, const double *scr, const double *drec,
                         cudaStream_t stream);
-void launch_sink_aux(const KParams &P, const Box &S, const double *u, double *grec, double *drec, double *dtr,
-                     double *deta, cudaStream_t stream);
+void launch_sink_aux(const KParams &P, const Box &S, const double *u, double *grec, double *gcs, double *drec,
+                     double *dtr, double *deta, cudaStream_t stream);
 // Steps 3 + 5 for sinks: eta per valid cell (into deta, for Step 4)
 // and U += eta Delta U^sum, in one pass.
 void launch_sink_eta_apply(const KParams &P, const Box &S, double *u, const Box &B, const double *b, const double *dtr,

@@ -247,12 +247,13 @@ __global__ void __launch_bounds__(kApplyThreads, PMP_FB_APPLY_MINB) k_apply_fb_s
 }
 
 // Per-cell sink records, each value in the order the sink formulas state it:
-// G = (rho, p, rho c_s) for the gather; D = (p inv, E inv) with inv = 1/rho
-// for the spread and Step 4; rho - rho_Tr (Eq. truelove) for the deposit and
-// the limiter; eta = 1 until Step 3 limits the cell.
+// G = (rho, p) and rho c_s for the gather; D = (p inv, E inv) with inv =
+// 1/rho for the spread and Step 4; rho - rho_Tr (Eq. truelove) for the
+// deposit and the limiter; eta = 1 until Step 3 limits the cell.
 __global__ void __launch_bounds__(256) k_sink_aux(KParams P, Box S, const double *__restrict__ u,
-                                                  double *__restrict__ grec, double *__restrict__ drec,
-                                                  double *__restrict__ dtr, double *__restrict__ deta)
+                                                  double *__restrict__ grec, double *__restrict__ gcs,
+                                                  double *__restrict__ drec, double *__restrict__ dtr,
+                                                  double *__restrict__ deta)
 {
     const long long nvalid = (long long)S.n0 * S.n1 * S.n2;
     const long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -264,10 +265,10 @@ __global__ void __launch_bounds__(256) k_sink_aux(KParams P, Box S, const double
     load_cell(u, S, S.at(i, j, k), U);
     const double inv = exact::div_rn(1.0, U[0]);
     sink_cell(P, U, inv, cs, rtr);
-    double2 *g = reinterpret_cast<double2 *>(grec + v * kRec);
+    double2 *g = reinterpret_cast<double2 *>(grec + v * kGRec);
     g[0] = make_double2(U[0], U[1]);
     g[1] = make_double2(U[2], U[3]);
-    g[2] = make_double2(U[0] * cs, 0.0);
+    gcs[v] = U[0] * cs;
     double2 *d = reinterpret_cast<double2 *>(drec + v * kDRec);
     d[0] = make_double2(U[1] * inv, U[2] * inv);
     d[1] = make_double2(U[3] * inv, U[4] * inv);
@@ -677,11 +678,11 @@ void launch_fold(const Box &B, double *b, cudaStream_t stream)
     k_fold<<<(unsigned)((threads + 255) / 256), 256, 0, stream>>>(B, b);
 }
 
-void launch_sink_aux(const KParams &P, const Box &S, const double *u, double *grec, double *drec, double *dtr,
-                     double *deta, cudaStream_t stream)
+void launch_sink_aux(const KParams &P, const Box &S, const double *u, double *grec, double *gcs, double *drec,
+                     double *dtr, double *deta, cudaStream_t stream)
 {
     const long long nvalid = (long long)S.n0 * S.n1 * S.n2;
-    k_sink_aux<<<(unsigned)((nvalid + 255) / 256), 256, 0, stream>>>(P, S, u, grec, drec, dtr, deta);
+    k_sink_aux<<<(unsigned)((nvalid + 255) / 256), 256, 0, stream>>>(P, S, u, grec, gcs, drec, dtr, deta);
 }
 
 void launch_sink_spread(const Box &S, const Box &B, double *b, const double *scr, const double *drec,

@@ -646,15 +646,16 @@ __device__ __forceinline__ void gather_sink_particle(const KParams &P, const Box
     double srho = 0.0, sp0 = 0.0, sp1 = 0.0, sp2 = 0.0, src = 0.0;
     unsigned q = 0;
     for (; q + kUnroll <= nc; q += kUnroll) {
-        double2 g[kUnroll][3];
+        double2 g[kUnroll][2];
+        double gc[kUnroll];
 #pragma unroll
         for (int k = 0; k < kUnroll; ++k) {
             const PairCell c = unpack_pair(slot_load<NC>(pl.slots + b0 + q + k), P.R);
-            const double2 *r = reinterpret_cast<const double2 *>(
-                pl.grec + vidx(S, owner(c.i, S.n0), owner(c.j, S.n1), owner(c.k, S.n2)) * kRec);
+            const long long vc = vidx(S, owner(c.i, S.n0), owner(c.j, S.n1), owner(c.k, S.n2));
+            const double2 *r = reinterpret_cast<const double2 *>(pl.grec + vc * kGRec);
             g[k][0] = __ldg(r);
             g[k][1] = __ldg(r + 1);
-            g[k][2] = __ldg(r + 2);
+            gc[k] = __ldg(pl.gcs + vc);
         }
 #pragma unroll
         for (int k = 0; k < kUnroll; ++k) {
@@ -662,19 +663,19 @@ __device__ __forceinline__ void gather_sink_particle(const KParams &P, const Box
             sp0 = sp0 + g[k][0].y;
             sp1 = sp1 + g[k][1].x;
             sp2 = sp2 + g[k][1].y;
-            src = src + g[k][2].x;
+            src = src + gc[k];
         }
     }
     for (; q < nc; ++q) {
         const PairCell c = unpack_pair(slot_load<NC>(pl.slots + b0 + q), P.R);
-        const double2 *g =
-            reinterpret_cast<const double2 *>(pl.grec + vidx(S, owner(c.i, S.n0), owner(c.j, S.n1), owner(c.k, S.n2)) * kRec);
-        const double2 g0 = __ldg(g), g1 = __ldg(g + 1), g2 = __ldg(g + 2);
+        const long long vc = vidx(S, owner(c.i, S.n0), owner(c.j, S.n1), owner(c.k, S.n2));
+        const double2 *g = reinterpret_cast<const double2 *>(pl.grec + vc * kGRec);
+        const double2 g0 = __ldg(g), g1 = __ldg(g + 1);
         srho = srho + g0.x;
         sp0 = sp0 + g0.y;
         sp1 = sp1 + g1.x;
         sp2 = sp2 + g1.y;
-        src = src + g2.x;
+        src = src + __ldg(pl.gcs + vc);
     }
     gather_sink_finish<R>(P, pl, G, gs, st, t, s, x, y, z, ms, ps0, ps1, ps2, nc, srho, sp0, sp1, sp2, src);
 }
@@ -1478,7 +1479,7 @@ void launch_gather(const KParams &P, const Box &S, const double *u, const Parts 
     } else if (P.kind == PMP_KIND_MASS) {
         k_gather_mass<<<nb, 128, 0, stream>>>(P, S, p, pl, G, st);
     } else {
-        const unsigned nbs = window_blocks(S, p.count, kSinkThreads, 8.0 * kRec, 1.5, PMP_SINK_GATHER_BPS);
+        const unsigned nbs = window_blocks(S, p.count, kSinkThreads, kWindowBytesPerCell, 1.5, PMP_SINK_GATHER_BPS);
         PMP_DISPATCH_R(P.R, (k_gather_sink<RR><<<nbs, kSinkThreads, 0, stream>>>(P, S, u, p, pl, G, st)));
     }
 }
@@ -1495,7 +1496,7 @@ static void pass1_sink_one(const KParams &P, const Box &S, const double *u, cons
     constexpr int W = 2 * R + 1;
     constexpr int warps = 4;
     const size_t sm = (size_t)(W * W * W * 4 + 15) / 16 * 16 + (size_t)warps * pass1_sink_warp_bytes(W);
-    const unsigned nb = window_blocks(S, (p.count + 31) / 32 * 32, 32 * warps, 8.0 * kRec, 2.0, PMP_SINK_PASS1_BPS);
+    const unsigned nb = window_blocks(S, (p.count + 31) / 32 * 32, 32 * warps, kWindowBytesPerCell, 2.0, PMP_SINK_PASS1_BPS);
     const long long need = (p.count + 32LL * warps - 1) / (32LL * warps);
     const unsigned grid = (unsigned)(need < (long long)nb ? need : (long long)nb);
     k_pass1_sink<R><<<grid, 32 * warps, sm, stream>>>(P, S, u, B, scr, p, pl, G, st);
@@ -1609,7 +1610,7 @@ void launch_return_sinks_stored(const KParams &P, const Box &S, const Parts &p, 
     if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_return_sinks_stored, 256, 0) != cudaSuccess || occ < 1)
         occ = 1;
-    const unsigned nb = window_blocks(S, p.count, 8, 8.0 * kRec, 1.0, PMP_SINK_RETURN_STORED_BPS);
+    const unsigned nb = window_blocks(S, p.count, 8, kWindowBytesPerCell, 1.0, PMP_SINK_RETURN_STORED_BPS);
     const long long cap = (long long)nsm * occ;
     const unsigned grid = (unsigned)((long long)nb < cap ? (long long)nb : cap);
     k_return_sinks_stored<<<grid, 256, 0, stream>>>(P, S, p, pl);
@@ -1619,7 +1620,7 @@ void launch_return_sinks(const KParams &P, const Box &S, const Parts &p, const d
                          DevStatus *st, cudaStream_t stream)
 {
     if (p.count == 0) return;
-    const unsigned nb = window_blocks(S, p.count, kSinkThreads, 8.0 * kRec, 1.0, PMP_SINK_RETURN_BPS);
+    const unsigned nb = window_blocks(S, p.count, kSinkThreads, kWindowBytesPerCell, 1.0, PMP_SINK_RETURN_BPS);
     PMP_DISPATCH_R(P.R, (k_return_sinks<RR><<<nb, kSinkThreads, 0, stream>>>(P, S, p, G, pl, st)));
 }
 
