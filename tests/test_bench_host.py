@@ -96,6 +96,17 @@ def test_cell_pass_hbm_rates():
     assert "sink_spread" not in out  # a pass that was not timed is left out
 
 
+def test_batched_hbm_view_counts_zero_fold_and_apply_per_pass():
+    # one 16^3 patch with 4 ghost cells per side: 24^3 buffer cells
+    v, p = 16 ** 3, 24 ** 3
+    out = bench.batched_hbm_view(v, p, 2.0, 6800.0, "measured")
+    per_pass = 40 * p + 120 * (p - v) + 120 * v
+    assert out["algorithmic_bytes_per_cycle"] == 2 * per_pass
+    assert out["GB/s"] == pytest.approx(2 * per_pass / 2e-3 / 1e9)
+    assert out["frac"] == pytest.approx(out["GB/s"] / 6800.0)
+    assert out["peak_source"] == "measured"
+
+
 class _Done:
     def terminate(self):
         pass
