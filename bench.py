@@ -254,15 +254,43 @@ def cell_pass_hbm(kernel_ms, box, hbm_peak):
 DIGEST_EXCLUDES = ("pmp_batch.cu", "pmp_noalloc.cu", "pmp_probe.cu", "pmp_exchange.cu")
 
 
-def src_digest():
-    """Digest of the sources that define and launch the single-box kernels
-    (every csrc/ file but DIGEST_EXCLUDES)."""
+def code_of(text):
+    """C/C++/CUDA source without its comments, trailing blanks and empty
+    lines: what a compiler sees of it, up to layout.  String and character
+    literals are kept as they are (a // or /* inside one is not a comment)."""
+    out, i, n = [], 0, len(text)
+    while i < n:
+        c = text[i]
+        if text.startswith("//", i):
+            j = text.find("\n", i)
+            i = n if j < 0 else j
+        elif text.startswith("/*", i):
+            j = text.find("*/", i + 2)
+            out.append(" ")
+            i = n if j < 0 else j + 2
+        elif c in "\"'":
+            j = i + 1
+            while j < n and text[j] != c and text[j] != "\n":
+                j += 2 if text[j] == "\\" else 1
+            out.append(text[i:j + 1])
+            i = j + 1
+        else:
+            out.append(c)
+            i += 1
+    lines = (line.rstrip() for line in "".join(out).split("\n"))
+    return "\n".join(line for line in lines if line)
+
+
+def src_digest(d=None):
+    """Digest of the code (comments and blank lines left out) of the sources
+    that define and launch the single-box kernels: every csrc/ file but
+    DIGEST_EXCLUDES, each with its name."""
     h = hashlib.sha256()
-    d = os.path.join(ROOT, "paper_2509_18261_gb300", "csrc")
+    d = d or os.path.join(ROOT, "paper_2509_18261_gb300", "csrc")
     for f in sorted(os.listdir(d)):
         if f in DIGEST_EXCLUDES:
             continue
-        h.update(open(os.path.join(d, f), "rb").read())
+        h.update(f.encode() + b"\0" + code_of(open(os.path.join(d, f), encoding="utf-8").read()).encode() + b"\0")
     return h.hexdigest()[:16]
 
 

@@ -126,7 +126,7 @@ Layout layout(const pmp_params &p, long long n, long long nvalid, int mode)
     L.fr = take(16 * n1);
     if (sink) {
         L.wts = take(8 * n1 * 3 * (size_t)W);
-        // G records, D records, rho - rho_Tr, eta
+        // D records, G records, rho c_s, rho - rho_Tr, eta
         L.aux = take(8 * (size_t)(pmp::kDRec + pmp::kGRec + 3) * (size_t)(nvalid > 0 ? nvalid : 1));
         // ATOMIC: each pair's removal a, stored by the fused deposit for Step 4
         if (mode == PMP_MODE_ATOMIC) L.pa = take(8 * pairs);

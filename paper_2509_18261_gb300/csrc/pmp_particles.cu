@@ -1425,8 +1425,8 @@ void launch_plan_gather_fb(const KParams &P, const Box &S, const double *u, cons
 // Blocks of the thread-per-sink kernels.  They run grid-stride over the
 // processing order, so the sinks in flight are a window of grid x
 // kSinkThreads consecutive sinks; its kernel cells (about cells / sinks of
-// them per sink, 48-byte records) are kept within half the L2, else every
-// record is read from DRAM several times.
+// them per sink, counted at kWindowBytesPerCell bytes each) are kept within
+// half the L2, else every record is read from DRAM several times.
 //
 // The window is set in units of "L2 windows": blocks per SM such that the
 // window's records take about one L2.  Measured on the 512^3 workload (sink

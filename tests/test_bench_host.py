@@ -96,6 +96,22 @@ def test_cell_pass_hbm_rates():
     assert "sink_spread" not in out  # a pass that was not timed is left out
 
 
+def test_source_digest_follows_code_not_comments(tmp_path):
+    src = 'int a; // sum\n/* two\n   lines */ const char *s = "//x";\n\nchar q = \'"\';  \n'
+    (tmp_path / "k.cu").write_text(src)
+    base = bench.src_digest(str(tmp_path))
+    (tmp_path / "k.cu").write_text(src.replace("// sum", "// total").replace("two", "three") + "\n// more\n")
+    assert bench.src_digest(str(tmp_path)) == base
+    (tmp_path / "k.cu").write_text(src.replace('"//x"', '"//y"'))  # inside a string literal: code
+    assert bench.src_digest(str(tmp_path)) != base
+    (tmp_path / "k.cu").write_text(src.replace("int a;", "int b;"))
+    assert bench.src_digest(str(tmp_path)) != base
+    (tmp_path / "k.cu").write_text(src)
+    (tmp_path / "pmp_batch.cu").write_text("int z;")  # excluded: not a single-box kernel source
+    assert bench.src_digest(str(tmp_path)) == base
+    assert bench.code_of(src) == 'int a;\n  const char *s = "//x";\nchar q = \'"\';'
+
+
 def test_batched_hbm_view_counts_zero_fold_and_apply_per_pass():
     # one 16^3 patch with 4 ghost cells per side: 24^3 buffer cells
     v, p = 16 ** 3, 24 ** 3
