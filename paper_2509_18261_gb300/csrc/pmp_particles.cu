@@ -1485,10 +1485,12 @@ void launch_gather(const KParams &P, const Box &S, const double *u, const Parts 
 }
 
 // The fused sink kernel: 4-warp blocks, each warp 32 sinks; a block has as
-// many sinks in flight as a 128-thread gather block, so an L2 window sets its
-// grid.  512^3 sweep (blocks per SM): 2 -> 45.7 ms, 3 -> 32.8 ms, 4 -> 27.5
-// ms, 6 -> 37.5 ms; two L2 windows give 4 (the separate plan, gather and
-// deposit took 2.6 + 16.2 + 9.6 ms).
+// many sinks in flight as a 128-thread gather block.  Its grid is
+// PMP_SINK_PASS1_BPS blocks per SM (the sweep is at k_pass1_sink); with the
+// macro set to 0, two L2 windows set it.  The first 512^3 sweep, before the
+// kernel was compiled for its occupancy (blocks per SM): 2 -> 45.7 ms, 3 ->
+// 32.8 ms, 4 -> 27.5 ms, 6 -> 37.5 ms (the separate plan, gather and deposit
+// took 2.6 + 16.2 + 9.6 ms).
 template <int R>
 static void pass1_sink_one(const KParams &P, const Box &S, const double *u, const Box &B, double *scr,
                            const Parts &p, const PlanPtrs &pl, double *G, DevStatus *st, cudaStream_t stream)

@@ -1,5 +1,5 @@
 """Soundness of the FP32 decisions of the kernels: the limiters' pre-tests
-(k_sink_eta_apply and k_apply_fb_fast: whenever one decides eta = 1, the
+(k_sink_eta_apply and k_apply_fb_stream: whenever one decides eta = 1, the
 FP64 test agrees) and the plan's kernel-membership, full-cell and sub-point
 decisions (taken in FP32 outside a 2^-14 band around r_K^2, each equal to the
 FP64 decision of the canonical order).
@@ -110,7 +110,7 @@ def test_pretest_takes_the_common_case():
 
 
 # ---------------------------------------------------------------------------
-# the supernova apply's FP32 pre-check of Eq. lambda (k_apply_fb_fast)
+# the supernova apply's FP32 pre-check of Eq. lambda (k_apply_fb_stream)
 # ---------------------------------------------------------------------------
 
 def sn_pretest(U, D):
