@@ -114,6 +114,55 @@ def test_sink_edge_boxes(orc, mode, n, g, rK, periodic, dt):
     assert ref["counts"][0] > 0
 
 
+def lambda_case_cells():
+    """A 4 x 2 x 1 box whose first cells hold Eq. lambda's hard cases: three
+    cells where no lambda in [0, 1] satisfies the constraint (no real root;
+    both roots below 0; both above 1), one limited cell (one root in (0, 1)),
+    one change without momentum; the rest of the buffer is zero."""
+    box = syn.Box((4, 2, 1), 1)
+    state = syn.gas_state(np.random.default_rng(5), box)
+    buf = box.empty(0.0)
+    sv, bv = box.valid(state), box.valid(buf)
+    cells = [((1.0, 1.0, 0.0, 0.0, 1.0), (1.0, 0.0, 1.0, 0.0, 0.1)),
+             ((1.0, 1.0, 0.0, 0.0, 1.0), (1.0, 1.0, 0.0, 0.0, 0.1)),
+             ((1.0, 1.0, 0.0, 0.0, 1.0), (1.0, -0.3, 0.0, 0.0, 0.1)),
+             ((1.3, 0.2, 0.0, 0.0, 0.8), (0.2, 3.0, -4.0, 1.5, 0.9)),
+             (None, (0.1, 0.0, 0.0, 0.0, 0.2))]
+    for c, (U, D) in enumerate(cells):
+        if U is not None:
+            sv[:, 0, c // 4, c % 4] = U
+        bv[:, 0, c // 4, c % 4] = D
+    return box, state, buf
+
+
+def test_feedback_apply_without_a_feasible_lambda(orc):
+    """Steps 3 + 5 alone on cells where Eq. lambda has no feasible value (the
+    reading: lambda = 0, counted), beside a limited cell and a change without
+    momentum: state, eta and both counters bit for bit against the oracle."""
+    import torch
+
+    from paper_2509_18261_gb300 import pmp
+
+    box, state, buf = lambda_case_cells()
+    params = syn.feedback_params()
+    want = state.copy()
+    eta_want, counts_want = orc.apply(params, box, want, buf.copy(), want_eta=True)
+    assert counts_want[1] == 3 and counts_want[0] == 4
+    ctx = pmp.Context(params)
+    try:
+        st = pmp.Mesh(torch.from_numpy(state.copy()).to("cuda"), box.n, box.g)
+        bm = pmp.Mesh(torch.from_numpy(buf.copy()).to("cuda"), box.n, box.g)
+        eta = torch.empty(box.ncells_valid, dtype=torch.float64, device="cuda")
+        pmp.pmp_apply_limited(ctx, st, bm, eta_out=eta)
+        counts = pmp.pmp_limiter_counts(ctx)
+        assert pmp.pmp_get_error(ctx) == (0, -1)
+    finally:
+        ctx.close()
+    assert_bits_equal(valid_flat(box, st.data.cpu().numpy()), valid_flat(box, want), "state after Step 5")
+    assert_bits_equal(eta.cpu().numpy(), eta_want, "eta")
+    assert tuple(counts) == (counts_want[0], counts_want[1])
+
+
 @pytest.mark.parametrize("kind", ["feedback", "sink"])
 def test_no_particles(orc, kind):
     box = syn.Box((6, 6, 6), 4)

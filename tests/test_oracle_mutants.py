@@ -197,6 +197,12 @@ MUTANTS = [
     ("Eq. lambda's roots swapped when p . dp < 0",
      "        double Q = sq - B;\n        hi = Q / A;\n        lo = C / Q;",
      "        double Q = sq - B;\n        hi = C / Q;\n        lo = Q / A;"),
+    ("Eq. lambda keeps the whole momentum change when the quadratic has no real root",
+     "    if (!(disc >= 0.0)) { *noroot = 1; return 0.0; }",
+     "    if (!(disc >= 0.0)) { *noroot = 1; return 1.0; }"),
+    ("Eq. lambda keeps the whole momentum change when both roots lie outside [0, 1]",
+     "    if (hi < 0.0 || lo > 1.0) { *noroot = 1; return 0.0; }",
+     "    if (hi < 0.0 || lo > 1.0) { *noroot = 1; return 1.0; }"),
     ("gathered gas mass without the cell volume",
      "    double Mgas = sr * V;",
      "    double Mgas = sr;"),

@@ -551,6 +551,27 @@ def test_sn_lambda_is_the_largest_feasible_value(orc, case):
     assert lam == pytest.approx(want, abs=1e-9)
 
 
+@pytest.mark.parametrize("case", [
+    # dp orthogonal to p: |p + l dp| >= |p| for every l, the quadratic has no real root
+    ([1.0, 1.0, 0.0, 0.0, 1.0], [1.0, 0.0, 1.0, 0.0, 0.1]),
+    # dp along p: both roots negative
+    ([1.0, 1.0, 0.0, 0.0, 1.0], [1.0, 1.0, 0.0, 0.0, 0.1]),
+    # a small dp against p: both roots above 1
+    ([1.0, 1.0, 0.0, 0.0, 1.0], [1.0, -0.3, 0.0, 0.0, 0.1]),
+])
+def test_sn_lambda_without_a_feasible_value(orc, case):
+    """Where no lambda in [0, 1] satisfies Eq. lambda (brute force), the
+    momentum change is dropped (lambda = 0, the reading for that case) and the
+    cell is counted; the mass and energy changes still go in."""
+    U, D = np.array(case[0]), np.array(case[1])
+    assert _largest_feasible_lambda(U, D) is None
+    new, lam, counts = _apply_single_cell(orc, U, D, syn.feedback_params())
+    assert lam == 0.0
+    assert counts[1] == 1
+    assert np.array_equal(new[1:4], U[1:4])
+    assert new[0] == U[0] + D[0] and new[4] == U[4] + D[4]
+
+
 # --------------------------------------------------------------------------
 # regimes (Eq. dp, Eq. psnr)
 # --------------------------------------------------------------------------
