@@ -24,7 +24,10 @@ PINS = ["tests/test_oracle_pins.py", "tests/test_oracle_create.py", "tests/test_
 # (name, the original text, its mutated form); the original occurs once.
 # Equivalent mutants are left out: e.g. folding ghosts of a non-periodic axis
 # too changes nothing, because the kernel is cut at that face and those
-# ghosts only ever hold zeros.
+# ghosts only ever hold zeros; and the accretion limiter's eta needs no cap at
+# 1 on a buffer from the sink deposit, where every pair removes at least
+# rho - rho_Tr, so the summed removal is never below rho - rho_Tr (rounding
+# is monotone) and the limited removal never exceeds it.
 MUTANTS = [
     ("accretion removes instead of adding to the buffer's density row",
      "    dU[0] = -a;\n    for (int k = 0; k < 3; k++) dU[1 + k] = -(a * (U[1 + k] * inv));",
@@ -197,6 +200,15 @@ MUTANTS = [
     ("Eq. lambda's roots swapped when p . dp < 0",
      "        double Q = sq - B;\n        hi = Q / A;\n        lo = C / Q;",
      "        double Q = sq - B;\n        hi = C / Q;\n        lo = Q / A;"),
+    ("Eq. lambda's roots swapped when p . dp >= 0",
+     "        hi = Q != 0.0 ? C / Q : 0.0;\n        lo = Q / A;",
+     "        hi = Q / A;\n        lo = Q != 0.0 ? C / Q : 0.0;"),
+    ("accretion limiter caps at rho - rho_Tr instead of keeping it as a floor",
+     "    al = al > t ? al : t;",
+     "    al = al < t ? al : t;"),
+    ("accretion limiter lets a negative limited removal through",
+     "    if (al < 0.0) al = 0.0;\n    return al < a ? al / a : 1.0;",
+     "    return al < a ? al / a : 1.0;"),
     ("Eq. lambda keeps the whole momentum change when the quadratic has no real root",
      "    if (!(disc >= 0.0)) { *noroot = 1; return 0.0; }",
      "    if (!(disc >= 0.0)) { *noroot = 1; return 1.0; }"),
