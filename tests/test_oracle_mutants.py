@@ -209,6 +209,33 @@ MUTANTS = [
     ("accretion limiter lets a negative limited removal through",
      "    if (al < 0.0) al = 0.0;\n    return al < a ? al / a : 1.0;",
      "    return al < a ? al / a : 1.0;"),
+    ("Truelove density with J instead of J^2",
+     "double ctr = ((P->J * P->J) * OR_PI) / (P->G * (dx * dx));",
+     "double ctr = (P->J * OR_PI) / (P->G * (dx * dx));"),
+    ("Truelove density without pi",
+     "double ctr = ((P->J * P->J) * OR_PI) / (P->G * (dx * dx));",
+     "double ctr = (P->J * P->J) / (P->G * (dx * dx));"),
+    ("Truelove density over dx instead of dx^2",
+     "double ctr = ((P->J * P->J) * OR_PI) / (P->G * (dx * dx));",
+     "double ctr = ((P->J * P->J) * OR_PI) / (P->G * dx);"),
+    ("stencil half-width truncated instead of rounded up",
+     "static int stencil_halfwidth(double rK) { return (int)ceil(rK); }",
+     "static int stencil_halfwidth(double rK) { return (int)rK; }"),
+    ("r_acc in length units instead of cells",
+     "    double racc = r_bh / S->dx;",
+     "    double racc = r_bh;"),
+    ("accretion kernel normalisation without the cell volume",
+     "    double K = ((mdot * P->dt) / V) / sumw;",
+     "    double K = (mdot * P->dt) / sumw;"),
+    ("n_H without the mean mass per hydrogen",
+     "    double nH = Msnr / (P->mu_H * Vsnr);",
+     "    double nH = Msnr / Vsnr;"),
+    ("ejecta density per SN mass instead of per volume",
+     "    G[FB_Q * stride] = m / Vsnr;",
+     "    G[FB_Q * stride] = m / Msnr;"),
+    ("v_COM divided by the gas mass alone",
+     "    for (int a = 0; a < 3; a++) vc[a] = (sp[a] * V + pe[a]) / Msnr;",
+     "    for (int a = 0; a < 3; a++) vc[a] = (sp[a] * V + pe[a]) / Mgas;"),
     ("Eq. lambda keeps the whole momentum change when the quadratic has no real root",
      "    if (!(disc >= 0.0)) { *noroot = 1; return 0.0; }",
      "    if (!(disc >= 0.0)) { *noroot = 1; return 1.0; }"),

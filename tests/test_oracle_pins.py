@@ -145,18 +145,19 @@ def test_fig1_worked_example(orc):
 # Bondi / Bondi-Hoyle closed forms (Eq. rbh, Eq. mdot)
 # --------------------------------------------------------------------------
 
-@pytest.mark.parametrize("Gm,r_acc", [(0.1, 0.25), (3.0, 2.0), (1.2, 1.2)])
-def test_accretion_kernel_shape(orc, Gm, r_acc):
+@pytest.mark.parametrize("Gm,r_acc,dx", [(0.1, 0.25, 1.0), (3.0, 2.0, 1.0), (1.2, 1.2, 1.0), (0.6, 1.2, 0.5)])
+def test_accretion_kernel_shape(orc, Gm, r_acc, dx):
     """Gas at rest, one sink at rest, Bondi branch only: the removal per cell
     follows the Gaussian of Eq. kernel, exp(-|x_c - x_s|^2 / r_acc^2), with
     r_acc = r_BH = G m / c_s^2 kept between a quarter of a cell and r_K/2
-    (Sec. 3.1.1).  Ratios to the host cell, from cell centres computed here."""
+    (Sec. 3.1.1); distances and r_acc in cells (r_BH / dx).  Ratios to the
+    host cell, from cell centres computed here."""
     params = syn.sink_params(r_K=4.0, gamma=2.0, G=0.01, dt=1e-9, rho_min=0.0)
     box = syn.Box((16, 16, 16), 4)
     state = syn.uniform_gas(box, 1.0, e_th=0.5)  # c_s = 1
     xs = np.array([8.3, 7.6, 8.45])
     sink = one(*xs, Gm / 0.01)
-    r = orc.cycle(params, box, state, sink)
+    r = orc.cycle(params, box, state, sink, dx=dx)
     assert r["counts"][0] == 0
     drho = box.valid(r["buf"])[0]
     k, j, i = np.nonzero(drho)
@@ -168,6 +169,33 @@ def test_accretion_kernel_shape(orc, Gm, r_acc):
     keep = want > 1e-250
     assert keep.sum() > 6
     assert np.allclose(got[keep], want[keep], rtol=1e-11, atol=0)
+
+
+@pytest.mark.parametrize("dx", [1.0, 0.5])
+def test_truelove_density_is_the_floor_of_accretion(orc, dx):
+    """A sink whose Bondi rate is negligible, in uniform gas above the Truelove
+    density rho_Tr = J^2 pi c_s^2 / (G dx^2) (Eq. truelove): the accretion
+    rate that enforces the Truelove condition removes rho - rho_Tr from every
+    kernel cell, which the 25% limiter lets through (Sec. 3.1.1), so every
+    kernel cell ends at rho_Tr and every other cell keeps rho."""
+    J, G, gamma = 0.25, 0.035, 5.0 / 3.0
+    params = syn.sink_params(r_K=2.0, gamma=gamma, G=G, J=J, dt=1e-12, rho_min=0.0)
+    box = syn.Box((8, 8, 8), 2)
+    rho0 = 40.0
+    state = syn.uniform_gas(box, rho0, e_th=0.9)  # c_s^2 = gamma (gamma - 1) e_th = 1
+    cs2 = gamma * (gamma - 1.0) * 0.9
+    rho_tr = J * J * math.pi * cs2 / (G * dx * dx)
+    assert rho_tr < rho0 and rho0 - rho_tr > rho0 / 4
+    xs = (4.2, 3.7, 4.6)
+    r = orc.cycle(params, box, state, one(*xs, 1.0), dx=dx)
+    rho = box.valid(state)[0]
+    k, j, i = np.indices(rho.shape)
+    d2 = (i + 0.5 - xs[0]) ** 2 + (j + 0.5 - xs[1]) ** 2 + (k + 0.5 - xs[2]) ** 2
+    inside = d2 < 4.0
+    assert inside.sum() > 20
+    assert np.allclose(rho[inside], rho_tr, rtol=1e-13, atol=0)
+    assert np.all(rho[~inside] == rho0)
+    assert r["counts"][0] == 0
 
 
 def test_bondi_hoyle_depends_on_the_relative_velocity(orc):
@@ -576,12 +604,14 @@ def test_sn_lambda_without_a_feasible_value(orc, case):
 # regimes (Eq. dp, Eq. psnr)
 # --------------------------------------------------------------------------
 
+@pytest.mark.parametrize("mu_H", [1.0, 1.4])
 @pytest.mark.parametrize("target", [0.02, 0.5, 3.0])
-def test_regime_and_radial_momentum(orc, target):
+def test_regime_and_radial_momentum(orc, target, mu_H):
     """Uniform density rho0 chosen so that R_M hits the target; |p_radial|
-    must be 0 (EJ), sqrt(2 M_ej eps_K E_sn) (ST) or A_p n_H^-0.17 (MC)."""
+    must be 0 (EJ), sqrt(2 M_ej eps_K E_sn) (ST) or A_p n_H^-0.17 (MC), with
+    n_H = M_snr / (mu_H V_snr) the hydrogen number density."""
     box = syn.Box((12, 12, 12), 2)
-    params = syn.feedback_params()
+    params = syn.feedback_params(mu_H=mu_H)
     M_ej, E_sn = 0.01, 1.0
     pos = (5.3, 6.2, 4.7)
     # V_snr does not depend on the gas: read it once, then solve for rho0.
@@ -590,7 +620,7 @@ def test_regime_and_radial_momentum(orc, target):
 
     def R_M(rho0):
         M = rho0 * Vsnr + M_ej
-        n = M / Vsnr
+        n = M / (mu_H * Vsnr)
         return M / (params["A_sf"] * n ** -0.26)
 
     lo, hi = 1e-6, 1e6
@@ -603,7 +633,7 @@ def test_regime_and_radial_momentum(orc, target):
     rho0 = math.sqrt(lo * hi)
     G = orc.gather(params, box, syn.uniform_gas(box, rho0), one(*pos, M_ej, e=E_sn))[:, 0]
     assert G[6] == pytest.approx(target, rel=1e-9)
-    nH = (rho0 * Vsnr + M_ej) / Vsnr
+    nH = (rho0 * Vsnr + M_ej) / (mu_H * Vsnr)
     assert G[5] == pytest.approx(nH, rel=1e-12)
     if target <= 0.027:
         assert G[11] == 0 and G[7] == 0.0
@@ -694,7 +724,27 @@ def test_membership_ties_are_outside(orc, rK):
             assert [c for c in brute_members(box, x, y, z, rK + 1e-9) if c not in want]
 
 
-@pytest.mark.parametrize("n,g,rK,seed", [(5, 2, 2.0, 1), (4, 3, 2.5, 2), (7, 4, 4.0, 3), (6, 2, 1.5, 4)])
+@pytest.mark.parametrize("rK", [1.7, 2.7, 3.6])
+def test_membership_reaches_ceil_rK_cells_away(orc, rK):
+    """With a fractional part of r_K above 1/2, a cell ceil(r_K) cells from the
+    host cell can be inside the kernel: offset o qualifies along x when
+    o + 1/2 - f < r_K, f the particle's position within its cell.  A particle
+    at f = 0.95 (y, z on centres) reaches it on the +x side, as a scan of the
+    whole box finds."""
+    box = syn.Box((12, 12, 12), 4)
+    params = syn.feedback_params(r_K=rK, subsample=2)
+    x, y, z = 5.95, 6.5, 4.5
+    ijk, _ = orc.kernel_of(params, box, x, y, z)
+    want = brute_members(box, x, y, z, rK)
+    assert {tuple(c) for c in ijk} == want
+    assert (5 + math.ceil(rK), 6, 4) in want
+
+
+# r_K = 2.7: cells ceil(r_K) away can lie inside (an offset o qualifies when
+# o < r_K - 1/2 + f, f the position within the host cell), which half-integer
+# radii never show
+@pytest.mark.parametrize("n,g,rK,seed", [(5, 2, 2.0, 1), (4, 3, 2.5, 2), (7, 4, 4.0, 3), (6, 2, 1.5, 4),
+                                         (5, 3, 2.7, 5)])
 def test_membership_and_fold_brute_force(orc, n, g, rK, seed):
     """Every (particle, buffer cell) pair found by scanning the whole padded
     box equals the oracle's kernel; after Step 2 every valid cell holds the sum
