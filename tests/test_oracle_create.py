@@ -141,3 +141,19 @@ def test_peaks_and_kernels():
     cnt, new = oracle.create_sinks(params, box, st.copy(), box.empty(0.0))
     cells = set(zip(new["x"] - 0.5, new["y"] - 0.5, new["z"] - 0.5))
     assert (4.0, 4.0, 4.0) not in cells and (6.0, 4.0, 4.0) not in cells and (12.0, 4.0, 4.0) in cells
+    # two peaks exactly r_K = 4 cells apart: neither lies within r_K of the
+    # other (the strict "< r_K" of kernel membership), so both
+    box, st = _state(1, n, peaks=[((4, 4, 4), 40.0), ((8, 4, 4), 50.0)])
+    cnt, new = oracle.create_sinks(params, box, st.copy(), box.empty(0.0))
+    cells = set(zip(new["x"] - 0.5, new["y"] - 0.5, new["z"] - 0.5))
+    assert {(4.0, 4.0, 4.0), (8.0, 4.0, 4.0)} <= cells
+    # peaks at the two faces of the x axis, one cell apart through the face:
+    # on a periodic axis the higher one only; on a non-periodic axis nothing
+    # lies beyond the face, both are maxima
+    box, st = _state(1, n, peaks=[((0, 4, 4), 40.0), ((15, 4, 4), 50.0)])
+    cnt, new = oracle.create_sinks(params, box, st.copy(), box.empty(0.0))
+    cells = set(zip(new["x"] - 0.5, new["y"] - 0.5, new["z"] - 0.5))
+    assert (15.0, 4.0, 4.0) in cells and (0.0, 4.0, 4.0) not in cells
+    cnt, new = oracle.create_sinks(params, box, st.copy(), box.empty(0.0), periodic=(0, 1, 1))
+    cells = set(zip(new["x"] - 0.5, new["y"] - 0.5, new["z"] - 0.5))
+    assert {(0.0, 4.0, 4.0), (15.0, 4.0, 4.0)} <= cells

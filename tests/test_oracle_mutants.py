@@ -236,6 +236,42 @@ MUTANTS = [
     ("v_COM divided by the gas mass alone",
      "    for (int a = 0; a < 3; a++) vc[a] = (sp[a] * V + pe[a]) / Msnr;",
      "    for (int a = 0; a < 3; a++) vc[a] = (sp[a] * V + pe[a]) / Mgas;"),
+    ("supernova energy row without the v_COM . p_rad term",
+     "    dU[4] = fma(w, e, fma(vc[2], pr[2], fma(vc[1], pr[1], vc[0] * pr[0])));",
+     "    dU[4] = w * e;"),
+    ("radial direction not guarded at the particle's own cell centre",
+     "    double s = c->d2 > 0.0 ? (w * Pv) / dist : 0.0;",
+     "    double s = (w * Pv) / dist;"),
+    ("accretion removal takes the smaller of K w and rho - rho_Tr",
+     "    double a = bh >= tr ? bh : tr;",
+     "    double a = bh <= tr ? bh : tr;"),
+    ("omega over S^2 sub-points",
+     "    return (double)cnt / (double)(S * S * S);",
+     "    return (double)cnt / (double)(S * S);"),
+    ("Eq. lambda's factor applied to the energy change too",
+     "        eta[0] = 1.0; eta[1] = l; eta[2] = l; eta[3] = l; eta[4] = 1.0;",
+     "        eta[0] = 1.0; eta[1] = l; eta[2] = l; eta[3] = l; eta[4] = l;"),
+    ("Eq. lambda's factor applied to the density change too",
+     "        eta[0] = 1.0; eta[1] = l; eta[2] = l; eta[3] = l; eta[4] = 1.0;",
+     "        eta[0] = l; eta[1] = l; eta[2] = l; eta[3] = l; eta[4] = 1.0;"),
+    ("ghost fold misses the outermost ghost layer",
+     "                            if (gi < -g || gi >= nx + g || gj < -g || gj >= ny + g || gk < -g || gk >= nz + g) continue;",
+     "                            if (gi <= -g || gi >= nx + g || gj <= -g || gj >= ny + g || gk <= -g || gk >= nz + g) continue;"),
+    ("App. A.1 rounding drops one bit more than N_bit",
+     "    if (nbit > 0) bits &= ~((((uint64_t)1) << nbit) - 1);",
+     "    if (nbit > 0) bits &= ~((((uint64_t)1) << (nbit + 1)) - 1);"),
+    ("created sink placed at the cell corner",
+     "                    x[n] = (double)i + 0.5;",
+     "                    x[n] = (double)i;"),
+    ("sink creation's local maximum wraps across a non-periodic face",
+     "                            if (a < 0 || a >= nx) { if (!S->periodic[0]) continue; a = (a + nx) % nx; }",
+     "                            if (a < 0 || a >= nx) { a = (a + nx) % nx; }"),
+    ("sink creation's local maximum includes cells exactly r_K away",
+     "                            if (!(d2 < r2)) continue;\n                            int a = i + ox",
+     "                            if (!(d2 <= r2)) continue;\n                            int a = i + ox"),
+    ("created sink's cell keeps its energy density instead of its specific energy",
+     "                    S->u[(int64_t)4 * S->fstride + c] = rtr * es;",
+     "                    S->u[(int64_t)4 * S->fstride + c] = U[4];"),
     ("Eq. lambda keeps the whole momentum change when the quadratic has no real root",
      "    if (!(disc >= 0.0)) { *noroot = 1; return 0.0; }",
      "    if (!(disc >= 0.0)) { *noroot = 1; return 1.0; }"),
