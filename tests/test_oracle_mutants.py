@@ -18,8 +18,11 @@ import pytest
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 SRC = os.path.join(ROOT, "oracle", "pmp_oracle.c")
 DUAL = os.path.join(ROOT, "oracle", "dual.py")
+# The last file checks the one-by-one evaluation that gives the expected
+# values of the full-size GPU tests against the whole cycle.
 PINS = ["tests/test_oracle_pins.py", "tests/test_oracle_create.py", "tests/test_oracle_extra.py",
-        "tests/test_oracle_mass.py", "tests/test_oracle_batch.py", "tests/test_oracle_repro.py"]
+        "tests/test_oracle_mass.py", "tests/test_oracle_batch.py", "tests/test_oracle_repro.py",
+        "tests/test_oracle_one_by_one.py"]
 
 # (name, the original text, its mutated form); the original occurs once.
 # Equivalent mutants are left out: e.g. folding ghosts of a non-periodic axis
@@ -272,6 +275,18 @@ MUTANTS = [
     ("created sink's cell keeps its energy density instead of its specific energy",
      "                    S->u[(int64_t)4 * S->fstride + c] = rtr * es;",
      "                    S->u[(int64_t)4 * S->fstride + c] = U[4];"),
+    ("one-by-one evaluation misses the particles R cells below a cell",
+     "        lo[a] = b[a] - R < 0 ? 0 : b[a] - R;",
+     "        lo[a] = b[a] - R + 1 < 0 ? 0 : b[a] - R + 1;"),
+    ("one-by-one fold adds the cell itself instead of its image",
+     "                int st = deposit_at(P, S, p, bins, kc, gi, gj, gk, v, av);",
+     "                int st = deposit_at(P, S, p, bins, kc, i, j, k, v, av);"),
+    ("one-by-one state update without eta",
+     "            out_new[NF * t + f] = zero ? U[f] : U[f] + eta[f] * D[f];",
+     "            out_new[NF * t + f] = zero ? U[f] : U[f] + D[f];"),
+    ("one-by-one Step 4 takes eta from the unfolded buffer",
+     "            st = folded_at(P, S, p, bins, g, kc2, kc[q].wi, kc[q].wj, kc[q].wk, D, A);",
+     "            st = deposit_at(P, S, p, bins, kc2, kc[q].wi, kc[q].wj, kc[q].wk, D, A);"),
     ("Eq. lambda keeps the whole momentum change when the quadratic has no real root",
      "    if (!(disc >= 0.0)) { *noroot = 1; return 0.0; }",
      "    if (!(disc >= 0.0)) { *noroot = 1; return 1.0; }"),
