@@ -287,6 +287,15 @@ MUTANTS = [
     ("one-by-one Step 4 takes eta from the unfolded buffer",
      "            st = folded_at(P, S, p, bins, g, kc2, kc[q].wi, kc[q].wj, kc[q].wk, D, A);",
      "            st = deposit_at(P, S, p, bins, kc2, kc[q].wi, kc[q].wj, kc[q].wk, D, A);"),
+    ("batched state ghost fill copies face ghosts only",
+     "                    if (i >= 0 && i < M.n[0] && j >= 0 && j < M.n[1] && k >= 0 && k < M.n[2]) continue;",
+     "                    if ((i < 0 || i >= M.n[0]) + (j < 0 || j >= M.n[1]) + (k < 0 || k >= M.n[2]) != 1) continue;"),
+    ("batched Step 4 takes eta at a ghost image from the unfolded ghost",
+     "            batch_fill_ghosts_n(T, owned, bcopy);\n",
+     ""),
+    ("batched limiter counts keep only the last patch's",
+     "            tot[0] += c2[0];",
+     "            tot[0] = c2[0];"),
     ("Eq. lambda keeps the whole momentum change when the quadratic has no real root",
      "    if (!(disc >= 0.0)) { *noroot = 1; return 0.0; }",
      "    if (!(disc >= 0.0)) { *noroot = 1; return 1.0; }"),
