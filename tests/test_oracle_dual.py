@@ -69,6 +69,28 @@ def test_dual_tangent_matches_central_differences(orc, field):
         assert fd == pytest.approx(want, rel=2e-6, abs=1e-9 * (abs(want) + 1e-3))
 
 
+def test_dual_tangent_vanishes_where_the_limiter_acts(orc):
+    """The adjoint's definition: eta is held fixed and a cell where the
+    limiter acts passes no tangent.  With every other cell marked as limited,
+    the tangent is exactly zero there and unchanged elsewhere; the values do
+    not depend on the mask."""
+    from oracle import dual
+
+    box, state, parts = _case(seed=23, count=4)
+    params = syn.feedback_params()
+    rng = np.random.default_rng(6)
+    tang = {k: rng.standard_normal(len(parts["x"])) for k in FIELDS}
+    full = np.ones(box.n[::-1], bool)
+    k, j, i = np.indices(box.n[::-1])
+    mask = (i + j + k) % 2 == 0
+    val1, tan1 = dual.pass_tangent(orc, params, box, state, parts, tang, full)
+    val2, tan2 = dual.pass_tangent(orc, params, box, state, parts, tang, mask)
+    assert np.count_nonzero(tan1[:, ~mask]) > 20
+    assert np.all(tan2[:, ~mask] == 0.0)
+    assert np.array_equal(tan2[:, mask], tan1[:, mask])
+    assert np.array_equal(val1, val2)
+
+
 def test_fourth_order_differences_agree_with_the_dual_tangents_at_1e8(orc):
     """The finite-difference procedure of the GPU adjoint test
     (helpers.fd_derivative) against the dual-number tangents on a clustered

@@ -386,6 +386,15 @@ DUAL_MUTANTS = [
     ("ST momentum without the ejecta energy's tangent",
      "prad = dsqrt(2.0 * m * params[\"eps_K\"] * E)",
      "prad = dsqrt(2.0 * m * params[\"eps_K\"] * E.v)"),
+    ("tangent passed through cells where the limiter acts",
+     "                if passmask[c]:\n                    tan[(f,) + c] += dU[f].t",
+     "                tan[(f,) + c] += dU[f].t"),
+    ("ejecta kinetic energy without the 1/2",
+     "Ekin = (pe[0] * pe[0] + pe[1] * pe[1] + pe[2] * pe[2]) / (2.0 * m)",
+     "Ekin = (pe[0] * pe[0] + pe[1] * pe[1] + pe[2] * pe[2]) / m"),
+    ("power derivative with the exponent not lowered",
+     "Dual(r, e * a.v ** (e - 1.0) * a.t)",
+     "Dual(r, e * a.v ** e * a.t)"),
     ("cell offset tangent dropped (positions carry no derivative)",
      "d = [(float(cc) + 0.5) - xx for cc, xx in zip((i, j, k), xs)]",
      "d = [(float(cc) + 0.5) - Dual(xx.v) for cc, xx in zip((i, j, k), xs)]"),
