@@ -47,6 +47,51 @@ def test_gathered_rows_without_gpu(lib):
     assert lib.pmp_gathered_rows(0) == 12 and lib.pmp_gathered_rows(1) == 8 and lib.pmp_gathered_rows(7) == 0
 
 
+C_CALLER = r"""
+#include "pmp.h"
+#include <stdio.h>
+
+int main(void)
+{
+    if (pmp_gathered_rows(PMP_KIND_FEEDBACK) != 12 || pmp_gathered_rows(PMP_KIND_SINK) != 8) return 2;
+    pmp_params p = {0};
+    p.kind = PMP_KIND_FEEDBACK;
+    p.subsample = 4;
+    p.r_K = 0.5; /* below the allowed range: rejected before any device work */
+    p.gamma = 5.0 / 3.0;
+    p.A_sf = 30.0;
+    p.A_p = 5.0;
+    p.mu_H = 1.0;
+    p.RM_ej = 0.027;
+    p.RM_st = 1.0;
+    p.eps_K = 0.28;
+    pmp_ctx *ctx = (pmp_ctx *)&p; /* must come back NULL */
+    if (pmp_create(&ctx, &p, NULL) != PMP_ERR_ARG || ctx != NULL) return 3;
+    pmp_destroy(NULL);
+    puts("ok");
+    return 0;
+}
+"""
+
+
+def test_header_compiles_as_c_and_the_library_links_from_c(lib, tmp_path):
+    """A caller written in C11 (no C++, no Python) includes only pmp.h, links
+    libpmp.so and makes calls that need no GPU."""
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if not cc:
+        pytest.skip("no C compiler")
+    import subprocess
+
+    src = tmp_path / "caller.c"
+    src.write_text(C_CALLER)
+    libdir = os.path.dirname(lib._name)
+    exe = tmp_path / "caller"
+    subprocess.run([cc, "-std=c11", "-Wall", "-Wextra", "-pedantic", "-Werror", "-I", os.path.join(ROOT, "include"),
+                    str(src), "-L", libdir, "-lpmp", "-Wl,-rpath," + libdir, "-o", str(exe)], check=True)
+    r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=60)
+    assert r.returncode == 0 and r.stdout.strip() == "ok", (r.returncode, r.stdout, r.stderr)
+
+
 def test_binding_fails_loudly_without_the_library(tmp_path, monkeypatch):
     """No CPU fallback: with libpmp.so absent, the first call raises instead
     of computing anything another way."""
