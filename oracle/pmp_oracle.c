@@ -1130,7 +1130,6 @@ static int deposit_at(const or_params *P, const or_mesh *S, const or_particles *
     int R = stencil_halfwidth(P->r_K);
     int64_t *cand;
     int64_t nc = candidates(S, bins, R, bi, bj, bk, &cand);
-    int rows = or_gathered_rows(P->kind);
     double G[MAX_ROWS];
     int status = OR_OK;
     for (int f = 0; f < NF; f++) { out[f] = 0.0; absout[f] = 0.0; }
@@ -1145,7 +1144,6 @@ static int deposit_at(const or_params *P, const or_mesh *S, const or_particles *
         kcell c = kc[hit];
         int st = gather_one(P, S, p, s, kc, G, 1);
         if (st && !status) status = st;
-        (void)rows;
         double w = cell_fraction(P, &c, x, y, z);
         if (w == 0.0) continue;
         double U[NF], dU[NF];

@@ -85,7 +85,7 @@ def test_profiled_row_reads_the_binding_counters(monkeypatch):
 
 def test_cell_pass_hbm_rates():
     box = _box()
-    km = {"fb_apply": (1.0, 5.2), "sink_apply": (1.0, 7.2), "fb_zero": (1.0, 0.86)}
+    km = {"fb_apply": (1.0, 5.2), "sink_apply": (1.0, 7.2), "fb_zero": (1.0, 0.86), "sink_cell_records": (1.0, 4.4)}
     out = bench.cell_pass_hbm(km, box, 6793.4)
     assert out["fb_apply"]["ms"] == pytest.approx(5.2)
     assert out["fb_apply"]["GB/s"] == pytest.approx(120 * 512 ** 3 / 5.2e-3 / 1e9, rel=1e-3)
@@ -93,6 +93,8 @@ def test_cell_pass_hbm_rates():
     assert out["sink_apply"]["bytes"] == 128 * 512 ** 3
     assert out["sink_apply"]["ms"] == pytest.approx(7.2)
     assert out["fb_zero"]["bytes"] == 40 * box.ncells_padded
+    # state read (40 B), then the 32-byte G and D records and three dense 8-byte arrays written
+    assert out["sink_cell_records"]["bytes"] == (40 + 32 + 32 + 3 * 8) * 512 ** 3
     assert "sink_spread" not in out  # a pass that was not timed is left out
 
 
