@@ -1171,8 +1171,7 @@ template <int R, bool FB>
 cudaError_t launch_persistent(pmp_batch *b, const BArgs &a, cudaStream_t st)
 {
     auto kern = pmp::k_batch_persistent<R, FB>;
-    cudaLaunchConfig_t cfg;
-    std::memset(&cfg, 0, sizeof(cfg));
+    cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)b->grid);
     cfg.blockDim = dim3(pmp::kThreads);
     cfg.dynamicSmemBytes = b->smem;
