@@ -153,10 +153,14 @@ pmp_status pmp_partition_sfc(int32_t n_patches, const int32_t *pos, const int64_
         const long double mid = acc + 0.5L * (long double)cost[p];
         int want = (int)(mid * n_ranks / total);
         if (want > n_ranks - 1) want = n_ranks - 1;
+        if (want < r) want = r;
+        // no rank skipped: a patch that carries more than 1 / n_ranks of the
+        // cost would otherwise carry the cut past the next rank
+        const int next = i == 0 ? 0 : r + 1;
+        if (want > next) want = next;
         // leave at least one patch for each later rank
         const int left = n_patches - i;
         if (n_ranks - want > left) want = n_ranks - left;
-        if (want < r) want = r;
         r = want;
         rank_of[p] = r;
         acc += (long double)cost[p];

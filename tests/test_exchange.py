@@ -66,6 +66,23 @@ def test_partition_follows_the_morton_curve_and_balances_cost():
         share = sum(cost) / n
         loads = [sum(c for c, r in zip(cost, rank_of) if r == k) for k in range(n)]
         assert max(loads) <= share + max(cost)
+        # each cut sits at the patch boundary nearest to k/n of the total:
+        # between the two patches whose cost midpoints straddle it
+        c = [cost[p] for p in order]
+        mids = np.cumsum(c) - 0.5 * np.asarray(c, dtype=float)
+        for k in range(1, n):
+            s = ranks.index(k)
+            assert mids[s - 1] < k * share <= mids[s], (n, k)
+
+
+def test_partition_leaves_a_patch_for_every_rank():
+    """A patch that carries most of the cost takes one rank; the ranks after
+    it still get a patch each while there are patches left."""
+    pos = [(0, 0, 0), (1, 0, 0), (0, 1, 0), (1, 1, 0), (0, 0, 1), (1, 0, 1)]
+    for cost, n in (([1000, 1, 1, 1], 4), ([1, 1000, 1, 1, 1, 1], 5), ([1, 1, 1, 1, 1, 5000], 3)):
+        rank_of = xch.partition(pos[:len(cost)], cost, n)
+        ranks = list(rank_of)  # Morton order is index order here
+        assert ranks == sorted(ranks) and set(ranks) == set(range(n)), (cost, n, ranks)
 
 
 @pytest.mark.parametrize("n_ranks", [2, 3, 4])
@@ -97,6 +114,34 @@ def test_plans_send_what_the_peers_receive(n_ranks):
                     assert pr.local["global_id"][a["patch"]] == ps.local["global_id"][b["patch"]]
                     assert a["lo"] == b["lo"] and a["hi"] == b["hi"]
                     assert a["offset"] - base_m == b["offset"] - base_t
+
+
+@pytest.mark.parametrize("n_ranks", [2, 3, 4])
+def test_plans_send_each_needed_box_once(n_ranks):
+    """A plan moves no more than the pass needs: STATE and FOLDED regions lie
+    in a patch's valid cells, GHOST regions in its ghost shell only, and no
+    box appears twice in a list."""
+    batch, _, _, first = _workload("feedback")
+    _, plans = _plans(batch, first, n_ranks)
+    seen = 0
+    for pr in plans:
+        for kind in (xch.STATE, xch.GHOST, xch.FOLDED):
+            for side in (0, 1):
+                regs = pr.regions[(kind, side)]
+                keys = [(x["peer"], x["patch"], tuple(x["lo"]), tuple(x["hi"])) for x in regs]
+                assert len(keys) == len(set(keys)), (kind, side)
+                for x in regs:
+                    n = [int(v) for v in pr.local["dims"][x["patch"]]]
+                    lo, hi = list(x["lo"]), list(x["hi"])
+                    assert all(l < h for l, h in zip(lo, hi))
+                    inside = [0 <= l and h <= na for l, h, na in zip(lo, hi, n)]
+                    if kind == xch.GHOST:
+                        assert not all(inside), "a GHOST region reaches into valid cells"
+                        assert all(lo[a] >= n[a] or hi[a] <= 0 or inside[a] for a in range(3))
+                    else:
+                        assert all(inside), "a STATE or FOLDED region reaches into ghost cells"
+                    seen += 1
+    assert seen > 0
 
 
 def _compare(orc, kind, batch, state, parts, first, ranks, rank_of):
