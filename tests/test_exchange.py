@@ -116,12 +116,18 @@ def test_plans_send_what_the_peers_receive(n_ranks):
                     assert a["offset"] - base_m == b["offset"] - base_t
 
 
-@pytest.mark.parametrize("n_ranks", [2, 3, 4])
-def test_plans_send_each_needed_box_once(n_ranks):
+@pytest.mark.parametrize("n_ranks,tiny", [(2, False), (3, False), (4, False), (2, True)])
+def test_plans_send_each_needed_box_once(n_ranks, tiny):
     """A plan moves no more than the pass needs: STATE and FOLDED regions lie
     in a patch's valid cells, GHOST regions in its ghost shell only, and no
-    box appears twice in a list."""
-    batch, _, _, first = _workload("feedback")
+    box appears twice in a list.  `tiny`: two 4-cell patches with 4 ghost
+    cells side by side, where a neighbour's boxes for offsets -1, 0 and +1
+    along an axis coincide."""
+    if tiny:
+        _, batch, _ = mr.small_batch(1, supergrid=(2, 1, 1), edges=(4,), g=4)
+        first = np.zeros(batch.np + 1, dtype=np.int64)
+    else:
+        batch, _, _, first = _workload("feedback")
     _, plans = _plans(batch, first, n_ranks)
     seen = 0
     for pr in plans:
