@@ -236,12 +236,17 @@ pmp_status make_box(const pmp_mesh *m, Box *b)
     return PMP_OK;
 }
 
+// True when the byte ranges of two meshes' data intersect: five fields
+// field_stride apart, the last one ending after its padded cells.  Both
+// meshes have passed make_box.
 bool overlaps(const pmp_mesh *a, const pmp_mesh *b)
 {
+    auto extent = [](const pmp_mesh *m) {
+        const size_t cells = (size_t)(m->n[0] + 2 * m->ng) * (size_t)(m->n[1] + 2 * m->ng) * (size_t)(m->n[2] + 2 * m->ng);
+        return sizeof(double) * (4 * (size_t)m->field_stride + cells);
+    };
     const char *a0 = reinterpret_cast<const char *>(a->data), *b0 = reinterpret_cast<const char *>(b->data);
-    const char *a1 = a0 + sizeof(double) * (size_t)(4 * a->field_stride + 1);
-    const char *b1 = b0 + sizeof(double) * (size_t)(4 * b->field_stride + 1);
-    return a0 < b1 && b0 < a1;
+    return a0 < b0 + extent(b) && b0 < a0 + extent(a);
 }
 
 pmp_status check_params(const pmp_params *p)

@@ -99,6 +99,14 @@ def test_noalloc_rejects_a_state_that_overlaps_the_buffer(lib):
     assert _noalloc(lib, fb, m, _parts(10), _buf(data=FAKE + 8 * 1000)) == ARG  # inside the state's fields
     inside = _mesh((32, 32, 32), 4, data=FAKE_BUF + 8 * 64000 * 4)  # state inside the buffer's last field
     assert _noalloc(lib, fb, inside, _parts(10), _buf()) == ARG
+    # a state starting further into the buffer's last field, and a buffer
+    # starting inside the state's last field: each shares cells with the other
+    inside = _mesh((32, 32, 32), 4, data=FAKE_BUF + 8 * (64000 * 4 + 100))
+    assert _noalloc(lib, fb, inside, _parts(10), _buf()) == ARG
+    assert _noalloc(lib, fb, m, _parts(10), _buf(data=FAKE + 8 * (64000 * 4 + 63999))) == ARG
+    # right after the state's last cell: no shared cell, so the call gets as
+    # far as its scratch limit (a count beyond it keeps it from enqueueing)
+    assert _noalloc(lib, fb, m, _parts(10_000_000), _buf(data=FAKE + 8 * 64000 * 5)) == WORKSPACE
 
 
 @pytest.mark.parametrize("what", ["misaligned state", "misaligned buffer", "periodic 2", "dx inf", "dx nan",
