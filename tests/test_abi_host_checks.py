@@ -110,7 +110,7 @@ def test_noalloc_rejects_a_state_that_overlaps_the_buffer(lib):
 
 
 @pytest.mark.parametrize("what", ["misaligned state", "misaligned buffer", "periodic 2", "dx inf", "dx nan",
-                                  "negative ng"])
+                                  "negative ng", "field stride one cell short", "no cells along an axis"])
 def test_noalloc_checks_its_meshes_as_the_context_calls_do(lib, what):
     fb = pmp._params_struct(syn.feedback_params())
     m, b = _mesh((32, 32, 32), 4), _buf()
@@ -125,6 +125,10 @@ def test_noalloc_checks_its_meshes_as_the_context_calls_do(lib, what):
         m.dx = b.dx = float("inf")
     elif what == "dx nan":
         m.dx = b.dx = float("nan")
+    elif what == "field stride one cell short":
+        b.field_stride = 40 * 40 * 40 - 1
+    elif what == "no cells along an axis":
+        m.n[0] = b.n[0] = 0
     else:
         m.ng = -1
     assert _noalloc(lib, fb, m, _parts(10), b) == ARG
