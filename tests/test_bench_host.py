@@ -50,6 +50,18 @@ def test_hbm_roofline_of_the_sink_apply():
     assert r["frac"] == pytest.approx(r["achieved"] / 6793.4, rel=1e-12)
 
 
+def test_hbm_roofline_of_the_zero_and_fold_passes():
+    box = _box()
+    ghosts = box.ncells_padded - 512 ** 3  # the 520^3 buffer less its valid cells
+    r = bench.roofline("fb_fold", 0.27, {"fb": 1, "sink": 1}, box, 1, 1, 6793.4, "measured")
+    assert r["bound"] == "hbm"
+    assert r["achieved"] == pytest.approx(120 * ghosts / 0.27e-3 / 1e9, rel=1e-12)
+    r = bench.roofline("sink_zero", 0.86, {"fb": 1, "sink": 1}, box, 1, 1, 6793.4, "measured")
+    assert r["achieved"] == pytest.approx(40 * 520 ** 3 / 0.86e-3 / 1e9, rel=1e-12)
+    out = bench.cell_pass_hbm({"sink_fold": (1.0, 0.27)}, box, 6793.4)
+    assert out["sink_fold"]["bytes"] == 120 * ghosts
+
+
 def test_traffic_is_reported_only_for_the_profiled_sources(monkeypatch):
     # the committed summary names the digest of the sources it was taken on
     import re
