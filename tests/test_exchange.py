@@ -255,8 +255,11 @@ def _gloo_rank(rank, world, port, kind, out_dir):
         dist.destroy_process_group()
 
 
+@pytest.mark.parametrize("world", [2, 3])
 @pytest.mark.parametrize("kind", KINDS)
-def test_two_gloo_ranks_equal_the_one_rank_pass(orc, kind, tmp_path):
+def test_gloo_ranks_equal_the_one_rank_pass(orc, kind, world, tmp_path):
+    """With three ranks each rank has two peers, whose messages sit at
+    different offsets of its send and receive buffers."""
     import socket
 
     import torch.multiprocessing as tmp
@@ -264,11 +267,11 @@ def test_two_gloo_ranks_equal_the_one_rank_pass(orc, kind, tmp_path):
     with socket.socket() as s:
         s.bind(("127.0.0.1", 0))
         port = s.getsockname()[1]
-    tmp.spawn(_gloo_rank, args=(2, port, kind, str(tmp_path)), nprocs=2, join=True)
+    tmp.spawn(_gloo_rank, args=(world, port, kind, str(tmp_path)), nprocs=world, join=True)
     batch, state, parts, first = _workload(kind)
-    rank_of, plans = _plans(batch, first, 2)
+    rank_of, plans = _plans(batch, first, world)
     ranks = []
-    for r in range(2):
+    for r in range(world):
         d = np.load(tmp_path / f"rank{r}.npz")
         rk = mr.OracleRank(orc, _params(kind), plans[r], batch, state, parts, first)
         rk.state, rk.eta, rk.gathered = d["state"], d["eta"], d["gathered"]
