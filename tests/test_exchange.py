@@ -258,8 +258,8 @@ def _gloo_rank(rank, world, port, kind, out_dir):
 @pytest.mark.parametrize("world", [2, 3])
 @pytest.mark.parametrize("kind", KINDS)
 def test_gloo_ranks_equal_the_one_rank_pass(orc, kind, world, tmp_path):
-    """With three ranks each rank has two peers, whose messages sit at
-    different offsets of its send and receive buffers."""
+    """With three ranks a rank exchanges with two peers at once, one message
+    per peer in each buffer."""
     import socket
 
     import torch.multiprocessing as tmp
