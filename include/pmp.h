@@ -475,8 +475,10 @@ void pmp_batch_destroy(pmp_batch *batch);
  * place in the super-grid), ties by index, then cut into runs of consecutive
  * patches of about equal total cost (cost[p] >= 1, e.g. valid cells plus a
  * weight per particle); rank_of (host, n entries) receives the rank of each
- * patch.  A patch costlier than a rank's share can leave a rank without
- * patches.  Host only; PMP_ERR_ARG on a bad argument. */
+ * patch.  Each cut falls at the patch boundary nearest to k / n_ranks of the
+ * total cost; no rank is skipped, and with at least as many patches as ranks
+ * every rank gets one (a patch costlier than a rank's share then moves the
+ * later cuts along the curve).  Host only; PMP_ERR_ARG on a bad argument. */
 pmp_status pmp_partition_sfc(int32_t n_patches, const int32_t *pos, const int64_t *cost, int32_t n_ranks,
                              int32_t *rank_of);
 
